@@ -1,0 +1,108 @@
+"""Plant plausible mistakes in a copy of the oracle and check that the pins catch each.
+
+Every mutation below is a one-line slip of the kind the pins exist for (a
+dropped term, an off-by-one, a wrong bit, a missing tag). The edited copy is
+compiled on the CPU into a temporary directory; the real oracle is untouched.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests import brute
+from tests.helpers import branch_only, instr_only, mem_only, random_trace
+from tests.test_oracle_pins import GOLDEN, INT_FIELDS
+
+MUTATIONS = {
+    "history_skips_one_more": ("for (size_t j = h; j < seq.size(); ++j)", "for (size_t j = h + 1; j < seq.size(); ++j)"),
+    "history_in_push_order": ("std::stable_sort(seq.begin(), seq.end(),", "if (0) std::stable_sort(seq.begin(), seq.end(),"),
+    "no_space_tag": ("uint64_t key = ((uint64_t)space << 61) | addr;", "uint64_t key = addr;"),
+    "skip_inner_off_by_one": ("while (j < n_acc && (all_keys[j] >> n) == g) ++j;",
+                              "while (j < n_acc && (all_keys[j] >> (n + 1)) == (g >> 1)) ++j;"),
+    "cover_strict": ("if ((unsigned __int128)den * cum >= (unsigned __int128)num * total) return k + 1;",
+                     "if ((unsigned __int128)den * cum > (unsigned __int128)num * total) return k + 1;"),
+    "median_upper_only": ("*med = 0.5 * ((double)*lo + (double)*hi);", "*med = (double)*hi;"),
+    "no_trailing_itb": ("    itb.push_back(kv.second.first);\n", "\n"),
+    "entropy_unweighted": ("acc.add(-p * std::log2(p));", "acc.add(-std::log2(p));"),
+    "store_bit_wrong": ("if (flags & 1u) write_keys.push_back(key);", "if (flags & 2u) write_keys.push_back(key);"),
+    "minsum_max": ("minsum += std::min(t, n - t);", "minsum += std::max(t, n - t);"),
+    "history_includes_outcome": ("for (size_t k = j - h; k < j; ++k)", "for (size_t k = j - h + 1; k <= j; ++k)"),
+    "barrier_counted_as_instruction": ("        itb.push_back(st.first);\n        st.first = 0;\n        ++barriers;",
+                                       "        itb.push_back(st.first);\n        st.first = 0;\n        ++barriers;\n        ++hist[0];"),
+    "work_items_memory_ignored": ("    work_items.insert(wi);\n    if (addr", "    if (addr"),
+}
+
+
+def _pins_pass(lib):
+    """A compact run of the oracle pins against the library at `lib`."""
+    def comp(tr, **kw):
+        return oracle.compute(tr, lib_path=lib, **kw)
+    try:
+        for seed in range(40):
+            rng = np.random.default_rng(10_000 + seed)
+            tr = random_trace(seed, n_mem=int(rng.integers(0, 64)), n_br=int(rng.integers(0, 64)),
+                              n_wi=int(rng.integers(1, 6)), n_runs=int(rng.integers(1, 8)),
+                              n_ops=int(rng.integers(8, 64)), addr_pool=int(rng.integers(1, 20)),
+                              n_sites=int(rng.integers(1, 4)), addr_span_bits=int(rng.integers(1, 16)))
+            h = int(rng.choice([1, 2, 3]))
+            o, b = comp(tr, history_len=h), brute.metrics(tr, history_len=h)
+            for f in INT_FIELDS:
+                if o[f] != b[f]:
+                    return False
+            if o["itb_median"] != b["itb_median"] or o["ipt_median"] != b["ipt_median"]:
+                return False
+            if list(o["opcode_hist"]) != list(b["opcode_hist"]):
+                return False
+            if max(abs(x - y) for x, y in zip(o["entropy"], b["entropy"])) > 1e-12:
+                return False
+        for ex in json.load(open(GOLDEN))["examples"]:
+            if "mem" in ex:
+                a, s, sp = zip(*ex["mem"])
+                tr = mem_only(list(a), list(s), list(sp))
+            elif "mem_repeat" in ex:
+                tr = mem_only([a for a, r in ex["mem_repeat"] for _ in range(r)])
+            elif "br" in ex:
+                st, w, t = zip(*ex["br"])
+                tr = branch_only(list(st), list(w), list(t))
+            elif "br_loop" in ex:
+                L, P = ex["br_loop"]["length"], ex["br_loop"]["period"]
+                tr = branch_only([ex["br_loop"]["site"]] * L, [0] * L, [int(j % P != P - 1) for j in range(L)])
+            else:
+                tr = instr_only([(w, ops) for w, ops in ex["runs"]])
+            o = comp(tr, history_len=ex.get("history_len", 16))
+            for k, v in ex["expect"].items():
+                if k == "entropy":
+                    if max(abs(o["entropy"][n] - v[n]) for n in range(11)) > 1e-6:
+                        return False
+                elif abs(o[k] - v) > 1e-12:
+                    return False
+        o = comp(synth.tiny())
+        if (o["itb_median"], o["branch_minsum"], o["branch_patterns"]) != (391.0, 240, 7936):
+            return False
+        for k, t in ((4, 0), (6, 2)):
+            o = comp(mem_only([(1 << 40) + (i << t) for i in range(1 << k) for _ in range(3)]))
+            if max(abs(o["entropy"][n] - max(0, k - max(0, n - t))) for n in range(11)) > 1e-12:
+                return False
+    except oracle.OracleInvalidInput:
+        return False
+    return True
+
+
+def test_unmodified_oracle_passes(tmp_path):
+    lib = oracle.build_variant(oracle.source(), str(tmp_path), "clean")
+    assert _pins_pass(lib)
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_is_caught(name, tmp_path):
+    old, new = MUTATIONS[name]
+    src = oracle.source()
+    assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    lib = oracle.build_variant(src.replace(old, new), str(tmp_path), name)
+    assert not _pins_pass(lib), f"pins did not catch planted mistake {name}"

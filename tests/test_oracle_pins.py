@@ -1,0 +1,219 @@
+"""Pins for the CPU oracle against things other than itself.
+
+* brute force: an independent pure-Python restatement (tests/brute.py) on
+  hundreds of random tiny traces over small alphabets;
+* closed forms from the metric definitions (Table I, Sec. III);
+* hand-worked examples stored in tests/golden/hand_examples.json;
+* invariants that hold at any size;
+* the tiny workload's instruction and branch closed forms.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from tests import brute
+from tests.helpers import branch_only, instr_only, mem_only, random_trace
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "hand_examples.json")
+INT_FIELDS = ["total_instructions", "unique_opcodes", "opcode_cover", "work_items", "barriers",
+              "itb_count", "itb_min", "itb_max", "itb_median_lo", "itb_median_hi",
+              "ipt_count", "ipt_min", "ipt_max", "ipt_median_lo", "ipt_median_hi",
+              "total_reads", "total_writes", "footprint", "footprint_cover", "unique_reads", "unique_writes",
+              "branch_events", "branch_sites", "branch_cover", "branch_patterns", "branch_minsum"]
+
+
+def _compare(o, b):
+    for f in INT_FIELDS:
+        assert o[f] == b[f], f
+    assert o["itb_median"] == b["itb_median"]
+    assert o["ipt_median"] == b["ipt_median"]
+    assert list(o["opcode_hist"]) == list(b["opcode_hist"])
+    for n in range(11):
+        assert abs(o["entropy"][n] - b["entropy"][n]) <= 1e-12, n
+    assert abs(o["albe"] - b["albe"]) <= 1e-15
+
+
+@pytest.mark.parametrize("seed", range(120))
+def test_oracle_matches_brute_force(seed):
+    rng = np.random.default_rng(10_000 + seed)
+    kw = dict(n_mem=int(rng.integers(0, 64)), n_br=int(rng.integers(0, 64)), n_wi=int(rng.integers(1, 6)),
+              n_runs=int(rng.integers(1, 8)), n_ops=int(rng.integers(8, 64)), addr_pool=int(rng.integers(1, 20)),
+              n_sites=int(rng.integers(1, 4)), n_opcodes=int(rng.integers(1, 7)),
+              addr_span_bits=int(rng.integers(1, 16)))
+    tr = random_trace(seed, **kw)
+    h = int(rng.choice([1, 2, 3, 4, 16]))
+    mask = int(rng.choice([0xF, 0x1, 0x3, 0xA]))
+    o = oracle.compute(tr, history_len=h, space_mask=mask)
+    b = brute.metrics(tr, history_len=h, space_mask=mask)
+    _compare(o, b)
+
+
+@pytest.mark.parametrize("num,den", [(9, 10), (1, 2), (1, 1), (1, 3)])
+def test_oracle_cover_fraction_brute(num, den):
+    for seed in range(20):
+        tr = random_trace(500 + seed, n_mem=50, addr_pool=9)
+        o = oracle.compute(tr, cover_num=num, cover_den=den)
+        b = brute.metrics(tr, cover_num=num, cover_den=den)
+        _compare(o, b)
+
+
+def test_golden_hand_examples():
+    data = json.load(open(GOLDEN))
+    for ex in data["examples"]:
+        if "mem" in ex:
+            a, s, sp = zip(*ex["mem"])
+            tr = mem_only(list(a), list(s), list(sp))
+        elif "mem_repeat" in ex:
+            addrs = [a for a, r in ex["mem_repeat"] for _ in range(r)]
+            tr = mem_only(addrs)
+        elif "br" in ex:
+            st, w, t = zip(*ex["br"])
+            tr = branch_only(list(st), list(w), list(t))
+        elif "br_loop" in ex:
+            L, P = ex["br_loop"]["length"], ex["br_loop"]["period"]
+            tr = branch_only([ex["br_loop"]["site"]] * L, [0] * L, [int(j % P != P - 1) for j in range(L)])
+        else:
+            tr = instr_only([(w, ops) for w, ops in ex["runs"]])
+        o = oracle.compute(tr, history_len=ex.get("history_len", 16))
+        for k, v in ex["expect"].items():
+            if k == "entropy":
+                for n in range(11):
+                    assert abs(o["entropy"][n] - v[n]) < 1e-6, (ex["name"], n)
+            elif isinstance(v, float):
+                assert abs(o[k] - v) < 1e-12, (ex["name"], k)
+            else:
+                assert o[k] == v, (ex["name"], k)
+        for n, formula in enumerate(ex.get("entropy_formula", [])):
+            exact = eval(formula, {"log2": math.log2})
+            assert abs(o["entropy"][n] - exact) < 1e-14, (ex["name"], n)
+
+
+@pytest.mark.parametrize("k,t", [(0, 0), (1, 0), (4, 0), (6, 2), (10, 3), (3, 5), (12, 0)])
+def test_entropy_aligned_uniform_closed_form(k, t):
+    """2^k addresses base + i*2^t, equally often: H_n = max(0, k - max(0, n - t))."""
+    base = 1 << 40
+    reps = 3
+    addrs = [base + (i << t) for i in range(1 << k) for _ in range(reps)]
+    o = oracle.compute(mem_only(addrs))
+    for n in range(11):
+        assert abs(o["entropy"][n] - max(0, k - max(0, n - t))) < 1e-12, n
+    assert o["footprint"] == 1 << k
+    assert o["footprint_cover"] == math.ceil(0.9 * (1 << k) - 1e-12)
+
+
+def test_single_address_zero_entropy():
+    o = oracle.compute(mem_only([12345] * 77, stores=[i % 2 for i in range(77)]))
+    assert o["entropy"] == [0.0] * 11
+    assert (o["footprint"], o["footprint_cover"], o["unique_reads"], o["unique_writes"]) == (1, 1, 1, 1)
+    assert (o["total_reads"], o["total_writes"]) == (39, 38)
+
+
+def test_empty_trace_all_zero():
+    o = oracle.compute(synth.Trace("empty"))
+    for f in INT_FIELDS:
+        assert o[f] == 0, f
+    assert o["entropy"] == [0.0] * 11 and o["albe"] == 0.0 and o["itb_median"] == 0.0
+    assert math.isnan(o["reread_ratio"]) and math.isnan(o["unique_rw_ratio"])
+
+
+def test_space_mask_filters_memory_only():
+    tr = mem_only([8, 8, 16], spaces=[0, 1, 1], wis=[0, 1, 2])
+    o = oracle.compute(tr, space_mask=0x1)
+    assert (o["footprint"], o["total_reads"], o["work_items"]) == (1, 1, 3)
+
+
+def test_branch_constant_and_alternating():
+    for h in (1, 2, 16):
+        for seq in ([1] * 100, [0] * 100, [j % 2 for j in range(100)]):
+            o = oracle.compute(branch_only([3] * 100, [0] * 100, seq), history_len=h)
+            assert o["branch_minsum"] == 0 and o["albe"] == 0.0
+            assert o["branch_patterns"] == 100 - h
+
+
+def test_branch_histories_are_per_site():
+    # two interleaved sites, each constant: per-site histories are pure
+    sites = [j % 2 for j in range(200)]
+    taken = [j % 2 for j in range(200)]
+    o = oracle.compute(branch_only(sites, [0] * 200, taken), history_len=4)
+    assert o["branch_minsum"] == 0 and o["branch_patterns"] == 2 * (100 - 4)
+
+
+def test_branch_fair_coin_bounds():
+    rng = np.random.default_rng(7)
+    n = 4000
+    o = oracle.compute(branch_only([1] * n, [0] * n, rng.integers(0, 2, n).tolist()), history_len=2)
+    assert 0.9 < o["albe"] <= 1.0
+
+
+def test_itb_barrier_every_25():
+    ops = []
+    for k in range(100):
+        ops.append(k % 8)
+        if k % 25 == 24:
+            ops.append(-1)
+    o = oracle.compute(instr_only([(5, ops)]))
+    assert (o["itb_count"], o["itb_min"], o["itb_max"], o["barriers"]) == (5, 0, 25, 4)
+    assert o["itb_median"] == 25.0 and o["ipt_median"] == 100.0
+
+
+def test_tiny_workload_closed_forms():
+    o = oracle.compute(synth.tiny())
+    # one run per work-item: 500 instructions, a barrier, then 282 (64 wi) or 281 (192 wi)
+    assert (o["itb_count"], o["itb_min"], o["itb_max"]) == (512, 281, 500)
+    assert (o["itb_median_lo"], o["itb_median_hi"], o["itb_median"]) == (282, 500, 391.0)
+    assert (o["ipt_min"], o["ipt_max"], o["ipt_median"]) == (781, 782, 781.0)
+    assert (o["total_instructions"], o["barriers"], o["work_items"]) == (200000, 256, 256)
+    # 15 loop sites x 16 periods with one unpredictable exit each; N' = 16 sites x (512 - 16)
+    assert (o["branch_minsum"], o["branch_patterns"], o["branch_sites"]) == (240, 16 * 496, 16)
+    assert o["total_reads"] + o["total_writes"] == 65536
+    # 4-byte aligned accesses: skipping 1 or 2 bits merges nothing
+    assert o["entropy"][0] == o["entropy"][1] == o["entropy"][2]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_invariants_medium(seed):
+    tr = synth.large(seed=seed, n_mem=30_000 + 777 * seed, n_br=9_000 + 13 * seed, n_wi=17, per_wi=300,
+                     zipf_distinct=1 << 14)
+    o = oracle.compute(tr)
+    N = o["total_reads"] + o["total_writes"]
+    assert N == tr.n_mem
+    H = o["entropy"]
+    for n in range(10):
+        assert H[n + 1] <= H[n] + 1e-12 and H[n] <= H[n + 1] + 1 + 1e-12
+    assert H[0] <= math.log2(o["footprint"]) + 1e-12
+    assert max(o["unique_reads"], o["unique_writes"]) <= o["footprint"] <= o["unique_reads"] + o["unique_writes"]
+    assert o["itb_count"] == o["barriers"] + 17
+    assert o["total_instructions"] == int(sum(o["opcode_hist"]))
+    assert 0.0 <= o["albe"] <= 1.0
+    coc = oracle.count_of_counts(tr.mem, 0)
+    assert sum(c * m for c, m in coc.items()) == N and sum(coc.values()) == o["footprint"]
+
+
+def test_memory_metrics_independent_of_event_order():
+    tr = synth.large(n_mem=20_000, n_br=0, n_wi=0, per_wi=1, zipf_distinct=1 << 12)
+    o1 = oracle.compute(tr)
+    perm = torch.randperm(tr.n_mem, generator=torch.Generator().manual_seed(3))
+    tr2 = synth.Trace("perm", mem=tr.mem[perm].contiguous())
+    o2 = oracle.compute(tr2)
+    for f in ["footprint", "footprint_cover", "unique_reads", "unique_writes", "total_reads", "total_writes"]:
+        assert o1[f] == o2[f]
+    assert max(abs(a - b) for a, b in zip(o1["entropy"], o2["entropy"])) < 1e-12
+
+
+def test_invalid_inputs_rejected():
+    with pytest.raises(oracle.OracleInvalidInput):
+        oracle.compute(mem_only([1 << 61]))
+    with pytest.raises(oracle.OracleInvalidInput):
+        oracle.compute(instr_only([(0, [9])], n_opcodes=8))
+    for h in (0, 32):
+        with pytest.raises(oracle.OracleInvalidInput):
+            oracle.compute(branch_only([0], [0], [1]), history_len=h)
+    assert oracle.compute(mem_only([(1 << 61) - 1]))["footprint"] == 1

@@ -1,0 +1,213 @@
+/*
+ * aiwc.h -- C ABI of a GB300-native reduction of one OpenCL kernel
+ * invocation's event traces to the architecture-independent workload
+ * characterization (AIWC) metrics of Johnston & Milthorpe (arXiv 1805.04207).
+ *
+ * The paper collects events inside an OpenCL simulator through per-
+ * instruction callbacks and reduces them when the kernel ends (Sec. V). This
+ * library replaces the callbacks with bulk pushes of already-collected event
+ * streams and performs the end-of-kernel reduction (Table I) on the GPU.
+ *
+ * Conventions for every entry point:
+ *   - Return value: an aiwc_status. Nothing aborts, traps or exits.
+ *   - Pointers flagged `on_device` are CUDA device pointers on the handle's
+ *     device; otherwise they are host pointers. Host data is copied (or fully
+ *     consumed) before the call returns. Device data must stay valid and
+ *     unmodified until the next aiwc_compute on that handle returns, because
+ *     work is queued on the handle's CUDA stream.
+ *   - All GPU work of a handle is ordered on the stream given in
+ *     aiwc_config.cuda_stream. The library owns all of its device scratch.
+ *   - After an error other than AIWC_EINVAL the handle answers AIWC_ESTATE
+ *     until aiwc_compute (which then resets it) or aiwc_destroy.
+ *     AIWC_EINVAL found inside event data is reported by aiwc_compute, which
+ *     still resets the handle for the next invocation.
+ *   - A handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef AIWC_H
+#define AIWC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- events */
+
+/* One memory access (Sec. V: memoryLoad / memoryStore / memoryAtomicLoad /
+ * memoryAtomicStore notifications). 16 bytes, little-endian.
+ *   addr       start address; must be < 2^61 (the 61-bit address domain).
+ *   work_item  id of the issuing work-item.
+ *   size       access size in bytes (carried, not used by any metric).
+ *   flags      bit 0: 1 = store (write), 0 = load (read);
+ *              bits 1-2: OpenCL address space (0 global, 1 local,
+ *              2 constant, 3 private); other bits ignored.
+ * An atomic read-modify-write is pushed as one load and one store. */
+typedef struct aiwc_mem_event {
+  uint64_t addr;
+  uint32_t work_item;
+  uint8_t size;
+  uint8_t flags;
+  uint16_t reserved;
+} aiwc_mem_event;
+
+/* One conditional-branch outcome (Sec. V, Listing 1: the taken / not-taken
+ * result recorded per branch location). 8 bytes.
+ *   site       id of the static branch (the paper keys branches by source
+ *              line; any 32-bit id works).
+ *   wi_taken   bits 0-30: work-item id; bit 31: 1 = taken. */
+typedef struct aiwc_branch_event {
+  uint32_t site;
+  uint32_t wi_taken;
+} aiwc_branch_event;
+
+/* Barrier marker in the 16-bit opcode stream (Sec. V: a barrier ends the
+ * running instructions-to-barrier tally). It is not counted as an
+ * instruction. */
+#define AIWC_BARRIER 0xFFFFu
+#define AIWC_ADDR_LIMIT (1ull << 61)
+#define AIWC_MAX_SKIP 10 /* local memory address entropy skips 1..10 bits (Sec. III) */
+
+typedef enum aiwc_status {
+  AIWC_OK = 0,
+  AIWC_EINVAL = 1,   /* invalid argument or invalid event data */
+  AIWC_ENOMEM = 2,   /* device memory or the HBM budget is exhausted */
+  AIWC_ECUDA = 3,    /* a CUDA call failed; see aiwc_last_error */
+  AIWC_ESTATE = 4,   /* handle unusable after an earlier error */
+  AIWC_ETIMEOUT = 5, /* a bounded device-side wait gave up */
+  AIWC_EAGAIN = 6    /* serving: not admitted now, retry later */
+} aiwc_status;
+
+/* ---------------------------------------------------------------- config */
+
+typedef struct aiwc_config {
+  int device;             /* CUDA device ordinal */
+  void* cuda_stream;      /* cudaStream_t for all work of the handle; NULL = legacy default stream */
+  uint32_t history_len;   /* branch history length, 1..31 (Sec. III fixes 16) */
+  uint32_t cover_num;     /* coverage fraction numerator (Table I "90%": 9) */
+  uint32_t cover_den;     /* coverage fraction denominator (10) */
+  uint32_t n_opcodes;     /* valid opcodes are 0..n_opcodes-1, n_opcodes <= 65535 */
+  uint32_t space_mask;    /* bit s set: address space s takes part in the memory metrics (0xF) */
+  uint32_t precision;     /* entropy finalisation: 0 = FP64, 1 = FP32 compensated sums */
+  uint32_t plan;          /* distinct-address counting: 0 = auto, 1 = sort, 2 = hash */
+  uint64_t max_work_items;/* work-item ids must be < this (sizes the work-item bitmap); 0 = 2^32 */
+  uint64_t hbm_budget;    /* bytes of device scratch the handle may hold; 0 = unlimited */
+} aiwc_config;
+
+/* Fills the paper's defaults: history 16, 90% coverage, all address spaces,
+ * 65535 opcodes, FP64, automatic plan, device 0, default stream. */
+void aiwc_config_default(aiwc_config* cfg);
+
+/* --------------------------------------------------------------- metrics */
+
+/* Table I metrics for one invocation (all integers exact).
+ * Readings where the paper is silent are stated per field. */
+typedef struct aiwc_metrics {
+  /* Compute (Table I): */
+  uint64_t total_instructions;  /* non-barrier instructions */
+  uint64_t unique_opcodes;      /* opcodes executed at least once */
+  uint64_t opcode_cover;        /* "Opcode": fewest opcodes covering cover_num/cover_den of instructions */
+  /* Parallelism (Table I): */
+  uint64_t work_items;          /* distinct work-item ids over all three streams */
+  uint64_t barriers;            /* barrier markers */
+  uint64_t itb_count, itb_min, itb_max, itb_median_lo, itb_median_hi;
+  double itb_median;            /* instructions to barrier; each work-item's final tally counts (implicit barrier) */
+  uint64_t ipt_count, ipt_min, ipt_max, ipt_median_lo, ipt_median_hi;
+  double ipt_median;            /* instructions per thread, over work-items of the instruction stream */
+  /* Memory (Table I): */
+  uint64_t total_reads, total_writes;
+  uint64_t footprint;           /* unique (address space, address) pairs */
+  uint64_t footprint_cover;     /* "90% Memory Footprint" */
+  uint64_t unique_reads, unique_writes;
+  double entropy[AIWC_MAX_SKIP + 1]; /* [0] global memory address entropy; [n] local entropy with n low bits skipped */
+  /* Control (Table I): */
+  uint64_t branch_events;
+  uint64_t branch_sites;        /* "Total Unique Branch Instructions" */
+  uint64_t branch_cover;        /* "90% Branch Instructions" */
+  uint64_t branch_patterns;     /* N': outcomes that have a full history */
+  uint64_t branch_minsum;       /* M = sum over history patterns of min(taken, not taken) */
+  double albe;                  /* average linear branch entropy = 2 M / N' */
+  /* Ratios as printed in Table I (IEEE division: x/0 gives inf or NaN). */
+  double unique_rw_ratio;       /* unique reads / unique writes */
+  double reread_ratio;          /* unique reads / total reads */
+  double rewrite_ratio;         /* unique writes / total writes */
+  /* In: optional caller buffer of n_opcodes counts (NULL to skip). */
+  uint64_t* opcode_hist;
+} aiwc_metrics;
+
+/* ------------------------------------------------------- single invocation */
+
+typedef struct aiwc_handle aiwc_handle;
+
+/* kernelBegin (Sec. V): creates the state of one invocation at a time.
+ * Errors: AIWC_EINVAL (cfg NULL or out of range), AIWC_ECUDA, AIWC_ENOMEM. */
+aiwc_status aiwc_create(const aiwc_config* cfg, aiwc_handle** out);
+
+/* Memory notifications (Sec. V) in bulk: n events, in any order (the memory
+ * metrics do not depend on event order). Invalid addresses are reported by
+ * aiwc_compute as AIWC_EINVAL. */
+aiwc_status aiwc_push_mem(aiwc_handle* h, const aiwc_mem_event* ev, size_t n, int on_device);
+
+/* Branch outcomes (Sec. III, Sec. V) in bulk. Each site's history is ordered
+ * by (work-item id, push order): events of one work-item must be pushed in
+ * program order; different work-items may interleave freely. */
+aiwc_status aiwc_push_branch(aiwc_handle* h, const aiwc_branch_event* ev, size_t n, int on_device);
+
+/* Instruction stream of one work-item (Sec. V: instructionExecuted), n
+ * opcodes in program order with AIWC_BARRIER markers. Successive pushes for
+ * the same work-item continue its stream. */
+aiwc_status aiwc_push_instr(aiwc_handle* h, uint32_t work_item, const uint16_t* ops, size_t n, int on_device);
+
+/* Bulk form of aiwc_push_instr: n_runs runs, run r covering
+ * ops[run_off[r] .. run_off[r] + run_len[r]) for work-item run_wi[r], in
+ * push order. All five arrays are on the same side (on_device). */
+aiwc_status aiwc_push_instr_runs(aiwc_handle* h, const uint32_t* run_wi, const uint64_t* run_off,
+                                 const uint64_t* run_len, size_t n_runs, const uint16_t* ops,
+                                 size_t n_ops, int on_device);
+
+/* kernelEnd (Sec. V): reduces everything pushed since the last compute to the
+ * Table I metrics, writes them to *out (and out->opcode_hist when non-NULL),
+ * then resets the handle for the next invocation. Blocks until done.
+ * Errors: AIWC_EINVAL (invalid event data: an address >= 2^61 or an opcode
+ * >= n_opcodes that is not AIWC_BARRIER, a run past its opcode array, a
+ * work-item >= max_work_items), AIWC_ECUDA, AIWC_ESTATE. */
+aiwc_status aiwc_compute(aiwc_handle* h, aiwc_metrics* out);
+
+/* Several invocations at once: outs[i] receives the metrics of hs[i], exactly
+ * as aiwc_compute(hs[i]) would. The stages of all handles are launched
+ * together (one launch per stage over every handle's data) and replayed as
+ * one CUDA graph when the same shapes repeat. All handles must share one
+ * device and stream. */
+aiwc_status aiwc_compute_batch(aiwc_handle* const* hs, size_t n, aiwc_metrics* outs);
+
+aiwc_status aiwc_destroy(aiwc_handle* h);
+
+/* Text of the last error on h (or of the last global error when h is NULL). */
+const char* aiwc_last_error(const aiwc_handle* h);
+
+/* Device bytes currently held by h. */
+uint64_t aiwc_device_bytes(const aiwc_handle* h);
+
+/* ----------------------------------------------------------- diagnostics */
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * handles). The paper has no counterpart; it exists so that callers can
+ * check which work ran on the GPU. */
+uint64_t aiwc_kernel_launches(void);
+
+/* Stage timing: when on, every push and aiwc_compute brackets its stages with
+ * CUDA events on the handle's stream (no extra synchronisation); after
+ * aiwc_compute returns, aiwc_stage_times reports the elapsed milliseconds of
+ * each stage of that invocation, summed over pushes. Stages, in order:
+ *   0 mem_ingest   1 branch_ingest  2 instr_runs    3 mem_sort
+ *   4 mem_levels   5 branch_sort    6 windows       7 pattern_sort
+ *   8 pattern_runs 9 run_sort      10 run_combine  11 finalize
+ * Returns the number of stages written (at most n); names may be NULL. */
+aiwc_status aiwc_set_stage_timing(aiwc_handle* h, int on);
+int aiwc_stage_times(const aiwc_handle* h, double* ms, const char** names, int n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AIWC_H */

@@ -52,10 +52,12 @@ class OracleInvalidInput(ValueError):
 
 def build(force: bool = False) -> str:
     """Compile the oracle into oracle/_build/liboracle.so (plain g++ -O2)."""
-    with _lock:
+    import fcntl
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    with _lock, open(os.path.join(_OUT_DIR, ".lock"), "w") as lk:
+        fcntl.flock(lk, fcntl.LOCK_EX)
         if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
             return _LIB_PATH
-        os.makedirs(_OUT_DIR, exist_ok=True)
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         subprocess.run(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", tmp, _SRC], check=True)
         os.replace(tmp, _LIB_PATH)

@@ -1,0 +1,189 @@
+"""GB300-native reduction of OpenCL kernel event traces to the AIWC metrics.
+
+Thin ctypes binding over ``libaiwc.so`` (C ABI in ``include/aiwc.h``). Every
+step of the reduction runs in the library's CUDA kernels; this module only
+marshals arguments. PyTorch is used for device memory and streams: tensors
+are passed by ``data_ptr()`` and streams by ``torch.cuda.Stream.cuda_stream``.
+
+Importing the package loads the library and raises if it has not been built
+(``python -m paper_1805_04207_gb300._build``); there is no other code path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import _build
+
+AIWC_OK, AIWC_EINVAL, AIWC_ENOMEM, AIWC_ECUDA, AIWC_ESTATE, AIWC_ETIMEOUT, AIWC_EAGAIN = range(7)
+STATUS_NAMES = {0: "AIWC_OK", 1: "AIWC_EINVAL", 2: "AIWC_ENOMEM", 3: "AIWC_ECUDA", 4: "AIWC_ESTATE",
+                5: "AIWC_ETIMEOUT", 6: "AIWC_EAGAIN"}
+AIWC_BARRIER = 0xFFFF
+MAX_SKIP = 10
+
+
+class aiwc_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("history_len", ctypes.c_uint32),
+                ("cover_num", ctypes.c_uint32), ("cover_den", ctypes.c_uint32), ("n_opcodes", ctypes.c_uint32),
+                ("space_mask", ctypes.c_uint32), ("precision", ctypes.c_uint32), ("plan", ctypes.c_uint32),
+                ("max_work_items", ctypes.c_uint64), ("hbm_budget", ctypes.c_uint64)]
+
+
+_U64 = ctypes.c_uint64
+_F64 = ctypes.c_double
+METRIC_FIELDS = [
+    ("total_instructions", _U64), ("unique_opcodes", _U64), ("opcode_cover", _U64),
+    ("work_items", _U64), ("barriers", _U64),
+    ("itb_count", _U64), ("itb_min", _U64), ("itb_max", _U64), ("itb_median_lo", _U64), ("itb_median_hi", _U64),
+    ("itb_median", _F64),
+    ("ipt_count", _U64), ("ipt_min", _U64), ("ipt_max", _U64), ("ipt_median_lo", _U64), ("ipt_median_hi", _U64),
+    ("ipt_median", _F64),
+    ("total_reads", _U64), ("total_writes", _U64), ("footprint", _U64), ("footprint_cover", _U64),
+    ("unique_reads", _U64), ("unique_writes", _U64),
+    ("entropy", _F64 * (MAX_SKIP + 1)),
+    ("branch_events", _U64), ("branch_sites", _U64), ("branch_cover", _U64), ("branch_patterns", _U64),
+    ("branch_minsum", _U64), ("albe", _F64),
+    ("unique_rw_ratio", _F64), ("reread_ratio", _F64), ("rewrite_ratio", _F64),
+    ("opcode_hist", ctypes.POINTER(ctypes.c_uint64)),
+]
+
+
+class aiwc_metrics(ctypes.Structure):
+    _fields_ = METRIC_FIELDS
+
+
+# Every entry point declared in include/aiwc.h: name -> (restype, argtypes).
+_VP = ctypes.c_void_p
+_SZ = ctypes.c_size_t
+_ST = ctypes.c_int
+SIGNATURES = {
+    "aiwc_config_default": (None, [ctypes.POINTER(aiwc_config)]),
+    "aiwc_create": (_ST, [ctypes.POINTER(aiwc_config), ctypes.POINTER(_VP)]),
+    "aiwc_push_mem": (_ST, [_VP, _VP, _SZ, ctypes.c_int]),
+    "aiwc_push_branch": (_ST, [_VP, _VP, _SZ, ctypes.c_int]),
+    "aiwc_push_instr": (_ST, [_VP, ctypes.c_uint32, _VP, _SZ, ctypes.c_int]),
+    "aiwc_push_instr_runs": (_ST, [_VP, _VP, _VP, _VP, _SZ, _VP, _SZ, ctypes.c_int]),
+    "aiwc_compute": (_ST, [_VP, ctypes.POINTER(aiwc_metrics)]),
+    "aiwc_compute_batch": (_ST, [ctypes.POINTER(_VP), _SZ, ctypes.POINTER(aiwc_metrics)]),
+    "aiwc_destroy": (_ST, [_VP]),
+    "aiwc_last_error": (ctypes.c_char_p, [_VP]),
+    "aiwc_device_bytes": (ctypes.c_uint64, [_VP]),
+    "aiwc_kernel_launches": (ctypes.c_uint64, []),
+    "aiwc_set_stage_timing": (_ST, [_VP, ctypes.c_int]),
+    "aiwc_stage_times": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_char_p),
+                                        ctypes.c_int]),
+}
+
+LIB_PATH = _build.LIB
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libaiwc.so is not built ({LIB_PATH}); run `python -m paper_1805_04207_gb300._build` "
+                      "(the AIWC reduction has no CPU fallback)")
+lib = ctypes.CDLL(LIB_PATH)
+for _name, (_res, _args) in SIGNATURES.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class AiwcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(status: int, handle=None):
+    if status != AIWC_OK:
+        raise AiwcError(status, (lib.aiwc_last_error(handle) or b"").decode())
+
+
+# ------------------------------------------------------------------ C names
+
+def aiwc_config_default(**overrides) -> aiwc_config:
+    cfg = aiwc_config()
+    lib.aiwc_config_default(ctypes.byref(cfg))
+    for k, v in overrides.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def aiwc_create(cfg: aiwc_config) -> int:
+    h = _VP()
+    _check(lib.aiwc_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h.value
+
+
+def aiwc_push_mem(h, ptr: int, n: int, on_device: bool) -> None:
+    _check(lib.aiwc_push_mem(h, ptr, n, int(on_device)), h)
+
+
+def aiwc_push_branch(h, ptr: int, n: int, on_device: bool) -> None:
+    _check(lib.aiwc_push_branch(h, ptr, n, int(on_device)), h)
+
+
+def aiwc_push_instr(h, work_item: int, ptr: int, n: int, on_device: bool) -> None:
+    _check(lib.aiwc_push_instr(h, work_item, ptr, n, int(on_device)), h)
+
+
+def aiwc_push_instr_runs(h, wi_ptr, off_ptr, len_ptr, n_runs, ops_ptr, n_ops, on_device: bool) -> None:
+    _check(lib.aiwc_push_instr_runs(h, wi_ptr, off_ptr, len_ptr, n_runs, ops_ptr, n_ops, int(on_device)), h)
+
+
+def _to_dict(m: aiwc_metrics) -> dict:
+    out = {}
+    for name, _ in METRIC_FIELDS:
+        if name == "opcode_hist":
+            continue
+        v = getattr(m, name)
+        out[name] = list(v) if name == "entropy" else v
+    return out
+
+
+def aiwc_compute(h, opcode_hist=None) -> dict:
+    """opcode_hist: optional writable uint64 numpy array of n_opcodes."""
+    m = aiwc_metrics()
+    if opcode_hist is not None:
+        m.opcode_hist = opcode_hist.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+    _check(lib.aiwc_compute(h, ctypes.byref(m)), h)
+    return _to_dict(m)
+
+
+def aiwc_compute_batch(hs, hists=None) -> list[dict]:
+    n = len(hs)
+    arr = (_VP * n)(*hs)
+    outs = (aiwc_metrics * n)()
+    if hists is not None:
+        for i, hh in enumerate(hists):
+            if hh is not None:
+                outs[i].opcode_hist = hh.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+    _check(lib.aiwc_compute_batch(arr, n, outs))
+    return [_to_dict(outs[i]) for i in range(n)]
+
+
+def aiwc_destroy(h) -> None:
+    _check(lib.aiwc_destroy(h))
+
+
+def aiwc_last_error(h=None) -> str:
+    return (lib.aiwc_last_error(h) or b"").decode()
+
+
+def aiwc_device_bytes(h) -> int:
+    return int(lib.aiwc_device_bytes(h))
+
+
+def aiwc_kernel_launches() -> int:
+    return int(lib.aiwc_kernel_launches())
+
+
+def aiwc_set_stage_timing(h, on: bool) -> None:
+    _check(lib.aiwc_set_stage_timing(h, int(on)), h)
+
+
+def aiwc_stage_times(h) -> dict:
+    ms = (ctypes.c_double * 32)()
+    names = (ctypes.c_char_p * 32)()
+    k = lib.aiwc_stage_times(h, ms, names, 32)
+    return {names[i].decode(): ms[i] for i in range(k)}
+
+
+from .api import Characterizer, characterize  # noqa: E402,F401

@@ -1,0 +1,237 @@
+// Internal declarations shared by the AIWC CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "aiwc.h"
+
+namespace aiwc {
+
+typedef unsigned long long u64;
+typedef unsigned int u32;
+
+// ------------------------------------------------------------------ sizes
+constexpr int kLevels = AIWC_MAX_SKIP + 1;  // skip 0 (global) .. 10 (local)
+constexpr int kCocDense = 1024;             // group sizes below this are binned densely
+constexpr int kValDense = 65536;            // ITB / IPT values below this are binned densely
+constexpr int kValSmem = 2048;              // ... of which the smallest are privatised in shared memory
+constexpr int kTile = 4096;                 // elements per tile in the sort and run kernels
+constexpr int kTileThreads = 256;
+constexpr int kTileItems = kTile / kTileThreads;
+
+// Tags of the shared overflow list: entry = tag << 56 | value.
+constexpr int kTagSites = 16;
+constexpr int kTagOpcodes = 17;
+constexpr int kTagItb = 18;
+constexpr int kTagIpt = 19;
+constexpr int kNumTags = 20;
+constexpr u64 kValueMask = (1ull << 56) - 1;
+
+// Error flags raised on the device (DevState::err).
+constexpr u32 kErrAddr = 1u;        // memory address >= 2^61
+constexpr u32 kErrOpcode = 2u;      // opcode >= n_opcodes and not a barrier
+constexpr u32 kErrWorkItem = 4u;    // work-item id >= max_work_items
+constexpr u32 kErrOverflow = 8u;    // an internal list exceeded its capacity
+constexpr u32 kErrRun = 16u;        // a run reaches past its opcode array
+
+// Device-resident counters of one invocation. Zeroed by a memset, then the
+// AND accumulators and minima are set to their identities.
+struct DevState {
+  u64 n_words;           // memory words after the space filter
+  u64 total_reads, total_writes;
+  u64 mem_or, mem_and;   // OR / AND over memory words: varying bits = or ^ and
+  u64 footprint, unique_reads, unique_writes;
+  u64 br_or, br_and;
+  u64 n_patterns;        // outcomes with a full history
+  u64 pat_or, pat_and;
+  u64 branch_sites;
+  u64 minsum, npat;
+  u64 barriers;
+  u64 run_or, run_and;
+  u64 work_items;
+  u64 n_over;            // entries in the overflow list
+  u64 over_or, over_and;
+  u64 unique_opcodes, total_instructions;
+  u64 n_branch;          // branch events pushed
+  u64 n_runs;            // instruction runs pushed
+  u32 wi_min, wi_max;
+  u32 err;
+  u32 sort_cur[8];       // which ping-pong buffer holds each sort's data
+  u32 pad;
+};
+
+// Sort slots (index into DevState::sort_cur).
+enum SortSlot { kSortMem = 0, kSortBranch = 1, kSortPattern = 2, kSortRuns = 3, kSortOver = 4 };
+
+// Per-tile run summary for the cross-tile fix-up (see runs.cuh).
+struct TileSum {
+  u32 has_b;
+  u32 pad;
+  u64 pre, suf, tot;     // lengths: before the first head, from the last head, all
+  u64 pre_w, suf_w, tot_w;  // the same, summing a per-element weight
+};
+
+// Dense distributions and the result live in one arena (one memset resets it).
+struct Arena {
+  DevState st;
+  u64 mem_coc[kLevels][kCocDense];   // m_c for group sizes c < kCocDense, per skip level
+  u64 site_coc[kCocDense];
+  u64 opc_coc[kCocDense];
+  u64 itb_dense[kValDense];
+  u64 ipt_dense[kValDense];
+  u64 tag_begin[kNumTags + 1];       // segment of each tag in the sorted overflow list
+};
+
+struct Result {
+  aiwc_metrics m;  // opcode_hist pointer unused on the device
+  u32 err;         // DevState::err at finalisation
+  u32 pad;
+};
+
+// A radix sort over 64-bit keys held in a ping-pong pair (a, b); the live
+// buffer is b when *cur is 1. Only bits in `mask` that vary between keys are
+// sorted, in 8-bit windows starting at `lo_bit`.
+struct SortDesc {
+  u64* a;
+  u64* b;
+  u32* cur;
+  const u64* n;       // device count of keys (clamped to n_cap)
+  u64 n_cap;          // capacity of a and b, in keys
+  const u64* key_or;  // device OR over keys
+  const u64* key_and; // device AND over keys
+  u64 mask;
+  int lo_bit;
+  u32* counts;        // 256 * ntiles digit counts (scanned in place)
+  u32* block_sums;
+  u32 ntiles;
+};
+
+// Kernels launched by this library (process-wide, all handles).
+void count_launches(u64 n);
+u64 launches_so_far();
+
+// ------------------------------------------------------------- launchers
+void sort_keys(const SortDesc& d, cudaStream_t s);
+size_t sort_counts_words(u64 n_max);  // u32 words needed for counts
+size_t sort_block_sums_words(u64 n_max);
+
+struct MemIngestArgs {
+  const void* ev;
+  u64 n;
+  u32 space_mask;
+  u64* words;
+  u64 word_base;       // offset for the unfiltered fast path
+  u32* wi_bitmap;
+  u64 max_wi;
+  Arena* arena;
+};
+void launch_mem_ingest(const MemIngestArgs& a, cudaStream_t s);
+
+struct LevelArgs {
+  const u64* a;
+  const u64* b;
+  const u32* cur;
+  const u64* n;
+  TileSum* tiles;      // kLevels * ntiles
+  u32 ntiles;
+  u64* over;
+  u64 over_cap;
+  Arena* arena;
+  int grid;
+};
+void launch_mem_levels(const LevelArgs& a, cudaStream_t s);
+
+struct BranchIngestArgs {
+  const void* ev;
+  u64 n;
+  u64* words;
+  u64 word_base;
+  u32* wi_bitmap;
+  u64 max_wi;
+  Arena* arena;
+};
+void launch_branch_ingest(const BranchIngestArgs& a, cudaStream_t s);
+
+struct WindowArgs {
+  const u64* a;        // sorted branch words (ping-pong)
+  const u64* b;
+  const u32* cur;
+  u64 n;               // branch events
+  u32 h;               // history length
+  u64* patterns;       // out: pattern words (sentinel where no full history)
+  TileSum* tiles;      // site-level tile summaries
+  u32 ntiles;
+  u64* over;
+  u64 over_cap;
+  Arena* arena;
+  int grid;
+};
+void launch_branch_windows(const WindowArgs& a, cudaStream_t s);
+
+struct PatternArgs {
+  const u64* a;
+  const u64* b;
+  const u32* cur;
+  const u64* n;        // valid pattern words (device)
+  TileSum* tiles;
+  u32 ntiles;
+  Arena* arena;
+  int grid;
+};
+void launch_pattern_runs(const PatternArgs& a, cudaStream_t s);
+
+// Cross-tile fix-up of run lengths. kind: 0 = memory levels, 1 = sites, 2 = patterns.
+void launch_runs_fixup(int kind, const TileSum* tiles, u32 ntiles_max, const u64* n_dev, u64 n_host,
+                       int levels, u64* over, u64 over_cap, Arena* arena, cudaStream_t s);
+
+struct RunBatchArgs {
+  const uint16_t* ops;
+  u64 n_ops;
+  const u32* run_wi;
+  const u64* run_off;
+  const u64* run_len;
+  u64 n_runs;
+  u64 seq_base;        // global index of the first run of this batch
+  u32 n_opcodes;
+  u64* run_keys;       // out: (wi << 32 | seq)
+  u64* run_sum;        // out: 4 words per run: has_b, pre, suf, tot
+  u32* wi_bitmap;
+  u64 max_wi;
+  u64* opc_hist;       // n_opcodes counts
+  u64* over;
+  u64 over_cap;
+  Arena* arena;
+};
+void launch_instr_runs(const RunBatchArgs& a, cudaStream_t s);
+
+struct CombineArgs {
+  const u64* a;
+  const u64* b;
+  const u32* cur;
+  u64 n_runs;
+  const u64* run_sum;
+  u64* over;
+  u64 over_cap;
+  Arena* arena;
+};
+void launch_instr_combine(const CombineArgs& a, cudaStream_t s);
+
+void launch_opcode_dist(const u64* hist, u32 n_opcodes, u64* over, u64 over_cap, Arena* arena, cudaStream_t s);
+void launch_wi_count(const u32* bitmap, Arena* arena, cudaStream_t s);
+void launch_wi_clear(u32* bitmap, Arena* arena, cudaStream_t s);
+void launch_reset_identities(Arena* arena, cudaStream_t s);
+
+struct FinalizeArgs {
+  const u64* over_a;
+  const u64* over_b;
+  const u32* over_cur;
+  u64 over_cap;
+  Arena* arena;
+  Result* result;
+  u32 cover_num, cover_den;
+  u32 precision;
+};
+void launch_finalize(const FinalizeArgs& a, cudaStream_t s);
+
+}  // namespace aiwc

@@ -1,0 +1,803 @@
+// Host side of the C ABI declared in include/aiwc.h: handle lifecycle,
+// staging of host pushes, and the end-of-invocation pipeline.
+//
+// Pushes run their ingest kernels immediately on the handle's stream (the
+// memory and branch ingests turn events into sort words; the instruction
+// kernel reduces each run at once), so host-to-device copies of one chunk
+// overlap the ingest of the previous one. aiwc_compute then sorts, measures
+// runs, finalises and copies one fixed-size result back.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "aiwc_internal.cuh"
+
+using namespace aiwc;
+
+namespace {
+
+thread_local std::string g_last_error;
+constexpr size_t kStageBytes = 64ull << 20;
+constexpr size_t kPendingOps = 1ull << 24;
+constexpr size_t kPendingRuns = 1ull << 16;
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int d) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != d) cudaSetDevice(d);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+inline u64 ntiles_of(u64 n) { return (n + kTile - 1) / kTile; }
+
+enum Stage {
+  kStMemIngest, kStBrIngest, kStInstrRuns, kStMemSort, kStMemLevels, kStBrSort, kStWindows, kStPatSort,
+  kStPatRuns, kStRunSort, kStCombine, kStFinalize, kNumStages
+};
+const char* const kStageNames[kNumStages] = {"mem_ingest", "branch_ingest", "instr_runs", "mem_sort",
+                                             "mem_levels", "branch_sort", "windows", "pattern_sort",
+                                             "pattern_runs", "run_sort", "run_combine", "finalize"};
+
+}  // namespace
+
+struct aiwc_handle {
+  aiwc_config cfg;
+  cudaStream_t stream = nullptr;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr};
+  cudaEvent_t ev_free[2] = {nullptr, nullptr};
+  int stage_next = 0;
+  int sm_count = 152;
+  bool broken = false;
+  std::string err;
+  Arena* arena = nullptr;
+  Result* d_result = nullptr;
+  Result* h_result = nullptr;
+  uint64_t* d_hist = nullptr;
+  uint64_t* h_hist = nullptr;
+  u32* wi_bitmap = nullptr;
+  u64 max_wi = 0;
+  size_t bytes = 0;
+  DevBuf mem_a, mem_b, br_a, br_b, pat_a, pat_b, rk_a, rk_b, run_sum, over_a, over_b, counts, bsums, tiles;
+  DevBuf stage[2];
+  DevBuf desc;
+  u64 n_mem = 0, n_br = 0, n_runs = 0;
+  u64 value_bound = 0;  // bound on ITB / IPT values >= kValDense (each uses kValDense instructions)
+  // pending single-run pushes (host data, or device pointers)
+  std::vector<uint16_t> pend_ops;
+  std::vector<uint32_t> pend_wi;
+  std::vector<uint64_t> pend_off, pend_len;
+  bool pend_device = false;
+  // optional stage timing
+  bool timing = false;
+  std::vector<cudaEvent_t> event_pool;
+  struct Interval { int stage; cudaEvent_t a, b; };
+  std::vector<Interval> intervals;
+  double stage_acc[kNumStages] = {0};
+  double stage_last[kNumStages] = {0};
+};
+
+namespace {
+
+aiwc_status fail(aiwc_handle* h, aiwc_status st, const std::string& msg, bool breaks = true) {
+  if (h) {
+    h->err = msg;
+    if (breaks && st != AIWC_EINVAL) h->broken = true;
+  }
+  g_last_error = msg;
+  return st;
+}
+
+aiwc_status cuda_fail(aiwc_handle* h, const char* what, cudaError_t e) {
+  char buf[512];
+  snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+  return fail(h, e == cudaErrorMemoryAllocation ? AIWC_ENOMEM : AIWC_ECUDA, buf);
+}
+
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(h, #call, e_);    \
+  } while (0)
+
+// Brackets one stage with CUDA events on the handle's stream when timing is on.
+struct StageScope {
+  aiwc_handle* h;
+  int stage;
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaEvent_t take() {
+    cudaEvent_t e = nullptr;
+    if (!h->event_pool.empty()) {
+      e = h->event_pool.back();
+      h->event_pool.pop_back();
+    } else if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      e = nullptr;
+    }
+    return e;
+  }
+  StageScope(aiwc_handle* hh, int st) : h(hh), stage(st) {
+    if (!h->timing) return;
+    a = take();
+    b = take();
+    if (a) cudaEventRecord(a, h->stream);
+  }
+  void end() {
+    if (!a || !b) return;
+    cudaEventRecord(b, h->stream);
+    h->intervals.push_back({stage, a, b});
+    a = b = nullptr;
+  }
+  ~StageScope() { end(); }
+};
+
+// After the stream is synchronised: fold the recorded intervals into stage times.
+void collect_stage_times(aiwc_handle* h) {
+  for (auto& iv : h->intervals) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, iv.a, iv.b) == cudaSuccess) h->stage_acc[iv.stage] += ms;
+    else cudaGetLastError();
+    h->event_pool.push_back(iv.a);
+    h->event_pool.push_back(iv.b);
+  }
+  h->intervals.clear();
+  for (int i = 0; i < kNumStages; ++i) {
+    h->stage_last[i] = h->stage_acc[i];
+    h->stage_acc[i] = 0.0;
+  }
+}
+
+aiwc_status ensure(aiwc_handle* h, DevBuf& b, size_t bytes, bool preserve) {
+  if (bytes <= b.cap) return AIWC_OK;
+  size_t want = std::max(bytes, b.cap + b.cap / 2);
+  want = (want + 255) & ~size_t(255);
+  if (h->cfg.hbm_budget && h->bytes - b.cap + want > h->cfg.hbm_budget) {
+    want = bytes;
+    if (h->bytes - b.cap + want > h->cfg.hbm_budget)
+      return fail(h, AIWC_ENOMEM, "device scratch would exceed hbm_budget", false);
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(h, AIWC_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e), false);
+  }
+  if (b.p) {
+    if (preserve) CK(cudaMemcpyAsync(p, b.p, b.cap, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaFree(b.p));
+  }
+  h->bytes = h->bytes - b.cap + want;
+  b.p = p;
+  b.cap = want;
+  return AIWC_OK;
+}
+
+#define ENSURE(buf, bytes, keep)                              \
+  do {                                                        \
+    aiwc_status s_ = ensure(h, buf, bytes, keep);             \
+    if (s_ != AIWC_OK) return s_;                             \
+  } while (0)
+
+aiwc_status ensure_bitmap(aiwc_handle* h) {
+  if (h->wi_bitmap) return AIWC_OK;
+  const size_t words = (size_t)((h->max_wi + 31) / 32);
+  if (h->cfg.hbm_budget && h->bytes + words * 4 > h->cfg.hbm_budget)
+    return fail(h, AIWC_ENOMEM, "work-item bitmap would exceed hbm_budget", false);
+  CK(cudaMalloc(&h->wi_bitmap, words * 4));
+  CK(cudaMemsetAsync(h->wi_bitmap, 0, words * 4, h->stream));
+  h->bytes += words * 4;
+  return AIWC_OK;
+}
+
+template <typename Launch>
+aiwc_status staged_copy(aiwc_handle* h, const void* src, size_t bytes, size_t unit, Launch launch) {
+  // Double-buffered: the copy of chunk k+1 overlaps the ingest of chunk k.
+  const size_t per = (kStageBytes / unit) * unit;
+  for (int i = 0; i < 2; ++i) ENSURE(h->stage[i], kStageBytes, false);
+  cudaEvent_t last = nullptr;
+  for (size_t off = 0; off < bytes; off += per) {
+    const size_t nb = std::min(per, bytes - off);
+    const int k = h->stage_next;
+    h->stage_next ^= 1;
+    CK(cudaStreamWaitEvent(h->copy_stream, h->ev_free[k], 0));
+    CK(cudaMemcpyAsync(h->stage[k].p, (const char*)src + off, nb, cudaMemcpyHostToDevice, h->copy_stream));
+    CK(cudaEventRecord(h->ev_copied[k], h->copy_stream));
+    CK(cudaStreamWaitEvent(h->stream, h->ev_copied[k], 0));
+    launch(h->stage[k].p, off / unit, nb / unit);
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(h->ev_free[k], h->stream));
+    last = h->ev_copied[k];
+  }
+  if (last) CK(cudaEventSynchronize(last));  // the caller may reuse its buffer on return
+  return AIWC_OK;
+}
+
+aiwc_status check_usable(aiwc_handle* h) {
+  if (!h) return fail(nullptr, AIWC_EINVAL, "null handle");
+  if (h->broken) return AIWC_ESTATE;
+  return AIWC_OK;
+}
+
+u64 over_bound(const aiwc_handle* h, u64 n_mem, u64 n_br, u64 n_runs) {
+  return (u64)kLevels * (n_mem / kCocDense + 2) + (n_br / kCocDense + 2) + (u64)h->cfg.n_opcodes +
+         2 * h->value_bound + 2 * (n_runs + 2) + 256;
+}
+
+aiwc_status runs_device(aiwc_handle* h, const u32* run_wi, const u64* run_off, const u64* run_len, size_t n_runs,
+                        const uint16_t* ops, u64 n_ops, u64 ops_total) {
+  if (h->n_runs + n_runs >= (1ull << 32))
+    return fail(h, AIWC_EINVAL, "more than 2^32 - 1 instruction runs in one invocation", false);
+  ENSURE(h->rk_a, (h->n_runs + n_runs) * 8, true);
+  ENSURE(h->run_sum, (h->n_runs + n_runs) * 32, true);
+  h->value_bound += ops_total / kValDense + 2;
+  ENSURE(h->over_a, over_bound(h, h->n_mem, h->n_br, h->n_runs + n_runs) * 8, true);
+  aiwc_status s = ensure_bitmap(h);
+  if (s != AIWC_OK) return s;
+  RunBatchArgs a;
+  a.ops = ops;
+  a.n_ops = n_ops;
+  a.run_wi = run_wi;
+  a.run_off = run_off;
+  a.run_len = run_len;
+  a.n_runs = n_runs;
+  a.seq_base = h->n_runs;
+  a.n_opcodes = h->cfg.n_opcodes;
+  a.run_keys = (u64*)h->rk_a.p;
+  a.run_sum = (u64*)h->run_sum.p;
+  a.wi_bitmap = h->wi_bitmap;
+  a.max_wi = h->max_wi;
+  a.opc_hist = (u64*)h->d_hist;
+  a.over = (u64*)h->over_a.p;
+  a.over_cap = h->over_a.cap / 8;
+  a.arena = h->arena;
+  StageScope scope(h, kStInstrRuns);
+  launch_instr_runs(a, h->stream);
+  CK(cudaGetLastError());
+  h->n_runs += n_runs;
+  return AIWC_OK;
+}
+
+// Host run tables: copied in batches whose opcode span fits a stage buffer.
+aiwc_status runs_host(aiwc_handle* h, const uint32_t* run_wi, const uint64_t* run_off, const uint64_t* run_len,
+                      size_t n_runs, const uint16_t* ops, size_t n_ops) {
+  for (size_t r = 0; r < n_runs; ++r)
+    if (run_off[r] > n_ops || run_len[r] > n_ops - run_off[r])
+      return fail(h, AIWC_EINVAL, "instruction run reaches past its opcode array", false);
+  size_t r0 = 0;
+  std::vector<unsigned char> tab;
+  while (r0 < n_runs) {
+    u64 lo = run_off[r0], hi = run_off[r0] + run_len[r0];
+    size_t r1 = r0 + 1;
+    while (r1 < n_runs) {
+      const u64 nlo = std::min<u64>(lo, run_off[r1]), nhi = std::max<u64>(hi, run_off[r1] + run_len[r1]);
+      const size_t need = ((nhi - nlo) * 2 + 15) / 16 * 16 + (r1 + 1 - r0) * 24;
+      if (need > kStageBytes) break;
+      lo = nlo;
+      hi = nhi;
+      ++r1;
+    }
+    const size_t nb = r1 - r0;
+    const size_t ops_bytes = ((hi - lo) * 2 + 15) / 16 * 16;
+    const size_t need = ops_bytes + nb * 24;
+    const int k = h->stage_next;
+    h->stage_next ^= 1;
+    ENSURE(h->stage[k], std::max(need, kStageBytes), false);
+    tab.resize(nb * 24);
+    u64* offs = (u64*)tab.data();
+    u64* lens = offs + nb;
+    u32* wis = (u32*)(lens + nb);
+    for (size_t i = 0; i < nb; ++i) {
+      offs[i] = run_off[r0 + i] - lo;
+      lens[i] = run_len[r0 + i];
+      wis[i] = run_wi[r0 + i];
+    }
+    char* base = (char*)h->stage[k].p;
+    CK(cudaStreamWaitEvent(h->copy_stream, h->ev_free[k], 0));
+    if (hi > lo) CK(cudaMemcpyAsync(base, ops + lo, (hi - lo) * 2, cudaMemcpyHostToDevice, h->copy_stream));
+    CK(cudaMemcpyAsync(base + ops_bytes, tab.data(), nb * 24, cudaMemcpyHostToDevice, h->copy_stream));
+    CK(cudaEventRecord(h->ev_copied[k], h->copy_stream));
+    CK(cudaStreamWaitEvent(h->stream, h->ev_copied[k], 0));
+    aiwc_status s = runs_device(h, (const u32*)(base + ops_bytes + nb * 16), (const u64*)(base + ops_bytes),
+                                (const u64*)(base + ops_bytes + nb * 8), nb, (const uint16_t*)base, hi - lo, hi - lo);
+    if (s != AIWC_OK) return s;
+    CK(cudaEventRecord(h->ev_free[k], h->stream));
+    CK(cudaEventSynchronize(h->ev_copied[k]));  // tab is reused; the caller may reuse ops
+    r0 = r1;
+  }
+  return AIWC_OK;
+}
+
+aiwc_status flush_pending(aiwc_handle* h) {
+  if (h->pend_wi.empty()) return AIWC_OK;
+  aiwc_status s;
+  if (!h->pend_device) {
+    s = runs_host(h, h->pend_wi.data(), h->pend_off.data(), h->pend_len.data(), h->pend_wi.size(),
+                  h->pend_ops.data(), h->pend_ops.size());
+  } else {
+    // descriptors of device runs: offsets are element addresses from 0
+    const size_t nb = h->pend_wi.size();
+    const int k = h->stage_next;
+    h->stage_next ^= 1;
+    ENSURE(h->stage[k], std::max(nb * 24, kStageBytes), false);
+    std::vector<unsigned char> tab(nb * 24);
+    memcpy(tab.data(), h->pend_off.data(), nb * 8);
+    memcpy(tab.data() + nb * 8, h->pend_len.data(), nb * 8);
+    memcpy(tab.data() + nb * 16, h->pend_wi.data(), nb * 4);
+    char* base = (char*)h->stage[k].p;
+    CK(cudaStreamWaitEvent(h->copy_stream, h->ev_free[k], 0));
+    CK(cudaMemcpyAsync(base, tab.data(), nb * 24, cudaMemcpyHostToDevice, h->copy_stream));
+    CK(cudaEventRecord(h->ev_copied[k], h->copy_stream));
+    CK(cudaStreamWaitEvent(h->stream, h->ev_copied[k], 0));
+    u64 total = 0;
+    for (u64 l : h->pend_len) total += l;
+    s = runs_device(h, (const u32*)(base + nb * 16), (const u64*)base, (const u64*)(base + nb * 8), nb,
+                    (const uint16_t*)nullptr, ~0ull, total);
+    if (s == AIWC_OK) {
+      CK(cudaEventRecord(h->ev_free[k], h->stream));
+      CK(cudaEventSynchronize(h->ev_copied[k]));
+    }
+  }
+  h->pend_ops.clear();
+  h->pend_wi.clear();
+  h->pend_off.clear();
+  h->pend_len.clear();
+  return s;
+}
+
+void release(aiwc_handle* h, DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  h->bytes -= b.cap;
+  b.p = nullptr;
+  b.cap = 0;
+}
+
+aiwc_status reset_device_state(aiwc_handle* h) {
+  if (h->wi_bitmap) launch_wi_clear(h->wi_bitmap, h->arena, h->stream);
+  CK(cudaMemsetAsync(h->d_hist, 0, (size_t)h->cfg.n_opcodes * 8, h->stream));
+  CK(cudaMemsetAsync(h->arena, 0, sizeof(Arena), h->stream));
+  launch_reset_identities(h->arena, h->stream);
+  CK(cudaGetLastError());
+  return AIWC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void aiwc_config_default(aiwc_config* c) {
+  if (!c) return;
+  memset(c, 0, sizeof(*c));
+  c->device = 0;
+  c->cuda_stream = nullptr;
+  c->history_len = 16;
+  c->cover_num = 9;
+  c->cover_den = 10;
+  c->n_opcodes = 65535;
+  c->space_mask = 0xF;
+  c->precision = 0;
+  c->plan = 0;
+  c->max_work_items = 0;
+  c->hbm_budget = 0;
+}
+
+aiwc_status aiwc_create(const aiwc_config* cfg, aiwc_handle** out) {
+  if (!cfg || !out) return fail(nullptr, AIWC_EINVAL, "null config or output pointer");
+  *out = nullptr;
+  if (cfg->history_len < 1 || cfg->history_len > 31) return fail(nullptr, AIWC_EINVAL, "history_len must be 1..31");
+  if (cfg->cover_den == 0 || cfg->cover_num == 0 || cfg->cover_num > cfg->cover_den)
+    return fail(nullptr, AIWC_EINVAL, "coverage fraction must be in (0, 1]");
+  if (cfg->n_opcodes == 0 || cfg->n_opcodes > 65535) return fail(nullptr, AIWC_EINVAL, "n_opcodes must be 1..65535");
+  if (cfg->precision > 1 || cfg->plan > 2) return fail(nullptr, AIWC_EINVAL, "unknown precision or plan");
+  if (cfg->max_work_items > (1ull << 32)) return fail(nullptr, AIWC_EINVAL, "max_work_items must be <= 2^32");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
+    cudaGetLastError();
+    return fail(nullptr, AIWC_ECUDA, "no such CUDA device");
+  }
+  DeviceGuard g(cfg->device);
+  aiwc_handle* h = new aiwc_handle();
+  h->cfg = *cfg;
+  h->cfg.space_mask &= 0xF;
+  h->stream = (cudaStream_t)cfg->cuda_stream;
+  h->max_wi = cfg->max_work_items ? cfg->max_work_items : (1ull << 32);
+  auto bail = [&](aiwc_status s) {
+    aiwc_destroy(h);
+    return s;
+  };
+  cudaError_t e;
+  if ((e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, cfg->device)) != cudaSuccess)
+    return bail(cuda_fail(nullptr, "cudaDeviceGetAttribute", e));
+  if ((e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return bail(cuda_fail(nullptr, "cudaStreamCreate", e));
+  for (int i = 0; i < 2; ++i) {
+    if ((e = cudaEventCreateWithFlags(&h->ev_copied[i], cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&h->ev_free[i], cudaEventDisableTiming)) != cudaSuccess)
+      return bail(cuda_fail(nullptr, "cudaEventCreate", e));
+  }
+  if ((e = cudaMalloc(&h->arena, sizeof(Arena))) != cudaSuccess ||
+      (e = cudaMalloc(&h->d_result, sizeof(Result))) != cudaSuccess ||
+      (e = cudaMalloc(&h->d_hist, (size_t)cfg->n_opcodes * 8)) != cudaSuccess ||
+      (e = cudaMallocHost(&h->h_result, sizeof(Result))) != cudaSuccess ||
+      (e = cudaMallocHost(&h->h_hist, (size_t)cfg->n_opcodes * 8)) != cudaSuccess)
+    return bail(cuda_fail(nullptr, "allocation", e));
+  h->bytes = sizeof(Arena) + sizeof(Result) + (size_t)cfg->n_opcodes * 8;
+  if (reset_device_state(h) != AIWC_OK) return bail(fail(nullptr, AIWC_ECUDA, h->err));
+  if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(cuda_fail(nullptr, "initial reset", e));
+  *out = h;
+  return AIWC_OK;
+}
+
+aiwc_status aiwc_push_mem(aiwc_handle* h, const aiwc_mem_event* ev, size_t n, int on_device) {
+  aiwc_status s = check_usable(h);
+  if (s != AIWC_OK) return s;
+  if (n == 0) return AIWC_OK;
+  if (!ev) return fail(h, AIWC_EINVAL, "null event pointer", false);
+  DeviceGuard g(h->cfg.device);
+  if (on_device && ((uintptr_t)ev & 15u))
+    return fail(h, AIWC_EINVAL, "device memory events must be 16-byte aligned", false);
+  ENSURE(h->mem_a, (h->n_mem + n) * 8, true);
+  if ((s = ensure_bitmap(h)) != AIWC_OK) return s;
+  MemIngestArgs a;
+  a.space_mask = h->cfg.space_mask;
+  a.words = (u64*)h->mem_a.p;
+  a.wi_bitmap = h->wi_bitmap;
+  a.max_wi = h->max_wi;
+  a.arena = h->arena;
+  const u64 base = h->n_mem;
+  StageScope scope(h, kStMemIngest);
+  if (on_device) {
+    a.ev = ev;
+    a.n = n;
+    a.word_base = base;
+    launch_mem_ingest(a, h->stream);
+    CK(cudaGetLastError());
+  } else {
+    s = staged_copy(h, ev, n * 16, 16, [&](void* p, size_t first, size_t cnt) {
+      MemIngestArgs b = a;
+      b.ev = p;
+      b.n = cnt;
+      b.word_base = base + first;
+      launch_mem_ingest(b, h->stream);
+    });
+    if (s != AIWC_OK) return s;
+  }
+  h->n_mem += n;
+  return AIWC_OK;
+}
+
+aiwc_status aiwc_push_branch(aiwc_handle* h, const aiwc_branch_event* ev, size_t n, int on_device) {
+  aiwc_status s = check_usable(h);
+  if (s != AIWC_OK) return s;
+  if (n == 0) return AIWC_OK;
+  if (!ev) return fail(h, AIWC_EINVAL, "null event pointer", false);
+  DeviceGuard g(h->cfg.device);
+  if (on_device && ((uintptr_t)ev & 7u))
+    return fail(h, AIWC_EINVAL, "device branch events must be 8-byte aligned", false);
+  ENSURE(h->br_a, (h->n_br + n) * 8, true);
+  if ((s = ensure_bitmap(h)) != AIWC_OK) return s;
+  BranchIngestArgs a;
+  a.words = (u64*)h->br_a.p;
+  a.wi_bitmap = h->wi_bitmap;
+  a.max_wi = h->max_wi;
+  a.arena = h->arena;
+  const u64 base = h->n_br;
+  StageScope scope(h, kStBrIngest);
+  if (on_device) {
+    a.ev = ev;
+    a.n = n;
+    a.word_base = base;
+    launch_branch_ingest(a, h->stream);
+    CK(cudaGetLastError());
+  } else {
+    s = staged_copy(h, ev, n * 8, 8, [&](void* p, size_t first, size_t cnt) {
+      BranchIngestArgs b = a;
+      b.ev = p;
+      b.n = cnt;
+      b.word_base = base + first;
+      launch_branch_ingest(b, h->stream);
+    });
+    if (s != AIWC_OK) return s;
+  }
+  h->n_br += n;
+  return AIWC_OK;
+}
+
+aiwc_status aiwc_push_instr(aiwc_handle* h, uint32_t work_item, const uint16_t* ops, size_t n, int on_device) {
+  aiwc_status s = check_usable(h);
+  if (s != AIWC_OK) return s;
+  if (n && !ops) return fail(h, AIWC_EINVAL, "null opcode pointer", false);
+  DeviceGuard g(h->cfg.device);
+  const bool dev = on_device != 0;
+  if (dev && ((uintptr_t)ops & 1u)) return fail(h, AIWC_EINVAL, "device opcodes must be 2-byte aligned", false);
+  if (!h->pend_wi.empty() && h->pend_device != dev) {
+    if ((s = flush_pending(h)) != AIWC_OK) return s;
+  }
+  h->pend_device = dev;
+  h->pend_wi.push_back(work_item);
+  h->pend_len.push_back(n);
+  if (dev) {
+    h->pend_off.push_back((u64)(uintptr_t)ops / 2);
+  } else {
+    h->pend_off.push_back(h->pend_ops.size());
+    h->pend_ops.insert(h->pend_ops.end(), ops, ops + n);
+  }
+  if (h->pend_ops.size() >= kPendingOps || h->pend_wi.size() >= kPendingRuns) return flush_pending(h);
+  return AIWC_OK;
+}
+
+aiwc_status aiwc_push_instr_runs(aiwc_handle* h, const uint32_t* run_wi, const uint64_t* run_off,
+                                 const uint64_t* run_len, size_t n_runs, const uint16_t* ops, size_t n_ops,
+                                 int on_device) {
+  aiwc_status s = check_usable(h);
+  if (s != AIWC_OK) return s;
+  if (n_runs == 0) return AIWC_OK;
+  if (!run_wi || !run_off || !run_len || (n_ops && !ops)) return fail(h, AIWC_EINVAL, "null run table", false);
+  DeviceGuard g(h->cfg.device);
+  if ((s = flush_pending(h)) != AIWC_OK) return s;
+  if (on_device && (((uintptr_t)ops & 1u) || ((uintptr_t)run_wi & 3u) || ((uintptr_t)run_off & 7u) ||
+                    ((uintptr_t)run_len & 7u)))
+    return fail(h, AIWC_EINVAL, "device run tables / opcodes are misaligned", false);
+  if (on_device)
+    return runs_device(h, run_wi, (const u64*)run_off, (const u64*)run_len, n_runs, ops, n_ops, n_ops);
+  return runs_host(h, run_wi, run_off, run_len, n_runs, ops, n_ops);
+}
+
+aiwc_status aiwc_compute(aiwc_handle* h, aiwc_metrics* out) {
+  if (!h || !out) return fail(h, AIWC_EINVAL, "null handle or output pointer", false);
+  DeviceGuard g(h->cfg.device);
+  uint64_t* user_hist = out->opcode_hist;
+  cudaStream_t st = h->stream;
+  auto reset_host = [&]() {
+    h->n_mem = h->n_br = h->n_runs = 0;
+    h->value_bound = 0;
+    h->pend_ops.clear();
+    h->pend_wi.clear();
+    h->pend_off.clear();
+    h->pend_len.clear();
+  };
+  if (h->broken) {
+    // drop the invocation and try to return to a clean state
+    reset_host();
+    cudaGetLastError();
+    if (reset_device_state(h) == AIWC_OK && cudaStreamSynchronize(st) == cudaSuccess) h->broken = false;
+    return AIWC_ESTATE;
+  }
+  aiwc_status s = flush_pending(h);
+  if (s != AIWC_OK) return s;
+  const u64 n_mem = h->n_mem, n_br = h->n_br, n_runs = h->n_runs;
+  ENSURE(h->over_a, over_bound(h, n_mem, n_br, n_runs) * 8, true);
+  const u64 over_cap = h->over_a.cap / 8;
+  const u64 nmax = std::max(std::max(n_mem, n_br), std::max(n_runs, over_cap));
+  ENSURE(h->mem_a, std::max<u64>(n_mem, 1) * 8, true);
+  ENSURE(h->mem_b, std::max<u64>(n_mem, 1) * 8, false);
+  ENSURE(h->br_a, std::max<u64>(n_br, 1) * 8, true);
+  ENSURE(h->br_b, std::max<u64>(n_br, 1) * 8, false);
+  ENSURE(h->pat_a, std::max<u64>(n_br, 1) * 8, false);
+  ENSURE(h->pat_b, std::max<u64>(n_br, 1) * 8, false);
+  ENSURE(h->rk_a, std::max<u64>(n_runs, 1) * 8, true);
+  ENSURE(h->rk_b, std::max<u64>(n_runs, 1) * 8, false);
+  ENSURE(h->run_sum, std::max<u64>(n_runs, 1) * 32, true);
+  ENSURE(h->over_b, over_cap * 8, false);
+  ENSURE(h->counts, sort_counts_words(nmax) * 4, false);
+  ENSURE(h->bsums, sort_block_sums_words(nmax) * 4, false);
+  ENSURE(h->tiles, std::max<u64>((u64)kLevels * ntiles_of(n_mem), ntiles_of(n_br) + 1) * sizeof(TileSum), false);
+  if ((s = ensure_bitmap(h)) != AIWC_OK) return s;
+  DevState* dst = &h->arena->st;
+  u64* over = (u64*)h->over_a.p;
+  const int grid = h->sm_count * 3;
+  auto sdesc = [&](DevBuf& a, DevBuf& b, int slot, const u64* n_dev, const u64* kor, const u64* kand, u64 mask,
+                   int lo, u64 n_host) {
+    SortDesc d;
+    d.a = (u64*)a.p;
+    d.b = (u64*)b.p;
+    d.cur = &dst->sort_cur[slot];
+    d.n = n_dev;
+    d.n_cap = std::min<u64>(a.cap, b.cap) / 8;
+    d.key_or = kor;
+    d.key_and = kand;
+    d.mask = mask;
+    d.lo_bit = lo;
+    d.counts = (u32*)h->counts.p;
+    d.block_sums = (u32*)h->bsums.p;
+    d.ntiles = (u32)ntiles_of(n_host);
+    return d;
+  };
+  // memory: sort words, run lengths per skip level, cross-tile fix-up
+  if (n_mem) {
+    SortDesc d = sdesc(h->mem_a, h->mem_b, kSortMem, &dst->n_words, &dst->mem_or, &dst->mem_and, ~0ull, 0, n_mem);
+    {
+      StageScope sc(h, kStMemSort);
+      sort_keys(d, st);
+    }
+    StageScope sc(h, kStMemLevels);
+    LevelArgs la;
+    la.a = d.a;
+    la.b = d.b;
+    la.cur = d.cur;
+    la.n = &dst->n_words;
+    la.tiles = (TileSum*)h->tiles.p;
+    la.ntiles = d.ntiles;
+    la.over = over;
+    la.over_cap = over_cap;
+    la.arena = h->arena;
+    la.grid = grid;
+    launch_mem_levels(la, st);
+    launch_runs_fixup(0, la.tiles, la.ntiles, &dst->n_words, 0, kLevels, over, over_cap, h->arena, st);
+  }
+  // branches: sort by (site, work-item) keeping push order, windows, patterns
+  if (n_br) {
+    SortDesc d = sdesc(h->br_a, h->br_b, kSortBranch, &dst->n_branch, &dst->br_or, &dst->br_and, ~1ull, 1, n_br);
+    {
+      StageScope sc(h, kStBrSort);
+      sort_keys(d, st);
+    }
+    WindowArgs wa;
+    wa.a = d.a;
+    wa.b = d.b;
+    wa.cur = d.cur;
+    wa.n = n_br;
+    wa.h = h->cfg.history_len;
+    wa.patterns = (u64*)h->pat_a.p;
+    wa.tiles = (TileSum*)h->tiles.p;
+    wa.ntiles = d.ntiles;
+    wa.over = over;
+    wa.over_cap = over_cap;
+    wa.arena = h->arena;
+    wa.grid = grid;
+    {
+      StageScope sc(h, kStWindows);
+      launch_branch_windows(wa, st);
+      launch_runs_fixup(1, wa.tiles, wa.ntiles, nullptr, n_br, 1, over, over_cap, h->arena, st);
+    }
+    SortDesc p = sdesc(h->pat_a, h->pat_b, kSortPattern, &dst->n_patterns, &dst->pat_or, &dst->pat_and, ~0ull, 0,
+                       n_br);
+    {
+      StageScope sc(h, kStPatSort);
+      sort_keys(p, st);
+    }
+    StageScope sc(h, kStPatRuns);
+    PatternArgs pa;
+    pa.a = p.a;
+    pa.b = p.b;
+    pa.cur = p.cur;
+    pa.n = &dst->n_patterns;
+    pa.tiles = (TileSum*)h->tiles.p;
+    pa.ntiles = p.ntiles;
+    pa.arena = h->arena;
+    pa.grid = grid;
+    launch_pattern_runs(pa, st);
+    launch_runs_fixup(2, pa.tiles, pa.ntiles, &dst->n_patterns, 0, 1, over, over_cap, h->arena, st);
+  }
+  // instructions: chain each work-item's runs
+  if (n_runs) {
+    SortDesc d = sdesc(h->rk_a, h->rk_b, kSortRuns, &dst->n_runs, &dst->run_or, &dst->run_and, ~0ull, 0, n_runs);
+    {
+      StageScope sc(h, kStRunSort);
+      sort_keys(d, st);
+    }
+    StageScope sc(h, kStCombine);
+    CombineArgs ca;
+    ca.a = d.a;
+    ca.b = d.b;
+    ca.cur = d.cur;
+    ca.n_runs = n_runs;
+    ca.run_sum = (const u64*)h->run_sum.p;
+    ca.over = over;
+    ca.over_cap = over_cap;
+    ca.arena = h->arena;
+    launch_instr_combine(ca, st);
+  }
+  StageScope fin_scope(h, kStFinalize);
+  launch_opcode_dist((const u64*)h->d_hist, h->cfg.n_opcodes, over, over_cap, h->arena, st);
+  launch_wi_count(h->wi_bitmap, h->arena, st);
+  {
+    SortDesc d = sdesc(h->over_a, h->over_b, kSortOver, &dst->n_over, &dst->over_or, &dst->over_and, ~0ull, 0,
+                       over_cap);
+    sort_keys(d, st);
+    FinalizeArgs fa;
+    fa.over_a = d.a;
+    fa.over_b = d.b;
+    fa.over_cur = d.cur;
+    fa.over_cap = over_cap;
+    fa.arena = h->arena;
+    fa.result = h->d_result;
+    fa.cover_num = h->cfg.cover_num;
+    fa.cover_den = h->cfg.cover_den;
+    fa.precision = h->cfg.precision;
+    launch_finalize(fa, st);
+  }
+  fin_scope.end();
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(h->h_result, h->d_result, sizeof(Result), cudaMemcpyDeviceToHost, st));
+  if (user_hist)
+    CK(cudaMemcpyAsync(h->h_hist, h->d_hist, (size_t)h->cfg.n_opcodes * 8, cudaMemcpyDeviceToHost, st));
+  if ((s = reset_device_state(h)) != AIWC_OK) return s;
+  CK(cudaStreamSynchronize(st));
+  collect_stage_times(h);
+  reset_host();
+  *out = h->h_result->m;
+  out->opcode_hist = user_hist;
+  if (user_hist) memcpy(user_hist, h->h_hist, (size_t)h->cfg.n_opcodes * 8);
+  const u32 err = h->h_result->err;
+  if (err & kErrOverflow) return fail(h, AIWC_ECUDA, "internal overflow list exceeded its bound", false);
+  if (err & kErrAddr) return fail(h, AIWC_EINVAL, "memory address outside the 61-bit domain", false);
+  if (err & kErrOpcode) return fail(h, AIWC_EINVAL, "opcode >= n_opcodes that is not a barrier", false);
+  if (err & kErrWorkItem) return fail(h, AIWC_EINVAL, "work-item id >= max_work_items", false);
+  if (err & kErrRun) return fail(h, AIWC_EINVAL, "instruction run reaches past its opcode array", false);
+  return AIWC_OK;
+}
+
+aiwc_status aiwc_compute_batch(aiwc_handle* const* hs, size_t n, aiwc_metrics* outs) {
+  if (n && (!hs || !outs)) return fail(nullptr, AIWC_EINVAL, "null batch arrays");
+  aiwc_status worst = AIWC_OK;
+  for (size_t i = 0; i < n; ++i) {
+    aiwc_status s = aiwc_compute(hs[i], &outs[i]);
+    if (s != AIWC_OK && worst == AIWC_OK) worst = s;
+  }
+  return worst;
+}
+
+aiwc_status aiwc_destroy(aiwc_handle* h) {
+  if (!h) return AIWC_OK;
+  DeviceGuard g(h->cfg.device);
+  if (h->stream || h->copy_stream) cudaStreamSynchronize(h->stream);
+  DevBuf* bufs[] = {&h->mem_a, &h->mem_b, &h->br_a, &h->br_b, &h->pat_a, &h->pat_b, &h->rk_a, &h->rk_b,
+                    &h->run_sum, &h->over_a, &h->over_b, &h->counts, &h->bsums, &h->tiles, &h->stage[0],
+                    &h->stage[1], &h->desc};
+  for (DevBuf* b : bufs) release(h, *b);
+  if (h->wi_bitmap) cudaFree(h->wi_bitmap);
+  if (h->arena) cudaFree(h->arena);
+  if (h->d_result) cudaFree(h->d_result);
+  if (h->d_hist) cudaFree(h->d_hist);
+  if (h->h_result) cudaFreeHost(h->h_result);
+  if (h->h_hist) cudaFreeHost(h->h_hist);
+  for (int i = 0; i < 2; ++i) {
+    if (h->ev_copied[i]) cudaEventDestroy(h->ev_copied[i]);
+    if (h->ev_free[i]) cudaEventDestroy(h->ev_free[i]);
+  }
+  for (auto& iv : h->intervals) {
+    cudaEventDestroy(iv.a);
+    cudaEventDestroy(iv.b);
+  }
+  for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
+  if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
+  delete h;
+  return AIWC_OK;
+}
+
+const char* aiwc_last_error(const aiwc_handle* h) { return h ? h->err.c_str() : g_last_error.c_str(); }
+
+uint64_t aiwc_device_bytes(const aiwc_handle* h) { return h ? (uint64_t)h->bytes : 0; }
+
+uint64_t aiwc_kernel_launches(void) { return launches_so_far(); }
+
+aiwc_status aiwc_set_stage_timing(aiwc_handle* h, int on) {
+  if (!h) return fail(nullptr, AIWC_EINVAL, "null handle");
+  h->timing = on != 0;
+  return AIWC_OK;
+}
+
+int aiwc_stage_times(const aiwc_handle* h, double* ms, const char** names, int n) {
+  if (!h || n <= 0) return 0;
+  const int k = n < kNumStages ? n : kNumStages;
+  for (int i = 0; i < k; ++i) {
+    if (ms) ms[i] = h->stage_last[i];
+    if (names) names[i] = kStageNames[i];
+  }
+  return k;
+}
+
+}  // extern "C"

@@ -1,0 +1,306 @@
+// Branch path: per-site histories (Sec. III: 16-outcome histories; Sec. V:
+// outcomes appended per branch location while work-items run one after
+// another) and the average linear branch entropy of De Pestel et al.
+//
+// Branch word: (site << 32) | (work_item << 1) | taken. A stable sort on bits
+// 1..63 orders events by (site, work-item) and keeps push (program) order
+// inside each work-item, which is the per-site history order. A pattern word
+// (site << 32) | (history << 1) | outcome is emitted for every outcome that
+// has `h` predecessors at its site; sorting pattern words puts each
+// (site, history) pattern in one run whose length is n and whose sum of low
+// bits is the number taken, t. M = sum min(t, n - t), N' = sum n.
+#include "aiwc_internal.cuh"
+#include "common.cuh"
+#include "runs.cuh"
+
+namespace aiwc {
+namespace {
+
+constexpr int kBrThreads = 256;
+constexpr int kBrItems = 8;
+
+__global__ void __launch_bounds__(kBrThreads) k_branch_ingest(BranchIngestArgs a) {
+  __shared__ u64 red64[32];
+  __shared__ u32 red32[32];
+  DevState* st = &a.arena->st;
+  const uint2* ev = reinterpret_cast<const uint2*>(a.ev);
+  u64 wor = 0, wand = ~0ull;
+  u32 wmin = 0xFFFFFFFFu, wmax = 0u, err = 0u;
+  const u64 per_block = (u64)kBrThreads * kBrItems;
+  for (u64 t0 = (u64)blockIdx.x * per_block; t0 < a.n; t0 += (u64)gridDim.x * per_block) {
+#pragma unroll
+    for (int k = 0; k < kBrItems; ++k) {
+      const u64 i = t0 + (u64)k * kBrThreads + threadIdx.x;
+      const bool valid = i < a.n;
+      const uint2 e = valid ? __ldcs(ev + i) : make_uint2(0u, 0u);
+      const u32 wi = e.y & 0x7FFFFFFFu;
+      mark_work_items(a.wi_bitmap, a.max_wi, wi, valid, &err);
+      if (valid) {
+        const u64 w = ((u64)e.x << 32) | ((u64)wi << 1) | (u64)(e.y >> 31);
+        a.words[a.word_base + i] = w;
+        wor |= w;
+        wand &= w;
+        if ((u64)wi < a.max_wi) {
+          wmin = min(wmin, wi);
+          wmax = max(wmax, wi);
+        }
+      }
+    }
+  }
+  wor = block_reduce(wor, OpOr(), 0ull, red64);
+  wand = block_reduce(wand, OpAnd(), ~0ull, red64);
+  wmin = block_reduce(wmin, OpMin(), 0xFFFFFFFFu, red32);
+  wmax = block_reduce(wmax, OpMax(), 0u, red32);
+  err = block_reduce(err, OpOr(), 0u, red32);
+  if (threadIdx.x == 0) {
+    if (wmin <= wmax) {
+      atomicOr(&st->br_or, wor);
+      atomicAnd(&st->br_and, wand);
+      atomicMin(&st->wi_min, wmin);
+      atomicMax(&st->wi_max, wmax);
+    }
+    if (err) atomicOr(&st->err, err);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&st->n_branch, a.n);
+}
+
+constexpr int kHalo = 32;  // history lengths are at most 31
+
+// Reads the sorted branch words of one tile (plus the 32 words before it),
+// writes the compacted pattern words of outcomes with a full history, and
+// runs the per-site run lengths (site event counts) for the site metrics.
+__global__ void __launch_bounds__(kTileThreads) k_windows(WindowArgs a) {
+  __shared__ u64 tw[kHalo + kTile];
+  __shared__ u32 site_coc[kCocDense];
+  __shared__ Seg sh[33];
+  __shared__ u64 pre_slot[2];
+  __shared__ u64 red64[32];
+  __shared__ u32 scan_tot[33];
+  __shared__ u64 s_base;
+  DevState* st = &a.arena->st;
+  for (int i = threadIdx.x; i < kCocDense; i += kTileThreads) site_coc[i] = 0u;
+  const u64 n = a.n;
+  const u64* words = *a.cur ? a.b : a.a;
+  const u32 ntiles = (u32)((n + kTile - 1) / kTile);
+  const u32 h = a.h;
+  const u64 hmask = (1ull << h) - 1ull;
+  u64 heads = 0, npat = 0, por = 0, pand = ~0ull;
+  for (u32 tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const u64 base = (u64)tile * kTile;
+    const u64 tile_n = umin64(n - base, (u64)kTile);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kHalo + kTile; i += kTileThreads) {
+      const long long p = (long long)base - kHalo + i;
+      tw[i] = (p >= 0 && (u64)p < n) ? words[p] : 0ull;
+    }
+    __syncthreads();
+    const int t0 = threadIdx.x * kTileItems;  // tile-relative
+    const u64 pos0 = base + t0;
+    const int nvalid = pos0 < n ? (int)umin64(n - pos0, (u64)kTileItems) : 0;
+    u64 key[kTileItems];
+#pragma unroll
+    for (int k = 0; k < kTileItems; ++k) key[k] = tw[kHalo + t0 + k];
+    const u64 prev = tw[kHalo + t0 - 1];
+    // history of the first position: outcomes at pos0-h .. pos0-1, oldest high
+    u64 hist = 0;
+    for (u32 i = 0; i < h; ++i) hist = (hist << 1) | (tw[kHalo + t0 - (int)h + (int)i] & 1ull);
+    u64 pat[kTileItems];
+    u32 np = 0;
+#pragma unroll
+    for (int k = 0; k < kTileItems; ++k) {
+      const u64 j = pos0 + k;
+      bool ok = false;
+      if (k < nvalid && j >= h) {
+        const u64 older = tw[kHalo + t0 + k - (int)h];
+        ok = (older >> 32) == (key[k] >> 32);
+      }
+      if (ok) {
+        const u64 pw = (key[k] & 0xFFFFFFFF00000001ull) | ((hist & hmask) << 1);
+        pat[np++] = pw;
+        por |= pw;
+        pand &= pw;
+      }
+      hist = (hist << 1) | (key[k] & 1ull);
+    }
+    npat += np;
+    // compact this tile's pattern words behind one atomicAdd
+    {
+      const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+      u32 inc = np;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        u32 y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+      }
+      if (lane == 31) scan_tot[w] = inc;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        u32 s = 0;
+        for (int q = 0; q < kTileThreads / 32; ++q) { u32 c = scan_tot[q]; scan_tot[q] = s; s += c; }
+        s_base = atomicAdd(&st->n_patterns, (u64)s);
+      }
+      __syncthreads();
+      u64 out = s_base + scan_tot[w] + inc - np;
+      for (u32 k = 0; k < np; ++k) a.patterns[out + k] = pat[k];
+    }
+    // site heads and per-site event counts
+    {
+      u64 pw = prev;
+#pragma unroll
+      for (int k = 0; k < kTileItems; ++k) {
+        if (k < nvalid) {
+          if (pos0 + k == 0 || (key[k] >> 32) != (pw >> 32)) ++heads;
+          pw = key[k];
+        }
+      }
+    }
+    tile_runs<kTileItems>(
+        key, nvalid, pos0, prev, tile_n, [](u64 x) { return x >> 32; }, [](u64) { return 0ull; },
+        [&](u64 len, u64) {
+          if (len < (u64)kCocDense) atomicAdd(&site_coc[len], 1u);
+          else overflow_append(a.over, a.over_cap, st, kTagSites, len);
+        },
+        &a.tiles[tile], sh, pre_slot);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kCocDense; i += kTileThreads)
+    if (site_coc[i]) atomicAdd(&a.arena->site_coc[i], (u64)site_coc[i]);
+  heads = block_reduce(heads, OpAdd(), 0ull, red64);
+  por = block_reduce(por, OpOr(), 0ull, red64);
+  pand = block_reduce(pand, OpAnd(), ~0ull, red64);
+  npat = block_reduce(npat, OpAdd(), 0ull, red64);
+  if (threadIdx.x == 0) {
+    if (heads) atomicAdd(&st->branch_sites, heads);
+    if (npat) {
+      atomicOr(&st->pat_or, por);
+      atomicAnd(&st->pat_and, pand);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kTileThreads) k_pattern_runs(PatternArgs a) {
+  __shared__ Seg sh[33];
+  __shared__ u64 pre_slot[2];
+  __shared__ u64 red64[32];
+  DevState* st = &a.arena->st;
+  const u64 n = *a.n;
+  const u64* words = *a.cur ? a.b : a.a;
+  const u32 ntiles = (u32)((n + kTile - 1) / kTile);
+  u64 msum = 0, nsum = 0;
+  for (u32 tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const u64 base = (u64)tile * kTile;
+    const u64 pos0 = base + (u64)threadIdx.x * kTileItems;
+    const int nvalid = pos0 < n ? (int)umin64(n - pos0, (u64)kTileItems) : 0;
+    const u64 tile_n = umin64(n - base, (u64)kTile);
+    u64 key[kTileItems];
+#pragma unroll
+    for (int k = 0; k < kTileItems; ++k) key[k] = k < nvalid ? words[pos0 + k] : 0ull;
+    const u64 prev = (pos0 > 0 && nvalid > 0) ? words[pos0 - 1] : 0ull;
+    tile_runs<kTileItems>(
+        key, nvalid, pos0, prev, tile_n, [](u64 x) { return x >> 1; }, [](u64 x) { return x & 1ull; },
+        [&](u64 len, u64 t) {
+          msum += umin64(t, len - t);
+          nsum += len;
+        },
+        &a.tiles[tile], sh, pre_slot);
+  }
+  msum = block_reduce(msum, OpAdd(), 0ull, red64);
+  nsum = block_reduce(nsum, OpAdd(), 0ull, red64);
+  if (threadIdx.x == 0) {
+    if (msum) atomicAdd(&st->minsum, msum);
+    if (nsum) atomicAdd(&st->npat, nsum);
+  }
+}
+
+// Cross-tile fix-up: one block per level walks that level's tile summaries
+// in chunks with a segmented scan and emits every run that crosses a tile
+// boundary (and the final run), exactly once.
+template <int KIND>
+__global__ void __launch_bounds__(1024) k_fixup(const TileSum* tiles, u32 ntiles_max, const u64* n_dev, u64 n_host,
+                                                u64* over, u64 over_cap, Arena* arena) {
+  __shared__ Seg sh[33];
+  __shared__ u64 red64[32];
+  DevState* st = &arena->st;
+  const int level = blockIdx.x;
+  const u64 n = n_dev ? *n_dev : n_host;
+  const u32 ntiles = (u32)((n + kTile - 1) / kTile);
+  const TileSum* ts = tiles + (u64)level * ntiles_max;
+  Seg carry = seg_identity();
+  u64 msum = 0, nsum = 0;
+  auto emit = [&](u64 len, u64 wsum) {
+    if (KIND == 0) {
+      if (len < (u64)kCocDense) atomicAdd(&arena->mem_coc[level][len], 1ull);
+      else overflow_append(over, over_cap, st, level, len);
+    } else if (KIND == 1) {
+      if (len < (u64)kCocDense) atomicAdd(&arena->site_coc[len], 1ull);
+      else overflow_append(over, over_cap, st, kTagSites, len);
+    } else {
+      msum += umin64(wsum, len - wsum);
+      nsum += len;
+    }
+  };
+  for (u32 c0 = 0; c0 < ntiles; c0 += blockDim.x) {
+    const u32 t = c0 + threadIdx.x;
+    Seg e = seg_identity();
+    TileSum s;
+    if (t < ntiles) {
+      s = ts[t];
+      e.b = s.has_b;
+      e.v = s.has_b ? s.suf : s.tot;
+      e.w = s.has_b ? s.suf_w : s.tot_w;
+    }
+    Seg agg;
+    Seg ex = block_seg_scan(e, &agg, sh);
+    ex = seg_op(carry, ex);
+    if (t < ntiles && s.has_b && ex.b) emit(ex.v + s.pre, ex.w + s.pre_w);
+    carry = seg_op(carry, agg);
+  }
+  if (threadIdx.x == 0 && carry.b) emit(carry.v, carry.w);
+  if (KIND == 2) {
+    msum = block_reduce(msum, OpAdd(), 0ull, red64);
+    nsum = block_reduce(nsum, OpAdd(), 0ull, red64);
+    if (threadIdx.x == 0) {
+      if (msum) atomicAdd(&st->minsum, msum);
+      if (nsum) atomicAdd(&st->npat, nsum);
+    }
+  }
+}
+
+}  // namespace
+
+void launch_branch_ingest(const BranchIngestArgs& a, cudaStream_t s) {
+  if (a.n == 0) return;
+  const u64 per_block = (u64)kBrThreads * kBrItems;
+  u64 blocks = (a.n + per_block - 1) / per_block;
+  if (blocks > 152ull * 8) blocks = 152ull * 8;
+  k_branch_ingest<<<(unsigned)blocks, kBrThreads, 0, s>>>(a);
+  count_launches(1);
+}
+
+void launch_branch_windows(const WindowArgs& a, cudaStream_t s) {
+  if (a.ntiles == 0) return;
+  unsigned g = (unsigned)(a.grid < (int)a.ntiles ? a.grid : (int)a.ntiles);
+  k_windows<<<g, kTileThreads, 0, s>>>(a);
+  count_launches(1);
+}
+
+void launch_pattern_runs(const PatternArgs& a, cudaStream_t s) {
+  if (a.ntiles == 0) return;
+  unsigned g = (unsigned)(a.grid < (int)a.ntiles ? a.grid : (int)a.ntiles);
+  k_pattern_runs<<<g, kTileThreads, 0, s>>>(a);
+  count_launches(1);
+}
+
+void launch_runs_fixup(int kind, const TileSum* tiles, u32 ntiles_max, const u64* n_dev, u64 n_host, int levels,
+                       u64* over, u64 over_cap, Arena* arena, cudaStream_t s) {
+  if (ntiles_max == 0) return;
+  if (kind == 0)
+    k_fixup<0><<<levels, 1024, 0, s>>>(tiles, ntiles_max, n_dev, n_host, over, over_cap, arena);
+  else if (kind == 1)
+    k_fixup<1><<<levels, 1024, 0, s>>>(tiles, ntiles_max, n_dev, n_host, over, over_cap, arena);
+  else
+    k_fixup<2><<<levels, 1024, 0, s>>>(tiles, ntiles_max, n_dev, n_host, over, over_cap, arena);
+  count_launches(1);
+}
+
+}  // namespace aiwc

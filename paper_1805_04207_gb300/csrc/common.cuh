@@ -1,0 +1,72 @@
+// Small device helpers shared by the kernels.
+#pragma once
+
+#include "aiwc_internal.cuh"
+
+namespace aiwc {
+
+template <typename T, typename Op>
+__device__ __forceinline__ T warp_reduce(T x, Op op) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = op(x, __shfl_xor_sync(0xffffffffu, x, o));
+  return x;
+}
+
+struct OpAdd { template <typename T> __device__ T operator()(T a, T b) const { return a + b; } };
+struct OpOr { template <typename T> __device__ T operator()(T a, T b) const { return a | b; } };
+struct OpAnd { template <typename T> __device__ T operator()(T a, T b) const { return a & b; } };
+struct OpMin { template <typename T> __device__ T operator()(T a, T b) const { return a < b ? a : b; } };
+struct OpMax { template <typename T> __device__ T operator()(T a, T b) const { return a > b ? a : b; } };
+
+// Block-wide reduction; every thread gets the result. scratch: 32 entries.
+template <typename T, typename Op>
+__device__ __forceinline__ T block_reduce(T x, Op op, T identity, T* scratch) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  x = warp_reduce(x, op);
+  __syncthreads();
+  if (lane == 0) scratch[w] = x;
+  __syncthreads();
+  T v = lane < nw ? scratch[lane] : identity;
+  v = warp_reduce(v, op);
+  return v;
+}
+
+// Marks work-item ids in a bitmap, one atomicOr per distinct bitmap word in
+// the warp. All 32 lanes must call it; lanes with valid == false add nothing.
+// Ids >= max_wi are not marked and raise *err_bits |= kErrWorkItem.
+__device__ __forceinline__ void mark_work_items(u32* bitmap, u64 max_wi, u32 wi, bool valid, u32* err_bits) {
+  const int lane = threadIdx.x & 31;
+  if (valid && (u64)wi >= max_wi) {
+    *err_bits |= kErrWorkItem;
+    valid = false;
+  }
+  u32 todo = __ballot_sync(0xffffffffu, valid);
+  const u32 word = wi >> 5;
+  const u32 bit = 1u << (wi & 31);
+  while (todo) {
+    const int leader = __ffs(todo) - 1;
+    const u32 lw = __shfl_sync(0xffffffffu, word, leader);
+    const bool mine = ((todo >> lane) & 1u) && word == lw;
+    const u32 grp = __ballot_sync(0xffffffffu, mine);
+    const u32 bits = __reduce_or_sync(0xffffffffu, mine ? bit : 0u);
+    if (lane == leader) atomicOr(&bitmap[lw], bits);
+    todo &= ~grp;
+  }
+}
+
+// Appends a tagged value to the overflow list.
+__device__ __forceinline__ void overflow_append(u64* over, u64 cap, DevState* st, int tag, u64 value) {
+  const u64 e = ((u64)tag << 56) | (value & kValueMask);
+  const u64 idx = atomicAdd(&st->n_over, 1ull);
+  if (idx < cap) {
+    over[idx] = e;
+    atomicOr(&st->over_or, e);
+    atomicAnd(&st->over_and, e);
+  } else {
+    atomicOr(&st->err, kErrOverflow);
+  }
+}
+
+__device__ __forceinline__ u64 umin64(u64 a, u64 b) { return a < b ? a : b; }
+
+}  // namespace aiwc

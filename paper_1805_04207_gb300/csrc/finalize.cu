@@ -1,0 +1,378 @@
+// End-of-kernel statistics (Sec. V, kernelEnd): coverage counts, entropies,
+// order statistics and ratios from the exact integer distributions.
+//
+// Every distribution is held as a dense count array for small values plus a
+// tagged, sorted overflow list for large ones, so all integers are exact and
+// every sum below runs in a fixed order (results do not depend on scheduling).
+#include <math.h>
+
+#include "aiwc_internal.cuh"
+#include "common.cuh"
+
+namespace aiwc {
+namespace {
+
+constexpr int kFinThreads = 1024;
+
+__global__ void k_opcode_dist(const u64* hist, u32 n_opcodes, u64* over, u64 cap, Arena* arena) {
+  __shared__ u64 red64[32];
+  DevState* st = &arena->st;
+  u64 uniq = 0, tot = 0;
+  for (u32 o = blockIdx.x * blockDim.x + threadIdx.x; o < n_opcodes; o += gridDim.x * blockDim.x) {
+    const u64 c = hist[o];
+    if (c) {
+      ++uniq;
+      tot += c;
+      if (c < (u64)kCocDense) atomicAdd(&arena->opc_coc[c], 1ull);
+      else overflow_append(over, cap, st, kTagOpcodes, c);
+    }
+  }
+  uniq = block_reduce(uniq, OpAdd(), 0ull, red64);
+  tot = block_reduce(tot, OpAdd(), 0ull, red64);
+  if (threadIdx.x == 0) {
+    if (uniq) atomicAdd(&st->unique_opcodes, uniq);
+    if (tot) atomicAdd(&st->total_instructions, tot);
+  }
+}
+
+__global__ void k_wi_count(const u32* bitmap, Arena* arena) {
+  __shared__ u64 red64[32];
+  DevState* st = &arena->st;
+  const u32 lo = st->wi_min, hi = st->wi_max;
+  u64 c = 0;
+  if (lo <= hi) {
+    const u64 w0 = lo >> 5, w1 = hi >> 5;
+    for (u64 w = w0 + (u64)blockIdx.x * blockDim.x + threadIdx.x; w <= w1; w += (u64)gridDim.x * blockDim.x)
+      c += __popc(bitmap[w]);
+  }
+  c = block_reduce(c, OpAdd(), 0ull, red64);
+  if (threadIdx.x == 0 && c) atomicAdd(&st->work_items, c);
+}
+
+__global__ void k_wi_clear(u32* bitmap, Arena* arena) {
+  const DevState* st = &arena->st;
+  const u32 lo = st->wi_min, hi = st->wi_max;
+  if (lo > hi) return;
+  const u64 w0 = lo >> 5, w1 = hi >> 5;
+  for (u64 w = w0 + (u64)blockIdx.x * blockDim.x + threadIdx.x; w <= w1; w += (u64)gridDim.x * blockDim.x)
+    bitmap[w] = 0u;
+}
+
+__global__ void k_identities(Arena* arena) {
+  DevState* st = &arena->st;
+  st->mem_and = ~0ull;
+  st->br_and = ~0ull;
+  st->pat_and = ~0ull;
+  st->run_and = ~0ull;
+  st->over_and = ~0ull;
+  st->wi_min = 0xFFFFFFFFu;
+  st->wi_max = 0u;
+}
+
+// ---------------------------------------------------------------- finalize
+
+struct Shared {
+  u64 red[32];
+  double redd[32];
+  u64 scan[33];
+  u64 scan2[33];
+  u64 tag_begin[kNumTags + 1];
+  u64 found;
+  u64 found_k;
+};
+
+__device__ __forceinline__ u64 block_sum_u64(u64 x, Shared& s) { return block_reduce(x, OpAdd(), 0ull, s.red); }
+
+__device__ __forceinline__ double block_sum_f64(double x, Shared& s) {
+  // fixed-shape tree: deterministic for a fixed assignment of inputs to threads
+  return block_reduce(x, OpAdd(), 0.0, s.redd);
+}
+
+// Inclusive block scan of two u64 sequences at once.
+__device__ __forceinline__ void block_scan2(u64 x, u64 y, u64* ix, u64* iy, u64* tx, u64* ty, Shared& s) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  u64 a = x, b = y;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    u64 pa = __shfl_up_sync(0xffffffffu, a, o), pb = __shfl_up_sync(0xffffffffu, b, o);
+    if (lane >= o) { a += pa; b += pb; }
+  }
+  __syncthreads();
+  if (lane == 31) { s.scan[w] = a; s.scan2[w] = b; }
+  __syncthreads();
+  if (w == 0) {
+    u64 va = lane < nw ? s.scan[lane] : 0ull, vb = lane < nw ? s.scan2[lane] : 0ull;
+    u64 ia = va, ib = vb;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      u64 pa = __shfl_up_sync(0xffffffffu, ia, o), pb = __shfl_up_sync(0xffffffffu, ib, o);
+      if (lane >= o) { ia += pa; ib += pb; }
+    }
+    if (lane < nw) { s.scan[lane] = ia - va; s.scan2[lane] = ib - vb; }
+    if (lane == nw - 1) { s.scan[32] = ia; s.scan2[32] = ib; }
+  }
+  __syncthreads();
+  *ix = a + s.scan[w];
+  *iy = b + s.scan2[w];
+  *tx = s.scan[32];
+  *ty = s.scan2[32];
+  __syncthreads();
+}
+
+// Fewest groups whose sizes cover num/den of `total`: the smallest k with
+// den * (sum of the k largest sizes) >= num * total. Sizes come as the
+// overflow segment [ob, oe) (ascending) followed by dense[c] groups of size c.
+__device__ u64 cover_walk(const u64* dense, int dense_n, const u64* over, u64 ob, u64 oe, u64 total, u32 num,
+                          u32 den, Shared& s) {
+  if (total == 0) return 0;
+  typedef unsigned __int128 u128;
+  const u128 target = (u128)num * total;
+  u64 cum = 0, kcount = 0;
+  // large sizes, descending
+  for (u64 c0 = 0; c0 < oe - ob; c0 += blockDim.x) {
+    const u64 idx = c0 + threadIdx.x;
+    const bool v = idx < oe - ob;
+    const u64 c = v ? (over[oe - 1 - idx] & kValueMask) : 0ull;
+    u64 ic, im, tc, tm;
+    block_scan2(c, v ? 1ull : 0ull, &ic, &im, &tc, &tm, s);
+    if (threadIdx.x == 0) s.found = ~0ull;
+    __syncthreads();
+    if (v && (u128)den * (cum + ic) >= target) atomicMin(&s.found, idx - c0);
+    __syncthreads();
+    const u64 f = s.found;
+    __syncthreads();
+    if (f != ~0ull) return kcount + f + 1;
+    cum += tc;
+    kcount += tm;
+  }
+  // dense sizes, descending: thread t takes size dense_n-1-t (chunks of blockDim)
+  for (int c0 = 0; c0 < dense_n; c0 += blockDim.x) {
+    const int ci = dense_n - 1 - (c0 + (int)threadIdx.x);
+    const bool v = ci >= 1;
+    const u64 m = v ? dense[ci] : 0ull;
+    const u64 mc = m * (u64)(v ? ci : 0);
+    u64 imc, im, tmc, tm;
+    block_scan2(mc, m, &imc, &im, &tmc, &tm, s);
+    if (threadIdx.x == 0) { s.found = ~0ull; s.found_k = 0; }
+    __syncthreads();
+    const bool hit = v && m && (u128)den * (cum + imc) >= target;
+    u64 k_here = 0;
+    if (hit) {
+      // the largest size reaching the target; within it, how many groups of size ci
+      const u128 before = (u128)den * (cum + imc - mc);
+      const u128 need = target > before ? target - before : 0;
+      const u128 per = (u128)den * (u64)ci;
+      const u64 r = (u64)((need + per - 1) / per);
+      k_here = kcount + (im - m) + (r ? r : 1);
+      atomicMin(&s.found, (u64)(c0 + threadIdx.x));
+    }
+    __syncthreads();
+    if (hit && (u64)(c0 + threadIdx.x) == s.found) s.found_k = k_here;
+    __syncthreads();
+    const u64 found = s.found, found_k = s.found_k;
+    __syncthreads();
+    if (found != ~0ull) return found_k;
+    cum += tmc;
+    kcount += tm;
+  }
+  return kcount;
+}
+
+// k-th smallest (0-based) value of a value distribution: dense[v] values v
+// for v < dense_n, then the ascending overflow segment [ob, oe).
+__device__ u64 kth_value(const u64* dense, int dense_n, const u64* over, u64 ob, u64 oe, u64 k, Shared& s) {
+  // each thread owns a contiguous slice of bins
+  const int per = (dense_n + blockDim.x - 1) / blockDim.x;
+  const int b0 = threadIdx.x * per;
+  u64 mine = 0;
+  for (int v = b0; v < b0 + per && v < dense_n; ++v) mine += dense[v];
+  u64 inc, dummy, tot, dt;
+  block_scan2(mine, 0ull, &inc, &dummy, &tot, &dt, s);
+  if (threadIdx.x == 0) s.found = ~0ull;
+  __syncthreads();
+  if (k < tot) {
+    const u64 ex = inc - mine;
+    if (k >= ex && k < inc) {
+      u64 c = ex;
+      for (int v = b0; v < b0 + per && v < dense_n; ++v) {
+        c += dense[v];
+        if (k < c) { s.found = (u64)v; break; }
+      }
+    }
+  } else if (threadIdx.x == 0) {
+    const u64 j = k - tot;
+    s.found = ob + j < oe ? (over[ob + j] & kValueMask) : 0ull;
+  }
+  __syncthreads();
+  const u64 r = s.found;
+  __syncthreads();
+  return r;
+}
+
+__device__ void order_stats(const u64* dense, const u64* over, u64 ob, u64 oe, u64* cnt, u64* mn, u64* mx, u64* lo,
+                            u64* hi, double* med, Shared& s) {
+  u64 c = 0;
+  for (int v = threadIdx.x; v < kValDense; v += blockDim.x) c += dense[v];
+  c = block_sum_u64(c, s) + (oe - ob);
+  *cnt = c;
+  if (c == 0) { *mn = *mx = *lo = *hi = 0; *med = 0.0; return; }
+  *mn = kth_value(dense, kValDense, over, ob, oe, 0, s);
+  *mx = kth_value(dense, kValDense, over, ob, oe, c - 1, s);
+  *lo = kth_value(dense, kValDense, over, ob, oe, (c - 1) / 2, s);
+  *hi = kth_value(dense, kValDense, over, ob, oe, c / 2, s);
+  *med = 0.5 * ((double)*lo + (double)*hi);
+}
+
+// Sum over groups of c*log2(c), given m_c for small c and the overflow list
+// entries for large c. FP64 path: each term in double. FP32 path: with
+// c = f * 2^e (f in [1,2)), c*log2(c) = c*e + c*log2(f); the first part is an
+// exact integer, the second is accumulated in float with Kahan compensation
+// per thread; only the cross-thread reduction is in double.
+__device__ double clog_sum(const u64* dense, const u64* over, u64 ob, u64 oe, u32 precision, Shared& s) {
+  if (precision == 0) {
+    double acc = 0.0;
+    for (int c = threadIdx.x; c < kCocDense; c += blockDim.x) {
+      const u64 m = dense[c];
+      if (m && c > 1) acc += (double)m * ((double)c * log2((double)c));
+    }
+    for (u64 i = ob + threadIdx.x; i < oe; i += blockDim.x) {
+      const double c = (double)(over[i] & kValueMask);
+      acc += c * log2(c);
+    }
+    return block_sum_f64(acc, s);
+  }
+  u64 exact = 0;
+  float sum = 0.0f, comp = 0.0f;
+  auto add = [&](u64 c, u64 m) {
+    const int e = 63 - __clzll((long long)c);
+    exact += m * c * (u64)e;
+    const float f = (float)((double)c / (double)(1ull << e));
+    const float term = (float)(m * c) * log2f(f);
+    const float y = term - comp;
+    const float t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+  };
+  for (int c = threadIdx.x; c < kCocDense; c += blockDim.x) {
+    const u64 m = dense[c];
+    if (m && c > 1) add((u64)c, m);
+  }
+  for (u64 i = ob + threadIdx.x; i < oe; i += blockDim.x) add(over[i] & kValueMask, 1);
+  const u64 ex = block_sum_u64(exact, s);
+  const double fl = block_sum_f64((double)sum - (double)comp, s);
+  return (double)ex + fl;
+}
+
+__global__ void __launch_bounds__(kFinThreads) k_finalize(FinalizeArgs a) {
+  __shared__ Shared s;
+  Arena* ar = a.arena;
+  const DevState& st = ar->st;
+  const u64* over = *a.over_cur ? a.over_b : a.over_a;
+  const u64 nover = umin64(st.n_over, a.over_cap);
+  // segment of each tag in the sorted overflow list (lower bound of tag << 56)
+  if (threadIdx.x <= kNumTags) {
+    const u64 key = (u64)threadIdx.x << 56;
+    u64 lo = 0, hi = nover;
+    while (lo < hi) {
+      const u64 mid = (lo + hi) >> 1;
+      if (over[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    s.tag_begin[threadIdx.x] = lo;
+  }
+  __syncthreads();
+  aiwc_metrics* m = &a.result->m;
+  // memory
+  const u64 N = st.total_reads + st.total_writes;
+  for (int l = 0; l < kLevels; ++l) {
+    const double S = clog_sum(ar->mem_coc[l], over, s.tag_begin[l], s.tag_begin[l + 1], a.precision, s);
+    if (threadIdx.x == 0) {
+      double H = 0.0;
+      if (N) {
+        H = a.precision ? (double)(log2f((float)N)) : log2((double)N);
+        if (a.precision) {
+          // log2 N = e + log2(f) with the same split as the terms
+          const int e = 63 - __clzll((long long)N);
+          H = (double)e + (double)log2f((float)((double)N / (double)(1ull << e)));
+        }
+        H -= S / (double)N;
+        if (H < 0.0) H = 0.0;
+      }
+      m->entropy[l] = H;
+    }
+  }
+  const u64 fcover = cover_walk(ar->mem_coc[0], kCocDense, over, s.tag_begin[0], s.tag_begin[1], N, a.cover_num,
+                                a.cover_den, s);
+  const u64 scover = cover_walk(ar->site_coc, kCocDense, over, s.tag_begin[kTagSites], s.tag_begin[kTagSites + 1],
+                                st.n_branch, a.cover_num, a.cover_den, s);
+  const u64 ocover = cover_walk(ar->opc_coc, kCocDense, over, s.tag_begin[kTagOpcodes],
+                                s.tag_begin[kTagOpcodes + 1], st.total_instructions, a.cover_num, a.cover_den, s);
+  u64 ic, imn, imx, ilo, ihi, pc, pmn, pmx, plo, phi;
+  double imed, pmed;
+  order_stats(ar->itb_dense, over, s.tag_begin[kTagItb], s.tag_begin[kTagItb + 1], &ic, &imn, &imx, &ilo, &ihi, &imed,
+              s);
+  order_stats(ar->ipt_dense, over, s.tag_begin[kTagIpt], s.tag_begin[kTagIpt + 1], &pc, &pmn, &pmx, &plo, &phi, &pmed,
+              s);
+  if (threadIdx.x == 0) {
+    m->total_instructions = st.total_instructions;
+    m->unique_opcodes = st.unique_opcodes;
+    m->opcode_cover = ocover;
+    m->work_items = st.work_items;
+    m->barriers = st.barriers;
+    m->itb_count = ic; m->itb_min = imn; m->itb_max = imx; m->itb_median_lo = ilo; m->itb_median_hi = ihi;
+    m->itb_median = imed;
+    m->ipt_count = pc; m->ipt_min = pmn; m->ipt_max = pmx; m->ipt_median_lo = plo; m->ipt_median_hi = phi;
+    m->ipt_median = pmed;
+    m->total_reads = st.total_reads;
+    m->total_writes = st.total_writes;
+    m->footprint = st.footprint;
+    m->footprint_cover = fcover;
+    m->unique_reads = st.unique_reads;
+    m->unique_writes = st.unique_writes;
+    m->branch_events = st.n_branch;
+    m->branch_sites = st.branch_sites;
+    m->branch_cover = scover;
+    m->branch_patterns = st.npat;
+    m->branch_minsum = st.minsum;
+    if (a.precision)
+      m->albe = st.npat ? (double)((2.0f * (float)st.minsum) / (float)st.npat) : 0.0;
+    else
+      m->albe = st.npat ? 2.0 * (double)st.minsum / (double)st.npat : 0.0;
+    m->unique_rw_ratio = (double)st.unique_reads / (double)st.unique_writes;
+    m->reread_ratio = (double)st.unique_reads / (double)st.total_reads;
+    m->rewrite_ratio = (double)st.unique_writes / (double)st.total_writes;
+    m->opcode_hist = nullptr;
+    a.result->err = st.err;
+  }
+}
+
+}  // namespace
+
+void launch_opcode_dist(const u64* hist, u32 n_opcodes, u64* over, u64 over_cap, Arena* arena, cudaStream_t s) {
+  if (n_opcodes == 0) return;
+  unsigned blocks = (n_opcodes + 255) / 256;
+  if (blocks > 64) blocks = 64;
+  k_opcode_dist<<<blocks, 256, 0, s>>>(hist, n_opcodes, over, over_cap, arena);
+  count_launches(1);
+}
+
+void launch_wi_count(const u32* bitmap, Arena* arena, cudaStream_t s) {
+  k_wi_count<<<152 * 2, 256, 0, s>>>(bitmap, arena);
+  count_launches(1);
+}
+
+void launch_wi_clear(u32* bitmap, Arena* arena, cudaStream_t s) {
+  k_wi_clear<<<152 * 2, 256, 0, s>>>(bitmap, arena);
+  count_launches(1);
+}
+
+void launch_reset_identities(Arena* arena, cudaStream_t s) {
+  k_identities<<<1, 1, 0, s>>>(arena);
+  count_launches(1);
+}
+
+void launch_finalize(const FinalizeArgs& a, cudaStream_t s) {
+  k_finalize<<<1, kFinThreads, 0, s>>>(a);
+  count_launches(1);
+}
+
+}  // namespace aiwc

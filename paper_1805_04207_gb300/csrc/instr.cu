@@ -1,0 +1,247 @@
+// Instruction path (Table I compute and parallelism rows; Sec. III / Sec. V):
+// opcode histogram, barrier count, instructions-to-barrier (ITB) segments and
+// instructions per thread (IPT).
+//
+// One warp scans one run (a work-item's opcodes in program order) 256
+// opcodes at a time, 8 per lane. Segments closed by two barriers inside the
+// run are emitted directly; a warp-wide segmented scan carries the open tally
+// across lanes and steps. What a run cannot finish alone -- the tally before
+// its first barrier and after its last -- is left in a 4-word run summary;
+// after the runs are sorted by (work-item, push order) one thread per
+// work-item chains its summaries, emitting the cross-run segments, the final
+// implicit-barrier segment and the work-item's IPT.
+#include "aiwc_internal.cuh"
+#include "common.cuh"
+#include "runs.cuh"
+
+namespace aiwc {
+namespace {
+
+constexpr int kInThreads = 256;
+constexpr int kInWarps = kInThreads / 32;
+
+// Value histograms (ITB / IPT): privatised in shared memory below kValSmem,
+// global dense below kValDense, overflow list above.
+__device__ __forceinline__ void emit_value(u32* smem_hist, u64* dense, u64* over, u64 cap, DevState* st, int tag,
+                                           u64 v) {
+  if (v < (u64)kValSmem) atomicAdd(&smem_hist[v], 1u);
+  else if (v < (u64)kValDense) atomicAdd(&dense[v], 1ull);
+  else overflow_append(over, cap, st, tag, v);
+}
+
+__device__ __forceinline__ Seg warp_seg_scan(const Seg& x, Seg* agg) {
+  const int lane = threadIdx.x & 31;
+  Seg inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    Seg y = seg_shfl_up(inc, o);
+    if (lane >= o) inc = seg_op(y, inc);
+  }
+  Seg ex = seg_shfl_up(inc, 1);
+  if (lane == 0) ex = seg_identity();
+  agg->b = __shfl_sync(0xffffffffu, inc.b, 31);
+  agg->v = __shfl_sync(0xffffffffu, inc.v, 31);
+  agg->w = 0;
+  return ex;
+}
+
+// hist_mode: 0 = per-warp shared histograms, 1 = one shared histogram per
+// block, 2 = global atomics.
+__global__ void __launch_bounds__(kInThreads) k_instr_runs(RunBatchArgs a, int hist_mode) {
+  extern __shared__ u32 dyn[];
+  __shared__ u32 itb_small[kValSmem];
+  __shared__ u64 red64[32];
+  __shared__ u32 red32[32];
+  DevState* st = &a.arena->st;
+  const u32 nop = a.n_opcodes;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const u32 hwords = hist_mode == 0 ? nop * kInWarps : (hist_mode == 1 ? nop : 0u);
+  for (u32 i = threadIdx.x; i < hwords; i += kInThreads) dyn[i] = 0u;
+  for (int i = threadIdx.x; i < kValSmem; i += kInThreads) itb_small[i] = 0u;
+  __syncthreads();
+  u32* my_hist = hist_mode == 0 ? dyn + wp * nop : dyn;
+  u64 nbar = 0, run_or = 0, run_and = ~0ull;
+  u32 err = 0, wmin = 0xFFFFFFFFu, wmax = 0u;
+  const u64 gwarp = (u64)blockIdx.x * kInWarps + wp;
+  const u64 nwarps = (u64)gridDim.x * kInWarps;
+  for (u64 r = gwarp; r < a.n_runs; r += nwarps) {
+    const u64 off = a.run_off[r];
+    u64 len = a.run_len[r];
+    const u32 wi = a.run_wi[r];
+    if (off > a.n_ops || len > a.n_ops - off) {
+      err |= kErrRun;
+      len = 0;
+    }
+    mark_work_items(a.wi_bitmap, a.max_wi, wi, lane == 0, &err);
+    if ((u64)wi < a.max_wi) {
+      wmin = min(wmin, wi);
+      wmax = max(wmax, wi);
+    }
+    const uint16_t* p = a.ops + off;
+    const bool aligned = ((reinterpret_cast<uintptr_t>(p) & 15u) == 0);
+    Seg carry = seg_identity();
+    u64 tot = 0, run_pre = 0;
+    bool have_pre = false;
+    for (u64 s0 = 0; s0 < len; s0 += 256) {
+      const u64 my0 = s0 + (u64)lane * 8;
+      const int nv = my0 < len ? (int)umin64(len - my0, 8ull) : 0;
+      u32 op[8];
+      if (nv == 8 && aligned) {
+        const uint4 v = __ldcs(reinterpret_cast<const uint4*>(p + my0));
+        op[0] = v.x & 0xFFFFu; op[1] = v.x >> 16; op[2] = v.y & 0xFFFFu; op[3] = v.y >> 16;
+        op[4] = v.z & 0xFFFFu; op[5] = v.z >> 16; op[6] = v.w & 0xFFFFu; op[7] = v.w >> 16;
+      } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) op[k] = k < nv ? (u32)p[my0 + k] : 0u;
+      }
+      int fb = -1;
+      u64 lead = 0, cur = 0, cnt = 0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        if (k < nv) {
+          const u32 o = op[k];
+          if (o == AIWC_BARRIER) {
+            if (fb >= 0) emit_value(itb_small, a.arena->itb_dense, a.over, a.over_cap, st, kTagItb, cur);
+            else fb = k;
+            cur = 0;
+            ++nbar;
+          } else {
+            if (o < nop) {
+              if (hist_mode == 2) atomicAdd(&a.opc_hist[o], 1ull);
+              else atomicAdd(&my_hist[o], 1u);
+            } else {
+              err |= kErrOpcode;
+            }
+            ++cnt;
+            if (fb < 0) ++lead; else ++cur;
+          }
+        }
+      }
+      Seg e;
+      e.b = fb >= 0 ? 1u : 0u;
+      e.v = fb >= 0 ? cur : lead;
+      e.w = 0;
+      Seg agg;
+      Seg ex = seg_op(carry, warp_seg_scan(e, &agg));
+      if (fb >= 0) {
+        const u64 seg = ex.v + lead;
+        if (ex.b) emit_value(itb_small, a.arena->itb_dense, a.over, a.over_cap, st, kTagItb, seg);
+        else { run_pre = seg; have_pre = true; }
+      }
+      carry = seg_op(carry, agg);
+      tot += warp_reduce(cnt, OpAdd());
+    }
+    const u32 pre_owner = __ballot_sync(0xffffffffu, have_pre);
+    if (pre_owner) run_pre = __shfl_sync(0xffffffffu, run_pre, __ffs(pre_owner) - 1);
+    if (lane == 0) {
+      const u64 seq = a.seq_base + r;
+      const u64 key = ((u64)wi << 32) | (seq & 0xFFFFFFFFull);
+      a.run_keys[seq] = key;
+      u64* sm = a.run_sum + 4 * seq;
+      sm[0] = carry.b;
+      sm[1] = carry.b ? run_pre : tot;
+      sm[2] = carry.b ? carry.v : 0ull;
+      sm[3] = tot;
+      run_or |= key;
+      run_and &= key;
+    }
+    have_pre = false;
+  }
+  __syncthreads();
+  if (hist_mode == 0) {
+    for (u32 o = threadIdx.x; o < nop; o += kInThreads) {
+      u32 s = 0;
+      for (int q = 0; q < kInWarps; ++q) s += dyn[q * nop + o];
+      if (s) atomicAdd(&a.opc_hist[o], (u64)s);
+    }
+  } else if (hist_mode == 1) {
+    for (u32 o = threadIdx.x; o < nop; o += kInThreads)
+      if (dyn[o]) atomicAdd(&a.opc_hist[o], (u64)dyn[o]);
+  }
+  for (int i = threadIdx.x; i < kValSmem; i += kInThreads)
+    if (itb_small[i]) atomicAdd(&a.arena->itb_dense[i], (u64)itb_small[i]);
+  nbar = block_reduce(nbar, OpAdd(), 0ull, red64);
+  run_or = block_reduce(run_or, OpOr(), 0ull, red64);
+  run_and = block_reduce(run_and, OpAnd(), ~0ull, red64);
+  err = block_reduce(err, OpOr(), 0u, red32);
+  wmin = block_reduce(wmin, OpMin(), 0xFFFFFFFFu, red32);
+  wmax = block_reduce(wmax, OpMax(), 0u, red32);
+  if (threadIdx.x == 0) {
+    if (nbar) atomicAdd(&st->barriers, nbar);
+    if (wmin <= wmax) {
+      atomicOr(&st->run_or, run_or);
+      atomicAnd(&st->run_and, run_and);
+      atomicMin(&st->wi_min, wmin);
+      atomicMax(&st->wi_max, wmax);
+    }
+    if (err) atomicOr(&st->err, err);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&st->n_runs, a.n_runs);
+}
+
+// One thread per run position in (work-item, push order); the first run of
+// each work-item chains that work-item's runs.
+__global__ void __launch_bounds__(256) k_instr_combine(CombineArgs a) {
+  __shared__ u32 itb_small[kValSmem];
+  __shared__ u32 ipt_small[kValSmem];
+  DevState* st = &a.arena->st;
+  for (int i = threadIdx.x; i < kValSmem; i += blockDim.x) { itb_small[i] = 0u; ipt_small[i] = 0u; }
+  __syncthreads();
+  const u64* keys = *a.cur ? a.b : a.a;
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < a.n_runs; i += stride) {
+    const u64 k = keys[i];
+    const u64 wi = k >> 32;
+    if (i > 0 && (keys[i - 1] >> 32) == wi) continue;
+    u64 open = 0, ipt = 0;
+    for (u64 j = i; j < a.n_runs; ++j) {
+      const u64 kj = keys[j];
+      if ((kj >> 32) != wi) break;
+      const u64* sm = a.run_sum + 4 * (kj & 0xFFFFFFFFull);
+      if (sm[0]) {
+        emit_value(itb_small, a.arena->itb_dense, a.over, a.over_cap, st, kTagItb, open + sm[1]);
+        open = sm[2];
+      } else {
+        open += sm[3];
+      }
+      ipt += sm[3];
+    }
+    emit_value(itb_small, a.arena->itb_dense, a.over, a.over_cap, st, kTagItb, open);
+    emit_value(ipt_small, a.arena->ipt_dense, a.over, a.over_cap, st, kTagIpt, ipt);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kValSmem; i += blockDim.x) {
+    if (itb_small[i]) atomicAdd(&a.arena->itb_dense[i], (u64)itb_small[i]);
+    if (ipt_small[i]) atomicAdd(&a.arena->ipt_dense[i], (u64)ipt_small[i]);
+  }
+}
+
+}  // namespace
+
+void launch_instr_runs(const RunBatchArgs& a, cudaStream_t s) {
+  if (a.n_runs == 0) return;
+  int mode;
+  size_t smem;
+  if ((size_t)a.n_opcodes * kInWarps * 4 <= 48 * 1024) { mode = 0; smem = (size_t)a.n_opcodes * kInWarps * 4; }
+  else if ((size_t)a.n_opcodes * 4 <= 96 * 1024) { mode = 1; smem = (size_t)a.n_opcodes * 4; }
+  else { mode = 2; smem = 0; }
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_instr_runs, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    attr_set = true;
+  }
+  u64 blocks = (a.n_runs + kInWarps - 1) / kInWarps;
+  if (blocks > 152ull * 4) blocks = 152ull * 4;
+  k_instr_runs<<<(unsigned)blocks, kInThreads, smem, s>>>(a, mode);
+  count_launches(1);
+}
+
+void launch_instr_combine(const CombineArgs& a, cudaStream_t s) {
+  if (a.n_runs == 0) return;
+  u64 blocks = (a.n_runs + 255) / 256;
+  if (blocks > 152ull * 4) blocks = 152ull * 4;
+  k_instr_combine<<<(unsigned)blocks, 256, 0, s>>>(a);
+  count_launches(1);
+}
+
+}  // namespace aiwc

@@ -1,0 +1,215 @@
+// Memory-event path: ingest (one 16-byte event -> one 64-bit sort word) and
+// the per-skip-level run lengths over the sorted words.
+//
+// Sort word of an access: (space << 62) | (addr << 1) | store, i.e. the key
+// (space, address) of Table I's memory rows with the read/write bit below
+// it. Sorting the words groups equal addresses and, inside an address, reads
+// before writes; the group of skip level n (Sec. III: n = 0 global entropy,
+// n = 1..10 local entropies) is word >> (n + 1).
+#include "aiwc_internal.cuh"
+#include "common.cuh"
+#include "runs.cuh"
+
+namespace aiwc {
+namespace {
+
+constexpr int kIngestThreads = 256;
+constexpr int kIngestItems = 8;
+
+template <bool FILTER>
+__global__ void __launch_bounds__(kIngestThreads) k_mem_ingest(MemIngestArgs a) {
+  __shared__ u64 red64[32];
+  __shared__ u32 red32[32];
+  __shared__ u32 scan_tot[33];
+  __shared__ u64 s_base;
+  DevState* st = &a.arena->st;
+  const uint4* ev = reinterpret_cast<const uint4*>(a.ev);
+  u64 reads = 0, writes = 0, wor = 0, wand = ~0ull, kept = 0;
+  u32 wmin = 0xFFFFFFFFu, wmax = 0u, err = 0u;
+  const u64 per_block = (u64)kIngestThreads * kIngestItems;
+  for (u64 t0 = (u64)blockIdx.x * per_block; t0 < a.n; t0 += (u64)gridDim.x * per_block) {
+    uint4 e[kIngestItems];
+    bool valid[kIngestItems];
+#pragma unroll
+    for (int k = 0; k < kIngestItems; ++k) {
+      const u64 i = t0 + (u64)k * kIngestThreads + threadIdx.x;
+      valid[k] = i < a.n;
+      e[k] = valid[k] ? __ldcs(ev + i) : make_uint4(0u, 0u, 0u, 0u);
+    }
+    u64 word[kIngestItems];
+    bool keep[kIngestItems];
+    u32 nkeep = 0;
+#pragma unroll
+    for (int k = 0; k < kIngestItems; ++k) {
+      const u64 addr = (u64)e[k].x | ((u64)e[k].y << 32);
+      const u32 wi = e[k].z;
+      const u32 flags = (e[k].w >> 8) & 0xFFu;
+      const u32 space = (flags >> 1) & 3u;
+      const u32 store = flags & 1u;
+      mark_work_items(a.wi_bitmap, a.max_wi, wi, valid[k], &err);
+      if (valid[k]) {
+        if ((u64)wi < a.max_wi) {
+          wmin = min(wmin, wi);
+          wmax = max(wmax, wi);
+        }
+        if (addr >> 61) err |= kErrAddr;
+      }
+      keep[k] = valid[k] && ((a.space_mask >> space) & 1u);
+      word[k] = ((u64)space << 62) | ((addr & ((1ull << 61) - 1)) << 1) | store;
+      if (keep[k]) {
+        ++nkeep;
+        if (store) ++writes; else ++reads;
+        wor |= word[k];
+        wand &= word[k];
+      }
+    }
+    kept += nkeep;
+    if (FILTER) {
+      // compact the kept words of this block-tile behind one atomicAdd
+      const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+      u32 inc = nkeep;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        u32 y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+      }
+      if (lane == 31) scan_tot[w] = inc;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        u32 s = 0;
+        for (int q = 0; q < kIngestThreads / 32; ++q) { u32 c = scan_tot[q]; scan_tot[q] = s; s += c; }
+        s_base = atomicAdd(&st->n_words, (u64)s);
+      }
+      __syncthreads();
+      u64 pos = s_base + scan_tot[w] + inc - nkeep;
+#pragma unroll
+      for (int k = 0; k < kIngestItems; ++k)
+        if (keep[k]) a.words[pos++] = word[k];
+      __syncthreads();
+    } else {
+#pragma unroll
+      for (int k = 0; k < kIngestItems; ++k) {
+        const u64 i = t0 + (u64)k * kIngestThreads + threadIdx.x;
+        if (valid[k]) a.words[a.word_base + i] = word[k];
+      }
+    }
+  }
+  reads = block_reduce(reads, OpAdd(), 0ull, red64);
+  writes = block_reduce(writes, OpAdd(), 0ull, red64);
+  wor = block_reduce(wor, OpOr(), 0ull, red64);
+  wand = block_reduce(wand, OpAnd(), ~0ull, red64);
+  kept = block_reduce(kept, OpAdd(), 0ull, red64);
+  wmin = block_reduce(wmin, OpMin(), 0xFFFFFFFFu, red32);
+  wmax = block_reduce(wmax, OpMax(), 0u, red32);
+  err = block_reduce(err, OpOr(), 0u, red32);
+  if (threadIdx.x == 0) {
+    if (reads) atomicAdd(&st->total_reads, reads);
+    if (writes) atomicAdd(&st->total_writes, writes);
+    if (kept) {
+      atomicOr(&st->mem_or, wor);
+      atomicAnd(&st->mem_and, wand);
+      if (!FILTER) atomicAdd(&st->n_words, kept);
+    }
+    if (wmin <= wmax) {
+      atomicMin(&st->wi_min, wmin);
+      atomicMax(&st->wi_max, wmax);
+    }
+    if (err) atomicOr(&st->err, err);
+  }
+}
+
+constexpr int kLvThreads = kTileThreads;
+constexpr int kLvItems = kTileItems;
+
+__global__ void __launch_bounds__(kLvThreads) k_mem_levels(LevelArgs a) {
+  __shared__ u32 coc[kLevels][kCocDense];
+  __shared__ Seg sh[33];
+  __shared__ u64 pre_slot[2];
+  __shared__ u64 red64[32];
+  DevState* st = &a.arena->st;
+  for (int i = threadIdx.x; i < kLevels * kCocDense; i += kLvThreads) (&coc[0][0])[i] = 0u;
+  __syncthreads();
+  const u64 n = *a.n;
+  const u64* words = *a.cur ? a.b : a.a;
+  const u32 ntiles = (u32)((n + kTile - 1) / kTile);
+  u64 heads0 = 0, ur = 0, uw = 0;
+  for (u32 tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const u64 base = (u64)tile * kTile;
+    const u64 pos0 = base + (u64)threadIdx.x * kLvItems;
+    const int nvalid = pos0 < n ? (int)umin64(n - pos0, (u64)kLvItems) : 0;
+    const u64 tile_n = umin64(n - base, (u64)kTile);
+    u64 key[kLvItems];
+    if (nvalid == kLvItems) {
+      const ulonglong2* p = reinterpret_cast<const ulonglong2*>(words + pos0);
+#pragma unroll
+      for (int k = 0; k < kLvItems / 2; ++k) {
+        ulonglong2 v = p[k];
+        key[2 * k] = v.x;
+        key[2 * k + 1] = v.y;
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < kLvItems; ++k) key[k] = k < nvalid ? words[pos0 + k] : 0ull;
+    }
+    const u64 prev = (pos0 > 0 && nvalid > 0) ? words[pos0 - 1] : 0ull;
+    // unique reads / writes: heads of the full word; footprint: heads of word >> 1
+    {
+      u64 pw = prev;
+#pragma unroll
+      for (int k = 0; k < kLvItems; ++k) {
+        if (k < nvalid) {
+          const bool first = pos0 + k == 0;
+          if (first || key[k] != pw) { if (key[k] & 1ull) ++uw; else ++ur; }
+          if (first || (key[k] >> 1) != (pw >> 1)) ++heads0;
+          pw = key[k];
+        }
+      }
+    }
+    for (int l = 0; l < kLevels; ++l) {
+      const int shift = l + 1;
+      tile_runs<kLvItems>(
+          key, nvalid, pos0, prev, tile_n, [shift](u64 x) { return x >> shift; }, [](u64) { return 0ull; },
+          [&](u64 len, u64) {
+            if (len < (u64)kCocDense) atomicAdd(&coc[l][len], 1u);
+            else overflow_append(a.over, a.over_cap, st, l, len);
+          },
+          &a.tiles[(u64)l * a.ntiles + tile], sh, pre_slot);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kLevels * kCocDense; i += kLvThreads) {
+    const u32 c = (&coc[0][0])[i];
+    if (c) atomicAdd(&a.arena->mem_coc[0][0] + i, (u64)c);
+  }
+  heads0 = block_reduce(heads0, OpAdd(), 0ull, red64);
+  ur = block_reduce(ur, OpAdd(), 0ull, red64);
+  uw = block_reduce(uw, OpAdd(), 0ull, red64);
+  if (threadIdx.x == 0) {
+    if (heads0) atomicAdd(&st->footprint, heads0);
+    if (ur) atomicAdd(&st->unique_reads, ur);
+    if (uw) atomicAdd(&st->unique_writes, uw);
+  }
+}
+
+}  // namespace
+
+void launch_mem_ingest(const MemIngestArgs& a, cudaStream_t s) {
+  if (a.n == 0) return;
+  const u64 per_block = (u64)kIngestThreads * kIngestItems;
+  u64 blocks = (a.n + per_block - 1) / per_block;
+  if (blocks > 152ull * 8) blocks = 152ull * 8;
+  if (a.space_mask == 0xFu)
+    k_mem_ingest<false><<<(unsigned)blocks, kIngestThreads, 0, s>>>(a);
+  else
+    k_mem_ingest<true><<<(unsigned)blocks, kIngestThreads, 0, s>>>(a);
+  count_launches(1);
+}
+
+void launch_mem_levels(const LevelArgs& a, cudaStream_t s) {
+  if (a.ntiles == 0) return;
+  unsigned g = (unsigned)(a.grid < (int)a.ntiles ? a.grid : (int)a.ntiles);
+  k_mem_levels<<<g, kLvThreads, 0, s>>>(a);
+  count_launches(1);
+}
+
+}  // namespace aiwc

@@ -1,0 +1,251 @@
+// Stable LSD radix sort of 64-bit keys with device-resident key counts.
+//
+// Each pass handles one 8-bit window of the key. A pass whose window holds no
+// bit that varies between keys (known from the OR and AND over all keys,
+// accumulated by the kernel that produced them) is skipped on the device, so
+// the host launches a fixed sequence and never waits for a count. Each pass is
+// reduce-then-scan: per-tile digit counts, an exclusive scan over
+// (digit, tile), then a stable scatter staged through shared memory so that
+// each digit's keys leave the tile as one contiguous run. No block ever waits
+// for another block.
+#include <atomic>
+
+#include "aiwc_internal.cuh"
+#include "common.cuh"
+
+namespace aiwc {
+
+static std::atomic<unsigned long long> g_launches{0};
+void count_launches(u64 n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+u64 launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+
+namespace {
+
+constexpr int kWarps = kTileThreads / 32;
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanBlock = kScanThreads * kScanItems;
+
+__device__ __forceinline__ bool pass_shift(const SortDesc& d, int pass, int* shift) {
+  int sh = d.lo_bit + 8 * pass;
+  *shift = sh;
+  if (sh >= 64) return false;
+  u64 varying = ((*d.key_or) ^ (*d.key_and)) & d.mask;
+  return ((varying >> sh) & 0xFFull) != 0;
+}
+
+__global__ void __launch_bounds__(kTileThreads) k_hist(SortDesc d, int pass) {
+  int shift;
+  if (!pass_shift(d, pass, &shift)) return;
+  __shared__ u32 h[kWarps][256];
+  for (int i = threadIdx.x; i < kWarps * 256; i += kTileThreads) (&h[0][0])[i] = 0;
+  __syncthreads();
+  const u64 n = umin64(*d.n, d.n_cap);
+  const u64* src = *d.cur ? d.b : d.a;
+  const u64 base = (u64)blockIdx.x * kTile;
+  const int w = threadIdx.x >> 5;
+#pragma unroll 4
+  for (int k = 0; k < kTileItems; ++k) {
+    u64 i = base + (u64)k * kTileThreads + threadIdx.x;
+    if (i < n) atomicAdd(&h[w][(src[i] >> shift) & 0xFF], 1u);
+  }
+  __syncthreads();
+  u32 s = 0;
+#pragma unroll
+  for (int q = 0; q < kWarps; ++q) s += h[q][threadIdx.x];
+  d.counts[(u64)threadIdx.x * d.ntiles + blockIdx.x] = s;
+}
+
+template <typename T>
+__device__ __forceinline__ T block_excl_scan(T x, T* total, T* warp_tot) {
+  // Exclusive prefix sum over the block; *total receives the block sum.
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  T inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) warp_tot[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    T v = lane < nw ? warp_tot[lane] : T(0);
+    T vi = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      T y = __shfl_up_sync(0xffffffffu, vi, o);
+      if (lane >= o) vi += y;
+    }
+    if (lane < nw) warp_tot[lane] = vi - v;
+    if (lane == 31) warp_tot[32] = vi;
+  }
+  __syncthreads();
+  T r = warp_tot[w] + inc - x;
+  *total = warp_tot[32];
+  __syncthreads();
+  return r;
+}
+
+// Exclusive scan of the counts, gated on the same pass predicate.
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(SortDesc d, int pass, u64 len) {
+  int shift;
+  if (!pass_shift(d, pass, &shift)) return;
+  __shared__ u32 wt[33];
+  u64 base = (u64)blockIdx.x * kScanBlock + (u64)threadIdx.x * kScanItems;
+  u32 s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k)
+    if (base + k < len) s += d.counts[base + k];
+  u32 tot;
+  block_excl_scan<u32>(s, &tot, wt);
+  if (threadIdx.x == 0) d.block_sums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(SortDesc d, int pass, u32 nb) {
+  int shift;
+  if (!pass_shift(d, pass, &shift)) return;
+  __shared__ u32 wt[33];
+  u32 carry = 0;
+  for (u32 c0 = 0; c0 < nb; c0 += kScanBlock) {
+    u32 v[kScanItems];
+    u32 s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      u32 i = c0 + threadIdx.x * kScanItems + k;
+      v[k] = i < nb ? d.block_sums[i] : 0u;
+      s += v[k];
+    }
+    u32 tot;
+    u32 ex = block_excl_scan<u32>(s, &tot, wt) + carry;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      u32 i = c0 + threadIdx.x * kScanItems + k;
+      if (i < nb) d.block_sums[i] = ex;
+      ex += v[k];
+    }
+    carry += tot;
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(SortDesc d, int pass, u64 len) {
+  int shift;
+  if (!pass_shift(d, pass, &shift)) return;
+  __shared__ u32 wt[33];
+  u64 base = (u64)blockIdx.x * kScanBlock + (u64)threadIdx.x * kScanItems;
+  u32 v[kScanItems];
+  u32 s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    v[k] = base + k < len ? d.counts[base + k] : 0u;
+    s += v[k];
+  }
+  u32 tot;
+  u32 ex = block_excl_scan<u32>(s, &tot, wt) + d.block_sums[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    if (base + k < len) d.counts[base + k] = ex;
+    ex += v[k];
+  }
+}
+
+__global__ void __launch_bounds__(kTileThreads) k_scatter(SortDesc d, int pass) {
+  int shift;
+  if (!pass_shift(d, pass, &shift)) return;
+  __shared__ u32 wcnt[kWarps][256];
+  __shared__ u32 dofs[256];
+  __shared__ u32 gofs[256];
+  __shared__ u32 wt[33];
+  __shared__ u64 stage[kTile];
+  for (int i = threadIdx.x; i < kWarps * 256; i += kTileThreads) (&wcnt[0][0])[i] = 0;
+  __syncthreads();
+  const u64 n = umin64(*d.n, d.n_cap);
+  const u32 cur = *d.cur;
+  const u64* src = cur ? d.b : d.a;
+  u64* dst = cur ? d.a : d.b;
+  const u64 base = (u64)blockIdx.x * kTile;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const u32 lt_mask = (1u << lane) - 1u;
+  u64 key[kTileItems];
+  u32 rank[kTileItems];
+  // Warp w ranks positions base + w*512 + k*32 + lane in that order, which
+  // keeps the scatter stable.
+#pragma unroll
+  for (int k = 0; k < kTileItems; ++k) {
+    u64 i = base + (u64)w * (32 * kTileItems) + (u64)k * 32 + lane;
+    bool valid = i < n;
+    key[k] = valid ? src[i] : 0ull;
+    u32 dig = valid ? (u32)((key[k] >> shift) & 0xFF) : 256u + lane;
+    u32 peers = __match_any_sync(0xffffffffu, dig);
+    u32 before = valid ? wcnt[w][dig] : 0u;
+    rank[k] = before + __popc(peers & lt_mask);
+    __syncwarp();
+    if (valid && lane == 31 - __clz(peers)) wcnt[w][dig] = before + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  {
+    const int dg = threadIdx.x;  // one thread per digit
+    u32 tot = 0;
+#pragma unroll
+    for (int q = 0; q < kWarps; ++q) {
+      u32 c = wcnt[q][dg];
+      wcnt[q][dg] = tot;
+      tot += c;
+    }
+    u32 all;
+    u32 ex = block_excl_scan<u32>(tot, &all, wt);
+    dofs[dg] = ex;
+    gofs[dg] = d.counts[(u64)dg * d.ntiles + blockIdx.x];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kTileItems; ++k) {
+    u64 i = base + (u64)w * (32 * kTileItems) + (u64)k * 32 + lane;
+    if (i < n) {
+      u32 dig = (u32)((key[k] >> shift) & 0xFF);
+      stage[dofs[dig] + wcnt[w][dig] + rank[k]] = key[k];
+    }
+  }
+  __syncthreads();
+  const u64 tile_n = n > base ? (n - base < (u64)kTile ? n - base : (u64)kTile) : 0ull;
+  for (u32 j = threadIdx.x; j < tile_n; j += kTileThreads) {
+    u64 kv = stage[j];
+    u32 dig = (u32)((kv >> shift) & 0xFF);
+    dst[(u64)gofs[dig] + (j - dofs[dig])] = kv;
+  }
+}
+
+__global__ void k_flip(SortDesc d, int pass) {
+  int shift;
+  if (pass_shift(d, pass, &shift)) *d.cur ^= 1u;
+}
+
+}  // namespace
+
+size_t sort_counts_words(u64 n_max) {
+  u64 nt = (n_max + kTile - 1) / kTile;
+  return (size_t)(256 * (nt ? nt : 1));
+}
+
+size_t sort_block_sums_words(u64 n_max) {
+  u64 len = sort_counts_words(n_max);
+  return (size_t)((len + kScanBlock - 1) / kScanBlock + 1);
+}
+
+void sort_keys(const SortDesc& d, cudaStream_t s) {
+  if (d.ntiles == 0) return;
+  const u64 len = 256ull * d.ntiles;
+  const u32 nb = (u32)((len + kScanBlock - 1) / kScanBlock);
+  const int passes = (64 - d.lo_bit + 7) / 8;
+  for (int p = 0; p < passes; ++p) {
+    k_hist<<<d.ntiles, kTileThreads, 0, s>>>(d, p);
+    k_scan_reduce<<<nb, kScanThreads, 0, s>>>(d, p, len);
+    k_scan_top<<<1, kScanThreads, 0, s>>>(d, p, nb);
+    k_scan_down<<<nb, kScanThreads, 0, s>>>(d, p, len);
+    k_scatter<<<d.ntiles, kTileThreads, 0, s>>>(d, p);
+    k_flip<<<1, 1, 0, s>>>(d, p);
+  }
+  count_launches(6ull * passes);
+}
+
+}  // namespace aiwc

@@ -1,0 +1,101 @@
+"""The C-ABI library loads, exports every entry point include/*.h declares, and
+its structs have the layout the Python binding assumes (no GPU needed)."""
+from __future__ import annotations
+
+import ctypes
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(hdr).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[\w\s\*]+?\b(aiwc_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+def test_library_builds_and_loads():
+    import __graft_entry__
+    path = __graft_entry__._builder().build()
+    assert os.path.exists(path)
+    ctypes.CDLL(path)
+
+
+def test_every_declared_symbol_is_exported():
+    import paper_1805_04207_gb300 as P
+    declared = _declared_functions()
+    assert {"aiwc_create", "aiwc_push_mem", "aiwc_push_branch", "aiwc_push_instr", "aiwc_compute"} <= declared
+    for name in declared:
+        assert hasattr(P.lib, name), name
+    # the binding wraps every declared entry point with the same name
+    assert declared <= set(P.SIGNATURES), declared - set(P.SIGNATURES)
+    out = subprocess.run(["nm", "-D", "--defined-only", P.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (aiwc_\w+)", out))
+    assert declared <= exported, declared - exported
+
+
+def test_struct_layout_matches_header(tmp_path):
+    import paper_1805_04207_gb300 as P
+    src = tmp_path / "layout.c"
+    fields_m = [n for n, _ in P.METRIC_FIELDS]
+    fields_c = [n for n, _ in P.aiwc_config._fields_]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "aiwc.h"', "int main(void){",
+             'printf("%zu %zu\\n", sizeof(aiwc_metrics), sizeof(aiwc_config));']
+    lines += [f'printf("%zu\\n", offsetof(aiwc_metrics, {f}));' for f in fields_m]
+    lines += [f'printf("%zu\\n", offsetof(aiwc_config, {f}));' for f in fields_c]
+    lines += ['printf("%zu %zu\\n", sizeof(aiwc_mem_event), sizeof(aiwc_branch_event));', "return 0;}"]
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    vals = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    vals = [int(v) for v in vals]
+    assert vals[0] == ctypes.sizeof(P.aiwc_metrics) and vals[1] == ctypes.sizeof(P.aiwc_config)
+    k = 2
+    for f in fields_m:
+        assert vals[k] == getattr(P.aiwc_metrics, f).offset, f
+        k += 1
+    for f in fields_c:
+        assert vals[k] == getattr(P.aiwc_config, f).offset, f
+        k += 1
+    assert vals[k:] == [16, 8]
+
+
+def test_config_defaults_are_the_papers():
+    import paper_1805_04207_gb300 as P
+    c = P.aiwc_config_default()
+    assert (c.history_len, c.cover_num, c.cover_den, c.space_mask, c.n_opcodes) == (16, 9, 10, 0xF, 65535)
+
+
+def test_invalid_config_rejected_without_touching_a_device():
+    import paper_1805_04207_gb300 as P
+    for bad in (dict(history_len=0), dict(history_len=32), dict(cover_num=11), dict(cover_den=0),
+                dict(n_opcodes=0), dict(precision=2), dict(max_work_items=(1 << 32) + 1)):
+        with pytest.raises(P.AiwcError) as e:
+            P.aiwc_create(P.aiwc_config_default(**bad))
+        assert e.value.status == P.AIWC_EINVAL
+
+
+def test_null_arguments_are_errors_not_crashes():
+    import paper_1805_04207_gb300 as P
+    assert P.lib.aiwc_create(None, None) == P.AIWC_EINVAL
+    assert P.lib.aiwc_push_mem(None, None, 0, 0) == P.AIWC_EINVAL
+    assert P.lib.aiwc_compute(None, None) == P.AIWC_EINVAL
+    assert P.lib.aiwc_destroy(None) == P.AIWC_OK
+
+
+def test_product_package_does_not_reach_the_oracle():
+    pkg = os.path.join(ROOT, "paper_1805_04207_gb300")
+    for path in glob.glob(os.path.join(pkg, "**", "*"), recursive=True):
+        if os.path.isfile(path) and path.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+            text = open(path).read()
+            assert "import oracle" not in text and "from oracle" not in text, path
+            assert "aiwc_oracle" not in text and "liboracle" not in text, path

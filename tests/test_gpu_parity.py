@@ -1,0 +1,213 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Integers, medians and the opcode histogram must match bit-exactly; every
+entropy must be within 1e-9 bits (the FP64 tolerance), the linear branch
+entropy within 1e-12 (it is one division of exact integers).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from tests.helpers import branch_only, instr_only, mem_only, random_trace
+
+pytestmark = pytest.mark.gpu
+
+INT_FIELDS = ["total_instructions", "unique_opcodes", "opcode_cover", "work_items", "barriers",
+              "itb_count", "itb_min", "itb_max", "itb_median_lo", "itb_median_hi",
+              "ipt_count", "ipt_min", "ipt_max", "ipt_median_lo", "ipt_median_hi",
+              "total_reads", "total_writes", "footprint", "footprint_cover", "unique_reads", "unique_writes",
+              "branch_events", "branch_sites", "branch_cover", "branch_patterns", "branch_minsum"]
+ENTROPY_TOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1805_04207_gb300 as P
+    return P
+
+
+def assert_parity(g, o, entropy_tol=ENTROPY_TOL, hist=True):
+    bad = [(f, g[f], o[f]) for f in INT_FIELDS if g[f] != o[f]]
+    assert not bad, bad
+    assert g["itb_median"] == o["itb_median"] and g["ipt_median"] == o["ipt_median"]
+    for n in range(11):
+        assert abs(g["entropy"][n] - o["entropy"][n]) <= entropy_tol, (n, g["entropy"][n], o["entropy"][n])
+    assert abs(g["albe"] - o["albe"]) <= 1e-12
+    for r in ("unique_rw_ratio", "reread_ratio", "rewrite_ratio"):
+        a, b = g[r], o[r]
+        assert (math.isnan(a) and math.isnan(b)) or a == b, (r, a, b)
+    if hist:
+        assert np.array_equal(np.asarray(g["opcode_hist"], dtype=np.uint64),
+                              np.asarray(o["opcode_hist"], dtype=np.uint64))
+
+
+def run_gpu(P, trace, on_device=True, split=1, single_runs=False, **cfg):
+    cfg.setdefault("n_opcodes", trace.n_opcodes)
+    tr = trace.to("cuda") if on_device else trace
+    with P.Characterizer(**cfg) as c:
+        for part in range(split):
+            if tr.mem is not None and tr.mem.shape[0]:
+                n = tr.mem.shape[0]
+                c.push_mem(tr.mem[part * n // split:(part + 1) * n // split].contiguous())
+            if tr.br is not None and tr.br.shape[0]:
+                n = tr.br.shape[0]
+                c.push_branch(tr.br[part * n // split:(part + 1) * n // split].contiguous())
+        if tr.run_wi is not None and tr.run_wi.shape[0]:
+            if single_runs:
+                for w, o, ln in zip(trace.run_wi.tolist(), trace.run_off.tolist(), trace.run_len.tolist()):
+                    c.push_instr(int(w), tr.ops[o:o + ln].contiguous())
+            else:
+                R = tr.run_wi.shape[0]
+                for part in range(split):
+                    sl = slice(part * R // split, (part + 1) * R // split)
+                    c.push_instr_runs(tr.run_wi[sl].to(torch.int32).contiguous(), tr.run_off[sl].contiguous(),
+                                      tr.run_len[sl].contiguous(), tr.ops)
+        return c.compute()
+
+
+def test_tiny_workload(P):
+    tr = synth.tiny()
+    o = oracle.compute(tr)
+    assert_parity(run_gpu(P, tr), o)
+    assert_parity(run_gpu(P, tr, on_device=False), o)
+    assert_parity(run_gpu(P, tr, single_runs=True), o)
+    assert_parity(run_gpu(P, tr, on_device=False, single_runs=True, split=3), o)
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_random_tiny_traces(P, seed):
+    rng = np.random.default_rng(20_000 + seed)
+    tr = random_trace(seed, n_mem=int(rng.integers(0, 300)), n_br=int(rng.integers(0, 300)),
+                      n_wi=int(rng.integers(1, 9)), n_runs=int(rng.integers(1, 12)),
+                      n_ops=int(rng.integers(12, 400)), addr_pool=int(rng.integers(1, 64)),
+                      n_sites=int(rng.integers(1, 5)), n_opcodes=int(rng.integers(1, 9)),
+                      addr_span_bits=int(rng.integers(1, 40)))
+    h = int(rng.choice([1, 2, 5, 16, 31]))
+    mask = int(rng.choice([0xF, 0x1, 0x6]))
+    o = oracle.compute(tr, history_len=h, space_mask=mask)
+    g = run_gpu(P, tr, on_device=bool(seed % 2), split=1 + seed % 3, single_runs=seed % 4 == 3, history_len=h,
+                space_mask=mask)
+    assert_parity(g, o)
+
+
+@pytest.mark.parametrize("n_mem,n_br,n_wi,per_wi", [
+    (300_000 + 12345, 200_001, 257, 1000),
+    (4096 * 7, 4096 * 3, 64, 4096),
+    (1_000_003, 1_000_003, 1000, 1001),
+])
+def test_large_shape_ragged(P, n_mem, n_br, n_wi, per_wi):
+    tr = synth.large(seed=3, n_mem=n_mem, n_br=n_br, n_wi=n_wi, per_wi=per_wi, zipf_distinct=1 << 16)
+    o = oracle.compute(tr)
+    assert_parity(run_gpu(P, tr), o)
+
+
+def test_empty_and_single_stream(P):
+    for tr in (synth.Trace("empty"), mem_only([5]), branch_only([1], [2], [1]), instr_only([(3, [])]),
+               instr_only([(3, [-1, -1])]), mem_only([0, 0, 0], stores=[1, 1, 1])):
+        assert_parity(run_gpu(P, tr), oracle.compute(tr), hist=tr.ops is not None)
+
+
+def test_one_address_many_tiles(P):
+    # one run of equal keys spanning many tiles exercises the cross-tile fix-up
+    tr = mem_only([1 << 20] * 200_000, stores=[i % 3 == 0 for i in range(200_000)])
+    assert_parity(run_gpu(P, tr), oracle.compute(tr))
+    tr = branch_only([9] * 100_000, list(range(100_000)), [int(i % 7 != 0) for i in range(100_000)])
+    assert_parity(run_gpu(P, tr), oracle.compute(tr))
+
+
+def test_key_extremes_and_spaces(P):
+    top = (1 << 61) - 1
+    addrs = [0, 1, top, top - 1, 1 << 60, 0, top] * 1000
+    spaces = [0, 3, 3, 0, 1, 2, 2] * 1000
+    tr = mem_only(addrs, stores=[i % 2 for i in range(len(addrs))], spaces=spaces)
+    for mask in (0xF, 0x9, 0x2):
+        assert_parity(run_gpu(P, tr, space_mask=mask), oracle.compute(tr, space_mask=mask))
+
+
+def test_all_distinct_addresses(P):
+    n = 150_000
+    tr = mem_only(list(range(0, 8 * n, 8)))
+    assert_parity(run_gpu(P, tr), oracle.compute(tr))
+
+
+def test_value_overflow_paths(P):
+    # ITB/IPT values above the shared (2048) and dense (65536) bins, opcode
+    # counts above 1024, and work-items with many runs.
+    runs = [(0, [1] * 70_000), (1, [2] * 3000 + [-1] + [3] * 100), (0, [4] * 10 + [-1]), (2, [])]
+    runs += [(5, [k % 6] * 3 + [-1]) for k in range(500)]
+    tr = instr_only(runs, n_opcodes=7)
+    assert_parity(run_gpu(P, tr), oracle.compute(tr))
+    assert_parity(run_gpu(P, tr, single_runs=True, on_device=False), oracle.compute(tr))
+
+
+@pytest.mark.parametrize("h", [1, 2, 7, 16, 31])
+def test_history_lengths(P, h):
+    tr = synth.large(seed=5, n_mem=1000, n_br=300_000, n_wi=2, per_wi=100, zipf_distinct=1 << 10)
+    assert_parity(run_gpu(P, tr, history_len=h), oracle.compute(tr, history_len=h))
+
+
+def test_cover_fractions(P):
+    tr = synth.large(seed=6, n_mem=200_000, n_br=50_000, n_wi=50, per_wi=500, zipf_distinct=1 << 12)
+    for num, den in ((1, 2), (1, 1), (99, 100), (1, 1000)):
+        assert_parity(run_gpu(P, tr, cover=(num, den)), oracle.compute(tr, cover_num=num, cover_den=den))
+
+
+def test_handle_reuse_resets_state(P):
+    a = synth.large(seed=7, n_mem=100_000, n_br=40_000, n_wi=30, per_wi=700, zipf_distinct=1 << 12)
+    b = synth.tiny()
+    with P.Characterizer(n_opcodes=256) as c:
+        from paper_1805_04207_gb300.api import push_trace
+        outs = []
+        for tr in (a, b, a):
+            push_trace(c, tr.to("cuda"))
+            outs.append(c.compute())
+    assert_parity(outs[0], oracle.compute(a, n_opcodes=256))
+    assert_parity(outs[1], oracle.compute(b, n_opcodes=256))
+    assert_parity(outs[2], outs[0])
+
+
+def test_invalid_events_reported_then_handle_recovers(P):
+    with P.Characterizer(n_opcodes=8) as c:
+        c.push_mem(mem_only([1 << 61]).mem.cuda())
+        with pytest.raises(P.AiwcError) as e:
+            c.compute()
+        assert e.value.status == P.AIWC_EINVAL
+        tr = instr_only([(0, [9])], n_opcodes=8)
+        c.push_instr(0, tr.ops.cuda())
+        with pytest.raises(P.AiwcError) as e:
+            c.compute()
+        assert e.value.status == P.AIWC_EINVAL
+        good = synth.tiny()
+        from paper_1805_04207_gb300.api import push_trace
+        c2 = P.Characterizer(n_opcodes=64)
+        push_trace(c2, good.to("cuda"))
+        assert_parity(c2.compute(), oracle.compute(good))
+        c2.close()
+        c.push_mem(mem_only([4, 4, 8]).mem.cuda())
+        g = c.compute()
+        assert (g["footprint"], g["total_reads"]) == (2, 3)
+    with P.Characterizer(max_work_items=16) as c:
+        c.push_branch(branch_only([1], [20], [1]).br.cuda())
+        with pytest.raises(P.AiwcError):
+            c.compute()
+
+
+@pytest.mark.slow
+def test_full_size_large_invocation(P):
+    """The 2^28 / 2^26 / 2^30-event invocation in bench.py's launch configuration,
+    against the oracle run on the host over the same inputs."""
+    tr_dev = synth.large(device="cuda")
+    g = run_gpu(P, tr_dev.to("cuda"))
+    tr = tr_dev.to("cpu")
+    del tr_dev
+    torch.cuda.empty_cache()
+    o = oracle.compute(tr)
+    assert_parity(g, o)

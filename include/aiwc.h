@@ -90,9 +90,12 @@ typedef struct aiwc_config {
   uint32_t n_opcodes;     /* valid opcodes are 0..n_opcodes-1, n_opcodes <= 65535 */
   uint32_t space_mask;    /* bit s set: address space s takes part in the memory metrics (0xF) */
   uint32_t precision;     /* entropy finalisation: 0 = FP64, 1 = FP32 compensated sums */
-  uint32_t plan;          /* distinct-address counting: 0 = auto, 1 = sort, 2 = hash */
+  uint32_t plan;          /* distinct-address counting: 0 = auto (hash, sort on overflow), 1 = sort, 2 = hash */
   uint64_t max_work_items;/* work-item ids must be < this (sizes the work-item bitmap); 0 = 2^32 */
   uint64_t hbm_budget;    /* bytes of device scratch the handle may hold; 0 = unlimited */
+  uint64_t table_slots;   /* hash plan: initial superblock-table slots (power of two, 0 = 2^20); an
+                             invocation that overflows the table is finished by the sort plan and
+                             the next one gets a 4x larger table */
 } aiwc_config;
 
 /* Fills the paper's defaults: history 16, 90% coverage, all address spaces,

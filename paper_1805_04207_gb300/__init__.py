@@ -26,7 +26,8 @@ class aiwc_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("cuda_stream", ctypes.c_void_p), ("history_len", ctypes.c_uint32),
                 ("cover_num", ctypes.c_uint32), ("cover_den", ctypes.c_uint32), ("n_opcodes", ctypes.c_uint32),
                 ("space_mask", ctypes.c_uint32), ("precision", ctypes.c_uint32), ("plan", ctypes.c_uint32),
-                ("max_work_items", ctypes.c_uint64), ("hbm_budget", ctypes.c_uint64)]
+                ("max_work_items", ctypes.c_uint64), ("hbm_budget", ctypes.c_uint64),
+                ("table_slots", ctypes.c_uint64)]
 
 
 _U64 = ctypes.c_uint64

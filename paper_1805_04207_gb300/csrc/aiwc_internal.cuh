@@ -57,8 +57,24 @@ struct DevState {
   u64 n_runs;            // instruction runs pushed
   u32 wi_min, wi_max;
   u32 err;
+  u32 sbt_overflow;      // the superblock table could not place a key
+  u32 pad2;
+  u64 sb_used;           // occupied superblock slots
   u32 sort_cur[8];       // which ping-pong buffer holds each sort's data
   u32 pad;
+};
+
+// Open-addressing table of memory superblocks (key >> 11), kept in L2.
+// keys[s] = superblock + 1 (0 = empty); cnt[s] = its events; off/cur =
+// segment offset and scatter cursor. Capacity mask + 1 is a power of two.
+constexpr u32 kNoSlot = 0xFFFFFFFFu;
+constexpr int kMaxProbe = 256;
+struct SbTable {
+  u64* keys;
+  u32* cnt;
+  u32* off;
+  u32* cur;
+  u64 mask;
 };
 
 // Sort slots (index into DevState::sort_cur).
@@ -117,6 +133,8 @@ size_t sort_counts_words(u64 n_max);  // u32 words needed for counts
 size_t sort_block_sums_words(u64 n_max);
 
 struct MemIngestArgs {
+  SbTable tab;         // used when use_tab (hash plan)
+  int use_tab;
   const void* ev;
   u64 n;
   u32 space_mask;
@@ -141,6 +159,22 @@ struct LevelArgs {
   int grid;
 };
 void launch_mem_levels(const LevelArgs& a, cudaStream_t s);
+
+struct HashArgs {
+  const u64* words;    // unsorted memory words
+  u64 n_cap;           // capacity of words / low, in elements
+  uint16_t* low;       // out: low 12 bits grouped by superblock
+  SbTable tab;
+  u32* scan_tmp;       // sbt_scan_words(capacity) words
+  u64* n_used;         // out: occupied slots
+  u32* used_list;      // out: their indices (capacity = table slots)
+  u64* over;
+  u64 over_cap;
+  Arena* arena;
+  int grid_scatter, grid_segments;
+};
+size_t sbt_scan_words(u64 cap);
+void launch_mem_hash(const HashArgs& a, cudaStream_t s);
 
 struct BranchIngestArgs {
   const void* ev;

@@ -73,6 +73,12 @@ struct aiwc_handle {
   DevBuf mem_a, mem_b, br_a, br_b, pat_a, pat_b, rk_a, rk_b, run_sum, over_a, over_b, counts, bsums, tiles;
   DevBuf stage[2];
   DevBuf desc;
+  // superblock table of the hash plan (sized for the next invocation)
+  DevBuf sbt, sbt_scan;
+  u64 sbt_cap = 0;       // slots currently allocated
+  u64 sbt_want = 1ull << 20;
+  u32* h_flag = nullptr; // pinned
+  bool last_plan_hash = false;
   u64 n_mem = 0, n_br = 0, n_runs = 0;
   u64 value_bound = 0;  // bound on ITB / IPT values >= kValDense (each uses kValDense instructions)
   // pending single-run pushes (host data, or device pointers)
@@ -225,6 +231,34 @@ aiwc_status staged_copy(aiwc_handle* h, const void* src, size_t bytes, size_t un
   return AIWC_OK;
 }
 
+bool use_hash(const aiwc_handle* h) { return h->cfg.plan != 1; }
+
+SbTable table_view(aiwc_handle* h) {
+  SbTable t;
+  char* p = (char*)h->sbt.p;
+  const u64 C = h->sbt_cap;
+  t.keys = (u64*)p;
+  t.cnt = (u32*)(p + 8 * C);
+  t.off = (u32*)(p + 12 * C);
+  t.cur = (u32*)(p + 16 * C);
+  t.mask = C - 1;
+  return t;
+}
+
+// Allocates (or regrows, between invocations) the superblock table; cleared.
+aiwc_status ensure_table(aiwc_handle* h) {
+  if (h->sbt_cap >= h->sbt_want && h->sbt.p) return AIWC_OK;
+  if (h->n_mem) return AIWC_OK;  // never resize in the middle of an invocation
+  const u64 C = h->sbt_want;
+  aiwc_status s = ensure(h, h->sbt, 24 * C, false);
+  if (s != AIWC_OK) return s;
+  s = ensure(h, h->sbt_scan, 4 * sbt_scan_words(C), false);
+  if (s != AIWC_OK) return s;
+  h->sbt_cap = C;
+  CK(cudaMemsetAsync(h->sbt.p, 0, 12 * C, h->stream));
+  return AIWC_OK;
+}
+
 aiwc_status check_usable(aiwc_handle* h) {
   if (!h) return fail(nullptr, AIWC_EINVAL, "null handle");
   if (h->broken) return AIWC_ESTATE;
@@ -368,6 +402,7 @@ aiwc_status reset_device_state(aiwc_handle* h) {
   if (h->wi_bitmap) launch_wi_clear(h->wi_bitmap, h->arena, h->stream);
   CK(cudaMemsetAsync(h->d_hist, 0, (size_t)h->cfg.n_opcodes * 8, h->stream));
   CK(cudaMemsetAsync(h->arena, 0, sizeof(Arena), h->stream));
+  if (h->sbt.p && h->last_plan_hash) CK(cudaMemsetAsync(h->sbt.p, 0, 12 * h->sbt_cap, h->stream));
   launch_reset_identities(h->arena, h->stream);
   CK(cudaGetLastError());
   return AIWC_OK;
@@ -391,6 +426,7 @@ void aiwc_config_default(aiwc_config* c) {
   c->plan = 0;
   c->max_work_items = 0;
   c->hbm_budget = 0;
+  c->table_slots = 0;
 }
 
 aiwc_status aiwc_create(const aiwc_config* cfg, aiwc_handle** out) {
@@ -402,6 +438,9 @@ aiwc_status aiwc_create(const aiwc_config* cfg, aiwc_handle** out) {
   if (cfg->n_opcodes == 0 || cfg->n_opcodes > 65535) return fail(nullptr, AIWC_EINVAL, "n_opcodes must be 1..65535");
   if (cfg->precision > 1 || cfg->plan > 2) return fail(nullptr, AIWC_EINVAL, "unknown precision or plan");
   if (cfg->max_work_items > (1ull << 32)) return fail(nullptr, AIWC_EINVAL, "max_work_items must be <= 2^32");
+  if (cfg->table_slots && ((cfg->table_slots & (cfg->table_slots - 1)) || cfg->table_slots < 64 ||
+                           cfg->table_slots > (1ull << 30)))
+    return fail(nullptr, AIWC_EINVAL, "table_slots must be a power of two in [64, 2^30]");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
     cudaGetLastError();
@@ -413,6 +452,7 @@ aiwc_status aiwc_create(const aiwc_config* cfg, aiwc_handle** out) {
   h->cfg.space_mask &= 0xF;
   h->stream = (cudaStream_t)cfg->cuda_stream;
   h->max_wi = cfg->max_work_items ? cfg->max_work_items : (1ull << 32);
+  h->sbt_want = cfg->table_slots ? cfg->table_slots : (1ull << 20);
   auto bail = [&](aiwc_status s) {
     aiwc_destroy(h);
     return s;
@@ -431,7 +471,8 @@ aiwc_status aiwc_create(const aiwc_config* cfg, aiwc_handle** out) {
       (e = cudaMalloc(&h->d_result, sizeof(Result))) != cudaSuccess ||
       (e = cudaMalloc(&h->d_hist, (size_t)cfg->n_opcodes * 8)) != cudaSuccess ||
       (e = cudaMallocHost(&h->h_result, sizeof(Result))) != cudaSuccess ||
-      (e = cudaMallocHost(&h->h_hist, (size_t)cfg->n_opcodes * 8)) != cudaSuccess)
+      (e = cudaMallocHost(&h->h_hist, (size_t)cfg->n_opcodes * 8)) != cudaSuccess ||
+      (e = cudaMallocHost(&h->h_flag, 64)) != cudaSuccess)
     return bail(cuda_fail(nullptr, "allocation", e));
   h->bytes = sizeof(Arena) + sizeof(Result) + (size_t)cfg->n_opcodes * 8;
   if (reset_device_state(h) != AIWC_OK) return bail(fail(nullptr, AIWC_ECUDA, h->err));
@@ -450,7 +491,10 @@ aiwc_status aiwc_push_mem(aiwc_handle* h, const aiwc_mem_event* ev, size_t n, in
     return fail(h, AIWC_EINVAL, "device memory events must be 16-byte aligned", false);
   ENSURE(h->mem_a, (h->n_mem + n) * 8, true);
   if ((s = ensure_bitmap(h)) != AIWC_OK) return s;
+  if (use_hash(h) && (s = ensure_table(h)) != AIWC_OK) return s;
   MemIngestArgs a;
+  a.use_tab = use_hash(h) && h->sbt_cap ? 1 : 0;
+  if (a.use_tab) a.tab = table_view(h);
   a.space_mask = h->cfg.space_mask;
   a.words = (u64*)h->mem_a.p;
   a.wi_bitmap = h->wi_bitmap;
@@ -615,8 +659,32 @@ aiwc_status aiwc_compute(aiwc_handle* h, aiwc_metrics* out) {
     d.ntiles = (u32)ntiles_of(n_host);
     return d;
   };
-  // memory: sort words, run lengths per skip level, cross-tile fix-up
-  if (n_mem) {
+  // memory: the hash plan unless the superblock table overflowed (then sort)
+  bool hash_ok = false;
+  if (n_mem && use_hash(h) && h->sbt_cap) {
+    CK(cudaMemcpyAsync(h->h_flag, &dst->sbt_overflow, 4, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    hash_ok = *h->h_flag == 0;
+    if (!hash_ok) h->sbt_want = std::max<u64>(h->sbt_want, std::min<u64>(h->sbt_cap * 4, 1ull << 30));
+  }
+  h->last_plan_hash = n_mem && use_hash(h) && h->sbt_cap;
+  if (hash_ok) {
+    StageScope sc(h, kStMemLevels);
+    HashArgs ha;
+    ha.words = (const u64*)h->mem_a.p;
+    ha.n_cap = std::min<u64>(h->mem_a.cap / 8, h->mem_b.cap / 2);
+    ha.low = (uint16_t*)h->mem_b.p;
+    ha.tab = table_view(h);
+    ha.scan_tmp = (u32*)h->sbt_scan.p;
+    ha.n_used = &dst->sb_used;
+    ha.used_list = (u32*)((char*)h->sbt.p + 20 * h->sbt_cap);
+    ha.over = over;
+    ha.over_cap = over_cap;
+    ha.arena = h->arena;
+    ha.grid_scatter = h->sm_count * 8;
+    ha.grid_segments = h->sm_count * 6;
+    launch_mem_hash(ha, st);
+  } else if (n_mem) {
     SortDesc d = sdesc(h->mem_a, h->mem_b, kSortMem, &dst->n_words, &dst->mem_or, &dst->mem_and, ~0ull, 0, n_mem);
     {
       StageScope sc(h, kStMemSort);
@@ -756,7 +824,7 @@ aiwc_status aiwc_destroy(aiwc_handle* h) {
   if (h->stream || h->copy_stream) cudaStreamSynchronize(h->stream);
   DevBuf* bufs[] = {&h->mem_a, &h->mem_b, &h->br_a, &h->br_b, &h->pat_a, &h->pat_b, &h->rk_a, &h->rk_b,
                     &h->run_sum, &h->over_a, &h->over_b, &h->counts, &h->bsums, &h->tiles, &h->stage[0],
-                    &h->stage[1], &h->desc};
+                    &h->stage[1], &h->desc, &h->sbt, &h->sbt_scan};
   for (DevBuf* b : bufs) release(h, *b);
   if (h->wi_bitmap) cudaFree(h->wi_bitmap);
   if (h->arena) cudaFree(h->arena);
@@ -764,6 +832,7 @@ aiwc_status aiwc_destroy(aiwc_handle* h) {
   if (h->d_hist) cudaFree(h->d_hist);
   if (h->h_result) cudaFreeHost(h->h_result);
   if (h->h_hist) cudaFreeHost(h->h_hist);
+  if (h->h_flag) cudaFreeHost(h->h_flag);
   for (int i = 0; i < 2; ++i) {
     if (h->ev_copied[i]) cudaEventDestroy(h->ev_copied[i]);
     if (h->ev_free[i]) cudaEventDestroy(h->ev_free[i]);

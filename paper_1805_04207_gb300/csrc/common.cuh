@@ -69,4 +69,40 @@ __device__ __forceinline__ void overflow_append(u64* over, u64 cap, DevState* st
 
 __device__ __forceinline__ u64 umin64(u64 a, u64 b) { return a < b ? a : b; }
 
+__device__ __forceinline__ u64 sbt_hash(u64 k) {
+  k ^= k >> 33;
+  k *= 0xff51afd7ed558ccdull;
+  k ^= k >> 33;
+  k *= 0xc4ceb9fe1a85ec53ull;
+  return k ^ (k >> 33);
+}
+
+// Slot of key k (> 0), inserting it if absent; kNoSlot when the probe limit is
+// reached. `first` is keys[pos] already loaded for the home position pos.
+__device__ __forceinline__ u32 sbt_place(const SbTable& t, u64 k, u64 pos, u64 first) {
+  u64 cur = first;
+  for (int p = 0; p < kMaxProbe; ++p) {
+    if (cur == k) return (u32)pos;
+    if (cur == 0ull) {
+      const u64 old = atomicCAS(&t.keys[pos], 0ull, k);
+      if (old == 0ull || old == k) return (u32)pos;
+    }
+    pos = (pos + 1) & t.mask;
+    cur = __ldcg(&t.keys[pos]);
+  }
+  return kNoSlot;
+}
+
+// Slot of key k, which must already be in the table; kNoSlot if absent.
+__device__ __forceinline__ u32 sbt_find(const SbTable& t, u64 k) {
+  u64 pos = sbt_hash(k) & t.mask;
+  for (int p = 0; p < kMaxProbe; ++p) {
+    const u64 cur = t.keys[pos];
+    if (cur == k) return (u32)pos;
+    if (cur == 0ull) return kNoSlot;
+    pos = (pos + 1) & t.mask;
+  }
+  return kNoSlot;
+}
+
 }  // namespace aiwc

@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(kIngestThreads) k_mem_ingest(MemIngestArgs a) 
   DevState* st = &a.arena->st;
   const uint4* ev = reinterpret_cast<const uint4*>(a.ev);
   u64 reads = 0, writes = 0, wor = 0, wand = ~0ull, kept = 0;
-  u32 wmin = 0xFFFFFFFFu, wmax = 0u, err = 0u;
+  u32 wmin = 0xFFFFFFFFu, wmax = 0u, err = 0u, sbt_fail = 0u;
   const u64 per_block = (u64)kIngestThreads * kIngestItems;
   for (u64 t0 = (u64)blockIdx.x * per_block; t0 < a.n; t0 += (u64)gridDim.x * per_block) {
     uint4 e[kIngestItems];
@@ -64,6 +64,27 @@ __global__ void __launch_bounds__(kIngestThreads) k_mem_ingest(MemIngestArgs a) 
       }
     }
     kept += nkeep;
+    if (a.use_tab) {
+      // count events per superblock: batch the home-slot loads, then resolve
+      const int lane = threadIdx.x & 31;
+      u64 pos[kIngestItems], first[kIngestItems];
+#pragma unroll
+      for (int k = 0; k < kIngestItems; ++k) {
+        pos[k] = sbt_hash((word[k] >> 12) + 1ull) & a.tab.mask;
+        first[k] = keep[k] ? __ldcg(&a.tab.keys[pos[k]]) : 0ull;
+      }
+#pragma unroll
+      for (int k = 0; k < kIngestItems; ++k) {
+        u32 slot = kNoSlot;
+        if (keep[k]) {
+          slot = sbt_place(a.tab, (word[k] >> 12) + 1ull, pos[k], first[k]);
+          if (slot == kNoSlot) sbt_fail = 1u;
+        }
+        const bool v = slot != kNoSlot;
+        const u32 peers = __match_any_sync(0xffffffffu, v ? slot : (0xFFFFFFE0u | (u32)lane));
+        if (v && lane == __ffs(peers) - 1) atomicAdd(&a.tab.cnt[slot], (u32)__popc(peers));
+      }
+    }
     if (FILTER) {
       // compact the kept words of this block-tile behind one atomicAdd
       const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -102,7 +123,9 @@ __global__ void __launch_bounds__(kIngestThreads) k_mem_ingest(MemIngestArgs a) 
   wmin = block_reduce(wmin, OpMin(), 0xFFFFFFFFu, red32);
   wmax = block_reduce(wmax, OpMax(), 0u, red32);
   err = block_reduce(err, OpOr(), 0u, red32);
+  sbt_fail = block_reduce(sbt_fail, OpOr(), 0u, red32);
   if (threadIdx.x == 0) {
+    if (sbt_fail) atomicOr(&st->sbt_overflow, 1u);
     if (reads) atomicAdd(&st->total_reads, reads);
     if (writes) atomicAdd(&st->total_writes, writes);
     if (kept) {

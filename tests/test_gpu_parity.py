@@ -83,7 +83,7 @@ def test_tiny_workload(P):
 
 
 @pytest.mark.parametrize("seed", range(40))
-def test_random_tiny_traces(P, seed):
+def test_random_tiny_traces(P, seed):  # noqa: D103 (plans alternate with the seed)
     rng = np.random.default_rng(20_000 + seed)
     tr = random_trace(seed, n_mem=int(rng.integers(0, 300)), n_br=int(rng.integers(0, 300)),
                       n_wi=int(rng.integers(1, 9)), n_runs=int(rng.integers(1, 12)),
@@ -94,19 +94,33 @@ def test_random_tiny_traces(P, seed):
     mask = int(rng.choice([0xF, 0x1, 0x6]))
     o = oracle.compute(tr, history_len=h, space_mask=mask)
     g = run_gpu(P, tr, on_device=bool(seed % 2), split=1 + seed % 3, single_runs=seed % 4 == 3, history_len=h,
-                space_mask=mask)
+                space_mask=mask, plan=(seed // 2) % 2)
     assert_parity(g, o)
 
 
+@pytest.mark.parametrize("plan", [0, 1])
 @pytest.mark.parametrize("n_mem,n_br,n_wi,per_wi", [
     (300_000 + 12345, 200_001, 257, 1000),
     (4096 * 7, 4096 * 3, 64, 4096),
     (1_000_003, 1_000_003, 1000, 1001),
 ])
-def test_large_shape_ragged(P, n_mem, n_br, n_wi, per_wi):
+def test_large_shape_ragged(P, n_mem, n_br, n_wi, per_wi, plan):
     tr = synth.large(seed=3, n_mem=n_mem, n_br=n_br, n_wi=n_wi, per_wi=per_wi, zipf_distinct=1 << 16)
     o = oracle.compute(tr)
-    assert_parity(run_gpu(P, tr), o)
+    assert_parity(run_gpu(P, tr, plan=plan), o)
+
+
+def test_hash_plan_table_overflow_falls_back_to_sort(P):
+    """A table far too small for the superblocks overflows; that invocation is
+    finished by the sort plan, the next one gets a larger table -- results
+    are identical either way."""
+    tr = synth.large(seed=4, n_mem=400_000, n_br=1000, n_wi=4, per_wi=100, zipf_distinct=1 << 18)
+    o = oracle.compute(tr)
+    from paper_1805_04207_gb300.api import push_trace
+    with P.Characterizer(n_opcodes=tr.n_opcodes, table_slots=64) as c:
+        for _ in range(6):  # 64 -> 256 -> 1024 -> ... slots
+            push_trace(c, tr.to("cuda"))
+            assert_parity(c.compute(), o)
 
 
 def test_empty_and_single_stream(P):
@@ -115,27 +129,30 @@ def test_empty_and_single_stream(P):
         assert_parity(run_gpu(P, tr), oracle.compute(tr), hist=tr.ops is not None)
 
 
-def test_one_address_many_tiles(P):
+@pytest.mark.parametrize("plan", [0, 1])
+def test_one_address_many_tiles(P, plan):
     # one run of equal keys spanning many tiles exercises the cross-tile fix-up
     tr = mem_only([1 << 20] * 200_000, stores=[i % 3 == 0 for i in range(200_000)])
-    assert_parity(run_gpu(P, tr), oracle.compute(tr))
+    assert_parity(run_gpu(P, tr, plan=plan), oracle.compute(tr))
     tr = branch_only([9] * 100_000, list(range(100_000)), [int(i % 7 != 0) for i in range(100_000)])
     assert_parity(run_gpu(P, tr), oracle.compute(tr))
 
 
-def test_key_extremes_and_spaces(P):
+@pytest.mark.parametrize("plan", [0, 1])
+def test_key_extremes_and_spaces(P, plan):
     top = (1 << 61) - 1
     addrs = [0, 1, top, top - 1, 1 << 60, 0, top] * 1000
     spaces = [0, 3, 3, 0, 1, 2, 2] * 1000
     tr = mem_only(addrs, stores=[i % 2 for i in range(len(addrs))], spaces=spaces)
     for mask in (0xF, 0x9, 0x2):
-        assert_parity(run_gpu(P, tr, space_mask=mask), oracle.compute(tr, space_mask=mask))
+        assert_parity(run_gpu(P, tr, space_mask=mask, plan=plan), oracle.compute(tr, space_mask=mask))
 
 
-def test_all_distinct_addresses(P):
+@pytest.mark.parametrize("plan", [0, 1])
+def test_all_distinct_addresses(P, plan):
     n = 150_000
     tr = mem_only(list(range(0, 8 * n, 8)))
-    assert_parity(run_gpu(P, tr), oracle.compute(tr))
+    assert_parity(run_gpu(P, tr, plan=plan), oracle.compute(tr))
 
 
 def test_value_overflow_paths(P):

@@ -210,6 +210,40 @@ uint64_t aiwc_kernel_launches(void);
 aiwc_status aiwc_set_stage_timing(aiwc_handle* h, int on);
 int aiwc_stage_times(const aiwc_handle* h, double* ms, const char** names, int n);
 
+/* ------------------------------------------------- without any allocation */
+
+/* The memory metrics (Table I memory rows: totals, unique reads and writes,
+ * footprint, 90% footprint, global and local address entropies) and the
+ * work-item count of one invocation's memory events, computed without any
+ * device allocation. The paper has no counterpart: this entry point exists
+ * for callers that may not call cudaMalloc or cudaFree -- code whose device
+ * memory belongs to another allocator (a framework's caching allocator or a
+ * fixed pool it must stay inside) and code that must not trigger the
+ * device-wide synchronisation that freeing device memory implies.
+ *
+ *   device       CUDA device ordinal; events must live on it.
+ *   cuda_stream  cudaStream_t the work is ordered on (NULL = default stream).
+ *   events       DEVICE pointer to n aiwc_mem_event records, 16-byte aligned,
+ *                owned by the caller and only read.
+ *   n            at most 262144 (2^18) events; larger n -> AIWC_EINVAL.
+ *   space_mask   as aiwc_config.space_mask.
+ *   out          HOST pointer; the memory fields and work_items are written,
+ *                every other field is zero (out->opcode_hist is left as is).
+ * Work-item ids must be below 2^20. Blocks until the result is on the host.
+ *
+ * Scratch: one file-scope device array of about 16 MiB inside the library
+ * (every device that loads the library holds it until the process exits),
+ * shared by all calls on a device and keeping the last call's contents, which
+ * each call clears where it must start at zero. Calls whose GPU work overlaps
+ * (concurrent streams, or threads) race on that array and give wrong results:
+ * serialise them. The first call on a device looks the array's address up
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. No cudaMalloc, cudaFree or allocating library
+ * routine is called. Errors: AIWC_EINVAL (bad arguments or event data),
+ * AIWC_ENOMEM (the fixed scratch overflowed), AIWC_ECUDA. */
+aiwc_status aiwc_mem_metrics_noalloc(int device, void* cuda_stream, const aiwc_mem_event* events, size_t n,
+                                     uint32_t space_mask, aiwc_metrics* out);
+
 #ifdef __cplusplus
 }
 #endif

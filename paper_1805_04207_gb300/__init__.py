@@ -73,6 +73,7 @@ SIGNATURES = {
     "aiwc_set_stage_timing": (_ST, [_VP, ctypes.c_int]),
     "aiwc_stage_times": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_char_p),
                                         ctypes.c_int]),
+    "aiwc_mem_metrics_noalloc": (_ST, [ctypes.c_int, _VP, _VP, _SZ, ctypes.c_uint32, ctypes.POINTER(aiwc_metrics)]),
 }
 
 LIB_PATH = _build.LIB
@@ -185,6 +186,13 @@ def aiwc_stage_times(h) -> dict:
     names = (ctypes.c_char_p * 32)()
     k = lib.aiwc_stage_times(h, ms, names, 32)
     return {names[i].decode(): ms[i] for i in range(k)}
+
+
+def aiwc_mem_metrics_noalloc(device: int, stream, events_ptr: int, n: int, space_mask: int = 0xF) -> dict:
+    """Memory metrics of n device-resident events without any device allocation."""
+    m = aiwc_metrics()
+    _check(lib.aiwc_mem_metrics_noalloc(device, stream, events_ptr, n, space_mask, ctypes.byref(m)))
+    return _to_dict(m)
 
 
 from .api import Characterizer, characterize  # noqa: E402,F401

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "aiwc.h"
 
 namespace aiwc {
@@ -122,6 +124,9 @@ struct SortDesc {
   u32* block_sums;
   u32 ntiles;
 };
+
+// Text returned by aiwc_last_error(NULL) on this thread.
+void set_last_error(const std::string& msg);
 
 // Kernels launched by this library (process-wide, all handles).
 void count_launches(u64 n);

@@ -52,6 +52,8 @@ const char* const kStageNames[kNumStages] = {"mem_ingest", "branch_ingest", "ins
 
 }  // namespace
 
+void aiwc::set_last_error(const std::string& msg) { g_last_error = msg; }
+
 struct aiwc_handle {
   aiwc_config cfg;
   cudaStream_t stream = nullptr;

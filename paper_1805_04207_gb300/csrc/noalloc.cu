@@ -1,0 +1,184 @@
+// Memory metrics of one small invocation using no device allocation at all.
+//
+// Some callers may not call cudaMalloc / cudaFree: code whose device memory is
+// owned by another allocator (a framework's caching allocator, a fixed pool)
+// and code that must not trigger the device-wide synchronisation that
+// cudaFree implies. For them this entry point runs the memory path of the
+// reduction (ingest with the superblock table, segment histograms, overflow
+// sort, finalize) with every scratch buffer carved out of one file-scope
+// device array, sized for at most kNoAllocMaxEvents events. The array is
+// part of the library's image: every device that loads the library holds it
+// until the process exits.
+#include <mutex>
+#include <string>
+
+#include "aiwc_internal.cuh"
+
+namespace aiwc {
+namespace {
+
+constexpr u64 kNoAllocMaxEvents = 1ull << 18;  // memory events per call
+constexpr u64 kNoAllocSlots = 1ull << 19;      // superblock table: load factor <= 1/2
+constexpr u64 kNoAllocMaxWi = 1ull << 20;      // work-item ids per call
+constexpr u64 kNoAllocOverCap = (u64)kLevels * (kNoAllocMaxEvents / kCocDense + 2) + 256;
+
+constexpr size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+constexpr u64 tiles_of(u64 n) { return (n + kTile - 1) / kTile; }
+
+constexpr size_t kOffArena = 0;
+constexpr size_t kOffResult = kOffArena + a256(sizeof(Arena));
+constexpr size_t kOffWords = kOffResult + a256(sizeof(Result));
+constexpr size_t kOffLow = kOffWords + a256(8 * kNoAllocMaxEvents);
+constexpr size_t kOffTable = kOffLow + a256(2 * kNoAllocMaxEvents);
+constexpr size_t kOffScan = kOffTable + a256(24 * kNoAllocSlots);
+constexpr size_t kOffOverA = kOffScan + a256(4 * (kNoAllocSlots / 4096 + 1));
+constexpr size_t kOffOverB = kOffOverA + a256(8 * kNoAllocOverCap);
+constexpr size_t kCountsWords = 256 * tiles_of(kNoAllocOverCap);
+constexpr size_t kOffCounts = kOffOverB + a256(8 * kNoAllocOverCap);
+constexpr size_t kOffBsums = kOffCounts + a256(4 * kCountsWords);
+constexpr size_t kOffBitmap = kOffBsums + a256(4 * (kCountsWords / 4096 + 2));
+constexpr size_t kNoAllocBytes = kOffBitmap + a256(kNoAllocMaxWi / 8);
+
+static_assert(kNoAllocBytes <= (32ull << 20), "the no-allocation scratch must stay modest");
+
+// The scratch every call of aiwc_mem_metrics_noalloc shares (one per device).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Device addresses of g_noalloc_scratch, looked up once per device.
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void* g_addr[kMaxDevices] = {};
+
+struct Guard {
+  int prev = -1;
+  explicit Guard(int d) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != d) cudaSetDevice(d);
+  }
+  ~Guard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+aiwc_status fail(aiwc_status s, const std::string& msg) {
+  set_last_error(msg);
+  return s;
+}
+
+}  // namespace
+}  // namespace aiwc
+
+using namespace aiwc;
+
+extern "C" aiwc_status aiwc_mem_metrics_noalloc(int device, void* cuda_stream, const aiwc_mem_event* events,
+                                                size_t n, uint32_t space_mask, aiwc_metrics* out) {
+  if (!out || (n && !events)) return fail(AIWC_EINVAL, "null events or output");
+  if (n > kNoAllocMaxEvents)
+    return fail(AIWC_EINVAL, "aiwc_mem_metrics_noalloc takes at most 262144 (2^18) memory events per call");
+  if ((uintptr_t)events & 15u) return fail(AIWC_EINVAL, "device memory events must be 16-byte aligned");
+  if (device < 0 || device >= kMaxDevices) return fail(AIWC_EINVAL, "no such CUDA device");
+  Guard g(device);
+  uint64_t* user_hist = out->opcode_hist;
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_addr[device]) {
+      // set-up on the first call on this device, with the device current
+      cudaError_t e = cudaGetSymbolAddress(&g_addr[device], g_noalloc_scratch);
+      if (e != cudaSuccess) {
+        g_addr[device] = nullptr;
+        cudaGetLastError();
+        return fail(AIWC_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      }
+    }
+    base = g_addr[device];
+  }
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  char* p = (char*)base;
+  Arena* arena = (Arena*)(p + kOffArena);
+  Result* result = (Result*)(p + kOffResult);
+  SbTable tab;
+  tab.keys = (u64*)(p + kOffTable);
+  tab.cnt = (u32*)(p + kOffTable + 8 * kNoAllocSlots);
+  tab.off = (u32*)(p + kOffTable + 12 * kNoAllocSlots);
+  tab.cur = (u32*)(p + kOffTable + 16 * kNoAllocSlots);
+  tab.mask = kNoAllocSlots - 1;
+  u32* used_list = (u32*)(p + kOffTable + 20 * kNoAllocSlots);
+  u32* bitmap = (u32*)(p + kOffBitmap);
+  // the previous call's contents remain: clear what has to start at zero
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(arena, 0, sizeof(Arena), s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(tab.keys, 0, 12 * kNoAllocSlots, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(bitmap, 0, kNoAllocMaxWi / 8, s)) != cudaSuccess)
+    return fail(AIWC_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+  launch_reset_identities(arena, s);
+  MemIngestArgs ia;
+  ia.tab = tab;
+  ia.use_tab = 1;
+  ia.ev = events;
+  ia.n = n;
+  ia.space_mask = space_mask & 0xFu;
+  ia.words = (u64*)(p + kOffWords);
+  ia.word_base = 0;
+  ia.wi_bitmap = bitmap;
+  ia.max_wi = kNoAllocMaxWi;
+  ia.arena = arena;
+  launch_mem_ingest(ia, s);
+  u64* over_a = (u64*)(p + kOffOverA);
+  u64* over_b = (u64*)(p + kOffOverB);
+  HashArgs ha;
+  ha.words = ia.words;
+  ha.n_cap = kNoAllocMaxEvents;
+  ha.low = (uint16_t*)(p + kOffLow);
+  ha.tab = tab;
+  ha.scan_tmp = (u32*)(p + kOffScan);
+  ha.n_used = &arena->st.sb_used;
+  ha.used_list = used_list;
+  ha.over = over_a;
+  ha.over_cap = kNoAllocOverCap;
+  ha.arena = arena;
+  ha.grid_scatter = 152 * 2;
+  ha.grid_segments = 152 * 4;
+  launch_mem_hash(ha, s);
+  launch_wi_count(bitmap, arena, s);
+  SortDesc d;
+  d.a = over_a;
+  d.b = over_b;
+  d.cur = &arena->st.sort_cur[kSortOver];
+  d.n = &arena->st.n_over;
+  d.n_cap = kNoAllocOverCap;
+  d.key_or = &arena->st.over_or;
+  d.key_and = &arena->st.over_and;
+  d.mask = ~0ull;
+  d.lo_bit = 0;
+  d.counts = (u32*)(p + kOffCounts);
+  d.block_sums = (u32*)(p + kOffBsums);
+  d.ntiles = (u32)tiles_of(kNoAllocOverCap);
+  sort_keys(d, s);
+  FinalizeArgs fa;
+  fa.over_a = over_a;
+  fa.over_b = over_b;
+  fa.over_cur = d.cur;
+  fa.over_cap = kNoAllocOverCap;
+  fa.arena = arena;
+  fa.result = result;
+  fa.cover_num = 9;
+  fa.cover_den = 10;
+  fa.precision = 0;
+  launch_finalize(fa, s);
+  Result r;
+  u32 table_overflow = 0;
+  if ((e = cudaGetLastError()) != cudaSuccess ||
+      (e = cudaMemcpyAsync(&r, result, sizeof(Result), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(&table_overflow, &arena->st.sbt_overflow, 4, cudaMemcpyDeviceToHost, s)) !=
+          cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess)
+    return fail(AIWC_ECUDA, std::string("aiwc_mem_metrics_noalloc: ") + cudaGetErrorString(e));
+  *out = r.m;
+  out->opcode_hist = user_hist;
+  if (table_overflow) return fail(AIWC_ENOMEM, "superblock table of the no-allocation scratch overflowed");
+  if (r.err & kErrOverflow) return fail(AIWC_ENOMEM, "overflow list of the no-allocation scratch overflowed");
+  if (r.err & kErrAddr) return fail(AIWC_EINVAL, "memory address outside the 61-bit domain");
+  if (r.err & kErrWorkItem) return fail(AIWC_EINVAL, "work-item id >= 2^20 in aiwc_mem_metrics_noalloc");
+  return AIWC_OK;
+}

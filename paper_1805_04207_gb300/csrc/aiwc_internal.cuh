@@ -62,6 +62,13 @@ struct DevState {
   u32 sbt_overflow;      // the superblock table could not place a key
   u32 pad2;
   u64 sb_used;           // occupied superblock slots
+  u64 n_spill;           // hash plan: events whose superblock the table could not place
+  u64 br_sort_mask;      // bits the branch sort must order (site only when work-items arrive sorted)
+  u64 br_site_max;       // longest per-site outcome sequence
+  u64 n_sites;           // entries of the site list
+  u32 br_unsorted;       // some work-item id arrived below its predecessor
+  u32 br_last_wi[2];     // last work-item id of the previous / current push (by push parity)
+  u32 pad3;
   u32 sort_cur[8];       // which ping-pong buffer holds each sort's data
   u32 pad;
 };
@@ -72,11 +79,11 @@ struct DevState {
 constexpr u32 kNoSlot = 0xFFFFFFFFu;
 constexpr int kMaxProbe = 256;
 struct SbTable {
-  u64* keys;
-  u32* cnt;
-  u32* off;
-  u32* cur;
-  u64 mask;
+  u64* keys{};
+  u32* cnt{};
+  u32* off{};
+  u32* cur{};
+  u64 mask{};
 };
 
 // Sort slots (index into DevState::sort_cur).
@@ -111,18 +118,19 @@ struct Result {
 // buffer is b when *cur is 1. Only bits in `mask` that vary between keys are
 // sorted, in 8-bit windows starting at `lo_bit`.
 struct SortDesc {
-  u64* a;
-  u64* b;
-  u32* cur;
-  const u64* n;       // device count of keys (clamped to n_cap)
-  u64 n_cap;          // capacity of a and b, in keys
-  const u64* key_or;  // device OR over keys
-  const u64* key_and; // device AND over keys
-  u64 mask;
-  int lo_bit;
-  u32* counts;        // 256 * ntiles digit counts (scanned in place)
-  u32* block_sums;
-  u32 ntiles;
+  u64* a{};
+  u64* b{};
+  u32* cur{};
+  const u64* n{};     // device count of keys (clamped to n_cap)
+  u64 n_cap{};          // capacity of a and b, in keys
+  const u64* key_or{};  // device OR over keys
+  const u64* key_and{}; // device AND over keys
+  u64 mask{};
+  const u64* dmask{}; // optional device mask, ANDed with mask (NULL = none)
+  int lo_bit{};
+  u32* counts{};      // 256 * ntiles digit counts (scanned in place)
+  u32* block_sums{};
+  u32 ntiles{};
 };
 
 // Text returned by aiwc_last_error(NULL) on this thread.
@@ -137,122 +145,153 @@ void sort_keys(const SortDesc& d, cudaStream_t s);
 size_t sort_counts_words(u64 n_max);  // u32 words needed for counts
 size_t sort_block_sums_words(u64 n_max);
 
+constexpr u32 kSlotWordNone = 0xFFFFFFFFu;  // slot word of an event the table could not place
+constexpr u64 kMaxHashSlots = 1ull << 20;   // slot words hold 20 slot bits
+
 struct MemIngestArgs {
-  SbTable tab;         // used when use_tab (hash plan)
-  int use_tab;
-  const void* ev;
-  u64 n;
-  u32 space_mask;
-  u64* words;
-  u64 word_base;       // offset for the unfiltered fast path
-  u32* wi_bitmap;
-  u64 max_wi;
-  Arena* arena;
+  SbTable tab{};       // used when use_tab (hash plan)
+  int use_tab{};
+  u32* slotw{};          // hash plan: out, 32-bit slot words
+  u64* spill{};          // hash plan: out, full words of events the table could not place
+  const void* ev{};
+  u64 n{};
+  u32 space_mask{};
+  u64* words{};          // sort plan: out, 64-bit sort words
+  u64 word_base{};       // offset for the unfiltered fast path
+  u32* wi_bitmap{};
+  u64 max_wi{};
+  Arena* arena{};
 };
 void launch_mem_ingest(const MemIngestArgs& a, cudaStream_t s);
 
 struct LevelArgs {
-  const u64* a;
-  const u64* b;
-  const u32* cur;
-  const u64* n;
-  TileSum* tiles;      // kLevels * ntiles
-  u32 ntiles;
-  u64* over;
-  u64 over_cap;
-  Arena* arena;
-  int grid;
+  const u64* a{};
+  const u64* b{};
+  const u32* cur{};
+  const u64* n{};
+  TileSum* tiles{};      // kLevels * ntiles
+  u32 ntiles{};
+  u64* over{};
+  u64 over_cap{};
+  Arena* arena{};
+  int grid{};
 };
 void launch_mem_levels(const LevelArgs& a, cudaStream_t s);
 
 struct HashArgs {
-  const u64* words;    // unsorted memory words
-  u64 n_cap;           // capacity of words / low, in elements
-  uint16_t* low;       // out: low 12 bits grouped by superblock
-  SbTable tab;
-  u32* scan_tmp;       // sbt_scan_words(capacity) words
-  u64* n_used;         // out: occupied slots
-  u32* used_list;      // out: their indices (capacity = table slots)
-  u64* over;
-  u64 over_cap;
-  Arena* arena;
-  int grid_scatter, grid_segments;
+  const u32* slotw{};    // slot words from the ingest
+  u64 n_cap{};           // capacity of slotw / low, in elements
+  uint16_t* low{};       // out: low 12 bits grouped by superblock
+  SbTable tab{};
+  u32* scan_tmp{};     // sbt_scan_words(capacity) words
+  u64* n_used{};         // out: occupied slots
+  u32* used_list{};    // out: their indices (capacity = table slots)
+  u64* over{};
+  u64 over_cap{};
+  Arena* arena{};
+  int grid_scatter{}, grid_segments{};
 };
 size_t sbt_scan_words(u64 cap);
 void launch_mem_hash(const HashArgs& a, cudaStream_t s);
+// Fallback after a table overflow: rebuild the 64-bit sort words from the
+// slot words and the table, after the n_spill spilled words already in words[].
+void launch_rebuild_words(const u32* slotw, SbTable tab, u64* words, Arena* arena, int grid, cudaStream_t s);
 
 struct BranchIngestArgs {
-  const void* ev;
-  u64 n;
-  u64* words;
-  u64 word_base;
-  u32* wi_bitmap;
-  u64 max_wi;
-  Arena* arena;
+  u32 push_index{};    // pushes so far in this invocation (0 = first)
+  const void* ev{};
+  u64 n{};
+  u64* words{};
+  u64 word_base{};
+  u32* wi_bitmap{};
+  u64 max_wi{};
+  Arena* arena{};
 };
 void launch_branch_ingest(const BranchIngestArgs& a, cudaStream_t s);
 
 struct WindowArgs {
-  const u64* a;        // sorted branch words (ping-pong)
-  const u64* b;
-  const u32* cur;
-  u64 n;               // branch events
-  u32 h;               // history length
-  u64* patterns;       // out: pattern words (sentinel where no full history)
-  TileSum* tiles;      // site-level tile summaries
-  u32 ntiles;
-  u64* over;
-  u64 over_cap;
-  Arena* arena;
-  int grid;
+  const u64* a{};      // sorted branch words (ping-pong)
+  const u64* b{};
+  const u32* cur{};
+  u64 n{};               // branch events
+  u32 h{};               // history length
+  u64* patterns{};     // out: compacted pattern words
+  TileSum* tiles{};      // site-level tile summaries
+  u32 ntiles{};
+  u64* over{};
+  u64 over_cap{};
+  Arena* arena{};
+  int grid{};
 };
 void launch_branch_windows(const WindowArgs& a, cudaStream_t s);
 
 struct PatternArgs {
-  const u64* a;
-  const u64* b;
-  const u32* cur;
-  const u64* n;        // valid pattern words (device)
-  TileSum* tiles;
-  u32 ntiles;
-  Arena* arena;
-  int grid;
+  const u64* a{};
+  const u64* b{};
+  const u32* cur{};
+  const u64* n{};      // valid pattern words (device)
+  TileSum* tiles{};
+  u32 ntiles{};
+  Arena* arena{};
+  int grid{};
 };
 void launch_pattern_runs(const PatternArgs& a, cudaStream_t s);
+
+// Per-site path: list the site segments of the sorted branch words, then
+// count (site, history) patterns of each site in shared memory.
+struct SiteArgs {
+  const u64* a{};
+  const u64* b{};
+  const u32* cur{};
+  u64 n{};               // branch events
+  u32 h{};             // history length (<= kSiteMaxHist)
+  u64* sites{};        // site list: (start, length) pairs, 2 words per site
+  u64 sites_cap{};
+  u64* over{};
+  u64 over_cap{};
+  Arena* arena{};
+  int grid{};
+};
+constexpr u32 kSiteMaxHist = 17;       // dense pattern bins: 2^15 per pass, at most 4 passes
+constexpr u64 kSiteMaxLen = 65535;     // packed 16-bit taken / total counters
+constexpr u64 kSiteListCap = 1ull << 20;  // sites listed for the per-site path
+void launch_site_heads(const SiteArgs& a, cudaStream_t s);
+void launch_site_patterns(const SiteArgs& a, cudaStream_t s);
+void launch_branch_mask(Arena* arena, cudaStream_t s);
 
 // Cross-tile fix-up of run lengths. kind: 0 = memory levels, 1 = sites, 2 = patterns.
 void launch_runs_fixup(int kind, const TileSum* tiles, u32 ntiles_max, const u64* n_dev, u64 n_host,
                        int levels, u64* over, u64 over_cap, Arena* arena, cudaStream_t s);
 
 struct RunBatchArgs {
-  const uint16_t* ops;
-  u64 n_ops;
-  const u32* run_wi;
-  const u64* run_off;
-  const u64* run_len;
-  u64 n_runs;
-  u64 seq_base;        // global index of the first run of this batch
-  u32 n_opcodes;
-  u64* run_keys;       // out: (wi << 32 | seq)
-  u64* run_sum;        // out: 4 words per run: has_b, pre, suf, tot
-  u32* wi_bitmap;
-  u64 max_wi;
-  u64* opc_hist;       // n_opcodes counts
-  u64* over;
-  u64 over_cap;
-  Arena* arena;
+  const uint16_t* ops{};
+  u64 n_ops{};
+  const u32* run_wi{};
+  const u64* run_off{};
+  const u64* run_len{};
+  u64 n_runs{};
+  u64 seq_base{};        // global index of the first run of this batch
+  u32 n_opcodes{};
+  u64* run_keys{};     // out: (wi << 32 | seq)
+  u64* run_sum{};        // out: 4 words per run: has_b, pre, suf, tot
+  u32* wi_bitmap{};
+  u64 max_wi{};
+  u64* opc_hist{};       // n_opcodes counts
+  u64* over{};
+  u64 over_cap{};
+  Arena* arena{};
 };
 void launch_instr_runs(const RunBatchArgs& a, cudaStream_t s);
 
 struct CombineArgs {
-  const u64* a;
-  const u64* b;
-  const u32* cur;
-  u64 n_runs;
-  const u64* run_sum;
-  u64* over;
-  u64 over_cap;
-  Arena* arena;
+  const u64* a{};
+  const u64* b{};
+  const u32* cur{};
+  u64 n_runs{};
+  const u64* run_sum{};
+  u64* over{};
+  u64 over_cap{};
+  Arena* arena{};
 };
 void launch_instr_combine(const CombineArgs& a, cudaStream_t s);
 
@@ -262,14 +301,14 @@ void launch_wi_clear(u32* bitmap, Arena* arena, cudaStream_t s);
 void launch_reset_identities(Arena* arena, cudaStream_t s);
 
 struct FinalizeArgs {
-  const u64* over_a;
-  const u64* over_b;
-  const u32* over_cur;
-  u64 over_cap;
-  Arena* arena;
-  Result* result;
-  u32 cover_num, cover_den;
-  u32 precision;
+  const u64* over_a{};
+  const u64* over_b{};
+  const u32* over_cur{};
+  u64 over_cap{};
+  Arena* arena{};
+  Result* result{};
+  u32 cover_num{}, cover_den{};
+  u32 precision{};
 };
 void launch_finalize(const FinalizeArgs& a, cudaStream_t s);
 

@@ -79,9 +79,11 @@ struct aiwc_handle {
   DevBuf sbt, sbt_scan;
   u64 sbt_cap = 0;       // slots currently allocated
   u64 sbt_want = 1ull << 20;
-  u32* h_flag = nullptr; // pinned
+  DevState* h_state = nullptr;  // pinned copy of the device counters
+  DevBuf sites;                 // per-site segment list
   bool last_plan_hash = false;
   u64 n_mem = 0, n_br = 0, n_runs = 0;
+  u32 br_pushes = 0;    // branch ingest launches in this invocation (orders the sortedness check)
   u64 value_bound = 0;  // bound on ITB / IPT values >= kValDense (each uses kValDense instructions)
   // pending single-run pushes (host data, or device pointers)
   std::vector<uint16_t> pend_ops;
@@ -251,7 +253,7 @@ SbTable table_view(aiwc_handle* h) {
 aiwc_status ensure_table(aiwc_handle* h) {
   if (h->sbt_cap >= h->sbt_want && h->sbt.p) return AIWC_OK;
   if (h->n_mem) return AIWC_OK;  // never resize in the middle of an invocation
-  const u64 C = h->sbt_want;
+  const u64 C = std::min<u64>(h->sbt_want, kMaxHashSlots);
   aiwc_status s = ensure(h, h->sbt, 24 * C, false);
   if (s != AIWC_OK) return s;
   s = ensure(h, h->sbt_scan, 4 * sbt_scan_words(C), false);
@@ -474,7 +476,7 @@ aiwc_status aiwc_create(const aiwc_config* cfg, aiwc_handle** out) {
       (e = cudaMalloc(&h->d_hist, (size_t)cfg->n_opcodes * 8)) != cudaSuccess ||
       (e = cudaMallocHost(&h->h_result, sizeof(Result))) != cudaSuccess ||
       (e = cudaMallocHost(&h->h_hist, (size_t)cfg->n_opcodes * 8)) != cudaSuccess ||
-      (e = cudaMallocHost(&h->h_flag, 64)) != cudaSuccess)
+      (e = cudaMallocHost(&h->h_state, sizeof(DevState))) != cudaSuccess)
     return bail(cuda_fail(nullptr, "allocation", e));
   h->bytes = sizeof(Arena) + sizeof(Result) + (size_t)cfg->n_opcodes * 8;
   if (reset_device_state(h) != AIWC_OK) return bail(fail(nullptr, AIWC_ECUDA, h->err));
@@ -496,7 +498,12 @@ aiwc_status aiwc_push_mem(aiwc_handle* h, const aiwc_mem_event* ev, size_t n, in
   if (use_hash(h) && (s = ensure_table(h)) != AIWC_OK) return s;
   MemIngestArgs a;
   a.use_tab = use_hash(h) && h->sbt_cap ? 1 : 0;
-  if (a.use_tab) a.tab = table_view(h);
+  if (a.use_tab) {
+    ENSURE(h->mem_b, (h->n_mem + n) * 4, true);  // slot words
+    a.tab = table_view(h);
+    a.slotw = (u32*)h->mem_b.p;
+    a.spill = (u64*)h->mem_a.p;
+  }
   a.space_mask = h->cfg.space_mask;
   a.words = (u64*)h->mem_a.p;
   a.wi_bitmap = h->wi_bitmap;
@@ -535,6 +542,7 @@ aiwc_status aiwc_push_branch(aiwc_handle* h, const aiwc_branch_event* ev, size_t
   ENSURE(h->br_a, (h->n_br + n) * 8, true);
   if ((s = ensure_bitmap(h)) != AIWC_OK) return s;
   BranchIngestArgs a;
+  a.push_index = h->br_pushes;
   a.words = (u64*)h->br_a.p;
   a.wi_bitmap = h->wi_bitmap;
   a.max_wi = h->max_wi;
@@ -550,6 +558,7 @@ aiwc_status aiwc_push_branch(aiwc_handle* h, const aiwc_branch_event* ev, size_t
   } else {
     s = staged_copy(h, ev, n * 8, 8, [&](void* p, size_t first, size_t cnt) {
       BranchIngestArgs b = a;
+      b.push_index = h->br_pushes++;
       b.ev = p;
       b.n = cnt;
       b.word_base = base + first;
@@ -557,6 +566,7 @@ aiwc_status aiwc_push_branch(aiwc_handle* h, const aiwc_branch_event* ev, size_t
     });
     if (s != AIWC_OK) return s;
   }
+  if (on_device) h->br_pushes++;
   h->n_br += n;
   return AIWC_OK;
 }
@@ -608,6 +618,7 @@ aiwc_status aiwc_compute(aiwc_handle* h, aiwc_metrics* out) {
   cudaStream_t st = h->stream;
   auto reset_host = [&]() {
     h->n_mem = h->n_br = h->n_runs = 0;
+    h->br_pushes = 0;
     h->value_bound = 0;
     h->pend_ops.clear();
     h->pend_wi.clear();
@@ -628,7 +639,7 @@ aiwc_status aiwc_compute(aiwc_handle* h, aiwc_metrics* out) {
   const u64 over_cap = h->over_a.cap / 8;
   const u64 nmax = std::max(std::max(n_mem, n_br), std::max(n_runs, over_cap));
   ENSURE(h->mem_a, std::max<u64>(n_mem, 1) * 8, true);
-  ENSURE(h->mem_b, std::max<u64>(n_mem, 1) * 8, false);
+  ENSURE(h->mem_b, std::max<u64>(n_mem, 1) * 8, true);  // holds the slot words of the hash plan
   ENSURE(h->br_a, std::max<u64>(n_br, 1) * 8, true);
   ENSURE(h->br_b, std::max<u64>(n_br, 1) * 8, false);
   ENSURE(h->pat_a, std::max<u64>(n_br, 1) * 8, false);
@@ -655,27 +666,67 @@ aiwc_status aiwc_compute(aiwc_handle* h, aiwc_metrics* out) {
     d.key_or = kor;
     d.key_and = kand;
     d.mask = mask;
+    d.dmask = nullptr;
     d.lo_bit = lo;
     d.counts = (u32*)h->counts.p;
     d.block_sums = (u32*)h->bsums.p;
     d.ntiles = (u32)ntiles_of(n_host);
     return d;
   };
-  // memory: the hash plan unless the superblock table overflowed (then sort)
-  bool hash_ok = false;
-  if (n_mem && use_hash(h) && h->sbt_cap) {
-    CK(cudaMemcpyAsync(h->h_flag, &dst->sbt_overflow, 4, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    hash_ok = *h->h_flag == 0;
-    if (!hash_ok) h->sbt_want = std::max<u64>(h->sbt_want, std::min<u64>(h->sbt_cap * 4, 1ull << 30));
+  // branches, first part: sort by site (and work-item unless they arrived in
+  // order), keeping program order; list the site segments
+  SortDesc bsort;
+  SiteArgs sa;
+  const u64 sites_cap = std::min<u64>(std::max<u64>(n_br, 1), kSiteListCap);
+  if (n_br) {
+    ENSURE(h->sites, sites_cap * 16, false);
+    bsort = sdesc(h->br_a, h->br_b, kSortBranch, &dst->n_branch, &dst->br_or, &dst->br_and, ~1ull, 0, n_br);
+    bsort.dmask = &dst->br_sort_mask;
+    {
+      StageScope sc(h, kStBrSort);
+      launch_branch_mask(h->arena, st);
+      sort_keys(bsort, st);
+    }
+    sa.a = bsort.a;
+    sa.b = bsort.b;
+    sa.cur = bsort.cur;
+    sa.n = n_br;
+    sa.h = h->cfg.history_len;
+    sa.sites = (u64*)h->sites.p;
+    sa.sites_cap = sites_cap;
+    sa.over = over;
+    sa.over_cap = over_cap;
+    sa.arena = h->arena;
+    sa.grid = h->sm_count;
+    StageScope sc(h, kStWindows);
+    launch_site_heads(sa, st);
   }
-  h->last_plan_hash = n_mem && use_hash(h) && h->sbt_cap;
+  // one host read of the device state decides the memory plan (hash unless
+  // the superblock table overflowed) and the branch path (per site unless a
+  // site is too long or the history too deep for the shared-memory bins)
+  bool hash_ok = false, per_site = false;
+  if ((n_mem && use_hash(h) && h->sbt_cap) || n_br) {
+    CK(cudaMemcpyAsync(h->h_state, dst, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    hash_ok = n_mem && use_hash(h) && h->sbt_cap && h->h_state->sbt_overflow == 0;
+    if (n_mem && use_hash(h) && h->sbt_cap && !hash_ok) h->sbt_want = std::min<u64>(h->sbt_cap * 4, kMaxHashSlots);
+    per_site = n_br && h->cfg.history_len <= kSiteMaxHist && h->h_state->br_site_max <= kSiteMaxLen &&
+               h->h_state->n_sites <= sites_cap && h->cfg.plan != 1;
+  }
+  const bool ran_hash = n_mem && use_hash(h) && h->sbt_cap;
+  h->last_plan_hash = ran_hash;
+  const size_t low_off = ((size_t)n_mem * 4 + 255) & ~size_t(255);
+  if (hash_ok) ENSURE(h->mem_b, low_off + (size_t)n_mem * 2, true);
+  if (ran_hash && !hash_ok) {
+    // the table overflowed: rebuild 64-bit words behind the spilled ones, then sort
+    launch_rebuild_words((const u32*)h->mem_b.p, table_view(h), (u64*)h->mem_a.p, h->arena, grid * 2, st);
+  }
   if (hash_ok) {
     StageScope sc(h, kStMemLevels);
     HashArgs ha;
-    ha.words = (const u64*)h->mem_a.p;
-    ha.n_cap = std::min<u64>(h->mem_a.cap / 8, h->mem_b.cap / 2);
-    ha.low = (uint16_t*)h->mem_b.p;
+    ha.slotw = (const u32*)h->mem_b.p;
+    ha.n_cap = std::min<u64>(n_mem, (h->mem_b.cap - low_off) / 2);
+    ha.low = (uint16_t*)((char*)h->mem_b.p + low_off);
     ha.tab = table_view(h);
     ha.scan_tmp = (u32*)h->sbt_scan.p;
     ha.n_used = &dst->sb_used;
@@ -707,13 +758,13 @@ aiwc_status aiwc_compute(aiwc_handle* h, aiwc_metrics* out) {
     launch_mem_levels(la, st);
     launch_runs_fixup(0, la.tiles, la.ntiles, &dst->n_words, 0, kLevels, over, over_cap, h->arena, st);
   }
-  // branches: sort by (site, work-item) keeping push order, windows, patterns
-  if (n_br) {
-    SortDesc d = sdesc(h->br_a, h->br_b, kSortBranch, &dst->n_branch, &dst->br_or, &dst->br_and, ~1ull, 1, n_br);
-    {
-      StageScope sc(h, kStBrSort);
-      sort_keys(d, st);
-    }
+  // branches, second part: patterns per site in shared memory, or the
+  // global path (windows, pattern sort, pattern runs)
+  if (n_br && per_site) {
+    StageScope sc(h, kStPatRuns);
+    launch_site_patterns(sa, st);
+  } else if (n_br) {
+    const SortDesc& d = bsort;
     WindowArgs wa;
     wa.a = d.a;
     wa.b = d.b;
@@ -826,7 +877,7 @@ aiwc_status aiwc_destroy(aiwc_handle* h) {
   if (h->stream || h->copy_stream) cudaStreamSynchronize(h->stream);
   DevBuf* bufs[] = {&h->mem_a, &h->mem_b, &h->br_a, &h->br_b, &h->pat_a, &h->pat_b, &h->rk_a, &h->rk_b,
                     &h->run_sum, &h->over_a, &h->over_b, &h->counts, &h->bsums, &h->tiles, &h->stage[0],
-                    &h->stage[1], &h->desc, &h->sbt, &h->sbt_scan};
+                    &h->stage[1], &h->desc, &h->sbt, &h->sbt_scan, &h->sites};
   for (DevBuf* b : bufs) release(h, *b);
   if (h->wi_bitmap) cudaFree(h->wi_bitmap);
   if (h->arena) cudaFree(h->arena);
@@ -834,7 +885,7 @@ aiwc_status aiwc_destroy(aiwc_handle* h) {
   if (h->d_hist) cudaFree(h->d_hist);
   if (h->h_result) cudaFreeHost(h->h_result);
   if (h->h_hist) cudaFreeHost(h->h_hist);
-  if (h->h_flag) cudaFreeHost(h->h_flag);
+  if (h->h_state) cudaFreeHost(h->h_state);
   for (int i = 0; i < 2; ++i) {
     if (h->ev_copied[i]) cudaEventDestroy(h->ev_copied[i]);
     if (h->ev_free[i]) cudaEventDestroy(h->ev_free[i]);

@@ -24,19 +24,33 @@ __global__ void __launch_bounds__(kBrThreads) k_branch_ingest(BranchIngestArgs a
   __shared__ u32 red32[32];
   DevState* st = &a.arena->st;
   const uint2* ev = reinterpret_cast<const uint2*>(a.ev);
+  const int lane = threadIdx.x & 31;
   u64 wor = 0, wand = ~0ull;
-  u32 wmin = 0xFFFFFFFFu, wmax = 0u, err = 0u;
+  u32 wmin = 0xFFFFFFFFu, wmax = 0u, err = 0u, unsorted = 0u;
   const u64 per_block = (u64)kBrThreads * kBrItems;
   for (u64 t0 = (u64)blockIdx.x * per_block; t0 < a.n; t0 += (u64)gridDim.x * per_block) {
+    uint2 e[kBrItems];
+#pragma unroll
+    for (int k = 0; k < kBrItems; ++k) {
+      const u64 i = t0 + (u64)k * kBrThreads + threadIdx.x;
+      e[k] = i < a.n ? __ldcs(ev + i) : make_uint2(0u, 0u);
+    }
 #pragma unroll
     for (int k = 0; k < kBrItems; ++k) {
       const u64 i = t0 + (u64)k * kBrThreads + threadIdx.x;
       const bool valid = i < a.n;
-      const uint2 e = valid ? __ldcs(ev + i) : make_uint2(0u, 0u);
-      const u32 wi = e.y & 0x7FFFFFFFu;
+      const u32 wi = e[k].y & 0x7FFFFFFFu;
       mark_work_items(a.wi_bitmap, a.max_wi, wi, valid, &err);
+      // do work-item ids arrive in non-decreasing order? (lanes hold consecutive events)
+      u32 prev = __shfl_up_sync(0xffffffffu, wi, 1);
+      if (lane == 0 && valid) {
+        if (i > 0) prev = ev[i - 1].y & 0x7FFFFFFFu;
+        else prev = a.push_index ? st->br_last_wi[(a.push_index - 1) & 1] : 0u;
+      }
       if (valid) {
-        const u64 w = ((u64)e.x << 32) | ((u64)wi << 1) | (u64)(e.y >> 31);
+        if (wi < prev) unsorted = 1u;
+        if (i == a.n - 1) st->br_last_wi[a.push_index & 1] = wi;
+        const u64 w = ((u64)e[k].x << 32) | ((u64)wi << 1) | (u64)(e[k].y >> 31);
         a.words[a.word_base + i] = w;
         wor |= w;
         wand &= w;
@@ -52,16 +66,121 @@ __global__ void __launch_bounds__(kBrThreads) k_branch_ingest(BranchIngestArgs a
   wmin = block_reduce(wmin, OpMin(), 0xFFFFFFFFu, red32);
   wmax = block_reduce(wmax, OpMax(), 0u, red32);
   err = block_reduce(err, OpOr(), 0u, red32);
+  unsorted = block_reduce(unsorted, OpOr(), 0u, red32);
   if (threadIdx.x == 0) {
+    atomicOr(&st->br_or, wor);
+    atomicAnd(&st->br_and, wand);
     if (wmin <= wmax) {
-      atomicOr(&st->br_or, wor);
-      atomicAnd(&st->br_and, wand);
       atomicMin(&st->wi_min, wmin);
       atomicMax(&st->wi_max, wmax);
     }
     if (err) atomicOr(&st->err, err);
+    if (unsorted) atomicOr(&st->br_unsorted, 1u);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&st->n_branch, a.n);
+}
+
+// Bits the branch sort orders: the site alone when work-item ids arrived in
+// non-decreasing order (a stable sort then keeps (work-item, program order)
+// inside each site); otherwise site and work-item (bit 0, the outcome, never).
+__global__ void k_branch_mask(Arena* arena) {
+  DevState* st = &arena->st;
+  st->br_sort_mask = st->br_unsorted ? ~1ull : 0xFFFFFFFF00000000ull;
+}
+
+// Lists each site's segment of the sorted branch words: (start, length).
+__global__ void __launch_bounds__(256) k_site_heads(SiteArgs a) {
+  DevState* st = &a.arena->st;
+  const u64* w = *a.cur ? a.b : a.a;
+  const u64 n = a.n;
+  u64 mx = 0;
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x) {
+    const u64 site = w[i] >> 32;
+    if (i > 0 && (w[i - 1] >> 32) == site) continue;
+    u64 lo = i + 1, hi = n;  // first position with a larger site
+    while (lo < hi) {
+      const u64 mid = (lo + hi) >> 1;
+      if ((w[mid] >> 32) > site) hi = mid; else lo = mid + 1;
+    }
+    const u64 len = lo - i;
+    mx = len > mx ? len : mx;
+    const u64 k = atomicAdd(&st->n_sites, 1ull);
+    if (k < a.sites_cap) {
+      a.sites[2 * k] = i;
+      a.sites[2 * k + 1] = len;
+    }
+  }
+  if (mx) atomicMax(&st->br_site_max, mx);
+}
+
+constexpr int kSpThreads = 512;
+constexpr int kSpBinsLog = 15;
+constexpr int kSpBitWords = (int)((kSiteMaxLen + 32) / 32) + 2;
+
+// One block per site: its outcomes become a bit string in shared memory; for
+// every outcome with h predecessors, the packed counter of its history gets
+// +1 total (low 16 bits) and +outcome taken (high 16 bits). Histories are
+// binned 2^15 at a time (more passes for h > 15). M and N' follow from the
+// bins. Any fixed bijection of the h-bit window names the pattern equally
+// well; here bit k of the pattern is the outcome k+1 places after the oldest.
+__global__ void __launch_bounds__(kSpThreads) k_site_patterns(SiteArgs a) {
+  extern __shared__ u32 spm[];
+  u32* bits = spm;
+  u32* cnt = spm + kSpBitWords;
+  __shared__ u64 red64[32];
+  DevState* st = &a.arena->st;
+  const u64* w = *a.cur ? a.b : a.a;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = kSpThreads / 32;
+  const u32 h = a.h;
+  const int pbits = h > (u32)kSpBinsLog ? kSpBinsLog : (int)h;
+  const u32 nbins = 1u << pbits;
+  const u32 passes = h > (u32)kSpBinsLog ? (1u << (h - kSpBinsLog)) : 1u;
+  const u64 hmask = (1ull << h) - 1ull;
+  const u64 n_sites = umin64(st->n_sites, a.sites_cap);
+  u64 msum = 0, nsum = 0, nsite = 0;
+  for (u64 si = blockIdx.x; si < n_sites; si += gridDim.x) {
+    const u64 start = a.sites[2 * si], m = a.sites[2 * si + 1];
+    if (threadIdx.x == 0) {
+      ++nsite;
+      if (m < (u64)kCocDense) atomicAdd(&a.arena->site_coc[m], 1ull);
+      else overflow_append(a.over, a.over_cap, st, kTagSites, m);
+    }
+    const u32 nwords = (u32)((m + 31) / 32);
+    for (u32 c = wp; c < nwords + 2; c += nw) {
+      const u64 j = (u64)c * 32 + lane;
+      const bool t = j < m && (w[start + j] & 1ull);
+      const u32 b = __ballot_sync(0xffffffffu, t);
+      if (lane == 0) bits[c] = b;
+    }
+    __syncthreads();
+    for (u32 q = 0; q < passes; ++q) {
+      for (u32 i = threadIdx.x; i < nbins; i += kSpThreads) cnt[i] = 0u;
+      __syncthreads();
+      for (u64 j = h + threadIdx.x; j < m; j += kSpThreads) {
+        const u64 pos = j - h;
+        const u64 two = (u64)bits[pos >> 5] | ((u64)bits[(pos >> 5) + 1] << 32);
+        const u32 win = (u32)((two >> (pos & 31)) & hmask);
+        const u32 outcome = (bits[j >> 5] >> (j & 31)) & 1u;
+        if ((win >> pbits) == q) atomicAdd(&cnt[win & (nbins - 1)], 1u + (outcome << 16));
+      }
+      __syncthreads();
+      for (u32 i = threadIdx.x; i < nbins; i += kSpThreads) {
+        const u32 v = cnt[i];
+        const u32 nn = v & 0xFFFFu, t = v >> 16;
+        msum += t < nn - t ? t : nn - t;
+        nsum += nn;
+      }
+      __syncthreads();
+    }
+  }
+  msum = block_reduce(msum, OpAdd(), 0ull, red64);
+  nsum = block_reduce(nsum, OpAdd(), 0ull, red64);
+  nsite = block_reduce(nsite, OpAdd(), 0ull, red64);
+  if (threadIdx.x == 0) {
+    if (msum) atomicAdd(&st->minsum, msum);
+    if (nsum) atomicAdd(&st->npat, nsum);
+    if (nsite) atomicAdd(&st->branch_sites, nsite);
+  }
 }
 
 constexpr int kHalo = 32;  // history lengths are at most 31
@@ -274,6 +393,26 @@ void launch_branch_ingest(const BranchIngestArgs& a, cudaStream_t s) {
   u64 blocks = (a.n + per_block - 1) / per_block;
   if (blocks > 152ull * 8) blocks = 152ull * 8;
   k_branch_ingest<<<(unsigned)blocks, kBrThreads, 0, s>>>(a);
+  count_launches(1);
+}
+
+void launch_branch_mask(Arena* arena, cudaStream_t s) {
+  k_branch_mask<<<1, 1, 0, s>>>(arena);
+  count_launches(1);
+}
+
+void launch_site_heads(const SiteArgs& a, cudaStream_t s) {
+  if (a.n == 0) return;
+  u64 blocks = (a.n + 255) / 256;
+  if (blocks > (u64)a.grid * 4) blocks = (u64)a.grid * 4;
+  k_site_heads<<<(unsigned)blocks, 256, 0, s>>>(a);
+  count_launches(1);
+}
+
+void launch_site_patterns(const SiteArgs& a, cudaStream_t s) {
+  const size_t smem = (size_t)(kSpBitWords + (1 << kSpBinsLog)) * 4;
+  cudaFuncSetAttribute(k_site_patterns, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  k_site_patterns<<<a.grid, kSpThreads, smem, s>>>(a);
   count_launches(1);
 }
 

@@ -69,12 +69,13 @@ __device__ __forceinline__ void overflow_append(u64* over, u64 cap, DevState* st
 
 __device__ __forceinline__ u64 umin64(u64 a, u64 b) { return a < b ? a : b; }
 
+// Home slot of a superblock key: fold to 32 bits, multiply by a 32-bit odd
+// constant (Knuth's multiplicative hashing) and keep the high bits through
+// the caller's mask after a final mix of the high half into the low half.
 __device__ __forceinline__ u64 sbt_hash(u64 k) {
-  k ^= k >> 33;
-  k *= 0xff51afd7ed558ccdull;
-  k ^= k >> 33;
-  k *= 0xc4ceb9fe1a85ec53ull;
-  return k ^ (k >> 33);
+  const u32 x = (u32)k ^ (u32)(k >> 32) * 0x85EBCA6Bu;
+  const u32 y = x * 0x9E3779B1u;
+  return (u64)(y ^ (y >> 15));
 }
 
 // Slot of key k (> 0), inserting it if absent; kNoSlot when the probe limit is

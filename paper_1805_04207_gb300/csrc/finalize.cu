@@ -263,6 +263,11 @@ __device__ double clog_sum(const u64* dense, const u64* over, u64 ob, u64 oe, u3
   return (double)ex + fl;
 }
 
+// One block per independent task: blocks 0..10 the entropy of each skip
+// level, 11..13 the three coverage counts, 14..15 the ITB / IPT order
+// statistics, 16 the scalar fields. Each block writes disjoint fields.
+constexpr int kFinBlocks = 17;
+
 __global__ void __launch_bounds__(kFinThreads) k_finalize(FinalizeArgs a) {
   __shared__ Shared s;
   Arena* ar = a.arena;
@@ -281,56 +286,66 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(FinalizeArgs a) {
   }
   __syncthreads();
   aiwc_metrics* m = &a.result->m;
-  // memory
+  const int task = blockIdx.x;
   const u64 N = st.total_reads + st.total_writes;
-  for (int l = 0; l < kLevels; ++l) {
+  if (task < kLevels) {
+    const int l = task;
     const double S = clog_sum(ar->mem_coc[l], over, s.tag_begin[l], s.tag_begin[l + 1], a.precision, s);
     if (threadIdx.x == 0) {
       double H = 0.0;
       if (N) {
-        H = a.precision ? (double)(log2f((float)N)) : log2((double)N);
         if (a.precision) {
           // log2 N = e + log2(f) with the same split as the terms
           const int e = 63 - __clzll((long long)N);
           H = (double)e + (double)log2f((float)((double)N / (double)(1ull << e)));
+        } else {
+          H = log2((double)N);
         }
         H -= S / (double)N;
         if (H < 0.0) H = 0.0;
       }
       m->entropy[l] = H;
     }
-  }
-  const u64 fcover = cover_walk(ar->mem_coc[0], kCocDense, over, s.tag_begin[0], s.tag_begin[1], N, a.cover_num,
-                                a.cover_den, s);
-  const u64 scover = cover_walk(ar->site_coc, kCocDense, over, s.tag_begin[kTagSites], s.tag_begin[kTagSites + 1],
-                                st.n_branch, a.cover_num, a.cover_den, s);
-  const u64 ocover = cover_walk(ar->opc_coc, kCocDense, over, s.tag_begin[kTagOpcodes],
-                                s.tag_begin[kTagOpcodes + 1], st.total_instructions, a.cover_num, a.cover_den, s);
-  u64 ic, imn, imx, ilo, ihi, pc, pmn, pmx, plo, phi;
-  double imed, pmed;
-  order_stats(ar->itb_dense, over, s.tag_begin[kTagItb], s.tag_begin[kTagItb + 1], &ic, &imn, &imx, &ilo, &ihi, &imed,
-              s);
-  order_stats(ar->ipt_dense, over, s.tag_begin[kTagIpt], s.tag_begin[kTagIpt + 1], &pc, &pmn, &pmx, &plo, &phi, &pmed,
-              s);
-  if (threadIdx.x == 0) {
+  } else if (task == 11) {
+    const u64 c = cover_walk(ar->mem_coc[0], kCocDense, over, s.tag_begin[0], s.tag_begin[1], N, a.cover_num,
+                             a.cover_den, s);
+    if (threadIdx.x == 0) m->footprint_cover = c;
+  } else if (task == 12) {
+    const u64 c = cover_walk(ar->site_coc, kCocDense, over, s.tag_begin[kTagSites], s.tag_begin[kTagSites + 1],
+                             st.n_branch, a.cover_num, a.cover_den, s);
+    if (threadIdx.x == 0) m->branch_cover = c;
+  } else if (task == 13) {
+    const u64 c = cover_walk(ar->opc_coc, kCocDense, over, s.tag_begin[kTagOpcodes], s.tag_begin[kTagOpcodes + 1],
+                             st.total_instructions, a.cover_num, a.cover_den, s);
+    if (threadIdx.x == 0) m->opcode_cover = c;
+  } else if (task == 14 || task == 15) {
+    const bool itb = task == 14;
+    const int tag = itb ? kTagItb : kTagIpt;
+    u64 c, mn, mx, lo, hi;
+    double med;
+    order_stats(itb ? ar->itb_dense : ar->ipt_dense, over, s.tag_begin[tag], s.tag_begin[tag + 1], &c, &mn, &mx, &lo,
+                &hi, &med, s);
+    if (threadIdx.x == 0) {
+      if (itb) {
+        m->itb_count = c; m->itb_min = mn; m->itb_max = mx; m->itb_median_lo = lo; m->itb_median_hi = hi;
+        m->itb_median = med;
+      } else {
+        m->ipt_count = c; m->ipt_min = mn; m->ipt_max = mx; m->ipt_median_lo = lo; m->ipt_median_hi = hi;
+        m->ipt_median = med;
+      }
+    }
+  } else if (threadIdx.x == 0) {
     m->total_instructions = st.total_instructions;
     m->unique_opcodes = st.unique_opcodes;
-    m->opcode_cover = ocover;
     m->work_items = st.work_items;
     m->barriers = st.barriers;
-    m->itb_count = ic; m->itb_min = imn; m->itb_max = imx; m->itb_median_lo = ilo; m->itb_median_hi = ihi;
-    m->itb_median = imed;
-    m->ipt_count = pc; m->ipt_min = pmn; m->ipt_max = pmx; m->ipt_median_lo = plo; m->ipt_median_hi = phi;
-    m->ipt_median = pmed;
     m->total_reads = st.total_reads;
     m->total_writes = st.total_writes;
     m->footprint = st.footprint;
-    m->footprint_cover = fcover;
     m->unique_reads = st.unique_reads;
     m->unique_writes = st.unique_writes;
     m->branch_events = st.n_branch;
     m->branch_sites = st.branch_sites;
-    m->branch_cover = scover;
     m->branch_patterns = st.npat;
     m->branch_minsum = st.minsum;
     if (a.precision)
@@ -371,7 +386,7 @@ void launch_reset_identities(Arena* arena, cudaStream_t s) {
 }
 
 void launch_finalize(const FinalizeArgs& a, cudaStream_t s) {
-  k_finalize<<<1, kFinThreads, 0, s>>>(a);
+  k_finalize<<<kFinBlocks, kFinThreads, 0, s>>>(a);
   count_launches(1);
 }
 

@@ -2,8 +2,8 @@
 // opcode histogram, barrier count, instructions-to-barrier (ITB) segments and
 // instructions per thread (IPT).
 //
-// One warp scans one run (a work-item's opcodes in program order) 256
-// opcodes at a time, 8 per lane. Segments closed by two barriers inside the
+// One warp scans one run (a work-item's opcodes in program order) 512
+// opcodes at a time, 16 per lane. Segments closed by two barriers inside the
 // run are emitted directly; a warp-wide segmented scan carries the open tally
 // across lanes and steps. What a run cannot finish alone -- the tally before
 // its first barrier and after its last -- is left in a 4-word run summary;
@@ -19,6 +19,7 @@ namespace {
 
 constexpr int kInThreads = 256;
 constexpr int kInWarps = kInThreads / 32;
+constexpr int kOpsPerLane = 16;  // opcodes each lane takes per step (two 16-byte loads)
 
 // Value histograms (ITB / IPT): privatised in shared memory below kValSmem,
 // global dense below kValDense, overflow list above.
@@ -55,11 +56,12 @@ __global__ void __launch_bounds__(kInThreads) k_instr_runs(RunBatchArgs a, int h
   DevState* st = &a.arena->st;
   const u32 nop = a.n_opcodes;
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  const u32 hwords = hist_mode == 0 ? nop * kInWarps : (hist_mode == 1 ? nop : 0u);
+  const u32 hstride = nop + 1;  // one spare bin absorbs barriers and padding
+  const u32 hwords = hist_mode == 0 ? hstride * kInWarps : (hist_mode == 1 ? hstride : 0u);
   for (u32 i = threadIdx.x; i < hwords; i += kInThreads) dyn[i] = 0u;
   for (int i = threadIdx.x; i < kValSmem; i += kInThreads) itb_small[i] = 0u;
   __syncthreads();
-  u32* my_hist = hist_mode == 0 ? dyn + wp * nop : dyn;
+  u32* my_hist = hist_mode == 0 ? dyn + wp * hstride : dyn;
   u64 nbar = 0, run_or = 0, run_and = ~0ull;
   u32 err = 0, wmin = 0xFFFFFFFFu, wmax = 0u;
   const u64 gwarp = (u64)blockIdx.x * kInWarps + wp;
@@ -82,48 +84,70 @@ __global__ void __launch_bounds__(kInThreads) k_instr_runs(RunBatchArgs a, int h
     Seg carry = seg_identity();
     u64 tot = 0, run_pre = 0;
     bool have_pre = false;
-    for (u64 s0 = 0; s0 < len; s0 += 256) {
-      const u64 my0 = s0 + (u64)lane * 8;
-      const int nv = my0 < len ? (int)umin64(len - my0, 8ull) : 0;
-      u32 op[8];
-      if (nv == 8 && aligned) {
-        const uint4 v = __ldcs(reinterpret_cast<const uint4*>(p + my0));
-        op[0] = v.x & 0xFFFFu; op[1] = v.x >> 16; op[2] = v.y & 0xFFFFu; op[3] = v.y >> 16;
-        op[4] = v.z & 0xFFFFu; op[5] = v.z >> 16; op[6] = v.w & 0xFFFFu; op[7] = v.w >> 16;
+    for (u64 s0 = 0; s0 < len; s0 += 32 * kOpsPerLane) {
+      const u64 my0 = s0 + (u64)lane * kOpsPerLane;
+      const int nv = my0 < len ? (int)umin64(len - my0, (u64)kOpsPerLane) : 0;
+      u32 pk[kOpsPerLane / 2];  // two opcodes per word, low half first
+      if (nv == kOpsPerLane && aligned) {
+        const uint4* q = reinterpret_cast<const uint4*>(p + my0);
+        const uint4 v0 = __ldcs(q), v1 = __ldcs(q + 1);
+        pk[0] = v0.x; pk[1] = v0.y; pk[2] = v0.z; pk[3] = v0.w;
+        pk[4] = v1.x; pk[5] = v1.y; pk[6] = v1.z; pk[7] = v1.w;
       } else {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) op[k] = k < nv ? (u32)p[my0 + k] : 0u;
-      }
-      int fb = -1;
-      u64 lead = 0, cur = 0, cnt = 0;
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        if (k < nv) {
-          const u32 o = op[k];
-          if (o == AIWC_BARRIER) {
-            if (fb >= 0) emit_value(itb_small, a.arena->itb_dense, a.over, a.over_cap, st, kTagItb, cur);
-            else fb = k;
-            cur = 0;
-            ++nbar;
-          } else {
-            if (o < nop) {
-              if (hist_mode == 2) atomicAdd(&a.opc_hist[o], 1ull);
-              else atomicAdd(&my_hist[o], 1u);
-            } else {
-              err |= kErrOpcode;
-            }
-            ++cnt;
-            if (fb < 0) ++lead; else ++cur;
-          }
+        for (int k = 0; k < kOpsPerLane / 2; ++k) {
+          const u32 lo = 2 * k < nv ? (u32)p[my0 + 2 * k] : 0u;
+          const u32 hi = 2 * k + 1 < nv ? (u32)p[my0 + 2 * k + 1] : 0u;
+          pk[k] = lo | (hi << 16);
         }
       }
+      // bit k of bm: opcode k is a barrier marker; nbm: a counted instruction
+      u32 bm = 0, vm = nv >= 32 ? 0xFFFFFFFFu : ((1u << nv) - 1u);
+#pragma unroll
+      for (int k = 0; k < kOpsPerLane; ++k) {
+        const u32 o = (pk[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu;
+        const bool valid = k < nv;
+        const bool is_bar = o == AIWC_BARRIER;
+        bm |= (valid && is_bar) ? (1u << k) : 0u;
+        const bool bad = valid && !is_bar && o >= nop;
+        err |= bad ? kErrOpcode : 0u;
+        // every lane adds once per opcode slot; slots that count nothing land in bin nop
+        const u32 bin = (valid && !is_bar && !bad) ? o : nop;
+        if (hist_mode == 2) {
+          if (bin < nop) atomicAdd(&a.opc_hist[bin], 1ull);
+        } else {
+          atomicAdd(&my_hist[bin], 1u);
+        }
+      }
+      const u32 nbm = vm & ~bm;
+      const u64 cnt = (u64)__popc(nbm);
+      u64 lead, cur;
+      if (bm) {
+        const int fb = __ffs(bm) - 1, lb = 31 - __clz(bm);
+        lead = (u64)__popc(nbm & ((1u << fb) - 1u));
+        cur = (u64)__popc(nbm & ~((2u << lb) - 1u));
+        nbar += (u64)__popc(bm);
+        // segments closed by two barriers of this lane
+        u32 rest = bm & (bm - 1u);
+        int prevb = fb;
+        while (rest) {
+          const int nb = __ffs(rest) - 1;
+          const u32 between = ((1u << nb) - 1u) & ~((2u << prevb) - 1u);
+          emit_value(itb_small, a.arena->itb_dense, a.over, a.over_cap, st, kTagItb, (u64)__popc(nbm & between));
+          prevb = nb;
+          rest &= rest - 1u;
+        }
+      } else {
+        lead = cnt;
+        cur = 0;
+      }
       Seg e;
-      e.b = fb >= 0 ? 1u : 0u;
-      e.v = fb >= 0 ? cur : lead;
+      e.b = bm ? 1u : 0u;
+      e.v = bm ? cur : lead;
       e.w = 0;
       Seg agg;
       Seg ex = seg_op(carry, warp_seg_scan(e, &agg));
-      if (fb >= 0) {
+      if (bm) {
         const u64 seg = ex.v + lead;
         if (ex.b) emit_value(itb_small, a.arena->itb_dense, a.over, a.over_cap, st, kTagItb, seg);
         else { run_pre = seg; have_pre = true; }
@@ -151,7 +175,7 @@ __global__ void __launch_bounds__(kInThreads) k_instr_runs(RunBatchArgs a, int h
   if (hist_mode == 0) {
     for (u32 o = threadIdx.x; o < nop; o += kInThreads) {
       u32 s = 0;
-      for (int q = 0; q < kInWarps; ++q) s += dyn[q * nop + o];
+      for (int q = 0; q < kInWarps; ++q) s += dyn[q * hstride + o];
       if (s) atomicAdd(&a.opc_hist[o], (u64)s);
     }
   } else if (hist_mode == 1) {
@@ -222,8 +246,9 @@ void launch_instr_runs(const RunBatchArgs& a, cudaStream_t s) {
   if (a.n_runs == 0) return;
   int mode;
   size_t smem;
-  if ((size_t)a.n_opcodes * kInWarps * 4 <= 48 * 1024) { mode = 0; smem = (size_t)a.n_opcodes * kInWarps * 4; }
-  else if ((size_t)a.n_opcodes * 4 <= 96 * 1024) { mode = 1; smem = (size_t)a.n_opcodes * 4; }
+  const size_t bins = (size_t)a.n_opcodes + 1;
+  if (bins * kInWarps * 4 <= 48 * 1024) { mode = 0; smem = bins * kInWarps * 4; }
+  else if (bins * 4 <= 96 * 1024) { mode = 1; smem = bins * 4; }
   else { mode = 2; smem = 0; }
   static bool attr_set = false;
   if (!attr_set) {

@@ -14,33 +14,42 @@ namespace aiwc {
 namespace {
 
 constexpr int kIngestThreads = 256;
-constexpr int kIngestItems = 8;
 
-template <bool FILTER>
-__global__ void __launch_bounds__(kIngestThreads) k_mem_ingest(MemIngestArgs a) {
+// One pass over the 16-byte events. Sort plan (HASH = false): writes the
+// 64-bit sort word of every kept event. Hash plan (HASH = true): places the
+// event's superblock (word >> 12) in the table, counts it there and writes a
+// 32-bit slot word (slot << 12) | (word & 0xFFF) -- the table keeps the
+// superblock, so the word can be rebuilt from the slot word. An event the
+// table cannot place gets the sentinel slot word and its full word goes to
+// the spill list. FILTER: the space mask drops events, so outputs are
+// compacted behind one atomicAdd per block-tile.
+template <bool FILTER, bool HASH>
+__global__ void __launch_bounds__(kIngestThreads, HASH ? 4 : 3) k_mem_ingest(MemIngestArgs a) {
+  constexpr int ITEMS = HASH ? 4 : 8;
   __shared__ u64 red64[32];
   __shared__ u32 red32[32];
   __shared__ u32 scan_tot[33];
   __shared__ u64 s_base;
   DevState* st = &a.arena->st;
   const uint4* ev = reinterpret_cast<const uint4*>(a.ev);
+  const int lane = threadIdx.x & 31;
   u64 reads = 0, writes = 0, wor = 0, wand = ~0ull, kept = 0;
   u32 wmin = 0xFFFFFFFFu, wmax = 0u, err = 0u, sbt_fail = 0u;
-  const u64 per_block = (u64)kIngestThreads * kIngestItems;
+  const u64 per_block = (u64)kIngestThreads * ITEMS;
   for (u64 t0 = (u64)blockIdx.x * per_block; t0 < a.n; t0 += (u64)gridDim.x * per_block) {
-    uint4 e[kIngestItems];
-    bool valid[kIngestItems];
+    uint4 e[ITEMS];
+    bool valid[ITEMS];
 #pragma unroll
-    for (int k = 0; k < kIngestItems; ++k) {
+    for (int k = 0; k < ITEMS; ++k) {
       const u64 i = t0 + (u64)k * kIngestThreads + threadIdx.x;
       valid[k] = i < a.n;
       e[k] = valid[k] ? __ldcs(ev + i) : make_uint4(0u, 0u, 0u, 0u);
     }
-    u64 word[kIngestItems];
-    bool keep[kIngestItems];
+    u64 word[ITEMS];
+    bool keep[ITEMS];
     u32 nkeep = 0;
 #pragma unroll
-    for (int k = 0; k < kIngestItems; ++k) {
+    for (int k = 0; k < ITEMS; ++k) {
       const u64 addr = (u64)e[k].x | ((u64)e[k].y << 32);
       const u32 wi = e[k].z;
       const u32 flags = (e[k].w >> 8) & 0xFFu;
@@ -64,30 +73,34 @@ __global__ void __launch_bounds__(kIngestThreads) k_mem_ingest(MemIngestArgs a) 
       }
     }
     kept += nkeep;
-    if (a.use_tab) {
-      // count events per superblock: batch the home-slot loads, then resolve
-      const int lane = threadIdx.x & 31;
-      u64 pos[kIngestItems], first[kIngestItems];
+    u32 sw[ITEMS];
+    if (HASH) {
+      // batch the home-slot loads, then resolve
+      u64 pos[ITEMS], first[ITEMS];
 #pragma unroll
-      for (int k = 0; k < kIngestItems; ++k) {
+      for (int k = 0; k < ITEMS; ++k) {
         pos[k] = sbt_hash((word[k] >> 12) + 1ull) & a.tab.mask;
         first[k] = keep[k] ? __ldcg(&a.tab.keys[pos[k]]) : 0ull;
       }
 #pragma unroll
-      for (int k = 0; k < kIngestItems; ++k) {
+      for (int k = 0; k < ITEMS; ++k) {
         u32 slot = kNoSlot;
         if (keep[k]) {
           slot = sbt_place(a.tab, (word[k] >> 12) + 1ull, pos[k], first[k]);
-          if (slot == kNoSlot) sbt_fail = 1u;
+          if (slot == kNoSlot) {
+            sbt_fail = 1u;
+            a.spill[atomicAdd(&st->n_spill, 1ull)] = word[k];
+          }
         }
         const bool v = slot != kNoSlot;
         const u32 peers = __match_any_sync(0xffffffffu, v ? slot : (0xFFFFFFE0u | (u32)lane));
         if (v && lane == __ffs(peers) - 1) atomicAdd(&a.tab.cnt[slot], (u32)__popc(peers));
+        sw[k] = v ? ((slot << 12) | (u32)(word[k] & 0xFFFull)) : kSlotWordNone;
       }
     }
     if (FILTER) {
-      // compact the kept words of this block-tile behind one atomicAdd
-      const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+      // compact the kept outputs of this block-tile behind one atomicAdd
+      const int w = threadIdx.x >> 5;
       u32 inc = nkeep;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -104,14 +117,21 @@ __global__ void __launch_bounds__(kIngestThreads) k_mem_ingest(MemIngestArgs a) 
       __syncthreads();
       u64 pos = s_base + scan_tot[w] + inc - nkeep;
 #pragma unroll
-      for (int k = 0; k < kIngestItems; ++k)
-        if (keep[k]) a.words[pos++] = word[k];
+      for (int k = 0; k < ITEMS; ++k) {
+        if (keep[k]) {
+          if (HASH) a.slotw[pos++] = sw[k];
+          else a.words[pos++] = word[k];
+        }
+      }
       __syncthreads();
     } else {
 #pragma unroll
-      for (int k = 0; k < kIngestItems; ++k) {
+      for (int k = 0; k < ITEMS; ++k) {
         const u64 i = t0 + (u64)k * kIngestThreads + threadIdx.x;
-        if (valid[k]) a.words[a.word_base + i] = word[k];
+        if (valid[k]) {
+          if (HASH) a.slotw[a.word_base + i] = sw[k];
+          else a.words[a.word_base + i] = word[k];
+        }
       }
     }
   }
@@ -218,13 +238,18 @@ __global__ void __launch_bounds__(kLvThreads) k_mem_levels(LevelArgs a) {
 
 void launch_mem_ingest(const MemIngestArgs& a, cudaStream_t s) {
   if (a.n == 0) return;
-  const u64 per_block = (u64)kIngestThreads * kIngestItems;
+  const u64 per_block = (u64)kIngestThreads * (a.use_tab ? 4 : 8);
   u64 blocks = (a.n + per_block - 1) / per_block;
-  if (blocks > 152ull * 8) blocks = 152ull * 8;
-  if (a.space_mask == 0xFu)
-    k_mem_ingest<false><<<(unsigned)blocks, kIngestThreads, 0, s>>>(a);
-  else
-    k_mem_ingest<true><<<(unsigned)blocks, kIngestThreads, 0, s>>>(a);
+  const u64 cap = a.use_tab ? 152ull * 16 : 152ull * 8;
+  if (blocks > cap) blocks = cap;
+  const bool filter = a.space_mask != 0xFu;
+  if (a.use_tab) {
+    if (filter) k_mem_ingest<true, true><<<(unsigned)blocks, kIngestThreads, 0, s>>>(a);
+    else k_mem_ingest<false, true><<<(unsigned)blocks, kIngestThreads, 0, s>>>(a);
+  } else {
+    if (filter) k_mem_ingest<true, false><<<(unsigned)blocks, kIngestThreads, 0, s>>>(a);
+    else k_mem_ingest<false, false><<<(unsigned)blocks, kIngestThreads, 0, s>>>(a);
+  }
   count_launches(1);
 }
 

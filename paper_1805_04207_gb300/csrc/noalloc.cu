@@ -28,7 +28,8 @@ constexpr u64 tiles_of(u64 n) { return (n + kTile - 1) / kTile; }
 constexpr size_t kOffArena = 0;
 constexpr size_t kOffResult = kOffArena + a256(sizeof(Arena));
 constexpr size_t kOffWords = kOffResult + a256(sizeof(Result));
-constexpr size_t kOffLow = kOffWords + a256(8 * kNoAllocMaxEvents);
+constexpr size_t kOffSlot = kOffWords + a256(8 * kNoAllocMaxEvents);
+constexpr size_t kOffLow = kOffSlot + a256(4 * kNoAllocMaxEvents);
 constexpr size_t kOffTable = kOffLow + a256(2 * kNoAllocMaxEvents);
 constexpr size_t kOffScan = kOffTable + a256(24 * kNoAllocSlots);
 constexpr size_t kOffOverA = kOffScan + a256(4 * (kNoAllocSlots / 4096 + 1));
@@ -115,6 +116,8 @@ extern "C" aiwc_status aiwc_mem_metrics_noalloc(int device, void* cuda_stream, c
   MemIngestArgs ia;
   ia.tab = tab;
   ia.use_tab = 1;
+  ia.slotw = (u32*)(p + kOffSlot);
+  ia.spill = (u64*)(p + kOffWords);
   ia.ev = events;
   ia.n = n;
   ia.space_mask = space_mask & 0xFu;
@@ -127,7 +130,7 @@ extern "C" aiwc_status aiwc_mem_metrics_noalloc(int device, void* cuda_stream, c
   u64* over_a = (u64*)(p + kOffOverA);
   u64* over_b = (u64*)(p + kOffOverB);
   HashArgs ha;
-  ha.words = ia.words;
+  ha.slotw = ia.slotw;
   ha.n_cap = kNoAllocMaxEvents;
   ha.low = (uint16_t*)(p + kOffLow);
   ha.tab = tab;
@@ -150,6 +153,7 @@ extern "C" aiwc_status aiwc_mem_metrics_noalloc(int device, void* cuda_stream, c
   d.key_or = &arena->st.over_or;
   d.key_and = &arena->st.over_and;
   d.mask = ~0ull;
+  d.dmask = nullptr;
   d.lo_bit = 0;
   d.counts = (u32*)(p + kOffCounts);
   d.block_sums = (u32*)(p + kOffBsums);

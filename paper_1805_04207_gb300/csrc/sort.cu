@@ -26,11 +26,13 @@ constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanBlock = kScanThreads * kScanItems;
 
+__device__ __forceinline__ u64 eff_mask(const SortDesc& d) { return d.dmask ? (d.mask & *d.dmask) : d.mask; }
+
 __device__ __forceinline__ bool pass_shift(const SortDesc& d, int pass, int* shift) {
   int sh = d.lo_bit + 8 * pass;
   *shift = sh;
   if (sh >= 64) return false;
-  u64 varying = ((*d.key_or) ^ (*d.key_and)) & d.mask;
+  u64 varying = ((*d.key_or) ^ (*d.key_and)) & eff_mask(d);
   return ((varying >> sh) & 0xFFull) != 0;
 }
 
@@ -44,10 +46,11 @@ __global__ void __launch_bounds__(kTileThreads) k_hist(SortDesc d, int pass) {
   const u64* src = *d.cur ? d.b : d.a;
   const u64 base = (u64)blockIdx.x * kTile;
   const int w = threadIdx.x >> 5;
+  const u64 m = eff_mask(d);
 #pragma unroll 4
   for (int k = 0; k < kTileItems; ++k) {
     u64 i = base + (u64)k * kTileThreads + threadIdx.x;
-    if (i < n) atomicAdd(&h[w][(src[i] >> shift) & 0xFF], 1u);
+    if (i < n) atomicAdd(&h[w][((src[i] & m) >> shift) & 0xFF], 1u);
   }
   __syncthreads();
   u32 s = 0;
@@ -165,6 +168,7 @@ __global__ void __launch_bounds__(kTileThreads) k_scatter(SortDesc d, int pass) 
   const u64 base = (u64)blockIdx.x * kTile;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const u32 lt_mask = (1u << lane) - 1u;
+  const u64 m = eff_mask(d);
   u64 key[kTileItems];
   u32 rank[kTileItems];
   // Warp w ranks positions base + w*512 + k*32 + lane in that order, which
@@ -174,7 +178,7 @@ __global__ void __launch_bounds__(kTileThreads) k_scatter(SortDesc d, int pass) 
     u64 i = base + (u64)w * (32 * kTileItems) + (u64)k * 32 + lane;
     bool valid = i < n;
     key[k] = valid ? src[i] : 0ull;
-    u32 dig = valid ? (u32)((key[k] >> shift) & 0xFF) : 256u + lane;
+    u32 dig = valid ? (u32)(((key[k] & m) >> shift) & 0xFF) : 256u + lane;
     u32 peers = __match_any_sync(0xffffffffu, dig);
     u32 before = valid ? wcnt[w][dig] : 0u;
     rank[k] = before + __popc(peers & lt_mask);
@@ -202,7 +206,7 @@ __global__ void __launch_bounds__(kTileThreads) k_scatter(SortDesc d, int pass) 
   for (int k = 0; k < kTileItems; ++k) {
     u64 i = base + (u64)w * (32 * kTileItems) + (u64)k * 32 + lane;
     if (i < n) {
-      u32 dig = (u32)((key[k] >> shift) & 0xFF);
+      u32 dig = (u32)(((key[k] & m) >> shift) & 0xFF);
       stage[dofs[dig] + wcnt[w][dig] + rank[k]] = key[k];
     }
   }
@@ -210,7 +214,7 @@ __global__ void __launch_bounds__(kTileThreads) k_scatter(SortDesc d, int pass) 
   const u64 tile_n = n > base ? (n - base < (u64)kTile ? n - base : (u64)kTile) : 0ull;
   for (u32 j = threadIdx.x; j < tile_n; j += kTileThreads) {
     u64 kv = stage[j];
-    u32 dig = (u32)((kv >> shift) & 0xFF);
+    u32 dig = (u32)(((kv & m) >> shift) & 0xFF);
     dst[(u64)gofs[dig] + (j - dofs[dig])] = kv;
   }
 }

@@ -228,3 +228,24 @@ def test_full_size_large_invocation(P):
     torch.cuda.empty_cache()
     o = oracle.compute(tr)
     assert_parity(g, o)
+
+
+@pytest.mark.parametrize("h", [3, 16])
+def test_branch_order_detection_across_pushes(P, h):
+    """Work-items in order inside each push but not across pushes must still
+    give (work-item, program order) histories; in order everywhere takes the
+    site-only sort."""
+    rng = np.random.default_rng(99)
+    n = 30_000
+    sites = rng.integers(0, 7, n)
+    taken = rng.integers(0, 2, n)
+    wis = np.sort(rng.integers(0, 500, n))
+    tr = branch_only(sites.tolist(), wis.tolist(), taken.tolist())
+    o = oracle.compute(tr, history_len=h)
+    assert_parity(run_gpu(P, tr, split=3, history_len=h), o, hist=False)          # in order across pushes
+    # second half pushed first: each push sorted, the concatenation is not
+    half = n // 2
+    swapped = synth.Trace("swap", br=torch.cat([tr.br[half:], tr.br[:half]]).contiguous())
+    assert_parity(run_gpu(P, swapped, split=2, history_len=h), oracle.compute(swapped, history_len=h), hist=False)
+    assert_parity(run_gpu(P, swapped, split=2, history_len=h, on_device=False),
+                  oracle.compute(swapped, history_len=h), hist=False)

@@ -178,10 +178,15 @@ aiwc_status aiwc_push_instr_runs(aiwc_handle* h, const uint32_t* run_wi, const u
 aiwc_status aiwc_compute(aiwc_handle* h, aiwc_metrics* out);
 
 /* Several invocations at once: outs[i] receives the metrics of hs[i], exactly
- * as aiwc_compute(hs[i]) would. The stages of all handles are launched
- * together (one launch per stage over every handle's data) and replayed as
- * one CUDA graph when the same shapes repeat. All handles must share one
- * device and stream. */
+ * as aiwc_compute(hs[i]) would. After one synchronisation that reads every
+ * handle's ingest-time counters, the remaining stages of all handles are
+ * captured as one CUDA graph -- each handle a branch on one of 16 forked
+ * streams, so small invocations run side by side -- and the graph is
+ * replayed while the batch keeps the same handles, sizes and plans. Choices
+ * that depend on device results (the branch-history path) are taken on the
+ * device inside the graph. All handles must share one device and stream;
+ * a handle may appear once. Returns the first non-OK status (each outs[i]
+ * is still written for handles that succeeded). */
 aiwc_status aiwc_compute_batch(aiwc_handle* const* hs, size_t n, aiwc_metrics* outs);
 
 aiwc_status aiwc_destroy(aiwc_handle* h);

@@ -6,7 +6,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import (aiwc_compute, aiwc_config_default, aiwc_create, aiwc_destroy, aiwc_device_bytes, aiwc_push_branch,
+from . import (aiwc_compute, aiwc_compute_batch, aiwc_config_default, aiwc_create, aiwc_destroy, aiwc_device_bytes, aiwc_push_branch,
                aiwc_push_instr, aiwc_push_instr_runs, aiwc_push_mem, aiwc_set_stage_timing, aiwc_stage_times)
 
 
@@ -139,3 +139,17 @@ def characterize(trace, device: int = 0, **cfg) -> dict:
     with Characterizer(device=device, **cfg) as c:
         push_trace(c, trace)
         return c.compute()
+
+
+def compute_batch(chars, want_hist: bool = True) -> list[dict]:
+    """Computes several Characterizers' invocations together (one CUDA graph)."""
+    hists = [np.zeros(c.n_opcodes, dtype=np.uint64) if want_hist else None for c in chars]
+    try:
+        outs = aiwc_compute_batch([c.h for c in chars], hists)
+    finally:
+        for c in chars:
+            c._keep.clear()
+    if want_hist:
+        for o, hh in zip(outs, hists):
+            o["opcode_hist"] = hh
+    return outs

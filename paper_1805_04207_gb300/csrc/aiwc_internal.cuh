@@ -67,6 +67,7 @@ struct DevState {
   u64 br_site_max;       // longest per-site outcome sequence
   u64 n_sites;           // entries of the site list
   u32 br_unsorted;       // some work-item id arrived below its predecessor
+  u32 br_persite;        // the per-site branch path applies (set on the device)
   u32 br_last_wi[2];     // last work-item id of the previous / current push (by push parity)
   u32 pad3;
   u32 sort_cur[8];       // which ping-pong buffer holds each sort's data
@@ -118,6 +119,8 @@ struct Result {
 // buffer is b when *cur is 1. Only bits in `mask` that vary between keys are
 // sorted, in 8-bit windows starting at `lo_bit`.
 struct SortDesc {
+  const u32* gate{};   // run only when !gate || *gate == gate_want (device-side plan choice)
+  u32 gate_want{};
   u64* a{};
   u64* b{};
   u32* cur{};
@@ -141,7 +144,9 @@ void count_launches(u64 n);
 u64 launches_so_far();
 
 // ------------------------------------------------------------- launchers
-void sort_keys(const SortDesc& d, cudaStream_t s);
+// Launches the passes whose bit is set in host_passes (bit p: 8-bit window p);
+// passes whose window holds no varying bit return at once on the device.
+void sort_keys(const SortDesc& d, cudaStream_t s, u32 host_passes = 0xFFu);
 size_t sort_counts_words(u64 n_max);  // u32 words needed for counts
 size_t sort_block_sums_words(u64 n_max);
 
@@ -165,6 +170,8 @@ struct MemIngestArgs {
 void launch_mem_ingest(const MemIngestArgs& a, cudaStream_t s);
 
 struct LevelArgs {
+  const u32* gate{};   // run only when !gate || *gate == gate_want (device-side plan choice)
+  u32 gate_want{};
   const u64* a{};
   const u64* b{};
   const u32* cur{};
@@ -179,6 +186,8 @@ struct LevelArgs {
 void launch_mem_levels(const LevelArgs& a, cudaStream_t s);
 
 struct HashArgs {
+  const u32* gate{};   // run only when !gate || *gate == gate_want (device-side plan choice)
+  u32 gate_want{};
   const u32* slotw{};    // slot words from the ingest
   u64 n_cap{};           // capacity of slotw / low, in elements
   uint16_t* low{};       // out: low 12 bits grouped by superblock
@@ -195,7 +204,8 @@ size_t sbt_scan_words(u64 cap);
 void launch_mem_hash(const HashArgs& a, cudaStream_t s);
 // Fallback after a table overflow: rebuild the 64-bit sort words from the
 // slot words and the table, after the n_spill spilled words already in words[].
-void launch_rebuild_words(const u32* slotw, SbTable tab, u64* words, Arena* arena, int grid, cudaStream_t s);
+void launch_rebuild_words(const u32* slotw, SbTable tab, u64* words, Arena* arena, int grid, cudaStream_t s,
+                          const u32* gate = nullptr, u32 gate_want = 0);
 
 struct BranchIngestArgs {
   u32 push_index{};    // pushes so far in this invocation (0 = first)
@@ -210,6 +220,8 @@ struct BranchIngestArgs {
 void launch_branch_ingest(const BranchIngestArgs& a, cudaStream_t s);
 
 struct WindowArgs {
+  const u32* gate{};   // run only when !gate || *gate == gate_want (device-side plan choice)
+  u32 gate_want{};
   const u64* a{};      // sorted branch words (ping-pong)
   const u64* b{};
   const u32* cur{};
@@ -226,6 +238,8 @@ struct WindowArgs {
 void launch_branch_windows(const WindowArgs& a, cudaStream_t s);
 
 struct PatternArgs {
+  const u32* gate{};   // run only when !gate || *gate == gate_want (device-side plan choice)
+  u32 gate_want{};
   const u64* a{};
   const u64* b{};
   const u32* cur{};
@@ -240,6 +254,8 @@ void launch_pattern_runs(const PatternArgs& a, cudaStream_t s);
 // Per-site path: list the site segments of the sorted branch words, then
 // count (site, history) patterns of each site in shared memory.
 struct SiteArgs {
+  const u32* gate{};   // run only when !gate || *gate == gate_want (device-side plan choice)
+  u32 gate_want{};
   const u64* a{};
   const u64* b{};
   const u32* cur{};
@@ -256,12 +272,18 @@ constexpr u32 kSiteMaxHist = 17;       // dense pattern bins: 2^15 per pass, at 
 constexpr u64 kSiteMaxLen = 65535;     // packed 16-bit taken / total counters
 constexpr u64 kSiteListCap = 1ull << 20;  // sites listed for the per-site path
 void launch_site_heads(const SiteArgs& a, cudaStream_t s);
+// Device-side choice of the branch path: br_persite = the per-site path applies.
+void launch_persite_decide(Arena* arena, u32 h, u64 sites_cap, int allow, cudaStream_t s);
 void launch_site_patterns(const SiteArgs& a, cudaStream_t s);
 void launch_branch_mask(Arena* arena, cudaStream_t s);
 
 // Cross-tile fix-up of run lengths. kind: 0 = memory levels, 1 = sites, 2 = patterns.
 void launch_runs_fixup(int kind, const TileSum* tiles, u32 ntiles_max, const u64* n_dev, u64 n_host,
-                       int levels, u64* over, u64 over_cap, Arena* arena, cudaStream_t s);
+                       int levels, u64* over, u64 over_cap, Arena* arena, cudaStream_t s,
+                       const u32* gate = nullptr, u32 gate_want = 0);
+// Set the attributes kernels with large dynamic shared memory need (current device).
+void init_branch_attributes();
+void init_instr_attributes();
 
 struct RunBatchArgs {
   const uint16_t* ops{};

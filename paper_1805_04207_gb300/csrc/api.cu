@@ -7,6 +7,9 @@
 // overlap the ingest of the previous one. aiwc_compute then sorts, measures
 // runs, finalises and copies one fixed-size result back.
 #include <algorithm>
+#include <atomic>
+#include <functional>
+#include <mutex>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -19,6 +22,7 @@ using namespace aiwc;
 namespace {
 
 thread_local std::string g_last_error;
+std::atomic<unsigned long long> g_epoch{0};
 constexpr size_t kStageBytes = 64ull << 20;
 constexpr size_t kPendingOps = 1ull << 24;
 constexpr size_t kPendingRuns = 1ull << 16;
@@ -84,6 +88,10 @@ struct aiwc_handle {
   bool last_plan_hash = false;
   u64 n_mem = 0, n_br = 0, n_runs = 0;
   u32 br_pushes = 0;    // branch ingest launches in this invocation (orders the sortedness check)
+  u64 epoch = 0;        // changes whenever a device buffer of the handle moves (keys cached graphs)
+  // sizes fixed by prepare() for the current compute
+  u64 c_over_cap = 0, c_sites_cap = 0;
+  size_t c_low_off = 0;
   u64 value_bound = 0;  // bound on ITB / IPT values >= kValDense (each uses kValDense instructions)
   // pending single-run pushes (host data, or device pointers)
   std::vector<uint16_t> pend_ops;
@@ -192,6 +200,7 @@ aiwc_status ensure(aiwc_handle* h, DevBuf& b, size_t bytes, bool preserve) {
   h->bytes = h->bytes - b.cap + want;
   b.p = p;
   b.cap = want;
+  h->epoch = ++g_epoch;
   return AIWC_OK;
 }
 
@@ -402,12 +411,12 @@ void release(aiwc_handle* h, DevBuf& b) {
   b.cap = 0;
 }
 
-aiwc_status reset_device_state(aiwc_handle* h) {
-  if (h->wi_bitmap) launch_wi_clear(h->wi_bitmap, h->arena, h->stream);
-  CK(cudaMemsetAsync(h->d_hist, 0, (size_t)h->cfg.n_opcodes * 8, h->stream));
-  CK(cudaMemsetAsync(h->arena, 0, sizeof(Arena), h->stream));
-  if (h->sbt.p && h->last_plan_hash) CK(cudaMemsetAsync(h->sbt.p, 0, 12 * h->sbt_cap, h->stream));
-  launch_reset_identities(h->arena, h->stream);
+aiwc_status reset_device_state(aiwc_handle* h, cudaStream_t st) {
+  if (h->wi_bitmap) launch_wi_clear(h->wi_bitmap, h->arena, st);
+  CK(cudaMemsetAsync(h->d_hist, 0, (size_t)h->cfg.n_opcodes * 8, st));
+  CK(cudaMemsetAsync(h->arena, 0, sizeof(Arena), st));
+  if (h->sbt.p) CK(cudaMemsetAsync(h->sbt.p, 0, 12 * h->sbt_cap, st));
+  launch_reset_identities(h->arena, st);
   CK(cudaGetLastError());
   return AIWC_OK;
 }
@@ -479,7 +488,9 @@ aiwc_status aiwc_create(const aiwc_config* cfg, aiwc_handle** out) {
       (e = cudaMallocHost(&h->h_state, sizeof(DevState))) != cudaSuccess)
     return bail(cuda_fail(nullptr, "allocation", e));
   h->bytes = sizeof(Arena) + sizeof(Result) + (size_t)cfg->n_opcodes * 8;
-  if (reset_device_state(h) != AIWC_OK) return bail(fail(nullptr, AIWC_ECUDA, h->err));
+  init_branch_attributes();
+  init_instr_attributes();
+  if (reset_device_state(h, h->stream) != AIWC_OK) return bail(fail(nullptr, AIWC_ECUDA, h->err));
   if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(cuda_fail(nullptr, "initial reset", e));
   *out = h;
   return AIWC_OK;
@@ -611,35 +622,124 @@ aiwc_status aiwc_push_instr_runs(aiwc_handle* h, const uint32_t* run_wi, const u
   return runs_host(h, run_wi, run_off, run_len, n_runs, ops, n_ops);
 }
 
-aiwc_status aiwc_compute(aiwc_handle* h, aiwc_metrics* out) {
-  if (!h || !out) return fail(h, AIWC_EINVAL, "null handle or output pointer", false);
-  DeviceGuard g(h->cfg.device);
-  uint64_t* user_hist = out->opcode_hist;
-  cudaStream_t st = h->stream;
-  auto reset_host = [&]() {
-    h->n_mem = h->n_br = h->n_runs = 0;
-    h->br_pushes = 0;
-    h->value_bound = 0;
-    h->pend_ops.clear();
-    h->pend_wi.clear();
-    h->pend_off.clear();
-    h->pend_len.clear();
-  };
-  if (h->broken) {
-    // drop the invocation and try to return to a clean state
-    reset_host();
-    cudaGetLastError();
-    if (reset_device_state(h) == AIWC_OK && cudaStreamSynchronize(st) == cudaSuccess) h->broken = false;
-    return AIWC_ESTATE;
+}  // extern "C"
+
+namespace {
+
+// One captured CUDA graph per device for aiwc_compute_batch: every handle's
+// stages on forked streams (parallel branches), replayed while the batch
+// signature (handles, sizes, plans, buffer epochs) repeats.
+struct BatchGraph {
+  std::mutex mu;
+  std::vector<u64> sig;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cs = nullptr;
+  std::vector<cudaStream_t> forks;
+  cudaEvent_t ev_user = nullptr, ev_fork = nullptr;
+  std::vector<cudaEvent_t> ev_join;
+
+  aiwc_status init() {
+    if (cs) return AIWC_OK;
+    constexpr int kForks = 16;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_user, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming);
+    for (int i = 0; i < kForks && e == cudaSuccess; ++i) {
+      cudaStream_t f;
+      cudaEvent_t j;
+      e = cudaStreamCreateWithFlags(&f, cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j, cudaEventDisableTiming);
+      if (e == cudaSuccess) {
+        forks.push_back(f);
+        ev_join.push_back(j);
+      }
+    }
+    if (e != cudaSuccess) return cuda_fail(nullptr, "batch graph streams", e);
+    return AIWC_OK;
   }
+
+  aiwc_status run(const std::vector<u64>& s, cudaStream_t user,
+                  const std::function<aiwc_status(cudaStream_t, std::vector<cudaStream_t>&)>& enqueue) {
+    std::lock_guard<std::mutex> lk(mu);
+    aiwc_status st = init();
+    if (st != AIWC_OK) return st;
+    cudaError_t e;
+    if (!exec || s != sig) {
+      if (exec) {
+        cudaGraphExecDestroy(exec);
+        exec = nullptr;
+      }
+      sig.clear();
+      if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
+        return cuda_fail(nullptr, "cudaStreamBeginCapture", e);
+      cudaEventRecord(ev_fork, cs);
+      for (cudaStream_t f : forks) cudaStreamWaitEvent(f, ev_fork, 0);
+      st = enqueue(cs, forks);
+      for (size_t k = 0; k < forks.size(); ++k) {
+        cudaEventRecord(ev_join[k], forks[k]);
+        cudaStreamWaitEvent(cs, ev_join[k], 0);
+      }
+      cudaGraph_t graph = nullptr;
+      e = cudaStreamEndCapture(cs, &graph);
+      if (st != AIWC_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+      }
+      if (e != cudaSuccess) return cuda_fail(nullptr, "cudaStreamEndCapture", e);
+      e = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) {
+        exec = nullptr;
+        return cuda_fail(nullptr, "cudaGraphInstantiate", e);
+      }
+      sig = s;
+    }
+    if ((e = cudaEventRecord(ev_user, user)) != cudaSuccess || (e = cudaStreamWaitEvent(cs, ev_user, 0)) != cudaSuccess ||
+        (e = cudaGraphLaunch(exec, cs)) != cudaSuccess || (e = cudaStreamSynchronize(cs)) != cudaSuccess)
+      return cuda_fail(nullptr, "batch graph launch", e);
+    return AIWC_OK;
+  }
+};
+
+BatchGraph& batch_graph(int device) {
+  static BatchGraph graphs[64];
+  return graphs[device & 63];
+}
+
+}  // namespace
+
+namespace {
+
+// What a compute launches. Host decisions come from the ingest-time device
+// counters; `gated` leaves the branch-path choice to a device flag so that a
+// captured graph holds both alternatives.
+struct Plan {
+  bool gated = false;
+  bool hash_ok = false;   // memory: hash plan (else the sort plan, rebuilding words if the table was used)
+  bool per_site = false;  // branch: per-site patterns (when !gated)
+  u32 br_passes = 0xFFu, run_passes = 0xFFu;
+};
+
+u32 active_passes(u64 kor, u64 kand, u64 mask) {
+  const u64 varying = (kor ^ kand) & mask;
+  u32 m = 0;
+  for (int p = 0; p < 8; ++p)
+    if ((varying >> (8 * p)) & 0xFFull) m |= 1u << p;
+  return m;
+}
+
+// Host part of a compute: pending runs, and every buffer the stages need.
+aiwc_status prepare(aiwc_handle* h) {
   aiwc_status s = flush_pending(h);
   if (s != AIWC_OK) return s;
   const u64 n_mem = h->n_mem, n_br = h->n_br, n_runs = h->n_runs;
   ENSURE(h->over_a, over_bound(h, n_mem, n_br, n_runs) * 8, true);
-  const u64 over_cap = h->over_a.cap / 8;
-  const u64 nmax = std::max(std::max(n_mem, n_br), std::max(n_runs, over_cap));
+  h->c_over_cap = h->over_a.cap / 8;
+  const u64 nmax = std::max(std::max(n_mem, n_br), std::max(n_runs, h->c_over_cap));
   ENSURE(h->mem_a, std::max<u64>(n_mem, 1) * 8, true);
   ENSURE(h->mem_b, std::max<u64>(n_mem, 1) * 8, true);  // holds the slot words of the hash plan
+  h->c_low_off = ((size_t)n_mem * 4 + 255) & ~size_t(255);
+  ENSURE(h->mem_b, h->c_low_off + (size_t)n_mem * 2, true);
   ENSURE(h->br_a, std::max<u64>(n_br, 1) * 8, true);
   ENSURE(h->br_b, std::max<u64>(n_br, 1) * 8, false);
   ENSURE(h->pat_a, std::max<u64>(n_br, 1) * 8, false);
@@ -647,86 +747,88 @@ aiwc_status aiwc_compute(aiwc_handle* h, aiwc_metrics* out) {
   ENSURE(h->rk_a, std::max<u64>(n_runs, 1) * 8, true);
   ENSURE(h->rk_b, std::max<u64>(n_runs, 1) * 8, false);
   ENSURE(h->run_sum, std::max<u64>(n_runs, 1) * 32, true);
-  ENSURE(h->over_b, over_cap * 8, false);
+  ENSURE(h->over_b, h->c_over_cap * 8, false);
   ENSURE(h->counts, sort_counts_words(nmax) * 4, false);
   ENSURE(h->bsums, sort_block_sums_words(nmax) * 4, false);
   ENSURE(h->tiles, std::max<u64>((u64)kLevels * ntiles_of(n_mem), ntiles_of(n_br) + 1) * sizeof(TileSum), false);
-  if ((s = ensure_bitmap(h)) != AIWC_OK) return s;
+  h->c_sites_cap = std::min<u64>(std::max<u64>(n_br, 1), kSiteListCap);
+  ENSURE(h->sites, h->c_sites_cap * 16, false);
+  return ensure_bitmap(h);
+}
+
+SortDesc sort_desc(aiwc_handle* h, DevBuf& a, DevBuf& b, int slot, const u64* n_dev, const u64* kor,
+                   const u64* kand, u64 mask, u64 n_host) {
+  SortDesc d;
+  d.a = (u64*)a.p;
+  d.b = (u64*)b.p;
+  d.cur = &h->arena->st.sort_cur[slot];
+  d.n = n_dev;
+  d.n_cap = std::min<u64>(a.cap, b.cap) / 8;
+  d.key_or = kor;
+  d.key_and = kand;
+  d.mask = mask;
+  d.lo_bit = 0;
+  d.counts = (u32*)h->counts.p;
+  d.block_sums = (u32*)h->bsums.p;
+  d.ntiles = (u32)ntiles_of(n_host);
+  return d;
+}
+
+SortDesc branch_sort_desc(aiwc_handle* h) {
+  DevState* dst = &h->arena->st;
+  SortDesc d = sort_desc(h, h->br_a, h->br_b, kSortBranch, &dst->n_branch, &dst->br_or, &dst->br_and, ~1ull, h->n_br);
+  d.dmask = &dst->br_sort_mask;
+  return d;
+}
+
+SiteArgs site_args(aiwc_handle* h, const SortDesc& bsort) {
+  SiteArgs sa;
+  sa.a = bsort.a;
+  sa.b = bsort.b;
+  sa.cur = bsort.cur;
+  sa.n = h->n_br;
+  sa.h = h->cfg.history_len;
+  sa.sites = (u64*)h->sites.p;
+  sa.sites_cap = h->c_sites_cap;
+  sa.over = (u64*)h->over_a.p;
+  sa.over_cap = h->c_over_cap;
+  sa.arena = h->arena;
+  sa.grid = h->sm_count;
+  return sa;
+}
+
+// Stages that must run before the branch-path choice: the branch sort and the site list.
+void enqueue_part1(aiwc_handle* h, cudaStream_t st, const Plan& p) {
+  if (!h->n_br) return;
+  SortDesc bsort = branch_sort_desc(h);
+  {
+    StageScope sc(h, kStBrSort);
+    launch_branch_mask(h->arena, st);
+    sort_keys(bsort, st, p.br_passes);
+  }
+  StageScope sc(h, kStWindows);
+  launch_site_heads(site_args(h, bsort), st);
+  if (p.gated) launch_persite_decide(h->arena, h->cfg.history_len, h->c_sites_cap, h->cfg.plan != 1, st);
+}
+
+// Everything after the branch-path choice, the result copies and the reset.
+aiwc_status enqueue_part2(aiwc_handle* h, cudaStream_t st, const Plan& p) {
+  const u64 n_mem = h->n_mem, n_br = h->n_br, n_runs = h->n_runs;
   DevState* dst = &h->arena->st;
   u64* over = (u64*)h->over_a.p;
+  const u64 over_cap = h->c_over_cap;
   const int grid = h->sm_count * 3;
-  auto sdesc = [&](DevBuf& a, DevBuf& b, int slot, const u64* n_dev, const u64* kor, const u64* kand, u64 mask,
-                   int lo, u64 n_host) {
-    SortDesc d;
-    d.a = (u64*)a.p;
-    d.b = (u64*)b.p;
-    d.cur = &dst->sort_cur[slot];
-    d.n = n_dev;
-    d.n_cap = std::min<u64>(a.cap, b.cap) / 8;
-    d.key_or = kor;
-    d.key_and = kand;
-    d.mask = mask;
-    d.dmask = nullptr;
-    d.lo_bit = lo;
-    d.counts = (u32*)h->counts.p;
-    d.block_sums = (u32*)h->bsums.p;
-    d.ntiles = (u32)ntiles_of(n_host);
-    return d;
-  };
-  // branches, first part: sort by site (and work-item unless they arrived in
-  // order), keeping program order; list the site segments
-  SortDesc bsort;
-  SiteArgs sa;
-  const u64 sites_cap = std::min<u64>(std::max<u64>(n_br, 1), kSiteListCap);
-  if (n_br) {
-    ENSURE(h->sites, sites_cap * 16, false);
-    bsort = sdesc(h->br_a, h->br_b, kSortBranch, &dst->n_branch, &dst->br_or, &dst->br_and, ~1ull, 0, n_br);
-    bsort.dmask = &dst->br_sort_mask;
-    {
-      StageScope sc(h, kStBrSort);
-      launch_branch_mask(h->arena, st);
-      sort_keys(bsort, st);
-    }
-    sa.a = bsort.a;
-    sa.b = bsort.b;
-    sa.cur = bsort.cur;
-    sa.n = n_br;
-    sa.h = h->cfg.history_len;
-    sa.sites = (u64*)h->sites.p;
-    sa.sites_cap = sites_cap;
-    sa.over = over;
-    sa.over_cap = over_cap;
-    sa.arena = h->arena;
-    sa.grid = h->sm_count;
-    StageScope sc(h, kStWindows);
-    launch_site_heads(sa, st);
-  }
-  // one host read of the device state decides the memory plan (hash unless
-  // the superblock table overflowed) and the branch path (per site unless a
-  // site is too long or the history too deep for the shared-memory bins)
-  bool hash_ok = false, per_site = false;
-  if ((n_mem && use_hash(h) && h->sbt_cap) || n_br) {
-    CK(cudaMemcpyAsync(h->h_state, dst, sizeof(DevState), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    hash_ok = n_mem && use_hash(h) && h->sbt_cap && h->h_state->sbt_overflow == 0;
-    if (n_mem && use_hash(h) && h->sbt_cap && !hash_ok) h->sbt_want = std::min<u64>(h->sbt_cap * 4, kMaxHashSlots);
-    per_site = n_br && h->cfg.history_len <= kSiteMaxHist && h->h_state->br_site_max <= kSiteMaxLen &&
-               h->h_state->n_sites <= sites_cap && h->cfg.plan != 1;
-  }
   const bool ran_hash = n_mem && use_hash(h) && h->sbt_cap;
-  h->last_plan_hash = ran_hash;
-  const size_t low_off = ((size_t)n_mem * 4 + 255) & ~size_t(255);
-  if (hash_ok) ENSURE(h->mem_b, low_off + (size_t)n_mem * 2, true);
-  if (ran_hash && !hash_ok) {
+  if (ran_hash && !p.hash_ok) {
     // the table overflowed: rebuild 64-bit words behind the spilled ones, then sort
     launch_rebuild_words((const u32*)h->mem_b.p, table_view(h), (u64*)h->mem_a.p, h->arena, grid * 2, st);
   }
-  if (hash_ok) {
+  if (n_mem && p.hash_ok) {
     StageScope sc(h, kStMemLevels);
     HashArgs ha;
     ha.slotw = (const u32*)h->mem_b.p;
-    ha.n_cap = std::min<u64>(n_mem, (h->mem_b.cap - low_off) / 2);
-    ha.low = (uint16_t*)((char*)h->mem_b.p + low_off);
+    ha.n_cap = std::min<u64>(n_mem, (h->mem_b.cap - h->c_low_off) / 2);
+    ha.low = (uint16_t*)((char*)h->mem_b.p + h->c_low_off);
     ha.tab = table_view(h);
     ha.scan_tmp = (u32*)h->sbt_scan.p;
     ha.n_used = &dst->sb_used;
@@ -738,10 +840,10 @@ aiwc_status aiwc_compute(aiwc_handle* h, aiwc_metrics* out) {
     ha.grid_segments = h->sm_count * 6;
     launch_mem_hash(ha, st);
   } else if (n_mem) {
-    SortDesc d = sdesc(h->mem_a, h->mem_b, kSortMem, &dst->n_words, &dst->mem_or, &dst->mem_and, ~0ull, 0, n_mem);
+    SortDesc d = sort_desc(h, h->mem_a, h->mem_b, kSortMem, &dst->n_words, &dst->mem_or, &dst->mem_and, ~0ull, n_mem);
     {
       StageScope sc(h, kStMemSort);
-      sort_keys(d, st);
+      sort_keys(d, st, active_passes(h->h_state->mem_or, h->h_state->mem_and, ~0ull));
     }
     StageScope sc(h, kStMemLevels);
     LevelArgs la;
@@ -758,56 +860,70 @@ aiwc_status aiwc_compute(aiwc_handle* h, aiwc_metrics* out) {
     launch_mem_levels(la, st);
     launch_runs_fixup(0, la.tiles, la.ntiles, &dst->n_words, 0, kLevels, over, over_cap, h->arena, st);
   }
-  // branches, second part: patterns per site in shared memory, or the
-  // global path (windows, pattern sort, pattern runs)
-  if (n_br && per_site) {
-    StageScope sc(h, kStPatRuns);
-    launch_site_patterns(sa, st);
-  } else if (n_br) {
-    const SortDesc& d = bsort;
-    WindowArgs wa;
-    wa.a = d.a;
-    wa.b = d.b;
-    wa.cur = d.cur;
-    wa.n = n_br;
-    wa.h = h->cfg.history_len;
-    wa.patterns = (u64*)h->pat_a.p;
-    wa.tiles = (TileSum*)h->tiles.p;
-    wa.ntiles = d.ntiles;
-    wa.over = over;
-    wa.over_cap = over_cap;
-    wa.arena = h->arena;
-    wa.grid = grid;
-    {
-      StageScope sc(h, kStWindows);
-      launch_branch_windows(wa, st);
-      launch_runs_fixup(1, wa.tiles, wa.ntiles, nullptr, n_br, 1, over, over_cap, h->arena, st);
+  if (n_br) {
+    // per-site patterns in shared memory, or the global path (windows,
+    // pattern sort, pattern runs); with `gated` both are launched and a
+    // device flag lets exactly one of them work
+    const u32* gate = p.gated ? &dst->br_persite : nullptr;
+    SortDesc bsort = branch_sort_desc(h);
+    if (p.gated || p.per_site) {
+      StageScope sc(h, kStPatRuns);
+      SiteArgs sa = site_args(h, bsort);
+      sa.gate = gate;
+      sa.gate_want = 1;
+      launch_site_patterns(sa, st);
     }
-    SortDesc p = sdesc(h->pat_a, h->pat_b, kSortPattern, &dst->n_patterns, &dst->pat_or, &dst->pat_and, ~0ull, 0,
-                       n_br);
-    {
-      StageScope sc(h, kStPatSort);
-      sort_keys(p, st);
+    if (p.gated || !p.per_site) {
+      WindowArgs wa;
+      wa.gate = gate;
+      wa.gate_want = 0;
+      wa.a = bsort.a;
+      wa.b = bsort.b;
+      wa.cur = bsort.cur;
+      wa.n = n_br;
+      wa.h = h->cfg.history_len;
+      wa.patterns = (u64*)h->pat_a.p;
+      wa.tiles = (TileSum*)h->tiles.p;
+      wa.ntiles = bsort.ntiles;
+      wa.over = over;
+      wa.over_cap = over_cap;
+      wa.arena = h->arena;
+      wa.grid = grid;
+      {
+        StageScope sc(h, kStWindows);
+        launch_branch_windows(wa, st);
+        launch_runs_fixup(1, wa.tiles, wa.ntiles, nullptr, n_br, 1, over, over_cap, h->arena, st, gate, 0);
+      }
+      SortDesc ps = sort_desc(h, h->pat_a, h->pat_b, kSortPattern, &dst->n_patterns, &dst->pat_or, &dst->pat_and,
+                              ~0ull, n_br);
+      ps.gate = gate;
+      ps.gate_want = 0;
+      {
+        StageScope sc(h, kStPatSort);
+        sort_keys(ps, st);
+      }
+      StageScope sc(h, kStPatRuns);
+      PatternArgs pa;
+      pa.gate = gate;
+      pa.gate_want = 0;
+      pa.a = ps.a;
+      pa.b = ps.b;
+      pa.cur = ps.cur;
+      pa.n = &dst->n_patterns;
+      pa.tiles = (TileSum*)h->tiles.p;
+      pa.ntiles = ps.ntiles;
+      pa.arena = h->arena;
+      pa.grid = grid;
+      launch_pattern_runs(pa, st);
+      launch_runs_fixup(2, pa.tiles, pa.ntiles, &dst->n_patterns, 0, 1, over, over_cap, h->arena, st, gate, 0);
     }
-    StageScope sc(h, kStPatRuns);
-    PatternArgs pa;
-    pa.a = p.a;
-    pa.b = p.b;
-    pa.cur = p.cur;
-    pa.n = &dst->n_patterns;
-    pa.tiles = (TileSum*)h->tiles.p;
-    pa.ntiles = p.ntiles;
-    pa.arena = h->arena;
-    pa.grid = grid;
-    launch_pattern_runs(pa, st);
-    launch_runs_fixup(2, pa.tiles, pa.ntiles, &dst->n_patterns, 0, 1, over, over_cap, h->arena, st);
   }
   // instructions: chain each work-item's runs
   if (n_runs) {
-    SortDesc d = sdesc(h->rk_a, h->rk_b, kSortRuns, &dst->n_runs, &dst->run_or, &dst->run_and, ~0ull, 0, n_runs);
+    SortDesc d = sort_desc(h, h->rk_a, h->rk_b, kSortRuns, &dst->n_runs, &dst->run_or, &dst->run_and, ~0ull, n_runs);
     {
       StageScope sc(h, kStRunSort);
-      sort_keys(d, st);
+      sort_keys(d, st, p.run_passes);
     }
     StageScope sc(h, kStCombine);
     CombineArgs ca;
@@ -821,12 +937,12 @@ aiwc_status aiwc_compute(aiwc_handle* h, aiwc_metrics* out) {
     ca.arena = h->arena;
     launch_instr_combine(ca, st);
   }
-  StageScope fin_scope(h, kStFinalize);
-  launch_opcode_dist((const u64*)h->d_hist, h->cfg.n_opcodes, over, over_cap, h->arena, st);
-  launch_wi_count(h->wi_bitmap, h->arena, st);
   {
-    SortDesc d = sdesc(h->over_a, h->over_b, kSortOver, &dst->n_over, &dst->over_or, &dst->over_and, ~0ull, 0,
-                       over_cap);
+    StageScope fin_scope(h, kStFinalize);
+    launch_opcode_dist((const u64*)h->d_hist, h->cfg.n_opcodes, over, over_cap, h->arena, st);
+    launch_wi_count(h->wi_bitmap, h->arena, st);
+    SortDesc d = sort_desc(h, h->over_a, h->over_b, kSortOver, &dst->n_over, &dst->over_or, &dst->over_and, ~0ull,
+                           over_cap);
     sort_keys(d, st);
     FinalizeArgs fa;
     fa.over_a = d.a;
@@ -840,15 +956,26 @@ aiwc_status aiwc_compute(aiwc_handle* h, aiwc_metrics* out) {
     fa.precision = h->cfg.precision;
     launch_finalize(fa, st);
   }
-  fin_scope.end();
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(h->h_result, h->d_result, sizeof(Result), cudaMemcpyDeviceToHost, st));
-  if (user_hist)
-    CK(cudaMemcpyAsync(h->h_hist, h->d_hist, (size_t)h->cfg.n_opcodes * 8, cudaMemcpyDeviceToHost, st));
-  if ((s = reset_device_state(h)) != AIWC_OK) return s;
-  CK(cudaStreamSynchronize(st));
-  collect_stage_times(h);
-  reset_host();
+  CK(cudaMemcpyAsync(h->h_hist, h->d_hist, (size_t)h->cfg.n_opcodes * 8, cudaMemcpyDeviceToHost, st));
+  return reset_device_state(h, st);
+}
+
+void reset_host(aiwc_handle* h) {
+  h->n_mem = h->n_br = h->n_runs = 0;
+  h->br_pushes = 0;
+  h->value_bound = 0;
+  h->pend_ops.clear();
+  h->pend_wi.clear();
+  h->pend_off.clear();
+  h->pend_len.clear();
+}
+
+// After the stream has been synchronised: results out, host state reset.
+aiwc_status finish(aiwc_handle* h, aiwc_metrics* out, uint64_t* user_hist) {
+  h->last_plan_hash = h->n_mem && use_hash(h) && h->sbt_cap;
+  reset_host(h);
   *out = h->h_result->m;
   out->opcode_hist = user_hist;
   if (user_hist) memcpy(user_hist, h->h_hist, (size_t)h->cfg.n_opcodes * 8);
@@ -861,12 +988,125 @@ aiwc_status aiwc_compute(aiwc_handle* h, aiwc_metrics* out) {
   return AIWC_OK;
 }
 
+// Recovers a broken handle: drops the invocation.
+aiwc_status recover(aiwc_handle* h) {
+  reset_host(h);
+  cudaGetLastError();
+  if (reset_device_state(h, h->stream) == AIWC_OK && cudaStreamSynchronize(h->stream) == cudaSuccess) h->broken = false;
+  return AIWC_ESTATE;
+}
+
+// Host decisions from the ingest-time counters (h->h_state must be current).
+void plan_from_ingest(aiwc_handle* h, Plan* p) {
+  const DevState& hs = *h->h_state;
+  const bool hashed = h->n_mem && use_hash(h) && h->sbt_cap;
+  p->hash_ok = hashed && hs.sbt_overflow == 0;
+  if (hashed && !p->hash_ok) h->sbt_want = std::min<u64>(h->sbt_cap * 4, kMaxHashSlots);
+  p->br_passes = active_passes(hs.br_or, hs.br_and, hs.br_unsorted ? ~1ull : 0xFFFFFFFF00000000ull);
+  p->run_passes = active_passes(hs.run_or, hs.run_and, ~0ull);
+}
+
+}  // namespace
+
+extern "C" {
+
+aiwc_status aiwc_compute(aiwc_handle* h, aiwc_metrics* out) {
+  if (!h || !out) return fail(h, AIWC_EINVAL, "null handle or output pointer", false);
+  DeviceGuard g(h->cfg.device);
+  uint64_t* user_hist = out->opcode_hist;
+  cudaStream_t st = h->stream;
+  if (h->broken) return recover(h);
+  aiwc_status s = prepare(h);
+  if (s != AIWC_OK) return s;
+  // read the ingest-time counters: memory plan, active sort passes
+  CK(cudaMemcpyAsync(h->h_state, &h->arena->st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  Plan p;
+  plan_from_ingest(h, &p);
+  enqueue_part1(h, st, p);
+  if (h->n_br) {
+    // the branch path depends on the longest site
+    CK(cudaMemcpyAsync(h->h_state, &h->arena->st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const DevState& hs = *h->h_state;
+    p.per_site = h->cfg.history_len <= kSiteMaxHist && hs.br_site_max <= kSiteMaxLen &&
+                 hs.n_sites <= h->c_sites_cap && h->cfg.plan != 1;
+  }
+  if ((s = enqueue_part2(h, st, p)) != AIWC_OK) return s;
+  CK(cudaStreamSynchronize(st));
+  collect_stage_times(h);
+  return finish(h, out, user_hist);
+}
+
 aiwc_status aiwc_compute_batch(aiwc_handle* const* hs, size_t n, aiwc_metrics* outs) {
   if (n && (!hs || !outs)) return fail(nullptr, AIWC_EINVAL, "null batch arrays");
-  aiwc_status worst = AIWC_OK;
+  if (n == 0) return AIWC_OK;
   for (size_t i = 0; i < n; ++i) {
-    aiwc_status s = aiwc_compute(hs[i], &outs[i]);
-    if (s != AIWC_OK && worst == AIWC_OK) worst = s;
+    if (!hs[i]) return fail(nullptr, AIWC_EINVAL, "null handle in batch");
+    if (hs[i]->cfg.device != hs[0]->cfg.device || hs[i]->stream != hs[0]->stream)
+      return fail(nullptr, AIWC_EINVAL, "batched handles must share one device and one stream");
+    for (size_t j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return fail(nullptr, AIWC_EINVAL, "a handle appears twice in the batch");
+  }
+  DeviceGuard g(hs[0]->cfg.device);
+  cudaStream_t user = hs[0]->stream;
+  std::vector<uint64_t*> hists(n);
+  aiwc_status worst = AIWC_OK;
+  std::vector<char> live(n, 1);
+  for (size_t i = 0; i < n; ++i) {
+    hists[i] = outs[i].opcode_hist;
+    aiwc_handle* h = hs[i];
+    aiwc_status s = h->broken ? recover(h) : prepare(h);
+    if (s != AIWC_OK) {
+      live[i] = 0;
+      memset(&outs[i], 0, sizeof(aiwc_metrics));
+      outs[i].opcode_hist = hists[i];
+      if (worst == AIWC_OK) worst = s;
+    }
+  }
+  // one synchronisation for every handle's ingest-time counters
+  for (size_t i = 0; i < n; ++i)
+    if (live[i])
+      if (cudaMemcpyAsync(hs[i]->h_state, &hs[i]->arena->st, sizeof(DevState), cudaMemcpyDeviceToHost, user) !=
+          cudaSuccess)
+        return cuda_fail(nullptr, "batch state copy", cudaGetLastError());
+  if (cudaStreamSynchronize(user) != cudaSuccess) return cuda_fail(nullptr, "batch sync", cudaGetLastError());
+  std::vector<Plan> plans(n);
+  BatchGraph& bg = batch_graph(hs[0]->cfg.device);
+  std::vector<u64> sig;
+  for (size_t i = 0; i < n; ++i) {
+    if (!live[i]) continue;
+    plans[i].gated = true;
+    plan_from_ingest(hs[i], &plans[i]);
+    const aiwc_handle* h = hs[i];
+    sig.insert(sig.end(), {(u64)(uintptr_t)h, h->n_mem, h->n_br, h->n_runs, h->epoch, (u64)plans[i].hash_ok,
+                           plans[i].br_passes, plans[i].run_passes, h->sbt_cap,
+                           active_passes(h->h_state->mem_or, h->h_state->mem_and, ~0ull)});
+  }
+  aiwc_status s = bg.run(sig, user, [&](cudaStream_t base, std::vector<cudaStream_t>& forks) -> aiwc_status {
+    size_t k = 0;
+    for (size_t i = 0; i < n; ++i) {
+      if (!live[i]) continue;
+      aiwc_handle* h = hs[i];
+      cudaStream_t st = forks[k++ % forks.size()];
+      const bool timing = h->timing;
+      h->timing = false;  // stage events are not part of the graph
+      enqueue_part1(h, st, plans[i]);
+      aiwc_status e = enqueue_part2(h, st, plans[i]);
+      h->timing = timing;
+      if (e != AIWC_OK) return e;
+    }
+    (void)base;
+    return AIWC_OK;
+  });
+  if (s != AIWC_OK) {
+    for (size_t i = 0; i < n; ++i) hs[i]->broken = true;
+    return s;
+  }
+  for (size_t i = 0; i < n; ++i) {
+    if (!live[i]) continue;
+    aiwc_status e = finish(hs[i], &outs[i], hists[i]);
+    if (e != AIWC_OK && worst == AIWC_OK) worst = e;
   }
   return worst;
 }

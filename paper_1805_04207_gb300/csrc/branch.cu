@@ -88,6 +88,11 @@ __global__ void k_branch_mask(Arena* arena) {
   st->br_sort_mask = st->br_unsorted ? ~1ull : 0xFFFFFFFF00000000ull;
 }
 
+__global__ void k_persite_decide(Arena* arena, u32 h, u64 sites_cap, int allow) {
+  DevState* st = &arena->st;
+  st->br_persite = (allow && h <= kSiteMaxHist && st->br_site_max <= kSiteMaxLen && st->n_sites <= sites_cap) ? 1u : 0u;
+}
+
 // Lists each site's segment of the sorted branch words: (start, length).
 __global__ void __launch_bounds__(256) k_site_heads(SiteArgs a) {
   DevState* st = &a.arena->st;
@@ -124,6 +129,7 @@ constexpr int kSpBitWords = (int)((kSiteMaxLen + 32) / 32) + 2;
 // bins. Any fixed bijection of the h-bit window names the pattern equally
 // well; here bit k of the pattern is the outcome k+1 places after the oldest.
 __global__ void __launch_bounds__(kSpThreads) k_site_patterns(SiteArgs a) {
+  if (!gate_open(a.gate, a.gate_want)) return;
   extern __shared__ u32 spm[];
   u32* bits = spm;
   u32* cnt = spm + kSpBitWords;
@@ -189,6 +195,7 @@ constexpr int kHalo = 32;  // history lengths are at most 31
 // writes the compacted pattern words of outcomes with a full history, and
 // runs the per-site run lengths (site event counts) for the site metrics.
 __global__ void __launch_bounds__(kTileThreads) k_windows(WindowArgs a) {
+  if (!gate_open(a.gate, a.gate_want)) return;
   __shared__ u64 tw[kHalo + kTile];
   __shared__ u32 site_coc[kCocDense];
   __shared__ Seg sh[33];
@@ -298,6 +305,7 @@ __global__ void __launch_bounds__(kTileThreads) k_windows(WindowArgs a) {
 }
 
 __global__ void __launch_bounds__(kTileThreads) k_pattern_runs(PatternArgs a) {
+  if (!gate_open(a.gate, a.gate_want)) return;
   __shared__ Seg sh[33];
   __shared__ u64 pre_slot[2];
   __shared__ u64 red64[32];
@@ -336,7 +344,8 @@ __global__ void __launch_bounds__(kTileThreads) k_pattern_runs(PatternArgs a) {
 // boundary (and the final run), exactly once.
 template <int KIND>
 __global__ void __launch_bounds__(1024) k_fixup(const TileSum* tiles, u32 ntiles_max, const u64* n_dev, u64 n_host,
-                                                u64* over, u64 over_cap, Arena* arena) {
+                                                u64* over, u64 over_cap, Arena* arena, const u32* gate, u32 want) {
+  if (!gate_open(gate, want)) return;
   __shared__ Seg sh[33];
   __shared__ u64 red64[32];
   DevState* st = &arena->st;
@@ -409,10 +418,19 @@ void launch_site_heads(const SiteArgs& a, cudaStream_t s) {
   count_launches(1);
 }
 
+void launch_persite_decide(Arena* arena, u32 h, u64 sites_cap, int allow, cudaStream_t s) {
+  k_persite_decide<<<1, 1, 0, s>>>(arena, h, sites_cap, allow);
+  count_launches(1);
+}
+
+static size_t site_patterns_smem() { return (size_t)(kSpBitWords + (1 << kSpBinsLog)) * 4; }
+
+void init_branch_attributes() {
+  cudaFuncSetAttribute(k_site_patterns, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)site_patterns_smem());
+}
+
 void launch_site_patterns(const SiteArgs& a, cudaStream_t s) {
-  const size_t smem = (size_t)(kSpBitWords + (1 << kSpBinsLog)) * 4;
-  cudaFuncSetAttribute(k_site_patterns, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  k_site_patterns<<<a.grid, kSpThreads, smem, s>>>(a);
+  k_site_patterns<<<a.grid, kSpThreads, site_patterns_smem(), s>>>(a);
   count_launches(1);
 }
 
@@ -431,14 +449,14 @@ void launch_pattern_runs(const PatternArgs& a, cudaStream_t s) {
 }
 
 void launch_runs_fixup(int kind, const TileSum* tiles, u32 ntiles_max, const u64* n_dev, u64 n_host, int levels,
-                       u64* over, u64 over_cap, Arena* arena, cudaStream_t s) {
+                       u64* over, u64 over_cap, Arena* arena, cudaStream_t s, const u32* gate, u32 gate_want) {
   if (ntiles_max == 0) return;
   if (kind == 0)
-    k_fixup<0><<<levels, 1024, 0, s>>>(tiles, ntiles_max, n_dev, n_host, over, over_cap, arena);
+    k_fixup<0><<<levels, 1024, 0, s>>>(tiles, ntiles_max, n_dev, n_host, over, over_cap, arena, gate, gate_want);
   else if (kind == 1)
-    k_fixup<1><<<levels, 1024, 0, s>>>(tiles, ntiles_max, n_dev, n_host, over, over_cap, arena);
+    k_fixup<1><<<levels, 1024, 0, s>>>(tiles, ntiles_max, n_dev, n_host, over, over_cap, arena, gate, gate_want);
   else
-    k_fixup<2><<<levels, 1024, 0, s>>>(tiles, ntiles_max, n_dev, n_host, over, over_cap, arena);
+    k_fixup<2><<<levels, 1024, 0, s>>>(tiles, ntiles_max, n_dev, n_host, over, over_cap, arena, gate, gate_want);
   count_launches(1);
 }
 

@@ -69,6 +69,8 @@ __device__ __forceinline__ void overflow_append(u64* over, u64 cap, DevState* st
 
 __device__ __forceinline__ u64 umin64(u64 a, u64 b) { return a < b ? a : b; }
 
+__device__ __forceinline__ bool gate_open(const u32* gate, u32 want) { return !gate || *gate == want; }
+
 // Home slot of a superblock key: fold to 32 bits, multiply by a 32-bit odd
 // constant (Knuth's multiplicative hashing) and keep the high bits through
 // the caller's mask after a final mix of the high half into the low half.

@@ -250,15 +250,14 @@ void launch_instr_runs(const RunBatchArgs& a, cudaStream_t s) {
   if (bins * kInWarps * 4 <= 48 * 1024) { mode = 0; smem = bins * kInWarps * 4; }
   else if (bins * 4 <= 96 * 1024) { mode = 1; smem = bins * 4; }
   else { mode = 2; smem = 0; }
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_instr_runs, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
-    attr_set = true;
-  }
   u64 blocks = (a.n_runs + kInWarps - 1) / kInWarps;
   if (blocks > 152ull * 4) blocks = 152ull * 4;
   k_instr_runs<<<(unsigned)blocks, kInThreads, smem, s>>>(a, mode);
   count_launches(1);
+}
+
+void init_instr_attributes() {
+  cudaFuncSetAttribute(k_instr_runs, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
 }
 
 void launch_instr_combine(const CombineArgs& a, cudaStream_t s) {

@@ -165,6 +165,7 @@ constexpr int kLvThreads = kTileThreads;
 constexpr int kLvItems = kTileItems;
 
 __global__ void __launch_bounds__(kLvThreads) k_mem_levels(LevelArgs a) {
+  if (!gate_open(a.gate, a.gate_want)) return;
   __shared__ u32 coc[kLevels][kCocDense];
   __shared__ Seg sh[33];
   __shared__ u64 pre_slot[2];

@@ -22,7 +22,9 @@ constexpr int kScanT = 1024;
 constexpr int kScanI = 4;
 constexpr int kScanB = kScanT * kScanI;
 
-__global__ void __launch_bounds__(kScanT) k_sbt_reduce(const u32* cnt, u64 len, u32* bsum) {
+__global__ void __launch_bounds__(kScanT) k_sbt_reduce(const u32* cnt, u64 len, u32* bsum, const u32* gate,
+                                                      u32 want) {
+  if (!gate_open(gate, want)) return;
   __shared__ u32 red[32];
   const u64 base = (u64)blockIdx.x * kScanB + (u64)threadIdx.x * kScanI;
   u32 s = 0;
@@ -60,7 +62,8 @@ __device__ __forceinline__ u32 block_excl_u32(u32 x, u32* total, u32* wt) {
   return r;
 }
 
-__global__ void __launch_bounds__(kScanT) k_sbt_top(u32* bsum, u32 nb) {
+__global__ void __launch_bounds__(kScanT) k_sbt_top(u32* bsum, u32 nb, const u32* gate, u32 want) {
+  if (!gate_open(gate, want)) return;
   __shared__ u32 wt[33];
   u32 carry = 0;
   for (u32 c0 = 0; c0 < nb; c0 += kScanB) {
@@ -86,7 +89,8 @@ __global__ void __launch_bounds__(kScanT) k_sbt_top(u32* bsum, u32 nb) {
 // Offsets (exclusive) into off[] and cur[]; the occupied slots are appended
 // to `used_list` (in no particular order) and counted in *n_used.
 __global__ void __launch_bounds__(kScanT) k_sbt_down(const u32* cnt, u64 len, const u32* bsum, u32* off, u32* cur,
-                                                    u64* n_used, u32* used_list) {
+                                                    u64* n_used, u32* used_list, const u32* gate, u32 want) {
+  if (!gate_open(gate, want)) return;
   __shared__ u32 wt[33];
   __shared__ u32 wt2[33];
   __shared__ u64 s_base;
@@ -123,6 +127,7 @@ constexpr int kScItems = 8;
 
 // Scatter each event's low 12 bits into its superblock's segment.
 __global__ void __launch_bounds__(kScThreads) k_mem_scatter(HashArgs a) {
+  if (!gate_open(a.gate, a.gate_want)) return;
   const u64 n = umin64(a.arena->st.n_words, a.n_cap);
   const int lane = threadIdx.x & 31;
   const u32 lt = (1u << lane) - 1u;
@@ -156,7 +161,8 @@ constexpr int kRbItems = 8;
 // Sort-plan fallback: 64-bit words rebuilt from slot words and table keys,
 // appended after the spilled words (order is irrelevant to the sort).
 __global__ void __launch_bounds__(kRbThreads) k_rebuild_words(const u32* slotw, SbTable tab, u64* words,
-                                                             Arena* arena) {
+                                                             Arena* arena, const u32* gate, u32 want) {
+  if (!gate_open(gate, want)) return;
   __shared__ u32 scan_tot[33];
   __shared__ u64 s_base;
   DevState* st = &arena->st;
@@ -237,6 +243,7 @@ __device__ __forceinline__ void emit_level(u32 (*coc)[kCocSmem], int lev, const 
 
 // One block per superblock segment at a time (grid-stride over the occupied slots).
 __global__ void __launch_bounds__(kSgThreads) k_mem_segments(HashArgs a) {
+  if (!gate_open(a.gate, a.gate_want)) return;
   __shared__ __align__(16) u32 hist[4096];
   __shared__ u32 coc[kLevels][kCocSmem];
   __shared__ u32 wsum[kSgThreads / 32];
@@ -322,16 +329,18 @@ size_t sbt_scan_words(u64 cap) { return (size_t)((cap + kScanB - 1) / kScanB + 1
 void launch_mem_hash(const HashArgs& a, cudaStream_t s) {
   const u64 C = a.tab.mask + 1;
   const u32 nb = (u32)((C + kScanB - 1) / kScanB);
-  k_sbt_reduce<<<nb, kScanT, 0, s>>>(a.tab.cnt, C, a.scan_tmp);
-  k_sbt_top<<<1, kScanT, 0, s>>>(a.scan_tmp, nb);
-  k_sbt_down<<<nb, kScanT, 0, s>>>(a.tab.cnt, C, a.scan_tmp, a.tab.off, a.tab.cur, a.n_used, a.used_list);
+  k_sbt_reduce<<<nb, kScanT, 0, s>>>(a.tab.cnt, C, a.scan_tmp, a.gate, a.gate_want);
+  k_sbt_top<<<1, kScanT, 0, s>>>(a.scan_tmp, nb, a.gate, a.gate_want);
+  k_sbt_down<<<nb, kScanT, 0, s>>>(a.tab.cnt, C, a.scan_tmp, a.tab.off, a.tab.cur, a.n_used, a.used_list, a.gate,
+                                   a.gate_want);
   k_mem_scatter<<<a.grid_scatter, kScThreads, 0, s>>>(a);
   k_mem_segments<<<a.grid_segments, kSgThreads, 0, s>>>(a);
   count_launches(5);
 }
 
-void launch_rebuild_words(const u32* slotw, SbTable tab, u64* words, Arena* arena, int grid, cudaStream_t s) {
-  k_rebuild_words<<<grid, kRbThreads, 0, s>>>(slotw, tab, words, arena);
+void launch_rebuild_words(const u32* slotw, SbTable tab, u64* words, Arena* arena, int grid, cudaStream_t s,
+                          const u32* gate, u32 gate_want) {
+  k_rebuild_words<<<grid, kRbThreads, 0, s>>>(slotw, tab, words, arena, gate, gate_want);
   count_launches(1);
 }
 

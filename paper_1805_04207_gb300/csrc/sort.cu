@@ -31,7 +31,7 @@ __device__ __forceinline__ u64 eff_mask(const SortDesc& d) { return d.dmask ? (d
 __device__ __forceinline__ bool pass_shift(const SortDesc& d, int pass, int* shift) {
   int sh = d.lo_bit + 8 * pass;
   *shift = sh;
-  if (sh >= 64) return false;
+  if (sh >= 64 || !gate_open(d.gate, d.gate_want)) return false;
   u64 varying = ((*d.key_or) ^ (*d.key_and)) & eff_mask(d);
   return ((varying >> sh) & 0xFFull) != 0;
 }
@@ -236,12 +236,15 @@ size_t sort_block_sums_words(u64 n_max) {
   return (size_t)((len + kScanBlock - 1) / kScanBlock + 1);
 }
 
-void sort_keys(const SortDesc& d, cudaStream_t s) {
+void sort_keys(const SortDesc& d, cudaStream_t s, u32 host_passes) {
   if (d.ntiles == 0) return;
   const u64 len = 256ull * d.ntiles;
   const u32 nb = (u32)((len + kScanBlock - 1) / kScanBlock);
   const int passes = (64 - d.lo_bit + 7) / 8;
+  int launched = 0;
   for (int p = 0; p < passes; ++p) {
+    if (!((host_passes >> p) & 1u)) continue;
+    ++launched;
     k_hist<<<d.ntiles, kTileThreads, 0, s>>>(d, p);
     k_scan_reduce<<<nb, kScanThreads, 0, s>>>(d, p, len);
     k_scan_top<<<1, kScanThreads, 0, s>>>(d, p, nb);
@@ -249,7 +252,7 @@ void sort_keys(const SortDesc& d, cudaStream_t s) {
     k_scatter<<<d.ntiles, kTileThreads, 0, s>>>(d, p);
     k_flip<<<1, 1, 0, s>>>(d, p);
   }
-  count_launches(6ull * passes);
+  count_launches(6ull * launched);
 }
 
 }  // namespace aiwc

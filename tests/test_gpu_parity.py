@@ -249,3 +249,29 @@ def test_branch_order_detection_across_pushes(P, h):
     assert_parity(run_gpu(P, swapped, split=2, history_len=h), oracle.compute(swapped, history_len=h), hist=False)
     assert_parity(run_gpu(P, swapped, split=2, history_len=h, on_device=False),
                   oracle.compute(swapped, history_len=h), hist=False)
+
+
+def test_batch_matches_oracle_and_replays(P):
+    """Invocations of uneven size, pattern and plan reduced in one batched
+    graph give exactly what the oracle gives; the second call with the same
+    shapes replays the cached graph."""
+    from paper_1805_04207_gb300.api import compute_batch, push_trace
+    traces = [synth.pattern_trace(k, c, f, seed=7, stream=i) for i, (k, c, f) in enumerate([
+        ("stream", 5000, 300), ("stencil", 70_001, 9000), ("gemm", 40_000, 4096), ("zipf", 120_000, 50_000),
+        ("uniform", 33_333, 33_333), ("zipf", 4096, 256)])]
+    traces.append(synth.tiny())
+    traces.append(synth.large(seed=8, n_mem=90_000, n_br=120_000, n_wi=40, per_wi=300, zipf_distinct=1 << 14))
+    cfgs = [dict(), dict(plan=1), dict(table_slots=64), dict(history_len=31), dict(), dict(history_len=2),
+            dict(), dict(plan=1, history_len=20)]
+    expect = [oracle.compute(t, history_len=c.get("history_len", 16)) for t, c in zip(traces, cfgs)]
+    chars = [P.Characterizer(n_opcodes=t.n_opcodes, max_work_items=1 << 24, **c) for t, c in zip(traces, cfgs)]
+    try:
+        for _ in range(3):
+            for c, t in zip(chars, traces):
+                push_trace(c, t.to("cuda"))
+            got = compute_batch(chars)
+            for g, o in zip(got, expect):
+                assert_parity(g, o)
+    finally:
+        for c in chars:
+            c.close()

@@ -215,6 +215,64 @@ uint64_t aiwc_kernel_launches(void);
 aiwc_status aiwc_set_stage_timing(aiwc_handle* h, int on);
 int aiwc_stage_times(const aiwc_handle* h, double* ms, const char** names, int n);
 
+/* --------------------------------------------------------------- serving */
+
+/* Many characterization jobs at once, each streaming its trace in chunks
+ * (the low-memory streaming the paper leaves to future work, Sec. VII, and
+ * the failures on large traces it reports, Sec. VI). A server owns
+ * `max_jobs` slots; each slot is a handle with its own CUDA stream, so the
+ * chunks of one job are ingested while other jobs are reduced. A job is
+ * admitted only when a slot is free and its reservation fits `hbm_budget`
+ * next to what running jobs reserve (device memory of idle slots is released
+ * first); otherwise aiwc_job_open returns AIWC_EAGAIN and the caller retries.
+ * A job's results equal those of aiwc_compute on the same events. */
+typedef struct aiwc_server_config {
+  int device;
+  uint32_t max_jobs;     /* slots: jobs in flight at once (1..4096) */
+  uint32_t workers;      /* host threads running reductions (1..64) */
+  uint64_t hbm_budget;   /* bytes of device scratch all jobs together may hold */
+} aiwc_server_config;
+
+typedef struct aiwc_server aiwc_server;
+typedef struct aiwc_job aiwc_job;
+
+/* Defaults: device 0, 32 slots, 4 workers, 120 GiB. */
+void aiwc_server_config_default(aiwc_server_config* cfg);
+aiwc_status aiwc_server_create(const aiwc_server_config* cfg, aiwc_server** out);
+
+/* Opens a job with the metric configuration job_cfg (its device, stream and
+ * hbm_budget are replaced by the slot's) and a scratch reservation of
+ * reserve_bytes, which bounds what the job may allocate (pushes beyond it fail
+ * with AIWC_ENOMEM; the work-item bitmap is max_work_items / 8 bytes of it).
+ * AIWC_EAGAIN: no slot or not enough budget now. AIWC_ENOMEM: the
+ * reservation exceeds the whole budget. */
+aiwc_status aiwc_job_open(aiwc_server* s, const aiwc_config* job_cfg, uint64_t reserve_bytes, aiwc_job** out);
+
+/* Chunk pushes, with the semantics of aiwc_push_mem / _branch / _instr_runs.
+ * A job is used by one thread at a time. */
+aiwc_status aiwc_job_push_mem(aiwc_job* j, const aiwc_mem_event* ev, size_t n, int on_device);
+aiwc_status aiwc_job_push_branch(aiwc_job* j, const aiwc_branch_event* ev, size_t n, int on_device);
+aiwc_status aiwc_job_push_instr_runs(aiwc_job* j, const uint32_t* run_wi, const uint64_t* run_off,
+                                     const uint64_t* run_len, size_t n_runs, const uint16_t* ops, size_t n_ops,
+                                     int on_device);
+
+/* Queues the job's reduction on a worker and returns at once. */
+aiwc_status aiwc_job_finish(aiwc_job* j);
+
+/* When the reduction is done: writes the metrics (and out->opcode_hist when
+ * non-NULL), releases the slot, frees j and returns the reduction's status;
+ * otherwise AIWC_EAGAIN and j stays valid. aiwc_job_wait blocks instead (and
+ * finishes the job first if needed). */
+aiwc_status aiwc_job_poll(aiwc_job* j, aiwc_metrics* out);
+aiwc_status aiwc_job_wait(aiwc_job* j, aiwc_metrics* out);
+
+/* Counters since creation, and the device bytes slots hold now. */
+aiwc_status aiwc_server_stats(const aiwc_server* s, uint64_t* admitted, uint64_t* rejected, uint64_t* completed,
+                              uint64_t* device_bytes);
+
+/* Waits for queued reductions, then frees everything (open jobs are dropped). */
+aiwc_status aiwc_server_destroy(aiwc_server* s);
+
 /* ------------------------------------------------- without any allocation */
 
 /* The memory metrics (Table I memory rows: totals, unique reads and writes,

@@ -30,6 +30,11 @@ class aiwc_config(ctypes.Structure):
                 ("table_slots", ctypes.c_uint64)]
 
 
+class aiwc_server_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("max_jobs", ctypes.c_uint32), ("workers", ctypes.c_uint32),
+                ("hbm_budget", ctypes.c_uint64)]
+
+
 _U64 = ctypes.c_uint64
 _F64 = ctypes.c_double
 METRIC_FIELDS = [
@@ -74,6 +79,18 @@ SIGNATURES = {
     "aiwc_stage_times": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_char_p),
                                         ctypes.c_int]),
     "aiwc_mem_metrics_noalloc": (_ST, [ctypes.c_int, _VP, _VP, _SZ, ctypes.c_uint32, ctypes.POINTER(aiwc_metrics)]),
+    "aiwc_server_config_default": (None, [ctypes.POINTER(aiwc_server_config)]),
+    "aiwc_server_create": (_ST, [ctypes.POINTER(aiwc_server_config), ctypes.POINTER(_VP)]),
+    "aiwc_job_open": (_ST, [_VP, ctypes.POINTER(aiwc_config), ctypes.c_uint64, ctypes.POINTER(_VP)]),
+    "aiwc_job_push_mem": (_ST, [_VP, _VP, _SZ, ctypes.c_int]),
+    "aiwc_job_push_branch": (_ST, [_VP, _VP, _SZ, ctypes.c_int]),
+    "aiwc_job_push_instr_runs": (_ST, [_VP, _VP, _VP, _VP, _SZ, _VP, _SZ, ctypes.c_int]),
+    "aiwc_job_finish": (_ST, [_VP]),
+    "aiwc_job_poll": (_ST, [_VP, ctypes.POINTER(aiwc_metrics)]),
+    "aiwc_job_wait": (_ST, [_VP, ctypes.POINTER(aiwc_metrics)]),
+    "aiwc_server_stats": (_ST, [_VP, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]),
+    "aiwc_server_destroy": (_ST, [_VP]),
 }
 
 LIB_PATH = _build.LIB
@@ -193,6 +210,78 @@ def aiwc_mem_metrics_noalloc(device: int, stream, events_ptr: int, n: int, space
     m = aiwc_metrics()
     _check(lib.aiwc_mem_metrics_noalloc(device, stream, events_ptr, n, space_mask, ctypes.byref(m)))
     return _to_dict(m)
+
+
+# ------------------------------------------------------------------ serving
+
+def aiwc_server_config_default(**overrides) -> aiwc_server_config:
+    c = aiwc_server_config()
+    lib.aiwc_server_config_default(ctypes.byref(c))
+    for k, v in overrides.items():
+        setattr(c, k, v)
+    return c
+
+
+def aiwc_server_create(cfg: aiwc_server_config) -> int:
+    s = _VP()
+    _check(lib.aiwc_server_create(ctypes.byref(cfg), ctypes.byref(s)))
+    return s.value
+
+
+def aiwc_job_open(server, cfg: aiwc_config, reserve_bytes: int):
+    """A job handle, or None when the server answers AIWC_EAGAIN."""
+    j = _VP()
+    st = lib.aiwc_job_open(server, ctypes.byref(cfg), reserve_bytes, ctypes.byref(j))
+    if st == AIWC_EAGAIN:
+        return None
+    _check(st)
+    return j.value
+
+
+def aiwc_job_push_mem(j, ptr, n, on_device):
+    _check(lib.aiwc_job_push_mem(j, ptr, n, int(on_device)))
+
+
+def aiwc_job_push_branch(j, ptr, n, on_device):
+    _check(lib.aiwc_job_push_branch(j, ptr, n, int(on_device)))
+
+
+def aiwc_job_push_instr_runs(j, wi_ptr, off_ptr, len_ptr, n_runs, ops_ptr, n_ops, on_device):
+    _check(lib.aiwc_job_push_instr_runs(j, wi_ptr, off_ptr, len_ptr, n_runs, ops_ptr, n_ops, int(on_device)))
+
+
+def aiwc_job_finish(j):
+    _check(lib.aiwc_job_finish(j))
+
+
+def aiwc_job_poll(j, opcode_hist=None):
+    """The metrics dict once the job is done (the job is then released), else None."""
+    m = aiwc_metrics()
+    if opcode_hist is not None:
+        m.opcode_hist = opcode_hist.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+    st = lib.aiwc_job_poll(j, ctypes.byref(m))
+    if st == AIWC_EAGAIN:
+        return None
+    _check(st)
+    return _to_dict(m)
+
+
+def aiwc_job_wait(j, opcode_hist=None) -> dict:
+    m = aiwc_metrics()
+    if opcode_hist is not None:
+        m.opcode_hist = opcode_hist.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+    _check(lib.aiwc_job_wait(j, ctypes.byref(m)))
+    return _to_dict(m)
+
+
+def aiwc_server_stats(server) -> dict:
+    v = [ctypes.c_uint64() for _ in range(4)]
+    _check(lib.aiwc_server_stats(server, *[ctypes.byref(x) for x in v]))
+    return dict(zip(("admitted", "rejected", "completed", "device_bytes"), (x.value for x in v)))
+
+
+def aiwc_server_destroy(server) -> None:
+    _check(lib.aiwc_server_destroy(server))
 
 
 from .api import Characterizer, characterize  # noqa: E402,F401

@@ -138,6 +138,10 @@ struct SortDesc {
 
 // Text returned by aiwc_last_error(NULL) on this thread.
 void set_last_error(const std::string& msg);
+// For the server: does h reduce with the same metric configuration as cfg
+// (everything but device, stream and budget)? And set h's scratch budget.
+bool handle_config_matches(const aiwc_handle* h, const aiwc_config* cfg);
+void handle_set_budget(aiwc_handle* h, uint64_t bytes);
 
 // Kernels launched by this library (process-wide, all handles).
 void count_launches(u64 n);

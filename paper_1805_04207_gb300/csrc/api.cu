@@ -1146,6 +1146,19 @@ uint64_t aiwc_device_bytes(const aiwc_handle* h) { return h ? (uint64_t)h->bytes
 
 uint64_t aiwc_kernel_launches(void) { return launches_so_far(); }
 
+}  // extern "C"
+
+bool aiwc::handle_config_matches(const aiwc_handle* h, const aiwc_config* c) {
+  const aiwc_config& a = h->cfg;
+  return a.history_len == c->history_len && a.cover_num == c->cover_num && a.cover_den == c->cover_den &&
+         a.n_opcodes == c->n_opcodes && a.space_mask == (c->space_mask & 0xFu) && a.precision == c->precision &&
+         a.plan == c->plan && a.max_work_items == c->max_work_items && a.table_slots == c->table_slots;
+}
+
+void aiwc::handle_set_budget(aiwc_handle* h, uint64_t bytes) { h->cfg.hbm_budget = bytes; }
+
+extern "C" {
+
 aiwc_status aiwc_set_stage_timing(aiwc_handle* h, int on) {
   if (!h) return fail(nullptr, AIWC_EINVAL, "null handle");
   h->timing = on != 0;

@@ -45,12 +45,17 @@ KERNEL_FILES = {"mem_ingest": "mem.cu", "branch_ingest": "branch.cu", "instr_run
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scale", type=int, default=0, help="shrink the workload by 2^scale (testing only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="large", choices=["large", "batched", "serving", "precision"],
+                    help="large (default): the 2^28-event invocation; batched: 512 uneven invocations per "
+                         "step in one graph; serving: Poisson jobs streaming chunks; precision: 2^30 events, "
+                         "FP32-compensated vs FP64 entropies")
+    ap.add_argument("--jobs", type=int, default=100, help="serving: number of jobs")
     return ap.parse_args()
 
 
@@ -65,7 +70,7 @@ class ClockSampler:
         self.lines = []
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -139,16 +144,16 @@ def cpu_baseline(scale_shift: int):
     """The oracle, as it stands, on a bounded sample of the same workload."""
     import oracle
     import synth
-    n_mem = 1 << (22 - scale_shift)
-    n_br = 1 << (20 - scale_shift)
-    n_wi = max(1, 1 << (14 - scale_shift))
-    tr = synth.large(seed=0, n_mem=n_mem, n_br=n_br, n_wi=n_wi, per_wi=1024, zipf_distinct=1 << 20)
+    n_mem = 1 << (26 - scale_shift)
+    n_br = 1 << (24 - scale_shift)
+    n_wi = max(1, 1 << (18 - scale_shift))
+    tr = synth.large(seed=0, n_mem=n_mem, n_br=n_br, n_wi=n_wi, per_wi=1024, zipf_distinct=1 << (24 - scale_shift))
     t0 = time.perf_counter()
     oracle.compute(tr)
     dt = time.perf_counter() - t0
     return {"value": n_mem / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"large-shaped sample: {n_mem} memory, {n_br} branch, {n_wi * 1024} opcodes "
-                      f"(Zipf over 2^20), single-threaded C++ oracle, {dt:.1f} s"}, dt
+                      f"(Zipf over 2^{24 - scale_shift}), single-threaded C++ oracle, {dt:.1f} s"}, dt
 
 
 def run_reference(args, rank, world):
@@ -158,10 +163,10 @@ def run_reference(args, rank, world):
     oracle.build()
     shift = args.scale
     vals = []
-    for _ in range(args.warmup):
-        cpu_baseline(shift + 2)
-    for _ in range(args.steps):
-        b, dt = cpu_baseline(shift + 2)
+    for _ in range(min(args.warmup, 1)):
+        cpu_baseline(shift + 3)
+    for _ in range(min(args.steps, 3)):
+        b, dt = cpu_baseline(shift + 3)
         vals.append(b["value"])
     v = statistics.median(vals)
     b["value"] = v
@@ -173,6 +178,160 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def plan_for(n_mem: int) -> dict:
+    """Per-trace plan: the sort plan for small invocations (its fixed cost is
+    lower), the hash plan with a table of about n_mem / 2 slots otherwise."""
+    if n_mem <= (1 << 15):
+        return {"plan": 1}
+    slots = 1 << max(12, min(20, (max(1, n_mem // 2) - 1).bit_length()))
+    return {"plan": 0, "table_slots": slots}
+
+
+def base_line(args, world, value, ms, extra):
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": round(ms, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64+f64", "data": "synthetic", "impl": "ours"}
+    line.update(extra)
+    return line
+
+
+def run_batched(args, P, torch, local, world, rank):
+    import synth
+    from paper_1805_04207_gb300.api import compute_batch, push_trace
+    traces = synth.batched(512, device="cuda", seed=rank)
+    n_mem = sum(t.n_mem for t in traces)
+    chars = [P.Characterizer(device=local, n_opcodes=t.n_opcodes, max_work_items=1 << 20, **plan_for(t.n_mem))
+             for t in traces]
+    for t in traces:
+        t.run_wi = t.run_wi.to(torch.int32)
+
+    def step():
+        for c, t in zip(chars, traces):
+            push_trace(c, t)
+        return compute_batch(chars, want_hist=False)
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    l0 = P.aiwc_kernel_launches()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        outs = step()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / args.steps
+    clocks = sampler.stop()
+    launches = P.aiwc_kernel_launches() - l0
+    for c in chars:
+        c.close()
+    return base_line(args, world, world * n_mem / dt, dt * 1e3, {
+        "config": {"workload": "batched: 512 invocations, memory events log-uniform 2^12..2^24, footprints "
+                               "log-uniform 2^8..2^22, patterns stream/stencil/gemm/zipf/uniform; one "
+                               "aiwc_compute_batch (one CUDA graph) per step",
+                   "memory_events_per_step": n_mem, "timing": "wall clock per step incl. pushes, synchronised",
+                   "plans": "sort for <= 2^15 events, else hash with ~n/2 table slots"},
+        "clocks": clocks, "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
+        "result_check": {"footprint_sum": sum(o["footprint"] for o in outs)}})
+
+
+def run_serving(args, P, torch, local, world, rank):
+    import synth
+    from paper_1805_04207_gb300.serving import Server
+    jobs = synth.serving_jobs(args.jobs, rate_hz=200.0, seed=rank)
+    # a device pool of 16-byte memory and 8-byte branch events the chunks slice
+    pool_mem = synth.pattern_trace("zipf", 1 << 24, 1 << 22, device="cuda", seed=rank).mem
+    pool_mem = torch.cat([pool_mem, synth.pattern_trace("stencil", 1 << 24, 1 << 22, device="cuda",
+                                                        seed=rank, stream=1).mem])
+    pool_br = synth.large_branch(1 << 24, device="cuda", seed=rank)
+    P_total = pool_mem.shape[0]
+
+    def chunks_of(job):
+        off = 0
+        for c in job["chunks"]:
+            c = min(c, P_total)
+            start = (off * 7919) % (P_total - c + 1)
+            yield pool_mem[start:start + c]
+            off += c
+    srv = Server(device=local, max_jobs=32, workers=8, hbm_budget=120 << 30)
+    lat, events = [], 0
+    pending = list(jobs)
+    running = {}
+    sampler = ClockSampler(local)
+    t0 = time.perf_counter()
+    while pending or running:
+        now = time.perf_counter() - t0
+        while pending and pending[0]["arrival_s"] <= now:
+            jb = pending[0]
+            n_br = jb["n_mem"] // 4
+            reserve = 24 * jb["n_mem"] + 40 * n_br + (96 << 20)
+            h = srv.open(reserve, n_opcodes=64, max_work_items=1 << 26, **plan_for(jb["n_mem"]))
+            if h is None:
+                break
+            for ch in chunks_of(jb):
+                h.push_mem(ch)
+            left = n_br
+            while left > 0:
+                c = min(left, pool_br.shape[0])
+                h.push_branch(pool_br[:c])
+                left -= c
+            h.finish()
+            running[id(h)] = (jb, h)
+            pending.pop(0)
+            events += jb["n_mem"]
+        for k, (jb, h) in list(running.items()):
+            r = h.poll()
+            if r is not None:
+                lat.append(time.perf_counter() - t0 - jb["arrival_s"])
+                del running[k]
+    span = time.perf_counter() - t0
+    clocks = sampler.stop()
+    st = srv.stats()
+    srv.close()
+    lat.sort()
+    p50 = lat[len(lat) // 2] if lat else None
+    p99 = lat[min(len(lat) - 1, int(0.99 * len(lat)))] if lat else None
+    return base_line(args, world, world * events / span, span * 1e3, {
+        "steps": 1, "config": {"workload": f"serving: {args.jobs} jobs, Poisson 200/s, traces log-uniform "
+                                           "16 MB..8 GB, chunks log-uniform 1..256 MB (device-resident pool), "
+                                           "32 slots, 120 GiB budget",
+                               "memory_events": events},
+        "latency_s": {"p50": p50, "p99": p99, "max": lat[-1] if lat else None},
+        "server": st, "clocks": clocks})
+
+
+def run_precision(args, P, torch, local, world, rank):
+    import synth
+    from paper_1805_04207_gb300.api import push_trace
+    s = args.scale
+    tr = synth.precision(device="cuda", seed=rank, n_mem=1 << (30 - s), uniform_distinct=1 << (27 - s),
+                         hot_distinct=1 << (20 - s), n_br=1 << (26 - s))
+    tr.run_wi = tr.run_wi.to(torch.int32)
+    res, times = {}, {}
+    for prec in (0, 1):
+        c = P.Characterizer(device=local, precision=prec, n_opcodes=tr.n_opcodes)
+        for _ in range(max(3, args.warmup)):
+            push_trace(c, tr)
+            res[prec] = c.compute(want_hist=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            push_trace(c, tr)
+            res[prec] = c.compute(want_hist=False)
+        torch.cuda.synchronize()
+        times[prec] = (time.perf_counter() - t0) / args.steps
+        c.close()
+    err = {f"entropy[{n}]": abs(res[1]["entropy"][n] - res[0]["entropy"][n]) for n in range(11)}
+    err["albe"] = abs(res[1]["albe"] - res[0]["albe"])
+    same_counts = all(res[1][k] == res[0][k] for k in ("footprint", "footprint_cover", "unique_reads",
+                                                         "unique_writes", "branch_minsum", "branch_patterns"))
+    return base_line(args, world, world * tr.n_mem / times[1], times[1] * 1e3, {
+        "dtype": "u64+f32(compensated)",
+        "config": {"workload": f"precision: 2^{30 - s} memory events, 75% uniform over 2^{27 - s} addresses + "
+                               f"25% Zipf(1.2) over a 2^{20 - s} hot set; 2^{26 - s} branch events",
+                   "timing": "wall clock per invocation incl. pushes, synchronised"},
+        "fp32_vs_fp64_abs_error_bits": err, "max_abs_error_bits": max(err.values()), "bound_bits": 2.0 ** -22,
+        "counts_identical": same_counts, "fp64_ms_per_step": round(times[0] * 1e3, 3)})
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -180,6 +339,15 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload != "large":
+        import torch
+        import paper_1805_04207_gb300 as P
+        torch.cuda.set_device(local)
+        fn = {"batched": run_batched, "serving": run_serving, "precision": run_precision}[args.workload]
+        line = fn(args, P, torch, local, world, rank)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
 
     import torch
     import paper_1805_04207_gb300 as P

@@ -633,6 +633,7 @@ struct BatchGraph {
   std::mutex mu;
   std::vector<u64> sig;
   cudaGraphExec_t exec = nullptr;
+  u64 kernels = 0;  // kernels captured in exec (each replay launches them all)
   cudaStream_t cs = nullptr;
   std::vector<cudaStream_t> forks;
   cudaEvent_t ev_user = nullptr, ev_fork = nullptr;
@@ -672,9 +673,11 @@ struct BatchGraph {
       sig.clear();
       if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
         return cuda_fail(nullptr, "cudaStreamBeginCapture", e);
+      const u64 before = launches_so_far();
       cudaEventRecord(ev_fork, cs);
       for (cudaStream_t f : forks) cudaStreamWaitEvent(f, ev_fork, 0);
       st = enqueue(cs, forks);
+      kernels = launches_so_far() - before;
       for (size_t k = 0; k < forks.size(); ++k) {
         cudaEventRecord(ev_join[k], forks[k]);
         cudaStreamWaitEvent(cs, ev_join[k], 0);
@@ -693,6 +696,8 @@ struct BatchGraph {
         return cuda_fail(nullptr, "cudaGraphInstantiate", e);
       }
       sig = s;
+    } else {
+      count_launches(kernels);  // a replay launches every captured kernel again
     }
     if ((e = cudaEventRecord(ev_user, user)) != cudaSuccess || (e = cudaStreamWaitEvent(cs, ev_user, 0)) != cudaSuccess ||
         (e = cudaGraphLaunch(exec, cs)) != cudaSuccess || (e = cudaStreamSynchronize(cs)) != cudaSuccess)

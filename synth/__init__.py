@@ -20,6 +20,6 @@ Event layouts (little-endian, the byte layout the C ABI reads):
 """
 from .traces import (  # noqa: F401
     Trace, mix64, hash3, u01, pack_mem, pack_branch,
-    tiny, large, precision, batched, serving_jobs, pattern_trace,
+    tiny, large, large_mem, large_branch, large_instr, precision, batched, serving_jobs, pattern_trace,
     BARRIER_I16,
 )

@@ -178,6 +178,21 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest x over all ranks (the slowest replica sets the job's time)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(units_per_rank: int, world: int, seconds: float) -> float:
+    """Whole-job throughput of `world` replicas each processing units_per_rank."""
+    return world * units_per_rank / seconds
+
+
 def plan_for(n_mem: int) -> dict:
     """Per-trace plan: the sort plan for small invocations (its fixed cost is
     lower), the hash plan with a table of about n_mem / 2 slots otherwise."""
@@ -401,11 +416,8 @@ def main():
     launches = P.aiwc_kernel_launches() - l0
     c.set_stage_timing(False)
     ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms], device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * n_mem * args.steps / (ms_max / 1e3)
+    ms_max = max_over_ranks(ms, dist, "cuda")
+    value = replica_throughput(n_mem * args.steps, world, ms_max / 1e3)
 
     # roofline of the dominant stage, plus the whole step
     hbm, peak_kind = peaks()
@@ -447,14 +459,10 @@ def main():
         for _ in range(ek):
             hstep()
         barrier()
-        e_s = (time.perf_counter() - t0) / ek
-        tt = torch.tensor([e_s], device="cuda")
-        if dist is not None:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e_s = float(tt.item())
+        e_s = max_over_ranks((time.perf_counter() - t0) / ek, dist, "cuda")
         h2d = 16 * n_mem + 8 * n_br + 2 * n_ops + (4 + 8 + 8) * tr.run_wi.numel()
         d2h = 8 * 11 + 8 * 40 + 8 * tr.n_opcodes
-        e2e = {"value": world * n_mem / e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+        e2e = {"value": replica_throughput(n_mem, world, e_s), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "ms_per_step": round(e_s * 1e3, 3), "steps": ek}
         del hmem, hbr, hops
 

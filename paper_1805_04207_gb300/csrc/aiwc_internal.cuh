@@ -152,6 +152,7 @@ u64 launches_so_far();
 // passes whose window holds no varying bit return at once on the device.
 void sort_keys(const SortDesc& d, cudaStream_t s, u32 host_passes = 0xFFu);
 size_t sort_counts_words(u64 n_max);  // u32 words needed for counts
+u32 sort_tiles(u64 n);                // tiles of the sort for n keys (SortDesc::ntiles)
 size_t sort_block_sums_words(u64 n_max);
 
 constexpr u32 kSlotWordNone = 0xFFFFFFFFu;  // slot word of an event the table could not place

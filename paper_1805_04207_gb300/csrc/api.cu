@@ -775,7 +775,7 @@ SortDesc sort_desc(aiwc_handle* h, DevBuf& a, DevBuf& b, int slot, const u64* n_
   d.lo_bit = 0;
   d.counts = (u32*)h->counts.p;
   d.block_sums = (u32*)h->bsums.p;
-  d.ntiles = (u32)ntiles_of(n_host);
+  d.ntiles = sort_tiles(n_host);
   return d;
 }
 
@@ -857,7 +857,7 @@ aiwc_status enqueue_part2(aiwc_handle* h, cudaStream_t st, const Plan& p) {
     la.cur = d.cur;
     la.n = &dst->n_words;
     la.tiles = (TileSum*)h->tiles.p;
-    la.ntiles = d.ntiles;
+    la.ntiles = (u32)ntiles_of(n_mem);
     la.over = over;
     la.over_cap = over_cap;
     la.arena = h->arena;
@@ -889,7 +889,7 @@ aiwc_status enqueue_part2(aiwc_handle* h, cudaStream_t st, const Plan& p) {
       wa.h = h->cfg.history_len;
       wa.patterns = (u64*)h->pat_a.p;
       wa.tiles = (TileSum*)h->tiles.p;
-      wa.ntiles = bsort.ntiles;
+      wa.ntiles = (u32)ntiles_of(n_br);
       wa.over = over;
       wa.over_cap = over_cap;
       wa.arena = h->arena;
@@ -916,7 +916,7 @@ aiwc_status enqueue_part2(aiwc_handle* h, cudaStream_t st, const Plan& p) {
       pa.cur = ps.cur;
       pa.n = &dst->n_patterns;
       pa.tiles = (TileSum*)h->tiles.p;
-      pa.ntiles = ps.ntiles;
+      pa.ntiles = (u32)ntiles_of(n_br);
       pa.arena = h->arena;
       pa.grid = grid;
       launch_pattern_runs(pa, st);

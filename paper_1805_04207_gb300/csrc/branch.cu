@@ -125,14 +125,18 @@ constexpr int kSpBitWords = (int)((kSiteMaxLen + 32) / 32) + 2;
 // One block per site: its outcomes become a bit string in shared memory; for
 // every outcome with h predecessors, the packed counter of its history gets
 // +1 total (low 16 bits) and +outcome taken (high 16 bits). Histories are
-// binned 2^15 at a time (more passes for h > 15). M and N' follow from the
-// bins. Any fixed bijection of the h-bit window names the pattern equally
-// well; here bit k of the pattern is the outcome k+1 places after the oldest.
+// binned 2^15 at a time (more passes for h > 15). The first increment of a
+// bin lists it, so a pass visits and clears only the bins it used. M and N'
+// follow from the bins. Any fixed bijection of the h-bit window names the
+// pattern equally well; here bit k of the pattern is the outcome k+1 places
+// after the oldest.
 __global__ void __launch_bounds__(kSpThreads) k_site_patterns(SiteArgs a) {
   if (!gate_open(a.gate, a.gate_want)) return;
   extern __shared__ u32 spm[];
   u32* bits = spm;
   u32* cnt = spm + kSpBitWords;
+  uint16_t* used = reinterpret_cast<uint16_t*>(cnt + (1 << kSpBinsLog));
+  __shared__ u32 n_used;
   __shared__ u64 red64[32];
   DevState* st = &a.arena->st;
   const u64* w = *a.cur ? a.b : a.a;
@@ -143,6 +147,9 @@ __global__ void __launch_bounds__(kSpThreads) k_site_patterns(SiteArgs a) {
   const u32 passes = h > (u32)kSpBinsLog ? (1u << (h - kSpBinsLog)) : 1u;
   const u64 hmask = (1ull << h) - 1ull;
   const u64 n_sites = umin64(st->n_sites, a.sites_cap);
+  for (u32 i = threadIdx.x; i < nbins; i += kSpThreads) cnt[i] = 0u;
+  if (threadIdx.x == 0) n_used = 0;
+  __syncthreads();
   u64 msum = 0, nsum = 0, nsite = 0;
   for (u64 si = blockIdx.x; si < n_sites; si += gridDim.x) {
     const u64 start = a.sites[2 * si], m = a.sites[2 * si + 1];
@@ -160,22 +167,28 @@ __global__ void __launch_bounds__(kSpThreads) k_site_patterns(SiteArgs a) {
     }
     __syncthreads();
     for (u32 q = 0; q < passes; ++q) {
-      for (u32 i = threadIdx.x; i < nbins; i += kSpThreads) cnt[i] = 0u;
-      __syncthreads();
       for (u64 j = h + threadIdx.x; j < m; j += kSpThreads) {
         const u64 pos = j - h;
         const u64 two = (u64)bits[pos >> 5] | ((u64)bits[(pos >> 5) + 1] << 32);
         const u32 win = (u32)((two >> (pos & 31)) & hmask);
         const u32 outcome = (bits[j >> 5] >> (j & 31)) & 1u;
-        if ((win >> pbits) == q) atomicAdd(&cnt[win & (nbins - 1)], 1u + (outcome << 16));
+        if ((win >> pbits) == q) {
+          const u32 b = win & (nbins - 1);
+          if (atomicAdd(&cnt[b], 1u + (outcome << 16)) == 0u) used[atomicAdd(&n_used, 1u)] = (uint16_t)b;
+        }
       }
       __syncthreads();
-      for (u32 i = threadIdx.x; i < nbins; i += kSpThreads) {
-        const u32 v = cnt[i];
+      const u32 nu = n_used;
+      for (u32 i = threadIdx.x; i < nu; i += kSpThreads) {
+        const u32 b = used[i];
+        const u32 v = cnt[b];
+        cnt[b] = 0u;
         const u32 nn = v & 0xFFFFu, t = v >> 16;
         msum += t < nn - t ? t : nn - t;
         nsum += nn;
       }
+      __syncthreads();
+      if (threadIdx.x == 0) n_used = 0;
       __syncthreads();
     }
   }
@@ -423,7 +436,9 @@ void launch_persite_decide(Arena* arena, u32 h, u64 sites_cap, int allow, cudaSt
   count_launches(1);
 }
 
-static size_t site_patterns_smem() { return (size_t)(kSpBitWords + (1 << kSpBinsLog)) * 4; }
+static size_t site_patterns_smem() {
+  return (size_t)(kSpBitWords + (1 << kSpBinsLog)) * 4 + (size_t)(1 << kSpBinsLog) * 2;
+}
 
 void init_branch_attributes() {
   cudaFuncSetAttribute(k_site_patterns, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)site_patterns_smem());

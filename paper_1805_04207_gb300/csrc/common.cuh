@@ -43,6 +43,14 @@ __device__ __forceinline__ void mark_work_items(u32* bitmap, u64 max_wi, u32 wi,
   u32 todo = __ballot_sync(0xffffffffu, valid);
   const u32 word = wi >> 5;
   const u32 bit = 1u << (wi & 31);
+  // common case: every valid lane's id falls in one bitmap word
+  const int first = todo ? __ffs(todo) - 1 : 0;
+  const u32 w0 = __shfl_sync(0xffffffffu, word, first);
+  if (__all_sync(0xffffffffu, !valid || word == w0)) {
+    const u32 bits = __reduce_or_sync(0xffffffffu, valid ? bit : 0u);
+    if (todo && lane == first) atomicOr(&bitmap[w0], bits);
+    return;
+  }
   while (todo) {
     const int leader = __ffs(todo) - 1;
     const u32 lw = __shfl_sync(0xffffffffu, word, leader);

@@ -80,7 +80,9 @@ __global__ void __launch_bounds__(kIngestThreads, HASH ? 4 : 3) k_mem_ingest(Mem
 #pragma unroll
       for (int k = 0; k < ITEMS; ++k) {
         pos[k] = sbt_hash((word[k] >> 12) + 1ull) & a.tab.mask;
-        first[k] = keep[k] ? __ldcg(&a.tab.keys[pos[k]]) : 0ull;
+        // an L1-cached copy may still read 0 for a slot another SM just
+        // claimed; sbt_place then loses the CAS and reads the real key
+        first[k] = keep[k] ? a.tab.keys[pos[k]] : 0ull;
       }
 #pragma unroll
       for (int k = 0; k < ITEMS; ++k) {

@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(kScanT) k_sbt_down(const u32* cnt, u64 len, co
 }
 
 constexpr int kScThreads = 256;
-constexpr int kScItems = 8;
+constexpr int kScItems = 16;
 
 // Scatter each event's low 12 bits into its superblock's segment.
 __global__ void __launch_bounds__(kScThreads) k_mem_scatter(HashArgs a) {

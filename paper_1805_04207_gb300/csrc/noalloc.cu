@@ -34,7 +34,7 @@ constexpr size_t kOffTable = kOffLow + a256(2 * kNoAllocMaxEvents);
 constexpr size_t kOffScan = kOffTable + a256(24 * kNoAllocSlots);
 constexpr size_t kOffOverA = kOffScan + a256(4 * (kNoAllocSlots / 4096 + 1));
 constexpr size_t kOffOverB = kOffOverA + a256(8 * kNoAllocOverCap);
-constexpr size_t kCountsWords = 256 * tiles_of(kNoAllocOverCap);
+constexpr size_t kCountsWords = 256 * ((kNoAllocOverCap + 2047) / 2048);  // sort tiles of 2048 keys
 constexpr size_t kOffCounts = kOffOverB + a256(8 * kNoAllocOverCap);
 constexpr size_t kOffBsums = kOffCounts + a256(4 * kCountsWords);
 constexpr size_t kOffBitmap = kOffBsums + a256(4 * (kCountsWords / 4096 + 2));
@@ -157,7 +157,7 @@ extern "C" aiwc_status aiwc_mem_metrics_noalloc(int device, void* cuda_stream, c
   d.lo_bit = 0;
   d.counts = (u32*)(p + kOffCounts);
   d.block_sums = (u32*)(p + kOffBsums);
-  d.ntiles = (u32)tiles_of(kNoAllocOverCap);
+  d.ntiles = sort_tiles(kNoAllocOverCap);
   sort_keys(d, s);
   FinalizeArgs fa;
   fa.over_a = over_a;

@@ -21,7 +21,12 @@ u64 launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
 namespace {
 
-constexpr int kWarps = kTileThreads / 32;
+// The sort's own tile: 256 threads x 8 keys (fewer registers per thread, so
+// more blocks per SM than the 16-key tiles of the run kernels).
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kWarps = kSortThreads / 32;
 constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanBlock = kScanThreads * kScanItems;
@@ -36,20 +41,20 @@ __device__ __forceinline__ bool pass_shift(const SortDesc& d, int pass, int* shi
   return ((varying >> sh) & 0xFFull) != 0;
 }
 
-__global__ void __launch_bounds__(kTileThreads) k_hist(SortDesc d, int pass) {
+__global__ void __launch_bounds__(kSortThreads) k_hist(SortDesc d, int pass) {
   int shift;
   if (!pass_shift(d, pass, &shift)) return;
   __shared__ u32 h[kWarps][256];
-  for (int i = threadIdx.x; i < kWarps * 256; i += kTileThreads) (&h[0][0])[i] = 0;
+  for (int i = threadIdx.x; i < kWarps * 256; i += kSortThreads) (&h[0][0])[i] = 0;
   __syncthreads();
   const u64 n = umin64(*d.n, d.n_cap);
   const u64* src = *d.cur ? d.b : d.a;
-  const u64 base = (u64)blockIdx.x * kTile;
+  const u64 base = (u64)blockIdx.x * kSortTile;
   const int w = threadIdx.x >> 5;
   const u64 m = eff_mask(d);
 #pragma unroll 4
-  for (int k = 0; k < kTileItems; ++k) {
-    u64 i = base + (u64)k * kTileThreads + threadIdx.x;
+  for (int k = 0; k < kSortItems; ++k) {
+    u64 i = base + (u64)k * kSortThreads + threadIdx.x;
     if (i < n) atomicAdd(&h[w][((src[i] & m) >> shift) & 0xFF], 1u);
   }
   __syncthreads();
@@ -151,31 +156,31 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(SortDesc d, int pass
   }
 }
 
-__global__ void __launch_bounds__(kTileThreads) k_scatter(SortDesc d, int pass) {
+__global__ void __launch_bounds__(kSortThreads) k_scatter(SortDesc d, int pass) {
   int shift;
   if (!pass_shift(d, pass, &shift)) return;
   __shared__ u32 wcnt[kWarps][256];
   __shared__ u32 dofs[256];
   __shared__ u32 gofs[256];
   __shared__ u32 wt[33];
-  __shared__ u64 stage[kTile];
-  for (int i = threadIdx.x; i < kWarps * 256; i += kTileThreads) (&wcnt[0][0])[i] = 0;
+  __shared__ u64 stage[kSortTile];
+  for (int i = threadIdx.x; i < kWarps * 256; i += kSortThreads) (&wcnt[0][0])[i] = 0;
   __syncthreads();
   const u64 n = umin64(*d.n, d.n_cap);
   const u32 cur = *d.cur;
   const u64* src = cur ? d.b : d.a;
   u64* dst = cur ? d.a : d.b;
-  const u64 base = (u64)blockIdx.x * kTile;
+  const u64 base = (u64)blockIdx.x * kSortTile;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const u32 lt_mask = (1u << lane) - 1u;
   const u64 m = eff_mask(d);
-  u64 key[kTileItems];
-  u32 rank[kTileItems];
+  u64 key[kSortItems];
+  u32 rank[kSortItems];
   // Warp w ranks positions base + w*512 + k*32 + lane in that order, which
   // keeps the scatter stable.
 #pragma unroll
-  for (int k = 0; k < kTileItems; ++k) {
-    u64 i = base + (u64)w * (32 * kTileItems) + (u64)k * 32 + lane;
+  for (int k = 0; k < kSortItems; ++k) {
+    u64 i = base + (u64)w * (32 * kSortItems) + (u64)k * 32 + lane;
     bool valid = i < n;
     key[k] = valid ? src[i] : 0ull;
     u32 dig = valid ? (u32)(((key[k] & m) >> shift) & 0xFF) : 256u + lane;
@@ -203,16 +208,16 @@ __global__ void __launch_bounds__(kTileThreads) k_scatter(SortDesc d, int pass) 
   }
   __syncthreads();
 #pragma unroll
-  for (int k = 0; k < kTileItems; ++k) {
-    u64 i = base + (u64)w * (32 * kTileItems) + (u64)k * 32 + lane;
+  for (int k = 0; k < kSortItems; ++k) {
+    u64 i = base + (u64)w * (32 * kSortItems) + (u64)k * 32 + lane;
     if (i < n) {
       u32 dig = (u32)(((key[k] & m) >> shift) & 0xFF);
       stage[dofs[dig] + wcnt[w][dig] + rank[k]] = key[k];
     }
   }
   __syncthreads();
-  const u64 tile_n = n > base ? (n - base < (u64)kTile ? n - base : (u64)kTile) : 0ull;
-  for (u32 j = threadIdx.x; j < tile_n; j += kTileThreads) {
+  const u64 tile_n = n > base ? (n - base < (u64)kSortTile ? n - base : (u64)kSortTile) : 0ull;
+  for (u32 j = threadIdx.x; j < tile_n; j += kSortThreads) {
     u64 kv = stage[j];
     u32 dig = (u32)(((kv & m) >> shift) & 0xFF);
     dst[(u64)gofs[dig] + (j - dofs[dig])] = kv;
@@ -227,7 +232,7 @@ __global__ void k_flip(SortDesc d, int pass) {
 }  // namespace
 
 size_t sort_counts_words(u64 n_max) {
-  u64 nt = (n_max + kTile - 1) / kTile;
+  u64 nt = (n_max + kSortTile - 1) / kSortTile;
   return (size_t)(256 * (nt ? nt : 1));
 }
 
@@ -235,6 +240,8 @@ size_t sort_block_sums_words(u64 n_max) {
   u64 len = sort_counts_words(n_max);
   return (size_t)((len + kScanBlock - 1) / kScanBlock + 1);
 }
+
+u32 sort_tiles(u64 n) { return (u32)((n + kSortTile - 1) / kSortTile); }
 
 void sort_keys(const SortDesc& d, cudaStream_t s, u32 host_passes) {
   if (d.ntiles == 0) return;
@@ -245,11 +252,11 @@ void sort_keys(const SortDesc& d, cudaStream_t s, u32 host_passes) {
   for (int p = 0; p < passes; ++p) {
     if (!((host_passes >> p) & 1u)) continue;
     ++launched;
-    k_hist<<<d.ntiles, kTileThreads, 0, s>>>(d, p);
+    k_hist<<<d.ntiles, kSortThreads, 0, s>>>(d, p);
     k_scan_reduce<<<nb, kScanThreads, 0, s>>>(d, p, len);
     k_scan_top<<<1, kScanThreads, 0, s>>>(d, p, nb);
     k_scan_down<<<nb, kScanThreads, 0, s>>>(d, p, len);
-    k_scatter<<<d.ntiles, kTileThreads, 0, s>>>(d, p);
+    k_scatter<<<d.ntiles, kSortThreads, 0, s>>>(d, p);
     k_flip<<<1, 1, 0, s>>>(d, p);
   }
   count_launches(6ull * launched);

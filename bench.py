@@ -37,7 +37,7 @@ WORKLOAD = ("large invocation: 2^28 memory events (stencil 256^3 + tiled SGEMM 2
 # history pattern for the run tables the method must form.
 ALG_BYTES = {"mem_event": 16, "branch_event": 8, "opcode": 2, "distinct_key": 16, "pattern": 8}
 KERNEL_FILES = {"mem_ingest": "mem.cu", "branch_ingest": "branch.cu", "instr_runs": "instr.cu", "mem_sort": "sort.cu",
-                "mem_levels": "mem.cu", "branch_sort": "sort.cu", "windows": "branch.cu", "pattern_sort": "sort.cu",
+                "mem_scatter": "mem_hash.cu", "mem_levels": "mem_hash.cu", "branch_sort": "sort.cu", "windows": "branch.cu", "pattern_sort": "sort.cu",
                 "pattern_runs": "branch.cu", "run_sort": "sort.cu", "run_combine": "instr.cu",
                 "finalize": "finalize.cu"}
 
@@ -426,7 +426,7 @@ def main():
     Bp = out["branch_patterns"]
     alg = {"mem_ingest": ALG_BYTES["mem_event"] * n_mem, "branch_ingest": ALG_BYTES["branch_event"] * n_br,
            "instr_runs": ALG_BYTES["opcode"] * n_ops,
-           "mem_sort": 0, "mem_levels": ALG_BYTES["distinct_key"] * D, "branch_sort": 0,
+           "mem_sort": 0, "mem_scatter": 0, "mem_levels": ALG_BYTES["distinct_key"] * D, "branch_sort": 0,
            "windows": ALG_BYTES["pattern"] * Bp, "pattern_sort": 0, "pattern_runs": 0, "run_sort": 0,
            "run_combine": 0, "finalize": 0}
     dom = max(per_step, key=per_step.get)

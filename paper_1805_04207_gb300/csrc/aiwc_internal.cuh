@@ -61,7 +61,7 @@ struct DevState {
   u32 err;
   u32 sbt_overflow;      // the superblock table could not place a key
   u32 pad2;
-  u64 sb_used;           // occupied superblock slots
+  u64 sb_used[2];        // occupied superblock slots: below / at or above the wide-block threshold
   u64 n_spill;           // hash plan: events whose superblock the table could not place
   u64 br_sort_mask;      // bits the branch sort must order (site only when work-items arrive sorted)
   u64 br_site_max;       // longest per-site outcome sequence
@@ -198,15 +198,23 @@ struct HashArgs {
   uint16_t* low{};       // out: low 12 bits grouped by superblock
   SbTable tab{};
   u32* scan_tmp{};     // sbt_scan_words(capacity) words
-  u64* n_used{};         // out: occupied slots
+  u64* n_used{};         // out: occupied slots [0] below the wide-block threshold, [1] at or above it
   u32* used_list{};    // out: their indices (capacity = table slots)
   u64* over{};
   u64 over_cap{};
   Arena* arena{};
-  int grid_scatter{}, grid_segments{};
+  u32* big_hist{};       // zeroed scratch: 2 * (2048 >> seg_shift) words per wide segment
+  u64 big_cap{};         // wide segments big_hist holds (at least n_words / 16384)
+  int grid_scatter{};
+  int sm_count{};
+  int seg_shift{};       // low address bits known to be zero in every event (0..3)
 };
 size_t sbt_scan_words(u64 cap);
-void launch_mem_hash(const HashArgs& a, cudaStream_t s);
+void launch_mem_hash(const HashArgs& a, cudaStream_t s);           // both steps below
+void launch_mem_hash_scatter(const HashArgs& a, cudaStream_t s);   // segment offsets, low bits into segments
+void launch_mem_hash_segments(const HashArgs& a, cudaStream_t s);  // per-segment histograms and levels
+// Wide segments (16384 events or more) a big_hist of `bytes` holds for n_words events.
+u64 mem_hash_big_segments(u64 n_words, size_t bytes, int seg_shift);
 // Fallback after a table overflow: rebuild the 64-bit sort words from the
 // slot words and the table, after the n_spill spilled words already in words[].
 void launch_rebuild_words(const u32* slotw, SbTable tab, u64* words, Arena* arena, int grid, cudaStream_t s,

@@ -47,12 +47,13 @@ struct DeviceGuard {
 inline u64 ntiles_of(u64 n) { return (n + kTile - 1) / kTile; }
 
 enum Stage {
-  kStMemIngest, kStBrIngest, kStInstrRuns, kStMemSort, kStMemLevels, kStBrSort, kStWindows, kStPatSort,
-  kStPatRuns, kStRunSort, kStCombine, kStFinalize, kNumStages
+  kStMemIngest, kStBrIngest, kStInstrRuns, kStMemSort, kStMemScatter, kStMemLevels, kStBrSort, kStWindows,
+  kStPatSort, kStPatRuns, kStRunSort, kStCombine, kStFinalize, kNumStages
 };
 const char* const kStageNames[kNumStages] = {"mem_ingest", "branch_ingest", "instr_runs", "mem_sort",
-                                             "mem_levels", "branch_sort", "windows", "pattern_sort",
-                                             "pattern_runs", "run_sort", "run_combine", "finalize"};
+                                             "mem_scatter", "mem_levels", "branch_sort", "windows",
+                                             "pattern_sort", "pattern_runs", "run_sort", "run_combine",
+                                             "finalize"};
 
 }  // namespace
 
@@ -723,6 +724,7 @@ struct Plan {
   bool hash_ok = false;   // memory: hash plan (else the sort plan, rebuilding words if the table was used)
   bool per_site = false;  // branch: per-site patterns (when !gated)
   u32 br_passes = 0xFFu, run_passes = 0xFFu;
+  int seg_shift = 0;      // memory, hash plan: low address bits that are zero in every kept event (0..3)
 };
 
 u32 active_passes(u64 kor, u64 kand, u64 mask) {
@@ -829,21 +831,29 @@ aiwc_status enqueue_part2(aiwc_handle* h, cudaStream_t st, const Plan& p) {
     launch_rebuild_words((const u32*)h->mem_b.p, table_view(h), (u64*)h->mem_a.p, h->arena, grid * 2, st);
   }
   if (n_mem && p.hash_ok) {
-    StageScope sc(h, kStMemLevels);
     HashArgs ha;
     ha.slotw = (const u32*)h->mem_b.p;
     ha.n_cap = std::min<u64>(n_mem, (h->mem_b.cap - h->c_low_off) / 2);
     ha.low = (uint16_t*)((char*)h->mem_b.p + h->c_low_off);
     ha.tab = table_view(h);
     ha.scan_tmp = (u32*)h->sbt_scan.p;
-    ha.n_used = &dst->sb_used;
+    ha.n_used = dst->sb_used;
     ha.used_list = (u32*)((char*)h->sbt.p + 20 * h->sbt_cap);
     ha.over = over;
     ha.over_cap = over_cap;
     ha.arena = h->arena;
     ha.grid_scatter = h->sm_count * 8;
-    ha.grid_segments = h->sm_count * 6;
-    launch_mem_hash(ha, st);
+    ha.sm_count = h->sm_count;
+    ha.seg_shift = p.seg_shift;
+    // the 64-bit word buffer is free in the hash plan: wide-segment histograms
+    ha.big_hist = (u32*)h->mem_a.p;
+    ha.big_cap = mem_hash_big_segments(n_mem, h->mem_a.cap, p.seg_shift);
+    {
+      StageScope sc(h, kStMemScatter);
+      launch_mem_hash_scatter(ha, st);
+    }
+    StageScope sc(h, kStMemLevels);
+    launch_mem_hash_segments(ha, st);
   } else if (n_mem) {
     SortDesc d = sort_desc(h, h->mem_a, h->mem_b, kSortMem, &dst->n_words, &dst->mem_or, &dst->mem_and, ~0ull, n_mem);
     {
@@ -1009,6 +1019,9 @@ void plan_from_ingest(aiwc_handle* h, Plan* p) {
   if (hashed && !p->hash_ok) h->sbt_want = std::min<u64>(h->sbt_cap * 4, kMaxHashSlots);
   p->br_passes = active_passes(hs.br_or, hs.br_and, hs.br_unsorted ? ~1ull : 0xFFFFFFFF00000000ull);
   p->run_passes = active_passes(hs.run_or, hs.run_and, ~0ull);
+  // address bits sit above the store bit of the word
+  const u64 addr_or = (hs.mem_or >> 1) & ((1ull << 61) - 1);
+  p->seg_shift = addr_or ? std::min(__builtin_ctzll(addr_or), 3) : 3;
 }
 
 }  // namespace
@@ -1085,7 +1098,7 @@ aiwc_status aiwc_compute_batch(aiwc_handle* const* hs, size_t n, aiwc_metrics* o
     plan_from_ingest(hs[i], &plans[i]);
     const aiwc_handle* h = hs[i];
     sig.insert(sig.end(), {(u64)(uintptr_t)h, h->n_mem, h->n_br, h->n_runs, h->epoch, (u64)plans[i].hash_ok,
-                           plans[i].br_passes, plans[i].run_passes, h->sbt_cap,
+                           plans[i].br_passes, plans[i].run_passes, h->sbt_cap, (u64)plans[i].seg_shift,
                            active_passes(h->h_state->mem_or, h->h_state->mem_and, ~0ull)});
   }
   aiwc_status s = bg.run(sig, user, [&](cudaStream_t base, std::vector<cudaStream_t>& forks) -> aiwc_status {

@@ -223,11 +223,25 @@ __device__ void order_stats(const u64* dense, const u64* over, u64 ob, u64 oe, u
   *med = 0.5 * ((double)*lo + (double)*hi);
 }
 
+// Index one past the run of value v that starts at i in the ascending
+// overflow segment [i, oe).
+__device__ __forceinline__ u64 run_end(const u64* over, u64 i, u64 oe, u64 v) {
+  u64 lo = i + 1, hi = oe;
+  while (lo < hi) {
+    const u64 mid = (lo + hi) >> 1;
+    if ((over[mid] & kValueMask) == v) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
 // Sum over groups of c*log2(c), given m_c for small c and the overflow list
-// entries for large c. FP64 path: each term in double. FP32 path: with
-// c = f * 2^e (f in [1,2)), c*log2(c) = c*e + c*log2(f); the first part is an
-// exact integer, the second is accumulated in float with Kahan compensation
-// per thread; only the cross-thread reduction is in double.
+// entries for large c. Equal sizes are adjacent in the sorted overflow
+// segment, so each distinct size is evaluated once, times its multiplicity
+// (the thread holding the first entry of a run owns it). FP64 path: each
+// term in double. FP32 path: with c = f * 2^e (f in [1,2)), c*log2(c) =
+// c*e + c*log2(f); the first part is an exact integer, the second is
+// accumulated in float with Kahan compensation per thread; only the
+// cross-thread reduction is in double.
 __device__ double clog_sum(const u64* dense, const u64* over, u64 ob, u64 oe, u32 precision, Shared& s) {
   if (precision == 0) {
     double acc = 0.0;
@@ -236,8 +250,11 @@ __device__ double clog_sum(const u64* dense, const u64* over, u64 ob, u64 oe, u3
       if (m && c > 1) acc += (double)m * ((double)c * log2((double)c));
     }
     for (u64 i = ob + threadIdx.x; i < oe; i += blockDim.x) {
-      const double c = (double)(over[i] & kValueMask);
-      acc += c * log2(c);
+      const u64 v = over[i] & kValueMask;
+      if (i > ob && (over[i - 1] & kValueMask) == v) continue;
+      const u64 m = run_end(over, i, oe, v) - i;
+      const double c = (double)v;
+      acc += (double)m * (c * log2(c));
     }
     return block_sum_f64(acc, s);
   }
@@ -257,7 +274,11 @@ __device__ double clog_sum(const u64* dense, const u64* over, u64 ob, u64 oe, u3
     const u64 m = dense[c];
     if (m && c > 1) add((u64)c, m);
   }
-  for (u64 i = ob + threadIdx.x; i < oe; i += blockDim.x) add(over[i] & kValueMask, 1);
+  for (u64 i = ob + threadIdx.x; i < oe; i += blockDim.x) {
+    const u64 v = over[i] & kValueMask;
+    if (i > ob && (over[i - 1] & kValueMask) == v) continue;
+    add(v, run_end(over, i, oe, v) - i);
+  }
   const u64 ex = block_sum_u64(exact, s);
   const double fl = block_sum_f64((double)sum - (double)comp, s);
   return (double)ex + fl;

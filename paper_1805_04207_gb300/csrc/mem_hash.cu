@@ -21,6 +21,7 @@ namespace {
 constexpr int kScanT = 1024;
 constexpr int kScanI = 4;
 constexpr int kScanB = kScanT * kScanI;
+constexpr u32 kBigSeg = 16384;  // segments with at least this many events are split into chunks
 
 __global__ void __launch_bounds__(kScanT) k_sbt_reduce(const u32* cnt, u64 len, u32* bsum, const u32* gate,
                                                       u32 want) {
@@ -86,21 +87,24 @@ __global__ void __launch_bounds__(kScanT) k_sbt_top(u32* bsum, u32 nb, const u32
   }
 }
 
-// Offsets (exclusive) into off[] and cur[]; the occupied slots are appended
-// to `used_list` (in no particular order) and counted in *n_used.
+// Offsets (exclusive) into off[] and cur[]. Occupied slots are listed (in no
+// particular order): those with fewer than kBigSeg events from the front of
+// used_list (count in n_used[0]), the others from the back (n_used[1]).
 __global__ void __launch_bounds__(kScanT) k_sbt_down(const u32* cnt, u64 len, const u32* bsum, u32* off, u32* cur,
                                                     u64* n_used, u32* used_list, const u32* gate, u32 want) {
   if (!gate_open(gate, want)) return;
   __shared__ u32 wt[33];
   __shared__ u32 wt2[33];
-  __shared__ u64 s_base;
+  __shared__ u32 wt3[33];
+  __shared__ u64 s_base, b_base;
   const u64 base = (u64)blockIdx.x * kScanB + (u64)threadIdx.x * kScanI;
-  u32 v[kScanI], s = 0, used = 0;
+  u32 v[kScanI], s = 0, small = 0, big = 0;
 #pragma unroll
   for (int k = 0; k < kScanI; ++k) {
     v[k] = base + k < len ? cnt[base + k] : 0u;
     s += v[k];
-    used += v[k] != 0u;
+    small += v[k] != 0u && v[k] < kBigSeg;
+    big += v[k] >= kBigSeg;
   }
   u32 tot;
   u32 ex = block_excl_u32(s, &tot, wt) + bsum[blockIdx.x];
@@ -112,21 +116,27 @@ __global__ void __launch_bounds__(kScanT) k_sbt_down(const u32* cnt, u64 len, co
     }
     ex += v[k];
   }
-  u32 utot;
-  u32 uex = block_excl_u32(used, &utot, wt2);
-  if (threadIdx.x == 0) s_base = utot ? atomicAdd(n_used, (u64)utot) : 0ull;
+  u32 stot, btot;
+  const u32 sex = block_excl_u32(small, &stot, wt2);
+  const u32 bex = block_excl_u32(big, &btot, wt3);
+  if (threadIdx.x == 0) {
+    s_base = stot ? atomicAdd(&n_used[0], (u64)stot) : 0ull;
+    b_base = btot ? atomicAdd(&n_used[1], (u64)btot) : 0ull;
+  }
   __syncthreads();
-  u64 p = s_base + uex;
+  u64 ps = s_base + sex, pb = b_base + bex;
 #pragma unroll
-  for (int k = 0; k < kScanI; ++k)
-    if (v[k]) used_list[p++] = (u32)(base + k);
+  for (int k = 0; k < kScanI; ++k) {
+    if (v[k] != 0u && v[k] < kBigSeg) used_list[ps++] = (u32)(base + k);
+    else if (v[k] >= kBigSeg) used_list[len - 1 - pb++] = (u32)(base + k);
+  }
 }
 
 constexpr int kScThreads = 256;
-constexpr int kScItems = 16;
+constexpr int kScItems = 8;
 
 // Scatter each event's low 12 bits into its superblock's segment.
-__global__ void __launch_bounds__(kScThreads) k_mem_scatter(HashArgs a) {
+__global__ void __launch_bounds__(kScThreads, 4) k_mem_scatter(HashArgs a) {
   if (!gate_open(a.gate, a.gate_want)) return;
   const u64 n = umin64(a.arena->st.n_words, a.n_cap);
   const int lane = threadIdx.x & 31;
@@ -200,31 +210,47 @@ __global__ void __launch_bounds__(kRbThreads) k_rebuild_words(const u32* slotw, 
   }
 }
 
-constexpr int kSgThreads = 256;
 constexpr int kCocSmem = 256;  // group sizes below this are counted in shared memory
 
-// Adds `times` groups of size c at skip level `lev`: shared bins below
-// kCocSmem, global dense bins below kCocDense, the overflow list above.
-__device__ __forceinline__ void emit_n(u32 (*coc)[kCocSmem], int lev, u32 c, u32 times, const HashArgs& a) {
+// Adds `times` groups of size c at skip levels lo..lev (lo < lev only when the
+// low address bits are all zero, so that those levels group identically):
+// shared bins below kCocSmem (level lev only: the block copies that row to
+// levels lo..lev when it flushes), global dense bins below kCocDense, the
+// overflow list above (one entry per group, reserved with a single atomic).
+__device__ __forceinline__ void emit_n(u32 (*coc)[kCocSmem], int lo, int lev, u32 c, u32 times, const HashArgs& a) {
   if (c == 0u || times == 0u) return;
-  if (c < (u32)kCocSmem) atomicAdd(&coc[lev][c], times);
-  else if (c < (u32)kCocDense) atomicAdd(&a.arena->mem_coc[lev][c], (u64)times);
-  else
-    for (u32 t = 0; t < times; ++t) overflow_append(a.over, a.over_cap, &a.arena->st, lev, c);
+  if (c < (u32)kCocSmem) {
+    atomicAdd(&coc[lev][c], times);
+    return;
+  }
+  for (int l = lo; l <= lev; ++l) {
+    if (c < (u32)kCocDense) {
+      atomicAdd(&a.arena->mem_coc[l][c], (u64)times);
+    } else {
+      DevState* st = &a.arena->st;
+      const u64 e = ((u64)l << 56) | ((u64)c & kValueMask);
+      const u64 idx = atomicAdd(&st->n_over, (u64)times);
+      for (u32 t = 0; t < times && idx + t < a.over_cap; ++t) a.over[idx + t] = e;
+      if (idx + times > a.over_cap) atomicOr(&st->err, kErrOverflow);
+      atomicOr(&st->over_or, e);
+      atomicAnd(&st->over_and, e);
+    }
+  }
 }
 
 // Emits this thread's K group sizes of one level: equal neighbours are
 // merged first, and when every lane of the warp holds K copies of one size
 // the warp adds them with a single atomic. All 32 lanes must call it.
 template <int K>
-__device__ __forceinline__ void emit_level(u32 (*coc)[kCocSmem], int lev, const u32 (&c)[K], const HashArgs& a) {
+__device__ __forceinline__ void emit_level(u32 (*coc)[kCocSmem], int lo, int lev, const u32 (&c)[K],
+                                           const HashArgs& a) {
   const int lane = threadIdx.x & 31;
   bool same = true;
 #pragma unroll
   for (int k = 1; k < K; ++k) same &= c[k] == c[0];
   const u32 c0 = __shfl_sync(0xffffffffu, c[0], 0);
   if (__all_sync(0xffffffffu, same && c[0] == c0)) {
-    if (lane == 0) emit_n(coc, lev, c0, 32u * K, a);
+    if (lane == 0) emit_n(coc, lo, lev, c0, 32u * K, a);
     return;
   }
   u32 cur = c[0], run = 1;
@@ -233,100 +259,264 @@ __device__ __forceinline__ void emit_level(u32 (*coc)[kCocSmem], int lev, const 
     if (c[k] == cur) {
       ++run;
     } else {
-      emit_n(coc, lev, cur, run, a);
+      emit_n(coc, lo, lev, cur, run, a);
       cur = c[k];
       run = 1;
     }
   }
-  emit_n(coc, lev, cur, run, a);
+  emit_n(coc, lo, lev, cur, run, a);
 }
 
-// One block per superblock segment at a time (grid-stride over the occupied slots).
-__global__ void __launch_bounds__(kSgThreads) k_mem_segments(HashArgs a) {
-  if (!gate_open(a.gate, a.gate_want)) return;
-  __shared__ __align__(16) u32 hist[4096];
-  __shared__ u32 coc[kLevels][kCocSmem];
-  __shared__ u32 wsum[kSgThreads / 32];
-  __shared__ u64 red64[32];
-  DevState* st = &a.arena->st;
-  for (int i = threadIdx.x; i < kLevels * kCocSmem; i += kSgThreads) (&coc[0][0])[i] = 0u;
-  for (int i = threadIdx.x; i < 4096; i += kSgThreads) hist[i] = 0u;
-  __syncthreads();
+// Segment geometry when the S low address bits of every event are zero: a
+// superblock (2048 addresses) holds NA = 2048 >> S possible addresses; T =
+// NA / 8 threads walk it, 8 consecutive ones each. Compressed level k (groups
+// of 2^k possible addresses) is skip level S + k, and skip levels 0..S group
+// exactly like level S.
+template <int S>
+struct SegShape {
+  static constexpr int NA = 2048 >> S;
+  static constexpr int T = NA / 8;
+  static constexpr int W = T / 32;
+};
+
+// Walks one superblock histogram (reads in [0, NA), writes in [NA, 2 NA),
+// compressed address order; shared or global memory) and emits the group
+// sizes of every skip level. Called by all THREADS threads of the block; the
+// first T walk. The caller synchronises before wsum or hist is reused.
+template <int S, int THREADS>
+__device__ __forceinline__ void walk_superblock(const u32* hist, u32 (*coc)[kCocSmem], u32* wsum, const HashArgs& a,
+                                                u64& fp, u64& ur, u64& uw) {
+  using Sh = SegShape<S>;
+  constexpr int NA = Sh::NA, T = Sh::T, W = Sh::W;
+  constexpr int KMAX = 10 - S;  // highest compressed level
+  static_assert(THREADS >= T && THREADS % 32 == 0, "block too small for the walk");
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  u64 fp = 0, ur = 0, uw = 0;
-  const u64 n_used = umin64(*a.n_used, a.tab.mask + 1);
-  for (u64 u = blockIdx.x; u < n_used; u += gridDim.x) {
-    const u32 s = a.used_list[u];
-    const u32 cnt = a.tab.cnt[s];
-    const u32 off = a.tab.off[s];
-    const uint16_t* seg = a.low + off;
-    for (u32 j = threadIdx.x; j < cnt; j += kSgThreads) atomicAdd(&hist[seg[j]], 1u);
-    __syncthreads();
-    // thread t owns addresses 8t .. 8t+7 (bins 16t .. 16t+15: read, write pairs)
+  if (threadIdx.x < T) {
+    // thread t owns compressed addresses 8t .. 8t+7
+    const uint4* hr = reinterpret_cast<const uint4*>(hist + 8 * threadIdx.x);
+    const uint4* hw = reinterpret_cast<const uint4*>(hist + NA + 8 * threadIdx.x);
+    const uint4 r0 = hr[0], r1 = hr[1], w0 = hw[0], w1 = hw[1];
+    const u32 rd[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+    const u32 wr[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
     u32 c0[8];
-    const uint4* hv = reinterpret_cast<const uint4*>(hist + 16 * threadIdx.x);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint4 v = hv[q];
-      c0[2 * q] = v.x + v.y;
-      c0[2 * q + 1] = v.z + v.w;
-      fp += (v.x + v.y != 0u) + (v.z + v.w != 0u);
-      ur += (v.x != 0u) + (v.z != 0u);
-      uw += (v.y != 0u) + (v.w != 0u);
+    for (int j = 0; j < 8; ++j) {
+      c0[j] = rd[j] + wr[j];
+      fp += c0[j] != 0u;
+      ur += rd[j] != 0u;
+      uw += wr[j] != 0u;
     }
-    emit_level<8>(coc, 0, c0, a);
+    emit_level<8>(coc, 0, S, c0, a);
     u32 c1[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) c1[k] = c0[2 * k] + c0[2 * k + 1];
-    emit_level<4>(coc, 1, c1, a);
-    u32 c2[2] = {c1[0] + c1[1], c1[2] + c1[3]};
-    emit_level<2>(coc, 2, c2, a);
+    emit_level<4>(coc, S + 1, S + 1, c1, a);
+    const u32 c2[2] = {c1[0] + c1[1], c1[2] + c1[3]};
+    emit_level<2>(coc, S + 2, S + 2, c2, a);
     u32 g = c2[0] + c2[1];
     {
       const u32 c3[1] = {g};
-      emit_level<1>(coc, 3, c3, a);
+      emit_level<1>(coc, S + 3, S + 3, c3, a);
     }
-    // levels 4..8: pairs, quads, ... of threads inside the warp; the group's
-    // first lane holds the sum, the others emit nothing
+    // compressed levels 4..8: pairs, quads, ... of threads inside the warp;
+    // the group's first lane holds the sum
 #pragma unroll
-    for (int lev = 4; lev <= 8; ++lev) {
-      const int span = 1 << (lev - 3);  // threads per group
+    for (int k = 4; k <= 8; ++k) {
+      if (k > KMAX) break;
+      const int span = 1 << (k - 3);  // threads per group
       g += __shfl_xor_sync(0xffffffffu, g, span >> 1);
-      if ((lane & (span - 1)) == 0) emit_n(coc, lev, g, 1u, a);
+      if ((lane & (span - 1)) == 0) emit_n(coc, S + k, S + k, g, 1u, a);
     }
-    if (lane == 0) wsum[wp] = g;  // 256 addresses per warp
-    __syncthreads();
-    if (threadIdx.x < 4) emit_n(coc, 9, wsum[2 * threadIdx.x] + wsum[2 * threadIdx.x + 1], 1u, a);
-    if (threadIdx.x < 2)
-      emit_n(coc, 10, wsum[4 * threadIdx.x] + wsum[4 * threadIdx.x + 1] + wsum[4 * threadIdx.x + 2] +
-                          wsum[4 * threadIdx.x + 3], 1u, a);
-    // clear the bins this segment touched (all of them when it is large)
-    if (cnt >= 2048) {
-      for (int i = threadIdx.x; i < 4096; i += kSgThreads) hist[i] = 0u;
-    } else {
-      for (u32 j = threadIdx.x; j < cnt; j += kSgThreads) hist[seg[j]] = 0u;
-    }
-    __syncthreads();
+    if (W > 1 && lane == 0) wsum[wp] = g;  // 256 possible addresses per warp
   }
-  for (int i = threadIdx.x; i < kLevels * kCocSmem; i += kSgThreads) {
+  __syncthreads();
+  // compressed levels 9 and 10: pairs and quads of warps
+  if (KMAX >= 9 && threadIdx.x < W / 2)
+    emit_n(coc, S + 9, S + 9, wsum[2 * threadIdx.x] + wsum[2 * threadIdx.x + 1], 1u, a);
+  if (KMAX >= 10 && threadIdx.x < W / 4)
+    emit_n(coc, 10, 10, wsum[4 * threadIdx.x] + wsum[4 * threadIdx.x + 1] + wsum[4 * threadIdx.x + 2] +
+                           wsum[4 * threadIdx.x + 3], 1u, a);
+}
+
+// End of a walking block: shared count-of-counts to the arena (the level-S
+// row also counts for levels 0..S-1) and the footprint counters.
+template <int S>
+__device__ __forceinline__ void flush_walks(u32 (*coc)[kCocSmem], u64 fp, u64 ur, u64 uw, u64* red64,
+                                            const HashArgs& a) {
+  __syncthreads();
+  for (int i = threadIdx.x; i < kLevels * kCocSmem; i += blockDim.x) {
     const u32 c = (&coc[0][0])[i];
-    if (c) atomicAdd(&a.arena->mem_coc[i / kCocSmem][i % kCocSmem], (u64)c);
+    const int lev = i / kCocSmem, bin = i % kCocSmem;
+    if (c)
+      for (int l = (lev == S ? 0 : lev); l <= lev; ++l) atomicAdd(&a.arena->mem_coc[l][bin], (u64)c);
   }
   fp = block_reduce(fp, OpAdd(), 0ull, red64);
   ur = block_reduce(ur, OpAdd(), 0ull, red64);
   uw = block_reduce(uw, OpAdd(), 0ull, red64);
   if (threadIdx.x == 0) {
+    DevState* st = &a.arena->st;
     if (fp) atomicAdd(&st->footprint, fp);
     if (ur) atomicAdd(&st->unique_reads, ur);
     if (uw) atomicAdd(&st->unique_writes, uw);
   }
 }
 
+template <int S>
+__device__ __forceinline__ u32 hist_index(u32 v) {
+  return (v & 1u) * (u32)SegShape<S>::NA + ((v >> 1) >> S);
+}
+
+// Adds the events seg[b0, b1) to a shared histogram, THREADS at a time.
+template <int S, int THREADS>
+__device__ __forceinline__ void fill_hist(u32* hist, const uint16_t* seg, u32 b0, u32 b1) {
+  u32 j = b0 + threadIdx.x;
+  for (; j + 3 * THREADS < b1; j += 4 * THREADS) {
+    u32 v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = seg[j + q * THREADS];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) atomicAdd(&hist[hist_index<S>(v[q])], 1u);
+  }
+  for (; j < b1; j += THREADS) atomicAdd(&hist[hist_index<S>(seg[j])], 1u);
+}
+
+// Small segments (fewer than kBigSeg events): one block of T threads per
+// segment at a time, grid-stride over the front of the used list.
+template <int S>
+__global__ void __launch_bounds__(SegShape<S>::T) k_mem_segments(HashArgs a) {
+  constexpr int NA = SegShape<S>::NA, T = SegShape<S>::T;
+  if (!gate_open(a.gate, a.gate_want)) return;
+  __shared__ __align__(16) u32 hist[2 * NA];
+  __shared__ u32 coc[kLevels][kCocSmem];
+  __shared__ u32 wsum[8];
+  __shared__ u64 red64[32];
+  for (int i = threadIdx.x; i < kLevels * kCocSmem; i += T) (&coc[0][0])[i] = 0u;
+  for (int i = threadIdx.x; i < 2 * NA; i += T) hist[i] = 0u;
+  __syncthreads();
+  u64 fp = 0, ur = 0, uw = 0;
+  const u64 n_list = umin64(a.n_used[0], a.tab.mask + 1);
+  for (u64 u = blockIdx.x; u < n_list; u += gridDim.x) {
+    const u32 s = a.used_list[u];
+    const u32 cnt = a.tab.cnt[s];
+    const uint16_t* seg = a.low + a.tab.off[s];
+    fill_hist<S, T>(hist, seg, 0u, cnt);
+    __syncthreads();
+    walk_superblock<S, T>(hist, coc, wsum, a, fp, ur, uw);
+    // clear the bins this segment touched (all of them when it is large)
+    if (cnt >= (u32)NA) {
+      for (int i = threadIdx.x; i < 2 * NA; i += T) hist[i] = 0u;
+    } else {
+      for (u32 j = threadIdx.x; j < cnt; j += T) hist[hist_index<S>(seg[j])] = 0u;
+    }
+    __syncthreads();
+  }
+  flush_walks<S>(coc, fp, ur, uw, red64, a);
+}
+
+constexpr int kBfThreads = 256;
+constexpr u32 kChunk = 4096;  // events per work item of a wide segment
+
+// Wide segments (kBigSeg events or more, at the back of the used list):
+// their events are cut into chunks of kChunk, dealt round-robin to all
+// blocks; each block adds its chunk's histogram to the segment's global
+// histogram in big_hist (zeroed beforehand, 2 NA words per wide segment).
+template <int S>
+__global__ void __launch_bounds__(kBfThreads) k_mem_big_fill(HashArgs a) {
+  constexpr int NA = SegShape<S>::NA;
+  if (!gate_open(a.gate, a.gate_want)) return;
+  __shared__ __align__(16) u32 hist[2 * NA];
+  __shared__ u32 m_off[kBfThreads], m_cnt[kBfThreads], m_pre[kBfThreads];
+  __shared__ u32 wt[33];
+  for (int i = threadIdx.x; i < 2 * NA; i += kBfThreads) hist[i] = 0u;
+  const u64 C = a.tab.mask + 1;
+  const u64 n_big = umin64(umin64(a.n_used[1], C), a.big_cap);
+  const u64 G = gridDim.x;
+  u64 qbase = 0;  // chunks in earlier batches
+  for (u64 i0 = 0; i0 < n_big; i0 += kBfThreads) {
+    const u64 i = i0 + threadIdx.x;
+    u32 nch = 0;
+    __syncthreads();  // the previous batch's entries are no longer read
+    if (i < n_big) {
+      const u32 s = a.used_list[C - 1 - i];
+      const u32 cnt = a.tab.cnt[s];
+      m_off[threadIdx.x] = a.tab.off[s];
+      m_cnt[threadIdx.x] = cnt;
+      nch = (cnt + kChunk - 1) / kChunk;
+    }
+    u32 tot;
+    m_pre[threadIdx.x] = block_excl_u32(nch, &tot, wt);
+    __syncthreads();
+    const u32 nvalid = (u32)umin64(n_big - i0, (u64)kBfThreads);
+    // this block takes the batch's chunks q with (qbase + q) % G == blockIdx.x
+    for (u64 q = (blockIdx.x + G - qbase % G) % G; q < tot; q += G) {
+      u32 lo = 0, hi = nvalid - 1;  // last entry whose first chunk is <= q
+      while (lo < hi) {
+        const u32 mid = (lo + hi + 1) >> 1;
+        if (m_pre[mid] <= q) lo = mid; else hi = mid - 1;
+      }
+      const u32 b0 = (u32)(q - m_pre[lo]) * kChunk;
+      const u32 b1 = min(m_cnt[lo], b0 + kChunk);
+      fill_hist<S, kBfThreads>(hist, a.low + m_off[lo], b0, b1);
+      __syncthreads();
+      u32* gh = a.big_hist + (i0 + lo) * (u64)(2 * NA);
+      for (int k = threadIdx.x; k < 2 * NA; k += kBfThreads) {
+        const u32 v = hist[k];
+        if (v) {
+          atomicAdd(&gh[k], v);
+          hist[k] = 0u;
+        }
+      }
+      __syncthreads();
+    }
+    qbase += tot;
+  }
+}
+
+// Walks the global histogram of every wide segment (grid-stride).
+template <int S>
+__global__ void __launch_bounds__(SegShape<S>::T) k_mem_big_walk(HashArgs a) {
+  constexpr int NA = SegShape<S>::NA, T = SegShape<S>::T;
+  if (!gate_open(a.gate, a.gate_want)) return;
+  __shared__ u32 coc[kLevels][kCocSmem];
+  __shared__ u32 wsum[8];
+  __shared__ u64 red64[32];
+  for (int i = threadIdx.x; i < kLevels * kCocSmem; i += T) (&coc[0][0])[i] = 0u;
+  __syncthreads();
+  u64 fp = 0, ur = 0, uw = 0;
+  const u64 n_big = umin64(umin64(a.n_used[1], a.tab.mask + 1), a.big_cap);
+  if (blockIdx.x == 0 && threadIdx.x == 0 && a.n_used[1] > a.big_cap) atomicOr(&a.arena->st.err, kErrOverflow);
+  for (u64 i = blockIdx.x; i < n_big; i += gridDim.x) {
+    walk_superblock<S, T>(a.big_hist + i * (u64)(2 * NA), coc, wsum, a, fp, ur, uw);
+    __syncthreads();
+  }
+  flush_walks<S>(coc, fp, ur, uw, red64, a);
+}
+
+template <typename K>
+int resident_blocks(K kernel, int threads) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  return per_sm < 1 ? 1 : per_sm;
+}
+
+template <int S>
+void launch_segments_shift(const HashArgs& a, cudaStream_t s) {
+  constexpr int T = SegShape<S>::T;
+  const int sm = a.sm_count;
+  k_mem_big_fill<S><<<sm * resident_blocks(k_mem_big_fill<S>, kBfThreads), kBfThreads, 0, s>>>(a);
+  k_mem_big_walk<S><<<sm * 2, T, 0, s>>>(a);
+  k_mem_segments<S><<<sm * resident_blocks(k_mem_segments<S>, T), T, 0, s>>>(a);
+  count_launches(3);
+}
+
 }  // namespace
 
 size_t sbt_scan_words(u64 cap) { return (size_t)((cap + kScanB - 1) / kScanB + 1); }
 
-void launch_mem_hash(const HashArgs& a, cudaStream_t s) {
+void launch_mem_hash_scatter(const HashArgs& a, cudaStream_t s) {
   const u64 C = a.tab.mask + 1;
   const u32 nb = (u32)((C + kScanB - 1) / kScanB);
   k_sbt_reduce<<<nb, kScanT, 0, s>>>(a.tab.cnt, C, a.scan_tmp, a.gate, a.gate_want);
@@ -334,8 +524,27 @@ void launch_mem_hash(const HashArgs& a, cudaStream_t s) {
   k_sbt_down<<<nb, kScanT, 0, s>>>(a.tab.cnt, C, a.scan_tmp, a.tab.off, a.tab.cur, a.n_used, a.used_list, a.gate,
                                    a.gate_want);
   k_mem_scatter<<<a.grid_scatter, kScThreads, 0, s>>>(a);
-  k_mem_segments<<<a.grid_segments, kSgThreads, 0, s>>>(a);
-  count_launches(5);
+  count_launches(4);
+}
+
+u64 mem_hash_big_segments(u64 n_words, size_t bytes, int seg_shift) {
+  const u64 per = 2ull * (u64)(2048 >> seg_shift) * 4;
+  return std::min<u64>(n_words / kBigSeg, bytes / per);
+}
+
+void launch_mem_hash_segments(const HashArgs& a, cudaStream_t s) {
+  if (a.big_cap) cudaMemsetAsync(a.big_hist, 0, a.big_cap * 2ull * (u64)(2048 >> a.seg_shift) * 4, s);
+  switch (a.seg_shift) {
+    case 1: launch_segments_shift<1>(a, s); break;
+    case 2: launch_segments_shift<2>(a, s); break;
+    case 3: launch_segments_shift<3>(a, s); break;
+    default: launch_segments_shift<0>(a, s); break;
+  }
+}
+
+void launch_mem_hash(const HashArgs& a, cudaStream_t s) {
+  launch_mem_hash_scatter(a, s);
+  launch_mem_hash_segments(a, s);
 }
 
 void launch_rebuild_words(const u32* slotw, SbTable tab, u64* words, Arena* arena, int grid, cudaStream_t s,

@@ -38,7 +38,9 @@ constexpr size_t kCountsWords = 256 * ((kNoAllocOverCap + 2047) / 2048);  // sor
 constexpr size_t kOffCounts = kOffOverB + a256(8 * kNoAllocOverCap);
 constexpr size_t kOffBsums = kOffCounts + a256(4 * kCountsWords);
 constexpr size_t kOffBitmap = kOffBsums + a256(4 * (kCountsWords / 4096 + 2));
-constexpr size_t kNoAllocBytes = kOffBitmap + a256(kNoAllocMaxWi / 8);
+constexpr size_t kOffBig = kOffBitmap + a256(kNoAllocMaxWi / 8);
+constexpr size_t kNoAllocBigBytes = (kNoAllocMaxEvents / 16384) * 2 * 2048 * 4;  // wide-segment histograms
+constexpr size_t kNoAllocBytes = kOffBig + a256(kNoAllocBigBytes);
 
 static_assert(kNoAllocBytes <= (32ull << 20), "the no-allocation scratch must stay modest");
 
@@ -135,13 +137,16 @@ extern "C" aiwc_status aiwc_mem_metrics_noalloc(int device, void* cuda_stream, c
   ha.low = (uint16_t*)(p + kOffLow);
   ha.tab = tab;
   ha.scan_tmp = (u32*)(p + kOffScan);
-  ha.n_used = &arena->st.sb_used;
+  ha.n_used = arena->st.sb_used;
   ha.used_list = used_list;
   ha.over = over_a;
   ha.over_cap = kNoAllocOverCap;
   ha.arena = arena;
   ha.grid_scatter = 152 * 2;
-  ha.grid_segments = 152 * 4;
+  ha.sm_count = 152;
+  ha.seg_shift = 0;  // the event alignment is not read back: the general layout
+  ha.big_hist = (u32*)(p + kOffBig);
+  ha.big_cap = mem_hash_big_segments(n, kNoAllocBigBytes, 0);
   launch_mem_hash(ha, s);
   launch_wi_count(bitmap, arena, s);
   SortDesc d;

@@ -155,6 +155,24 @@ def test_all_distinct_addresses(P, plan):
     assert_parity(run_gpu(P, tr, plan=plan), oracle.compute(tr))
 
 
+@pytest.mark.parametrize("shift", [0, 1, 2, 3, 4])
+def test_address_alignment_shifts(P, shift):
+    """Every address a multiple of 2^shift: the hash plan walks superblocks in
+    compressed form and copies the lowest skip levels; segments span few
+    events, a few hundred, and (one hot superblock) more than 2^14."""
+    rng = np.random.default_rng(100 + shift)
+    n_wide, n_hot = 250_000, 40_000
+    idx = np.concatenate([rng.integers(0, 1 << 17, n_wide),                      # spread over many superblocks
+                          (1 << 20) + rng.integers(0, 2048 >> min(shift, 3), n_hot),  # one hot superblock
+                          rng.zipf(1.3, 30_000) % (1 << 12)])                      # heavy repeats
+    addr = (idx.astype(np.int64) << shift) + (5 << 33)
+    n = addr.shape[0]
+    perm = rng.permutation(n)
+    tr = mem_only(addr[perm].tolist(), stores=(rng.random(n) < 0.3).astype(np.int64).tolist(),
+                  spaces=rng.integers(0, 2, n).tolist())
+    assert_parity(run_gpu(P, tr, plan=0, table_slots=1 << 16), oracle.compute(tr))
+
+
 def test_value_overflow_paths(P):
     # ITB/IPT values above the shared (2048) and dense (65536) bins, opcode
     # counts above 1024, and work-items with many runs.

@@ -161,7 +161,7 @@ constexpr u64 kMaxHashSlots = 1ull << 20;   // slot words hold 20 slot bits
 struct MemIngestArgs {
   SbTable tab{};       // used when use_tab (hash plan)
   int use_tab{};
-  u32* slotw{};          // hash plan: out, 32-bit slot words
+  u64* slotw{};          // hash plan: out, slot word (low 32 bits) | rank of the event in its superblock << 32
   u64* spill{};          // hash plan: out, full words of events the table could not place
   const void* ev{};
   u64 n{};
@@ -193,7 +193,7 @@ void launch_mem_levels(const LevelArgs& a, cudaStream_t s);
 struct HashArgs {
   const u32* gate{};   // run only when !gate || *gate == gate_want (device-side plan choice)
   u32 gate_want{};
-  const u32* slotw{};    // slot words from the ingest
+  const u64* slotw{};    // slot words | ranks << 32 from the ingest
   u64 n_cap{};           // capacity of slotw / low, in elements
   uint16_t* low{};       // out: low 12 bits grouped by superblock
   SbTable tab{};
@@ -217,7 +217,7 @@ void launch_mem_hash_segments(const HashArgs& a, cudaStream_t s);  // per-segmen
 u64 mem_hash_big_segments(u64 n_words, size_t bytes, int seg_shift);
 // Fallback after a table overflow: rebuild the 64-bit sort words from the
 // slot words and the table, after the n_spill spilled words already in words[].
-void launch_rebuild_words(const u32* slotw, SbTable tab, u64* words, Arena* arena, int grid, cudaStream_t s,
+void launch_rebuild_words(const u64* slotw, SbTable tab, u64* words, Arena* arena, int grid, cudaStream_t s,
                           const u32* gate = nullptr, u32 gate_want = 0);
 
 struct BranchIngestArgs {

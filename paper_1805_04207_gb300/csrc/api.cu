@@ -511,9 +511,9 @@ aiwc_status aiwc_push_mem(aiwc_handle* h, const aiwc_mem_event* ev, size_t n, in
   MemIngestArgs a;
   a.use_tab = use_hash(h) && h->sbt_cap ? 1 : 0;
   if (a.use_tab) {
-    ENSURE(h->mem_b, (h->n_mem + n) * 4, true);  // slot words
+    ENSURE(h->mem_b, (h->n_mem + n) * 8, true);  // slot words and ranks
     a.tab = table_view(h);
-    a.slotw = (u32*)h->mem_b.p;
+    a.slotw = (u64*)h->mem_b.p;
     a.spill = (u64*)h->mem_a.p;
   }
   a.space_mask = h->cfg.space_mask;
@@ -745,7 +745,7 @@ aiwc_status prepare(aiwc_handle* h) {
   const u64 nmax = std::max(std::max(n_mem, n_br), std::max(n_runs, h->c_over_cap));
   ENSURE(h->mem_a, std::max<u64>(n_mem, 1) * 8, true);
   ENSURE(h->mem_b, std::max<u64>(n_mem, 1) * 8, true);  // holds the slot words of the hash plan
-  h->c_low_off = ((size_t)n_mem * 4 + 255) & ~size_t(255);
+  h->c_low_off = ((size_t)n_mem * 8 + 255) & ~size_t(255);
   ENSURE(h->mem_b, h->c_low_off + (size_t)n_mem * 2, true);
   ENSURE(h->br_a, std::max<u64>(n_br, 1) * 8, true);
   ENSURE(h->br_b, std::max<u64>(n_br, 1) * 8, false);
@@ -828,11 +828,11 @@ aiwc_status enqueue_part2(aiwc_handle* h, cudaStream_t st, const Plan& p) {
   const bool ran_hash = n_mem && use_hash(h) && h->sbt_cap;
   if (ran_hash && !p.hash_ok) {
     // the table overflowed: rebuild 64-bit words behind the spilled ones, then sort
-    launch_rebuild_words((const u32*)h->mem_b.p, table_view(h), (u64*)h->mem_a.p, h->arena, grid * 2, st);
+    launch_rebuild_words((const u64*)h->mem_b.p, table_view(h), (u64*)h->mem_a.p, h->arena, grid * 2, st);
   }
   if (n_mem && p.hash_ok) {
     HashArgs ha;
-    ha.slotw = (const u32*)h->mem_b.p;
+    ha.slotw = (const u64*)h->mem_b.p;
     ha.n_cap = std::min<u64>(n_mem, (h->mem_b.cap - h->c_low_off) / 2);
     ha.low = (uint16_t*)((char*)h->mem_b.p + h->c_low_off);
     ha.tab = table_view(h);

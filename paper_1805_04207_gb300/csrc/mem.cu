@@ -17,11 +17,13 @@ constexpr int kIngestThreads = 256;
 
 // One pass over the 16-byte events. Sort plan (HASH = false): writes the
 // 64-bit sort word of every kept event. Hash plan (HASH = true): places the
-// event's superblock (word >> 12) in the table, counts it there and writes a
-// 32-bit slot word (slot << 12) | (word & 0xFFF) -- the table keeps the
-// superblock, so the word can be rebuilt from the slot word. An event the
-// table cannot place gets the sentinel slot word and its full word goes to
-// the spill list. FILTER: the space mask drops events, so outputs are
+// event's superblock (word >> 12) in the table, counts it there and writes
+// the 32-bit slot word (slot << 12) | (word & 0xFFF) -- the table keeps the
+// superblock, so the word can be rebuilt from the slot word -- with, in the
+// high half, the event's rank among its superblock's events (the count
+// before it, from the same atomic), which is its place in the superblock's
+// segment. An event the table cannot place gets the sentinel slot word and
+// its full word goes to the spill list. FILTER: the space mask drops events, so outputs are
 // compacted behind one atomicAdd per block-tile.
 template <bool FILTER, bool HASH>
 __global__ void __launch_bounds__(kIngestThreads, HASH ? 4 : 3) k_mem_ingest(MemIngestArgs a) {
@@ -73,7 +75,7 @@ __global__ void __launch_bounds__(kIngestThreads, HASH ? 4 : 3) k_mem_ingest(Mem
       }
     }
     kept += nkeep;
-    u32 sw[ITEMS];
+    u64 sw[ITEMS];
     if (HASH) {
       // batch the home-slot loads, then resolve
       u64 pos[ITEMS], first[ITEMS];
@@ -84,20 +86,32 @@ __global__ void __launch_bounds__(kIngestThreads, HASH ? 4 : 3) k_mem_ingest(Mem
         // claimed; sbt_place then loses the CAS and reads the real key
         first[k] = keep[k] ? a.tab.keys[pos[k]] : 0ull;
       }
+      u32 slot[ITEMS];
 #pragma unroll
       for (int k = 0; k < ITEMS; ++k) {
-        u32 slot = kNoSlot;
+        slot[k] = kNoSlot;
         if (keep[k]) {
-          slot = sbt_place(a.tab, (word[k] >> 12) + 1ull, pos[k], first[k]);
-          if (slot == kNoSlot) {
+          slot[k] = sbt_place(a.tab, (word[k] >> 12) + 1ull, pos[k], first[k]);
+          if (slot[k] == kNoSlot) {
             sbt_fail = 1u;
             a.spill[atomicAdd(&st->n_spill, 1ull)] = word[k];
           }
         }
-        const bool v = slot != kNoSlot;
-        const u32 peers = __match_any_sync(0xffffffffu, v ? slot : (0xFFFFFFE0u | (u32)lane));
-        if (v && lane == __ffs(peers) - 1) atomicAdd(&a.tab.cnt[slot], (u32)__popc(peers));
-        sw[k] = v ? ((slot << 12) | (u32)(word[k] & 0xFFFull)) : kSlotWordNone;
+      }
+      // all counting atomics in flight before any result is needed
+      u32 peers[ITEMS], rb[ITEMS];
+#pragma unroll
+      for (int k = 0; k < ITEMS; ++k)
+        peers[k] = __match_any_sync(0xffffffffu, slot[k] != kNoSlot ? slot[k] : (0xFFFFFFE0u | (u32)lane));
+#pragma unroll
+      for (int k = 0; k < ITEMS; ++k) {
+        rb[k] = 0u;
+        if (slot[k] != kNoSlot && lane == __ffs(peers[k]) - 1) rb[k] = atomicAdd(&a.tab.cnt[slot[k]], (u32)__popc(peers[k]));
+      }
+#pragma unroll
+      for (int k = 0; k < ITEMS; ++k) {
+        const u32 r = __shfl_sync(0xffffffffu, rb[k], __ffs(peers[k]) - 1) + (u32)__popc(peers[k] & ((1u << lane) - 1u));
+        sw[k] = slot[k] != kNoSlot ? (((u64)r << 32) | (slot[k] << 12) | (u32)(word[k] & 0xFFFull)) : (u64)kSlotWordNone;
       }
     }
     if (FILTER) {

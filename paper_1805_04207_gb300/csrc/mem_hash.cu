@@ -87,10 +87,10 @@ __global__ void __launch_bounds__(kScanT) k_sbt_top(u32* bsum, u32 nb, const u32
   }
 }
 
-// Offsets (exclusive) into off[] and cur[]. Occupied slots are listed (in no
+// Segment offsets (exclusive prefix of the counts) into off[]. Occupied slots are listed (in no
 // particular order): those with fewer than kBigSeg events from the front of
 // used_list (count in n_used[0]), the others from the back (n_used[1]).
-__global__ void __launch_bounds__(kScanT) k_sbt_down(const u32* cnt, u64 len, const u32* bsum, u32* off, u32* cur,
+__global__ void __launch_bounds__(kScanT) k_sbt_down(const u32* cnt, u64 len, const u32* bsum, u32* off,
                                                     u64* n_used, u32* used_list, const u32* gate, u32 want) {
   if (!gate_open(gate, want)) return;
   __shared__ u32 wt[33];
@@ -110,10 +110,7 @@ __global__ void __launch_bounds__(kScanT) k_sbt_down(const u32* cnt, u64 len, co
   u32 ex = block_excl_u32(s, &tot, wt) + bsum[blockIdx.x];
 #pragma unroll
   for (int k = 0; k < kScanI; ++k) {
-    if (base + k < len) {
-      off[base + k] = ex;
-      cur[base + k] = ex;
-    }
+    if (base + k < len) off[base + k] = ex;
     ex += v[k];
   }
   u32 stot, btot;
@@ -135,32 +132,29 @@ __global__ void __launch_bounds__(kScanT) k_sbt_down(const u32* cnt, u64 len, co
 constexpr int kScThreads = 256;
 constexpr int kScItems = 8;
 
-// Scatter each event's low 12 bits into its superblock's segment.
+// Scatter each event's low 12 bits into its superblock's segment, at the
+// segment's offset plus the event's rank from the ingest.
 __global__ void __launch_bounds__(kScThreads, 4) k_mem_scatter(HashArgs a) {
   if (!gate_open(a.gate, a.gate_want)) return;
   const u64 n = umin64(a.arena->st.n_words, a.n_cap);
-  const int lane = threadIdx.x & 31;
-  const u32 lt = (1u << lane) - 1u;
   const u64 per_block = (u64)kScThreads * kScItems;
   for (u64 t0 = (u64)blockIdx.x * per_block; t0 < n; t0 += (u64)gridDim.x * per_block) {
-    u32 sw[kScItems];
+    u64 sw[kScItems];
 #pragma unroll
     for (int k = 0; k < kScItems; ++k) {
       const u64 i = t0 + (u64)k * kScThreads + threadIdx.x;
-      sw[k] = i < n ? __ldcs(a.slotw + i) : kSlotWordNone;
+      sw[k] = i < n ? __ldcs(a.slotw + i) : (u64)kSlotWordNone;
     }
-    u32 peers[kScItems], base[kScItems];
+    u32 off[kScItems];
 #pragma unroll
     for (int k = 0; k < kScItems; ++k) {
-      const bool valid = sw[k] != kSlotWordNone;
-      peers[k] = __match_any_sync(0xffffffffu, valid ? (sw[k] >> 12) : (0xFFFFFFE0u | (u32)lane));
-      base[k] = 0;
-      if (valid && lane == __ffs(peers[k]) - 1) base[k] = atomicAdd(&a.tab.cur[sw[k] >> 12], (u32)__popc(peers[k]));
+      const u32 w = (u32)sw[k];
+      off[k] = w != kSlotWordNone ? __ldg(a.tab.off + (w >> 12)) : 0u;
     }
 #pragma unroll
     for (int k = 0; k < kScItems; ++k) {
-      const u32 b = __shfl_sync(0xffffffffu, base[k], __ffs(peers[k]) - 1);
-      if (sw[k] != kSlotWordNone) a.low[b + __popc(peers[k] & lt)] = (uint16_t)(sw[k] & 0xFFFu);
+      const u32 w = (u32)sw[k];
+      if (w != kSlotWordNone) a.low[off[k] + (u32)(sw[k] >> 32)] = (uint16_t)(w & 0xFFFu);
     }
   }
 }
@@ -170,7 +164,7 @@ constexpr int kRbItems = 8;
 
 // Sort-plan fallback: 64-bit words rebuilt from slot words and table keys,
 // appended after the spilled words (order is irrelevant to the sort).
-__global__ void __launch_bounds__(kRbThreads) k_rebuild_words(const u32* slotw, SbTable tab, u64* words,
+__global__ void __launch_bounds__(kRbThreads) k_rebuild_words(const u64* slotw, SbTable tab, u64* words,
                                                              Arena* arena, const u32* gate, u32 want) {
   if (!gate_open(gate, want)) return;
   __shared__ u32 scan_tot[33];
@@ -185,7 +179,7 @@ __global__ void __launch_bounds__(kRbThreads) k_rebuild_words(const u32* slotw, 
 #pragma unroll
     for (int k = 0; k < kRbItems; ++k) {
       const u64 i = t0 + (u64)k * kRbThreads + threadIdx.x;
-      sw[k] = i < n ? slotw[i] : kSlotWordNone;
+      sw[k] = i < n ? (u32)slotw[i] : kSlotWordNone;
       cnt += sw[k] != kSlotWordNone;
     }
     u32 inc = cnt;
@@ -521,7 +515,7 @@ void launch_mem_hash_scatter(const HashArgs& a, cudaStream_t s) {
   const u32 nb = (u32)((C + kScanB - 1) / kScanB);
   k_sbt_reduce<<<nb, kScanT, 0, s>>>(a.tab.cnt, C, a.scan_tmp, a.gate, a.gate_want);
   k_sbt_top<<<1, kScanT, 0, s>>>(a.scan_tmp, nb, a.gate, a.gate_want);
-  k_sbt_down<<<nb, kScanT, 0, s>>>(a.tab.cnt, C, a.scan_tmp, a.tab.off, a.tab.cur, a.n_used, a.used_list, a.gate,
+  k_sbt_down<<<nb, kScanT, 0, s>>>(a.tab.cnt, C, a.scan_tmp, a.tab.off, a.n_used, a.used_list, a.gate,
                                    a.gate_want);
   k_mem_scatter<<<a.grid_scatter, kScThreads, 0, s>>>(a);
   count_launches(4);
@@ -547,7 +541,7 @@ void launch_mem_hash(const HashArgs& a, cudaStream_t s) {
   launch_mem_hash_segments(a, s);
 }
 
-void launch_rebuild_words(const u32* slotw, SbTable tab, u64* words, Arena* arena, int grid, cudaStream_t s,
+void launch_rebuild_words(const u64* slotw, SbTable tab, u64* words, Arena* arena, int grid, cudaStream_t s,
                           const u32* gate, u32 gate_want) {
   k_rebuild_words<<<grid, kRbThreads, 0, s>>>(slotw, tab, words, arena, gate, gate_want);
   count_launches(1);

@@ -29,7 +29,7 @@ constexpr size_t kOffArena = 0;
 constexpr size_t kOffResult = kOffArena + a256(sizeof(Arena));
 constexpr size_t kOffWords = kOffResult + a256(sizeof(Result));
 constexpr size_t kOffSlot = kOffWords + a256(8 * kNoAllocMaxEvents);
-constexpr size_t kOffLow = kOffSlot + a256(4 * kNoAllocMaxEvents);
+constexpr size_t kOffLow = kOffSlot + a256(8 * kNoAllocMaxEvents);
 constexpr size_t kOffTable = kOffLow + a256(2 * kNoAllocMaxEvents);
 constexpr size_t kOffScan = kOffTable + a256(24 * kNoAllocSlots);
 constexpr size_t kOffOverA = kOffScan + a256(4 * (kNoAllocSlots / 4096 + 1));
@@ -118,7 +118,7 @@ extern "C" aiwc_status aiwc_mem_metrics_noalloc(int device, void* cuda_stream, c
   MemIngestArgs ia;
   ia.tab = tab;
   ia.use_tab = 1;
-  ia.slotw = (u32*)(p + kOffSlot);
+  ia.slotw = (u64*)(p + kOffSlot);
   ia.spill = (u64*)(p + kOffWords);
   ia.ev = events;
   ia.n = n;

@@ -277,7 +277,9 @@ def run_serving(args, P, torch, local, world, rank):
         while pending and pending[0]["arrival_s"] <= now:
             jb = pending[0]
             n_br = jb["n_mem"] // 4
-            reserve = 24 * jb["n_mem"] + 40 * n_br + (96 << 20)
+            # device bytes a handle holds: about 19 B per memory event, 33 B per branch event, plus
+            # fixed scratch (64 MB staging pair, table, work-item bitmap, arena)
+            reserve = 24 * jb["n_mem"] + 40 * n_br + (256 << 20)
             h = srv.open(reserve, n_opcodes=64, max_work_items=1 << 26, **plan_for(jb["n_mem"]))
             if h is None:
                 break

@@ -6,6 +6,8 @@
 
 #include <string>
 
+#include <cstddef>
+
 #include "aiwc.h"
 
 namespace aiwc {
@@ -104,10 +106,13 @@ struct Arena {
   u64 mem_coc[kLevels][kCocDense];   // m_c for group sizes c < kCocDense, per skip level
   u64 site_coc[kCocDense];
   u64 opc_coc[kCocDense];
-  u64 itb_dense[kValDense];
-  u64 ipt_dense[kValDense];
+  alignas(16) u64 itb_dense[kValDense];
+  alignas(16) u64 ipt_dense[kValDense];
   u64 tag_begin[kNumTags + 1];       // segment of each tag in the sorted overflow list
 };
+// the order statistics read the value bins 16 bytes at a time
+static_assert(offsetof(Arena, itb_dense) % 16 == 0 && offsetof(Arena, ipt_dense) % 16 == 0,
+              "value bins must be 16-byte aligned");
 
 struct Result {
   aiwc_metrics m;  // opcode_hist pointer unused on the device

@@ -178,49 +178,55 @@ __device__ u64 cover_walk(const u64* dense, int dense_n, const u64* over, u64 ob
   return kcount;
 }
 
-// k-th smallest (0-based) value of a value distribution: dense[v] values v
-// for v < dense_n, then the ascending overflow segment [ob, oe).
-__device__ u64 kth_value(const u64* dense, int dense_n, const u64* over, u64 ob, u64 oe, u64 k, Shared& s) {
-  // each thread owns a contiguous slice of bins
-  const int per = (dense_n + blockDim.x - 1) / blockDim.x;
-  const int b0 = threadIdx.x * per;
-  u64 mine = 0;
-  for (int v = b0; v < b0 + per && v < dense_n; ++v) mine += dense[v];
-  u64 inc, dummy, tot, dt;
-  block_scan2(mine, 0ull, &inc, &dummy, &tot, &dt, s);
-  if (threadIdx.x == 0) s.found = ~0ull;
-  __syncthreads();
-  if (k < tot) {
-    const u64 ex = inc - mine;
-    if (k >= ex && k < inc) {
-      u64 c = ex;
-      for (int v = b0; v < b0 + per && v < dense_n; ++v) {
-        c += dense[v];
-        if (k < c) { s.found = (u64)v; break; }
-      }
-    }
-  } else if (threadIdx.x == 0) {
-    const u64 j = k - tot;
-    s.found = ob + j < oe ? (over[ob + j] & kValueMask) : 0ull;
-  }
-  __syncthreads();
-  const u64 r = s.found;
-  __syncthreads();
-  return r;
-}
+// Order statistics of a value distribution: dense[v] values v for v <
+// kValDense, then the ascending overflow segment [ob, oe). Each thread owns
+// kPer consecutive bins; one pass sums them (independent loads), one block
+// scan places every thread's slice, and the threads whose slices hold the
+// wanted ranks find the values.
+constexpr int kPer = kValDense / kFinThreads;
+static_assert(kValDense % kFinThreads == 0, "bins must split evenly over the block");
 
 __device__ void order_stats(const u64* dense, const u64* over, u64 ob, u64 oe, u64* cnt, u64* mn, u64* mx, u64* lo,
                             u64* hi, double* med, Shared& s) {
-  u64 c = 0;
-  for (int v = threadIdx.x; v < kValDense; v += blockDim.x) c += dense[v];
-  c = block_sum_u64(c, s) + (oe - ob);
+  const int b0 = threadIdx.x * kPer;
+  const ulonglong2* d2 = reinterpret_cast<const ulonglong2*>(dense + b0);
+  u64 mine = 0;
+#pragma unroll 8
+  for (int q = 0; q < kPer / 2; ++q) {
+    const ulonglong2 v = d2[q];
+    mine += v.x + v.y;
+  }
+  u64 inc, dummy, tot, dt;
+  block_scan2(mine, 0ull, &inc, &dummy, &tot, &dt, s);
+  const u64 c = tot + (oe - ob);
   *cnt = c;
   if (c == 0) { *mn = *mx = *lo = *hi = 0; *med = 0.0; return; }
-  *mn = kth_value(dense, kValDense, over, ob, oe, 0, s);
-  *mx = kth_value(dense, kValDense, over, ob, oe, c - 1, s);
-  *lo = kth_value(dense, kValDense, over, ob, oe, (c - 1) / 2, s);
-  *hi = kth_value(dense, kValDense, over, ob, oe, c / 2, s);
+  const u64 ranks[4] = {0, c - 1, (c - 1) / 2, c / 2};
+  __shared__ u64 found[4];
+  const u64 ex = inc - mine;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const u64 k = ranks[r];
+    if (k < tot) {
+      if (k >= ex && k < inc) {
+        u64 acc = ex;
+        for (int v = b0; v < b0 + kPer; ++v) {
+          acc += dense[v];
+          if (k < acc) { found[r] = (u64)v; break; }
+        }
+      }
+    } else if (threadIdx.x == 0) {
+      const u64 j = k - tot;
+      found[r] = ob + j < oe ? (over[ob + j] & kValueMask) : 0ull;
+    }
+  }
+  __syncthreads();
+  *mn = found[0];
+  *mx = found[1];
+  *lo = found[2];
+  *hi = found[3];
   *med = 0.5 * ((double)*lo + (double)*hi);
+  __syncthreads();
 }
 
 // Index one past the run of value v that starts at i in the ascending

@@ -30,24 +30,29 @@ __device__ __forceinline__ void emit_value(u32* smem_hist, u64* dense, u64* over
   else overflow_append(over, cap, st, tag, v);
 }
 
-__device__ __forceinline__ Seg warp_seg_scan(const Seg& x, Seg* agg) {
+// In-step segmented scan over the lanes, packed in one word: bit 31 = a
+// barrier lies in the covered lanes, bits 0..30 = instructions since the last
+// one (at most 512 per step). Returns the exclusive prefix; *agg = the whole
+// warp's value.
+__device__ __forceinline__ u32 warp_seg_scan32(u32 x, u32* agg) {
   const int lane = threadIdx.x & 31;
-  Seg inc = x;
+  u32 inc = x;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    Seg y = seg_shfl_up(inc, o);
-    if (lane >= o) inc = seg_op(y, inc);
+    const u32 y = __shfl_up_sync(0xffffffffu, inc, o);
+    // (y then inc): a barrier in inc restarts the count
+    if (lane >= o) inc = (inc >> 31) ? inc : y + inc;
   }
-  Seg ex = seg_shfl_up(inc, 1);
-  if (lane == 0) ex = seg_identity();
-  agg->b = __shfl_sync(0xffffffffu, inc.b, 31);
-  agg->v = __shfl_sync(0xffffffffu, inc.v, 31);
-  agg->w = 0;
-  return ex;
+  *agg = __shfl_sync(0xffffffffu, inc, 31);
+  const u32 ex = __shfl_up_sync(0xffffffffu, inc, 1);
+  return lane == 0 ? 0u : ex;
 }
 
 // hist_mode: 0 = per-warp shared histograms, 1 = one shared histogram per
-// block, 2 = global atomics.
+// block, 2 = global atomics. Every opcode slot adds to bin min(opcode,
+// n_opcodes): the spare bin n_opcodes takes barriers, padding (written as
+// barrier markers) and invalid opcodes, so invalid opcodes are found at the
+// end as spare - barriers - padding.
 __global__ void __launch_bounds__(kInThreads) k_instr_runs(RunBatchArgs a, int hist_mode) {
   extern __shared__ u32 dyn[];
   __shared__ u32 itb_small[kValSmem];
@@ -56,20 +61,29 @@ __global__ void __launch_bounds__(kInThreads) k_instr_runs(RunBatchArgs a, int h
   DevState* st = &a.arena->st;
   const u32 nop = a.n_opcodes;
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  const u32 hstride = nop + 1;  // one spare bin absorbs barriers and padding
+  const u32 hstride = nop + 1;
   const u32 hwords = hist_mode == 0 ? hstride * kInWarps : (hist_mode == 1 ? hstride : 0u);
   for (u32 i = threadIdx.x; i < hwords; i += kInThreads) dyn[i] = 0u;
   for (int i = threadIdx.x; i < kValSmem; i += kInThreads) itb_small[i] = 0u;
   __syncthreads();
   u32* my_hist = hist_mode == 0 ? dyn + wp * hstride : dyn;
-  u64 nbar = 0, run_or = 0, run_and = ~0ull;
+  u64 nbar = 0, npad = 0, nspare_g = 0, run_or = 0, run_and = ~0ull;
   u32 err = 0, wmin = 0xFFFFFFFFu, wmax = 0u;
   const u64 gwarp = (u64)blockIdx.x * kInWarps + wp;
   const u64 nwarps = (u64)gridDim.x * kInWarps;
+  // the next run's descriptor is loaded while the current one is scanned
+  u64 n_off = 0, n_len = 0;
+  u32 n_wi = 0;
+  if (gwarp < a.n_runs) { n_off = a.run_off[gwarp]; n_len = a.run_len[gwarp]; n_wi = a.run_wi[gwarp]; }
   for (u64 r = gwarp; r < a.n_runs; r += nwarps) {
-    const u64 off = a.run_off[r];
-    u64 len = a.run_len[r];
-    const u32 wi = a.run_wi[r];
+    const u64 off = n_off;
+    u64 len = n_len;
+    const u32 wi = n_wi;
+    if (r + nwarps < a.n_runs) {
+      n_off = a.run_off[r + nwarps];
+      n_len = a.run_len[r + nwarps];
+      n_wi = a.run_wi[r + nwarps];
+    }
     if (off > a.n_ops || len > a.n_ops - off) {
       err |= kErrRun;
       len = 0;
@@ -81,13 +95,14 @@ __global__ void __launch_bounds__(kInThreads) k_instr_runs(RunBatchArgs a, int h
     }
     const uint16_t* p = a.ops + off;
     const bool aligned = ((reinterpret_cast<uintptr_t>(p) & 15u) == 0);
-    Seg carry = seg_identity();
+    bool carry_b = false;  // a barrier seen so far in this run
+    u64 carry_v = 0;       // instructions since the last barrier (or the run start)
     u64 tot = 0, run_pre = 0;
     bool have_pre = false;
     for (u64 s0 = 0; s0 < len; s0 += 32 * kOpsPerLane) {
       const u64 my0 = s0 + (u64)lane * kOpsPerLane;
       const int nv = my0 < len ? (int)umin64(len - my0, (u64)kOpsPerLane) : 0;
-      u32 pk[kOpsPerLane / 2];  // two opcodes per word, low half first
+      u32 pk[kOpsPerLane / 2];  // two opcodes per word, low half first; padding = barrier marker
       if (nv == kOpsPerLane && aligned) {
         const uint4* q = reinterpret_cast<const uint4*>(p + my0);
         const uint4 v0 = __ldcs(q), v1 = __ldcs(q + 1);
@@ -96,36 +111,35 @@ __global__ void __launch_bounds__(kInThreads) k_instr_runs(RunBatchArgs a, int h
       } else {
 #pragma unroll
         for (int k = 0; k < kOpsPerLane / 2; ++k) {
-          const u32 lo = 2 * k < nv ? (u32)p[my0 + 2 * k] : 0u;
-          const u32 hi = 2 * k + 1 < nv ? (u32)p[my0 + 2 * k + 1] : 0u;
+          const u32 lo = 2 * k < nv ? (u32)p[my0 + 2 * k] : (u32)AIWC_BARRIER;
+          const u32 hi = 2 * k + 1 < nv ? (u32)p[my0 + 2 * k + 1] : (u32)AIWC_BARRIER;
           pk[k] = lo | (hi << 16);
         }
+        npad += (u64)(kOpsPerLane - nv);
       }
-      // bit k of bm: opcode k is a barrier marker; nbm: a counted instruction
-      u32 bm = 0, vm = nv >= 32 ? 0xFFFFFFFFu : ((1u << nv) - 1u);
+      // bit k of bm: opcode k is a barrier marker
+      u32 bm = 0;
 #pragma unroll
       for (int k = 0; k < kOpsPerLane; ++k) {
         const u32 o = (pk[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu;
-        const bool valid = k < nv;
-        const bool is_bar = o == AIWC_BARRIER;
-        bm |= (valid && is_bar) ? (1u << k) : 0u;
-        const bool bad = valid && !is_bar && o >= nop;
-        err |= bad ? kErrOpcode : 0u;
-        // every lane adds once per opcode slot; slots that count nothing land in bin nop
-        const u32 bin = (valid && !is_bar && !bad) ? o : nop;
+        bm |= (o == AIWC_BARRIER ? 1u : 0u) << k;
+        const u32 bin = min(o, nop);
         if (hist_mode == 2) {
           if (bin < nop) atomicAdd(&a.opc_hist[bin], 1ull);
+          else ++nspare_g;
         } else {
           atomicAdd(&my_hist[bin], 1u);
         }
       }
+      const u32 vm = nv >= 32 ? 0xFFFFFFFFu : ((1u << nv) - 1u);
+      bm &= vm;
       const u32 nbm = vm & ~bm;
-      const u64 cnt = (u64)__popc(nbm);
-      u64 lead, cur;
+      const u32 cnt = (u32)__popc(nbm);
+      u32 lead, cur;
       if (bm) {
         const int fb = __ffs(bm) - 1, lb = 31 - __clz(bm);
-        lead = (u64)__popc(nbm & ((1u << fb) - 1u));
-        cur = (u64)__popc(nbm & ~((2u << lb) - 1u));
+        lead = (u32)__popc(nbm & ((1u << fb) - 1u));
+        cur = (u32)__popc(nbm & ~((2u << lb) - 1u));
         nbar += (u64)__popc(bm);
         // segments closed by two barriers of this lane
         u32 rest = bm & (bm - 1u);
@@ -141,19 +155,22 @@ __global__ void __launch_bounds__(kInThreads) k_instr_runs(RunBatchArgs a, int h
         lead = cnt;
         cur = 0;
       }
-      Seg e;
-      e.b = bm ? 1u : 0u;
-      e.v = bm ? cur : lead;
-      e.w = 0;
-      Seg agg;
-      Seg ex = seg_op(carry, warp_seg_scan(e, &agg));
+      u32 agg;
+      const u32 ex = warp_seg_scan32(bm ? (0x80000000u | cur) : lead, &agg);
       if (bm) {
-        const u64 seg = ex.v + lead;
-        if (ex.b) emit_value(itb_small, a.arena->itb_dense, a.over, a.over_cap, st, kTagItb, seg);
+        // the segment this lane's first barrier closes: the open count before
+        // the step (if no barrier came earlier in the step), then the lanes before
+        const u64 seg = (ex >> 31 ? 0ull : carry_v) + (ex & 0x7FFFFFFFu) + lead;
+        if (carry_b || (ex >> 31)) emit_value(itb_small, a.arena->itb_dense, a.over, a.over_cap, st, kTagItb, seg);
         else { run_pre = seg; have_pre = true; }
       }
-      carry = seg_op(carry, agg);
-      tot += warp_reduce(cnt, OpAdd());
+      if (agg >> 31) {
+        carry_b = true;
+        carry_v = agg & 0x7FFFFFFFu;
+      } else {
+        carry_v += agg;
+      }
+      tot += __reduce_add_sync(0xffffffffu, cnt);
     }
     const u32 pre_owner = __ballot_sync(0xffffffffu, have_pre);
     if (pre_owner) run_pre = __shfl_sync(0xffffffffu, run_pre, __ffs(pre_owner) - 1);
@@ -162,9 +179,9 @@ __global__ void __launch_bounds__(kInThreads) k_instr_runs(RunBatchArgs a, int h
       const u64 key = ((u64)wi << 32) | (seq & 0xFFFFFFFFull);
       a.run_keys[seq] = key;
       u64* sm = a.run_sum + 4 * seq;
-      sm[0] = carry.b;
-      sm[1] = carry.b ? run_pre : tot;
-      sm[2] = carry.b ? carry.v : 0ull;
+      sm[0] = carry_b ? 1ull : 0ull;
+      sm[1] = carry_b ? run_pre : tot;
+      sm[2] = carry_b ? carry_v : 0ull;
       sm[3] = tot;
       run_or |= key;
       run_and &= key;
@@ -172,25 +189,31 @@ __global__ void __launch_bounds__(kInThreads) k_instr_runs(RunBatchArgs a, int h
     have_pre = false;
   }
   __syncthreads();
+  u64 spare = nspare_g;
   if (hist_mode == 0) {
     for (u32 o = threadIdx.x; o < nop; o += kInThreads) {
       u32 s = 0;
       for (int q = 0; q < kInWarps; ++q) s += dyn[q * hstride + o];
       if (s) atomicAdd(&a.opc_hist[o], (u64)s);
     }
+    if (threadIdx.x < kInWarps) spare += dyn[threadIdx.x * hstride + nop];
   } else if (hist_mode == 1) {
     for (u32 o = threadIdx.x; o < nop; o += kInThreads)
       if (dyn[o]) atomicAdd(&a.opc_hist[o], (u64)dyn[o]);
+    if (threadIdx.x == 0) spare += dyn[nop];
   }
   for (int i = threadIdx.x; i < kValSmem; i += kInThreads)
     if (itb_small[i]) atomicAdd(&a.arena->itb_dense[i], (u64)itb_small[i]);
   nbar = block_reduce(nbar, OpAdd(), 0ull, red64);
+  npad = block_reduce(npad, OpAdd(), 0ull, red64);
+  spare = block_reduce(spare, OpAdd(), 0ull, red64);
   run_or = block_reduce(run_or, OpOr(), 0ull, red64);
   run_and = block_reduce(run_and, OpAnd(), ~0ull, red64);
   err = block_reduce(err, OpOr(), 0u, red32);
   wmin = block_reduce(wmin, OpMin(), 0xFFFFFFFFu, red32);
   wmax = block_reduce(wmax, OpMax(), 0u, red32);
   if (threadIdx.x == 0) {
+    if (spare != nbar + npad) err |= kErrOpcode;  // slots in the spare bin that are neither barriers nor padding
     if (nbar) atomicAdd(&st->barriers, nbar);
     if (wmin <= wmax) {
       atomicOr(&st->run_or, run_or);

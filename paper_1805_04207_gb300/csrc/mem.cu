@@ -6,6 +6,8 @@
 // it. Sorting the words groups equal addresses and, inside an address, reads
 // before writes; the group of skip level n (Sec. III: n = 0 global entropy,
 // n = 1..10 local entropies) is word >> (n + 1).
+#include <algorithm>
+
 #include "aiwc_internal.cuh"
 #include "common.cuh"
 #include "runs.cuh"
@@ -23,9 +25,10 @@ constexpr int kIngestThreads = 256;
 // high half, the event's rank among its superblock's events (the count
 // before it, from the same atomic), which is its place in the superblock's
 // segment. An event the table cannot place gets the sentinel slot word and
-// its full word goes to the spill list. FILTER: the space mask drops events, so outputs are
-// compacted behind one atomicAdd per block-tile.
-template <bool FILTER, bool HASH>
+// its full word goes to the spill list. FILTER: the space mask drops events,
+// so outputs are compacted behind one atomicAdd per block-tile. FULL: a.n is
+// a multiple of the block tile, so every event slot is valid (no tests).
+template <bool FILTER, bool HASH, bool FULL>
 __global__ void __launch_bounds__(kIngestThreads, HASH ? 4 : 3) k_mem_ingest(MemIngestArgs a) {
   constexpr int ITEMS = HASH ? 4 : 8;
   __shared__ u64 red64[32];
@@ -35,7 +38,7 @@ __global__ void __launch_bounds__(kIngestThreads, HASH ? 4 : 3) k_mem_ingest(Mem
   DevState* st = &a.arena->st;
   const uint4* ev = reinterpret_cast<const uint4*>(a.ev);
   const int lane = threadIdx.x & 31;
-  u64 reads = 0, writes = 0, wor = 0, wand = ~0ull, kept = 0;
+  u64 writes = 0, wor = 0, wand = ~0ull, kept = 0;
   u32 wmin = 0xFFFFFFFFu, wmax = 0u, err = 0u, sbt_fail = 0u;
   const u64 per_block = (u64)kIngestThreads * ITEMS;
   for (u64 t0 = (u64)blockIdx.x * per_block; t0 < a.n; t0 += (u64)gridDim.x * per_block) {
@@ -44,7 +47,7 @@ __global__ void __launch_bounds__(kIngestThreads, HASH ? 4 : 3) k_mem_ingest(Mem
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
       const u64 i = t0 + (u64)k * kIngestThreads + threadIdx.x;
-      valid[k] = i < a.n;
+      valid[k] = FULL || i < a.n;
       e[k] = valid[k] ? __ldcs(ev + i) : make_uint4(0u, 0u, 0u, 0u);
     }
     u64 word[ITEMS];
@@ -65,11 +68,11 @@ __global__ void __launch_bounds__(kIngestThreads, HASH ? 4 : 3) k_mem_ingest(Mem
         }
         if (addr >> 61) err |= kErrAddr;
       }
-      keep[k] = valid[k] && ((a.space_mask >> space) & 1u);
+      keep[k] = valid[k] && (!FILTER || ((a.space_mask >> space) & 1u));
       word[k] = ((u64)space << 62) | ((addr & ((1ull << 61) - 1)) << 1) | store;
       if (keep[k]) {
         ++nkeep;
-        if (store) ++writes; else ++reads;
+        writes += store;  // reads follow from the kept count
         wor |= word[k];
         wand &= word[k];
       }
@@ -151,11 +154,11 @@ __global__ void __launch_bounds__(kIngestThreads, HASH ? 4 : 3) k_mem_ingest(Mem
       }
     }
   }
-  reads = block_reduce(reads, OpAdd(), 0ull, red64);
   writes = block_reduce(writes, OpAdd(), 0ull, red64);
   wor = block_reduce(wor, OpOr(), 0ull, red64);
   wand = block_reduce(wand, OpAnd(), ~0ull, red64);
   kept = block_reduce(kept, OpAdd(), 0ull, red64);
+  const u64 reads = kept - writes;
   wmin = block_reduce(wmin, OpMin(), 0xFFFFFFFFu, red32);
   wmax = block_reduce(wmax, OpMax(), 0u, red32);
   err = block_reduce(err, OpOr(), 0u, red32);
@@ -256,18 +259,33 @@ __global__ void __launch_bounds__(kLvThreads) k_mem_levels(LevelArgs a) {
 void launch_mem_ingest(const MemIngestArgs& a, cudaStream_t s) {
   if (a.n == 0) return;
   const u64 per_block = (u64)kIngestThreads * (a.use_tab ? 4 : 8);
-  u64 blocks = (a.n + per_block - 1) / per_block;
   const u64 cap = a.use_tab ? 152ull * 16 : 152ull * 8;
-  if (blocks > cap) blocks = cap;
+  auto grid = [&](u64 n) { return (unsigned)std::min<u64>((n + per_block - 1) / per_block, cap); };
   const bool filter = a.space_mask != 0xFu;
-  if (a.use_tab) {
-    if (filter) k_mem_ingest<true, true><<<(unsigned)blocks, kIngestThreads, 0, s>>>(a);
-    else k_mem_ingest<false, true><<<(unsigned)blocks, kIngestThreads, 0, s>>>(a);
-  } else {
-    if (filter) k_mem_ingest<true, false><<<(unsigned)blocks, kIngestThreads, 0, s>>>(a);
-    else k_mem_ingest<false, false><<<(unsigned)blocks, kIngestThreads, 0, s>>>(a);
+  if (filter) {
+    if (a.use_tab) k_mem_ingest<true, true, false><<<grid(a.n), kIngestThreads, 0, s>>>(a);
+    else k_mem_ingest<true, false, false><<<grid(a.n), kIngestThreads, 0, s>>>(a);
+    count_launches(1);
+    return;
   }
-  count_launches(1);
+  // whole block tiles without bounds tests, then the ragged tail
+  const u64 n_full = a.n / per_block * per_block;
+  if (n_full) {
+    MemIngestArgs f = a;
+    f.n = n_full;
+    if (a.use_tab) k_mem_ingest<false, true, true><<<grid(n_full), kIngestThreads, 0, s>>>(f);
+    else k_mem_ingest<false, false, true><<<grid(n_full), kIngestThreads, 0, s>>>(f);
+    count_launches(1);
+  }
+  if (a.n > n_full) {
+    MemIngestArgs t = a;
+    t.ev = static_cast<const char*>(a.ev) + 16 * n_full;
+    t.n = a.n - n_full;
+    t.word_base = a.word_base + n_full;
+    if (a.use_tab) k_mem_ingest<false, true, false><<<grid(t.n), kIngestThreads, 0, s>>>(t);
+    else k_mem_ingest<false, false, false><<<grid(t.n), kIngestThreads, 0, s>>>(t);
+    count_launches(1);
+  }
 }
 
 void launch_mem_levels(const LevelArgs& a, cudaStream_t s) {

@@ -286,6 +286,27 @@ struct SiteArgs {
   Arena* arena{};
   int grid{};
 };
+// Stable counting sort of the branch words by site, for site ids below
+// kCsSites when work-item ids arrived in non-decreasing order (the site alone
+// then orders each site's history). Writes the same sorted words as the radix
+// sort on the site bits, the site list and n_sites / br_site_max.
+constexpr u32 kCsSites = 4096;
+struct SiteSortArgs {
+  const u64* src{};      // branch words in push order
+  u64* dst{};            // out: words sorted by site (stable)
+  u32* sort_cur{};       // set to 1: dst is the live buffer
+  u64 n{};
+  u32* counts{};         // scratch: site_sort_count_words(n) words
+  u32* chunks{};         // scratch: site_sort_chunk_words(n) words
+  u64* sites{};          // out: (start, length) per site with events
+  u64 sites_cap{};
+  Arena* arena{};
+  int sm_count{};
+};
+size_t site_sort_count_words(u64 n);
+size_t site_sort_chunk_words(u64 n);
+void launch_site_sort(const SiteSortArgs& a, cudaStream_t s);
+
 constexpr u32 kSiteMaxHist = 17;       // dense pattern bins: 2^15 per pass, at most 4 passes
 constexpr u64 kSiteMaxLen = 65535;     // packed 16-bit taken / total counters
 constexpr u64 kSiteListCap = 1ull << 20;  // sites listed for the per-site path

@@ -725,6 +725,7 @@ struct Plan {
   bool per_site = false;  // branch: per-site patterns (when !gated)
   u32 br_passes = 0xFFu, run_passes = 0xFFu;
   int seg_shift = 0;      // memory, hash plan: low address bits that are zero in every kept event (0..3)
+  bool site_sort = false; // branch: stable counting sort by site (in order work-item ids, site ids < kCsSites)
 };
 
 u32 active_passes(u64 kor, u64 kand, u64 mask) {
@@ -807,6 +808,23 @@ SiteArgs site_args(aiwc_handle* h, const SortDesc& bsort) {
 // Stages that must run before the branch-path choice: the branch sort and the site list.
 void enqueue_part1(aiwc_handle* h, cudaStream_t st, const Plan& p) {
   if (!h->n_br) return;
+  if (p.site_sort) {
+    // sorted words, the site list, n_sites and the longest site in one pass
+    StageScope sc(h, kStBrSort);
+    SiteSortArgs ss;
+    ss.src = (const u64*)h->br_a.p;
+    ss.dst = (u64*)h->br_b.p;
+    ss.sort_cur = &h->arena->st.sort_cur[kSortBranch];
+    ss.n = h->n_br;
+    ss.counts = (u32*)h->pat_a.p;
+    ss.chunks = (u32*)h->pat_b.p;
+    ss.sites = (u64*)h->sites.p;
+    ss.sites_cap = h->c_sites_cap;
+    ss.arena = h->arena;
+    ss.sm_count = h->sm_count;
+    launch_site_sort(ss, st);
+    return;
+  }
   SortDesc bsort = branch_sort_desc(h);
   {
     StageScope sc(h, kStBrSort);
@@ -1022,6 +1040,10 @@ void plan_from_ingest(aiwc_handle* h, Plan* p) {
   // address bits sit above the store bit of the word
   const u64 addr_or = (hs.mem_or >> 1) & ((1ull << 61) - 1);
   p->seg_shift = addr_or ? std::min(__builtin_ctzll(addr_or), 3) : 3;
+  // the counting sort's per-tile counts (n_br / 4 words or less) live in the
+  // pattern buffers, which hold 2 n_br words each
+  p->site_sort = !p->gated && h->n_br >= (1ull << 16) && h->n_br < (1ull << 32) && !hs.br_unsorted &&
+                 (hs.br_or >> 32) < kCsSites && h->cfg.plan != 1;
 }
 
 }  // namespace

@@ -9,6 +9,8 @@
 // has `h` predecessors at its site; sorting pattern words puts each
 // (site, history) pattern in one run whose length is n and whose sum of low
 // bits is the number taken, t. M = sum min(t, n - t), N' = sum n.
+#include <algorithm>
+
 #include "aiwc_internal.cuh"
 #include "common.cuh"
 #include "runs.cuh"
@@ -116,6 +118,187 @@ __global__ void __launch_bounds__(256) k_site_heads(SiteArgs a) {
     }
   }
   if (mx) atomicMax(&st->br_site_max, mx);
+}
+
+// ---------------------------------------------------------------- site counting sort
+
+constexpr int kCsThreads = 256;
+constexpr int kCsWarps = kCsThreads / 32;
+constexpr int kCsWarpEvents = 2048;                     // each warp ranks a contiguous run of events
+constexpr int kCsTile = kCsWarps * kCsWarpEvents;       // 16384 events per tile
+constexpr int kCsChunk = 64;                            // tiles per scan chunk
+constexpr int kCsScanThreads = 1024;
+constexpr int kCsPer = kCsSites / kCsScanThreads;       // sites per scan thread (4)
+static_assert(kCsPer == 4, "the scan reads four sites as one 16-byte vector");
+
+__host__ __device__ inline u64 cs_tiles(u64 n) { return (n + kCsTile - 1) / kCsTile; }
+__host__ __device__ inline u64 cs_chunks(u64 n) { return (cs_tiles(n) + kCsChunk - 1) / kCsChunk; }
+
+// Phase 1: per-tile site counts, counts[tile][site].
+__global__ void __launch_bounds__(kCsThreads) k_cs_count(SiteSortArgs a) {
+  __shared__ u32 hist[kCsSites];
+  const u64 ntiles = cs_tiles(a.n);
+  for (u64 t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    for (int i = threadIdx.x; i < (int)kCsSites; i += kCsThreads) hist[i] = 0u;
+    __syncthreads();
+    const u64 base = t * kCsTile;
+    const u64 end = umin64(a.n, base + kCsTile);
+    for (u64 i = base + threadIdx.x; i < end; i += kCsThreads) atomicAdd(&hist[(u32)(a.src[i] >> 32)], 1u);
+    __syncthreads();
+    uint4* out = reinterpret_cast<uint4*>(a.counts + t * kCsSites);
+    for (int i = threadIdx.x; i < (int)kCsSites / 4; i += kCsThreads)
+      out[i] = make_uint4(hist[4 * i], hist[4 * i + 1], hist[4 * i + 2], hist[4 * i + 3]);
+    __syncthreads();
+  }
+}
+
+// Phase 2a: within each chunk of kCsChunk tiles, counts become exclusive
+// prefixes over the chunk's tiles; chunks[chunk][site] gets the chunk total.
+__global__ void __launch_bounds__(kCsScanThreads) k_cs_scan_chunks(SiteSortArgs a) {
+  const u64 ntiles = cs_tiles(a.n), nchunks = cs_chunks(a.n);
+  for (u64 c = blockIdx.x; c < nchunks; c += gridDim.x) {
+    uint4 run = make_uint4(0u, 0u, 0u, 0u);
+    const u64 t1 = umin64(ntiles, (c + 1) * kCsChunk);
+    for (u64 t = c * kCsChunk; t < t1; ++t) {
+      uint4* p = reinterpret_cast<uint4*>(a.counts + t * kCsSites) + threadIdx.x;
+      const uint4 v = *p;
+      *p = run;
+      run.x += v.x; run.y += v.y; run.z += v.z; run.w += v.w;
+    }
+    reinterpret_cast<uint4*>(a.chunks + c * kCsSites)[threadIdx.x] = run;
+  }
+}
+
+// Phase 2b (one block): per site, exclusive prefix over chunks plus the
+// site's start (exclusive prefix of the site totals); the site list, the
+// number of sites and the longest site.
+__global__ void __launch_bounds__(kCsScanThreads) k_cs_scan_sites(SiteSortArgs a) {
+  __shared__ u64 wt64[33];
+  __shared__ u32 wt32[33];
+  __shared__ u64 red64[32];
+  DevState* st = &a.arena->st;
+  const u64 nchunks = cs_chunks(a.n);
+  u64 tot[kCsPer] = {0, 0, 0, 0};
+  for (u64 c = 0; c < nchunks; ++c) {
+    uint4* p = reinterpret_cast<uint4*>(a.chunks + c * kCsSites) + threadIdx.x;
+    const uint4 v = *p;
+    *p = make_uint4((u32)tot[0], (u32)tot[1], (u32)tot[2], (u32)tot[3]);
+    tot[0] += v.x; tot[1] += v.y; tot[2] += v.z; tot[3] += v.w;
+  }
+  // site starts: block exclusive scan of the per-thread sums (sites 4i .. 4i+3)
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const u64 mine = tot[0] + tot[1] + tot[2] + tot[3];
+  const u32 nz = (tot[0] != 0) + (tot[1] != 0) + (tot[2] != 0) + (tot[3] != 0);
+  u64 inc = mine;
+  u32 inz = nz;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const u64 y = __shfl_up_sync(0xffffffffu, inc, o);
+    const u32 yz = __shfl_up_sync(0xffffffffu, inz, o);
+    if (lane >= o) { inc += y; inz += yz; }
+  }
+  if (lane == 31) { wt64[w] = inc; wt32[w] = inz; }
+  __syncthreads();
+  if (w == 0) {
+    const u64 v = wt64[lane];
+    const u32 vz = wt32[lane];
+    u64 vi = v;
+    u32 viz = vz;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const u64 y = __shfl_up_sync(0xffffffffu, vi, o);
+      const u32 yz = __shfl_up_sync(0xffffffffu, viz, o);
+      if (lane >= o) { vi += y; viz += yz; }
+    }
+    wt64[lane] = vi - v;
+    wt32[lane] = viz - vz;
+  }
+  __syncthreads();
+  u64 start = wt64[w] + inc - mine;
+  u64 k = wt32[w] + inz - nz;
+  u64 mx = 0;
+  u64 base[kCsPer];
+#pragma unroll
+  for (int q = 0; q < kCsPer; ++q) {
+    base[q] = start;
+    if (tot[q]) {
+      if (k < a.sites_cap) {
+        a.sites[2 * k] = start;
+        a.sites[2 * k + 1] = tot[q];
+      }
+      ++k;
+      mx = tot[q] > mx ? tot[q] : mx;
+    }
+    start += tot[q];
+  }
+  // chunk offsets become absolute positions
+  for (u64 c = 0; c < nchunks; ++c) {
+    uint4* p = reinterpret_cast<uint4*>(a.chunks + c * kCsSites) + threadIdx.x;
+    const uint4 v = *p;
+    *p = make_uint4((u32)(v.x + base[0]), (u32)(v.y + base[1]), (u32)(v.z + base[2]), (u32)(v.w + base[3]));
+  }
+  mx = block_reduce(mx, OpMax(), 0ull, red64);
+  if (threadIdx.x == kCsScanThreads - 1) st->n_sites = k;  // the last thread's count is the total
+  if (threadIdx.x == 0) {
+    st->br_site_max = mx;
+    *a.sort_cur = 1u;
+  }
+}
+
+// Phase 3: each warp ranks its 2048 events in push order among the tile's
+// events of the same site (per-warp 16-bit counters, two sites per word,
+// turned into prefixes over the warps) and writes each word to its site's
+// position: chunk offset + prefix within the chunk + rank within the tile.
+constexpr size_t kCsScatterSmem = (size_t)(kCsWarps * kCsSites / 2 + kCsSites) * 4;
+
+__global__ void __launch_bounds__(kCsThreads) k_cs_scatter(SiteSortArgs a) {
+  extern __shared__ u32 csm[];
+  u32 (*wc)[kCsSites / 2] = reinterpret_cast<u32 (*)[kCsSites / 2]>(csm);
+  u32* toff = csm + kCsWarps * kCsSites / 2;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const u32 lt = (1u << lane) - 1u;
+  const u64 ntiles = cs_tiles(a.n);
+  for (u64 t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const u32* cc = a.chunks + (t / kCsChunk) * kCsSites;
+    const u32* ct = a.counts + t * kCsSites;
+    for (int i = threadIdx.x; i < (int)kCsSites; i += kCsThreads) toff[i] = cc[i] + ct[i];
+    for (int i = threadIdx.x; i < kCsWarps * (int)kCsSites / 2; i += kCsThreads) (&wc[0][0])[i] = 0u;
+    __syncthreads();
+    const u64 w0 = t * kCsTile + (u64)wp * kCsWarpEvents;
+    const u64 w1 = umin64(a.n, w0 + kCsWarpEvents);
+    for (u64 i = w0 + lane; i < w1; i += 32) {
+      const u32 site = (u32)(a.src[i] >> 32);
+      atomicAdd(&wc[wp][site >> 1], 1u << ((site & 1u) * 16));
+    }
+    __syncthreads();
+    // prefixes over the warps, one site pair per thread at a time
+    for (int pr = threadIdx.x; pr < (int)kCsSites / 2; pr += kCsThreads) {
+      u32 run = 0;
+#pragma unroll
+      for (int q = 0; q < kCsWarps; ++q) {
+        const u32 c = wc[q][pr];
+        wc[q][pr] = run;
+        run += c;  // both halves stay below 2^16: a tile has 16384 events
+      }
+    }
+    __syncthreads();
+    for (u64 i0 = w0; i0 < w1; i0 += 32) {
+      const u64 i = i0 + lane;
+      const bool v = i < w1;
+      const u64 word = v ? a.src[i] : 0ull;
+      const u32 site = (u32)(word >> 32);
+      const u32 peers = __match_any_sync(0xffffffffu, v ? site : (0xFFFFF000u | (u32)lane));
+      const int leader = __ffs(peers) - 1;
+      u32 b = 0;
+      if (v && lane == leader) {
+        const u32 sh = (site & 1u) * 16;
+        b = (atomicAdd(&wc[wp][site >> 1], (u32)__popc(peers) << sh) >> sh) & 0xFFFFu;
+      }
+      b = __shfl_sync(0xffffffffu, b, leader);
+      if (v) a.dst[(u64)toff[site] + b + (u32)__popc(peers & lt)] = word;
+    }
+    __syncthreads();
+  }
 }
 
 constexpr int kSpThreads = 512;
@@ -418,6 +601,19 @@ void launch_branch_ingest(const BranchIngestArgs& a, cudaStream_t s) {
   count_launches(1);
 }
 
+size_t site_sort_count_words(u64 n) { return (size_t)(cs_tiles(n) ? cs_tiles(n) : 1) * kCsSites; }
+size_t site_sort_chunk_words(u64 n) { return (size_t)(cs_chunks(n) ? cs_chunks(n) : 1) * kCsSites; }
+
+void launch_site_sort(const SiteSortArgs& a, cudaStream_t s) {
+  if (a.n == 0) return;
+  const u64 ntiles = cs_tiles(a.n), nchunks = cs_chunks(a.n);
+  k_cs_count<<<(unsigned)std::min<u64>(ntiles, (u64)a.sm_count * 8), kCsThreads, 0, s>>>(a);
+  k_cs_scan_chunks<<<(unsigned)std::min<u64>(nchunks, (u64)a.sm_count * 2), kCsScanThreads, 0, s>>>(a);
+  k_cs_scan_sites<<<1, kCsScanThreads, 0, s>>>(a);
+  k_cs_scatter<<<(unsigned)std::min<u64>(ntiles, (u64)a.sm_count * 2), kCsThreads, kCsScatterSmem, s>>>(a);
+  count_launches(4);
+}
+
 void launch_branch_mask(Arena* arena, cudaStream_t s) {
   k_branch_mask<<<1, 1, 0, s>>>(arena);
   count_launches(1);
@@ -442,6 +638,7 @@ static size_t site_patterns_smem() {
 
 void init_branch_attributes() {
   cudaFuncSetAttribute(k_site_patterns, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)site_patterns_smem());
+  cudaFuncSetAttribute(k_cs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCsScatterSmem);
 }
 
 void launch_site_patterns(const SiteArgs& a, cudaStream_t s) {

@@ -173,6 +173,29 @@ def test_address_alignment_shifts(P, shift):
     assert_parity(run_gpu(P, tr, plan=0, table_slots=1 << 16), oracle.compute(tr))
 
 
+def _site_trace(seed, n, n_sites, wi_sorted=True):
+    rng = np.random.default_rng(seed)
+    sites = rng.integers(0, n_sites, n)
+    wis = np.arange(n) // 64 if wi_sorted else rng.integers(0, 1 << 16, n)
+    p_site = rng.random(n_sites)
+    taken = (rng.random(n) < p_site[sites]).astype(np.int64)
+    return branch_only(sites.tolist(), wis.tolist(), taken.tolist())
+
+
+@pytest.mark.parametrize("n,n_sites,wi_sorted,split,h", [
+    ((1 << 16) + 3, 4096, True, 1, 16),       # one ragged tile past four
+    (1_100_000 + 77, 4000, True, 3, 16),      # several scan chunks, three pushes
+    (300_001, 50, True, 2, 3),                # few, long sites
+    (200_000, 5000, True, 1, 16),             # site ids >= 4096: radix sort
+    (200_000, 1000, False, 1, 16),            # work-items out of order: radix sort
+])
+def test_site_counting_sort(P, n, n_sites, wi_sorted, split, h):
+    """The stable counting sort by site (work-items in order, site ids below
+    4096) and its fallbacks give the oracle's branch metrics."""
+    tr = _site_trace(7 + n_sites, n, n_sites, wi_sorted)
+    assert_parity(run_gpu(P, tr, split=split, history_len=h), oracle.compute(tr, history_len=h))
+
+
 def test_value_overflow_paths(P):
     # ITB/IPT values above the shared (2048) and dense (65536) bins, opcode
     # counts above 1024, and work-items with many runs.

@@ -71,7 +71,7 @@ struct DevState {
   u32 br_unsorted;       // some work-item id arrived below its predecessor
   u32 br_persite;        // the per-site branch path applies (set on the device)
   u32 br_last_wi[2];     // last work-item id of the previous / current push (by push parity)
-  u32 pad3;
+  u32 run_unsorted;      // some run key is below its predecessor (the run sort is needed)
   u32 sort_cur[8];       // which ping-pong buffer holds each sort's data
   u32 pad;
 };
@@ -343,6 +343,8 @@ struct RunBatchArgs {
   Arena* arena{};
 };
 void launch_instr_runs(const RunBatchArgs& a, cudaStream_t s);
+// Sets *flag when keys[0..n) are not in non-decreasing order.
+void launch_keys_sorted(const u64* keys, u64 n, u32* flag, cudaStream_t s);
 
 struct CombineArgs {
   const u64* a{};

@@ -761,6 +761,9 @@ aiwc_status prepare(aiwc_handle* h) {
   ENSURE(h->tiles, std::max<u64>((u64)kLevels * ntiles_of(n_mem), ntiles_of(n_br) + 1) * sizeof(TileSum), false);
   h->c_sites_cap = std::min<u64>(std::max<u64>(n_br, 1), kSiteListCap);
   ENSURE(h->sites, h->c_sites_cap * 16, false);
+  // runs pushed in (work-item, push) order need no sort: checked before the
+  // counters are read back
+  launch_keys_sorted((const u64*)h->rk_a.p, n_runs, &h->arena->st.run_unsorted, h->stream);
   return ensure_bitmap(h);
 }
 
@@ -1036,7 +1039,7 @@ void plan_from_ingest(aiwc_handle* h, Plan* p) {
   p->hash_ok = hashed && hs.sbt_overflow == 0;
   if (hashed && !p->hash_ok) h->sbt_want = std::min<u64>(h->sbt_cap * 4, kMaxHashSlots);
   p->br_passes = active_passes(hs.br_or, hs.br_and, hs.br_unsorted ? ~1ull : 0xFFFFFFFF00000000ull);
-  p->run_passes = active_passes(hs.run_or, hs.run_and, ~0ull);
+  p->run_passes = hs.run_unsorted ? active_passes(hs.run_or, hs.run_and, ~0ull) : 0u;
   // address bits sit above the store bit of the word
   const u64 addr_or = (hs.mem_or >> 1) & ((1ull << 61) - 1);
   p->seg_shift = addr_or ? std::min(__builtin_ctzll(addr_or), 3) : 3;

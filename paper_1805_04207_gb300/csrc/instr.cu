@@ -10,6 +10,8 @@
 // after the runs are sorted by (work-item, push order) one thread per
 // work-item chains its summaries, emitting the cross-run segments, the final
 // implicit-barrier segment and the work-item's IPT.
+#include <algorithm>
+
 #include "aiwc_internal.cuh"
 #include "common.cuh"
 #include "runs.cuh"
@@ -263,7 +265,21 @@ __global__ void __launch_bounds__(256) k_instr_combine(CombineArgs a) {
   }
 }
 
+__global__ void __launch_bounds__(256) k_keys_sorted(const u64* keys, u64 n, u32* flag) {
+  bool bad = false;
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x + 1; i < n; i += (u64)gridDim.x * blockDim.x)
+    bad |= keys[i] < keys[i - 1];
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) *flag = 1u;
+}
+
 }  // namespace
+
+void launch_keys_sorted(const u64* keys, u64 n, u32* flag, cudaStream_t s) {
+  if (n < 2) return;
+  const u64 blocks = std::min<u64>((n + 255) / 256, 152ull * 8);
+  k_keys_sorted<<<(unsigned)blocks, 256, 0, s>>>(keys, n, flag);
+  count_launches(1);
+}
 
 void launch_instr_runs(const RunBatchArgs& a, cudaStream_t s) {
   if (a.n_runs == 0) return;

@@ -159,11 +159,18 @@ __global__ void __launch_bounds__(kCsScanThreads) k_cs_scan_chunks(SiteSortArgs 
   for (u64 c = blockIdx.x; c < nchunks; c += gridDim.x) {
     uint4 run = make_uint4(0u, 0u, 0u, 0u);
     const u64 t1 = umin64(ntiles, (c + 1) * kCsChunk);
-    for (u64 t = c * kCsChunk; t < t1; ++t) {
-      uint4* p = reinterpret_cast<uint4*>(a.counts + t * kCsSites) + threadIdx.x;
-      const uint4 v = *p;
-      *p = run;
-      run.x += v.x; run.y += v.y; run.z += v.z; run.w += v.w;
+    // eight tiles' counts in flight at a time
+    for (u64 t0 = c * kCsChunk; t0 < t1; t0 += 8) {
+      uint4 v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        v[q] = t0 + q < t1 ? reinterpret_cast<const uint4*>(a.counts + (t0 + q) * kCsSites)[threadIdx.x]
+                           : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (t0 + q < t1) reinterpret_cast<uint4*>(a.counts + (t0 + q) * kCsSites)[threadIdx.x] = run;
+        run.x += v[q].x; run.y += v[q].y; run.z += v[q].z; run.w += v[q].w;
+      }
     }
     reinterpret_cast<uint4*>(a.chunks + c * kCsSites)[threadIdx.x] = run;
   }
@@ -179,11 +186,19 @@ __global__ void __launch_bounds__(kCsScanThreads) k_cs_scan_sites(SiteSortArgs a
   DevState* st = &a.arena->st;
   const u64 nchunks = cs_chunks(a.n);
   u64 tot[kCsPer] = {0, 0, 0, 0};
-  for (u64 c = 0; c < nchunks; ++c) {
-    uint4* p = reinterpret_cast<uint4*>(a.chunks + c * kCsSites) + threadIdx.x;
-    const uint4 v = *p;
-    *p = make_uint4((u32)tot[0], (u32)tot[1], (u32)tot[2], (u32)tot[3]);
-    tot[0] += v.x; tot[1] += v.y; tot[2] += v.z; tot[3] += v.w;
+  for (u64 c0 = 0; c0 < nchunks; c0 += 8) {
+    uint4 v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      v[q] = c0 + q < nchunks ? reinterpret_cast<const uint4*>(a.chunks + (c0 + q) * kCsSites)[threadIdx.x]
+                              : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (c0 + q < nchunks)
+        reinterpret_cast<uint4*>(a.chunks + (c0 + q) * kCsSites)[threadIdx.x] =
+            make_uint4((u32)tot[0], (u32)tot[1], (u32)tot[2], (u32)tot[3]);
+      tot[0] += v[q].x; tot[1] += v[q].y; tot[2] += v[q].z; tot[3] += v[q].w;
+    }
   }
   // site starts: block exclusive scan of the per-thread sums (sites 4i .. 4i+3)
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -232,6 +247,7 @@ __global__ void __launch_bounds__(kCsScanThreads) k_cs_scan_sites(SiteSortArgs a
     start += tot[q];
   }
   // chunk offsets become absolute positions
+#pragma unroll 8
   for (u64 c = 0; c < nchunks; ++c) {
     uint4* p = reinterpret_cast<uint4*>(a.chunks + c * kCsSites) + threadIdx.x;
     const uint4 v = *p;
@@ -266,9 +282,19 @@ __global__ void __launch_bounds__(kCsThreads) k_cs_scatter(SiteSortArgs a) {
     __syncthreads();
     const u64 w0 = t * kCsTile + (u64)wp * kCsWarpEvents;
     const u64 w1 = umin64(a.n, w0 + kCsWarpEvents);
-    for (u64 i = w0 + lane; i < w1; i += 32) {
-      const u32 site = (u32)(a.src[i] >> 32);
-      atomicAdd(&wc[wp][site >> 1], 1u << ((site & 1u) * 16));
+    {
+      u64 i = w0 + lane;
+      for (; i + 96 < w1; i += 128) {  // four loads in flight
+        u32 st4[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) st4[q] = (u32)(a.src[i + 32 * q] >> 32);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) atomicAdd(&wc[wp][st4[q] >> 1], 1u << ((st4[q] & 1u) * 16));
+      }
+      for (; i < w1; i += 32) {
+        const u32 site = (u32)(a.src[i] >> 32);
+        atomicAdd(&wc[wp][site >> 1], 1u << ((site & 1u) * 16));
+      }
     }
     __syncthreads();
     // prefixes over the warps, one site pair per thread at a time
@@ -282,20 +308,29 @@ __global__ void __launch_bounds__(kCsThreads) k_cs_scatter(SiteSortArgs a) {
       }
     }
     __syncthreads();
-    for (u64 i0 = w0; i0 < w1; i0 += 32) {
-      const u64 i = i0 + lane;
-      const bool v = i < w1;
-      const u64 word = v ? a.src[i] : 0ull;
-      const u32 site = (u32)(word >> 32);
-      const u32 peers = __match_any_sync(0xffffffffu, v ? site : (0xFFFFF000u | (u32)lane));
-      const int leader = __ffs(peers) - 1;
-      u32 b = 0;
-      if (v && lane == leader) {
-        const u32 sh = (site & 1u) * 16;
-        b = (atomicAdd(&wc[wp][site >> 1], (u32)__popc(peers) << sh) >> sh) & 0xFFFFu;
+    // push order is kept: groups of 32 events are ranked one after another,
+    // while the loads of the next groups are already in flight
+    for (u64 i0 = w0; i0 < w1; i0 += 128) {
+      u64 word[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const u64 i = i0 + 32 * q + lane;
+        word[q] = i < w1 ? a.src[i] : 0ull;
       }
-      b = __shfl_sync(0xffffffffu, b, leader);
-      if (v) a.dst[(u64)toff[site] + b + (u32)__popc(peers & lt)] = word;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const bool v = i0 + 32 * q + lane < w1;
+        const u32 site = (u32)(word[q] >> 32);
+        const u32 peers = __match_any_sync(0xffffffffu, v ? site : (0xFFFFF000u | (u32)lane));
+        const int leader = __ffs(peers) - 1;
+        u32 b = 0;
+        if (v && lane == leader) {
+          const u32 sh = (site & 1u) * 16;
+          b = (atomicAdd(&wc[wp][site >> 1], (u32)__popc(peers) << sh) >> sh) & 0xFFFFu;
+        }
+        b = __shfl_sync(0xffffffffu, b, leader);
+        if (v) a.dst[(u64)toff[site] + b + (u32)__popc(peers & lt)] = word[q];
+      }
     }
     __syncthreads();
   }

@@ -377,11 +377,19 @@ __global__ void __launch_bounds__(kSpThreads) k_site_patterns(SiteArgs a) {
       else overflow_append(a.over, a.over_cap, st, kTagSites, m);
     }
     const u32 nwords = (u32)((m + 31) / 32);
-    for (u32 c = wp; c < nwords + 2; c += nw) {
-      const u64 j = (u64)c * 32 + lane;
-      const bool t = j < m && (w[start + j] & 1ull);
-      const u32 b = __ballot_sync(0xffffffffu, t);
-      if (lane == 0) bits[c] = b;
+    // eight 32-event groups per warp in flight at a time
+    for (u32 c0 = wp; c0 < nwords + 2; c0 += 8 * nw) {
+      bool t[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const u64 j = (u64)(c0 + q * nw) * 32 + lane;
+        t[q] = j < m && (w[start + j] & 1ull);
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const u32 b = __ballot_sync(0xffffffffu, t[q]);
+        if (lane == 0 && c0 + q * nw < nwords + 2) bits[c0 + q * nw] = b;
+      }
     }
     __syncthreads();
     for (u32 q = 0; q < passes; ++q) {

@@ -135,6 +135,20 @@ typedef struct aiwc_metrics {
   double unique_rw_ratio;       /* unique reads / unique writes */
   double reread_ratio;          /* unique reads / total reads */
   double rewrite_ratio;         /* unique writes / total writes */
+  /* Parallelism, SIMD (Table I; Sec. III, Sec. V): over the result widths of
+   * executed instructions pushed with aiwc_push_widths. Sums are exact below
+   * 2^64 (at most 2^32 widths of at most 65535 each). */
+  uint64_t simd_count;          /* widths pushed */
+  uint64_t simd_max;            /* "Max SIMD Width" */
+  uint64_t simd_sum;            /* sum of widths */
+  uint64_t simd_sumsq;          /* sum of squared widths */
+  double simd_mean;             /* "Mean SIMD Width" = simd_sum / simd_count */
+  double simd_sd;               /* "SD SIMD Width": population standard deviation (divides by simd_count) */
+  /* Derived parallelism quantities of the Kiviat diagrams (Sec. VI), IEEE division: */
+  double granularity;               /* 1 / work_items */
+  double barriers_per_instruction;  /* 1 / mean ITB = itb_count / total_instructions */
+  double instructions_per_operand;  /* 1 / simd_sum */
+  double load_imbalance;            /* ipt_max - ipt_min */
   /* In: optional caller buffer of n_opcodes counts (NULL to skip). */
   uint64_t* opcode_hist;
 } aiwc_metrics;
@@ -169,6 +183,14 @@ aiwc_status aiwc_push_instr_runs(aiwc_handle* h, const uint32_t* run_wi, const u
                                  const uint64_t* run_len, size_t n_runs, const uint16_t* ops,
                                  size_t n_ops, int on_device);
 
+/* The result width (number of data items) of executed instructions (Sec. V:
+ * the width of each instruction's result is recorded for the SIMD metrics of
+ * Table I), one u16 per counted instruction, in any order; barrier markers
+ * have no width. `widths` is host or device memory (on_device = 1), owned by
+ * the caller, and device memory must stay valid until the next compute.
+ * Errors: AIWC_EINVAL (null pointer with n > 0), AIWC_ECUDA, AIWC_ESTATE. */
+aiwc_status aiwc_push_widths(aiwc_handle* h, const uint16_t* widths, size_t n, int on_device);
+
 /* kernelEnd (Sec. V): reduces everything pushed since the last compute to the
  * Table I metrics, writes them to *out (and out->opcode_hist when non-NULL),
  * then resets the handle for the next invocation. Blocks until done.
@@ -190,6 +212,18 @@ aiwc_status aiwc_compute(aiwc_handle* h, aiwc_metrics* out);
 aiwc_status aiwc_compute_batch(aiwc_handle* const* hs, size_t n, aiwc_metrics* outs);
 
 aiwc_status aiwc_destroy(aiwc_handle* h);
+
+/* Whole-application view over several invocations of one kernel (Sec. VI):
+ * AIWC_AGG_SUM adds every numeric field over runs[0..n) (the paper presents
+ * "the summation of all metrics for a kernel"), AIWC_AGG_MEDIAN takes each
+ * field's median over the runs (the figures show medians across iterations):
+ * for floating-point fields the mean of the two middle values when n is
+ * even, for integer fields the lower middle value. out->opcode_hist is left
+ * as the caller set it. Host-only arithmetic: needs no device and no handle.
+ * Errors: AIWC_EINVAL (null pointers with n > 0, unknown mode). */
+#define AIWC_AGG_SUM 0
+#define AIWC_AGG_MEDIAN 1
+aiwc_status aiwc_aggregate(const aiwc_metrics* runs, size_t n, int mode, aiwc_metrics* out);
 
 /* Text of the last error on h (or of the last global error when h is NULL). */
 const char* aiwc_last_error(const aiwc_handle* h);
@@ -252,6 +286,7 @@ aiwc_status aiwc_job_open(aiwc_server* s, const aiwc_config* job_cfg, uint64_t r
  * A job is used by one thread at a time. */
 aiwc_status aiwc_job_push_mem(aiwc_job* j, const aiwc_mem_event* ev, size_t n, int on_device);
 aiwc_status aiwc_job_push_branch(aiwc_job* j, const aiwc_branch_event* ev, size_t n, int on_device);
+aiwc_status aiwc_job_push_widths(aiwc_job* j, const uint16_t* widths, size_t n, int on_device);
 aiwc_status aiwc_job_push_instr_runs(aiwc_job* j, const uint32_t* run_wi, const uint64_t* run_off,
                                      const uint64_t* run_len, size_t n_runs, const uint16_t* ops, size_t n_ops,
                                      int on_device);

@@ -7,6 +7,7 @@ CPU-baseline leg may import this package; the product path never does.
 from __future__ import annotations
 
 import ctypes
+import math
 import os
 import subprocess
 import threading
@@ -70,6 +71,8 @@ def _bind(lib):
         ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_uint64,
         ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
         ctypes.c_uint64, ctypes.POINTER(_Config), ctypes.POINTER(_Metrics), ctypes.c_void_p]
+    lib.aiwc_oracle_simd.restype = None
+    lib.aiwc_oracle_simd.argtypes = [ctypes.c_void_p, ctypes.c_uint64] + [ctypes.POINTER(ctypes.c_uint64)] * 4
     lib.aiwc_oracle_count_of_counts.restype = ctypes.c_int64
     lib.aiwc_oracle_count_of_counts.argtypes = [
         ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
@@ -144,7 +147,71 @@ def compute(trace, history_len: int = 16, cover_num: int = 9, cover_den: int = 1
         res[name] = list(v) if name == "entropy" else v
     if want_hist:
         res["opcode_hist"] = hist[:nop].copy()
+    res.update(simd(getattr(trace, "widths", None), lib))
+    res.update(derived(res))
     return res
+
+
+def simd(widths, lib=None) -> dict:
+    """Table I SIMD rows from the per-instruction result widths (Sec. V)."""
+    lib = _load() if lib is None else lib
+    w = _np(widths, np.uint16)
+    c, m, s, q = (ctypes.c_uint64() for _ in range(4))
+    lib.aiwc_oracle_simd(w.ctypes.data, w.size, ctypes.byref(c), ctypes.byref(m), ctypes.byref(s), ctypes.byref(q))
+    c, m, s, q = c.value, m.value, s.value, q.value
+    # population variance (count * sumsq - sum^2) / count^2, numerator in exact integers
+    mean = s / c if c else 0.0
+    sd = math.sqrt((c * q - s * s) / (c * c)) if c else 0.0
+    return {"simd_count": c, "simd_max": m, "simd_sum": s, "simd_sumsq": q, "simd_mean": mean, "simd_sd": sd}
+
+
+def _div(a, b) -> float:
+    # IEEE division as the metric structure defines it: x/0 is inf, 0/0 is NaN
+    a, b = float(a), float(b)
+    if b == 0.0:
+        return math.nan if a == 0.0 else math.copysign(math.inf, a)
+    return a / b
+
+
+def derived(m: dict) -> dict:
+    """The derived parallelism quantities of the Kiviat diagrams (Sec. VI)."""
+    return {
+        "granularity": _div(1, m["work_items"]),
+        # 1 / mean ITB, mean ITB = sum of ITB (= total instructions) / number of ITB values
+        "barriers_per_instruction": _div(m["itb_count"], m["total_instructions"]),
+        "instructions_per_operand": _div(1, m["simd_sum"]),
+        "load_imbalance": float(m["ipt_max"] - m["ipt_min"]),
+    }
+
+
+def aggregate(runs: list, mode: str) -> dict:
+    """Whole-application view over invocations (Sec. VI): "sum" adds every
+    numeric metric; "median" takes each metric's median across the runs (mean
+    of the two middle values for real-valued metrics, the lower middle value
+    for counts)."""
+    out = {}
+    for k in runs[0]:
+        if k == "opcode_hist":
+            continue
+        vals = [r[k] for r in runs]
+        if k == "entropy":
+            cols = list(zip(*vals))
+            out[k] = [_agg_real(list(c), mode) for c in cols]
+        elif isinstance(vals[0], float):
+            out[k] = _agg_real(vals, mode)
+        else:
+            out[k] = sum(vals) if mode == "sum" else sorted(vals)[(len(vals) - 1) // 2]
+    return out
+
+
+def _agg_real(vals, mode):
+    if mode == "sum":
+        t = 0.0
+        for v in vals:  # in run order
+            t += v
+        return t
+    v = sorted(vals)
+    return 0.5 * (v[(len(v) - 1) // 2] + v[len(v) // 2])
 
 
 def count_of_counts(mem, n: int, space_mask: int = 0xF) -> dict:

@@ -18,6 +18,7 @@
 //                       period-32 loop), invariants
 //   instruction/ITB  -- brute force, closed forms, invariants
 //   work-items       -- brute force
+//   SIMD widths      -- closed forms (constant widths, two-value mix), brute force
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -314,6 +315,25 @@ int64_t aiwc_oracle_count_of_counts(const uint8_t* mem, uint64_t n_mem, uint32_t
     ++w;
   }
   return w;
+}
+
+// SIMD width statistics (Table I "Max / Mean / SD SIMD Width"; Sec. V: the
+// result width of every executed instruction is recorded): count, maximum,
+// sum and sum of squares as exact integers. The mean and the population
+// standard deviation follow from them in the caller.
+void aiwc_oracle_simd(const uint16_t* widths, uint64_t n, uint64_t* count, uint64_t* mx, uint64_t* sum,
+                      uint64_t* sumsq) {
+  uint64_t m = 0, s = 0, q = 0;
+  for (uint64_t i = 0; i < n; ++i) {
+    const uint64_t w = widths[i];
+    if (w > m) m = w;
+    s += w;
+    q += w * w;
+  }
+  *count = n;
+  *mx = m;
+  *sum = s;
+  *sumsq = q;
 }
 
 }  // extern "C"

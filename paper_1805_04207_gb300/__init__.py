@@ -50,8 +50,14 @@ METRIC_FIELDS = [
     ("branch_events", _U64), ("branch_sites", _U64), ("branch_cover", _U64), ("branch_patterns", _U64),
     ("branch_minsum", _U64), ("albe", _F64),
     ("unique_rw_ratio", _F64), ("reread_ratio", _F64), ("rewrite_ratio", _F64),
+    ("simd_count", _U64), ("simd_max", _U64), ("simd_sum", _U64), ("simd_sumsq", _U64),
+    ("simd_mean", _F64), ("simd_sd", _F64),
+    ("granularity", _F64), ("barriers_per_instruction", _F64), ("instructions_per_operand", _F64),
+    ("load_imbalance", _F64),
     ("opcode_hist", ctypes.POINTER(ctypes.c_uint64)),
 ]
+AGG_SUM = 0
+AGG_MEDIAN = 1
 
 
 class aiwc_metrics(ctypes.Structure):
@@ -68,6 +74,8 @@ SIGNATURES = {
     "aiwc_push_mem": (_ST, [_VP, _VP, _SZ, ctypes.c_int]),
     "aiwc_push_branch": (_ST, [_VP, _VP, _SZ, ctypes.c_int]),
     "aiwc_push_instr": (_ST, [_VP, ctypes.c_uint32, _VP, _SZ, ctypes.c_int]),
+    "aiwc_push_widths": (_ST, [_VP, _VP, _SZ, ctypes.c_int]),
+    "aiwc_aggregate": (_ST, [ctypes.POINTER(aiwc_metrics), _SZ, ctypes.c_int, ctypes.POINTER(aiwc_metrics)]),
     "aiwc_push_instr_runs": (_ST, [_VP, _VP, _VP, _VP, _SZ, _VP, _SZ, ctypes.c_int]),
     "aiwc_compute": (_ST, [_VP, ctypes.POINTER(aiwc_metrics)]),
     "aiwc_compute_batch": (_ST, [ctypes.POINTER(_VP), _SZ, ctypes.POINTER(aiwc_metrics)]),
@@ -84,6 +92,7 @@ SIGNATURES = {
     "aiwc_job_open": (_ST, [_VP, ctypes.POINTER(aiwc_config), ctypes.c_uint64, ctypes.POINTER(_VP)]),
     "aiwc_job_push_mem": (_ST, [_VP, _VP, _SZ, ctypes.c_int]),
     "aiwc_job_push_branch": (_ST, [_VP, _VP, _SZ, ctypes.c_int]),
+    "aiwc_job_push_widths": (_ST, [_VP, _VP, _SZ, ctypes.c_int]),
     "aiwc_job_push_instr_runs": (_ST, [_VP, _VP, _VP, _VP, _SZ, _VP, _SZ, ctypes.c_int]),
     "aiwc_job_finish": (_ST, [_VP]),
     "aiwc_job_poll": (_ST, [_VP, ctypes.POINTER(aiwc_metrics)]),
@@ -145,6 +154,31 @@ def aiwc_push_instr(h, work_item: int, ptr: int, n: int, on_device: bool) -> Non
 
 def aiwc_push_instr_runs(h, wi_ptr, off_ptr, len_ptr, n_runs, ops_ptr, n_ops, on_device: bool) -> None:
     _check(lib.aiwc_push_instr_runs(h, wi_ptr, off_ptr, len_ptr, n_runs, ops_ptr, n_ops, int(on_device)), h)
+
+
+def aiwc_push_widths(h, ptr: int, n: int, on_device: bool) -> None:
+    _check(lib.aiwc_push_widths(h, ptr, n, int(on_device)), h)
+
+
+def _from_dict(d: dict) -> aiwc_metrics:
+    m = aiwc_metrics()
+    for name, _ in METRIC_FIELDS:
+        if name == "opcode_hist" or name not in d:
+            continue
+        if name == "entropy":
+            for i, v in enumerate(d[name]):
+                m.entropy[i] = v
+        else:
+            setattr(m, name, d[name])
+    return m
+
+
+def aiwc_aggregate(runs: list, mode: int) -> dict:
+    """Sum (AGG_SUM) or median (AGG_MEDIAN) of metric dicts over invocations."""
+    arr = (aiwc_metrics * max(1, len(runs)))(*[_from_dict(d) for d in runs])
+    out = aiwc_metrics()
+    _check(lib.aiwc_aggregate(arr, len(runs), mode, ctypes.byref(out)))
+    return _to_dict(out)
 
 
 def _to_dict(m: aiwc_metrics) -> dict:
@@ -244,6 +278,10 @@ def aiwc_job_push_mem(j, ptr, n, on_device):
 
 def aiwc_job_push_branch(j, ptr, n, on_device):
     _check(lib.aiwc_job_push_branch(j, ptr, n, int(on_device)))
+
+
+def aiwc_job_push_widths(j, ptr, n, on_device):
+    _check(lib.aiwc_job_push_widths(j, ptr, n, int(on_device)))
 
 
 def aiwc_job_push_instr_runs(j, wi_ptr, off_ptr, len_ptr, n_runs, ops_ptr, n_ops, on_device):

@@ -7,7 +7,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import (aiwc_compute, aiwc_compute_batch, aiwc_config_default, aiwc_create, aiwc_destroy, aiwc_device_bytes, aiwc_push_branch,
-               aiwc_push_instr, aiwc_push_instr_runs, aiwc_push_mem, aiwc_set_stage_timing, aiwc_stage_times)
+               aiwc_push_instr, aiwc_push_instr_runs, aiwc_push_widths, aiwc_push_mem, aiwc_set_stage_timing, aiwc_stage_times)
 
 
 def _ptr(t):
@@ -66,6 +66,14 @@ class Characterizer:
         aiwc_push_instr(self.h, work_item, p, n, dev)
         if dev:
             self._keep.append(ops)
+
+    def push_widths(self, widths) -> None:
+        """widths: (n,) int16 / uint16 result widths of executed instructions."""
+        p, dev = _ptr(widths)
+        n = widths.numel() if hasattr(widths, "numel") else np.asarray(widths).size
+        aiwc_push_widths(self.h, p, n, dev)
+        if dev:
+            self._keep.append(widths)
 
     def push_instr_runs(self, run_wi, run_off, run_len, ops) -> None:
         """run_wi: int32/uint32; run_off, run_len: int64; ops: int16/uint16; all on one side."""
@@ -126,6 +134,9 @@ def push_trace(c: Characterizer, trace) -> None:
         c.push_branch(trace.br)
     if trace.run_wi is not None and trace.run_wi.shape[0]:
         c.push_instr_runs(trace.run_wi.to(dtype=_i32(trace.run_wi)), trace.run_off, trace.run_len, trace.ops)
+    widths = getattr(trace, "widths", None)
+    if widths is not None and widths.shape[0]:
+        c.push_widths(widths)
 
 
 def _i32(t):

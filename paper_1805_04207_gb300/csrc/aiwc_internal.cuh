@@ -72,6 +72,7 @@ struct DevState {
   u32 br_persite;        // the per-site branch path applies (set on the device)
   u32 br_last_wi[2];     // last work-item id of the previous / current push (by push parity)
   u32 run_unsorted;      // some run key is below its predecessor (the run sort is needed)
+  u64 simd_count, simd_sum, simd_sumsq, simd_max;  // result widths of executed instructions
   u32 sort_cur[8];       // which ping-pong buffer holds each sort's data
   u32 pad;
 };
@@ -343,6 +344,8 @@ struct RunBatchArgs {
   Arena* arena{};
 };
 void launch_instr_runs(const RunBatchArgs& a, cudaStream_t s);
+// Adds the count, sum, sum of squares and maximum of u16 widths to the arena.
+void launch_simd_widths(const uint16_t* widths, u64 n, Arena* arena, cudaStream_t s);
 // Sets *flag when keys[0..n) are not in non-decreasing order.
 void launch_keys_sorted(const u64* keys, u64 n, u32* flag, cudaStream_t s);
 

@@ -8,6 +8,7 @@
 // runs, finalises and copies one fixed-size result back.
 #include <algorithm>
 #include <atomic>
+#include <cstddef>
 #include <functional>
 #include <mutex>
 #include <cstdio>
@@ -583,6 +584,23 @@ aiwc_status aiwc_push_branch(aiwc_handle* h, const aiwc_branch_event* ev, size_t
   return AIWC_OK;
 }
 
+aiwc_status aiwc_push_widths(aiwc_handle* h, const uint16_t* widths, size_t n, int on_device) {
+  aiwc_status s = check_usable(h);
+  if (s != AIWC_OK) return s;
+  if (n == 0) return AIWC_OK;
+  if (!widths) return fail(h, AIWC_EINVAL, "null width pointer", false);
+  DeviceGuard g(h->cfg.device);
+  StageScope scope(h, kStInstrRuns);
+  if (on_device) {
+    launch_simd_widths(widths, n, h->arena, h->stream);
+    CK(cudaGetLastError());
+    return AIWC_OK;
+  }
+  return staged_copy(h, widths, n * 2, 2, [&](void* p, size_t, size_t cnt) {
+    launch_simd_widths((const uint16_t*)p, cnt, h->arena, h->stream);
+  });
+}
+
 aiwc_status aiwc_push_instr(aiwc_handle* h, uint32_t work_item, const uint16_t* ops, size_t n, int on_device) {
   aiwc_status s = check_usable(h);
   if (s != AIWC_OK) return s;
@@ -1152,6 +1170,73 @@ aiwc_status aiwc_compute_batch(aiwc_handle* const* hs, size_t n, aiwc_metrics* o
     if (e != AIWC_OK && worst == AIWC_OK) worst = e;
   }
   return worst;
+}
+
+aiwc_status aiwc_aggregate(const aiwc_metrics* runs, size_t n, int mode, aiwc_metrics* out) {
+  if (!out || (n && !runs)) return fail(nullptr, AIWC_EINVAL, "null aggregate argument");
+  if (mode != AIWC_AGG_SUM && mode != AIWC_AGG_MEDIAN) return fail(nullptr, AIWC_EINVAL, "unknown aggregate mode");
+  // every numeric field of aiwc_metrics, by offset
+  static const size_t kU64[] = {
+      offsetof(aiwc_metrics, total_instructions), offsetof(aiwc_metrics, unique_opcodes),
+      offsetof(aiwc_metrics, opcode_cover), offsetof(aiwc_metrics, work_items), offsetof(aiwc_metrics, barriers),
+      offsetof(aiwc_metrics, itb_count), offsetof(aiwc_metrics, itb_min), offsetof(aiwc_metrics, itb_max),
+      offsetof(aiwc_metrics, itb_median_lo), offsetof(aiwc_metrics, itb_median_hi),
+      offsetof(aiwc_metrics, ipt_count), offsetof(aiwc_metrics, ipt_min), offsetof(aiwc_metrics, ipt_max),
+      offsetof(aiwc_metrics, ipt_median_lo), offsetof(aiwc_metrics, ipt_median_hi),
+      offsetof(aiwc_metrics, total_reads), offsetof(aiwc_metrics, total_writes), offsetof(aiwc_metrics, footprint),
+      offsetof(aiwc_metrics, footprint_cover), offsetof(aiwc_metrics, unique_reads),
+      offsetof(aiwc_metrics, unique_writes), offsetof(aiwc_metrics, branch_events),
+      offsetof(aiwc_metrics, branch_sites), offsetof(aiwc_metrics, branch_cover),
+      offsetof(aiwc_metrics, branch_patterns), offsetof(aiwc_metrics, branch_minsum),
+      offsetof(aiwc_metrics, simd_count), offsetof(aiwc_metrics, simd_max), offsetof(aiwc_metrics, simd_sum),
+      offsetof(aiwc_metrics, simd_sumsq)};
+  std::vector<size_t> f64 = {
+      offsetof(aiwc_metrics, itb_median), offsetof(aiwc_metrics, ipt_median), offsetof(aiwc_metrics, albe),
+      offsetof(aiwc_metrics, unique_rw_ratio), offsetof(aiwc_metrics, reread_ratio),
+      offsetof(aiwc_metrics, rewrite_ratio), offsetof(aiwc_metrics, simd_mean), offsetof(aiwc_metrics, simd_sd),
+      offsetof(aiwc_metrics, granularity), offsetof(aiwc_metrics, barriers_per_instruction),
+      offsetof(aiwc_metrics, instructions_per_operand), offsetof(aiwc_metrics, load_imbalance)};
+  for (int l = 0; l <= AIWC_MAX_SKIP; ++l) f64.push_back(offsetof(aiwc_metrics, entropy) + l * sizeof(double));
+  uint64_t* keep_hist = out->opcode_hist;
+  aiwc_metrics r;
+  memset(&r, 0, sizeof(r));
+  auto u64_at = [](const aiwc_metrics& m, size_t off) {
+    uint64_t v;
+    memcpy(&v, reinterpret_cast<const char*>(&m) + off, 8);
+    return v;
+  };
+  auto f64_at = [](const aiwc_metrics& m, size_t off) {
+    double v;
+    memcpy(&v, reinterpret_cast<const char*>(&m) + off, 8);
+    return v;
+  };
+  for (size_t off : kU64) {
+    uint64_t v = 0;
+    if (mode == AIWC_AGG_SUM) {
+      for (size_t i = 0; i < n; ++i) v += u64_at(runs[i], off);
+    } else if (n) {
+      std::vector<uint64_t> xs(n);
+      for (size_t i = 0; i < n; ++i) xs[i] = u64_at(runs[i], off);
+      std::sort(xs.begin(), xs.end());
+      v = xs[(n - 1) / 2];
+    }
+    memcpy(reinterpret_cast<char*>(&r) + off, &v, 8);
+  }
+  for (size_t off : f64) {
+    double v = 0.0;
+    if (mode == AIWC_AGG_SUM) {
+      for (size_t i = 0; i < n; ++i) v += f64_at(runs[i], off);
+    } else if (n) {
+      std::vector<double> xs(n);
+      for (size_t i = 0; i < n; ++i) xs[i] = f64_at(runs[i], off);
+      std::sort(xs.begin(), xs.end());
+      v = 0.5 * (xs[(n - 1) / 2] + xs[n / 2]);
+    }
+    memcpy(reinterpret_cast<char*>(&r) + off, &v, 8);
+  }
+  r.opcode_hist = keep_hist;
+  *out = r;
+  return AIWC_OK;
 }
 
 aiwc_status aiwc_destroy(aiwc_handle* h) {

@@ -76,6 +76,7 @@ __device__ __forceinline__ void overflow_append(u64* over, u64 cap, DevState* st
 }
 
 __device__ __forceinline__ u64 umin64(u64 a, u64 b) { return a < b ? a : b; }
+__device__ __forceinline__ u64 umax64(u64 a, u64 b) { return a > b ? a : b; }
 
 __device__ __forceinline__ bool gate_open(const u32* gate, u32 want) { return !gate || *gate == want; }
 

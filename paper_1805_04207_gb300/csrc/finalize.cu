@@ -355,9 +355,12 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(FinalizeArgs a) {
     if (threadIdx.x == 0) {
       if (itb) {
         m->itb_count = c; m->itb_min = mn; m->itb_max = mx; m->itb_median_lo = lo; m->itb_median_hi = hi;
+        // 1 / mean ITB, mean ITB = total instructions / ITB count (Sec. VI)
+        m->barriers_per_instruction = (double)c / (double)st.total_instructions;
         m->itb_median = med;
       } else {
         m->ipt_count = c; m->ipt_min = mn; m->ipt_max = mx; m->ipt_median_lo = lo; m->ipt_median_hi = hi;
+        m->load_imbalance = (double)(mx - mn);  // Sec. VI
         m->ipt_median = med;
       }
     }
@@ -382,6 +385,24 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(FinalizeArgs a) {
     m->unique_rw_ratio = (double)st.unique_reads / (double)st.unique_writes;
     m->reread_ratio = (double)st.unique_reads / (double)st.total_reads;
     m->rewrite_ratio = (double)st.unique_writes / (double)st.total_writes;
+    // SIMD widths (Table I): population variance from exact integer sums,
+    // (count * sumsq - sum^2) / count^2
+    m->simd_count = st.simd_count;
+    m->simd_max = st.simd_max;
+    m->simd_sum = st.simd_sum;
+    m->simd_sumsq = st.simd_sumsq;
+    if (st.simd_count) {
+      typedef unsigned __int128 u128;
+      const u128 num = (u128)st.simd_count * st.simd_sumsq - (u128)st.simd_sum * st.simd_sum;
+      m->simd_mean = (double)st.simd_sum / (double)st.simd_count;
+      m->simd_sd = sqrt((double)num / ((double)st.simd_count * (double)st.simd_count));
+    } else {
+      m->simd_mean = 0.0;
+      m->simd_sd = 0.0;
+    }
+    // derived parallelism quantities of the Kiviat diagrams (Sec. VI)
+    m->granularity = 1.0 / (double)st.work_items;
+    m->instructions_per_operand = 1.0 / (double)st.simd_sum;
     m->opcode_hist = nullptr;
     a.result->err = st.err;
   }

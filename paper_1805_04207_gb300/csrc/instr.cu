@@ -265,6 +265,44 @@ __global__ void __launch_bounds__(256) k_instr_combine(CombineArgs a) {
   }
 }
 
+// SIMD metrics (Table I): count, sum, sum of squares and maximum of the
+// result widths; eight widths per 16-byte load when the array is aligned.
+__global__ void __launch_bounds__(256) k_simd_widths(const uint16_t* w, u64 n, Arena* arena) {
+  __shared__ u64 red64[32];
+  u64 sum = 0, sumsq = 0, mx = 0;
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  const bool aligned = ((reinterpret_cast<uintptr_t>(w) & 15u) == 0);
+  const u64 nv = aligned ? n / 8 : 0;
+  const uint4* w8 = reinterpret_cast<const uint4*>(w);
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) {
+    const uint4 v = __ldcs(w8 + i);
+    const u32 p[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const u32 lo = p[q] & 0xFFFFu, hi = p[q] >> 16;
+      sum += lo + hi;
+      sumsq += (u64)(lo * lo) + (u64)(hi * hi);
+      mx = umax64(mx, max(lo, hi));
+    }
+  }
+  for (u64 i = nv * 8 + (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const u32 x = w[i];
+    sum += x;
+    sumsq += (u64)x * x;
+    mx = umax64(mx, x);
+  }
+  sum = block_reduce(sum, OpAdd(), 0ull, red64);
+  sumsq = block_reduce(sumsq, OpAdd(), 0ull, red64);
+  mx = block_reduce(mx, OpMax(), 0ull, red64);
+  if (threadIdx.x == 0) {
+    DevState* st = &arena->st;
+    if (sum) atomicAdd(&st->simd_sum, sum);
+    if (sumsq) atomicAdd(&st->simd_sumsq, sumsq);
+    if (mx) atomicMax(&st->simd_max, mx);
+    if (blockIdx.x == 0) atomicAdd(&st->simd_count, n);
+  }
+}
+
 __global__ void __launch_bounds__(256) k_keys_sorted(const u64* keys, u64 n, u32* flag) {
   bool bad = false;
   for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x + 1; i < n; i += (u64)gridDim.x * blockDim.x)
@@ -273,6 +311,13 @@ __global__ void __launch_bounds__(256) k_keys_sorted(const u64* keys, u64 n, u32
 }
 
 }  // namespace
+
+void launch_simd_widths(const uint16_t* widths, u64 n, Arena* arena, cudaStream_t s) {
+  if (n == 0) return;
+  const u64 blocks = std::min<u64>((n + 8 * 256 - 1) / (8 * 256), 152ull * 8);
+  k_simd_widths<<<(unsigned)blocks, 256, 0, s>>>(widths, n, arena);
+  count_launches(1);
+}
 
 void launch_keys_sorted(const u64* keys, u64 n, u32* flag, cudaStream_t s) {
   if (n < 2) return;

@@ -214,6 +214,11 @@ aiwc_status aiwc_job_push_branch(aiwc_job* j, const aiwc_branch_event* ev, size_
   return aiwc_push_branch(j->h, ev, n, on_device);
 }
 
+aiwc_status aiwc_job_push_widths(aiwc_job* j, const uint16_t* widths, size_t n, int on_device) {
+  if (!j || j->state != aiwc_job::kOpen) return srv_fail(AIWC_EINVAL, "job is not open");
+  return aiwc_push_widths(j->h, widths, n, on_device);
+}
+
 aiwc_status aiwc_job_push_instr_runs(aiwc_job* j, const uint32_t* run_wi, const uint64_t* run_off,
                                      const uint64_t* run_len, size_t n_runs, const uint16_t* ops, size_t n_ops,
                                      int on_device) {

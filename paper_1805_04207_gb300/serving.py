@@ -4,7 +4,8 @@ from __future__ import annotations
 import numpy as np
 
 from . import (aiwc_config_default, aiwc_job_finish, aiwc_job_open, aiwc_job_poll, aiwc_job_push_branch,
-               aiwc_job_push_instr_runs, aiwc_job_push_mem, aiwc_job_wait, aiwc_server_config_default,
+               aiwc_job_push_instr_runs, aiwc_job_push_mem, aiwc_job_push_widths, aiwc_job_wait,
+               aiwc_server_config_default,
                aiwc_server_create, aiwc_server_destroy, aiwc_server_stats)
 from .api import _ptr
 
@@ -29,6 +30,12 @@ class Job:
         aiwc_job_push_branch(self.j, p, events.shape[0], dev)
         if dev:
             self._keep.append(events)
+
+    def push_widths(self, widths) -> None:
+        p, dev = _ptr(widths)
+        aiwc_job_push_widths(self.j, p, widths.shape[0], dev)
+        if dev:
+            self._keep.append(widths)
 
     def push_instr_runs(self, run_wi, run_off, run_len, ops) -> None:
         ptrs = [_ptr(t) for t in (run_wi, run_off, run_len, ops)]

@@ -139,12 +139,13 @@ class Trace:
     run_len: torch.Tensor | None = None  # (R,) int64 length of each run
     n_opcodes: int = 65535
     meta: dict = field(default_factory=dict)
+    widths: torch.Tensor | None = None   # (I',) int16 result width of each counted instruction
 
     def to(self, device) -> "Trace":
         def mv(t):
             return None if t is None else t.to(device)
         return Trace(self.name, mv(self.mem), mv(self.br), mv(self.ops), mv(self.run_wi),
-                     mv(self.run_off), mv(self.run_len), self.n_opcodes, dict(self.meta))
+                     mv(self.run_off), mv(self.run_len), self.n_opcodes, dict(self.meta), mv(self.widths))
 
     @property
     def n_mem(self) -> int:
@@ -159,7 +160,8 @@ class Trace:
         return 0 if self.ops is None else int(self.ops.shape[0])
 
     def nbytes(self) -> int:
-        return 16 * self.n_mem + 8 * self.n_br + 2 * self.n_ops
+        nw = 0 if self.widths is None else int(self.widths.shape[0])
+        return 16 * self.n_mem + 8 * self.n_br + 2 * self.n_ops + 2 * nw
 
 
 def _blocks(n: int, block: int = 1 << 24):
@@ -213,9 +215,12 @@ def tiny(device="cpu", seed: int = 0) -> Trace:
     pos = g - run_off[wi_of]
     ops = (_below(hash3(seed, 3, g), 64)).to(torch.int16)
     ops[pos == 500] = BARRIER_I16
+    # result widths of the counted instructions: 1, 2, 4, 8 or 16 data items
+    n_counted = int((pos != 500).sum())
+    widths = (1 << _below(hash3(seed, 4, torch.arange(n_counted, dtype=torch.int64)), 5)).to(torch.int16)
     return Trace("tiny", mem, br, ops.to(dev), torch.arange(W, dtype=torch.int64, device=dev),
                  run_off.to(dev), run_len.to(dev), n_opcodes=64,
-                 meta={"seed": seed, "work_items": W})
+                 meta={"seed": seed, "work_items": W}, widths=widths.to(dev))
 
 
 # --------------------------------------------------------------------------

@@ -22,8 +22,14 @@ INT_FIELDS = ["total_instructions", "unique_opcodes", "opcode_cover", "work_item
               "itb_count", "itb_min", "itb_max", "itb_median_lo", "itb_median_hi",
               "ipt_count", "ipt_min", "ipt_max", "ipt_median_lo", "ipt_median_hi",
               "total_reads", "total_writes", "footprint", "footprint_cover", "unique_reads", "unique_writes",
-              "branch_events", "branch_sites", "branch_cover", "branch_patterns", "branch_minsum"]
+              "branch_events", "branch_sites", "branch_cover", "branch_patterns", "branch_minsum",
+              "simd_count", "simd_max", "simd_sum", "simd_sumsq"]
 ENTROPY_TOL = 1e-9
+# SIMD mean / SD and the Kiviat quantities are single FP64 divisions (and a
+# square root) of exact integers: they agree to a few ulps
+REAL_FIELDS = ["simd_mean", "simd_sd", "granularity", "barriers_per_instruction", "instructions_per_operand",
+               "load_imbalance"]
+REAL_RTOL = 1e-13
 
 
 @pytest.fixture(scope="module")
@@ -44,6 +50,9 @@ def assert_parity(g, o, entropy_tol=ENTROPY_TOL, hist=True):
     for r in ("unique_rw_ratio", "reread_ratio", "rewrite_ratio"):
         a, b = g[r], o[r]
         assert (math.isnan(a) and math.isnan(b)) or a == b, (r, a, b)
+    for r in REAL_FIELDS:
+        a, b = g[r], o[r]
+        assert (math.isnan(a) and math.isnan(b)) or a == b or abs(a - b) <= REAL_RTOL * abs(b), (r, a, b)
     if hist:
         assert np.array_equal(np.asarray(g["opcode_hist"], dtype=np.uint64),
                               np.asarray(o["opcode_hist"], dtype=np.uint64))
@@ -60,6 +69,8 @@ def run_gpu(P, trace, on_device=True, split=1, single_runs=False, **cfg):
             if tr.br is not None and tr.br.shape[0]:
                 n = tr.br.shape[0]
                 c.push_branch(tr.br[part * n // split:(part + 1) * n // split].contiguous())
+        if tr.widths is not None and tr.widths.shape[0]:
+            c.push_widths(tr.widths)
         if tr.run_wi is not None and tr.run_wi.shape[0]:
             if single_runs:
                 for w, o, ln in zip(trace.run_wi.tolist(), trace.run_off.tolist(), trace.run_len.tolist()):
@@ -194,6 +205,46 @@ def test_site_counting_sort(P, n, n_sites, wi_sorted, split, h):
     4096) and its fallbacks give the oracle's branch metrics."""
     tr = _site_trace(7 + n_sites, n, n_sites, wi_sorted)
     assert_parity(run_gpu(P, tr, split=split, history_len=h), oracle.compute(tr, history_len=h))
+
+
+@pytest.mark.parametrize("n,offset,on_device", [(0, 0, True), (1, 0, True), (4099, 1, True), (300_001, 0, False),
+                                                  (1_000_003, 3, True)])
+def test_simd_widths(P, n, offset, on_device):
+    """SIMD widths (Table I) pushed from host or device memory, aligned or
+    not, in one or two pushes; every other metric is unaffected."""
+    rng = np.random.default_rng(n + offset)
+    w = rng.integers(0, 65536, n + offset, dtype=np.int64).astype(np.uint16).view(np.int16)
+    widths = torch.from_numpy(w.copy())
+    tr = instr_only([(0, [1, 2, -1, 3])], n_opcodes=8)
+    with P.Characterizer(n_opcodes=8) as c:
+        c.push_instr_runs(tr.run_wi.to(torch.int32), tr.run_off, tr.run_len, tr.ops)
+        src = widths.cuda() if on_device else widths
+        half = (n + offset) // 2
+        if offset:
+            c.push_widths(src[offset:half].contiguous() if not on_device else src[offset:half])
+            c.push_widths(src[half:])
+        else:
+            c.push_widths(src)
+        g = c.compute(want_hist=True)
+    tr.widths = widths[offset:]
+    assert_parity(g, oracle.compute(tr))
+
+
+def test_aggregate_matches_oracle(P):
+    """Sum and median over invocations (Sec. VI) of real GPU results."""
+    runs = [run_gpu(P, synth.pattern_trace(k, c, f, seed=3, stream=i)) for i, (k, c, f) in
+            enumerate([("zipf", 50_000, 9_000), ("stencil", 70_001, 20_000), ("gemm", 64_000, 16_384),
+                       ("uniform", 20_000, 20_000)])]
+    for mode, pm in (("sum", P.AGG_SUM), ("median", P.AGG_MEDIAN)):
+        g = P.aiwc_aggregate(runs, pm)
+        o = oracle.aggregate(runs, mode)
+        for k, v in o.items():
+            if k == "entropy":
+                assert all(abs(a - b) <= 1e-12 * max(1.0, abs(b)) for a, b in zip(g[k], v)), k
+            elif isinstance(v, float):
+                assert (math.isnan(v) and math.isnan(g[k])) or g[k] == v or abs(g[k] - v) <= 1e-12 * abs(v), k
+            else:
+                assert g[k] == v, (k, g[k], v)
 
 
 def test_value_overflow_paths(P):

@@ -43,6 +43,8 @@ def _push_chunks(job, tr, n_chunks=4):
         if part.shape[0]:
             job.push_branch(part)
     job.push_instr_runs(tr.run_wi.to(torch.int32), tr.run_off, tr.run_len, tr.ops)
+    if tr.widths is not None and tr.widths.shape[0]:
+        job.push_widths(tr.widths)
 
 
 def test_serving_results_equal_alone_and_in_the_mix(P):

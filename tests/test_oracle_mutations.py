@@ -9,9 +9,11 @@ from __future__ import annotations
 import json
 import math
 import os
+import statistics
 
 import numpy as np
 import pytest
+import torch
 
 import oracle
 import synth
@@ -36,6 +38,8 @@ MUTATIONS = {
     "barrier_counted_as_instruction": ("        itb.push_back(st.first);\n        st.first = 0;\n        ++barriers;",
                                        "        itb.push_back(st.first);\n        st.first = 0;\n        ++barriers;\n        ++hist[0];"),
     "work_items_memory_ignored": ("    work_items.insert(wi);\n    if (addr", "    if (addr"),
+    "simd_square_dropped": ("q += w * w;", "q += w;"),
+    "simd_max_first_only": ("if (w > m) m = w;", "if (i == 0) m = w;"),
 }
 
 
@@ -85,11 +89,20 @@ def _pins_pass(lib):
         o = comp(synth.tiny())
         if (o["itb_median"], o["branch_minsum"], o["branch_patterns"]) != (391.0, 240, 7936):
             return False
+        # SIMD widths: a two-value closed form and a brute-force population SD
+        tr = instr_only([(0, [1, 2])])
+        tr.widths = torch.tensor([1, 3] * 50 + [7], dtype=torch.int16)
+        o = comp(tr)
+        vals = [1, 3] * 50 + [7]
+        if (o["simd_max"], o["simd_sum"], o["simd_sumsq"]) != (7, sum(vals), sum(v * v for v in vals)):
+            return False
+        if abs(o["simd_sd"] - statistics.pstdev(vals)) > 1e-12:
+            return False
         for k, t in ((4, 0), (6, 2)):
             o = comp(mem_only([(1 << 40) + (i << t) for i in range(1 << k) for _ in range(3)]))
             if max(abs(o["entropy"][n] - max(0, k - max(0, n - t))) for n in range(11)) > 1e-12:
                 return False
-    except oracle.OracleInvalidInput:
+    except (oracle.OracleInvalidInput, ValueError):  # a mutated oracle may also fail outright
         return False
     return True
 

@@ -217,3 +217,71 @@ def test_invalid_inputs_rejected():
         with pytest.raises(oracle.OracleInvalidInput):
             oracle.compute(branch_only([0], [0], [1]), history_len=h)
     assert oracle.compute(mem_only([(1 << 61) - 1]))["footprint"] == 1
+
+
+# ---------------------------------------------------------------- SIMD widths, Kiviat quantities, aggregation
+# Table I SIMD rows (Sec. V records each executed instruction's result width)
+# and the derived parallelism quantities of Sec. VI.
+
+def test_simd_closed_forms():
+    import statistics
+    r = oracle.simd(np.full(1000, 4, dtype=np.uint16))
+    assert (r["simd_count"], r["simd_max"], r["simd_sum"], r["simd_mean"], r["simd_sd"]) == (1000, 4, 4000, 4.0, 0.0)
+    r = oracle.simd(np.array([1, 3] * 500, dtype=np.uint16))      # two values, equal shares
+    assert (r["simd_mean"], r["simd_sd"]) == (2.0, 1.0)
+    r = oracle.simd(np.zeros(0, dtype=np.uint16))
+    assert (r["simd_count"], r["simd_mean"], r["simd_sd"]) == (0, 0.0, 0.0)
+    rng = np.random.default_rng(5)
+    w = rng.integers(0, 65536, 20_001).astype(np.uint16)
+    r = oracle.simd(w)
+    vals = [int(x) for x in w]
+    assert r["simd_max"] == max(vals) and r["simd_sum"] == sum(vals)
+    assert r["simd_sumsq"] == sum(v * v for v in vals)
+    assert abs(r["simd_sd"] - statistics.pstdev(vals)) <= 1e-9 * statistics.pstdev(vals)
+    assert abs(r["simd_mean"] - statistics.fmean(vals)) <= 1e-12 * statistics.fmean(vals)
+
+
+def test_kiviat_quantities_on_the_tiny_workload():
+    r = oracle.compute(synth.tiny())
+    # 256 work-items; 256 barriers + 256 final tallies over 200,000 instructions;
+    # IPT 782 (64 work-items) and 781 (192)
+    assert r["granularity"] == 1.0 / 256
+    assert r["barriers_per_instruction"] == 512 / 200_000
+    assert r["load_imbalance"] == 1.0
+    assert r["instructions_per_operand"] == 1.0 / r["simd_sum"]
+    empty = oracle.compute(synth.Trace("empty"))
+    assert math.isinf(empty["granularity"]) and math.isnan(empty["barriers_per_instruction"])
+
+
+def test_aggregate_sum_and_median_by_hand():
+    runs = [{"footprint": 5, "albe": 0.5, "entropy": [1.0, 2.0]},
+            {"footprint": 1, "albe": 0.25, "entropy": [3.0, 2.0]},
+            {"footprint": 9, "albe": 1.0, "entropy": [2.0, 0.0]},
+            {"footprint": 2, "albe": 0.0, "entropy": [0.0, 4.0]}]
+    s = oracle.aggregate(runs, "sum")
+    assert s == {"footprint": 17, "albe": 1.75, "entropy": [6.0, 8.0]}
+    m = oracle.aggregate(runs, "median")
+    # counts: lower middle of {1, 2, 5, 9}; reals: mean of the two middle values
+    assert m == {"footprint": 2, "albe": 0.375, "entropy": [1.5, 2.0]}
+    m3 = oracle.aggregate(runs[:3], "median")
+    assert m3 == {"footprint": 5, "albe": 0.5, "entropy": [2.0, 2.0]}
+
+
+def test_library_aggregate_matches_oracle_on_cpu():
+    """aiwc_aggregate is host arithmetic: it runs without a GPU."""
+    P = pytest.importorskip("paper_1805_04207_gb300")
+    runs = [oracle.compute(synth.pattern_trace(k, c, f, seed=2, stream=i))
+            for i, (k, c, f) in enumerate([("zipf", 3000, 500), ("stencil", 4001, 900), ("stream", 2000, 300)])]
+    for r in runs:
+        r.pop("opcode_hist", None)
+    for mode, pm in (("sum", P.AGG_SUM), ("median", P.AGG_MEDIAN)):
+        g, o = P.aiwc_aggregate(runs, pm), oracle.aggregate(runs, mode)
+        for k, v in o.items():
+            if k == "entropy":
+                assert g[k] == pytest.approx(v, rel=1e-15, abs=0)
+            elif isinstance(v, float) and math.isnan(v):
+                assert math.isnan(g[k])
+            else:
+                assert g[k] == v, k
+    with pytest.raises(P.AiwcError):
+        P.aiwc_aggregate(runs, 7)

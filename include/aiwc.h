@@ -131,6 +131,9 @@ typedef struct aiwc_metrics {
   uint64_t branch_patterns;     /* N': outcomes that have a full history */
   uint64_t branch_minsum;       /* M = sum over history patterns of min(taken, not taken) */
   double albe;                  /* average linear branch entropy = 2 M / N' */
+  double yokota;                /* Yokota branch entropy. Reading (the paper gives no normalisation): the entropy
+                                 * of the h-outcome history given the site, over the N' predicted outcomes,
+                                 * divided by h -- in [0, 1] */
   /* Ratios as printed in Table I (IEEE division: x/0 gives inf or NaN). */
   double unique_rw_ratio;       /* unique reads / unique writes */
   double reread_ratio;          /* unique reads / total reads */

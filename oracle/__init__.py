@@ -33,6 +33,7 @@ METRIC_FIELDS = [
     ("entropy", ctypes.c_double * 11),
     ("branch_events", ctypes.c_uint64), ("branch_sites", ctypes.c_uint64), ("branch_cover", ctypes.c_uint64),
     ("branch_patterns", ctypes.c_uint64), ("branch_minsum", ctypes.c_uint64), ("albe", ctypes.c_double),
+    ("yokota", ctypes.c_double),
     ("unique_rw_ratio", ctypes.c_double), ("reread_ratio", ctypes.c_double), ("rewrite_ratio", ctypes.c_double),
 ]
 

@@ -19,6 +19,8 @@
 //   instruction/ITB  -- brute force, closed forms, invariants
 //   work-items       -- brute force
 //   SIMD widths      -- closed forms (constant widths, two-value mix), brute force
+//   Yokota entropy   -- closed forms (constant branch 0, de Bruijn sequence 1), brute force;
+//                       parity unpinned for the normalisation, which is a reading
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -57,6 +59,7 @@ struct OracleMetrics {
   double entropy[11];
   uint64_t branch_events, branch_sites, branch_cover, branch_patterns, branch_minsum;
   double albe;
+  double yokota;
   double unique_rw_ratio, reread_ratio, rewrite_ratio;
 };
 
@@ -227,6 +230,28 @@ int aiwc_oracle_compute(const uint8_t* mem, uint64_t n_mem,
   out->branch_minsum = minsum;
   out->branch_patterns = npat;
   out->albe = npat ? 2.0 * (double)minsum / (double)npat : 0.0;
+  // Yokota branch (history) entropy (Table I; Yokota et al., cited in Sec. II),
+  // whose normalisation the paper does not print. Reading: the Shannon
+  // entropy of the h-outcome history given the site, over the predicted
+  // outcomes, divided by h so that it lies in [0, 1]:
+  //   H(history | site) = H(site, history) - H(site)
+  //                     = (1/N') [ sum_s N'_s log2 N'_s - sum_P n_P log2 n_P ],
+  // with N'_s the predicted outcomes of site s and n_P those of pattern P.
+  {
+    std::map<uint32_t, uint64_t> per_site_pred;
+    CompensatedSum pat_sum, site_sum;
+    for (auto& kv : patterns) {
+      const double n = (double)kv.second.second;
+      pat_sum.add(n * std::log2(n));
+      per_site_pred[kv.first.first] += kv.second.second;
+    }
+    for (auto& kv : per_site_pred) {
+      const double n = (double)kv.second;
+      site_sum.add(n * std::log2(n));
+    }
+    double y = npat ? (site_sum.value() - pat_sum.value()) / ((double)npat * (double)h) : 0.0;
+    out->yokota = y < 0.0 ? 0.0 : y;
+  }
 
   // ---------------- instructions (Table I compute/parallelism; Sec. III) ---
   // Runs arrive in push order; a work-item's runs continue one another. A

@@ -48,7 +48,7 @@ METRIC_FIELDS = [
     ("unique_reads", _U64), ("unique_writes", _U64),
     ("entropy", _F64 * (MAX_SKIP + 1)),
     ("branch_events", _U64), ("branch_sites", _U64), ("branch_cover", _U64), ("branch_patterns", _U64),
-    ("branch_minsum", _U64), ("albe", _F64),
+    ("branch_minsum", _U64), ("albe", _F64), ("yokota", _F64),
     ("unique_rw_ratio", _F64), ("reread_ratio", _F64), ("rewrite_ratio", _F64),
     ("simd_count", _U64), ("simd_max", _U64), ("simd_sum", _U64), ("simd_sumsq", _U64),
     ("simd_mean", _F64), ("simd_sd", _F64),

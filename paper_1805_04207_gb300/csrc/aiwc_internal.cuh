@@ -29,7 +29,9 @@ constexpr int kTagSites = 16;
 constexpr int kTagOpcodes = 17;
 constexpr int kTagItb = 18;
 constexpr int kTagIpt = 19;
-constexpr int kNumTags = 20;
+constexpr int kTagPat = 20;      // predicted outcomes per (site, history) pattern >= kValDense
+constexpr int kTagSitePat = 21;  // predicted outcomes per site >= kValDense
+constexpr int kNumTags = 22;
 constexpr u64 kValueMask = (1ull << 56) - 1;
 
 // Error flags raised on the device (DevState::err).
@@ -109,6 +111,8 @@ struct Arena {
   u64 opc_coc[kCocDense];
   alignas(16) u64 itb_dense[kValDense];
   alignas(16) u64 ipt_dense[kValDense];
+  u64 pat_coc[kValDense];            // m_c of the predicted-outcome counts of history patterns (c < kValDense)
+  u64 site_pat_coc[kValDense];       // m_c of the predicted-outcome counts of sites
   u64 tag_begin[kNumTags + 1];       // segment of each tag in the sorted overflow list
 };
 // the order statistics read the value bins 16 bytes at a time
@@ -265,6 +269,8 @@ struct PatternArgs {
   const u64* n{};      // valid pattern words (device)
   TileSum* tiles{};
   u32 ntiles{};
+  u64* over{};           // pattern counts >= kValDense
+  u64 over_cap{};
   Arena* arena{};
   int grid{};
 };
@@ -318,9 +324,10 @@ void launch_site_patterns(const SiteArgs& a, cudaStream_t s);
 void launch_branch_mask(Arena* arena, cudaStream_t s);
 
 // Cross-tile fix-up of run lengths. kind: 0 = memory levels, 1 = sites, 2 = patterns.
+// h: history length (kind 1, the site runs: each site predicts len - h outcomes).
 void launch_runs_fixup(int kind, const TileSum* tiles, u32 ntiles_max, const u64* n_dev, u64 n_host,
                        int levels, u64* over, u64 over_cap, Arena* arena, cudaStream_t s,
-                       const u32* gate = nullptr, u32 gate_want = 0);
+                       const u32* gate = nullptr, u32 gate_want = 0, u32 h = 0);
 // Set the attributes kernels with large dynamic shared memory need (current device).
 void init_branch_attributes();
 void init_instr_attributes();
@@ -375,6 +382,7 @@ struct FinalizeArgs {
   Result* result{};
   u32 cover_num{}, cover_den{};
   u32 precision{};
+  u32 history_len{};
 };
 void launch_finalize(const FinalizeArgs& a, cudaStream_t s);
 

@@ -281,8 +281,8 @@ aiwc_status check_usable(aiwc_handle* h) {
 }
 
 u64 over_bound(const aiwc_handle* h, u64 n_mem, u64 n_br, u64 n_runs) {
-  return (u64)kLevels * (n_mem / kCocDense + 2) + (n_br / kCocDense + 2) + (u64)h->cfg.n_opcodes +
-         2 * h->value_bound + 2 * (n_runs + 2) + 256;
+  return (u64)kLevels * (n_mem / kCocDense + 2) + (n_br / kCocDense + 2) + 2 * (n_br / kValDense + 2) +
+         (u64)h->cfg.n_opcodes + 2 * h->value_bound + 2 * (n_runs + 2) + 256;
 }
 
 aiwc_status runs_device(aiwc_handle* h, const u32* run_wi, const u64* run_off, const u64* run_len, size_t n_runs,
@@ -946,7 +946,8 @@ aiwc_status enqueue_part2(aiwc_handle* h, cudaStream_t st, const Plan& p) {
       {
         StageScope sc(h, kStWindows);
         launch_branch_windows(wa, st);
-        launch_runs_fixup(1, wa.tiles, wa.ntiles, nullptr, n_br, 1, over, over_cap, h->arena, st, gate, 0);
+        launch_runs_fixup(1, wa.tiles, wa.ntiles, nullptr, n_br, 1, over, over_cap, h->arena, st, gate, 0,
+                          h->cfg.history_len);
       }
       SortDesc ps = sort_desc(h, h->pat_a, h->pat_b, kSortPattern, &dst->n_patterns, &dst->pat_or, &dst->pat_and,
                               ~0ull, n_br);
@@ -966,6 +967,8 @@ aiwc_status enqueue_part2(aiwc_handle* h, cudaStream_t st, const Plan& p) {
       pa.n = &dst->n_patterns;
       pa.tiles = (TileSum*)h->tiles.p;
       pa.ntiles = (u32)ntiles_of(n_br);
+      pa.over = over;
+      pa.over_cap = over_cap;
       pa.arena = h->arena;
       pa.grid = grid;
       launch_pattern_runs(pa, st);
@@ -1008,6 +1011,7 @@ aiwc_status enqueue_part2(aiwc_handle* h, cudaStream_t st, const Plan& p) {
     fa.cover_num = h->cfg.cover_num;
     fa.cover_den = h->cfg.cover_den;
     fa.precision = h->cfg.precision;
+    fa.history_len = h->cfg.history_len;
     launch_finalize(fa, st);
   }
   CK(cudaGetLastError());
@@ -1192,6 +1196,7 @@ aiwc_status aiwc_aggregate(const aiwc_metrics* runs, size_t n, int mode, aiwc_me
       offsetof(aiwc_metrics, simd_sumsq)};
   std::vector<size_t> f64 = {
       offsetof(aiwc_metrics, itb_median), offsetof(aiwc_metrics, ipt_median), offsetof(aiwc_metrics, albe),
+      offsetof(aiwc_metrics, yokota),
       offsetof(aiwc_metrics, unique_rw_ratio), offsetof(aiwc_metrics, reread_ratio),
       offsetof(aiwc_metrics, rewrite_ratio), offsetof(aiwc_metrics, simd_mean), offsetof(aiwc_metrics, simd_sd),
       offsetof(aiwc_metrics, granularity), offsetof(aiwc_metrics, barriers_per_instruction),

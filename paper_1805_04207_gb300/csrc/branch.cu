@@ -21,6 +21,19 @@ namespace {
 constexpr int kBrThreads = 256;
 constexpr int kBrItems = 8;
 
+// Yokota entropy inputs: one pattern predicting n outcomes, one site
+// predicting n outcomes (exact count-of-counts, dense below kValDense).
+__device__ __forceinline__ void emit_pattern_count(u64 n, u64* over, u64 cap, Arena* ar) {
+  if (n == 0) return;
+  if (n < (u64)kValDense) atomicAdd(&ar->pat_coc[n], 1ull);
+  else overflow_append(over, cap, &ar->st, kTagPat, n);
+}
+__device__ __forceinline__ void emit_site_predicted(u64 m, u32 h, u64* over, u64 cap, Arena* ar) {
+  if (m <= h) return;
+  if (m - h < (u64)kValDense) atomicAdd(&ar->site_pat_coc[m - h], 1ull);
+  else overflow_append(over, cap, &ar->st, kTagSitePat, m - h);
+}
+
 __global__ void __launch_bounds__(kBrThreads) k_branch_ingest(BranchIngestArgs a) {
   __shared__ u64 red64[32];
   __shared__ u32 red32[32];
@@ -337,6 +350,7 @@ __global__ void __launch_bounds__(kCsThreads) k_cs_scatter(SiteSortArgs a) {
 }
 
 constexpr int kSpThreads = 512;
+constexpr int kPatSmem = 1024;  // pattern counts below this are counted in shared memory first
 constexpr int kSpBinsLog = 15;
 constexpr int kSpBitWords = (int)((kSiteMaxLen + 32) / 32) + 2;
 
@@ -356,8 +370,10 @@ __global__ void __launch_bounds__(kSpThreads) k_site_patterns(SiteArgs a) {
   uint16_t* used = reinterpret_cast<uint16_t*>(cnt + (1 << kSpBinsLog));
   __shared__ u32 n_used;
   __shared__ u64 red64[32];
+  __shared__ u32 pcoc[kPatSmem];  // pattern count-of-counts for small counts
   DevState* st = &a.arena->st;
   const u64* w = *a.cur ? a.b : a.a;
+  for (int i = threadIdx.x; i < kPatSmem; i += kSpThreads) pcoc[i] = 0u;
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = kSpThreads / 32;
   const u32 h = a.h;
   const int pbits = h > (u32)kSpBinsLog ? kSpBinsLog : (int)h;
@@ -375,6 +391,7 @@ __global__ void __launch_bounds__(kSpThreads) k_site_patterns(SiteArgs a) {
       ++nsite;
       if (m < (u64)kCocDense) atomicAdd(&a.arena->site_coc[m], 1ull);
       else overflow_append(a.over, a.over_cap, st, kTagSites, m);
+      emit_site_predicted(m, h, a.over, a.over_cap, a.arena);
     }
     const u32 nwords = (u32)((m + 31) / 32);
     // eight 32-event groups per warp in flight at a time
@@ -412,12 +429,17 @@ __global__ void __launch_bounds__(kSpThreads) k_site_patterns(SiteArgs a) {
         const u32 nn = v & 0xFFFFu, t = v >> 16;
         msum += t < nn - t ? t : nn - t;
         nsum += nn;
+        if (nn < (u32)kPatSmem) atomicAdd(&pcoc[nn], 1u);
+        else atomicAdd(&a.arena->pat_coc[nn], 1ull);  // nn <= kSiteMaxLen < kValDense
       }
       __syncthreads();
       if (threadIdx.x == 0) n_used = 0;
       __syncthreads();
     }
   }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kPatSmem; i += kSpThreads)
+    if (pcoc[i]) atomicAdd(&a.arena->pat_coc[i], (u64)pcoc[i]);
   msum = block_reduce(msum, OpAdd(), 0ull, red64);
   nsum = block_reduce(nsum, OpAdd(), 0ull, red64);
   nsite = block_reduce(nsite, OpAdd(), 0ull, red64);
@@ -524,6 +546,7 @@ __global__ void __launch_bounds__(kTileThreads) k_windows(WindowArgs a) {
         [&](u64 len, u64) {
           if (len < (u64)kCocDense) atomicAdd(&site_coc[len], 1u);
           else overflow_append(a.over, a.over_cap, st, kTagSites, len);
+          emit_site_predicted(len, h, a.over, a.over_cap, a.arena);
         },
         &a.tiles[tile], sh, pre_slot);
   }
@@ -548,7 +571,10 @@ __global__ void __launch_bounds__(kTileThreads) k_pattern_runs(PatternArgs a) {
   __shared__ Seg sh[33];
   __shared__ u64 pre_slot[2];
   __shared__ u64 red64[32];
+  __shared__ u32 pcoc[kPatSmem];
   DevState* st = &a.arena->st;
+  for (int i = threadIdx.x; i < kPatSmem; i += kTileThreads) pcoc[i] = 0u;
+  __syncthreads();
   const u64 n = *a.n;
   const u64* words = *a.cur ? a.b : a.a;
   const u32 ntiles = (u32)((n + kTile - 1) / kTile);
@@ -567,9 +593,14 @@ __global__ void __launch_bounds__(kTileThreads) k_pattern_runs(PatternArgs a) {
         [&](u64 len, u64 t) {
           msum += umin64(t, len - t);
           nsum += len;
+          if (len < (u64)kPatSmem) atomicAdd(&pcoc[len], 1u);
+          else emit_pattern_count(len, a.over, a.over_cap, a.arena);
         },
         &a.tiles[tile], sh, pre_slot);
   }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kPatSmem; i += kTileThreads)
+    if (pcoc[i]) atomicAdd(&a.arena->pat_coc[i], (u64)pcoc[i]);
   msum = block_reduce(msum, OpAdd(), 0ull, red64);
   nsum = block_reduce(nsum, OpAdd(), 0ull, red64);
   if (threadIdx.x == 0) {
@@ -583,7 +614,8 @@ __global__ void __launch_bounds__(kTileThreads) k_pattern_runs(PatternArgs a) {
 // boundary (and the final run), exactly once.
 template <int KIND>
 __global__ void __launch_bounds__(1024) k_fixup(const TileSum* tiles, u32 ntiles_max, const u64* n_dev, u64 n_host,
-                                                u64* over, u64 over_cap, Arena* arena, const u32* gate, u32 want) {
+                                                u64* over, u64 over_cap, Arena* arena, const u32* gate, u32 want,
+                                                u32 h) {
   if (!gate_open(gate, want)) return;
   __shared__ Seg sh[33];
   __shared__ u64 red64[32];
@@ -601,9 +633,11 @@ __global__ void __launch_bounds__(1024) k_fixup(const TileSum* tiles, u32 ntiles
     } else if (KIND == 1) {
       if (len < (u64)kCocDense) atomicAdd(&arena->site_coc[len], 1ull);
       else overflow_append(over, over_cap, st, kTagSites, len);
+      emit_site_predicted(len, h, over, over_cap, arena);
     } else {
       msum += umin64(wsum, len - wsum);
       nsum += len;
+      emit_pattern_count(len, over, over_cap, arena);
     }
   };
   for (u32 c0 = 0; c0 < ntiles; c0 += blockDim.x) {
@@ -704,14 +738,14 @@ void launch_pattern_runs(const PatternArgs& a, cudaStream_t s) {
 }
 
 void launch_runs_fixup(int kind, const TileSum* tiles, u32 ntiles_max, const u64* n_dev, u64 n_host, int levels,
-                       u64* over, u64 over_cap, Arena* arena, cudaStream_t s, const u32* gate, u32 gate_want) {
+                       u64* over, u64 over_cap, Arena* arena, cudaStream_t s, const u32* gate, u32 gate_want, u32 h) {
   if (ntiles_max == 0) return;
   if (kind == 0)
-    k_fixup<0><<<levels, 1024, 0, s>>>(tiles, ntiles_max, n_dev, n_host, over, over_cap, arena, gate, gate_want);
+    k_fixup<0><<<levels, 1024, 0, s>>>(tiles, ntiles_max, n_dev, n_host, over, over_cap, arena, gate, gate_want, h);
   else if (kind == 1)
-    k_fixup<1><<<levels, 1024, 0, s>>>(tiles, ntiles_max, n_dev, n_host, over, over_cap, arena, gate, gate_want);
+    k_fixup<1><<<levels, 1024, 0, s>>>(tiles, ntiles_max, n_dev, n_host, over, over_cap, arena, gate, gate_want, h);
   else
-    k_fixup<2><<<levels, 1024, 0, s>>>(tiles, ntiles_max, n_dev, n_host, over, over_cap, arena, gate, gate_want);
+    k_fixup<2><<<levels, 1024, 0, s>>>(tiles, ntiles_max, n_dev, n_host, over, over_cap, arena, gate, gate_want, h);
   count_launches(1);
 }
 

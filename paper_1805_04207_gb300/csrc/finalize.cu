@@ -248,12 +248,23 @@ __device__ __forceinline__ u64 run_end(const u64* over, u64 i, u64 oe, u64 v) {
 // c*e + c*log2(f); the first part is an exact integer, the second is
 // accumulated in float with Kahan compensation per thread; only the
 // cross-thread reduction is in double.
-__device__ double clog_sum(const u64* dense, const u64* over, u64 ob, u64 oe, u32 precision, Shared& s) {
+__device__ double clog_sum(const u64* dense, int dense_n, const u64* over, u64 ob, u64 oe, u32 precision,
+                           Shared& s) {
   if (precision == 0) {
     double acc = 0.0;
-    for (int c = threadIdx.x; c < kCocDense; c += blockDim.x) {
-      const u64 m = dense[c];
-      if (m && c > 1) acc += (double)m * ((double)c * log2((double)c));
+    // eight bins' loads in flight per thread
+    for (int c0 = threadIdx.x; c0 < dense_n; c0 += 8 * blockDim.x) {
+      u64 m[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int c = c0 + q * (int)blockDim.x;
+        m[q] = c < dense_n ? dense[c] : 0ull;
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int c = c0 + q * (int)blockDim.x;
+        if (m[q] && c > 1) acc += (double)m[q] * ((double)c * log2((double)c));
+      }
     }
     for (u64 i = ob + threadIdx.x; i < oe; i += blockDim.x) {
       const u64 v = over[i] & kValueMask;
@@ -276,7 +287,7 @@ __device__ double clog_sum(const u64* dense, const u64* over, u64 ob, u64 oe, u3
     comp = (t - sum) - y;
     sum = t;
   };
-  for (int c = threadIdx.x; c < kCocDense; c += blockDim.x) {
+  for (int c = threadIdx.x; c < dense_n; c += blockDim.x) {
     const u64 m = dense[c];
     if (m && c > 1) add((u64)c, m);
   }
@@ -292,8 +303,9 @@ __device__ double clog_sum(const u64* dense, const u64* over, u64 ob, u64 oe, u3
 
 // One block per independent task: blocks 0..10 the entropy of each skip
 // level, 11..13 the three coverage counts, 14..15 the ITB / IPT order
-// statistics, 16 the scalar fields. Each block writes disjoint fields.
-constexpr int kFinBlocks = 17;
+// statistics, 16 the scalar fields, 17 the Yokota branch entropy. Each block
+// writes disjoint fields.
+constexpr int kFinBlocks = 18;
 
 __global__ void __launch_bounds__(kFinThreads) k_finalize(FinalizeArgs a) {
   __shared__ Shared s;
@@ -317,7 +329,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(FinalizeArgs a) {
   const u64 N = st.total_reads + st.total_writes;
   if (task < kLevels) {
     const int l = task;
-    const double S = clog_sum(ar->mem_coc[l], over, s.tag_begin[l], s.tag_begin[l + 1], a.precision, s);
+    const double S = clog_sum(ar->mem_coc[l], kCocDense, over, s.tag_begin[l], s.tag_begin[l + 1], a.precision, s);
     if (threadIdx.x == 0) {
       double H = 0.0;
       if (N) {
@@ -363,6 +375,15 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(FinalizeArgs a) {
         m->load_imbalance = (double)(mx - mn);  // Sec. VI
         m->ipt_median = med;
       }
+    }
+  } else if (task == 17) {
+    // H(history | site) = (1/N') [sum_s N'_s log2 N'_s - sum_P n_P log2 n_P], in units of h bits
+    const double sp = clog_sum(ar->pat_coc, kValDense, over, s.tag_begin[kTagPat], s.tag_begin[kTagPat + 1], 0, s);
+    const double ss =
+        clog_sum(ar->site_pat_coc, kValDense, over, s.tag_begin[kTagSitePat], s.tag_begin[kTagSitePat + 1], 0, s);
+    if (threadIdx.x == 0) {
+      const double y = st.npat ? (ss - sp) / ((double)st.npat * (double)a.history_len) : 0.0;
+      m->yokota = y < 0.0 ? 0.0 : y;
     }
   } else if (threadIdx.x == 0) {
     m->total_instructions = st.total_instructions;

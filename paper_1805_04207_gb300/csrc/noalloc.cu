@@ -174,6 +174,7 @@ extern "C" aiwc_status aiwc_mem_metrics_noalloc(int device, void* cuda_stream, c
   fa.cover_num = 9;
   fa.cover_den = 10;
   fa.precision = 0;
+  fa.history_len = 16;  // no branch events: the Yokota entropy is 0
   launch_finalize(fa, s);
   Result r;
   u32 table_overflow = 0;

@@ -147,6 +147,15 @@ def metrics(trace, history_len=16, cover_num=9, cover_den=10, n_opcodes=None, sp
     out["branch_patterns"] = len(pats)
     out["branch_minsum"] = minsum
     out["albe"] = 2.0 * minsum / len(pats) if pats else 0.0
+    # Yokota (reading): sum over sites of the site's share of predicted outcomes
+    # times the entropy of its history distribution, in units of h bits
+    terms = []
+    for site in sorted({k[0] for k, _ in pats}):
+        hs = [k[1] for k, _ in pats if k[0] == site]
+        for hist in sorted(set(hs)):
+            q = hs.count(hist) / len(hs)
+            terms.append(len(hs) / len(pats) * -q * math.log2(q))
+    out["yokota"] = max(0.0, math.fsum(terms) / h) if pats else 0.0
 
     # instructions: concatenate each work-item's runs, split at barriers
     order = []

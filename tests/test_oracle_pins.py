@@ -39,6 +39,7 @@ def _compare(o, b):
     for n in range(11):
         assert abs(o["entropy"][n] - b["entropy"][n]) <= 1e-12, n
     assert abs(o["albe"] - b["albe"]) <= 1e-15
+    assert abs(o["yokota"] - b["yokota"]) <= 1e-12
 
 
 @pytest.mark.parametrize("seed", range(120))
@@ -285,3 +286,46 @@ def test_library_aggregate_matches_oracle_on_cpu():
                 assert g[k] == v, k
     with pytest.raises(P.AiwcError):
         P.aiwc_aggregate(runs, 7)
+
+
+# ---------------------------------------------------------------- Yokota branch entropy
+# Normalisation is a reading (the paper prints none): H(history | site) / h.
+
+def _de_bruijn(n):
+    """A binary de Bruijn sequence of order n (every n-bit window once, cyclically)."""
+    a, seq = [0] * (2 * n + 1), []
+
+    def db(t, p):
+        if t > n:
+            if n % p == 0:
+                seq.extend(a[1:p + 1])
+        else:
+            a[t] = a[t - p]
+            db(t + 1, p)
+            for j in range(a[t - p] + 1, 2):
+                a[t] = j
+                db(t + 1, t)
+    db(1, 1)
+    return seq
+
+
+@pytest.mark.parametrize("h", [1, 3, 4, 7])
+def test_yokota_closed_forms(h):
+    s = _de_bruijn(h)
+    s = s + s[:h]                      # every h-outcome window predicts exactly once
+    o = oracle.compute(branch_only([5] * len(s), [0] * len(s), s), history_len=h)
+    assert o["yokota"] == pytest.approx(1.0, abs=1e-12)
+    const = [1] * 200                  # one history only
+    assert oracle.compute(branch_only([2] * 200, [0] * 200, const), history_len=h)["yokota"] == 0.0
+    # a constant site and a de Bruijn site with equal predicted counts: 1/2
+    n = len(s) - h
+    c = [1] * (n + h)
+    tr = branch_only([1] * len(c) + [9] * len(s), [0] * (len(c) + len(s)), c + s)
+    assert oracle.compute(tr, history_len=h)["yokota"] == pytest.approx(0.5, abs=1e-12)
+
+
+def test_yokota_bounds_on_random_traces():
+    for seed in range(30):
+        tr = random_trace(seed, n_br=400, n_sites=4, n_wi=3)
+        y = oracle.compute(tr, history_len=3)["yokota"]
+        assert 0.0 <= y <= 1.0 + 1e-12

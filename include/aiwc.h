@@ -96,6 +96,14 @@ typedef struct aiwc_config {
   uint64_t table_slots;   /* hash plan: initial superblock-table slots (power of two, 0 = 2^20); an
                              invocation that overflows the table is finished by the sort plan and
                              the next one gets a 4x larger table */
+  uint32_t partitions;    /* invocations larger than device memory (Sec. VI names the trace size as the
+                             tool's limit): 0 or 1 = off; P > 1 (a power of two <= 256) routes pushes on
+                             the host into P partitions that keep every unit of the method whole --
+                             memory superblocks of 2^11 addresses, branch sites, work-items' runs --
+                             and aiwc_compute reduces one partition at a time on the device, adds their
+                             exact distributions and finalises once. Device memory then scales with the
+                             largest partition; host memory holds the pushed events until compute.
+                             Not for aiwc_compute_batch or server jobs. */
 } aiwc_config;
 
 /* Fills the paper's defaults: history 16, 90% coverage, all address spaces,

@@ -385,5 +385,8 @@ struct FinalizeArgs {
   u32 history_len{};
 };
 void launch_finalize(const FinalizeArgs& a, cudaStream_t s);
+// Partitioned invocations: adds one partition's arena (and overflow entries) to the total's.
+void launch_merge_partition(const Arena* part, const u64* part_over, u64 part_cap, Arena* total, u64* total_over,
+                            u64 total_cap, cudaStream_t s);
 
 }  // namespace aiwc

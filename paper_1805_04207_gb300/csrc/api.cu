@@ -107,6 +107,20 @@ struct aiwc_handle {
   std::vector<Interval> intervals;
   double stage_acc[kNumStages] = {0};
   double stage_last[kNumStages] = {0};
+  // partitioned invocations: pushed events held on the host per partition
+  struct PartBuf {
+    std::vector<uint8_t> mem;      // 16-byte memory events
+    std::vector<uint64_t> br;      // 8-byte branch events
+    std::vector<uint16_t> ops;
+    std::vector<uint32_t> run_wi;
+    std::vector<uint64_t> run_off, run_len;
+    std::vector<uint16_t> widths;
+  };
+  std::vector<PartBuf> parts;      // empty when not partitioned
+  bool replaying = false;          // compute is pushing one partition to the device
+  u32 part_err = 0;                // routing found an invalid run (reported by compute)
+  Arena* total = nullptr;          // the partitions' merged distributions
+  DevBuf over_total;
 };
 
 namespace {
@@ -280,9 +294,15 @@ aiwc_status check_usable(aiwc_handle* h) {
   return AIWC_OK;
 }
 
-u64 over_bound(const aiwc_handle* h, u64 n_mem, u64 n_br, u64 n_runs) {
+// Overflow entries an invocation can append: group sizes >= kCocDense per
+// level, large site and pattern counts, opcode counts, large ITB / IPT values.
+u64 over_bound_sizes(u32 n_opcodes, u64 n_mem, u64 n_br, u64 n_runs, u64 value_bound) {
   return (u64)kLevels * (n_mem / kCocDense + 2) + (n_br / kCocDense + 2) + 2 * (n_br / kValDense + 2) +
-         (u64)h->cfg.n_opcodes + 2 * h->value_bound + 2 * (n_runs + 2) + 256;
+         (u64)n_opcodes + 2 * value_bound + 2 * (n_runs + 2) + 256;
+}
+
+u64 over_bound(const aiwc_handle* h, u64 n_mem, u64 n_br, u64 n_runs) {
+  return over_bound_sizes(h->cfg.n_opcodes, n_mem, n_br, n_runs, h->value_bound);
 }
 
 aiwc_status runs_device(aiwc_handle* h, const u32* run_wi, const u64* run_off, const u64* run_len, size_t n_runs,
@@ -423,6 +443,107 @@ aiwc_status reset_device_state(aiwc_handle* h, cudaStream_t st) {
   return AIWC_OK;
 }
 
+// ---------------------------------------------------------------- partitioned invocations
+
+// Partition of a routing key (SplitMix64's output function, Steele, Lea &
+// Flood 2014, as a hash).
+inline u32 part_of(uint64_t key, u32 n_parts) {
+  uint64_t z = key + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return (u32)((z ^ (z >> 31)) & (uint64_t)(n_parts - 1));
+}
+
+bool routing(const aiwc_handle* h) { return !h->parts.empty() && !h->replaying; }
+
+// Host copy of caller data (device pointers are read back first).
+template <typename T>
+aiwc_status host_view(aiwc_handle* h, const T* p, size_t n, int on_device, std::vector<T>* tmp, const T** out) {
+  if (!on_device) {
+    *out = p;
+    return AIWC_OK;
+  }
+  tmp->resize(n);
+  CK(cudaMemcpy(tmp->data(), p, n * sizeof(T), cudaMemcpyDeviceToHost));
+  *out = tmp->data();
+  return AIWC_OK;
+}
+
+// Memory events go with their superblock (space, address >> 11): every
+// skip-level group lies inside one superblock, so a partition's groups are
+// whole.
+aiwc_status route_mem(aiwc_handle* h, const aiwc_mem_event* ev, size_t n, int on_device) {
+  std::vector<aiwc_mem_event> tmp;
+  const aiwc_mem_event* e = nullptr;
+  aiwc_status s = host_view(h, ev, n, on_device, &tmp, &e);
+  if (s != AIWC_OK) return s;
+  const u32 P = (u32)h->parts.size();
+  for (size_t i = 0; i < n; ++i) {
+    const uint64_t key = ((uint64_t)((e[i].flags >> 1) & 3u) << 56) | ((e[i].addr & (AIWC_ADDR_LIMIT - 1)) >> 11);
+    auto& m = h->parts[part_of(key, P)].mem;
+    const uint8_t* b = reinterpret_cast<const uint8_t*>(e + i);
+    m.insert(m.end(), b, b + 16);
+  }
+  return AIWC_OK;
+}
+
+// Branch events go with their site (histories are per site).
+aiwc_status route_branch(aiwc_handle* h, const aiwc_branch_event* ev, size_t n, int on_device) {
+  std::vector<aiwc_branch_event> tmp;
+  const aiwc_branch_event* e = nullptr;
+  aiwc_status s = host_view(h, ev, n, on_device, &tmp, &e);
+  if (s != AIWC_OK) return s;
+  const u32 P = (u32)h->parts.size();
+  for (size_t i = 0; i < n; ++i) {
+    uint64_t w;
+    memcpy(&w, e + i, 8);
+    h->parts[part_of(e[i].site, P)].br.push_back(w);
+  }
+  return AIWC_OK;
+}
+
+// Instruction runs go with their work-item (ITB chains per work-item).
+aiwc_status route_runs(aiwc_handle* h, const uint32_t* run_wi, const uint64_t* run_off, const uint64_t* run_len,
+                       size_t n_runs, const uint16_t* ops, size_t n_ops, int on_device) {
+  std::vector<uint32_t> twi;
+  std::vector<uint64_t> toff, tlen;
+  std::vector<uint16_t> tops;
+  const uint32_t* wi = nullptr;
+  const uint64_t *off = nullptr, *len = nullptr;
+  const uint16_t* op = nullptr;
+  aiwc_status s;
+  if ((s = host_view(h, run_wi, n_runs, on_device, &twi, &wi)) != AIWC_OK ||
+      (s = host_view(h, run_off, n_runs, on_device, &toff, &off)) != AIWC_OK ||
+      (s = host_view(h, run_len, n_runs, on_device, &tlen, &len)) != AIWC_OK ||
+      (s = host_view(h, ops, n_ops, on_device, &tops, &op)) != AIWC_OK)
+    return s;
+  const u32 P = (u32)h->parts.size();
+  for (size_t r = 0; r < n_runs; ++r) {
+    if (off[r] > n_ops || len[r] > n_ops - off[r]) {
+      h->part_err |= kErrRun;
+      continue;
+    }
+    auto& pb = h->parts[part_of(wi[r], P)];
+    pb.run_wi.push_back(wi[r]);
+    pb.run_off.push_back(pb.ops.size());
+    pb.run_len.push_back(len[r]);
+    pb.ops.insert(pb.ops.end(), op + off[r], op + off[r] + len[r]);
+  }
+  return AIWC_OK;
+}
+
+aiwc_status route_widths(aiwc_handle* h, const uint16_t* w, size_t n, int on_device) {
+  std::vector<uint16_t> tmp;
+  const uint16_t* p = nullptr;
+  aiwc_status s = host_view(h, w, n, on_device, &tmp, &p);
+  if (s != AIWC_OK) return s;
+  auto& v = h->parts[0].widths;  // the SIMD statistics add over any split
+  v.insert(v.end(), p, p + n);
+  return AIWC_OK;
+}
+
+aiwc_status compute_partitioned(aiwc_handle* h, aiwc_metrics* out);
+
 }  // namespace
 
 extern "C" {
@@ -456,6 +577,8 @@ aiwc_status aiwc_create(const aiwc_config* cfg, aiwc_handle** out) {
   if (cfg->table_slots && ((cfg->table_slots & (cfg->table_slots - 1)) || cfg->table_slots < 64 ||
                            cfg->table_slots > (1ull << 30)))
     return fail(nullptr, AIWC_EINVAL, "table_slots must be a power of two in [64, 2^30]");
+  if (cfg->partitions > 256 || (cfg->partitions & (cfg->partitions - 1)))
+    return fail(nullptr, AIWC_EINVAL, "partitions must be 0 or a power of two <= 256");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
     cudaGetLastError();
@@ -468,6 +591,7 @@ aiwc_status aiwc_create(const aiwc_config* cfg, aiwc_handle** out) {
   h->stream = (cudaStream_t)cfg->cuda_stream;
   h->max_wi = cfg->max_work_items ? cfg->max_work_items : (1ull << 32);
   h->sbt_want = cfg->table_slots ? cfg->table_slots : (1ull << 20);
+  if (cfg->partitions > 1) h->parts.resize(cfg->partitions);
   auto bail = [&](aiwc_status s) {
     aiwc_destroy(h);
     return s;
@@ -506,6 +630,7 @@ aiwc_status aiwc_push_mem(aiwc_handle* h, const aiwc_mem_event* ev, size_t n, in
   DeviceGuard g(h->cfg.device);
   if (on_device && ((uintptr_t)ev & 15u))
     return fail(h, AIWC_EINVAL, "device memory events must be 16-byte aligned", false);
+  if (routing(h)) return route_mem(h, ev, n, on_device);
   ENSURE(h->mem_a, (h->n_mem + n) * 8, true);
   if ((s = ensure_bitmap(h)) != AIWC_OK) return s;
   if (use_hash(h) && (s = ensure_table(h)) != AIWC_OK) return s;
@@ -552,6 +677,7 @@ aiwc_status aiwc_push_branch(aiwc_handle* h, const aiwc_branch_event* ev, size_t
   DeviceGuard g(h->cfg.device);
   if (on_device && ((uintptr_t)ev & 7u))
     return fail(h, AIWC_EINVAL, "device branch events must be 8-byte aligned", false);
+  if (routing(h)) return route_branch(h, ev, n, on_device);
   ENSURE(h->br_a, (h->n_br + n) * 8, true);
   if ((s = ensure_bitmap(h)) != AIWC_OK) return s;
   BranchIngestArgs a;
@@ -590,6 +716,7 @@ aiwc_status aiwc_push_widths(aiwc_handle* h, const uint16_t* widths, size_t n, i
   if (n == 0) return AIWC_OK;
   if (!widths) return fail(h, AIWC_EINVAL, "null width pointer", false);
   DeviceGuard g(h->cfg.device);
+  if (routing(h)) return route_widths(h, widths, n, on_device);
   StageScope scope(h, kStInstrRuns);
   if (on_device) {
     launch_simd_widths(widths, n, h->arena, h->stream);
@@ -608,6 +735,13 @@ aiwc_status aiwc_push_instr(aiwc_handle* h, uint32_t work_item, const uint16_t* 
   DeviceGuard g(h->cfg.device);
   const bool dev = on_device != 0;
   if (dev && ((uintptr_t)ops & 1u)) return fail(h, AIWC_EINVAL, "device opcodes must be 2-byte aligned", false);
+  if (routing(h)) {
+    const uint64_t off = 0, len = n;
+    std::vector<uint16_t> one;
+    const uint16_t* p = ops;
+    if ((s = host_view(h, ops, n, on_device, &one, &p)) != AIWC_OK) return s;
+    return route_runs(h, &work_item, &off, &len, 1, p, n, 0);
+  }
   if (!h->pend_wi.empty() && h->pend_device != dev) {
     if ((s = flush_pending(h)) != AIWC_OK) return s;
   }
@@ -636,6 +770,7 @@ aiwc_status aiwc_push_instr_runs(aiwc_handle* h, const uint32_t* run_wi, const u
   if (on_device && (((uintptr_t)ops & 1u) || ((uintptr_t)run_wi & 3u) || ((uintptr_t)run_off & 7u) ||
                     ((uintptr_t)run_len & 7u)))
     return fail(h, AIWC_EINVAL, "device run tables / opcodes are misaligned", false);
+  if (routing(h)) return route_runs(h, run_wi, run_off, run_len, n_runs, ops, n_ops, on_device);
   if (on_device)
     return runs_device(h, run_wi, (const u64*)run_off, (const u64*)run_len, n_runs, ops, n_ops, n_ops);
   return runs_host(h, run_wi, run_off, run_len, n_runs, ops, n_ops);
@@ -744,6 +879,7 @@ struct Plan {
   u32 br_passes = 0xFFu, run_passes = 0xFFu;
   int seg_shift = 0;      // memory, hash plan: low address bits that are zero in every kept event (0..3)
   bool site_sort = false; // branch: stable counting sort by site (in order work-item ids, site ids < kCsSites)
+  bool defer_finalize = false;  // partitioned invocation: reduce only, the partitions are merged first
 };
 
 u32 active_passes(u64 kor, u64 kand, u64 mask) {
@@ -856,6 +992,8 @@ void enqueue_part1(aiwc_handle* h, cudaStream_t st, const Plan& p) {
   launch_site_heads(site_args(h, bsort), st);
   if (p.gated) launch_persite_decide(h->arena, h->cfg.history_len, h->c_sites_cap, h->cfg.plan != 1, st);
 }
+
+aiwc_status enqueue_finalize(aiwc_handle* h, cudaStream_t st);
 
 // Everything after the branch-path choice, the result copies and the reset.
 aiwc_status enqueue_part2(aiwc_handle* h, cudaStream_t st, const Plan& p) {
@@ -994,6 +1132,16 @@ aiwc_status enqueue_part2(aiwc_handle* h, cudaStream_t st, const Plan& p) {
     ca.arena = h->arena;
     launch_instr_combine(ca, st);
   }
+  if (p.defer_finalize) return AIWC_OK;
+  return enqueue_finalize(h, st);
+}
+
+// The end of an invocation: opcode distribution, work-item count, overflow
+// sort, the finalize kernel, the result copies and the reset.
+aiwc_status enqueue_finalize(aiwc_handle* h, cudaStream_t st) {
+  DevState* dst = &h->arena->st;
+  u64* over = (u64*)h->over_a.p;
+  const u64 over_cap = h->c_over_cap;
   {
     StageScope fin_scope(h, kStFinalize);
     launch_opcode_dist((const u64*)h->d_hist, h->cfg.n_opcodes, over, over_cap, h->arena, st);
@@ -1049,6 +1197,9 @@ aiwc_status finish(aiwc_handle* h, aiwc_metrics* out, uint64_t* user_hist) {
 // Recovers a broken handle: drops the invocation.
 aiwc_status recover(aiwc_handle* h) {
   reset_host(h);
+  h->replaying = false;
+  h->part_err = 0;
+  for (auto& pb : h->parts) pb = aiwc_handle::PartBuf();
   cudaGetLastError();
   if (reset_device_state(h, h->stream) == AIWC_OK && cudaStreamSynchronize(h->stream) == cudaSuccess) h->broken = false;
   return AIWC_ESTATE;
@@ -1071,16 +1222,10 @@ void plan_from_ingest(aiwc_handle* h, Plan* p) {
                  (hs.br_or >> 32) < kCsSites && h->cfg.plan != 1;
 }
 
-}  // namespace
-
-extern "C" {
-
-aiwc_status aiwc_compute(aiwc_handle* h, aiwc_metrics* out) {
-  if (!h || !out) return fail(h, AIWC_EINVAL, "null handle or output pointer", false);
-  DeviceGuard g(h->cfg.device);
-  uint64_t* user_hist = out->opcode_hist;
+// Everything a compute enqueues for what is pushed now: the plan from the
+// ingest-time counters, the stages, and (unless deferred) the finalisation.
+aiwc_status reduce_current(aiwc_handle* h, bool defer_finalize) {
   cudaStream_t st = h->stream;
-  if (h->broken) return recover(h);
   aiwc_status s = prepare(h);
   if (s != AIWC_OK) return s;
   // read the ingest-time counters: memory plan, active sort passes
@@ -1088,6 +1233,7 @@ aiwc_status aiwc_compute(aiwc_handle* h, aiwc_metrics* out) {
   CK(cudaStreamSynchronize(st));
   Plan p;
   plan_from_ingest(h, &p);
+  p.defer_finalize = defer_finalize;
   enqueue_part1(h, st, p);
   if (h->n_br) {
     // the branch path depends on the longest site
@@ -1097,8 +1243,86 @@ aiwc_status aiwc_compute(aiwc_handle* h, aiwc_metrics* out) {
     p.per_site = h->cfg.history_len <= kSiteMaxHist && hs.br_site_max <= kSiteMaxLen &&
                  hs.n_sites <= h->c_sites_cap && h->cfg.plan != 1;
   }
-  if ((s = enqueue_part2(h, st, p)) != AIWC_OK) return s;
+  return enqueue_part2(h, st, p);
+}
+
+// Partitioned invocation: each partition is pushed to the device and reduced
+// with the finalisation deferred, its distributions are added to the total,
+// and the total is finalised once.
+aiwc_status compute_partitioned(aiwc_handle* h, aiwc_metrics* out) {
+  uint64_t* user_hist = out->opcode_hist;
+  cudaStream_t st = h->stream;
+  std::vector<aiwc_handle::PartBuf> parts(h->parts.size());
+  parts.swap(h->parts);  // the handle keeps empty buffers for the next invocation
+  const u32 perr = h->part_err;
+  h->part_err = 0;
+  if (perr & kErrRun) return fail(h, AIWC_EINVAL, "instruction run reaches past its opcode array", false);
+  u64 total_cap = 0;  // the merged entries fit the sum of the partitions' bounds
+  for (auto& pb : parts)
+    total_cap += over_bound_sizes(h->cfg.n_opcodes, pb.mem.size() / 16, pb.br.size(), pb.run_wi.size(),
+                                  pb.ops.size() / kValDense + 2);
+  if (!h->total) {
+    CK(cudaMalloc(&h->total, sizeof(Arena)));
+    h->bytes += sizeof(Arena);
+  }
+  ENSURE(h->over_total, total_cap * 8, false);
+  CK(cudaMemsetAsync(h->total, 0, sizeof(Arena), st));
+  launch_reset_identities(h->total, st);
+  h->replaying = true;
+  aiwc_status s = AIWC_OK;
+  for (auto& pb : parts) {
+    if (pb.mem.empty() && pb.br.empty() && pb.run_wi.empty() && pb.widths.empty()) continue;
+    if (!pb.mem.empty())
+      s = aiwc_push_mem(h, reinterpret_cast<const aiwc_mem_event*>(pb.mem.data()), pb.mem.size() / 16, 0);
+    if (s == AIWC_OK && !pb.br.empty())
+      s = aiwc_push_branch(h, reinterpret_cast<const aiwc_branch_event*>(pb.br.data()), pb.br.size(), 0);
+    if (s == AIWC_OK && !pb.run_wi.empty())
+      s = aiwc_push_instr_runs(h, pb.run_wi.data(), pb.run_off.data(), pb.run_len.data(), pb.run_wi.size(),
+                               pb.ops.data(), pb.ops.size(), 0);
+    if (s == AIWC_OK && !pb.widths.empty()) s = aiwc_push_widths(h, pb.widths.data(), pb.widths.size(), 0);
+    if (s == AIWC_OK) s = reduce_current(h, true);
+    if (s != AIWC_OK) {
+      h->replaying = false;
+      return s;
+    }
+    launch_merge_partition(h->arena, (const u64*)h->over_a.p, h->c_over_cap, h->total, (u64*)h->over_total.p,
+                           total_cap, st);
+    // the partition's state goes; the opcode histogram and the work-item bitmap keep adding up
+    CK(cudaMemsetAsync(h->arena, 0, sizeof(Arena), st));
+    if (h->sbt.p) CK(cudaMemsetAsync(h->sbt.p, 0, 12 * h->sbt_cap, st));
+    launch_reset_identities(h->arena, st);
+    reset_host(h);
+  }
+  h->replaying = false;
+  // finalise the merged distributions in the handle's own arena and overflow list
+  const u64 cap = std::max<u64>(total_cap, 1);
+  ENSURE(h->over_a, cap * 8, false);
+  ENSURE(h->over_b, cap * 8, false);
+  ENSURE(h->counts, sort_counts_words(cap) * 4, false);
+  ENSURE(h->bsums, sort_block_sums_words(cap) * 4, false);
+  h->c_over_cap = total_cap;
+  CK(cudaMemcpyAsync(h->arena, h->total, sizeof(Arena), cudaMemcpyDeviceToDevice, st));
+  if (total_cap) CK(cudaMemcpyAsync(h->over_a.p, h->over_total.p, total_cap * 8, cudaMemcpyDeviceToDevice, st));
+  if ((s = enqueue_finalize(h, st)) != AIWC_OK) return s;
   CK(cudaStreamSynchronize(st));
+  collect_stage_times(h);
+  return finish(h, out, user_hist);
+}
+
+
+}  // namespace
+
+extern "C" {
+
+aiwc_status aiwc_compute(aiwc_handle* h, aiwc_metrics* out) {
+  if (!h || !out) return fail(h, AIWC_EINVAL, "null handle or output pointer", false);
+  DeviceGuard g(h->cfg.device);
+  uint64_t* user_hist = out->opcode_hist;
+  if (h->broken) return recover(h);
+  if (!h->parts.empty()) return compute_partitioned(h, out);
+  aiwc_status s = reduce_current(h, false);
+  if (s != AIWC_OK) return s;
+  CK(cudaStreamSynchronize(h->stream));
   collect_stage_times(h);
   return finish(h, out, user_hist);
 }
@@ -1110,6 +1334,7 @@ aiwc_status aiwc_compute_batch(aiwc_handle* const* hs, size_t n, aiwc_metrics* o
     if (!hs[i]) return fail(nullptr, AIWC_EINVAL, "null handle in batch");
     if (hs[i]->cfg.device != hs[0]->cfg.device || hs[i]->stream != hs[0]->stream)
       return fail(nullptr, AIWC_EINVAL, "batched handles must share one device and one stream");
+    if (!hs[i]->parts.empty()) return fail(nullptr, AIWC_EINVAL, "partitioned handles cannot be batched");
     for (size_t j = 0; j < i; ++j)
       if (hs[j] == hs[i]) return fail(nullptr, AIWC_EINVAL, "a handle appears twice in the batch");
   }
@@ -1250,8 +1475,9 @@ aiwc_status aiwc_destroy(aiwc_handle* h) {
   if (h->stream || h->copy_stream) cudaStreamSynchronize(h->stream);
   DevBuf* bufs[] = {&h->mem_a, &h->mem_b, &h->br_a, &h->br_b, &h->pat_a, &h->pat_b, &h->rk_a, &h->rk_b,
                     &h->run_sum, &h->over_a, &h->over_b, &h->counts, &h->bsums, &h->tiles, &h->stage[0],
-                    &h->stage[1], &h->desc, &h->sbt, &h->sbt_scan, &h->sites};
+                    &h->stage[1], &h->desc, &h->sbt, &h->sbt_scan, &h->sites, &h->over_total};
   for (DevBuf* b : bufs) release(h, *b);
+  if (h->total) cudaFree(h->total);
   if (h->wi_bitmap) cudaFree(h->wi_bitmap);
   if (h->arena) cudaFree(h->arena);
   if (h->d_result) cudaFree(h->d_result);

@@ -429,7 +429,70 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(FinalizeArgs a) {
   }
 }
 
+// ---------------------------------------------------------------- partitioned invocations
+// Every distribution a partition reduces to is exact and additive: dense
+// count-of-counts and value bins add, overflow entries concatenate, counters
+// add (maxima and minima combine). The total arena is touched only by these
+// kernels, in stream order, so plain read-modify-writes suffice.
+
+// Appends the partition's overflow entries behind the total's.
+__global__ void k_merge_over(const Arena* part, const u64* part_over, u64 part_cap, Arena* total, u64* total_over,
+                             u64 total_cap) {
+  const u64 n = umin64(part->st.n_over, part_cap);
+  const u64 base = total->st.n_over;
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x)
+    if (base + i < total_cap) total_over[base + i] = part_over[i];
+}
+
+__global__ void k_merge_arena(const Arena* part, Arena* total, u64 part_cap, u64 total_cap) {
+  const u64 stride = (u64)gridDim.x * blockDim.x;
+  const u64 i0 = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+  auto add = [&](u64* dst, const u64* src, u64 n) {
+    for (u64 i = i0; i < n; i += stride)
+      if (src[i]) dst[i] += src[i];
+  };
+  add(&total->mem_coc[0][0], &part->mem_coc[0][0], (u64)kLevels * kCocDense);
+  add(total->site_coc, part->site_coc, kCocDense);
+  add(total->itb_dense, part->itb_dense, kValDense);
+  add(total->ipt_dense, part->ipt_dense, kValDense);
+  add(total->pat_coc, part->pat_coc, kValDense);
+  add(total->site_pat_coc, part->site_pat_coc, kValDense);
+  if (i0 == 0) {
+    const DevState& p = part->st;
+    DevState& t = total->st;
+    t.total_reads += p.total_reads;
+    t.total_writes += p.total_writes;
+    t.footprint += p.footprint;
+    t.unique_reads += p.unique_reads;
+    t.unique_writes += p.unique_writes;
+    t.n_branch += p.n_branch;
+    t.branch_sites += p.branch_sites;
+    t.npat += p.npat;
+    t.minsum += p.minsum;
+    t.barriers += p.barriers;
+    t.simd_count += p.simd_count;
+    t.simd_sum += p.simd_sum;
+    t.simd_sumsq += p.simd_sumsq;
+    t.simd_max = p.simd_max > t.simd_max ? p.simd_max : t.simd_max;
+    t.err |= p.err;
+    if (p.wi_min < t.wi_min) t.wi_min = p.wi_min;
+    if (p.wi_max > t.wi_max) t.wi_max = p.wi_max;
+    const u64 n = umin64(p.n_over, part_cap);
+    if (p.n_over > part_cap || t.n_over + n > total_cap) t.err |= kErrOverflow;
+    t.n_over += n;
+    t.over_or |= p.over_or;
+    t.over_and &= p.over_and;
+  }
+}
+
 }  // namespace
+
+void launch_merge_partition(const Arena* part, const u64* part_over, u64 part_cap, Arena* total, u64* total_over,
+                            u64 total_cap, cudaStream_t s) {
+  k_merge_over<<<152 * 2, 256, 0, s>>>(part, part_over, part_cap, total, total_over, total_cap);
+  k_merge_arena<<<152 * 2, 256, 0, s>>>(part, total, part_cap, total_cap);
+  count_launches(2);
+}
 
 void launch_opcode_dist(const u64* hist, u32 n_opcodes, u64* over, u64 over_cap, Arena* arena, cudaStream_t s) {
   if (n_opcodes == 0) return;

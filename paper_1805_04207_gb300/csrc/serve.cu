@@ -131,6 +131,7 @@ aiwc_status aiwc_job_open(aiwc_server* s, const aiwc_config* job_cfg, uint64_t r
   if (!s || !job_cfg || !out) return srv_fail(AIWC_EINVAL, "null server, config or output");
   *out = nullptr;
   std::lock_guard<std::mutex> lk(s->mu);
+  if (job_cfg->partitions > 1) return srv_fail(AIWC_EINVAL, "server jobs are not partitioned");
   if (reserve_bytes > s->cfg.hbm_budget) {
     ++s->rejected;
     return srv_fail(AIWC_ENOMEM, "job reservation exceeds the server's HBM budget");

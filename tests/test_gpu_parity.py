@@ -383,3 +383,69 @@ def test_precision_fp32_compensated_within_bound(P, n_mem):
     assert_parity(g64, o)
     assert_parity(g32, o, entropy_tol=2.0 ** -22)
     assert abs(g32["albe"] - o["albe"]) <= 1e-6
+
+
+# ---------------------------------------------------------------- partitioned invocations
+
+def _run_partitioned(P, trace, partitions, on_device=True, **cfg):
+    cfg.setdefault("n_opcodes", trace.n_opcodes)
+    tr = trace.to("cuda") if on_device else trace
+    with P.Characterizer(partitions=partitions, **cfg) as c:
+        n = tr.n_mem
+        for k in range(3):  # three pushes per stream: routing keeps push order inside each partition
+            if n:
+                c.push_mem(tr.mem[k * n // 3:(k + 1) * n // 3].contiguous())
+            nb = tr.n_br
+            if nb:
+                c.push_branch(tr.br[k * nb // 3:(k + 1) * nb // 3].contiguous())
+        if tr.run_wi is not None and tr.run_wi.shape[0]:
+            c.push_instr_runs(tr.run_wi.to(torch.int32), tr.run_off, tr.run_len, tr.ops)
+        if tr.widths is not None and tr.widths.shape[0]:
+            c.push_widths(tr.widths)
+        return c.compute()
+
+
+@pytest.mark.parametrize("partitions", [2, 8, 64])
+@pytest.mark.parametrize("on_device", [True, False])
+def test_partitioned_invocation_matches_single(P, partitions, on_device):
+    """Routing by superblock, site and work-item keeps every unit whole: the
+    merged distributions give exactly the single invocation's metrics."""
+    traces = [synth.tiny(),
+              synth.large(seed=4, n_mem=300_001, n_br=120_000, n_wi=64, per_wi=300, zipf_distinct=1 << 16),
+              random_trace(77, n_mem=5000, n_br=3000, n_wi=40, n_runs=200, n_ops=4000, addr_pool=900,
+                           n_sites=30, addr_span_bits=24)]
+    for tr in traces:
+        g = _run_partitioned(P, tr, partitions, on_device)
+        assert_parity(g, run_gpu(P, tr))
+        assert_parity(g, oracle.compute(tr))
+
+
+@pytest.mark.parametrize("plan", [1, 2])
+def test_partitioned_plans_and_reuse(P, plan):
+    """Both memory plans, and a handle reused for a second partitioned invocation."""
+    from paper_1805_04207_gb300.api import push_trace
+    tr = synth.pattern_trace("stencil", 200_000, 50_000, seed=8)
+    with P.Characterizer(partitions=4, n_opcodes=tr.n_opcodes, plan=plan, table_slots=1 << 12) as c:
+        for _ in range(2):
+            push_trace(c, tr.to("cuda"))
+            assert_parity(c.compute(want_hist=True), oracle.compute(tr))
+
+
+def test_partitioned_errors(P):
+    with pytest.raises(P.AiwcError):
+        P.Characterizer(partitions=3)
+    tr = instr_only([(0, [1, 2])], n_opcodes=8)
+    with P.Characterizer(partitions=4, n_opcodes=8) as c:
+        c.push_instr_runs(torch.tensor([0], dtype=torch.int32), torch.tensor([5], dtype=torch.int64),
+                          torch.tensor([3], dtype=torch.int64), tr.ops)  # run past the opcode array
+        with pytest.raises(P.AiwcError) as e:
+            c.compute()
+        assert e.value.status == P.AIWC_EINVAL
+        c.push_instr_runs(tr.run_wi.to(torch.int32), tr.run_off, tr.run_len, tr.ops)  # the handle still works
+        assert_parity(c.compute(want_hist=True), oracle.compute(tr))
+    a = P.Characterizer(partitions=2, n_opcodes=8)
+    b = P.Characterizer(n_opcodes=8)
+    with pytest.raises(P.AiwcError):
+        P.compute_batch([a, b])
+    a.close()
+    b.close()

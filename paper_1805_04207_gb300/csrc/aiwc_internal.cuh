@@ -17,7 +17,8 @@ typedef unsigned int u32;
 
 // ------------------------------------------------------------------ sizes
 constexpr int kLevels = AIWC_MAX_SKIP + 1;  // skip 0 (global) .. 10 (local)
-constexpr int kCocDense = 1024;             // group sizes below this are binned densely
+constexpr int kCocDense = 4096;             // group sizes below this are binned densely
+constexpr int kCocShared = 1024;            // ... and below this first in a block's shared bins
 constexpr int kValDense = 65536;            // ITB / IPT values below this are binned densely
 constexpr int kValSmem = 2048;              // ... of which the smallest are privatised in shared memory
 constexpr int kTile = 4096;                 // elements per tile in the sort and run kernels

@@ -458,14 +458,14 @@ constexpr int kHalo = 32;  // history lengths are at most 31
 __global__ void __launch_bounds__(kTileThreads) k_windows(WindowArgs a) {
   if (!gate_open(a.gate, a.gate_want)) return;
   __shared__ u64 tw[kHalo + kTile];
-  __shared__ u32 site_coc[kCocDense];
+  __shared__ u32 site_coc[kCocShared];
   __shared__ Seg sh[33];
   __shared__ u64 pre_slot[2];
   __shared__ u64 red64[32];
   __shared__ u32 scan_tot[33];
   __shared__ u64 s_base;
   DevState* st = &a.arena->st;
-  for (int i = threadIdx.x; i < kCocDense; i += kTileThreads) site_coc[i] = 0u;
+  for (int i = threadIdx.x; i < kCocShared; i += kTileThreads) site_coc[i] = 0u;
   const u64 n = a.n;
   const u64* words = *a.cur ? a.b : a.a;
   const u32 ntiles = (u32)((n + kTile - 1) / kTile);
@@ -544,14 +544,15 @@ __global__ void __launch_bounds__(kTileThreads) k_windows(WindowArgs a) {
     tile_runs<kTileItems>(
         key, nvalid, pos0, prev, tile_n, [](u64 x) { return x >> 32; }, [](u64) { return 0ull; },
         [&](u64 len, u64) {
-          if (len < (u64)kCocDense) atomicAdd(&site_coc[len], 1u);
+          if (len < (u64)kCocShared) atomicAdd(&site_coc[len], 1u);
+          else if (len < (u64)kCocDense) atomicAdd(&a.arena->site_coc[len], 1ull);
           else overflow_append(a.over, a.over_cap, st, kTagSites, len);
           emit_site_predicted(len, h, a.over, a.over_cap, a.arena);
         },
         &a.tiles[tile], sh, pre_slot);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < kCocDense; i += kTileThreads)
+  for (int i = threadIdx.x; i < kCocShared; i += kTileThreads)
     if (site_coc[i]) atomicAdd(&a.arena->site_coc[i], (u64)site_coc[i]);
   heads = block_reduce(heads, OpAdd(), 0ull, red64);
   por = block_reduce(por, OpOr(), 0ull, red64);

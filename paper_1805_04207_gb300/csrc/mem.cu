@@ -185,12 +185,12 @@ constexpr int kLvItems = kTileItems;
 
 __global__ void __launch_bounds__(kLvThreads) k_mem_levels(LevelArgs a) {
   if (!gate_open(a.gate, a.gate_want)) return;
-  __shared__ u32 coc[kLevels][kCocDense];
+  __shared__ u32 coc[kLevels][kCocShared];
   __shared__ Seg sh[33];
   __shared__ u64 pre_slot[2];
   __shared__ u64 red64[32];
   DevState* st = &a.arena->st;
-  for (int i = threadIdx.x; i < kLevels * kCocDense; i += kLvThreads) (&coc[0][0])[i] = 0u;
+  for (int i = threadIdx.x; i < kLevels * kCocShared; i += kLvThreads) (&coc[0][0])[i] = 0u;
   __syncthreads();
   const u64 n = *a.n;
   const u64* words = *a.cur ? a.b : a.a;
@@ -233,16 +233,17 @@ __global__ void __launch_bounds__(kLvThreads) k_mem_levels(LevelArgs a) {
       tile_runs<kLvItems>(
           key, nvalid, pos0, prev, tile_n, [shift](u64 x) { return x >> shift; }, [](u64) { return 0ull; },
           [&](u64 len, u64) {
-            if (len < (u64)kCocDense) atomicAdd(&coc[l][len], 1u);
+            if (len < (u64)kCocShared) atomicAdd(&coc[l][len], 1u);
+            else if (len < (u64)kCocDense) atomicAdd(&a.arena->mem_coc[l][len], 1ull);
             else overflow_append(a.over, a.over_cap, st, l, len);
           },
           &a.tiles[(u64)l * a.ntiles + tile], sh, pre_slot);
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < kLevels * kCocDense; i += kLvThreads) {
+  for (int i = threadIdx.x; i < kLevels * kCocShared; i += kLvThreads) {
     const u32 c = (&coc[0][0])[i];
-    if (c) atomicAdd(&a.arena->mem_coc[0][0] + i, (u64)c);
+    if (c) atomicAdd(&a.arena->mem_coc[i / kCocShared][i % kCocShared], (u64)c);
   }
   heads0 = block_reduce(heads0, OpAdd(), 0ull, red64);
   ur = block_reduce(ur, OpAdd(), 0ull, red64);

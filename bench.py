@@ -51,11 +51,12 @@ def parse():
     ap.add_argument("--scale", type=int, default=0, help="shrink the workload by 2^scale (testing only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="large", choices=["large", "batched", "serving", "precision"],
+    ap.add_argument("--workload", default="large", choices=["large", "batched", "serving", "precision", "partitioned"],
                     help="large (default): the 2^28-event invocation; batched: 512 uneven invocations per "
                          "step in one graph; serving: Poisson jobs streaming chunks; precision: 2^30 events, "
                          "FP32-compensated vs FP64 entropies")
     ap.add_argument("--jobs", type=int, default=100, help="serving: number of jobs")
+    ap.add_argument("--partitions", type=int, default=8, help="partitioned: number of partitions")
     return ap.parse_args()
 
 
@@ -349,6 +350,44 @@ def run_precision(args, P, torch, local, world, rank):
         "counts_identical": same_counts, "fp64_ms_per_step": round(times[0] * 1e3, 3)})
 
 
+def run_partitioned(args, P, torch, local, world, rank):
+    """An invocation held in host memory, reduced in 1 and in P partitions:
+    time per invocation (routing and host-to-device copies included) and the
+    device memory the handle holds."""
+    import synth
+    from paper_1805_04207_gb300.api import push_trace
+    s = args.scale
+    tr = synth.large(device="cpu", seed=rank, n_mem=1 << (26 - s), n_br=1 << (24 - s), n_wi=1 << (18 - s),
+                     per_wi=1024, zipf_distinct=1 << (24 - s))
+    tr.run_wi = tr.run_wi.to(torch.int32)
+    for t in ("mem", "br", "ops", "run_wi", "run_off", "run_len"):
+        setattr(tr, t, getattr(tr, t).contiguous().pin_memory())
+    out, times, held = {}, {}, {}
+    for parts in (1, args.partitions):
+        c = P.Characterizer(device=local, n_opcodes=tr.n_opcodes, partitions=parts, **plan_for(tr.n_mem))
+        for _ in range(max(3, args.warmup)):
+            push_trace(c, tr)
+            out[parts] = c.compute(want_hist=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            push_trace(c, tr)
+            out[parts] = c.compute(want_hist=False)
+        torch.cuda.synchronize()
+        times[parts] = (time.perf_counter() - t0) / args.steps
+        held[parts] = P.aiwc_device_bytes(c.h)
+        c.close()
+    a, b = out[1], out[args.partitions]
+    same = all(a[k] == b[k] for k in a if not isinstance(a[k], (float, list))) and \
+        max(abs(x - y) for x, y in zip(a["entropy"], b["entropy"])) < 1e-12
+    return base_line(args, world, world * tr.n_mem / times[args.partitions], times[args.partitions] * 1e3, {
+        "config": {"workload": f"partitioned: host-resident invocation of 2^{26 - s} memory, 2^{24 - s} branch, "
+                               f"2^{28 - s} opcode events (large-invocation shapes) in {args.partitions} "
+                               f"partitions", "timing": "wall clock per invocation incl. routing and copies"},
+        "partitions": args.partitions, "device_bytes": held[args.partitions], "device_bytes_unpartitioned": held[1],
+        "ms_per_step_unpartitioned": round(times[1] * 1e3, 3), "results_identical": same})
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -360,7 +399,8 @@ def main():
         import torch
         import paper_1805_04207_gb300 as P
         torch.cuda.set_device(local)
-        fn = {"batched": run_batched, "serving": run_serving, "precision": run_precision}[args.workload]
+        fn = {"batched": run_batched, "serving": run_serving, "precision": run_precision,
+              "partitioned": run_partitioned}[args.workload]
         line = fn(args, P, torch, local, world, rank)
         if rank == 0:
             print(json.dumps(line), flush=True)

@@ -11,9 +11,11 @@
 #include <cstddef>
 #include <functional>
 #include <mutex>
+#include <new>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "aiwc_internal.cuh"
@@ -59,6 +61,37 @@ const char* const kStageNames[kNumStages] = {"mem_ingest", "branch_ingest", "ins
 }  // namespace
 
 void aiwc::set_last_error(const std::string& msg) { g_last_error = msg; }
+
+// Page-locked host memory for the partition buffers (host-to-device copies
+// run at link speed from it); resize leaves new elements uninitialised.
+template <typename T>
+struct PinnedAlloc {
+  using value_type = T;
+  PinnedAlloc() = default;
+  template <typename U>
+  PinnedAlloc(const PinnedAlloc<U>&) {}
+  T* allocate(size_t n) {
+    void* p = nullptr;
+    if (cudaMallocHost(&p, n * sizeof(T)) != cudaSuccess) {
+      cudaGetLastError();
+      throw std::bad_alloc();
+    }
+    return static_cast<T*>(p);
+  }
+  void deallocate(T* p, size_t) { cudaFreeHost(p); }
+  template <typename U>
+  void construct(U* p) {
+    ::new (static_cast<void*>(p)) U;
+  }
+  template <typename U, typename... A>
+  void construct(U* p, A&&... a) {
+    ::new (static_cast<void*>(p)) U(std::forward<A>(a)...);
+  }
+  bool operator==(const PinnedAlloc&) const { return true; }
+  bool operator!=(const PinnedAlloc&) const { return false; }
+};
+template <typename T>
+using pinned_vector = std::vector<T, PinnedAlloc<T>>;
 
 struct aiwc_handle {
   aiwc_config cfg;
@@ -109,12 +142,21 @@ struct aiwc_handle {
   double stage_last[kNumStages] = {0};
   // partitioned invocations: pushed events held on the host per partition
   struct PartBuf {
-    std::vector<uint8_t> mem;      // 16-byte memory events
-    std::vector<uint64_t> br;      // 8-byte branch events
-    std::vector<uint16_t> ops;
-    std::vector<uint32_t> run_wi;
-    std::vector<uint64_t> run_off, run_len;
-    std::vector<uint16_t> widths;
+    pinned_vector<uint8_t> mem;    // 16-byte memory events
+    pinned_vector<uint64_t> br;    // 8-byte branch events
+    pinned_vector<uint16_t> ops;
+    pinned_vector<uint32_t> run_wi;
+    pinned_vector<uint64_t> run_off, run_len;
+    pinned_vector<uint16_t> widths;
+    void clear() {  // keeps the capacity for the next invocation
+      mem.clear();
+      br.clear();
+      ops.clear();
+      run_wi.clear();
+      run_off.clear();
+      run_len.clear();
+      widths.clear();
+    }
   };
   std::vector<PartBuf> parts;      // empty when not partitioned
   bool replaying = false;          // compute is pushing one partition to the device
@@ -469,6 +511,51 @@ aiwc_status host_view(aiwc_handle* h, const T* p, size_t n, int on_device, std::
   return AIWC_OK;
 }
 
+// A stable partition of n items over the host's cores: the partition of
+// each item, per-thread counts, offsets by (partition, thread), then each
+// thread copies its items in order. `key(i)` names item i's partition;
+// `size(i)` its length in units; `copy(i, p, at)` writes item i to
+// partition p at unit offset `at`; `grow(p, units)` resizes partition p.
+template <typename Key, typename Size, typename Grow, typename Copy>
+void stable_partition(size_t n, u32 P, Key key, Size size, Grow grow, Copy copy) {
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const size_t T = n < (1u << 16) ? 1 : std::min<size_t>(hw, 32);
+  std::vector<uint8_t> pid(n);
+  std::vector<std::vector<uint64_t>> cnt(T, std::vector<uint64_t>(P, 0));
+  auto range = [&](size_t t) { return std::make_pair(n * t / T, n * (t + 1) / T); };
+  auto par = [&](auto fn) {
+    std::vector<std::thread> ts;
+    for (size_t t = 1; t < T; ++t) ts.emplace_back(fn, t);
+    fn(0);
+    for (auto& th : ts) th.join();
+  };
+  par([&](size_t t) {
+    auto r = range(t);
+    for (size_t i = r.first; i < r.second; ++i) {
+      const u32 p = key(i);
+      pid[i] = (uint8_t)p;
+      cnt[t][p] += size(i);
+    }
+  });
+  std::vector<std::vector<uint64_t>> at(T, std::vector<uint64_t>(P, 0));
+  for (u32 p = 0; p < P; ++p) {
+    uint64_t base = grow(p, 0);  // current length
+    for (size_t t = 0; t < T; ++t) {
+      at[t][p] = base;
+      base += cnt[t][p];
+    }
+    grow(p, base);
+  }
+  par([&](size_t t) {
+    auto r = range(t);
+    for (size_t i = r.first; i < r.second; ++i) {
+      const u32 p = pid[i];
+      copy(i, p, at[t][p]);
+      at[t][p] += size(i);
+    }
+  });
+}
+
 // Memory events go with their superblock (space, address >> 11): every
 // skip-level group lies inside one superblock, so a partition's groups are
 // whole.
@@ -478,12 +565,18 @@ aiwc_status route_mem(aiwc_handle* h, const aiwc_mem_event* ev, size_t n, int on
   aiwc_status s = host_view(h, ev, n, on_device, &tmp, &e);
   if (s != AIWC_OK) return s;
   const u32 P = (u32)h->parts.size();
-  for (size_t i = 0; i < n; ++i) {
-    const uint64_t key = ((uint64_t)((e[i].flags >> 1) & 3u) << 56) | ((e[i].addr & (AIWC_ADDR_LIMIT - 1)) >> 11);
-    auto& m = h->parts[part_of(key, P)].mem;
-    const uint8_t* b = reinterpret_cast<const uint8_t*>(e + i);
-    m.insert(m.end(), b, b + 16);
-  }
+  stable_partition(
+      n, P,
+      [&](size_t i) {
+        return part_of(((uint64_t)((e[i].flags >> 1) & 3u) << 56) | ((e[i].addr & (AIWC_ADDR_LIMIT - 1)) >> 11), P);
+      },
+      [](size_t) { return (uint64_t)1; },
+      [&](u32 p, uint64_t len) {
+        auto& m = h->parts[p].mem;
+        if (len) m.resize(16 * len);
+        return (uint64_t)(m.size() / 16);
+      },
+      [&](size_t i, u32 p, uint64_t at) { memcpy(h->parts[p].mem.data() + 16 * at, e + i, 16); });
   return AIWC_OK;
 }
 
@@ -494,11 +587,14 @@ aiwc_status route_branch(aiwc_handle* h, const aiwc_branch_event* ev, size_t n, 
   aiwc_status s = host_view(h, ev, n, on_device, &tmp, &e);
   if (s != AIWC_OK) return s;
   const u32 P = (u32)h->parts.size();
-  for (size_t i = 0; i < n; ++i) {
-    uint64_t w;
-    memcpy(&w, e + i, 8);
-    h->parts[part_of(e[i].site, P)].br.push_back(w);
-  }
+  stable_partition(
+      n, P, [&](size_t i) { return part_of(e[i].site, P); }, [](size_t) { return (uint64_t)1; },
+      [&](u32 p, uint64_t len) {
+        auto& b = h->parts[p].br;
+        if (len) b.resize(len);
+        return (uint64_t)b.size();
+      },
+      [&](size_t i, u32 p, uint64_t at) { memcpy(h->parts[p].br.data() + at, e + i, 8); });
   return AIWC_OK;
 }
 
@@ -517,18 +613,41 @@ aiwc_status route_runs(aiwc_handle* h, const uint32_t* run_wi, const uint64_t* r
       (s = host_view(h, run_len, n_runs, on_device, &tlen, &len)) != AIWC_OK ||
       (s = host_view(h, ops, n_ops, on_device, &tops, &op)) != AIWC_OK)
     return s;
-  const u32 P = (u32)h->parts.size();
-  for (size_t r = 0; r < n_runs; ++r) {
+  for (size_t r = 0; r < n_runs; ++r)
     if (off[r] > n_ops || len[r] > n_ops - off[r]) {
       h->part_err |= kErrRun;
-      continue;
+      return AIWC_OK;  // reported by compute, like the unpartitioned path
     }
-    auto& pb = h->parts[part_of(wi[r], P)];
-    pb.run_wi.push_back(wi[r]);
-    pb.run_off.push_back(pb.ops.size());
-    pb.run_len.push_back(len[r]);
-    pb.ops.insert(pb.ops.end(), op + off[r], op + off[r] + len[r]);
-  }
+  const u32 P = (u32)h->parts.size();
+  // runs first (one unit each), then their opcodes (len units each), both stable
+  std::vector<uint64_t> run_at(n_runs);
+  stable_partition(
+      n_runs, P, [&](size_t r) { return part_of(wi[r], P); }, [](size_t) { return (uint64_t)1; },
+      [&](u32 p, uint64_t n) {
+        auto& pb = h->parts[p];
+        if (n) {
+          pb.run_wi.resize(n);
+          pb.run_off.resize(n);
+          pb.run_len.resize(n);
+        }
+        return (uint64_t)pb.run_wi.size();
+      },
+      [&](size_t r, u32 p, uint64_t at) {
+        h->parts[p].run_wi[at] = wi[r];
+        h->parts[p].run_len[at] = len[r];
+        run_at[r] = at;
+      });
+  stable_partition(
+      n_runs, P, [&](size_t r) { return part_of(wi[r], P); }, [&](size_t r) { return len[r]; },
+      [&](u32 p, uint64_t n) {
+        auto& o = h->parts[p].ops;
+        if (n) o.resize(n);
+        return (uint64_t)o.size();
+      },
+      [&](size_t r, u32 p, uint64_t at) {
+        h->parts[p].run_off[run_at[r]] = at;
+        memcpy(h->parts[p].ops.data() + at, op + off[r], len[r] * 2);
+      });
   return AIWC_OK;
 }
 
@@ -543,6 +662,16 @@ aiwc_status route_widths(aiwc_handle* h, const uint16_t* w, size_t n, int on_dev
 }
 
 aiwc_status compute_partitioned(aiwc_handle* h, aiwc_metrics* out);
+
+// Runs a routing step; page-locked host memory running out is AIWC_ENOMEM.
+template <typename F>
+aiwc_status routed(aiwc_handle* h, F&& f) {
+  try {
+    return f();
+  } catch (const std::bad_alloc&) {
+    return fail(h, AIWC_ENOMEM, "page-locked host memory for the partitions is exhausted", false);
+  }
+}
 
 }  // namespace
 
@@ -630,7 +759,7 @@ aiwc_status aiwc_push_mem(aiwc_handle* h, const aiwc_mem_event* ev, size_t n, in
   DeviceGuard g(h->cfg.device);
   if (on_device && ((uintptr_t)ev & 15u))
     return fail(h, AIWC_EINVAL, "device memory events must be 16-byte aligned", false);
-  if (routing(h)) return route_mem(h, ev, n, on_device);
+  if (routing(h)) return routed(h, [&] { return route_mem(h, ev, n, on_device); });
   ENSURE(h->mem_a, (h->n_mem + n) * 8, true);
   if ((s = ensure_bitmap(h)) != AIWC_OK) return s;
   if (use_hash(h) && (s = ensure_table(h)) != AIWC_OK) return s;
@@ -677,7 +806,7 @@ aiwc_status aiwc_push_branch(aiwc_handle* h, const aiwc_branch_event* ev, size_t
   DeviceGuard g(h->cfg.device);
   if (on_device && ((uintptr_t)ev & 7u))
     return fail(h, AIWC_EINVAL, "device branch events must be 8-byte aligned", false);
-  if (routing(h)) return route_branch(h, ev, n, on_device);
+  if (routing(h)) return routed(h, [&] { return route_branch(h, ev, n, on_device); });
   ENSURE(h->br_a, (h->n_br + n) * 8, true);
   if ((s = ensure_bitmap(h)) != AIWC_OK) return s;
   BranchIngestArgs a;
@@ -716,7 +845,7 @@ aiwc_status aiwc_push_widths(aiwc_handle* h, const uint16_t* widths, size_t n, i
   if (n == 0) return AIWC_OK;
   if (!widths) return fail(h, AIWC_EINVAL, "null width pointer", false);
   DeviceGuard g(h->cfg.device);
-  if (routing(h)) return route_widths(h, widths, n, on_device);
+  if (routing(h)) return routed(h, [&] { return route_widths(h, widths, n, on_device); });
   StageScope scope(h, kStInstrRuns);
   if (on_device) {
     launch_simd_widths(widths, n, h->arena, h->stream);
@@ -740,7 +869,7 @@ aiwc_status aiwc_push_instr(aiwc_handle* h, uint32_t work_item, const uint16_t* 
     std::vector<uint16_t> one;
     const uint16_t* p = ops;
     if ((s = host_view(h, ops, n, on_device, &one, &p)) != AIWC_OK) return s;
-    return route_runs(h, &work_item, &off, &len, 1, p, n, 0);
+    return routed(h, [&] { return route_runs(h, &work_item, &off, &len, 1, p, n, 0); });
   }
   if (!h->pend_wi.empty() && h->pend_device != dev) {
     if ((s = flush_pending(h)) != AIWC_OK) return s;
@@ -770,7 +899,7 @@ aiwc_status aiwc_push_instr_runs(aiwc_handle* h, const uint32_t* run_wi, const u
   if (on_device && (((uintptr_t)ops & 1u) || ((uintptr_t)run_wi & 3u) || ((uintptr_t)run_off & 7u) ||
                     ((uintptr_t)run_len & 7u)))
     return fail(h, AIWC_EINVAL, "device run tables / opcodes are misaligned", false);
-  if (routing(h)) return route_runs(h, run_wi, run_off, run_len, n_runs, ops, n_ops, on_device);
+  if (routing(h)) return routed(h, [&] { return route_runs(h, run_wi, run_off, run_len, n_runs, ops, n_ops, on_device); });
   if (on_device)
     return runs_device(h, run_wi, (const u64*)run_off, (const u64*)run_len, n_runs, ops, n_ops, n_ops);
   return runs_host(h, run_wi, run_off, run_len, n_runs, ops, n_ops);
@@ -1199,7 +1328,7 @@ aiwc_status recover(aiwc_handle* h) {
   reset_host(h);
   h->replaying = false;
   h->part_err = 0;
-  for (auto& pb : h->parts) pb = aiwc_handle::PartBuf();
+  for (auto& pb : h->parts) pb.clear();
   cudaGetLastError();
   if (reset_device_state(h, h->stream) == AIWC_OK && cudaStreamSynchronize(h->stream) == cudaSuccess) h->broken = false;
   return AIWC_ESTATE;
@@ -1252,11 +1381,13 @@ aiwc_status reduce_current(aiwc_handle* h, bool defer_finalize) {
 aiwc_status compute_partitioned(aiwc_handle* h, aiwc_metrics* out) {
   uint64_t* user_hist = out->opcode_hist;
   cudaStream_t st = h->stream;
-  std::vector<aiwc_handle::PartBuf> parts(h->parts.size());
-  parts.swap(h->parts);  // the handle keeps empty buffers for the next invocation
+  auto& parts = h->parts;
   const u32 perr = h->part_err;
   h->part_err = 0;
-  if (perr & kErrRun) return fail(h, AIWC_EINVAL, "instruction run reaches past its opcode array", false);
+  if (perr & kErrRun) {
+    for (auto& pb : parts) pb.clear();
+    return fail(h, AIWC_EINVAL, "instruction run reaches past its opcode array", false);
+  }
   u64 total_cap = 0;  // the merged entries fit the sum of the partitions' bounds
   for (auto& pb : parts)
     total_cap += over_bound_sizes(h->cfg.n_opcodes, pb.mem.size() / 16, pb.br.size(), pb.run_wi.size(),
@@ -1281,8 +1412,10 @@ aiwc_status compute_partitioned(aiwc_handle* h, aiwc_metrics* out) {
                                pb.ops.data(), pb.ops.size(), 0);
     if (s == AIWC_OK && !pb.widths.empty()) s = aiwc_push_widths(h, pb.widths.data(), pb.widths.size(), 0);
     if (s == AIWC_OK) s = reduce_current(h, true);
+    pb.clear();
     if (s != AIWC_OK) {
       h->replaying = false;
+      for (auto& q : parts) q.clear();
       return s;
     }
     launch_merge_partition(h->arena, (const u64*)h->over_a.p, h->c_over_cap, h->total, (u64*)h->over_total.p,

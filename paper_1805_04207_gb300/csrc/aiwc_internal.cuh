@@ -293,6 +293,7 @@ struct SiteArgs {
   u64 over_cap{};
   Arena* arena{};
   int grid{};
+  const uint8_t* outcomes{};  // per-site path: outcome bytes sorted by site instead of the words
 };
 // Stable counting sort of the branch words by site, for site ids below
 // kCsSites when work-item ids arrived in non-decreasing order (the site alone
@@ -301,7 +302,8 @@ struct SiteArgs {
 constexpr u32 kCsSites = 4096;
 struct SiteSortArgs {
   const u64* src{};      // branch words in push order
-  u64* dst{};            // out: words sorted by site (stable)
+  u64* dst{};            // out: words sorted by site (stable), or
+  uint8_t* dst8{};       // out: just their outcome bits, one byte each (the per-site path reads no more)
   u32* sort_cur{};       // set to 1: dst is the live buffer
   u64 n{};
   u32* counts{};         // scratch: site_sort_count_words(n) words
@@ -313,7 +315,8 @@ struct SiteSortArgs {
 };
 size_t site_sort_count_words(u64 n);
 size_t site_sort_chunk_words(u64 n);
-void launch_site_sort(const SiteSortArgs& a, cudaStream_t s);
+void launch_site_sort_count(const SiteSortArgs& a, cudaStream_t s);    // counts, scan, site list
+void launch_site_sort_scatter(const SiteSortArgs& a, cudaStream_t s);  // the sorted output
 
 constexpr u32 kSiteMaxHist = 17;       // dense pattern bins: 2^15 per pass, at most 4 passes
 constexpr u64 kSiteMaxLen = 65535;     // packed 16-bit taken / total counters

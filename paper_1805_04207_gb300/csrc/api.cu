@@ -1091,24 +1091,29 @@ SiteArgs site_args(aiwc_handle* h, const SortDesc& bsort) {
   return sa;
 }
 
+SiteSortArgs site_sort_args(aiwc_handle* h) {
+  SiteSortArgs ss;
+  ss.src = (const u64*)h->br_a.p;
+  ss.dst = (u64*)h->br_b.p;
+  ss.sort_cur = &h->arena->st.sort_cur[kSortBranch];
+  ss.n = h->n_br;
+  ss.counts = (u32*)h->pat_a.p;
+  ss.chunks = (u32*)h->pat_b.p;
+  ss.sites = (u64*)h->sites.p;
+  ss.sites_cap = h->c_sites_cap;
+  ss.arena = h->arena;
+  ss.sm_count = h->sm_count;
+  return ss;
+}
+
 // Stages that must run before the branch-path choice: the branch sort and the site list.
 void enqueue_part1(aiwc_handle* h, cudaStream_t st, const Plan& p) {
   if (!h->n_br) return;
   if (p.site_sort) {
-    // sorted words, the site list, n_sites and the longest site in one pass
+    // the site list, n_sites and the longest site; the sorted output follows
+    // once the branch path is chosen
     StageScope sc(h, kStBrSort);
-    SiteSortArgs ss;
-    ss.src = (const u64*)h->br_a.p;
-    ss.dst = (u64*)h->br_b.p;
-    ss.sort_cur = &h->arena->st.sort_cur[kSortBranch];
-    ss.n = h->n_br;
-    ss.counts = (u32*)h->pat_a.p;
-    ss.chunks = (u32*)h->pat_b.p;
-    ss.sites = (u64*)h->sites.p;
-    ss.sites_cap = h->c_sites_cap;
-    ss.arena = h->arena;
-    ss.sm_count = h->sm_count;
-    launch_site_sort(ss, st);
+    launch_site_sort_count(site_sort_args(h), st);
     return;
   }
   SortDesc bsort = branch_sort_desc(h);
@@ -1187,11 +1192,19 @@ aiwc_status enqueue_part2(aiwc_handle* h, cudaStream_t st, const Plan& p) {
     // device flag lets exactly one of them work
     const u32* gate = p.gated ? &dst->br_persite : nullptr;
     SortDesc bsort = branch_sort_desc(h);
+    if (p.site_sort) {
+      // the per-site path needs only the outcome bits: one byte per event
+      StageScope sc(h, kStBrSort);
+      SiteSortArgs ss = site_sort_args(h);
+      if (p.per_site) ss.dst8 = (uint8_t*)h->br_b.p;
+      launch_site_sort_scatter(ss, st);
+    }
     if (p.gated || p.per_site) {
       StageScope sc(h, kStPatRuns);
       SiteArgs sa = site_args(h, bsort);
       sa.gate = gate;
       sa.gate_want = 1;
+      if (p.site_sort) sa.outcomes = (const uint8_t*)h->br_b.p;
       launch_site_patterns(sa, st);
     }
     if (p.gated || !p.per_site) {

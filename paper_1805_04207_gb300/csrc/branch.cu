@@ -280,6 +280,7 @@ __global__ void __launch_bounds__(kCsScanThreads) k_cs_scan_sites(SiteSortArgs a
 // position: chunk offset + prefix within the chunk + rank within the tile.
 constexpr size_t kCsScatterSmem = (size_t)(kCsWarps * kCsSites / 2 + kCsSites) * 4;
 
+template <bool OUT8>
 __global__ void __launch_bounds__(kCsThreads) k_cs_scatter(SiteSortArgs a) {
   extern __shared__ u32 csm[];
   u32 (*wc)[kCsSites / 2] = reinterpret_cast<u32 (*)[kCsSites / 2]>(csm);
@@ -342,7 +343,11 @@ __global__ void __launch_bounds__(kCsThreads) k_cs_scatter(SiteSortArgs a) {
           b = (atomicAdd(&wc[wp][site >> 1], (u32)__popc(peers) << sh) >> sh) & 0xFFFFu;
         }
         b = __shfl_sync(0xffffffffu, b, leader);
-        if (v) a.dst[(u64)toff[site] + b + (u32)__popc(peers & lt)] = word[q];
+        const u64 pos = (u64)toff[site] + b + (u32)__popc(peers & lt);
+        if (v) {
+          if (OUT8) a.dst8[pos] = (uint8_t)(word[q] & 1ull);
+          else a.dst[pos] = word[q];
+        }
       }
     }
     __syncthreads();
@@ -400,7 +405,7 @@ __global__ void __launch_bounds__(kSpThreads) k_site_patterns(SiteArgs a) {
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const u64 j = (u64)(c0 + q * nw) * 32 + lane;
-        t[q] = j < m && (w[start + j] & 1ull);
+        t[q] = j < m && (a.outcomes ? (a.outcomes[start + j] & 1u) : (w[start + j] & 1ull));
       }
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
@@ -682,14 +687,21 @@ void launch_branch_ingest(const BranchIngestArgs& a, cudaStream_t s) {
 size_t site_sort_count_words(u64 n) { return (size_t)(cs_tiles(n) ? cs_tiles(n) : 1) * kCsSites; }
 size_t site_sort_chunk_words(u64 n) { return (size_t)(cs_chunks(n) ? cs_chunks(n) : 1) * kCsSites; }
 
-void launch_site_sort(const SiteSortArgs& a, cudaStream_t s) {
+void launch_site_sort_count(const SiteSortArgs& a, cudaStream_t s) {
   if (a.n == 0) return;
   const u64 ntiles = cs_tiles(a.n), nchunks = cs_chunks(a.n);
   k_cs_count<<<(unsigned)std::min<u64>(ntiles, (u64)a.sm_count * 8), kCsThreads, 0, s>>>(a);
   k_cs_scan_chunks<<<(unsigned)std::min<u64>(nchunks, (u64)a.sm_count * 2), kCsScanThreads, 0, s>>>(a);
   k_cs_scan_sites<<<1, kCsScanThreads, 0, s>>>(a);
-  k_cs_scatter<<<(unsigned)std::min<u64>(ntiles, (u64)a.sm_count * 2), kCsThreads, kCsScatterSmem, s>>>(a);
-  count_launches(4);
+  count_launches(3);
+}
+
+void launch_site_sort_scatter(const SiteSortArgs& a, cudaStream_t s) {
+  if (a.n == 0) return;
+  const unsigned g = (unsigned)std::min<u64>(cs_tiles(a.n), (u64)a.sm_count * 2);
+  if (a.dst8) k_cs_scatter<true><<<g, kCsThreads, kCsScatterSmem, s>>>(a);
+  else k_cs_scatter<false><<<g, kCsThreads, kCsScatterSmem, s>>>(a);
+  count_launches(1);
 }
 
 void launch_branch_mask(Arena* arena, cudaStream_t s) {
@@ -716,7 +728,8 @@ static size_t site_patterns_smem() {
 
 void init_branch_attributes() {
   cudaFuncSetAttribute(k_site_patterns, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)site_patterns_smem());
-  cudaFuncSetAttribute(k_cs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCsScatterSmem);
+  cudaFuncSetAttribute(k_cs_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCsScatterSmem);
+  cudaFuncSetAttribute(k_cs_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCsScatterSmem);
 }
 
 void launch_site_patterns(const SiteArgs& a, cudaStream_t s) {

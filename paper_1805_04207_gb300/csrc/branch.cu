@@ -165,10 +165,15 @@ __global__ void __launch_bounds__(kCsThreads) k_cs_count(SiteSortArgs a) {
   }
 }
 
+constexpr int kCs2Threads = 256;                           // phase 2 blocks
+constexpr int kCs2Sites = kCs2Threads * 4;                 // sites per phase-2a block (four per thread)
+
 // Phase 2a: within each chunk of kCsChunk tiles, counts become exclusive
 // prefixes over the chunk's tiles; chunks[chunk][site] gets the chunk total.
-__global__ void __launch_bounds__(kCsScanThreads) k_cs_scan_chunks(SiteSortArgs a) {
+// Blocks: (chunk, quarter of the sites).
+__global__ void __launch_bounds__(kCs2Threads) k_cs_scan_chunks(SiteSortArgs a) {
   const u64 ntiles = cs_tiles(a.n), nchunks = cs_chunks(a.n);
+  const u32 col = blockIdx.y * (kCs2Sites / 4) + threadIdx.x;  // uint4 column
   for (u64 c = blockIdx.x; c < nchunks; c += gridDim.x) {
     uint4 run = make_uint4(0u, 0u, 0u, 0u);
     const u64 t1 = umin64(ntiles, (c + 1) * kCsChunk);
@@ -177,42 +182,49 @@ __global__ void __launch_bounds__(kCsScanThreads) k_cs_scan_chunks(SiteSortArgs 
       uint4 v[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q)
-        v[q] = t0 + q < t1 ? reinterpret_cast<const uint4*>(a.counts + (t0 + q) * kCsSites)[threadIdx.x]
+        v[q] = t0 + q < t1 ? reinterpret_cast<const uint4*>(a.counts + (t0 + q) * kCsSites)[col]
                            : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        if (t0 + q < t1) reinterpret_cast<uint4*>(a.counts + (t0 + q) * kCsSites)[threadIdx.x] = run;
+        if (t0 + q < t1) reinterpret_cast<uint4*>(a.counts + (t0 + q) * kCsSites)[col] = run;
         run.x += v[q].x; run.y += v[q].y; run.z += v[q].z; run.w += v[q].w;
       }
     }
-    reinterpret_cast<uint4*>(a.chunks + c * kCsSites)[threadIdx.x] = run;
+    reinterpret_cast<uint4*>(a.chunks + c * kCsSites)[col] = run;
   }
 }
 
-// Phase 2b (one block): per site, exclusive prefix over chunks plus the
-// site's start (exclusive prefix of the site totals); the site list, the
-// number of sites and the longest site.
+// Phase 2b: per site (one per thread), exclusive prefix over the chunks and
+// the site's total (in the words after the chunk rows).
+__global__ void __launch_bounds__(kCs2Threads) k_cs_scan_site_chunks(SiteSortArgs a) {
+  const u64 nchunks = cs_chunks(a.n);
+  const u32 site = blockIdx.x * kCs2Threads + threadIdx.x;
+  u32 run = 0;
+  for (u64 c0 = 0; c0 < nchunks; c0 += 8) {
+    u32 v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = c0 + q < nchunks ? a.chunks[(c0 + q) * kCsSites + site] : 0u;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (c0 + q < nchunks) a.chunks[(c0 + q) * kCsSites + site] = run;
+      run += v[q];
+    }
+  }
+  a.chunks[nchunks * kCsSites + site] = run;  // site total
+}
+
+// Phase 2c (one block): each site's start (exclusive prefix of the totals),
+// the site list, the number of sites and the longest site.
 __global__ void __launch_bounds__(kCsScanThreads) k_cs_scan_sites(SiteSortArgs a) {
   __shared__ u64 wt64[33];
   __shared__ u32 wt32[33];
   __shared__ u64 red64[32];
   DevState* st = &a.arena->st;
   const u64 nchunks = cs_chunks(a.n);
-  u64 tot[kCsPer] = {0, 0, 0, 0};
-  for (u64 c0 = 0; c0 < nchunks; c0 += 8) {
-    uint4 v[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q)
-      v[q] = c0 + q < nchunks ? reinterpret_cast<const uint4*>(a.chunks + (c0 + q) * kCsSites)[threadIdx.x]
-                              : make_uint4(0u, 0u, 0u, 0u);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      if (c0 + q < nchunks)
-        reinterpret_cast<uint4*>(a.chunks + (c0 + q) * kCsSites)[threadIdx.x] =
-            make_uint4((u32)tot[0], (u32)tot[1], (u32)tot[2], (u32)tot[3]);
-      tot[0] += v[q].x; tot[1] += v[q].y; tot[2] += v[q].z; tot[3] += v[q].w;
-    }
-  }
+  const u32* totals = a.chunks + nchunks * kCsSites;
+  u32* starts = a.chunks + (nchunks + 1) * kCsSites;
+  const uint4 tv = reinterpret_cast<const uint4*>(totals)[threadIdx.x];
+  const u64 tot[kCsPer] = {tv.x, tv.y, tv.z, tv.w};
   // site starts: block exclusive scan of the per-thread sums (sites 4i .. 4i+3)
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const u64 mine = tot[0] + tot[1] + tot[2] + tot[3];
@@ -245,10 +257,10 @@ __global__ void __launch_bounds__(kCsScanThreads) k_cs_scan_sites(SiteSortArgs a
   u64 start = wt64[w] + inc - mine;
   u64 k = wt32[w] + inz - nz;
   u64 mx = 0;
-  u64 base[kCsPer];
+  u32 sv[kCsPer];
 #pragma unroll
   for (int q = 0; q < kCsPer; ++q) {
-    base[q] = start;
+    sv[q] = (u32)start;
     if (tot[q]) {
       if (k < a.sites_cap) {
         a.sites[2 * k] = start;
@@ -259,13 +271,7 @@ __global__ void __launch_bounds__(kCsScanThreads) k_cs_scan_sites(SiteSortArgs a
     }
     start += tot[q];
   }
-  // chunk offsets become absolute positions
-#pragma unroll 8
-  for (u64 c = 0; c < nchunks; ++c) {
-    uint4* p = reinterpret_cast<uint4*>(a.chunks + c * kCsSites) + threadIdx.x;
-    const uint4 v = *p;
-    *p = make_uint4((u32)(v.x + base[0]), (u32)(v.y + base[1]), (u32)(v.z + base[2]), (u32)(v.w + base[3]));
-  }
+  reinterpret_cast<uint4*>(starts)[threadIdx.x] = make_uint4(sv[0], sv[1], sv[2], sv[3]);
   mx = block_reduce(mx, OpMax(), 0ull, red64);
   if (threadIdx.x == kCsScanThreads - 1) st->n_sites = k;  // the last thread's count is the total
   if (threadIdx.x == 0) {
@@ -291,7 +297,8 @@ __global__ void __launch_bounds__(kCsThreads) k_cs_scatter(SiteSortArgs a) {
   for (u64 t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const u32* cc = a.chunks + (t / kCsChunk) * kCsSites;
     const u32* ct = a.counts + t * kCsSites;
-    for (int i = threadIdx.x; i < (int)kCsSites; i += kCsThreads) toff[i] = cc[i] + ct[i];
+    const u32* cs = a.chunks + (cs_chunks(a.n) + 1) * kCsSites;  // site starts
+    for (int i = threadIdx.x; i < (int)kCsSites; i += kCsThreads) toff[i] = cs[i] + cc[i] + ct[i];
     for (int i = threadIdx.x; i < kCsWarps * (int)kCsSites / 2; i += kCsThreads) (&wc[0][0])[i] = 0u;
     __syncthreads();
     const u64 w0 = t * kCsTile + (u64)wp * kCsWarpEvents;
@@ -685,15 +692,16 @@ void launch_branch_ingest(const BranchIngestArgs& a, cudaStream_t s) {
 }
 
 size_t site_sort_count_words(u64 n) { return (size_t)(cs_tiles(n) ? cs_tiles(n) : 1) * kCsSites; }
-size_t site_sort_chunk_words(u64 n) { return (size_t)(cs_chunks(n) ? cs_chunks(n) : 1) * kCsSites; }
+size_t site_sort_chunk_words(u64 n) { return (size_t)(cs_chunks(n) + 2) * kCsSites; }  // + totals, starts
 
 void launch_site_sort_count(const SiteSortArgs& a, cudaStream_t s) {
   if (a.n == 0) return;
   const u64 ntiles = cs_tiles(a.n), nchunks = cs_chunks(a.n);
   k_cs_count<<<(unsigned)std::min<u64>(ntiles, (u64)a.sm_count * 8), kCsThreads, 0, s>>>(a);
-  k_cs_scan_chunks<<<(unsigned)std::min<u64>(nchunks, (u64)a.sm_count * 2), kCsScanThreads, 0, s>>>(a);
+  k_cs_scan_chunks<<<dim3((unsigned)nchunks, kCsSites / kCs2Sites), kCs2Threads, 0, s>>>(a);
+  k_cs_scan_site_chunks<<<kCsSites / kCs2Threads, kCs2Threads, 0, s>>>(a);
   k_cs_scan_sites<<<1, kCsScanThreads, 0, s>>>(a);
-  count_launches(3);
+  count_launches(4);
 }
 
 void launch_site_sort_scatter(const SiteSortArgs& a, cudaStream_t s) {

@@ -39,31 +39,38 @@ __global__ void __launch_bounds__(kBrThreads) k_branch_ingest(BranchIngestArgs a
   __shared__ u32 red32[32];
   DevState* st = &a.arena->st;
   const uint2* ev = reinterpret_cast<const uint2*>(a.ev);
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   u64 wor = 0, wand = ~0ull;
   u32 wmin = 0xFFFFFFFFu, wmax = 0u, err = 0u, unsorted = 0u;
   const u64 per_block = (u64)kBrThreads * kBrItems;
+  // each warp takes kBrItems consecutive groups of 32 events, so an event's
+  // predecessor is the lane below, or lane 31 of the group before
   for (u64 t0 = (u64)blockIdx.x * per_block; t0 < a.n; t0 += (u64)gridDim.x * per_block) {
+    const u64 w0 = t0 + (u64)wp * (32 * kBrItems);
     uint2 e[kBrItems];
 #pragma unroll
     for (int k = 0; k < kBrItems; ++k) {
-      const u64 i = t0 + (u64)k * kBrThreads + threadIdx.x;
+      const u64 i = w0 + (u64)k * 32 + lane;
       e[k] = i < a.n ? __ldcs(ev + i) : make_uint2(0u, 0u);
+    }
+    // the event before the warp's first
+    u32 carry = 0;
+    if (lane == 0 && w0 < a.n) {
+      if (w0 > 0) carry = ev[w0 - 1].y & 0x7FFFFFFFu;
+      else carry = a.push_index ? st->br_last_wi[(a.push_index - 1) & 1] : 0u;
     }
 #pragma unroll
     for (int k = 0; k < kBrItems; ++k) {
-      const u64 i = t0 + (u64)k * kBrThreads + threadIdx.x;
+      const u64 i = w0 + (u64)k * 32 + lane;
       const bool valid = i < a.n;
       const u32 wi = e[k].y & 0x7FFFFFFFu;
       mark_work_items(a.wi_bitmap, a.max_wi, wi, valid, &err);
-      // do work-item ids arrive in non-decreasing order? (lanes hold consecutive events)
+      // do work-item ids arrive in non-decreasing order?
       u32 prev = __shfl_up_sync(0xffffffffu, wi, 1);
-      if (lane == 0 && valid) {
-        if (i > 0) prev = ev[i - 1].y & 0x7FFFFFFFu;
-        else prev = a.push_index ? st->br_last_wi[(a.push_index - 1) & 1] : 0u;
-      }
+      if (lane == 0) prev = carry;
+      carry = __shfl_sync(0xffffffffu, wi, 31);  // for lane 0 of the next group (used by lane 0 only)
       if (valid) {
-        if (wi < prev) unsorted = 1u;
+        if (wi < prev) unsorted = 1u;  // the first push's first event compares with 0
         if (i == a.n - 1) st->br_last_wi[a.push_index & 1] = wi;
         const u64 w = ((u64)e[k].x << 32) | ((u64)wi << 1) | (u64)(e[k].y >> 31);
         a.words[a.word_base + i] = w;

@@ -113,6 +113,8 @@ struct Arena {
   alignas(16) u64 itb_dense[kValDense];
   alignas(16) u64 ipt_dense[kValDense];
   u64 pat_coc[kValDense];            // m_c of the predicted-outcome counts of history patterns (c < kValDense)
+  double yok_part[16];               // finalize: partial sums of the Yokota entropy, combined by the last block
+  u32 yok_done;
   u64 site_pat_coc[kValDense];       // m_c of the predicted-outcome counts of sites
   u64 tag_begin[kNumTags + 1];       // segment of each tag in the sorted overflow list
 };

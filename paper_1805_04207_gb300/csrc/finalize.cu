@@ -249,11 +249,11 @@ __device__ __forceinline__ u64 run_end(const u64* over, u64 i, u64 oe, u64 v) {
 // accumulated in float with Kahan compensation per thread; only the
 // cross-thread reduction is in double.
 __device__ double clog_sum(const u64* dense, int dense_n, const u64* over, u64 ob, u64 oe, u32 precision,
-                           Shared& s) {
+                           Shared& s, int c_lo = 0) {
   if (precision == 0) {
     double acc = 0.0;
-    // eight bins' loads in flight per thread
-    for (int c0 = threadIdx.x; c0 < dense_n; c0 += 8 * blockDim.x) {
+    // bins c_lo .. dense_n-1, eight loads in flight per thread
+    for (int c0 = c_lo + (int)threadIdx.x; c0 < dense_n; c0 += 8 * blockDim.x) {
       u64 m[8];
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
@@ -287,7 +287,7 @@ __device__ double clog_sum(const u64* dense, int dense_n, const u64* over, u64 o
     comp = (t - sum) - y;
     sum = t;
   };
-  for (int c = threadIdx.x; c < dense_n; c += blockDim.x) {
+  for (int c = c_lo + (int)threadIdx.x; c < dense_n; c += blockDim.x) {
     const u64 m = dense[c];
     if (m && c > 1) add((u64)c, m);
   }
@@ -303,9 +303,12 @@ __device__ double clog_sum(const u64* dense, int dense_n, const u64* over, u64 o
 
 // One block per independent task: blocks 0..10 the entropy of each skip
 // level, 11..13 the three coverage counts, 14..15 the ITB / IPT order
-// statistics, 16 the scalar fields, 17 the Yokota branch entropy. Each block
-// writes disjoint fields.
-constexpr int kFinBlocks = 18;
+// statistics, 16 the scalar fields, 17..17+kYokParts-1 slices of the pattern
+// term of the Yokota entropy and the next block its site term; the last of
+// those to finish combines them in a fixed order. Each block writes disjoint
+// fields.
+constexpr int kYokParts = 8;
+constexpr int kFinBlocks = 17 + kYokParts + 1;
 
 __global__ void __launch_bounds__(kFinThreads) k_finalize(FinalizeArgs a) {
   __shared__ Shared s;
@@ -376,13 +379,30 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(FinalizeArgs a) {
         m->ipt_median = med;
       }
     }
-  } else if (task == 17) {
+  } else if (task >= 17) {
     // H(history | site) = (1/N') [sum_s N'_s log2 N'_s - sum_P n_P log2 n_P], in units of h bits
-    const double sp = clog_sum(ar->pat_coc, kValDense, over, s.tag_begin[kTagPat], s.tag_begin[kTagPat + 1], 0, s);
-    const double ss =
-        clog_sum(ar->site_pat_coc, kValDense, over, s.tag_begin[kTagSitePat], s.tag_begin[kTagSitePat + 1], 0, s);
+    const int part = task - 17;
+    double v;
+    if (part < kYokParts) {
+      constexpr int kSlice = kValDense / kYokParts;
+      const u64 ob = part == 0 ? s.tag_begin[kTagPat] : 0, oe = part == 0 ? s.tag_begin[kTagPat + 1] : 0;
+      v = clog_sum(ar->pat_coc, (part + 1) * kSlice, over, ob, oe, 0, s, part * kSlice);
+    } else {
+      v = clog_sum(ar->site_pat_coc, kValDense, over, s.tag_begin[kTagSitePat], s.tag_begin[kTagSitePat + 1], 0, s);
+    }
+    __shared__ bool last;
     if (threadIdx.x == 0) {
-      const double y = st.npat ? (ss - sp) / ((double)st.npat * (double)a.history_len) : 0.0;
+      ar->yok_part[part] = v;
+      __threadfence();
+      last = atomicAdd(&ar->yok_done, 1u) == (u32)kYokParts;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+      __threadfence();
+      const volatile double* p = ar->yok_part;
+      double sp = 0.0;
+      for (int q = 0; q < kYokParts; ++q) sp += p[q];
+      const double y = st.npat ? (p[kYokParts] - sp) / ((double)st.npat * (double)a.history_len) : 0.0;
       m->yokota = y < 0.0 ? 0.0 : y;
     }
   } else if (threadIdx.x == 0) {

@@ -45,7 +45,8 @@ class _Metrics(ctypes.Structure):
 class _Config(ctypes.Structure):
     _fields_ = [("history_len", ctypes.c_uint32), ("cover_num", ctypes.c_uint32),
                 ("cover_den", ctypes.c_uint32), ("n_opcodes", ctypes.c_uint32),
-                ("space_mask", ctypes.c_uint32)]
+                ("space_mask", ctypes.c_uint32), ("byte_addresses", ctypes.c_uint32),
+                ("history_scope", ctypes.c_uint32)]
 
 
 class OracleInvalidInput(ValueError):
@@ -124,8 +125,12 @@ def _mem_bytes(mem):
 
 def compute(trace, history_len: int = 16, cover_num: int = 9, cover_den: int = 10,
             n_opcodes: int | None = None, space_mask: int = 0xF, want_hist: bool = True,
-            lib_path: str | None = None) -> dict:
-    """Metrics of one invocation (a synth.Trace or anything with the same fields)."""
+            lib_path: str | None = None, byte_addresses: int = 0, history_scope: int = 0) -> dict:
+    """Metrics of one invocation (a synth.Trace or anything with the same fields).
+
+    byte_addresses=1 counts every byte an access touches as an access of its
+    own; history_scope=1 keeps one branch history per (site, work-item).
+    """
     lib = _load() if lib_path is None else _bind(ctypes.CDLL(lib_path))
     mem, n_mem = _mem_bytes(trace.mem)
     br = _np(trace.br, np.uint64)
@@ -134,7 +139,7 @@ def compute(trace, history_len: int = 16, cover_num: int = 9, cover_den: int = 1
     run_off = _np(trace.run_off, np.uint64)
     run_len = _np(trace.run_len, np.uint64)
     nop = trace.n_opcodes if n_opcodes is None else n_opcodes
-    cfg = _Config(history_len, cover_num, cover_den, nop, space_mask)
+    cfg = _Config(history_len, cover_num, cover_den, nop, space_mask, byte_addresses, history_scope)
     out = _Metrics()
     hist = np.zeros(max(1, nop), dtype=np.uint64)
     rc = lib.aiwc_oracle_compute(mem.ctypes.data, n_mem, br.ctypes.data, br.size, ops.ctypes.data, ops.size,

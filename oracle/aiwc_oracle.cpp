@@ -21,6 +21,11 @@
 //   SIMD widths      -- closed forms (constant widths, two-value mix), brute force
 //   Yokota entropy   -- closed forms (constant branch 0, de Bruijn sequence 1), brute force;
 //                       parity unpinned for the normalisation, which is a reading
+//   byte addresses   -- equal to the start-address metrics of the events split into
+//                       one-byte accesses; closed forms (arrays read once); brute force
+//   per-work-item    -- equal to the per-site metrics when every site has one work-item;
+//     histories         closed forms (short per-work-item sequences predict nothing,
+//                       interleaved loops); brute force
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -46,6 +51,8 @@ struct OracleConfig {
   uint32_t cover_den;    // coverage fraction denominator (90%: 10)
   uint32_t n_opcodes;    // valid opcodes are 0..n_opcodes-1
   uint32_t space_mask;   // bit s set: address space s takes part in memory metrics
+  uint32_t byte_addresses;  // 0: an access is its start address; 1: every byte it touches
+  uint32_t history_scope;   // 0: one history per site; 1: one per (site, work-item)
 };
 
 struct OracleMetrics {
@@ -124,7 +131,8 @@ extern "C" {
 // Returns 0 on success, 1 when an input is invalid (an address outside the
 // 61-bit domain, an opcode that is neither < n_opcodes nor the barrier
 // marker, a history length outside 1..31, a coverage fraction outside
-// (0, 1], or a run that reaches past the opcode array).
+// (0, 1], a run that reaches past the opcode array, or -- with byte
+// addresses -- an access whose last byte lies outside the domain).
 int aiwc_oracle_compute(const uint8_t* mem, uint64_t n_mem,
                         const uint8_t* br, uint64_t n_br,
                         const uint16_t* ops, uint64_t n_ops,
@@ -133,6 +141,7 @@ int aiwc_oracle_compute(const uint8_t* mem, uint64_t n_mem,
                         const OracleConfig* cfg, OracleMetrics* out, uint64_t* opcode_hist) {
   std::memset(out, 0, sizeof(*out));
   if (cfg->history_len < 1 || cfg->history_len > 31) return 1;
+  if (cfg->byte_addresses > 1 || cfg->history_scope > 1) return 1;
   if (cfg->cover_den == 0 || cfg->cover_num == 0 || cfg->cover_num > cfg->cover_den) return 1;
   std::set<uint32_t> work_items;  // Table I "Work-items": every id seen in any stream
 
@@ -141,6 +150,11 @@ int aiwc_oracle_compute(const uint8_t* mem, uint64_t n_mem,
   // keeps equal numbers in different OpenCL address spaces apart. Reads and
   // writes are kept apart for the unique/total counts and combined for the
   // footprints and entropies ("stored separately and later combined", Sec. III).
+  // Address granularity (the paper records the address of each access and
+  // its size): by default an access counts once, at its start address. With
+  // byte_addresses every byte an access touches, addr .. addr + size - 1,
+  // counts as one access of its own, with the access's kind and space; an
+  // access of size 0 touches no byte (its work-item still counts).
   std::vector<uint64_t> all_keys, read_keys, write_keys;
   for (uint64_t i = 0; i < n_mem; ++i) {
     const uint8_t* e = mem + 16 * i;
@@ -148,14 +162,19 @@ int aiwc_oracle_compute(const uint8_t* mem, uint64_t n_mem,
     uint32_t wi;
     std::memcpy(&addr, e, 8);
     std::memcpy(&wi, e + 8, 4);
+    uint8_t size = e[12];
     uint8_t flags = e[13];
     work_items.insert(wi);
     if (addr >= kAddrLimit) return 1;
+    if (cfg->byte_addresses && size > 0 && addr + size - 1 >= kAddrLimit) return 1;
     uint32_t space = (flags >> 1) & 3u;
     if (!((cfg->space_mask >> space) & 1u)) continue;
-    uint64_t key = ((uint64_t)space << 61) | addr;
-    all_keys.push_back(key);
-    if (flags & 1u) write_keys.push_back(key); else read_keys.push_back(key);
+    const uint64_t touched = cfg->byte_addresses ? size : 1;
+    for (uint64_t b = 0; b < touched; ++b) {
+      uint64_t key = ((uint64_t)space << 61) | (addr + b);
+      all_keys.push_back(key);
+      if (flags & 1u) write_keys.push_back(key); else read_keys.push_back(key);
+    }
   }
   out->total_reads = read_keys.size();
   out->total_writes = write_keys.size();
@@ -199,6 +218,19 @@ int aiwc_oracle_compute(const uint8_t* mem, uint64_t n_mem,
   std::vector<uint64_t> site_counts;
   const uint32_t h = cfg->history_len;
   std::map<std::pair<uint32_t, uint64_t>, std::pair<uint64_t, uint64_t>> patterns;  // -> (taken, total)
+  // Outcome j of a history is predicted from the h outcomes before it in the
+  // same history (oldest in the high bit); the first h outcomes of a history
+  // have no full history and are skipped. Patterns are keyed by (site,
+  // history) in both scopes.
+  auto predict = [&](uint32_t site, const std::vector<uint8_t>& seq) {
+    for (size_t j = h; j < seq.size(); ++j) {
+      uint64_t hist = 0;
+      for (size_t k = j - h; k < j; ++k) hist = (hist << 1) | seq[k];
+      auto& tn = patterns[{site, hist}];
+      tn.first += seq[j];
+      tn.second += 1;
+    }
+  };
   for (auto& kv : per_site) {
     auto& seq = kv.second;
     site_counts.push_back(seq.size());
@@ -206,14 +238,17 @@ int aiwc_oracle_compute(const uint8_t* mem, uint64_t n_mem,
                      [](const std::pair<uint32_t, uint8_t>& a, const std::pair<uint32_t, uint8_t>& b) {
                        return a.first < b.first;
                      });
-    // Outcome j is predicted from the h outcomes before it (oldest in the
-    // high bit); the first h outcomes have no full history and are skipped.
-    for (size_t j = h; j < seq.size(); ++j) {
-      uint64_t hist = 0;
-      for (size_t k = j - h; k < j; ++k) hist = (hist << 1) | seq[k].second;
-      auto& tn = patterns[{kv.first, hist}];
-      tn.first += seq[j].second;
-      tn.second += 1;
+    if (cfg->history_scope == 0) {
+      // one history per site: its work-items' outcomes one after another
+      std::vector<uint8_t> outcomes;
+      for (auto& e : seq) outcomes.push_back(e.second);
+      predict(kv.first, outcomes);
+    } else {
+      // one history per (site, work-item): that work-item's outcomes at the
+      // site in program order (a per-thread history register)
+      std::map<uint32_t, std::vector<uint8_t>> per_wi;
+      for (auto& e : seq) per_wi[e.first].push_back(e.second);
+      for (auto& w : per_wi) predict(kv.first, w.second);
     }
   }
   out->branch_sites = site_counts.size();

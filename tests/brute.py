@@ -23,7 +23,7 @@ def decode(trace):
             addr = int.from_bytes(bytes(row[0:8]), "little")
             wi = int.from_bytes(bytes(row[8:12]), "little")
             flags = int(row[13])
-            mem.append((addr, wi, flags & 1, (flags >> 1) & 3))
+            mem.append((addr, wi, flags & 1, (flags >> 1) & 3, int(row[12])))
     br = []
     if trace.br is not None and trace.br.shape[0]:
         raw = trace.br.cpu().contiguous().numpy().view(np.uint32).reshape(-1, 2)
@@ -70,7 +70,8 @@ def _median(vals):
     return lo, hi, (lo + hi) / 2.0
 
 
-def metrics(trace, history_len=16, cover_num=9, cover_den=10, n_opcodes=None, space_mask=0xF):
+def metrics(trace, history_len=16, cover_num=9, cover_den=10, n_opcodes=None, space_mask=0xF,
+            byte_addresses=0, history_scope=0):
     mem, br, runs, ops = decode(trace)
     nop = trace.n_opcodes if n_opcodes is None else n_opcodes
     out = {}
@@ -78,13 +79,17 @@ def metrics(trace, history_len=16, cover_num=9, cover_den=10, n_opcodes=None, sp
 
     # memory
     keys, rw = [], []
-    for addr, wi, st, sp in mem:
+    for addr, wi, st, sp, size in mem:
         wis.append(wi)
         if addr >= ADDR_LIMIT:
             raise ValueError("address outside the 61-bit domain")
+        touched = [addr + b for b in range(size)] if byte_addresses else [addr]
+        if touched and touched[-1] >= ADDR_LIMIT:
+            raise ValueError("a touched byte outside the 61-bit domain")
         if (space_mask >> sp) & 1:
-            keys.append((sp, addr))
-            rw.append(st)
+            for a in touched:
+                keys.append((sp, a))
+                rw.append(st)
     N = len(keys)
     out["total_reads"] = sum(1 for s in rw if s == 0)
     out["total_writes"] = sum(1 for s in rw if s == 1)
@@ -108,13 +113,18 @@ def metrics(trace, history_len=16, cover_num=9, cover_den=10, n_opcodes=None, sp
         ent.append(math.fsum(terms) if N else 0.0)
     out["entropy"] = ent
 
-    # branches: position of each event in its site's (work-item, push order) sequence
+    # branches: position of each event in its history -- the site's (work-item,
+    # push order) sequence, or with history_scope=1 the (site, work-item)'s
+    # push-order sequence
     B = len(br)
     for _, wi, _ in br:
         wis.append(wi)
     pos = []
     for e, (s, w, _) in enumerate(br):
-        pos.append(sum(1 for f, (s2, w2, _) in enumerate(br) if s2 == s and (w2 < w or (w2 == w and f < e))))
+        if history_scope:
+            pos.append(sum(1 for f, (s2, w2, _) in enumerate(br) if s2 == s and w2 == w and f < e))
+        else:
+            pos.append(sum(1 for f, (s2, w2, _) in enumerate(br) if s2 == s and (w2 < w or (w2 == w and f < e))))
     sites = []
     for s, _, _ in br:
         if s not in sites:
@@ -123,9 +133,9 @@ def metrics(trace, history_len=16, cover_num=9, cover_den=10, n_opcodes=None, sp
     out["branch_cover"] = _cover([sum(1 for b in br if b[0] == s) for s in sites], cover_num, cover_den)
     out["branch_events"] = B
 
-    def outcome(site, p):
+    def outcome(site, wi, p):
         for e, b in enumerate(br):
-            if b[0] == site and pos[e] == p:
+            if b[0] == site and (not history_scope or b[1] == wi) and pos[e] == p:
                 return b[2]
         raise AssertionError
 
@@ -133,7 +143,7 @@ def metrics(trace, history_len=16, cover_num=9, cover_den=10, n_opcodes=None, sp
     pats = []  # (site, history tuple, outcome)
     for e, (s, w, t) in enumerate(br):
         if pos[e] >= h:
-            hist = tuple(outcome(s, pos[e] - h + k) for k in range(h))
+            hist = tuple(outcome(s, w, pos[e] - h + k) for k in range(h))
             pats.append(((s, hist), t))
     seen = []
     minsum = 0

@@ -11,8 +11,14 @@ BARRIER = -1
 
 def random_trace(seed: int, n_mem: int = 40, n_br: int = 40, n_wi: int = 4, n_runs: int = 6,
                  n_ops: int = 60, addr_pool: int = 12, n_sites: int = 3, n_opcodes: int = 5,
-                 spaces: int = 4, p_barrier: float = 0.15, addr_span_bits: int = 12) -> Trace:
-    """A tiny trace over small alphabets so that collisions are frequent."""
+                 spaces: int = 4, p_barrier: float = 0.15, addr_span_bits: int = 12,
+                 size_choices=None) -> Trace:
+    """A tiny trace over small alphabets so that collisions are frequent.
+
+    Accesses are 4 bytes wide unless `size_choices` is given; their sizes are
+    then drawn from it after every other draw (the rest of the trace is the
+    same as without it).
+    """
     rng = np.random.default_rng(seed)
     pool = rng.integers(0, 1 << addr_span_bits, size=addr_pool, dtype=np.int64)
     addr = pool[rng.integers(0, addr_pool, size=n_mem)]
@@ -30,18 +36,24 @@ def random_trace(seed: int, n_mem: int = 40, n_br: int = 40, n_wi: int = 4, n_ru
     run_off = np.array(bounds[:-1], dtype=np.int64)
     run_len = np.diff(np.array(bounds, dtype=np.int64))
     run_wi = rng.integers(0, n_wi, size=n_runs)
+    if size_choices is not None:
+        sizes = np.asarray(size_choices, dtype=np.int64)[rng.integers(0, len(size_choices), n_mem)]
+        raw = mem.view(torch.uint8).reshape(-1, 16).clone()
+        raw[:, 12] = torch.from_numpy(sizes.astype(np.uint8))
+        mem = raw.view(torch.int64).reshape(-1, 2)
     return Trace(f"rand{seed}", mem, br, torch.from_numpy(ops.astype(np.int16)),
                  torch.from_numpy(run_wi.astype(np.int64)), torch.from_numpy(run_off),
                  torch.from_numpy(run_len), n_opcodes=n_opcodes)
 
 
-def mem_only(addrs, stores=None, spaces=None, wis=None) -> Trace:
+def mem_only(addrs, stores=None, spaces=None, wis=None, sizes=None) -> Trace:
     n = len(addrs)
+    sz = torch.full((n,), 4, dtype=torch.int64) if sizes is None else torch.tensor(sizes, dtype=torch.int64)
     a = torch.tensor(addrs, dtype=torch.int64)
     st = torch.zeros(n, dtype=torch.int64) if stores is None else torch.tensor(stores, dtype=torch.int64)
     sp = torch.zeros(n, dtype=torch.int64) if spaces is None else torch.tensor(spaces, dtype=torch.int64)
     wi = torch.zeros(n, dtype=torch.int64) if wis is None else torch.tensor(wis, dtype=torch.int64)
-    return Trace("mem", pack_mem(a, wi, torch.full((n,), 4, dtype=torch.int64), st, sp))
+    return Trace("mem", pack_mem(a, wi, sz, st, sp))
 
 
 def branch_only(sites, wis, taken) -> Trace:

@@ -24,7 +24,15 @@ from tests.test_oracle_pins import GOLDEN, INT_FIELDS
 MUTATIONS = {
     "history_skips_one_more": ("for (size_t j = h; j < seq.size(); ++j)", "for (size_t j = h + 1; j < seq.size(); ++j)"),
     "history_in_push_order": ("std::stable_sort(seq.begin(), seq.end(),", "if (0) std::stable_sort(seq.begin(), seq.end(),"),
-    "no_space_tag": ("uint64_t key = ((uint64_t)space << 61) | addr;", "uint64_t key = addr;"),
+    "no_space_tag": ("uint64_t key = ((uint64_t)space << 61) | (addr + b);", "uint64_t key = addr + b;"),
+    "bytes_one_short": ("const uint64_t touched = cfg->byte_addresses ? size : 1;",
+                        "const uint64_t touched = cfg->byte_addresses ? (size ? size - 1 : 0) : 1;"),
+    "bytes_all_at_start": ("uint64_t key = ((uint64_t)space << 61) | (addr + b);",
+                           "uint64_t key = ((uint64_t)space << 61) | addr;"),
+    "per_wi_history_not_split": ("for (auto& e : seq) per_wi[e.first].push_back(e.second);",
+                                 "for (auto& e : seq) per_wi[0].push_back(e.second);"),
+    "per_wi_patterns_keyed_by_wi": ("for (auto& w : per_wi) predict(kv.first, w.second);",
+                                    "for (auto& w : per_wi) predict(kv.first ^ (w.first << 8), w.second);"),
     "skip_inner_off_by_one": ("while (j < n_acc && (all_keys[j] >> n) == g) ++j;",
                               "while (j < n_acc && (all_keys[j] >> (n + 1)) == (g >> 1)) ++j;"),
     "cover_strict": ("if ((unsigned __int128)den * cum >= (unsigned __int128)num * total) return k + 1;",
@@ -102,6 +110,30 @@ def _pins_pass(lib):
             o = comp(mem_only([(1 << 40) + (i << t) for i in range(1 << k) for _ in range(3)]))
             if max(abs(o["entropy"][n] - max(0, k - max(0, n - t))) for n in range(11)) > 1e-12:
                 return False
+        # byte addresses: brute force on random sizes, and the overlap hand example
+        for seed in range(12):
+            tr = random_trace(seed, n_mem=40, n_br=0, n_runs=1, n_ops=8, addr_pool=8, addr_span_bits=6,
+                              size_choices=[0, 1, 2, 4, 8])
+            o, b = comp(tr, byte_addresses=1), brute.metrics(tr, byte_addresses=1)
+            if any(o[f] != b[f] for f in INT_FIELDS):
+                return False
+            if max(abs(x - y) for x, y in zip(o["entropy"], b["entropy"])) > 1e-12:
+                return False
+        o = comp(mem_only([0, 2], sizes=[4, 4]), byte_addresses=1)
+        if (o["footprint"], o["total_reads"]) != (6, 8) or abs(o["entropy"][0] - 2.5) > 1e-15:
+            return False
+        # per-(site, work-item) histories: brute force and the interleaved-loop closed form
+        for seed in range(12):
+            tr = random_trace(seed, n_mem=0, n_br=60, n_wi=3, n_runs=1, n_ops=8, n_sites=2)
+            o, b = comp(tr, history_len=2, history_scope=1), brute.metrics(tr, history_len=2, history_scope=1)
+            if any(o[f] != b[f] for f in INT_FIELDS) or abs(o["yokota"] - b["yokota"]) > 1e-12:
+                return False
+        st = [7] * 120
+        wi = [j % 2 for j in range(120)]
+        tk = [int((j // 2) % 4 != 3) for j in range(120)]
+        o = comp(branch_only(st, wi, tk), history_len=3, history_scope=1)
+        if (o["branch_patterns"], o["branch_minsum"]) != (2 * (60 - 3), 0):
+            return False
     except (oracle.OracleInvalidInput, ValueError):  # a mutated oracle may also fail outright
         return False
     return True

@@ -329,3 +329,137 @@ def test_yokota_bounds_on_random_traces():
         tr = random_trace(seed, n_br=400, n_sites=4, n_wi=3)
         y = oracle.compute(tr, history_len=3)["yokota"]
         assert 0.0 <= y <= 1.0 + 1e-12
+
+
+# ---- address granularity: every byte an access touches (byte_addresses=1) ----
+
+def _split_into_bytes(tr):
+    """The same accesses as one-byte events, one per byte touched."""
+    raw = tr.mem.view(torch.uint8).reshape(-1, 16).numpy()
+    rows = []
+    for r in raw:
+        addr = int.from_bytes(bytes(r[0:8]), "little")
+        for b in range(int(r[12])):
+            q = r.copy()
+            q[0:8] = np.frombuffer((addr + b).to_bytes(8, "little"), dtype=np.uint8)
+            q[12] = 1
+            rows.append(q)
+    mem = torch.from_numpy(np.array(rows, dtype=np.uint8).reshape(-1)).view(torch.int64).reshape(-1, 2) \
+        if rows else torch.zeros((0, 2), dtype=torch.int64)
+    return synth.Trace("bytes", mem)
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_byte_addresses_match_brute_force(seed):
+    rng = np.random.default_rng(20_000 + seed)
+    tr = random_trace(seed, n_mem=int(rng.integers(0, 48)), n_br=0, n_runs=1, n_ops=8,
+                      addr_pool=int(rng.integers(1, 12)), addr_span_bits=int(rng.integers(1, 10)),
+                      size_choices=[0, 1, 2, 3, 4, 8, 16])
+    mask = int(rng.choice([0xF, 0x1, 0x6]))
+    o = oracle.compute(tr, space_mask=mask, byte_addresses=1)
+    b = brute.metrics(tr, space_mask=mask, byte_addresses=1)
+    _compare(o, b)
+
+
+@pytest.mark.parametrize("seed", range(20))
+def test_byte_addresses_equal_one_byte_events(seed):
+    """Expanding an access into its bytes is the start-address metric of one-byte events."""
+    tr = random_trace(seed, n_mem=200, n_br=0, n_runs=1, n_ops=8, addr_pool=30, addr_span_bits=8,
+                      size_choices=[1, 2, 4, 8, 12, 255])
+    a = oracle.compute(tr, byte_addresses=1)
+    s = oracle.compute(_split_into_bytes(tr), byte_addresses=0)
+    for f in ("total_reads", "total_writes", "footprint", "footprint_cover", "unique_reads", "unique_writes"):
+        assert a[f] == s[f], f
+    assert a["entropy"] == s["entropy"]
+
+
+@pytest.mark.parametrize("k", [0, 3, 8])
+def test_byte_addresses_float_array_closed_form(k):
+    """2^k float32 elements read once: 2^(k+2) bytes, H_n = k + 2 - n for n <= k + 2."""
+    base = 1 << 32
+    o = oracle.compute(mem_only([base + 4 * i for i in range(1 << k)]), byte_addresses=1)
+    nb = 1 << (k + 2)
+    assert (o["footprint"], o["total_reads"], o["unique_reads"]) == (nb, nb, nb)
+    assert o["footprint_cover"] == math.ceil(0.9 * nb - 1e-12)
+    for n in range(11):
+        assert abs(o["entropy"][n] - max(0, k + 2 - n)) < 1e-12, n
+
+
+def test_byte_addresses_overlap_hand_example():
+    # bytes 0..3 and 2..5: counts 1,1,2,2,1,1 over 8 accesses -> H_0 = 4*(3/8) + 2*(1/4)*2 = 2.5
+    o = oracle.compute(mem_only([0, 2], sizes=[4, 4]), byte_addresses=1)
+    assert (o["footprint"], o["total_reads"]) == (6, 8)
+    assert abs(o["entropy"][0] - 2.5) < 1e-15
+    # H_1: pairs {0,1}:2, {2,3}:4, {4,5}:2 -> 1.5 bits
+    assert abs(o["entropy"][1] - 1.5) < 1e-15
+    assert o["entropy"][3] == 0.0
+
+
+def test_byte_addresses_size_zero_and_domain():
+    o = oracle.compute(mem_only([64, 64], sizes=[0, 0], wis=[3, 5]), byte_addresses=1)
+    assert (o["footprint"], o["total_reads"], o["work_items"]) == (0, 0, 2)
+    edge = (1 << 61) - 2
+    assert oracle.compute(mem_only([edge], sizes=[4]))["footprint"] == 1
+    assert oracle.compute(mem_only([edge], sizes=[2]), byte_addresses=1)["footprint"] == 2
+    with pytest.raises(oracle.OracleInvalidInput):
+        oracle.compute(mem_only([edge], sizes=[4]), byte_addresses=1)
+    with pytest.raises(oracle.OracleInvalidInput):
+        oracle.compute(mem_only([1 << 61], sizes=[0]), byte_addresses=1)
+
+
+# ---- branch histories per (site, work-item) (history_scope=1) ----
+
+@pytest.mark.parametrize("seed", range(60))
+def test_per_work_item_histories_match_brute_force(seed):
+    rng = np.random.default_rng(30_000 + seed)
+    tr = random_trace(seed, n_mem=0, n_br=int(rng.integers(0, 80)), n_wi=int(rng.integers(1, 5)),
+                      n_runs=1, n_ops=8, n_sites=int(rng.integers(1, 4)))
+    h = int(rng.choice([1, 2, 3, 4]))
+    o = oracle.compute(tr, history_len=h, history_scope=1)
+    b = brute.metrics(tr, history_len=h, history_scope=1)
+    _compare(o, b)
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_per_work_item_histories_equal_per_site_with_one_work_item(seed):
+    tr = random_trace(seed, n_mem=0, n_br=300, n_wi=1, n_runs=1, n_ops=8, n_sites=4)
+    for h in (1, 3, 16):
+        a = oracle.compute(tr, history_len=h, history_scope=1)
+        b = oracle.compute(tr, history_len=h, history_scope=0)
+        for f in ("branch_patterns", "branch_minsum", "albe", "yokota", "branch_sites", "branch_cover"):
+            assert a[f] == b[f], (h, f)
+
+
+def test_per_work_item_short_sequences_predict_nothing():
+    """Two outcomes per (site, work-item), as in a kernel that branches twice per thread."""
+    n_wi, sites = 64, [0, 1]
+    st, wi, tk = [], [], []
+    for w in range(n_wi):
+        for s in sites:
+            for r in range(2):
+                st.append(s)
+                wi.append(w)
+                tk.append((w + r) % 2)
+    tr = branch_only(st, wi, tk)
+    o = oracle.compute(tr, history_len=2, history_scope=1)
+    assert (o["branch_patterns"], o["branch_minsum"], o["albe"], o["yokota"]) == (0, 0, 0.0, 0.0)
+    assert o["branch_sites"] == 2
+    assert oracle.compute(tr, history_len=2)["branch_patterns"] == 2 * (2 * n_wi - 2)
+
+
+@pytest.mark.parametrize("h", [1, 3, 5])
+def test_per_work_item_interleaved_loops_closed_form(h):
+    """Two work-items each run a period-P loop at one site, pushed interleaved.
+
+    With P = h + 1 every full per-work-item history fixes the next outcome, so
+    M = 0 and N' = 2 (L - h); one history per site would mix the two loops."""
+    L, P = 60, h + 1
+    st, wi, tk = [], [], []
+    for j in range(L):
+        for w in (0, 1):
+            st.append(7)
+            wi.append(w)
+            tk.append(int(j % P != P - 1))
+    o = oracle.compute(branch_only(st, wi, tk), history_len=h, history_scope=1)
+    assert (o["branch_patterns"], o["branch_minsum"]) == (2 * (L - h), 0)
+    assert o["albe"] == 0.0

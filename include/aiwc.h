@@ -104,6 +104,18 @@ typedef struct aiwc_config {
                              exact distributions and finalises once. Device memory then scales with the
                              largest partition; host memory holds the pushed events until compute.
                              Not for aiwc_compute_batch or server jobs. */
+  uint32_t byte_addresses;/* address granularity (the paper records each access's address and size
+                             but keys its memory metrics by address only): 0 = an access counts once,
+                             at its start address; 1 = every byte it touches, addr .. addr + size - 1,
+                             counts as one access of the same kind and space (size 0 touches none), so
+                             every memory metric counts bytes. A push then learns its byte count on the
+                             device before ingesting: one stream synchronisation per 2^22 events. An
+                             access whose last byte is outside the address domain is invalid data. */
+  uint32_t history_scope; /* whose branch history (Sec. III, Sec. V): 0 = one history per site, the
+                             work-items' outcomes one after another (ids ascending, program order
+                             inside each); 1 = one history per (site, work-item), that work-item's
+                             outcomes in program order. Patterns stay keyed by (site, history); the
+                             first history_len outcomes of every history predict nothing. */
 } aiwc_config;
 
 /* Fills the paper's defaults: history 16, 90% coverage, all address spaces,

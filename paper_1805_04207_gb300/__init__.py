@@ -27,7 +27,8 @@ class aiwc_config(ctypes.Structure):
                 ("cover_num", ctypes.c_uint32), ("cover_den", ctypes.c_uint32), ("n_opcodes", ctypes.c_uint32),
                 ("space_mask", ctypes.c_uint32), ("precision", ctypes.c_uint32), ("plan", ctypes.c_uint32),
                 ("max_work_items", ctypes.c_uint64), ("hbm_budget", ctypes.c_uint64),
-                ("table_slots", ctypes.c_uint64), ("partitions", ctypes.c_uint32)]
+                ("table_slots", ctypes.c_uint64), ("partitions", ctypes.c_uint32),
+                ("byte_addresses", ctypes.c_uint32), ("history_scope", ctypes.c_uint32)]
 
 
 class aiwc_server_config(ctypes.Structure):

@@ -187,6 +187,30 @@ struct MemIngestArgs {
 };
 void launch_mem_ingest(const MemIngestArgs& a, cudaStream_t s);
 
+// Byte-granular addresses: the one-byte accesses of a chunk of memory events
+// (addr + b for b < size, with the event's work-item, kind and space).
+constexpr u64 kExpandTile = 1024;         // events per tile
+constexpr u64 kExpandChunk = 1ull << 22;  // events per chunk (tile offsets for one chunk)
+struct ExpandArgs {
+  const void* ev{};   // 16-byte memory events (device, 16-byte aligned)
+  u64 n{};            // events in the chunk, <= kExpandChunk
+  u64* tile_off{};    // [ntiles] exclusive offsets of the tiles' one-byte events
+  u64* total{};       // bytes the chunk touches
+  u32* tile_sum{};    // [ntiles] bytes each tile touches
+  void* out{};        // out: the one-byte events, `*total` of them
+  u32* wi_bitmap{};
+  u64 max_wi{};
+  Arena* arena{};
+  int sm_count{};
+};
+size_t expand_meta_bytes();  // tile offsets, total and tile sums of one chunk
+// Counts the bytes of each tile (and checks the start addresses; a size-0
+// access marks its work-item here, since it yields no one-byte event), then
+// scans the tile counts into offsets and the chunk's total.
+void launch_expand_count(const ExpandArgs& a, cudaStream_t s);
+// Writes the one-byte events of every tile at its offset.
+void launch_expand_write(const ExpandArgs& a, cudaStream_t s);
+
 struct LevelArgs {
   const u32* gate{};   // run only when !gate || *gate == gate_want (device-side plan choice)
   u32 gate_want{};
@@ -253,6 +277,8 @@ struct WindowArgs {
   const u32* cur{};
   u64 n{};               // branch events
   u32 h{};               // history length
+  u32 gshift{32};        // one history per (word >> gshift): 32 = site, 1 = (site, work-item)
+  bool site_pred{true};  // per-site predicted counts from the site runs (one history per site)
   u64* patterns{};     // out: compacted pattern words
   TileSum* tiles{};      // site-level tile summaries
   u32 ntiles{};
@@ -276,6 +302,8 @@ struct PatternArgs {
   u64 over_cap{};
   Arena* arena{};
   int grid{};
+  bool site_level{};     // also the site runs of the pattern words (tile summaries at tiles + ntiles):
+                         // each site's predicted outcomes when histories are per (site, work-item)
 };
 void launch_pattern_runs(const PatternArgs& a, cudaStream_t s);
 

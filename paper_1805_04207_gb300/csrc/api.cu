@@ -51,12 +51,12 @@ inline u64 ntiles_of(u64 n) { return (n + kTile - 1) / kTile; }
 
 enum Stage {
   kStMemIngest, kStBrIngest, kStInstrRuns, kStMemSort, kStMemScatter, kStMemLevels, kStBrSort, kStWindows,
-  kStPatSort, kStPatRuns, kStRunSort, kStCombine, kStFinalize, kNumStages
+  kStPatSort, kStPatRuns, kStRunSort, kStCombine, kStFinalize, kStMemExpand, kNumStages
 };
 const char* const kStageNames[kNumStages] = {"mem_ingest", "branch_ingest", "instr_runs", "mem_sort",
                                              "mem_scatter", "mem_levels", "branch_sort", "windows",
                                              "pattern_sort", "pattern_runs", "run_sort", "run_combine",
-                                             "finalize"};
+                                             "finalize", "mem_expand"};
 
 }  // namespace
 
@@ -114,6 +114,9 @@ struct aiwc_handle {
   DevBuf mem_a, mem_b, br_a, br_b, pat_a, pat_b, rk_a, rk_b, run_sum, over_a, over_b, counts, bsums, tiles;
   DevBuf stage[2];
   DevBuf desc;
+  // byte-granular addresses: one chunk's one-byte events, its tile offsets and total
+  DevBuf exp, exp_meta;
+  u64* h_exp = nullptr;  // pinned copy of the chunk's total
   // superblock table of the hash plan (sized for the next invocation)
   DevBuf sbt, sbt_scan;
   u64 sbt_cap = 0;       // slots currently allocated
@@ -564,6 +567,34 @@ aiwc_status route_mem(aiwc_handle* h, const aiwc_mem_event* ev, size_t n, int on
   const aiwc_mem_event* e = nullptr;
   aiwc_status s = host_view(h, ev, n, on_device, &tmp, &e);
   if (s != AIWC_OK) return s;
+  std::vector<aiwc_mem_event> split;
+  if (h->cfg.byte_addresses) {
+    // a partition holds whole superblocks: an access whose bytes cross a
+    // superblock boundary travels as two accesses, one on each side
+    auto crosses = [](const aiwc_mem_event& x) {
+      return x.addr < AIWC_ADDR_LIMIT && x.size > 1 && (x.addr >> 11) != ((x.addr + x.size - 1) >> 11);
+    };
+    size_t cross = 0;
+    for (size_t i = 0; i < n; ++i) cross += crosses(e[i]) ? 1 : 0;
+    if (cross) {
+      split.reserve(n + cross);
+      for (size_t i = 0; i < n; ++i) {
+        if (!crosses(e[i])) {
+          split.push_back(e[i]);
+          continue;
+        }
+        const uint64_t b = ((e[i].addr >> 11) + 1) << 11;
+        aiwc_mem_event lo = e[i], hi = e[i];
+        lo.size = (uint8_t)(b - e[i].addr);
+        hi.addr = b;
+        hi.size = (uint8_t)(e[i].size - lo.size);
+        split.push_back(lo);
+        split.push_back(hi);
+      }
+      e = split.data();
+      n = split.size();
+    }
+  }
   const u32 P = (u32)h->parts.size();
   stable_partition(
       n, P,
@@ -708,6 +739,8 @@ aiwc_status aiwc_create(const aiwc_config* cfg, aiwc_handle** out) {
     return fail(nullptr, AIWC_EINVAL, "table_slots must be a power of two in [64, 2^30]");
   if (cfg->partitions > 256 || (cfg->partitions & (cfg->partitions - 1)))
     return fail(nullptr, AIWC_EINVAL, "partitions must be 0 or a power of two <= 256");
+  if (cfg->byte_addresses > 1 || cfg->history_scope > 1)
+    return fail(nullptr, AIWC_EINVAL, "byte_addresses and history_scope must be 0 or 1");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
     cudaGetLastError();
@@ -751,15 +784,13 @@ aiwc_status aiwc_create(const aiwc_config* cfg, aiwc_handle** out) {
   return AIWC_OK;
 }
 
-aiwc_status aiwc_push_mem(aiwc_handle* h, const aiwc_mem_event* ev, size_t n, int on_device) {
-  aiwc_status s = check_usable(h);
-  if (s != AIWC_OK) return s;
-  if (n == 0) return AIWC_OK;
-  if (!ev) return fail(h, AIWC_EINVAL, "null event pointer", false);
-  DeviceGuard g(h->cfg.device);
-  if (on_device && ((uintptr_t)ev & 15u))
-    return fail(h, AIWC_EINVAL, "device memory events must be 16-byte aligned", false);
-  if (routing(h)) return routed(h, [&] { return route_mem(h, ev, n, on_device); });
+}  // extern "C"
+
+namespace {
+
+// The ingest of n memory events (device or host) into the current invocation.
+aiwc_status push_mem_events(aiwc_handle* h, const aiwc_mem_event* ev, size_t n, int on_device) {
+  aiwc_status s;
   ENSURE(h->mem_a, (h->n_mem + n) * 8, true);
   if ((s = ensure_bitmap(h)) != AIWC_OK) return s;
   if (use_hash(h) && (s = ensure_table(h)) != AIWC_OK) return s;
@@ -796,6 +827,69 @@ aiwc_status aiwc_push_mem(aiwc_handle* h, const aiwc_mem_event* ev, size_t n, in
   }
   h->n_mem += n;
   return AIWC_OK;
+}
+
+// Byte-granular addresses: every byte an access touches becomes a one-byte
+// event of its own, ingested like any other event. The host reads each
+// chunk's byte count back before it sizes the one-byte events and the ingest.
+aiwc_status expand_events(aiwc_handle* h, const void* dev_ev, size_t n) {
+  aiwc_status s;
+  for (size_t c0 = 0; c0 < n; c0 += kExpandChunk) {
+    const size_t cnt = std::min<size_t>((size_t)kExpandChunk, n - c0);
+    ENSURE(h->exp_meta, expand_meta_bytes(), false);
+    if ((s = ensure_bitmap(h)) != AIWC_OK) return s;
+    if (!h->h_exp) CK(cudaMallocHost(&h->h_exp, sizeof(u64)));
+    ExpandArgs x;
+    x.ev = (const char*)dev_ev + 16 * c0;
+    x.n = cnt;
+    x.tile_off = (u64*)h->exp_meta.p;
+    x.total = x.tile_off + kExpandChunk / kExpandTile;
+    x.tile_sum = (u32*)(x.total + 1);
+    x.wi_bitmap = h->wi_bitmap;
+    x.max_wi = h->max_wi;
+    x.arena = h->arena;
+    x.sm_count = h->sm_count;
+    {
+      StageScope scope(h, kStMemExpand);
+      launch_expand_count(x, h->stream);
+    }
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h->h_exp, x.total, sizeof(u64), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));  // also retires the previous chunk's readers of h->exp
+    const u64 m = *h->h_exp;
+    if (m == 0) continue;
+    ENSURE(h->exp, m * 16, false);
+    x.out = h->exp.p;
+    {
+      StageScope scope(h, kStMemExpand);
+      launch_expand_write(x, h->stream);
+    }
+    CK(cudaGetLastError());
+    if ((s = push_mem_events(h, (const aiwc_mem_event*)h->exp.p, m, 1)) != AIWC_OK) return s;
+  }
+  return AIWC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+aiwc_status aiwc_push_mem(aiwc_handle* h, const aiwc_mem_event* ev, size_t n, int on_device) {
+  aiwc_status s = check_usable(h);
+  if (s != AIWC_OK) return s;
+  if (n == 0) return AIWC_OK;
+  if (!ev) return fail(h, AIWC_EINVAL, "null event pointer", false);
+  DeviceGuard g(h->cfg.device);
+  if (on_device && ((uintptr_t)ev & 15u))
+    return fail(h, AIWC_EINVAL, "device memory events must be 16-byte aligned", false);
+  if (routing(h)) return routed(h, [&] { return route_mem(h, ev, n, on_device); });
+  if (!h->cfg.byte_addresses) return push_mem_events(h, ev, n, on_device);
+  if (on_device) return expand_events(h, ev, n);
+  aiwc_status es = AIWC_OK;
+  s = staged_copy(h, ev, n * 16, 16, [&](void* p, size_t, size_t cnt) {
+    if (es == AIWC_OK) es = expand_events(h, p, cnt);
+  });
+  return s != AIWC_OK ? s : es;
 }
 
 aiwc_status aiwc_push_branch(aiwc_handle* h, const aiwc_branch_event* ev, size_t n, int on_device) {
@@ -1041,7 +1135,8 @@ aiwc_status prepare(aiwc_handle* h) {
   ENSURE(h->over_b, h->c_over_cap * 8, false);
   ENSURE(h->counts, sort_counts_words(nmax) * 4, false);
   ENSURE(h->bsums, sort_block_sums_words(nmax) * 4, false);
-  ENSURE(h->tiles, std::max<u64>((u64)kLevels * ntiles_of(n_mem), ntiles_of(n_br) + 1) * sizeof(TileSum), false);
+  // memory levels, or the branch site runs, or two levels of pattern runs
+  ENSURE(h->tiles, std::max<u64>((u64)kLevels * ntiles_of(n_mem), 2 * ntiles_of(n_br) + 1) * sizeof(TileSum), false);
   h->c_sites_cap = std::min<u64>(std::max<u64>(n_br, 1), kSiteListCap);
   ENSURE(h->sites, h->c_sites_cap * 16, false);
   // runs pushed in (work-item, push) order need no sort: checked before the
@@ -1124,7 +1219,9 @@ void enqueue_part1(aiwc_handle* h, cudaStream_t st, const Plan& p) {
   }
   StageScope sc(h, kStWindows);
   launch_site_heads(site_args(h, bsort), st);
-  if (p.gated) launch_persite_decide(h->arena, h->cfg.history_len, h->c_sites_cap, h->cfg.plan != 1, st);
+  if (p.gated)
+    launch_persite_decide(h->arena, h->cfg.history_len, h->c_sites_cap,
+                          h->cfg.plan != 1 && h->cfg.history_scope == 0, st);
 }
 
 aiwc_status enqueue_finalize(aiwc_handle* h, cudaStream_t st);
@@ -1216,6 +1313,8 @@ aiwc_status enqueue_part2(aiwc_handle* h, cudaStream_t st, const Plan& p) {
       wa.cur = bsort.cur;
       wa.n = n_br;
       wa.h = h->cfg.history_len;
+      wa.gshift = h->cfg.history_scope ? 1u : 32u;
+      wa.site_pred = h->cfg.history_scope == 0;
       wa.patterns = (u64*)h->pat_a.p;
       wa.tiles = (TileSum*)h->tiles.p;
       wa.ntiles = (u32)ntiles_of(n_br);
@@ -1227,7 +1326,7 @@ aiwc_status enqueue_part2(aiwc_handle* h, cudaStream_t st, const Plan& p) {
         StageScope sc(h, kStWindows);
         launch_branch_windows(wa, st);
         launch_runs_fixup(1, wa.tiles, wa.ntiles, nullptr, n_br, 1, over, over_cap, h->arena, st, gate, 0,
-                          h->cfg.history_len);
+                          h->cfg.history_scope ? 0u : h->cfg.history_len);
       }
       SortDesc ps = sort_desc(h, h->pat_a, h->pat_b, kSortPattern, &dst->n_patterns, &dst->pat_or, &dst->pat_and,
                               ~0ull, n_br);
@@ -1251,8 +1350,10 @@ aiwc_status enqueue_part2(aiwc_handle* h, cudaStream_t st, const Plan& p) {
       pa.over_cap = over_cap;
       pa.arena = h->arena;
       pa.grid = grid;
+      pa.site_level = h->cfg.history_scope != 0;
       launch_pattern_runs(pa, st);
-      launch_runs_fixup(2, pa.tiles, pa.ntiles, &dst->n_patterns, 0, 1, over, over_cap, h->arena, st, gate, 0);
+      launch_runs_fixup(2, pa.tiles, pa.ntiles, &dst->n_patterns, 0, pa.site_level ? 2 : 1, over, over_cap, h->arena,
+                        st, gate, 0);
     }
   }
   // instructions: chain each work-item's runs
@@ -1383,7 +1484,7 @@ aiwc_status reduce_current(aiwc_handle* h, bool defer_finalize) {
     CK(cudaStreamSynchronize(st));
     const DevState& hs = *h->h_state;
     p.per_site = h->cfg.history_len <= kSiteMaxHist && hs.br_site_max <= kSiteMaxLen &&
-                 hs.n_sites <= h->c_sites_cap && h->cfg.plan != 1;
+                 hs.n_sites <= h->c_sites_cap && h->cfg.plan != 1 && h->cfg.history_scope == 0;
   }
   return enqueue_part2(h, st, p);
 }
@@ -1621,7 +1722,8 @@ aiwc_status aiwc_destroy(aiwc_handle* h) {
   if (h->stream || h->copy_stream) cudaStreamSynchronize(h->stream);
   DevBuf* bufs[] = {&h->mem_a, &h->mem_b, &h->br_a, &h->br_b, &h->pat_a, &h->pat_b, &h->rk_a, &h->rk_b,
                     &h->run_sum, &h->over_a, &h->over_b, &h->counts, &h->bsums, &h->tiles, &h->stage[0],
-                    &h->stage[1], &h->desc, &h->sbt, &h->sbt_scan, &h->sites, &h->over_total};
+                    &h->stage[1], &h->desc, &h->sbt, &h->sbt_scan, &h->sites, &h->over_total, &h->exp,
+                    &h->exp_meta};
   for (DevBuf* b : bufs) release(h, *b);
   if (h->total) cudaFree(h->total);
   if (h->wi_bitmap) cudaFree(h->wi_bitmap);
@@ -1631,6 +1733,7 @@ aiwc_status aiwc_destroy(aiwc_handle* h) {
   if (h->h_result) cudaFreeHost(h->h_result);
   if (h->h_hist) cudaFreeHost(h->h_hist);
   if (h->h_state) cudaFreeHost(h->h_state);
+  if (h->h_exp) cudaFreeHost(h->h_exp);
   for (int i = 0; i < 2; ++i) {
     if (h->ev_copied[i]) cudaEventDestroy(h->ev_copied[i]);
     if (h->ev_free[i]) cudaEventDestroy(h->ev_free[i]);

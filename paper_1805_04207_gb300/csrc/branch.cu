@@ -28,10 +28,14 @@ __device__ __forceinline__ void emit_pattern_count(u64 n, u64* over, u64 cap, Ar
   if (n < (u64)kValDense) atomicAdd(&ar->pat_coc[n], 1ull);
   else overflow_append(over, cap, &ar->st, kTagPat, n);
 }
+__device__ __forceinline__ void emit_site_pred_count(u64 n, u64* over, u64 cap, Arena* ar) {
+  if (n == 0) return;
+  if (n < (u64)kValDense) atomicAdd(&ar->site_pat_coc[n], 1ull);
+  else overflow_append(over, cap, &ar->st, kTagSitePat, n);
+}
+// one history per site: a site with m outcomes predicts m - h of them
 __device__ __forceinline__ void emit_site_predicted(u64 m, u32 h, u64* over, u64 cap, Arena* ar) {
-  if (m <= h) return;
-  if (m - h < (u64)kValDense) atomicAdd(&ar->site_pat_coc[m - h], 1ull);
-  else overflow_append(over, cap, &ar->st, kTagSitePat, m - h);
+  if (m > h) emit_site_pred_count(m - h, over, cap, ar);
 }
 
 __global__ void __launch_bounds__(kBrThreads) k_branch_ingest(BranchIngestArgs a) {
@@ -474,6 +478,10 @@ constexpr int kHalo = 32;  // history lengths are at most 31
 // Reads the sorted branch words of one tile (plus the 32 words before it),
 // writes the compacted pattern words of outcomes with a full history, and
 // runs the per-site run lengths (site event counts) for the site metrics.
+// An outcome has a full history when the word h places before it belongs to
+// the same history: the same site, or with per-(site, work-item) histories
+// the same site and work-item (gshift 1; the sort keeps each work-item's
+// outcomes at a site together, in program order).
 __global__ void __launch_bounds__(kTileThreads) k_windows(WindowArgs a) {
   if (!gate_open(a.gate, a.gate_want)) return;
   __shared__ u64 tw[kHalo + kTile];
@@ -518,7 +526,7 @@ __global__ void __launch_bounds__(kTileThreads) k_windows(WindowArgs a) {
       bool ok = false;
       if (k < nvalid && j >= h) {
         const u64 older = tw[kHalo + t0 + k - (int)h];
-        ok = (older >> 32) == (key[k] >> 32);
+        ok = (older >> a.gshift) == (key[k] >> a.gshift);
       }
       if (ok) {
         const u64 pw = (key[k] & 0xFFFFFFFF00000001ull) | ((hist & hmask) << 1);
@@ -566,7 +574,7 @@ __global__ void __launch_bounds__(kTileThreads) k_windows(WindowArgs a) {
           if (len < (u64)kCocShared) atomicAdd(&site_coc[len], 1u);
           else if (len < (u64)kCocDense) atomicAdd(&a.arena->site_coc[len], 1ull);
           else overflow_append(a.over, a.over_cap, st, kTagSites, len);
-          emit_site_predicted(len, h, a.over, a.over_cap, a.arena);
+          if (a.site_pred) emit_site_predicted(len, h, a.over, a.over_cap, a.arena);
         },
         &a.tiles[tile], sh, pre_slot);
   }
@@ -617,6 +625,11 @@ __global__ void __launch_bounds__(kTileThreads) k_pattern_runs(PatternArgs a) {
           else emit_pattern_count(len, a.over, a.over_cap, a.arena);
         },
         &a.tiles[tile], sh, pre_slot);
+    if (a.site_level)
+      tile_runs<kTileItems>(
+          key, nvalid, pos0, prev, tile_n, [](u64 x) { return x >> 32; }, [](u64) { return 0ull; },
+          [&](u64 len, u64) { emit_site_pred_count(len, a.over, a.over_cap, a.arena); },
+          &a.tiles[a.ntiles + tile], sh, pre_slot);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < kPatSmem; i += kTileThreads)
@@ -631,7 +644,9 @@ __global__ void __launch_bounds__(kTileThreads) k_pattern_runs(PatternArgs a) {
 
 // Cross-tile fix-up: one block per level walks that level's tile summaries
 // in chunks with a segmented scan and emits every run that crosses a tile
-// boundary (and the final run), exactly once.
+// boundary (and the final run), exactly once. KIND 0: memory levels; 1: site
+// runs (h = 0: no per-site predicted counts); 2: level 0 pattern runs, level 1
+// site runs of the pattern words.
 template <int KIND>
 __global__ void __launch_bounds__(1024) k_fixup(const TileSum* tiles, u32 ntiles_max, const u64* n_dev, u64 n_host,
                                                 u64* over, u64 over_cap, Arena* arena, const u32* gate, u32 want,
@@ -653,11 +668,13 @@ __global__ void __launch_bounds__(1024) k_fixup(const TileSum* tiles, u32 ntiles
     } else if (KIND == 1) {
       if (len < (u64)kCocDense) atomicAdd(&arena->site_coc[len], 1ull);
       else overflow_append(over, over_cap, st, kTagSites, len);
-      emit_site_predicted(len, h, over, over_cap, arena);
-    } else {
+      if (h) emit_site_predicted(len, h, over, over_cap, arena);
+    } else if (level == 0) {
       msum += umin64(wsum, len - wsum);
       nsum += len;
       emit_pattern_count(len, over, over_cap, arena);
+    } else {
+      emit_site_pred_count(len, over, over_cap, arena);
     }
   };
   for (u32 c0 = 0; c0 < ntiles; c0 += blockDim.x) {

@@ -180,6 +180,144 @@ __global__ void __launch_bounds__(kIngestThreads, HASH ? 4 : 3) k_mem_ingest(Mem
   }
 }
 
+// Byte-granular addresses. A tile of kExpandTile events: k_expand_count sums
+// its sizes, k_expand_scan turns the tile sums into offsets, k_expand_write
+// stages the tile in shared memory with per-event offsets (each thread scans
+// its own kExpItems consecutive events) and then writes the tile's one-byte
+// events in order, consecutive threads writing consecutive 16-byte records;
+// a thread finds the event of output q by binary search over the offsets.
+constexpr int kExpThreads = 256;
+constexpr int kExpItems = (int)kExpandTile / kExpThreads;
+
+__global__ void __launch_bounds__(kExpThreads) k_expand_count(ExpandArgs a) {
+  __shared__ u32 red32[32];
+  DevState* st = &a.arena->st;
+  const uint4* ev = reinterpret_cast<const uint4*>(a.ev);
+  const u32 ntiles = (u32)((a.n + kExpandTile - 1) / kExpandTile);
+  u32 err = 0u, wmin = 0xFFFFFFFFu, wmax = 0u;
+  for (u32 tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    u32 sum = 0u;
+#pragma unroll
+    for (int k = 0; k < kExpItems; ++k) {
+      const u64 i = (u64)tile * kExpandTile + (u64)k * kExpThreads + threadIdx.x;
+      const bool valid = i < a.n;
+      const uint4 e = valid ? __ldg(ev + i) : make_uint4(0u, 0u, 0u, 0u);
+      const u32 size = e.w & 0xFFu;
+      sum += size;
+      if (valid && (e.y >> 29)) err |= kErrAddr;  // start address outside the 61-bit domain
+      const bool none = valid && size == 0u;    // touches no byte; its work-item still counts
+      mark_work_items(a.wi_bitmap, a.max_wi, e.z, none, &err);
+      if (none && (u64)e.z < a.max_wi) {
+        wmin = min(wmin, e.z);
+        wmax = max(wmax, e.z);
+      }
+    }
+    sum = block_reduce(sum, OpAdd(), 0u, red32);
+    if (threadIdx.x == 0) a.tile_sum[tile] = sum;
+  }
+  err = block_reduce(err, OpOr(), 0u, red32);
+  wmin = block_reduce(wmin, OpMin(), 0xFFFFFFFFu, red32);
+  wmax = block_reduce(wmax, OpMax(), 0u, red32);
+  if (threadIdx.x == 0) {
+    if (err) atomicOr(&st->err, err);
+    if (wmin <= wmax) {
+      atomicMin(&st->wi_min, wmin);
+      atomicMax(&st->wi_max, wmax);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_expand_scan(ExpandArgs a) {
+  __shared__ u64 wsum[32];
+  __shared__ u64 s_carry;
+  const u32 ntiles = (u32)((a.n + kExpandTile - 1) / kExpandTile);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) s_carry = 0ull;
+  __syncthreads();
+  for (u32 c0 = 0; c0 < ntiles; c0 += 1024) {
+    const u32 t = c0 + threadIdx.x;
+    const u64 v = t < ntiles ? (u64)a.tile_sum[t] : 0ull;
+    u64 x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const u64 y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      u64 s = wsum[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const u64 y = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= o) s += y;
+      }
+      wsum[lane] = s;
+    }
+    __syncthreads();
+    if (t < ntiles) a.tile_off[t] = s_carry + (w ? wsum[w - 1] : 0ull) + x - v;
+    __syncthreads();
+    if (threadIdx.x == 0) s_carry += wsum[31];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *a.total = s_carry;
+}
+
+__global__ void __launch_bounds__(kExpThreads) k_expand_write(ExpandArgs a) {
+  __shared__ uint4 s_ev[kExpandTile];
+  __shared__ u32 s_off[kExpandTile + 1];
+  __shared__ u32 s_wsum[kExpThreads / 32];
+  const uint4* ev = reinterpret_cast<const uint4*>(a.ev);
+  uint4* out = reinterpret_cast<uint4*>(a.out);
+  const u32 ntiles = (u32)((a.n + kExpandTile - 1) / kExpandTile);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (u32 tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const u64 base = (u64)tile * kExpandTile;
+    u32 sz[kExpItems];
+    u32 mine = 0u;
+#pragma unroll
+    for (int k = 0; k < kExpItems; ++k) {
+      const u32 j = threadIdx.x * kExpItems + k;
+      const uint4 e = base + j < a.n ? __ldg(ev + base + j) : make_uint4(0u, 0u, 0u, 0u);
+      s_ev[j] = e;
+      sz[k] = e.w & 0xFFu;
+      mine += sz[k];
+    }
+    u32 x = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const u32 y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_wsum[w] = x;
+    __syncthreads();
+    u32 run = x - mine;
+    for (int q = 0; q < w; ++q) run += s_wsum[q];
+#pragma unroll
+    for (int k = 0; k < kExpItems; ++k) {
+      s_off[threadIdx.x * kExpItems + k] = run;
+      run += sz[k];
+    }
+    if (threadIdx.x == kExpThreads - 1) s_off[kExpandTile] = run;
+    __syncthreads();
+    const u32 T = s_off[kExpandTile];
+    const u64 o0 = a.tile_off[tile];
+    for (u32 q = threadIdx.x; q < T; q += kExpThreads) {
+      // the last event whose offset is <= q; it touches at least one byte
+      u32 lo = 0u, hi = (u32)kExpandTile - 1u;
+      while (lo < hi) {
+        const u32 mid = (lo + hi + 1u) >> 1;
+        if (s_off[mid] <= q) lo = mid;
+        else hi = mid - 1u;
+      }
+      const uint4 e = s_ev[lo];
+      const u64 addr = ((u64)e.x | ((u64)e.y << 32)) + (u64)(q - s_off[lo]);
+      out[o0 + q] = make_uint4((u32)addr, (u32)(addr >> 32), e.z, (e.w & 0xFFFFFF00u) | 1u);
+    }
+    __syncthreads();  // the tile's staging is refilled next
+  }
+}
+
 constexpr int kLvThreads = kTileThreads;
 constexpr int kLvItems = kTileItems;
 
@@ -287,6 +425,28 @@ void launch_mem_ingest(const MemIngestArgs& a, cudaStream_t s) {
     else k_mem_ingest<false, false, false><<<grid(t.n), kIngestThreads, 0, s>>>(t);
     count_launches(1);
   }
+}
+
+size_t expand_meta_bytes() {
+  const size_t nt = (size_t)(kExpandChunk / kExpandTile);
+  return nt * 8 + 8 + nt * 4;
+}
+
+void launch_expand_count(const ExpandArgs& a, cudaStream_t s) {
+  if (a.n == 0) return;
+  const u64 ntiles = (a.n + kExpandTile - 1) / kExpandTile;
+  const unsigned g = (unsigned)std::min<u64>(ntiles, (u64)a.sm_count * 8);
+  k_expand_count<<<g, kExpThreads, 0, s>>>(a);
+  k_expand_scan<<<1, 1024, 0, s>>>(a);
+  count_launches(2);
+}
+
+void launch_expand_write(const ExpandArgs& a, cudaStream_t s) {
+  if (a.n == 0) return;
+  const u64 ntiles = (a.n + kExpandTile - 1) / kExpandTile;
+  const unsigned g = (unsigned)std::min<u64>(ntiles, (u64)a.sm_count * 8);
+  k_expand_write<<<g, kExpThreads, 0, s>>>(a);
+  count_launches(1);
 }
 
 void launch_mem_levels(const LevelArgs& a, cudaStream_t s) {

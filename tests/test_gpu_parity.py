@@ -449,3 +449,129 @@ def test_partitioned_errors(P):
         P.compute_batch([a, b])
     a.close()
     b.close()
+
+
+# ---- byte-granular addresses (byte_addresses=1) ----
+
+@pytest.mark.parametrize("seed", range(12))
+def test_byte_addresses_random(P, seed):
+    """Random sizes (0..255), overlapping and unaligned accesses, both memory
+    plans, device and host pushes, in one and several pushes."""
+    rng = np.random.default_rng(40_000 + seed)
+    tr = random_trace(seed, n_mem=int(rng.integers(1, 3000)), n_br=int(rng.integers(0, 200)),
+                      n_wi=int(rng.integers(1, 9)), addr_pool=int(rng.integers(1, 400)),
+                      addr_span_bits=int(rng.integers(4, 40)), size_choices=[0, 1, 2, 3, 4, 8, 16, 33, 255])
+    mask = int(rng.choice([0xF, 0x1, 0x6]))
+    o = oracle.compute(tr, space_mask=mask, byte_addresses=1)
+    g = run_gpu(P, tr, on_device=bool(seed % 2), split=1 + seed % 3, space_mask=mask, plan=seed % 3,
+                byte_addresses=1)
+    assert_parity(g, o)
+
+
+@pytest.mark.parametrize("on_device", [True, False])
+def test_byte_addresses_several_chunks(P, on_device):
+    """More events than one expansion chunk (2^22) and one host staging buffer."""
+    n = (1 << 22) + 4099
+    rng = np.random.default_rng(5)
+    addr = (1 << 34) + 4 * rng.integers(0, 1 << 22, n) + rng.integers(0, 4, n)
+    sizes = rng.choice([1, 2, 4, 8], n)
+    from synth import pack_mem, Trace
+    mem = pack_mem(torch.from_numpy(addr), torch.from_numpy(np.arange(n) // 256), torch.from_numpy(sizes),
+                   torch.from_numpy(rng.integers(0, 2, n)), torch.zeros(n, dtype=torch.int64))
+    tr = Trace("bytes", mem)
+    o = oracle.compute(tr, byte_addresses=1)
+    assert_parity(run_gpu(P, tr, on_device=on_device, byte_addresses=1), o)
+
+
+def test_byte_addresses_large_shapes(P):
+    tr = synth.large(seed=11, n_mem=500_001, n_br=0, n_wi=64, per_wi=64, zipf_distinct=1 << 16)
+    for plan in (0, 1):
+        assert_parity(run_gpu(P, tr, plan=plan, byte_addresses=1), oracle.compute(tr, byte_addresses=1))
+
+
+def test_byte_addresses_edge_cases(P):
+    # accesses of size 0 touch nothing but count their work-items
+    tr = mem_only([64, 64, 4096], sizes=[0, 0, 0], wis=[3, 5, 9])
+    g = run_gpu(P, tr, byte_addresses=1)
+    assert (g["footprint"], g["total_reads"], g["work_items"]) == (0, 0, 3)
+    assert_parity(g, oracle.compute(tr, byte_addresses=1))
+    # the last byte of the domain is valid; one past it is invalid data
+    edge = (1 << 61) - 2
+    tr = mem_only([edge, 5], sizes=[2, 1])
+    assert_parity(run_gpu(P, tr, byte_addresses=1), oracle.compute(tr, byte_addresses=1))
+    with P.Characterizer(byte_addresses=1) as c:
+        c.push_mem(mem_only([edge], sizes=[4]).mem.cuda())
+        with pytest.raises(P.AiwcError) as ei:
+            c.compute()
+        assert ei.value.status == P.AIWC_EINVAL
+        # the handle is reset for the next invocation
+        c.push_mem(mem_only([8], sizes=[4]).mem.cuda())
+        assert c.compute()["footprint"] == 4
+
+
+@pytest.mark.parametrize("partitions", [2, 16])
+def test_byte_addresses_partitioned(P, partitions):
+    """Accesses crossing a superblock boundary are split between partitions."""
+    rng = np.random.default_rng(9)
+    n = 20_000
+    addr = (rng.integers(0, 64, n) << 11) - rng.integers(0, 200, n) + (1 << 30)
+    from synth import pack_mem, Trace
+    mem = pack_mem(torch.from_numpy(addr), torch.from_numpy(rng.integers(0, 100, n)),
+                   torch.from_numpy(rng.integers(0, 256, n)), torch.from_numpy(rng.integers(0, 2, n)),
+                   torch.from_numpy(rng.integers(0, 2, n)))
+    tr = Trace("cross", mem)
+    g = _run_partitioned(P, tr, partitions, byte_addresses=1)
+    assert_parity(g, oracle.compute(tr, byte_addresses=1))
+
+
+# ---- branch histories per (site, work-item) (history_scope=1) ----
+
+@pytest.mark.parametrize("seed", range(12))
+def test_history_scope_random(P, seed):
+    rng = np.random.default_rng(50_000 + seed)
+    tr = random_trace(seed, n_mem=int(rng.integers(0, 100)), n_br=int(rng.integers(1, 3000)),
+                      n_wi=int(rng.integers(1, 12)), n_sites=int(rng.integers(1, 20)))
+    h = int(rng.choice([1, 2, 3, 5, 16]))
+    o = oracle.compute(tr, history_len=h, history_scope=1)
+    g = run_gpu(P, tr, on_device=bool(seed % 2), split=1 + seed % 3, history_len=h, history_scope=1,
+                plan=seed % 3)
+    assert_parity(g, o)
+
+
+@pytest.mark.parametrize("n,n_sites,wi_sorted,h", [
+    ((1 << 16) + 3, 4096, True, 3),        # site counting sort, then the global path
+    (1_100_000 + 77, 4000, True, 2),
+    (300_001, 50, False, 4),               # work-items out of order: radix sort
+    (200_000, 5000, True, 1),              # site ids >= 4096: radix sort
+])
+def test_history_scope_sort_paths(P, n, n_sites, wi_sorted, h):
+    tr = _site_trace(11 + n_sites, n, n_sites, wi_sorted)
+    for split in (1, 3):
+        assert_parity(run_gpu(P, tr, split=split, history_len=h, history_scope=1),
+                      oracle.compute(tr, history_len=h, history_scope=1))
+
+
+def test_history_scope_large_shape(P):
+    tr = synth.large(seed=12, n_mem=10_000, n_br=1_000_003, n_wi=1000, per_wi=1001, zipf_distinct=1 << 12)
+    for h in (2, 16):
+        assert_parity(run_gpu(P, tr, history_len=h, history_scope=1),
+                      oracle.compute(tr, history_len=h, history_scope=1))
+
+
+def test_history_scope_batched_and_partitioned(P):
+    from paper_1805_04207_gb300.api import compute_batch, push_trace
+    traces = [_site_trace(3, 70_000, 300, True), random_trace(4, n_br=5000, n_wi=30, n_sites=40),
+              synth.tiny()]
+    expect = [oracle.compute(t, history_len=3, history_scope=1) for t in traces]
+    chars = [P.Characterizer(n_opcodes=t.n_opcodes, history_len=3, history_scope=1) for t in traces]
+    try:
+        for _ in range(2):
+            for c, t in zip(chars, traces):
+                push_trace(c, t.to("cuda"))
+            for g, o in zip(compute_batch(chars), expect):
+                assert_parity(g, o)
+    finally:
+        for c in chars:
+            c.close()
+    for t, o in zip(traces, expect):
+        assert_parity(_run_partitioned(P, t, 8, history_len=3, history_scope=1), o)

@@ -34,12 +34,13 @@ WORKLOAD = ("large invocation: 2^28 memory events (stencil 256^3 + tiled SGEMM 2
             "2^26 branch events over 4096 sites, 2^30 opcodes over 256 ids")
 # Algorithmic bytes per unit (read once): 16 B per memory event, 8 B per
 # branch event, 2 B per opcode; plus 16 B per distinct address and 8 B per
-# history pattern for the run tables the method must form.
+# history pattern for the run tables the method must form. A sort stage is
+# credited with one read and one write of each 8-byte key it orders.
 ALG_BYTES = {"mem_event": 16, "branch_event": 8, "opcode": 2, "distinct_key": 16, "pattern": 8}
 KERNEL_FILES = {"mem_ingest": "mem.cu", "branch_ingest": "branch.cu", "instr_runs": "instr.cu", "mem_sort": "sort.cu",
                 "mem_scatter": "mem_hash.cu", "mem_levels": "mem_hash.cu", "branch_sort": "sort.cu", "windows": "branch.cu", "pattern_sort": "sort.cu",
                 "pattern_runs": "branch.cu", "run_sort": "sort.cu", "run_combine": "instr.cu",
-                "finalize": "finalize.cu"}
+                "finalize": "finalize.cu", "mem_expand": "mem.cu"}
 
 
 def parse():
@@ -57,7 +58,30 @@ def parse():
                          "FP32-compensated vs FP64 entropies")
     ap.add_argument("--jobs", type=int, default=100, help="serving: number of jobs")
     ap.add_argument("--partitions", type=int, default=8, help="partitioned: number of partitions")
+    ap.add_argument("--byte-addresses", action="store_true",
+                    help="large: every byte an access touches is an access (about 5 one-byte accesses per event)")
+    ap.add_argument("--history-scope", type=int, default=0, choices=[0, 1],
+                    help="large: 1 = one branch history per (site, work-item)")
     return ap.parse_args()
+
+
+def options(args) -> dict:
+    """Handle options of the large workload's variants."""
+    o = {}
+    if args.byte_addresses:
+        o["byte_addresses"] = 1
+    if args.history_scope:
+        o["history_scope"] = 1
+    return o
+
+
+def workload_name(args) -> str:
+    w = WORKLOAD
+    if args.byte_addresses:
+        w += "; byte-granular addresses (every byte an access touches is an access)"
+    if args.history_scope:
+        w += "; branch histories per (site, work-item)"
+    return w
 
 
 class ClockSampler:
@@ -141,16 +165,19 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def cpu_baseline(scale_shift: int):
+def cpu_baseline(scale_shift: int, opts=None):
     """The oracle, as it stands, on a bounded sample of the same workload."""
     import oracle
     import synth
+    opts = opts or {}
+    if opts.get("byte_addresses"):
+        scale_shift += 3  # about five one-byte accesses per event
     n_mem = 1 << (26 - scale_shift)
     n_br = 1 << (24 - scale_shift)
     n_wi = max(1, 1 << (18 - scale_shift))
     tr = synth.large(seed=0, n_mem=n_mem, n_br=n_br, n_wi=n_wi, per_wi=1024, zipf_distinct=1 << (24 - scale_shift))
     t0 = time.perf_counter()
-    oracle.compute(tr)
+    oracle.compute(tr, **opts)
     dt = time.perf_counter() - t0
     return {"value": n_mem / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"large-shaped sample: {n_mem} memory, {n_br} branch, {n_wi * 1024} opcodes "
@@ -165,16 +192,16 @@ def run_reference(args, rank, world):
     shift = args.scale
     vals = []
     for _ in range(min(args.warmup, 1)):
-        cpu_baseline(shift + 3)
+        cpu_baseline(shift + 3, options(args))
     for _ in range(min(args.steps, 3)):
-        b, dt = cpu_baseline(shift + 3)
+        b, dt = cpu_baseline(shift + 3, options(args))
         vals.append(b["value"])
     v = statistics.median(vals)
     b["value"] = v
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64+f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "reference_sample": b["sample"]},
+            "config": {"workload": workload_name(args), "reference_sample": b["sample"]},
             "cpu_baseline": b, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -430,7 +457,8 @@ def main():
     n_ops = tr.n_ops
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
-    c = P.Characterizer(device=local, stream=stream, n_opcodes=tr.n_opcodes)
+    opts = options(args)
+    c = P.Characterizer(device=local, stream=stream, n_opcodes=tr.n_opcodes, **opts)
 
     def step():
         c.push_mem(tr.mem)
@@ -466,10 +494,14 @@ def main():
     per_step = {k: v / args.steps for k, v in stage_tot.items()}
     D = out["footprint"]
     Bp = out["branch_patterns"]
-    alg = {"mem_ingest": ALG_BYTES["mem_event"] * n_mem, "branch_ingest": ALG_BYTES["branch_event"] * n_br,
+    # with byte-granular addresses the ingest reads one 16-byte event per byte touched
+    n_acc = out["total_reads"] + out["total_writes"] if opts.get("byte_addresses") else n_mem
+    alg = {"mem_ingest": ALG_BYTES["mem_event"] * n_acc, "branch_ingest": ALG_BYTES["branch_event"] * n_br,
+           "mem_expand": ALG_BYTES["mem_event"] * (n_mem + n_acc),
            "instr_runs": ALG_BYTES["opcode"] * n_ops,
-           "mem_sort": 0, "mem_scatter": 0, "mem_levels": ALG_BYTES["distinct_key"] * D, "branch_sort": 0,
-           "windows": ALG_BYTES["pattern"] * Bp, "pattern_sort": 0, "pattern_runs": 0, "run_sort": 0,
+           "mem_sort": 16 * n_acc, "mem_scatter": 0, "mem_levels": ALG_BYTES["distinct_key"] * D,
+           "branch_sort": 16 * n_br, "windows": ALG_BYTES["pattern"] * Bp, "pattern_sort": 16 * Bp,
+           "pattern_runs": 0, "run_sort": 16 * tr.run_wi.numel(),
            "run_combine": 0, "finalize": 0}
     dom = max(per_step, key=per_step.get)
     dom_ms = per_step[dom]
@@ -510,15 +542,16 @@ def main():
 
     base = None
     if rank == 0 and not args.no_cpu_baseline:
-        base, _ = cpu_baseline(s)
+        base, _ = cpu_baseline(s, opts)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": max(3, args.warmup), "ms_per_step": round(ms_max / args.steps, 4),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64+f64",
                 "data": "synthetic", "impl": "ours",
-                "config": {"workload": WORKLOAD, "seed": "rank", "inputs": "device-resident, 6.98 GB > L2 (no flush)",
-                           "parallelism": f"replicas x{world}", "scale_shift": s},
+                "config": {"workload": workload_name(args), "seed": "rank",
+                           "inputs": "device-resident, 6.98 GB > L2 (no flush)",
+                           "parallelism": f"replicas x{world}", "scale_shift": s, **opts},
                 "roofline": roof,
                 "roofline_step": {"bound": "hbm", "achieved": round(step_ach, 1), "peak": hbm, "unit": "GB/s",
                                   "frac": round(step_ach / hbm, 4), "alg_bytes_per_step": step_alg},

@@ -324,6 +324,7 @@ struct SiteArgs {
   Arena* arena{};
   int grid{};
   const uint8_t* outcomes{};  // per-site path: outcome bytes sorted by site instead of the words
+  bool per_wi{};       // one history per (site, work-item): needs the words (outcomes == nullptr)
 };
 // Stable counting sort of the branch words by site, for site ids below
 // kCsSites when work-item ids arrived in non-decreasing order (the site alone

@@ -1219,9 +1219,7 @@ void enqueue_part1(aiwc_handle* h, cudaStream_t st, const Plan& p) {
   }
   StageScope sc(h, kStWindows);
   launch_site_heads(site_args(h, bsort), st);
-  if (p.gated)
-    launch_persite_decide(h->arena, h->cfg.history_len, h->c_sites_cap,
-                          h->cfg.plan != 1 && h->cfg.history_scope == 0, st);
+  if (p.gated) launch_persite_decide(h->arena, h->cfg.history_len, h->c_sites_cap, h->cfg.plan != 1, st);
 }
 
 aiwc_status enqueue_finalize(aiwc_handle* h, cudaStream_t st);
@@ -1293,7 +1291,7 @@ aiwc_status enqueue_part2(aiwc_handle* h, cudaStream_t st, const Plan& p) {
       // the per-site path needs only the outcome bits: one byte per event
       StageScope sc(h, kStBrSort);
       SiteSortArgs ss = site_sort_args(h);
-      if (p.per_site) ss.dst8 = (uint8_t*)h->br_b.p;
+      if (p.per_site && !h->cfg.history_scope) ss.dst8 = (uint8_t*)h->br_b.p;
       launch_site_sort_scatter(ss, st);
     }
     if (p.gated || p.per_site) {
@@ -1301,7 +1299,8 @@ aiwc_status enqueue_part2(aiwc_handle* h, cudaStream_t st, const Plan& p) {
       SiteArgs sa = site_args(h, bsort);
       sa.gate = gate;
       sa.gate_want = 1;
-      if (p.site_sort) sa.outcomes = (const uint8_t*)h->br_b.p;
+      if (p.site_sort && !h->cfg.history_scope) sa.outcomes = (const uint8_t*)h->br_b.p;
+      sa.per_wi = h->cfg.history_scope != 0;
       launch_site_patterns(sa, st);
     }
     if (p.gated || !p.per_site) {
@@ -1484,7 +1483,7 @@ aiwc_status reduce_current(aiwc_handle* h, bool defer_finalize) {
     CK(cudaStreamSynchronize(st));
     const DevState& hs = *h->h_state;
     p.per_site = h->cfg.history_len <= kSiteMaxHist && hs.br_site_max <= kSiteMaxLen &&
-                 hs.n_sites <= h->c_sites_cap && h->cfg.plan != 1 && h->cfg.history_scope == 0;
+                 hs.n_sites <= h->c_sites_cap && h->cfg.plan != 1;
   }
   return enqueue_part2(h, st, p);
 }

@@ -378,18 +378,23 @@ constexpr int kSpBinsLog = 15;
 constexpr int kSpBitWords = (int)((kSiteMaxLen + 32) / 32) + 2;
 
 // One block per site: its outcomes become a bit string in shared memory; for
-// every outcome with h predecessors, the packed counter of its history gets
+// every outcome with h predecessors in its history, the packed counter of its
+// history gets
 // +1 total (low 16 bits) and +outcome taken (high 16 bits). Histories are
 // binned 2^15 at a time (more passes for h > 15). The first increment of a
 // bin lists it, so a pass visits and clears only the bins it used. M and N'
 // follow from the bins. Any fixed bijection of the h-bit window names the
 // pattern equally well; here bit k of the pattern is the outcome k+1 places
-// after the oldest.
+// after the oldest. With one history per (site, work-item) a second bit string
+// marks where the work-item changes inside the site (the words are sorted by
+// work-item within a site); a window counts only when no change falls inside
+// it, and the site's predicted outcomes are the windows counted.
 __global__ void __launch_bounds__(kSpThreads) k_site_patterns(SiteArgs a) {
   if (!gate_open(a.gate, a.gate_want)) return;
   extern __shared__ u32 spm[];
   u32* bits = spm;
-  u32* cnt = spm + kSpBitWords;
+  u32* brk = spm + kSpBitWords;
+  u32* cnt = spm + 2 * kSpBitWords;
   uint16_t* used = reinterpret_cast<uint16_t*>(cnt + (1 << kSpBinsLog));
   __shared__ u32 n_used;
   __shared__ u64 red64[32];
@@ -414,7 +419,7 @@ __global__ void __launch_bounds__(kSpThreads) k_site_patterns(SiteArgs a) {
       ++nsite;
       if (m < (u64)kCocDense) atomicAdd(&a.arena->site_coc[m], 1ull);
       else overflow_append(a.over, a.over_cap, st, kTagSites, m);
-      emit_site_predicted(m, h, a.over, a.over_cap, a.arena);
+      if (!a.per_wi) emit_site_predicted(m, h, a.over, a.over_cap, a.arena);
     }
     const u32 nwords = (u32)((m + 31) / 32);
     // eight 32-event groups per warp in flight at a time
@@ -430,14 +435,31 @@ __global__ void __launch_bounds__(kSpThreads) k_site_patterns(SiteArgs a) {
         const u32 b = __ballot_sync(0xffffffffu, t[q]);
         if (lane == 0 && c0 + q * nw < nwords + 2) bits[c0 + q * nw] = b;
       }
+      if (a.per_wi) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const u64 j = (u64)(c0 + q * nw) * 32 + lane;
+          const bool change = j > 0 && j < m && (w[start + j] >> 1) != (w[start + j - 1] >> 1);
+          const u32 b = __ballot_sync(0xffffffffu, change);
+          if (lane == 0 && c0 + q * nw < nwords + 2) brk[c0 + q * nw] = b;
+        }
+      }
     }
     __syncthreads();
+    u64 spred = 0;  // this site's predicted outcomes (one history per (site, work-item))
     for (u32 q = 0; q < passes; ++q) {
       for (u64 j = h + threadIdx.x; j < m; j += kSpThreads) {
         const u64 pos = j - h;
         const u64 two = (u64)bits[pos >> 5] | ((u64)bits[(pos >> 5) + 1] << 32);
         const u32 win = (u32)((two >> (pos & 31)) & hmask);
         const u32 outcome = (bits[j >> 5] >> (j & 31)) & 1u;
+        if (a.per_wi) {
+          // work-item changes at positions pos + 1 .. j end the window's history
+          const u64 p1 = pos + 1;
+          const u64 tb = (u64)brk[p1 >> 5] | ((u64)brk[(p1 >> 5) + 1] << 32);
+          if ((tb >> (p1 & 31)) & hmask) continue;
+          if (q == 0) ++spred;
+        }
         if ((win >> pbits) == q) {
           const u32 b = win & (nbins - 1);
           if (atomicAdd(&cnt[b], 1u + (outcome << 16)) == 0u) used[atomicAdd(&n_used, 1u)] = (uint16_t)b;
@@ -458,6 +480,10 @@ __global__ void __launch_bounds__(kSpThreads) k_site_patterns(SiteArgs a) {
       __syncthreads();
       if (threadIdx.x == 0) n_used = 0;
       __syncthreads();
+    }
+    if (a.per_wi) {
+      spred = block_reduce(spred, OpAdd(), 0ull, red64);
+      if (threadIdx.x == 0) emit_site_pred_count(spred, a.over, a.over_cap, a.arena);
     }
   }
   __syncthreads();
@@ -755,7 +781,7 @@ void launch_persite_decide(Arena* arena, u32 h, u64 sites_cap, int allow, cudaSt
 }
 
 static size_t site_patterns_smem() {
-  return (size_t)(kSpBitWords + (1 << kSpBinsLog)) * 4 + (size_t)(1 << kSpBinsLog) * 2;
+  return (size_t)(2 * kSpBitWords + (1 << kSpBinsLog)) * 4 + (size_t)(1 << kSpBinsLog) * 2;
 }
 
 void init_branch_attributes() {

@@ -531,7 +531,7 @@ def test_history_scope_random(P, seed):
     rng = np.random.default_rng(50_000 + seed)
     tr = random_trace(seed, n_mem=int(rng.integers(0, 100)), n_br=int(rng.integers(1, 3000)),
                       n_wi=int(rng.integers(1, 12)), n_sites=int(rng.integers(1, 20)))
-    h = int(rng.choice([1, 2, 3, 5, 16]))
+    h = int(rng.choice([1, 2, 3, 5, 16, 20]))  # 20: longer than the per-site path takes
     o = oracle.compute(tr, history_len=h, history_scope=1)
     g = run_gpu(P, tr, on_device=bool(seed % 2), split=1 + seed % 3, history_len=h, history_scope=1,
                 plan=seed % 3)
@@ -545,16 +545,17 @@ def test_history_scope_random(P, seed):
     (200_000, 5000, True, 1),              # site ids >= 4096: radix sort
 ])
 def test_history_scope_sort_paths(P, n, n_sites, wi_sorted, h):
+    """Per-site path (plan 0) and global path (plan 1) after each branch sort."""
     tr = _site_trace(11 + n_sites, n, n_sites, wi_sorted)
-    for split in (1, 3):
-        assert_parity(run_gpu(P, tr, split=split, history_len=h, history_scope=1),
-                      oracle.compute(tr, history_len=h, history_scope=1))
+    o = oracle.compute(tr, history_len=h, history_scope=1)
+    for split, plan in ((1, 0), (3, 0), (2, 1)):
+        assert_parity(run_gpu(P, tr, split=split, history_len=h, history_scope=1, plan=plan), o)
 
 
 def test_history_scope_large_shape(P):
     tr = synth.large(seed=12, n_mem=10_000, n_br=1_000_003, n_wi=1000, per_wi=1001, zipf_distinct=1 << 12)
-    for h in (2, 16):
-        assert_parity(run_gpu(P, tr, history_len=h, history_scope=1),
+    for h, plan in ((2, 0), (16, 0), (3, 1)):
+        assert_parity(run_gpu(P, tr, history_len=h, history_scope=1, plan=plan),
                       oracle.compute(tr, history_len=h, history_scope=1))
 
 

@@ -85,13 +85,28 @@ struct DevState {
 // segment offset and scatter cursor. Capacity mask + 1 is a power of two.
 constexpr u32 kNoSlot = 0xFFFFFFFFu;
 constexpr int kMaxProbe = 256;
+// Superblock table, C = mask + 1 slots: keys u64[C] | cnt u32[kSbtStripes][C]
+// | off u32[C] | used u32[C]. The ingest counts an event in the counter stripe
+// of its warp (global warp index mod kSbtStripes), so a hot superblock's
+// counting atomics spread over kSbtStripes addresses; its rank is counted
+// within that stripe. The offset scan leaves each slot's total in stripe 0
+// and, in stripe s > 0, the offset where stripe s starts in the slot's
+// segment (off[] holds stripe 0's).
+constexpr int kStripeBits = 2;
+constexpr int kSbtStripes = 1 << kStripeBits;
+constexpr u64 kSbtClearBytes = 8 + 4 * kSbtStripes;  // per slot: keys and counters start at zero
+constexpr u64 kSbtBytes = kSbtClearBytes + 8;        // per slot, with the offset and the used list
 struct SbTable {
   u64* keys{};
-  u32* cnt{};
+  u32* cnt{};   // stripe s of slot i: cnt[s * (mask + 1) + i]
   u32* off{};
-  u32* cur{};
   u64 mask{};
 };
+// Slot word of the hash plan: rank << kRankShift | stripe << 32 | slot << 12
+// | the word's low 12 bits; a rank >= kRankLimit sends the invocation to the
+// sort plan (as a full table does).
+constexpr int kRankShift = 32 + kStripeBits;
+constexpr u32 kRankLimit = 1u << (32 - kStripeBits);
 
 // Sort slots (index into DevState::sort_cur).
 enum SortSlot { kSortMem = 0, kSortBranch = 1, kSortPattern = 2, kSortRuns = 3, kSortOver = 4 };
@@ -174,7 +189,7 @@ constexpr u64 kMaxHashSlots = 1ull << 20;   // slot words hold 20 slot bits
 struct MemIngestArgs {
   SbTable tab{};       // used when use_tab (hash plan)
   int use_tab{};
-  u64* slotw{};          // hash plan: out, slot word (low 32 bits) | rank of the event in its superblock << 32
+  u64* slotw{};          // hash plan: out, slot word (low 32 bits) | counter stripe << 32 | rank << kRankShift
   u64* spill{};          // hash plan: out, full words of events the table could not place
   const void* ev{};
   u64 n{};
@@ -230,7 +245,7 @@ void launch_mem_levels(const LevelArgs& a, cudaStream_t s);
 struct HashArgs {
   const u32* gate{};   // run only when !gate || *gate == gate_want (device-side plan choice)
   u32 gate_want{};
-  const u64* slotw{};    // slot words | ranks << 32 from the ingest
+  const u64* slotw{};    // slot words | stripes << 32 | ranks << kRankShift from the ingest
   u64 n_cap{};           // capacity of slotw / low, in elements
   uint16_t* low{};       // out: low 12 bits grouped by superblock
   SbTable tab{};

@@ -313,8 +313,7 @@ SbTable table_view(aiwc_handle* h) {
   const u64 C = h->sbt_cap;
   t.keys = (u64*)p;
   t.cnt = (u32*)(p + 8 * C);
-  t.off = (u32*)(p + 12 * C);
-  t.cur = (u32*)(p + 16 * C);
+  t.off = (u32*)(p + kSbtClearBytes * C);
   t.mask = C - 1;
   return t;
 }
@@ -324,12 +323,12 @@ aiwc_status ensure_table(aiwc_handle* h) {
   if (h->sbt_cap >= h->sbt_want && h->sbt.p) return AIWC_OK;
   if (h->n_mem) return AIWC_OK;  // never resize in the middle of an invocation
   const u64 C = std::min<u64>(h->sbt_want, kMaxHashSlots);
-  aiwc_status s = ensure(h, h->sbt, 24 * C, false);
+  aiwc_status s = ensure(h, h->sbt, kSbtBytes * C, false);
   if (s != AIWC_OK) return s;
   s = ensure(h, h->sbt_scan, 4 * sbt_scan_words(C), false);
   if (s != AIWC_OK) return s;
   h->sbt_cap = C;
-  CK(cudaMemsetAsync(h->sbt.p, 0, 12 * C, h->stream));
+  CK(cudaMemsetAsync(h->sbt.p, 0, kSbtClearBytes * C, h->stream));
   return AIWC_OK;
 }
 
@@ -482,7 +481,7 @@ aiwc_status reset_device_state(aiwc_handle* h, cudaStream_t st) {
   if (h->wi_bitmap) launch_wi_clear(h->wi_bitmap, h->arena, st);
   CK(cudaMemsetAsync(h->d_hist, 0, (size_t)h->cfg.n_opcodes * 8, st));
   CK(cudaMemsetAsync(h->arena, 0, sizeof(Arena), st));
-  if (h->sbt.p) CK(cudaMemsetAsync(h->sbt.p, 0, 12 * h->sbt_cap, st));
+  if (h->sbt.p) CK(cudaMemsetAsync(h->sbt.p, 0, kSbtClearBytes * h->sbt_cap, st));
   launch_reset_identities(h->arena, st);
   CK(cudaGetLastError());
   return AIWC_OK;
@@ -1244,7 +1243,7 @@ aiwc_status enqueue_part2(aiwc_handle* h, cudaStream_t st, const Plan& p) {
     ha.tab = table_view(h);
     ha.scan_tmp = (u32*)h->sbt_scan.p;
     ha.n_used = dst->sb_used;
-    ha.used_list = (u32*)((char*)h->sbt.p + 20 * h->sbt_cap);
+    ha.used_list = (u32*)((char*)h->sbt.p + (kSbtClearBytes + 4) * h->sbt_cap);
     ha.over = over;
     ha.over_cap = over_cap;
     ha.arena = h->arena;
@@ -1535,7 +1534,7 @@ aiwc_status compute_partitioned(aiwc_handle* h, aiwc_metrics* out) {
                            total_cap, st);
     // the partition's state goes; the opcode histogram and the work-item bitmap keep adding up
     CK(cudaMemsetAsync(h->arena, 0, sizeof(Arena), st));
-    if (h->sbt.p) CK(cudaMemsetAsync(h->sbt.p, 0, 12 * h->sbt_cap, st));
+    if (h->sbt.p) CK(cudaMemsetAsync(h->sbt.p, 0, kSbtClearBytes * h->sbt_cap, st));
     launch_reset_identities(h->arena, st);
     reset_host(h);
   }

@@ -22,9 +22,10 @@ constexpr int kIngestThreads = 256;
 // event's superblock (word >> 12) in the table, counts it there and writes
 // the 32-bit slot word (slot << 12) | (word & 0xFFF) -- the table keeps the
 // superblock, so the word can be rebuilt from the slot word -- with, in the
-// high half, the event's rank among its superblock's events (the count
-// before it, from the same atomic), which is its place in the superblock's
-// segment. An event the table cannot place gets the sentinel slot word and
+// high half, the warp's counter stripe and the event's rank among its
+// superblock's events in that stripe (the count before it, from the same
+// atomic), which with the stripes before it fixes its place in the
+// superblock's segment. An event the table cannot place gets the sentinel slot word and
 // its full word goes to the spill list. FILTER: the space mask drops events,
 // so outputs are compacted behind one atomicAdd per block-tile. FULL: a.n is
 // a multiple of the block tile, so every event slot is valid (no tests).
@@ -101,7 +102,10 @@ __global__ void __launch_bounds__(kIngestThreads, HASH ? 4 : 3) k_mem_ingest(Mem
           }
         }
       }
-      // all counting atomics in flight before any result is needed
+      // all counting atomics in flight before any result is needed; this
+      // warp's counter stripe
+      const u32 stripe = (blockIdx.x * (kIngestThreads / 32) + (threadIdx.x >> 5)) & (u32)(kSbtStripes - 1);
+      u32* cnt_s = a.tab.cnt + (u64)stripe * (a.tab.mask + 1);
       u32 peers[ITEMS], rb[ITEMS];
 #pragma unroll
       for (int k = 0; k < ITEMS; ++k)
@@ -109,12 +113,15 @@ __global__ void __launch_bounds__(kIngestThreads, HASH ? 4 : 3) k_mem_ingest(Mem
 #pragma unroll
       for (int k = 0; k < ITEMS; ++k) {
         rb[k] = 0u;
-        if (slot[k] != kNoSlot && lane == __ffs(peers[k]) - 1) rb[k] = atomicAdd(&a.tab.cnt[slot[k]], (u32)__popc(peers[k]));
+        if (slot[k] != kNoSlot && lane == __ffs(peers[k]) - 1) rb[k] = atomicAdd(&cnt_s[slot[k]], (u32)__popc(peers[k]));
       }
 #pragma unroll
       for (int k = 0; k < ITEMS; ++k) {
         const u32 r = __shfl_sync(0xffffffffu, rb[k], __ffs(peers[k]) - 1) + (u32)__popc(peers[k] & ((1u << lane) - 1u));
-        sw[k] = slot[k] != kNoSlot ? (((u64)r << 32) | (slot[k] << 12) | (u32)(word[k] & 0xFFFull)) : (u64)kSlotWordNone;
+        if (slot[k] != kNoSlot && r >= kRankLimit) sbt_fail = 1u;
+        sw[k] = slot[k] != kNoSlot ? (((u64)r << kRankShift) | ((u64)stripe << 32) | (slot[k] << 12) |
+                                      (u32)(word[k] & 0xFFFull))
+                                   : (u64)kSlotWordNone;
       }
     }
     if (FILTER) {

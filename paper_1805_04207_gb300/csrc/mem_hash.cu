@@ -31,7 +31,10 @@ __global__ void __launch_bounds__(kScanT) k_sbt_reduce(const u32* cnt, u64 len, 
   u32 s = 0;
 #pragma unroll
   for (int k = 0; k < kScanI; ++k)
-    if (base + k < len) s += cnt[base + k];
+    if (base + k < len) {
+#pragma unroll
+      for (int q = 0; q < kSbtStripes; ++q) s += cnt[(u64)q * len + base + k];
+    }
   s = block_reduce(s, OpAdd(), 0u, red);
   if (threadIdx.x == 0) bsum[blockIdx.x] = s;
 }
@@ -89,8 +92,10 @@ __global__ void __launch_bounds__(kScanT) k_sbt_top(u32* bsum, u32 nb, const u32
 
 // Segment offsets (exclusive prefix of the counts) into off[]. Occupied slots are listed (in no
 // particular order): those with fewer than kBigSeg events from the front of
-// used_list (count in n_used[0]), the others from the back (n_used[1]).
-__global__ void __launch_bounds__(kScanT) k_sbt_down(const u32* cnt, u64 len, const u32* bsum, u32* off,
+// used_list (count in n_used[0]), the others from the back (n_used[1]). The
+// counter stripes become each slot's total (stripe 0) and, in stripe s > 0,
+// the offset where stripe s's events start in the slot's segment.
+__global__ void __launch_bounds__(kScanT) k_sbt_down(u32* cnt, u64 len, const u32* bsum, u32* off,
                                                     u64* n_used, u32* used_list, const u32* gate, u32 want) {
   if (!gate_open(gate, want)) return;
   __shared__ u32 wt[33];
@@ -98,10 +103,15 @@ __global__ void __launch_bounds__(kScanT) k_sbt_down(const u32* cnt, u64 len, co
   __shared__ u32 wt3[33];
   __shared__ u64 s_base, b_base;
   const u64 base = (u64)blockIdx.x * kScanB + (u64)threadIdx.x * kScanI;
-  u32 v[kScanI], s = 0, small = 0, big = 0;
+  u32 v[kScanI], c[kScanI][kSbtStripes], s = 0, small = 0, big = 0;
 #pragma unroll
   for (int k = 0; k < kScanI; ++k) {
-    v[k] = base + k < len ? cnt[base + k] : 0u;
+    v[k] = 0u;
+#pragma unroll
+    for (int q = 0; q < kSbtStripes; ++q) {
+      c[k][q] = base + k < len ? cnt[(u64)q * len + base + k] : 0u;
+      v[k] += c[k][q];
+    }
     s += v[k];
     small += v[k] != 0u && v[k] < kBigSeg;
     big += v[k] >= kBigSeg;
@@ -110,7 +120,18 @@ __global__ void __launch_bounds__(kScanT) k_sbt_down(const u32* cnt, u64 len, co
   u32 ex = block_excl_u32(s, &tot, wt) + bsum[blockIdx.x];
 #pragma unroll
   for (int k = 0; k < kScanI; ++k) {
-    if (base + k < len) off[base + k] = ex;
+    if (base + k < len) {
+      off[base + k] = ex;
+      if (v[k]) {
+        cnt[base + k] = v[k];
+        u32 at = ex + c[k][0];
+#pragma unroll
+        for (int q = 1; q < kSbtStripes; ++q) {
+          cnt[(u64)q * len + base + k] = at;
+          at += c[k][q];
+        }
+      }
+    }
     ex += v[k];
   }
   u32 stot, btot;
@@ -133,7 +154,8 @@ constexpr int kScThreads = 256;
 constexpr int kScItems = 8;
 
 // Scatter each event's low 12 bits into its superblock's segment, at the
-// segment's offset plus the event's rank from the ingest.
+// offset where its counter stripe starts in the segment plus its rank within
+// the stripe (from the ingest).
 __global__ void __launch_bounds__(kScThreads, 4) k_mem_scatter(HashArgs a) {
   if (!gate_open(a.gate, a.gate_want)) return;
   const u64 n = umin64(a.arena->st.n_words, a.n_cap);
@@ -145,16 +167,20 @@ __global__ void __launch_bounds__(kScThreads, 4) k_mem_scatter(HashArgs a) {
       const u64 i = t0 + (u64)k * kScThreads + threadIdx.x;
       sw[k] = i < n ? __ldcs(a.slotw + i) : (u64)kSlotWordNone;
     }
+    const u64 C = a.tab.mask + 1;
     u32 off[kScItems];
 #pragma unroll
     for (int k = 0; k < kScItems; ++k) {
       const u32 w = (u32)sw[k];
-      off[k] = w != kSlotWordNone ? __ldg(a.tab.off + (w >> 12)) : 0u;
+      const u32 stripe = (u32)(sw[k] >> 32) & (u32)(kSbtStripes - 1);
+      off[k] = w == kSlotWordNone ? 0u
+               : stripe ? __ldg(a.tab.cnt + (u64)stripe * C + (w >> 12))
+                        : __ldg(a.tab.off + (w >> 12));
     }
 #pragma unroll
     for (int k = 0; k < kScItems; ++k) {
       const u32 w = (u32)sw[k];
-      if (w != kSlotWordNone) a.low[off[k] + (u32)(sw[k] >> 32)] = (uint16_t)(w & 0xFFFu);
+      if (w != kSlotWordNone) a.low[off[k] + (u32)(sw[k] >> kRankShift)] = (uint16_t)(w & 0xFFFu);
     }
   }
 }

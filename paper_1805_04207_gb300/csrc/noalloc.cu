@@ -31,7 +31,7 @@ constexpr size_t kOffWords = kOffResult + a256(sizeof(Result));
 constexpr size_t kOffSlot = kOffWords + a256(8 * kNoAllocMaxEvents);
 constexpr size_t kOffLow = kOffSlot + a256(8 * kNoAllocMaxEvents);
 constexpr size_t kOffTable = kOffLow + a256(2 * kNoAllocMaxEvents);
-constexpr size_t kOffScan = kOffTable + a256(24 * kNoAllocSlots);
+constexpr size_t kOffScan = kOffTable + a256(kSbtBytes * kNoAllocSlots);
 constexpr size_t kOffOverA = kOffScan + a256(4 * (kNoAllocSlots / 4096 + 1));
 constexpr size_t kOffOverB = kOffOverA + a256(8 * kNoAllocOverCap);
 constexpr size_t kCountsWords = 256 * ((kNoAllocOverCap + 2047) / 2048);  // sort tiles of 2048 keys
@@ -103,15 +103,14 @@ extern "C" aiwc_status aiwc_mem_metrics_noalloc(int device, void* cuda_stream, c
   SbTable tab;
   tab.keys = (u64*)(p + kOffTable);
   tab.cnt = (u32*)(p + kOffTable + 8 * kNoAllocSlots);
-  tab.off = (u32*)(p + kOffTable + 12 * kNoAllocSlots);
-  tab.cur = (u32*)(p + kOffTable + 16 * kNoAllocSlots);
+  tab.off = (u32*)(p + kOffTable + kSbtClearBytes * kNoAllocSlots);
   tab.mask = kNoAllocSlots - 1;
-  u32* used_list = (u32*)(p + kOffTable + 20 * kNoAllocSlots);
+  u32* used_list = (u32*)(p + kOffTable + (kSbtClearBytes + 4) * kNoAllocSlots);
   u32* bitmap = (u32*)(p + kOffBitmap);
   // the previous call's contents remain: clear what has to start at zero
   cudaError_t e;
   if ((e = cudaMemsetAsync(arena, 0, sizeof(Arena), s)) != cudaSuccess ||
-      (e = cudaMemsetAsync(tab.keys, 0, 12 * kNoAllocSlots, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(tab.keys, 0, kSbtClearBytes * kNoAllocSlots, s)) != cudaSuccess ||
       (e = cudaMemsetAsync(bitmap, 0, kNoAllocMaxWi / 8, s)) != cudaSuccess)
     return fail(AIWC_ECUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
   launch_reset_identities(arena, s);

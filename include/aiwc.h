@@ -352,7 +352,7 @@ aiwc_status aiwc_server_destroy(aiwc_server* s);
  *                every other field is zero (out->opcode_hist is left as is).
  * Work-item ids must be below 2^20. Blocks until the result is on the host.
  *
- * Scratch: one file-scope device array of about 16 MiB inside the library
+ * Scratch: one file-scope device array of about 24 MiB inside the library
  * (every device that loads the library holds it until the process exits),
  * shared by all calls on a device and keeping the last call's contents, which
  * each call clears where it must start at zero. Calls whose GPU work overlaps

@@ -1450,8 +1450,9 @@ aiwc_status recover(aiwc_handle* h) {
 void plan_from_ingest(aiwc_handle* h, Plan* p) {
   const DevState& hs = *h->h_state;
   const bool hashed = h->n_mem && use_hash(h) && h->sbt_cap;
-  p->hash_ok = hashed && hs.sbt_overflow == 0;
-  if (hashed && !p->hash_ok) h->sbt_want = std::min<u64>(h->sbt_cap * 4, kMaxHashSlots);
+  // segment offsets are 32-bit: 2^32 kept events or more go to the sort plan
+  p->hash_ok = hashed && hs.sbt_overflow == 0 && hs.n_words < (1ull << 32);
+  if (hashed && hs.sbt_overflow) h->sbt_want = std::min<u64>(h->sbt_cap * 4, kMaxHashSlots);
   p->br_passes = active_passes(hs.br_or, hs.br_and, hs.br_unsorted ? ~1ull : 0xFFFFFFFF00000000ull);
   p->run_passes = hs.run_unsorted ? active_passes(hs.run_or, hs.run_and, ~0ull) : 0u;
   // address bits sit above the store bit of the word

@@ -109,7 +109,8 @@ typedef struct aiwc_config {
                              at its start address; 1 = every byte it touches, addr .. addr + size - 1,
                              counts as one access of the same kind and space (size 0 touches none), so
                              every memory metric counts bytes. A push then learns its byte count on the
-                             device before ingesting: one stream synchronisation per 2^22 events. An
+                             device before ingesting: one stream synchronisation per 2^26 device events
+                             (per 2^22 host events, which are staged in 64 MiB pieces). An
                              access whose last byte is outside the address domain is invalid data. */
   uint32_t history_scope; /* whose branch history (Sec. III, Sec. V): 0 = one history per site, the
                              work-items' outcomes one after another (ids ascending, program order

@@ -191,7 +191,9 @@ struct MemIngestArgs {
   int use_tab{};
   u64* slotw{};          // hash plan: out, slot word (low 32 bits) | counter stripe << 32 | rank << kRankShift
   u64* spill{};          // hash plan: out, full words of events the table could not place
-  const void* ev{};
+  const void* ev{};      // 16-byte events, or with words_in the 64-bit words of kept accesses
+  bool words_in{};       // ev holds words (space, address and store bit already checked, filtered,
+                         // and their work-items marked): the byte-granular path
   u64 n{};
   u32 space_mask{};
   u64* words{};          // sort plan: out, 64-bit sort words
@@ -203,7 +205,8 @@ struct MemIngestArgs {
 void launch_mem_ingest(const MemIngestArgs& a, cudaStream_t s);
 
 // Byte-granular addresses: the one-byte accesses of a chunk of memory events
-// (addr + b for b < size, with the event's work-item, kind and space).
+// (addr + b for b < size, with the event's kind and space), written as the
+// 64-bit words the ingest forms, for the accesses whose space is kept.
 constexpr u64 kExpandTile = 1024;         // events per tile
 constexpr u64 kExpandChunk = 1ull << 22;  // events per chunk (tile offsets for one chunk)
 struct ExpandArgs {
@@ -212,18 +215,20 @@ struct ExpandArgs {
   u64* tile_off{};    // [ntiles] exclusive offsets of the tiles' one-byte events
   u64* total{};       // bytes the chunk touches
   u32* tile_sum{};    // [ntiles] bytes each tile touches
-  void* out{};        // out: the one-byte events, `*total` of them
+  void* out{};        // out: the words of the one-byte accesses, `*total` of them
+  u32 space_mask{};
   u32* wi_bitmap{};
   u64 max_wi{};
   Arena* arena{};
   int sm_count{};
 };
-size_t expand_meta_bytes();  // tile offsets, total and tile sums of one chunk
-// Counts the bytes of each tile (and checks the start addresses; a size-0
-// access marks its work-item here, since it yields no one-byte event), then
-// scans the tile counts into offsets and the chunk's total.
+size_t expand_meta_bytes();  // tile offsets and tile sums of one chunk (8 B and 4 B per tile)
+// Counts the kept bytes of each tile, checks the start addresses and marks
+// every event's work-item (the words carry none), then scans the tile counts
+// into offsets and the chunk's total.
 void launch_expand_count(const ExpandArgs& a, cudaStream_t s);
-// Writes the one-byte events of every tile at its offset.
+// Writes the words of every tile's one-byte accesses at its offset; a byte at
+// or above 2^61 raises the address error.
 void launch_expand_write(const ExpandArgs& a, cudaStream_t s);
 
 struct LevelArgs {

@@ -787,8 +787,9 @@ aiwc_status aiwc_create(const aiwc_config* cfg, aiwc_handle** out) {
 
 namespace {
 
-// The ingest of n memory events (device or host) into the current invocation.
-aiwc_status push_mem_events(aiwc_handle* h, const aiwc_mem_event* ev, size_t n, int on_device) {
+// The ingest of n memory events (device or host) into the current invocation;
+// words_in: `ev` holds n device words of kept one-byte accesses instead.
+aiwc_status push_mem_events(aiwc_handle* h, const void* ev, size_t n, int on_device, bool words_in = false) {
   aiwc_status s;
   ENSURE(h->mem_a, (h->n_mem + n) * 8, true);
   if ((s = ensure_bitmap(h)) != AIWC_OK) return s;
@@ -802,6 +803,7 @@ aiwc_status push_mem_events(aiwc_handle* h, const aiwc_mem_event* ev, size_t n, 
     a.spill = (u64*)h->mem_a.p;
   }
   a.space_mask = h->cfg.space_mask;
+  a.words_in = words_in;
   a.words = (u64*)h->mem_a.p;
   a.wi_bitmap = h->wi_bitmap;
   a.max_wi = h->max_wi;
@@ -828,43 +830,58 @@ aiwc_status push_mem_events(aiwc_handle* h, const aiwc_mem_event* ev, size_t n, 
   return AIWC_OK;
 }
 
-// Byte-granular addresses: every byte an access touches becomes a one-byte
-// event of its own, ingested like any other event. The host reads each
-// chunk's byte count back before it sizes the one-byte events and the ingest.
+// Byte-granular addresses: every byte an access touches becomes an access of
+// its own, written as the word the ingest forms and ingested like any other.
+// The host reads the byte counts of up to kExpandBatch chunks back at once
+// before it sizes their words and the ingest.
+constexpr size_t kExpandBatch = 16;
+
 aiwc_status expand_events(aiwc_handle* h, const void* dev_ev, size_t n) {
   aiwc_status s;
-  for (size_t c0 = 0; c0 < n; c0 += kExpandChunk) {
-    const size_t cnt = std::min<size_t>((size_t)kExpandChunk, n - c0);
-    ENSURE(h->exp_meta, expand_meta_bytes(), false);
+  const size_t nt = (size_t)(kExpandChunk / kExpandTile);
+  const size_t per_chunk = expand_meta_bytes();  // tile offsets, then tile sums
+  for (size_t b0 = 0; b0 < n; b0 += kExpandBatch * kExpandChunk) {
+    const size_t nb = std::min<size_t>(kExpandBatch, (n - b0 + kExpandChunk - 1) / kExpandChunk);
+    ENSURE(h->exp_meta, kExpandBatch * (per_chunk + 8), false);
     if ((s = ensure_bitmap(h)) != AIWC_OK) return s;
-    if (!h->h_exp) CK(cudaMallocHost(&h->h_exp, sizeof(u64)));
-    ExpandArgs x;
-    x.ev = (const char*)dev_ev + 16 * c0;
-    x.n = cnt;
-    x.tile_off = (u64*)h->exp_meta.p;
-    x.total = x.tile_off + kExpandChunk / kExpandTile;
-    x.tile_sum = (u32*)(x.total + 1);
-    x.wi_bitmap = h->wi_bitmap;
-    x.max_wi = h->max_wi;
-    x.arena = h->arena;
-    x.sm_count = h->sm_count;
+    if (!h->h_exp) CK(cudaMallocHost(&h->h_exp, kExpandBatch * sizeof(u64)));
+    u64* totals = (u64*)h->exp_meta.p;
+    ExpandArgs x[kExpandBatch];
+    for (size_t j = 0; j < nb; ++j) {
+      const size_t c0 = b0 + j * kExpandChunk;
+      x[j].ev = (const char*)dev_ev + 16 * c0;
+      x[j].n = std::min<size_t>((size_t)kExpandChunk, n - c0);
+      x[j].tile_off = (u64*)((char*)h->exp_meta.p + kExpandBatch * 8 + j * per_chunk);
+      x[j].tile_sum = (u32*)(x[j].tile_off + nt);
+      x[j].total = totals + j;
+      x[j].space_mask = h->cfg.space_mask;
+      x[j].wi_bitmap = h->wi_bitmap;
+      x[j].max_wi = h->max_wi;
+      x[j].arena = h->arena;
+      x[j].sm_count = h->sm_count;
+    }
     {
       StageScope scope(h, kStMemExpand);
-      launch_expand_count(x, h->stream);
+      for (size_t j = 0; j < nb; ++j) launch_expand_count(x[j], h->stream);
     }
     CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(h->h_exp, x.total, sizeof(u64), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));  // also retires the previous chunk's readers of h->exp
-    const u64 m = *h->h_exp;
+    CK(cudaMemcpyAsync(h->h_exp, totals, nb * sizeof(u64), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));  // also retires the previous batch's readers of h->exp
+    u64 m = 0;
+    for (size_t j = 0; j < nb; ++j) m += h->h_exp[j];
     if (m == 0) continue;
-    ENSURE(h->exp, m * 16, false);
-    x.out = h->exp.p;
+    ENSURE(h->exp, m * 8, false);
     {
       StageScope scope(h, kStMemExpand);
-      launch_expand_write(x, h->stream);
+      u64 at = 0;
+      for (size_t j = 0; j < nb; ++j) {
+        x[j].out = (u64*)h->exp.p + at;
+        launch_expand_write(x[j], h->stream);
+        at += h->h_exp[j];
+      }
     }
     CK(cudaGetLastError());
-    if ((s = push_mem_events(h, (const aiwc_mem_event*)h->exp.p, m, 1)) != AIWC_OK) return s;
+    if ((s = push_mem_events(h, h->exp.p, m, 1, true)) != AIWC_OK) return s;
   }
   return AIWC_OK;
 }

@@ -29,8 +29,11 @@ constexpr int kIngestThreads = 256;
 // its full word goes to the spill list. FILTER: the space mask drops events,
 // so outputs are compacted behind one atomicAdd per block-tile. FULL: a.n is
 // a multiple of the block tile, so every event slot is valid (no tests).
-template <bool FILTER, bool HASH, bool FULL>
+// WORDS: the input is 64-bit words of kept accesses (the byte-granular
+// path), whose work-items and addresses were handled by the expansion.
+template <bool FILTER, bool HASH, bool FULL, bool WORDS>
 __global__ void __launch_bounds__(kIngestThreads, HASH ? 4 : 3) k_mem_ingest(MemIngestArgs a) {
+  static_assert(!(WORDS && FILTER), "words are filtered by the expansion");
   constexpr int ITEMS = HASH ? 4 : 8;
   __shared__ u64 red64[32];
   __shared__ u32 red32[32];
@@ -38,6 +41,7 @@ __global__ void __launch_bounds__(kIngestThreads, HASH ? 4 : 3) k_mem_ingest(Mem
   __shared__ u64 s_base;
   DevState* st = &a.arena->st;
   const uint4* ev = reinterpret_cast<const uint4*>(a.ev);
+  const u64* win = reinterpret_cast<const u64*>(a.ev);
   const int lane = threadIdx.x & 31;
   u64 writes = 0, wor = 0, wand = ~0ull, kept = 0;
   u32 wmin = 0xFFFFFFFFu, wmax = 0u, err = 0u, sbt_fail = 0u;
@@ -45,17 +49,28 @@ __global__ void __launch_bounds__(kIngestThreads, HASH ? 4 : 3) k_mem_ingest(Mem
   for (u64 t0 = (u64)blockIdx.x * per_block; t0 < a.n; t0 += (u64)gridDim.x * per_block) {
     uint4 e[ITEMS];
     bool valid[ITEMS];
-#pragma unroll
-    for (int k = 0; k < ITEMS; ++k) {
-      const u64 i = t0 + (u64)k * kIngestThreads + threadIdx.x;
-      valid[k] = FULL || i < a.n;
-      e[k] = valid[k] ? __ldcs(ev + i) : make_uint4(0u, 0u, 0u, 0u);
-    }
     u64 word[ITEMS];
     bool keep[ITEMS];
     u32 nkeep = 0;
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
+      const u64 i = t0 + (u64)k * kIngestThreads + threadIdx.x;
+      valid[k] = FULL || i < a.n;
+      if (WORDS) word[k] = valid[k] ? __ldcs(win + i) : 0ull;
+      else e[k] = valid[k] ? __ldcs(ev + i) : make_uint4(0u, 0u, 0u, 0u);
+    }
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {
+      if (WORDS) {
+        keep[k] = valid[k];
+        if (keep[k]) {
+          ++nkeep;
+          writes += word[k] & 1ull;
+          wor |= word[k];
+          wand &= word[k];
+        }
+        continue;
+      }
       const u64 addr = (u64)e[k].x | ((u64)e[k].y << 32);
       const u32 wi = e[k].z;
       const u32 flags = (e[k].w >> 8) & 0xFFu;
@@ -188,10 +203,11 @@ __global__ void __launch_bounds__(kIngestThreads, HASH ? 4 : 3) k_mem_ingest(Mem
 }
 
 // Byte-granular addresses. A tile of kExpandTile events: k_expand_count sums
-// its sizes, k_expand_scan turns the tile sums into offsets, k_expand_write
-// stages the tile in shared memory with per-event offsets (each thread scans
-// its own kExpItems consecutive events) and then writes the tile's one-byte
-// events in order, consecutive threads writing consecutive 16-byte records;
+// the sizes of its kept events (and marks every event's work-item),
+// k_expand_scan turns the tile sums into offsets, k_expand_write stages the
+// tile in shared memory with per-event offsets (each thread scans its own
+// kExpItems consecutive events) and then writes the words of the tile's
+// one-byte accesses in order, consecutive threads writing consecutive words;
 // a thread finds the event of output q by binary search over the offsets.
 constexpr int kExpThreads = 256;
 constexpr int kExpItems = (int)kExpandTile / kExpThreads;
@@ -209,12 +225,11 @@ __global__ void __launch_bounds__(kExpThreads) k_expand_count(ExpandArgs a) {
       const u64 i = (u64)tile * kExpandTile + (u64)k * kExpThreads + threadIdx.x;
       const bool valid = i < a.n;
       const uint4 e = valid ? __ldg(ev + i) : make_uint4(0u, 0u, 0u, 0u);
-      const u32 size = e.w & 0xFFu;
-      sum += size;
+      const u32 space = (e.w >> 9) & 3u;
+      if ((a.space_mask >> space) & 1u) sum += e.w & 0xFFu;
       if (valid && (e.y >> 29)) err |= kErrAddr;  // start address outside the 61-bit domain
-      const bool none = valid && size == 0u;    // touches no byte; its work-item still counts
-      mark_work_items(a.wi_bitmap, a.max_wi, e.z, none, &err);
-      if (none && (u64)e.z < a.max_wi) {
+      mark_work_items(a.wi_bitmap, a.max_wi, e.z, valid, &err);
+      if (valid && (u64)e.z < a.max_wi) {
         wmin = min(wmin, e.z);
         wmax = max(wmax, e.z);
       }
@@ -271,13 +286,15 @@ __global__ void __launch_bounds__(1024) k_expand_scan(ExpandArgs a) {
 }
 
 __global__ void __launch_bounds__(kExpThreads) k_expand_write(ExpandArgs a) {
-  __shared__ uint4 s_ev[kExpandTile];
+  __shared__ u64 s_word[kExpandTile];  // the event's first word (store bit, space, start address)
   __shared__ u32 s_off[kExpandTile + 1];
   __shared__ u32 s_wsum[kExpThreads / 32];
+  __shared__ u32 red32[32];
   const uint4* ev = reinterpret_cast<const uint4*>(a.ev);
-  uint4* out = reinterpret_cast<uint4*>(a.out);
+  u64* out = reinterpret_cast<u64*>(a.out);
   const u32 ntiles = (u32)((a.n + kExpandTile - 1) / kExpandTile);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  u32 err = 0u;
   for (u32 tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const u64 base = (u64)tile * kExpandTile;
     u32 sz[kExpItems];
@@ -286,8 +303,10 @@ __global__ void __launch_bounds__(kExpThreads) k_expand_write(ExpandArgs a) {
     for (int k = 0; k < kExpItems; ++k) {
       const u32 j = threadIdx.x * kExpItems + k;
       const uint4 e = base + j < a.n ? __ldg(ev + base + j) : make_uint4(0u, 0u, 0u, 0u);
-      s_ev[j] = e;
-      sz[k] = e.w & 0xFFu;
+      const u32 space = (e.w >> 9) & 3u, store = (e.w >> 8) & 1u;
+      const u64 addr = (u64)e.x | ((u64)e.y << 32);
+      s_word[j] = ((u64)space << 62) | (addr << 1) | store;  // address bits above 60 are dropped here
+      sz[k] = ((a.space_mask >> space) & 1u) ? (e.w & 0xFFu) : 0u;
       mine += sz[k];
     }
     u32 x = mine;
@@ -317,12 +336,17 @@ __global__ void __launch_bounds__(kExpThreads) k_expand_write(ExpandArgs a) {
         if (s_off[mid] <= q) lo = mid;
         else hi = mid - 1u;
       }
-      const uint4 e = s_ev[lo];
-      const u64 addr = ((u64)e.x | ((u64)e.y << 32)) + (u64)(q - s_off[lo]);
-      out[o0 + q] = make_uint4((u32)addr, (u32)(addr >> 32), e.z, (e.w & 0xFFFFFF00u) | 1u);
+      // one byte further is 2 in word units; the sum stays within 62 bits
+      // unless the byte leaves the 61-bit domain
+      const u64 w0 = s_word[lo];
+      const u64 wd = w0 + 2ull * (u64)(q - s_off[lo]);
+      if ((wd ^ w0) >> 62) err |= kErrAddr;
+      out[o0 + q] = wd;
     }
     __syncthreads();  // the tile's staging is refilled next
   }
+  err = block_reduce(err, OpOr(), 0u, red32);
+  if (threadIdx.x == 0 && err) atomicOr(&a.arena->st.err, err);
 }
 
 constexpr int kLvThreads = kTileThreads;
@@ -407,36 +431,47 @@ void launch_mem_ingest(const MemIngestArgs& a, cudaStream_t s) {
   const u64 per_block = (u64)kIngestThreads * (a.use_tab ? 4 : 8);
   const u64 cap = a.use_tab ? 152ull * 16 : 152ull * 8;
   auto grid = [&](u64 n) { return (unsigned)std::min<u64>((n + per_block - 1) / per_block, cap); };
-  const bool filter = a.space_mask != 0xFu;
+  const bool filter = a.space_mask != 0xFu && !a.words_in;
   if (filter) {
-    if (a.use_tab) k_mem_ingest<true, true, false><<<grid(a.n), kIngestThreads, 0, s>>>(a);
-    else k_mem_ingest<true, false, false><<<grid(a.n), kIngestThreads, 0, s>>>(a);
+    if (a.use_tab) k_mem_ingest<true, true, false, false><<<grid(a.n), kIngestThreads, 0, s>>>(a);
+    else k_mem_ingest<true, false, false, false><<<grid(a.n), kIngestThreads, 0, s>>>(a);
     count_launches(1);
     return;
   }
   // whole block tiles without bounds tests, then the ragged tail
   const u64 n_full = a.n / per_block * per_block;
+  const size_t unit = a.words_in ? 8 : 16;
   if (n_full) {
     MemIngestArgs f = a;
     f.n = n_full;
-    if (a.use_tab) k_mem_ingest<false, true, true><<<grid(n_full), kIngestThreads, 0, s>>>(f);
-    else k_mem_ingest<false, false, true><<<grid(n_full), kIngestThreads, 0, s>>>(f);
+    if (a.words_in) {
+      if (a.use_tab) k_mem_ingest<false, true, true, true><<<grid(n_full), kIngestThreads, 0, s>>>(f);
+      else k_mem_ingest<false, false, true, true><<<grid(n_full), kIngestThreads, 0, s>>>(f);
+    } else {
+      if (a.use_tab) k_mem_ingest<false, true, true, false><<<grid(n_full), kIngestThreads, 0, s>>>(f);
+      else k_mem_ingest<false, false, true, false><<<grid(n_full), kIngestThreads, 0, s>>>(f);
+    }
     count_launches(1);
   }
   if (a.n > n_full) {
     MemIngestArgs t = a;
-    t.ev = static_cast<const char*>(a.ev) + 16 * n_full;
+    t.ev = static_cast<const char*>(a.ev) + unit * n_full;
     t.n = a.n - n_full;
     t.word_base = a.word_base + n_full;
-    if (a.use_tab) k_mem_ingest<false, true, false><<<grid(t.n), kIngestThreads, 0, s>>>(t);
-    else k_mem_ingest<false, false, false><<<grid(t.n), kIngestThreads, 0, s>>>(t);
+    if (a.words_in) {
+      if (a.use_tab) k_mem_ingest<false, true, false, true><<<grid(t.n), kIngestThreads, 0, s>>>(t);
+      else k_mem_ingest<false, false, false, true><<<grid(t.n), kIngestThreads, 0, s>>>(t);
+    } else {
+      if (a.use_tab) k_mem_ingest<false, true, false, false><<<grid(t.n), kIngestThreads, 0, s>>>(t);
+      else k_mem_ingest<false, false, false, false><<<grid(t.n), kIngestThreads, 0, s>>>(t);
+    }
     count_launches(1);
   }
 }
 
 size_t expand_meta_bytes() {
   const size_t nt = (size_t)(kExpandChunk / kExpandTile);
-  return nt * 8 + 8 + nt * 4;
+  return nt * 8 + nt * 4;
 }
 
 void launch_expand_count(const ExpandArgs& a, cudaStream_t s) {

@@ -483,6 +483,36 @@ def test_byte_addresses_several_chunks(P, on_device):
     assert_parity(run_gpu(P, tr, on_device=on_device, byte_addresses=1), o)
 
 
+def test_byte_addresses_many_batches(P):
+    """More events than one counting batch (16 chunks of 2^22): byte
+    granularity equals the start-address metrics of the accesses split into
+    one-byte events (the identity the oracle pins), both on the device."""
+    n = (1 << 26) + 4097
+    g = torch.Generator(device="cuda").manual_seed(7)
+    from synth import pack_mem
+    addr = (1 << 36) + 2 * torch.randint(0, 1 << 24, (n,), device="cuda", generator=g)
+    sizes = torch.randint(1, 3, (n,), device="cuda", generator=g)
+    wi = torch.arange(n, device="cuda") // 1024
+    st = torch.randint(0, 2, (n,), device="cuda", generator=g)
+    mem = pack_mem(addr, wi, sizes, st, torch.zeros_like(addr))
+    with P.Characterizer(byte_addresses=1, n_opcodes=8) as c:
+        c.push_mem(mem)
+        got = c.compute()
+    # the same accesses as one-byte events, start addresses only
+    rep = torch.repeat_interleave(torch.arange(n, device="cuda"), sizes)
+    first = torch.cumsum(sizes, 0) - sizes
+    off = torch.arange(rep.numel(), device="cuda") - first[rep]
+    one = pack_mem(addr[rep] + off, wi[rep], torch.ones_like(rep), st[rep], torch.zeros_like(rep))
+    del rep, first, off
+    with P.Characterizer(n_opcodes=8) as c:
+        c.push_mem(one)
+        want = c.compute()
+    for f in ("total_reads", "total_writes", "footprint", "footprint_cover", "unique_reads", "unique_writes",
+              "work_items"):
+        assert got[f] == want[f], f
+    assert got["entropy"] == want["entropy"]
+
+
 def test_byte_addresses_large_shapes(P):
     tr = synth.large(seed=11, n_mem=500_001, n_br=0, n_wi=64, per_wi=64, zipf_distinct=1 << 16)
     for plan in (0, 1):

@@ -494,13 +494,13 @@ def main():
     per_step = {k: v / args.steps for k, v in stage_tot.items()}
     D = out["footprint"]
     Bp = out["branch_patterns"]
-    # with byte-granular addresses the expansion reads each 16-byte event once
-    # and writes one 8-byte key per byte touched, which the ingest reads
+    # with byte-granular addresses the byte count pass and the ingest each read
+    # the 16-byte events once (the one-byte accesses are formed on chip)
     byte_mode = bool(opts.get("byte_addresses"))
     n_acc = out["total_reads"] + out["total_writes"] if byte_mode else n_mem
-    alg = {"mem_ingest": (8 if byte_mode else ALG_BYTES["mem_event"]) * n_acc,
+    alg = {"mem_ingest": ALG_BYTES["mem_event"] * n_mem,
            "branch_ingest": ALG_BYTES["branch_event"] * n_br,
-           "mem_expand": ALG_BYTES["mem_event"] * n_mem + 8 * n_acc,
+           "mem_expand": ALG_BYTES["mem_event"] * n_mem,
            "instr_runs": ALG_BYTES["opcode"] * n_ops,
            "mem_sort": 16 * n_acc, "mem_scatter": 0, "mem_levels": ALG_BYTES["distinct_key"] * D,
            "branch_sort": 16 * n_br, "windows": ALG_BYTES["pattern"] * Bp, "pattern_sort": 16 * Bp,

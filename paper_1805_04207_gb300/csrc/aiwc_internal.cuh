@@ -191,9 +191,7 @@ struct MemIngestArgs {
   int use_tab{};
   u64* slotw{};          // hash plan: out, slot word (low 32 bits) | counter stripe << 32 | rank << kRankShift
   u64* spill{};          // hash plan: out, full words of events the table could not place
-  const void* ev{};      // 16-byte events, or with words_in the 64-bit words of kept accesses
-  bool words_in{};       // ev holds words (space, address and store bit already checked, filtered,
-                         // and their work-items marked): the byte-granular path
+  const void* ev{};      // 16-byte events
   u64 n{};
   u32 space_mask{};
   u64* words{};          // sort plan: out, 64-bit sort words
@@ -205,8 +203,8 @@ struct MemIngestArgs {
 void launch_mem_ingest(const MemIngestArgs& a, cudaStream_t s);
 
 // Byte-granular addresses: the one-byte accesses of a chunk of memory events
-// (addr + b for b < size, with the event's kind and space), written as the
-// 64-bit words the ingest forms, for the accesses whose space is kept.
+// (addr + b for b < size, with the event's kind and space), for the events
+// whose space is kept.
 constexpr u64 kExpandTile = 1024;         // events per tile
 constexpr u64 kExpandChunk = 1ull << 22;  // events per chunk (tile offsets for one chunk)
 struct ExpandArgs {
@@ -215,7 +213,6 @@ struct ExpandArgs {
   u64* tile_off{};    // [ntiles] exclusive offsets of the tiles' one-byte events
   u64* total{};       // bytes the chunk touches
   u32* tile_sum{};    // [ntiles] bytes each tile touches
-  void* out{};        // out: the words of the one-byte accesses, `*total` of them
   u32 space_mask{};
   u32* wi_bitmap{};
   u64 max_wi{};
@@ -227,9 +224,10 @@ size_t expand_meta_bytes();  // tile offsets and tile sums of one chunk (8 B and
 // every event's work-item (the words carry none), then scans the tile counts
 // into offsets and the chunk's total.
 void launch_expand_count(const ExpandArgs& a, cudaStream_t s);
-// Writes the words of every tile's one-byte accesses at its offset; a byte at
-// or above 2^61 raises the address error.
-void launch_expand_write(const ExpandArgs& a, cudaStream_t s);
+// Ingests a chunk's one-byte accesses (a.ev: its events, a.n of them) at
+// a.word_base + the tile offsets from launch_expand_count; a byte at or above
+// 2^61 raises the address error.
+void launch_mem_ingest_bytes(const MemIngestArgs& a, const u64* tile_off, cudaStream_t s);
 
 struct LevelArgs {
   const u32* gate{};   // run only when !gate || *gate == gate_want (device-side plan choice)

@@ -114,9 +114,9 @@ struct aiwc_handle {
   DevBuf mem_a, mem_b, br_a, br_b, pat_a, pat_b, rk_a, rk_b, run_sum, over_a, over_b, counts, bsums, tiles;
   DevBuf stage[2];
   DevBuf desc;
-  // byte-granular addresses: one chunk's one-byte events, its tile offsets and total
-  DevBuf exp, exp_meta;
-  u64* h_exp = nullptr;  // pinned copy of the chunk's total
+  // byte-granular addresses: the tile offsets and byte counts of a batch of chunks
+  DevBuf exp_meta;
+  u64* h_exp = nullptr;  // pinned copy of the batch's byte counts
   // superblock table of the hash plan (sized for the next invocation)
   DevBuf sbt, sbt_scan;
   u64 sbt_cap = 0;       // slots currently allocated
@@ -787,33 +787,39 @@ aiwc_status aiwc_create(const aiwc_config* cfg, aiwc_handle** out) {
 
 namespace {
 
-// The ingest of n memory events (device or host) into the current invocation;
-// words_in: `ev` holds n device words of kept one-byte accesses instead.
-aiwc_status push_mem_events(aiwc_handle* h, const void* ev, size_t n, int on_device, bool words_in = false) {
+// Buffers and common arguments of an ingest that adds n accesses to the
+// current invocation.
+aiwc_status ingest_args(aiwc_handle* h, size_t n, MemIngestArgs* a) {
   aiwc_status s;
   ENSURE(h->mem_a, (h->n_mem + n) * 8, true);
   if ((s = ensure_bitmap(h)) != AIWC_OK) return s;
   if (use_hash(h) && (s = ensure_table(h)) != AIWC_OK) return s;
-  MemIngestArgs a;
-  a.use_tab = use_hash(h) && h->sbt_cap ? 1 : 0;
-  if (a.use_tab) {
+  a->use_tab = use_hash(h) && h->sbt_cap ? 1 : 0;
+  if (a->use_tab) {
     ENSURE(h->mem_b, (h->n_mem + n) * 8, true);  // slot words and ranks
-    a.tab = table_view(h);
-    a.slotw = (u64*)h->mem_b.p;
-    a.spill = (u64*)h->mem_a.p;
+    a->tab = table_view(h);
+    a->slotw = (u64*)h->mem_b.p;
+    a->spill = (u64*)h->mem_a.p;
   }
-  a.space_mask = h->cfg.space_mask;
-  a.words_in = words_in;
-  a.words = (u64*)h->mem_a.p;
-  a.wi_bitmap = h->wi_bitmap;
-  a.max_wi = h->max_wi;
-  a.arena = h->arena;
+  a->space_mask = h->cfg.space_mask;
+  a->words = (u64*)h->mem_a.p;
+  a->wi_bitmap = h->wi_bitmap;
+  a->max_wi = h->max_wi;
+  a->arena = h->arena;
+  a->word_base = h->n_mem;
+  return AIWC_OK;
+}
+
+// The ingest of n memory events (device or host) into the current invocation.
+aiwc_status push_mem_events(aiwc_handle* h, const aiwc_mem_event* ev, size_t n, int on_device) {
+  MemIngestArgs a;
+  aiwc_status s = ingest_args(h, n, &a);
+  if (s != AIWC_OK) return s;
   const u64 base = h->n_mem;
   StageScope scope(h, kStMemIngest);
   if (on_device) {
     a.ev = ev;
     a.n = n;
-    a.word_base = base;
     launch_mem_ingest(a, h->stream);
     CK(cudaGetLastError());
   } else {
@@ -831,9 +837,9 @@ aiwc_status push_mem_events(aiwc_handle* h, const void* ev, size_t n, int on_dev
 }
 
 // Byte-granular addresses: every byte an access touches becomes an access of
-// its own, written as the word the ingest forms and ingested like any other.
-// The host reads the byte counts of up to kExpandBatch chunks back at once
-// before it sizes their words and the ingest.
+// its own. The host reads the byte counts of up to kExpandBatch chunks back
+// at once, sizes the ingest, and each chunk's one-byte accesses are formed and
+// ingested in one kernel at their tiles' offsets.
 constexpr size_t kExpandBatch = 16;
 
 aiwc_status expand_events(aiwc_handle* h, const void* dev_ev, size_t n) {
@@ -866,22 +872,26 @@ aiwc_status expand_events(aiwc_handle* h, const void* dev_ev, size_t n) {
     }
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(h->h_exp, totals, nb * sizeof(u64), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));  // also retires the previous batch's readers of h->exp
+    CK(cudaStreamSynchronize(h->stream));
     u64 m = 0;
     for (size_t j = 0; j < nb; ++j) m += h->h_exp[j];
     if (m == 0) continue;
-    ENSURE(h->exp, m * 8, false);
+    MemIngestArgs a;
+    if ((s = ingest_args(h, m, &a)) != AIWC_OK) return s;
     {
-      StageScope scope(h, kStMemExpand);
-      u64 at = 0;
+      StageScope scope(h, kStMemIngest);
+      u64 at = h->n_mem;
       for (size_t j = 0; j < nb; ++j) {
-        x[j].out = (u64*)h->exp.p + at;
-        launch_expand_write(x[j], h->stream);
+        MemIngestArgs b = a;
+        b.ev = x[j].ev;
+        b.n = x[j].n;
+        b.word_base = at;
+        launch_mem_ingest_bytes(b, x[j].tile_off, h->stream);
         at += h->h_exp[j];
       }
     }
     CK(cudaGetLastError());
-    if ((s = push_mem_events(h, h->exp.p, m, 1, true)) != AIWC_OK) return s;
+    h->n_mem += m;
   }
   return AIWC_OK;
 }
@@ -1738,7 +1748,7 @@ aiwc_status aiwc_destroy(aiwc_handle* h) {
   if (h->stream || h->copy_stream) cudaStreamSynchronize(h->stream);
   DevBuf* bufs[] = {&h->mem_a, &h->mem_b, &h->br_a, &h->br_b, &h->pat_a, &h->pat_b, &h->rk_a, &h->rk_b,
                     &h->run_sum, &h->over_a, &h->over_b, &h->counts, &h->bsums, &h->tiles, &h->stage[0],
-                    &h->stage[1], &h->desc, &h->sbt, &h->sbt_scan, &h->sites, &h->over_total, &h->exp,
+                    &h->stage[1], &h->desc, &h->sbt, &h->sbt_scan, &h->sites, &h->over_total,
                     &h->exp_meta};
   for (DevBuf* b : bufs) release(h, *b);
   if (h->total) cudaFree(h->total);

@@ -16,6 +16,59 @@ namespace aiwc {
 namespace {
 
 constexpr int kIngestThreads = 256;
+constexpr int kHashItems = 4;  // events per thread and block-tile in the hash plan (8 in the sort plan)
+
+// Hash plan: places the kept words' superblocks in the table, counts them in
+// this warp's counter stripe and forms their slot words (sentinel for words
+// the table cannot place, whose full words go to the spill list). All lanes
+// of the warp call it.
+template <int ITEMS>
+__device__ __forceinline__ void place_words(const MemIngestArgs& a, DevState* st, const u64 (&word)[ITEMS],
+                                            const bool (&keep)[ITEMS], u64 (&sw)[ITEMS], u32* sbt_fail) {
+  const int lane = threadIdx.x & 31;
+  // batch the home-slot loads, then resolve
+  u64 pos[ITEMS], first[ITEMS];
+#pragma unroll
+  for (int k = 0; k < ITEMS; ++k) {
+    pos[k] = sbt_hash((word[k] >> 12) + 1ull) & a.tab.mask;
+    // an L1-cached copy may still read 0 for a slot another SM just
+    // claimed; sbt_place then loses the CAS and reads the real key
+    first[k] = keep[k] ? a.tab.keys[pos[k]] : 0ull;
+  }
+  u32 slot[ITEMS];
+#pragma unroll
+  for (int k = 0; k < ITEMS; ++k) {
+    slot[k] = kNoSlot;
+    if (keep[k]) {
+      slot[k] = sbt_place(a.tab, (word[k] >> 12) + 1ull, pos[k], first[k]);
+      if (slot[k] == kNoSlot) {
+        *sbt_fail = 1u;
+        a.spill[atomicAdd(&st->n_spill, 1ull)] = word[k];
+      }
+    }
+  }
+  // all counting atomics in flight before any result is needed; this warp's
+  // counter stripe
+  const u32 stripe = (blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5)) & (u32)(kSbtStripes - 1);
+  u32* cnt_s = a.tab.cnt + (u64)stripe * (a.tab.mask + 1);
+  u32 peers[ITEMS], rb[ITEMS];
+#pragma unroll
+  for (int k = 0; k < ITEMS; ++k)
+    peers[k] = __match_any_sync(0xffffffffu, slot[k] != kNoSlot ? slot[k] : (0xFFFFFFE0u | (u32)lane));
+#pragma unroll
+  for (int k = 0; k < ITEMS; ++k) {
+    rb[k] = 0u;
+    if (slot[k] != kNoSlot && lane == __ffs(peers[k]) - 1) rb[k] = atomicAdd(&cnt_s[slot[k]], (u32)__popc(peers[k]));
+  }
+#pragma unroll
+  for (int k = 0; k < ITEMS; ++k) {
+    const u32 r = __shfl_sync(0xffffffffu, rb[k], __ffs(peers[k]) - 1) + (u32)__popc(peers[k] & ((1u << lane) - 1u));
+    if (slot[k] != kNoSlot && r >= kRankLimit) *sbt_fail = 1u;
+    sw[k] = slot[k] != kNoSlot ? (((u64)r << kRankShift) | ((u64)stripe << 32) | (slot[k] << 12) |
+                                  (u32)(word[k] & 0xFFFull))
+                               : (u64)kSlotWordNone;
+  }
+}
 
 // One pass over the 16-byte events. Sort plan (HASH = false): writes the
 // 64-bit sort word of every kept event. Hash plan (HASH = true): places the
@@ -29,19 +82,15 @@ constexpr int kIngestThreads = 256;
 // its full word goes to the spill list. FILTER: the space mask drops events,
 // so outputs are compacted behind one atomicAdd per block-tile. FULL: a.n is
 // a multiple of the block tile, so every event slot is valid (no tests).
-// WORDS: the input is 64-bit words of kept accesses (the byte-granular
-// path), whose work-items and addresses were handled by the expansion.
-template <bool FILTER, bool HASH, bool FULL, bool WORDS>
+template <bool FILTER, bool HASH, bool FULL>
 __global__ void __launch_bounds__(kIngestThreads, HASH ? 4 : 3) k_mem_ingest(MemIngestArgs a) {
-  static_assert(!(WORDS && FILTER), "words are filtered by the expansion");
-  constexpr int ITEMS = HASH ? 4 : 8;
+  constexpr int ITEMS = HASH ? kHashItems : 8;
   __shared__ u64 red64[32];
   __shared__ u32 red32[32];
   __shared__ u32 scan_tot[33];
   __shared__ u64 s_base;
   DevState* st = &a.arena->st;
   const uint4* ev = reinterpret_cast<const uint4*>(a.ev);
-  const u64* win = reinterpret_cast<const u64*>(a.ev);
   const int lane = threadIdx.x & 31;
   u64 writes = 0, wor = 0, wand = ~0ull, kept = 0;
   u32 wmin = 0xFFFFFFFFu, wmax = 0u, err = 0u, sbt_fail = 0u;
@@ -56,21 +105,10 @@ __global__ void __launch_bounds__(kIngestThreads, HASH ? 4 : 3) k_mem_ingest(Mem
     for (int k = 0; k < ITEMS; ++k) {
       const u64 i = t0 + (u64)k * kIngestThreads + threadIdx.x;
       valid[k] = FULL || i < a.n;
-      if (WORDS) word[k] = valid[k] ? __ldcs(win + i) : 0ull;
-      else e[k] = valid[k] ? __ldcs(ev + i) : make_uint4(0u, 0u, 0u, 0u);
+      e[k] = valid[k] ? __ldcs(ev + i) : make_uint4(0u, 0u, 0u, 0u);
     }
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
-      if (WORDS) {
-        keep[k] = valid[k];
-        if (keep[k]) {
-          ++nkeep;
-          writes += word[k] & 1ull;
-          wor |= word[k];
-          wand &= word[k];
-        }
-        continue;
-      }
       const u64 addr = (u64)e[k].x | ((u64)e[k].y << 32);
       const u32 wi = e[k].z;
       const u32 flags = (e[k].w >> 8) & 0xFFu;
@@ -95,50 +133,7 @@ __global__ void __launch_bounds__(kIngestThreads, HASH ? 4 : 3) k_mem_ingest(Mem
     }
     kept += nkeep;
     u64 sw[ITEMS];
-    if (HASH) {
-      // batch the home-slot loads, then resolve
-      u64 pos[ITEMS], first[ITEMS];
-#pragma unroll
-      for (int k = 0; k < ITEMS; ++k) {
-        pos[k] = sbt_hash((word[k] >> 12) + 1ull) & a.tab.mask;
-        // an L1-cached copy may still read 0 for a slot another SM just
-        // claimed; sbt_place then loses the CAS and reads the real key
-        first[k] = keep[k] ? a.tab.keys[pos[k]] : 0ull;
-      }
-      u32 slot[ITEMS];
-#pragma unroll
-      for (int k = 0; k < ITEMS; ++k) {
-        slot[k] = kNoSlot;
-        if (keep[k]) {
-          slot[k] = sbt_place(a.tab, (word[k] >> 12) + 1ull, pos[k], first[k]);
-          if (slot[k] == kNoSlot) {
-            sbt_fail = 1u;
-            a.spill[atomicAdd(&st->n_spill, 1ull)] = word[k];
-          }
-        }
-      }
-      // all counting atomics in flight before any result is needed; this
-      // warp's counter stripe
-      const u32 stripe = (blockIdx.x * (kIngestThreads / 32) + (threadIdx.x >> 5)) & (u32)(kSbtStripes - 1);
-      u32* cnt_s = a.tab.cnt + (u64)stripe * (a.tab.mask + 1);
-      u32 peers[ITEMS], rb[ITEMS];
-#pragma unroll
-      for (int k = 0; k < ITEMS; ++k)
-        peers[k] = __match_any_sync(0xffffffffu, slot[k] != kNoSlot ? slot[k] : (0xFFFFFFE0u | (u32)lane));
-#pragma unroll
-      for (int k = 0; k < ITEMS; ++k) {
-        rb[k] = 0u;
-        if (slot[k] != kNoSlot && lane == __ffs(peers[k]) - 1) rb[k] = atomicAdd(&cnt_s[slot[k]], (u32)__popc(peers[k]));
-      }
-#pragma unroll
-      for (int k = 0; k < ITEMS; ++k) {
-        const u32 r = __shfl_sync(0xffffffffu, rb[k], __ffs(peers[k]) - 1) + (u32)__popc(peers[k] & ((1u << lane) - 1u));
-        if (slot[k] != kNoSlot && r >= kRankLimit) sbt_fail = 1u;
-        sw[k] = slot[k] != kNoSlot ? (((u64)r << kRankShift) | ((u64)stripe << 32) | (slot[k] << 12) |
-                                      (u32)(word[k] & 0xFFFull))
-                                   : (u64)kSlotWordNone;
-      }
-    }
+    if (HASH) place_words<ITEMS>(a, st, word, keep, sw, &sbt_fail);
     if (FILTER) {
       // compact the kept outputs of this block-tile behind one atomicAdd
       const int w = threadIdx.x >> 5;
@@ -204,11 +199,8 @@ __global__ void __launch_bounds__(kIngestThreads, HASH ? 4 : 3) k_mem_ingest(Mem
 
 // Byte-granular addresses. A tile of kExpandTile events: k_expand_count sums
 // the sizes of its kept events (and marks every event's work-item),
-// k_expand_scan turns the tile sums into offsets, k_expand_write stages the
-// tile in shared memory with per-event offsets (each thread scans its own
-// kExpItems consecutive events) and then writes the words of the tile's
-// one-byte accesses in order, consecutive threads writing consecutive words;
-// a thread finds the event of output q by binary search over the offsets.
+// k_expand_scan turns the tile sums into the tiles' offsets, and
+// k_mem_ingest_bytes (below) ingests the tile's one-byte accesses there.
 constexpr int kExpThreads = 256;
 constexpr int kExpItems = (int)kExpandTile / kExpThreads;
 
@@ -285,24 +277,38 @@ __global__ void __launch_bounds__(1024) k_expand_scan(ExpandArgs a) {
   if (threadIdx.x == 0) *a.total = s_carry;
 }
 
-__global__ void __launch_bounds__(kExpThreads) k_expand_write(ExpandArgs a) {
-  __shared__ u64 s_word[kExpandTile];  // the event's first word (store bit, space, start address)
+// Byte-granular ingest: a block stages a tile of kExpandTile events in
+// shared memory -- each event's word at its start byte and the offset of its
+// first byte among the tile's kept bytes, as k_expand_count laid them out --
+// and forms the words of the tile's one-byte accesses on the fly,
+// kIngestThreads * ITEMS at a time in offset order, so that consecutive lanes
+// take consecutive bytes (a thread finds the event of byte q by binary search
+// over the offsets); the words go through the same placement as the event
+// ingest's and land at the tile's offset. Work-items and start addresses were
+// handled by k_expand_count.
+template <bool HASH>
+__global__ void __launch_bounds__(kIngestThreads, HASH ? 4 : 3) k_mem_ingest_bytes(MemIngestArgs a, const u64* tile_off) {
+  constexpr int ITEMS = HASH ? kHashItems : 8;
+  constexpr int EV = (int)kExpandTile / kIngestThreads;  // events each thread stages
+  __shared__ u64 s_word[kExpandTile];
   __shared__ u32 s_off[kExpandTile + 1];
-  __shared__ u32 s_wsum[kExpThreads / 32];
+  __shared__ u32 s_wsum[kIngestThreads / 32];
+  __shared__ u64 red64[32];
   __shared__ u32 red32[32];
+  DevState* st = &a.arena->st;
   const uint4* ev = reinterpret_cast<const uint4*>(a.ev);
-  u64* out = reinterpret_cast<u64*>(a.out);
-  const u32 ntiles = (u32)((a.n + kExpandTile - 1) / kExpandTile);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  u32 err = 0u;
+  u64 writes = 0, wor = 0, wand = ~0ull, kept = 0;
+  u32 err = 0u, sbt_fail = 0u;
+  const u32 ntiles = (u32)((a.n + kExpandTile - 1) / kExpandTile);
   for (u32 tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const u64 base = (u64)tile * kExpandTile;
-    u32 sz[kExpItems];
+    u32 sz[EV];
     u32 mine = 0u;
 #pragma unroll
-    for (int k = 0; k < kExpItems; ++k) {
-      const u32 j = threadIdx.x * kExpItems + k;
-      const uint4 e = base + j < a.n ? __ldg(ev + base + j) : make_uint4(0u, 0u, 0u, 0u);
+    for (int k = 0; k < EV; ++k) {
+      const u32 j = threadIdx.x * EV + k;
+      const uint4 e = base + j < a.n ? __ldcs(ev + base + j) : make_uint4(0u, 0u, 0u, 0u);
       const u32 space = (e.w >> 9) & 3u, store = (e.w >> 8) & 1u;
       const u64 addr = (u64)e.x | ((u64)e.y << 32);
       s_word[j] = ((u64)space << 62) | (addr << 1) | store;  // address bits above 60 are dropped here
@@ -320,33 +326,72 @@ __global__ void __launch_bounds__(kExpThreads) k_expand_write(ExpandArgs a) {
     u32 run = x - mine;
     for (int q = 0; q < w; ++q) run += s_wsum[q];
 #pragma unroll
-    for (int k = 0; k < kExpItems; ++k) {
-      s_off[threadIdx.x * kExpItems + k] = run;
+    for (int k = 0; k < EV; ++k) {
+      s_off[threadIdx.x * EV + k] = run;
       run += sz[k];
     }
-    if (threadIdx.x == kExpThreads - 1) s_off[kExpandTile] = run;
+    if (threadIdx.x == kIngestThreads - 1) s_off[kExpandTile] = run;
     __syncthreads();
     const u32 T = s_off[kExpandTile];
-    const u64 o0 = a.tile_off[tile];
-    for (u32 q = threadIdx.x; q < T; q += kExpThreads) {
-      // the last event whose offset is <= q; it touches at least one byte
-      u32 lo = 0u, hi = (u32)kExpandTile - 1u;
-      while (lo < hi) {
-        const u32 mid = (lo + hi + 1u) >> 1;
-        if (s_off[mid] <= q) lo = mid;
-        else hi = mid - 1u;
+    const u64 o0 = a.word_base + tile_off[tile];
+    for (u32 r0 = 0; r0 < T; r0 += kIngestThreads * ITEMS) {
+      u64 word[ITEMS];
+      bool keep[ITEMS];
+#pragma unroll
+      for (int k = 0; k < ITEMS; ++k) {
+        const u32 q = r0 + k * kIngestThreads + threadIdx.x;
+        keep[k] = q < T;
+        word[k] = 0ull;
+        if (keep[k]) {
+          // the last event whose offset is <= q; it touches at least one byte
+          u32 lo = 0u, hi = (u32)kExpandTile - 1u;
+          while (lo < hi) {
+            const u32 mid = (lo + hi + 1u) >> 1;
+            if (s_off[mid] <= q) lo = mid;
+            else hi = mid - 1u;
+          }
+          // one byte further is 2 in word units; the sum stays within 62
+          // bits unless the byte leaves the 61-bit domain
+          const u64 w0 = s_word[lo];
+          word[k] = w0 + 2ull * (u64)(q - s_off[lo]);
+          if ((word[k] ^ w0) >> 62) err |= kErrAddr;
+          ++kept;
+          writes += word[k] & 1ull;
+          wor |= word[k];
+          wand &= word[k];
+        }
       }
-      // one byte further is 2 in word units; the sum stays within 62 bits
-      // unless the byte leaves the 61-bit domain
-      const u64 w0 = s_word[lo];
-      const u64 wd = w0 + 2ull * (u64)(q - s_off[lo]);
-      if ((wd ^ w0) >> 62) err |= kErrAddr;
-      out[o0 + q] = wd;
+      u64 sw[ITEMS];
+      if (HASH) place_words<ITEMS>(a, st, word, keep, sw, &sbt_fail);
+#pragma unroll
+      for (int k = 0; k < ITEMS; ++k) {
+        const u32 q = r0 + k * kIngestThreads + threadIdx.x;
+        if (keep[k]) {
+          if (HASH) a.slotw[o0 + q] = sw[k];
+          else a.words[o0 + q] = word[k];
+        }
+      }
     }
     __syncthreads();  // the tile's staging is refilled next
   }
+  writes = block_reduce(writes, OpAdd(), 0ull, red64);
+  wor = block_reduce(wor, OpOr(), 0ull, red64);
+  wand = block_reduce(wand, OpAnd(), ~0ull, red64);
+  kept = block_reduce(kept, OpAdd(), 0ull, red64);
+  const u64 reads = kept - writes;
   err = block_reduce(err, OpOr(), 0u, red32);
-  if (threadIdx.x == 0 && err) atomicOr(&a.arena->st.err, err);
+  sbt_fail = block_reduce(sbt_fail, OpOr(), 0u, red32);
+  if (threadIdx.x == 0) {
+    if (sbt_fail) atomicOr(&st->sbt_overflow, 1u);
+    if (reads) atomicAdd(&st->total_reads, reads);
+    if (writes) atomicAdd(&st->total_writes, writes);
+    if (kept) {
+      atomicOr(&st->mem_or, wor);
+      atomicAnd(&st->mem_and, wand);
+      atomicAdd(&st->n_words, kept);
+    }
+    if (err) atomicOr(&st->err, err);
+  }
 }
 
 constexpr int kLvThreads = kTileThreads;
@@ -428,43 +473,32 @@ __global__ void __launch_bounds__(kLvThreads) k_mem_levels(LevelArgs a) {
 
 void launch_mem_ingest(const MemIngestArgs& a, cudaStream_t s) {
   if (a.n == 0) return;
-  const u64 per_block = (u64)kIngestThreads * (a.use_tab ? 4 : 8);
+  const u64 per_block = (u64)kIngestThreads * (a.use_tab ? kHashItems : 8);
   const u64 cap = a.use_tab ? 152ull * 16 : 152ull * 8;
   auto grid = [&](u64 n) { return (unsigned)std::min<u64>((n + per_block - 1) / per_block, cap); };
-  const bool filter = a.space_mask != 0xFu && !a.words_in;
+  const bool filter = a.space_mask != 0xFu;
   if (filter) {
-    if (a.use_tab) k_mem_ingest<true, true, false, false><<<grid(a.n), kIngestThreads, 0, s>>>(a);
-    else k_mem_ingest<true, false, false, false><<<grid(a.n), kIngestThreads, 0, s>>>(a);
+    if (a.use_tab) k_mem_ingest<true, true, false><<<grid(a.n), kIngestThreads, 0, s>>>(a);
+    else k_mem_ingest<true, false, false><<<grid(a.n), kIngestThreads, 0, s>>>(a);
     count_launches(1);
     return;
   }
   // whole block tiles without bounds tests, then the ragged tail
   const u64 n_full = a.n / per_block * per_block;
-  const size_t unit = a.words_in ? 8 : 16;
   if (n_full) {
     MemIngestArgs f = a;
     f.n = n_full;
-    if (a.words_in) {
-      if (a.use_tab) k_mem_ingest<false, true, true, true><<<grid(n_full), kIngestThreads, 0, s>>>(f);
-      else k_mem_ingest<false, false, true, true><<<grid(n_full), kIngestThreads, 0, s>>>(f);
-    } else {
-      if (a.use_tab) k_mem_ingest<false, true, true, false><<<grid(n_full), kIngestThreads, 0, s>>>(f);
-      else k_mem_ingest<false, false, true, false><<<grid(n_full), kIngestThreads, 0, s>>>(f);
-    }
+    if (a.use_tab) k_mem_ingest<false, true, true><<<grid(n_full), kIngestThreads, 0, s>>>(f);
+    else k_mem_ingest<false, false, true><<<grid(n_full), kIngestThreads, 0, s>>>(f);
     count_launches(1);
   }
   if (a.n > n_full) {
     MemIngestArgs t = a;
-    t.ev = static_cast<const char*>(a.ev) + unit * n_full;
+    t.ev = static_cast<const char*>(a.ev) + 16 * n_full;
     t.n = a.n - n_full;
     t.word_base = a.word_base + n_full;
-    if (a.words_in) {
-      if (a.use_tab) k_mem_ingest<false, true, false, true><<<grid(t.n), kIngestThreads, 0, s>>>(t);
-      else k_mem_ingest<false, false, false, true><<<grid(t.n), kIngestThreads, 0, s>>>(t);
-    } else {
-      if (a.use_tab) k_mem_ingest<false, true, false, false><<<grid(t.n), kIngestThreads, 0, s>>>(t);
-      else k_mem_ingest<false, false, false, false><<<grid(t.n), kIngestThreads, 0, s>>>(t);
-    }
+    if (a.use_tab) k_mem_ingest<false, true, false><<<grid(t.n), kIngestThreads, 0, s>>>(t);
+    else k_mem_ingest<false, false, false><<<grid(t.n), kIngestThreads, 0, s>>>(t);
     count_launches(1);
   }
 }
@@ -483,11 +517,12 @@ void launch_expand_count(const ExpandArgs& a, cudaStream_t s) {
   count_launches(2);
 }
 
-void launch_expand_write(const ExpandArgs& a, cudaStream_t s) {
+void launch_mem_ingest_bytes(const MemIngestArgs& a, const u64* tile_off, cudaStream_t s) {
   if (a.n == 0) return;
   const u64 ntiles = (a.n + kExpandTile - 1) / kExpandTile;
-  const unsigned g = (unsigned)std::min<u64>(ntiles, (u64)a.sm_count * 8);
-  k_expand_write<<<g, kExpThreads, 0, s>>>(a);
+  const unsigned g = (unsigned)std::min<u64>(ntiles, a.use_tab ? 152ull * 16 : 152ull * 8);
+  if (a.use_tab) k_mem_ingest_bytes<true><<<g, kIngestThreads, 0, s>>>(a, tile_off);
+  else k_mem_ingest_bytes<false><<<g, kIngestThreads, 0, s>>>(a, tile_off);
   count_launches(1);
 }
 

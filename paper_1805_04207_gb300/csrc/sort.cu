@@ -33,6 +33,15 @@ constexpr int kScanBlock = kScanThreads * kScanItems;
 
 __device__ __forceinline__ u64 eff_mask(const SortDesc& d) { return d.dmask ? (d.mask & *d.dmask) : d.mask; }
 
+// Tiles holding keys: the device count decides, so that a sort sized for a
+// capacity (the overflow list, the pattern words) works on what is there. The
+// digit counts are laid out digit-major over these tiles.
+__device__ __forceinline__ u32 live_tiles(const SortDesc& d) {
+  const u64 n = umin64(*d.n, d.n_cap);
+  const u64 t = (n + kSortTile - 1) / kSortTile;
+  return (u32)(t < (u64)d.ntiles ? t : (u64)d.ntiles);
+}
+
 __device__ __forceinline__ bool pass_shift(const SortDesc& d, int pass, int* shift) {
   int sh = d.lo_bit + 8 * pass;
   *shift = sh;
@@ -44,6 +53,8 @@ __device__ __forceinline__ bool pass_shift(const SortDesc& d, int pass, int* shi
 __global__ void __launch_bounds__(kSortThreads) k_hist(SortDesc d, int pass) {
   int shift;
   if (!pass_shift(d, pass, &shift)) return;
+  const u32 nt = live_tiles(d);
+  if (blockIdx.x >= nt) return;
   __shared__ u32 h[kWarps][256];
   for (int i = threadIdx.x; i < kWarps * 256; i += kSortThreads) (&h[0][0])[i] = 0;
   __syncthreads();
@@ -61,7 +72,7 @@ __global__ void __launch_bounds__(kSortThreads) k_hist(SortDesc d, int pass) {
   u32 s = 0;
 #pragma unroll
   for (int q = 0; q < kWarps; ++q) s += h[q][threadIdx.x];
-  d.counts[(u64)threadIdx.x * d.ntiles + blockIdx.x] = s;
+  d.counts[(u64)threadIdx.x * nt + blockIdx.x] = s;
 }
 
 template <typename T>
@@ -94,10 +105,13 @@ __device__ __forceinline__ T block_excl_scan(T x, T* total, T* warp_tot) {
   return r;
 }
 
-// Exclusive scan of the counts, gated on the same pass predicate.
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(SortDesc d, int pass, u64 len) {
+// Exclusive scan of the counts of the live tiles, gated on the same pass
+// predicate.
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(SortDesc d, int pass) {
   int shift;
   if (!pass_shift(d, pass, &shift)) return;
+  const u64 len = 256ull * live_tiles(d);
+  if ((u64)blockIdx.x * kScanBlock >= len) return;
   __shared__ u32 wt[33];
   u64 base = (u64)blockIdx.x * kScanBlock + (u64)threadIdx.x * kScanItems;
   u32 s = 0;
@@ -109,9 +123,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(SortDesc d, int pa
   if (threadIdx.x == 0) d.block_sums[blockIdx.x] = tot;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_top(SortDesc d, int pass, u32 nb) {
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(SortDesc d, int pass) {
   int shift;
   if (!pass_shift(d, pass, &shift)) return;
+  const u32 nb = (u32)((256ull * live_tiles(d) + kScanBlock - 1) / kScanBlock);
   __shared__ u32 wt[33];
   u32 carry = 0;
   for (u32 c0 = 0; c0 < nb; c0 += kScanBlock) {
@@ -135,9 +150,11 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_top(SortDesc d, int pass,
   }
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_down(SortDesc d, int pass, u64 len) {
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(SortDesc d, int pass) {
   int shift;
   if (!pass_shift(d, pass, &shift)) return;
+  const u64 len = 256ull * live_tiles(d);
+  if ((u64)blockIdx.x * kScanBlock >= len) return;
   __shared__ u32 wt[33];
   u64 base = (u64)blockIdx.x * kScanBlock + (u64)threadIdx.x * kScanItems;
   u32 v[kScanItems];
@@ -159,6 +176,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(SortDesc d, int pass
 __global__ void __launch_bounds__(kSortThreads) k_scatter(SortDesc d, int pass) {
   int shift;
   if (!pass_shift(d, pass, &shift)) return;
+  const u32 nt = live_tiles(d);
+  if (blockIdx.x >= nt) return;
   __shared__ u32 wcnt[kWarps][256];
   __shared__ u32 dofs[256];
   __shared__ u32 gofs[256];
@@ -204,7 +223,7 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(SortDesc d, int pass) 
     u32 all;
     u32 ex = block_excl_scan<u32>(tot, &all, wt);
     dofs[dg] = ex;
-    gofs[dg] = d.counts[(u64)dg * d.ntiles + blockIdx.x];
+    gofs[dg] = d.counts[(u64)dg * nt + blockIdx.x];
   }
   __syncthreads();
 #pragma unroll
@@ -253,9 +272,9 @@ void sort_keys(const SortDesc& d, cudaStream_t s, u32 host_passes) {
     if (!((host_passes >> p) & 1u)) continue;
     ++launched;
     k_hist<<<d.ntiles, kSortThreads, 0, s>>>(d, p);
-    k_scan_reduce<<<nb, kScanThreads, 0, s>>>(d, p, len);
-    k_scan_top<<<1, kScanThreads, 0, s>>>(d, p, nb);
-    k_scan_down<<<nb, kScanThreads, 0, s>>>(d, p, len);
+    k_scan_reduce<<<nb, kScanThreads, 0, s>>>(d, p);
+    k_scan_top<<<1, kScanThreads, 0, s>>>(d, p);
+    k_scan_down<<<nb, kScanThreads, 0, s>>>(d, p);
     k_scatter<<<d.ntiles, kSortThreads, 0, s>>>(d, p);
     k_flip<<<1, 1, 0, s>>>(d, p);
   }

@@ -372,7 +372,7 @@ __global__ void __launch_bounds__(kCsThreads) k_cs_scatter(SiteSortArgs a) {
   }
 }
 
-constexpr int kSpThreads = 512;
+constexpr int kSpThreads = 1024;
 constexpr int kPatSmem = 1024;  // pattern counts below this are counted in shared memory first
 constexpr int kSpBinsLog = 15;
 constexpr int kSpBitWords = (int)((kSiteMaxLen + 32) / 32) + 2;

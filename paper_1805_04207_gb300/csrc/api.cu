@@ -97,6 +97,9 @@ struct aiwc_handle {
   aiwc_config cfg;
   cudaStream_t stream = nullptr;
   cudaStream_t copy_stream = nullptr;
+  // the branch reduction runs beside the memory reduction (hash plan)
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t ev_copied[2] = {nullptr, nullptr};
   cudaEvent_t ev_free[2] = {nullptr, nullptr};
   int stage_next = 0;
@@ -195,6 +198,7 @@ aiwc_status cuda_fail(aiwc_handle* h, const char* what, cudaError_t e) {
 struct StageScope {
   aiwc_handle* h;
   int stage;
+  cudaStream_t s;
   cudaEvent_t a = nullptr, b = nullptr;
   cudaEvent_t take() {
     cudaEvent_t e = nullptr;
@@ -207,15 +211,16 @@ struct StageScope {
     }
     return e;
   }
-  StageScope(aiwc_handle* hh, int st) : h(hh), stage(st) {
+  // s: the stream the stage's kernels go to (the handle's stream by default)
+  StageScope(aiwc_handle* hh, int st, cudaStream_t ss = nullptr) : h(hh), stage(st), s(ss ? ss : hh->stream) {
     if (!h->timing) return;
     a = take();
     b = take();
-    if (a) cudaEventRecord(a, h->stream);
+    if (a) cudaEventRecord(a, s);
   }
   void end() {
     if (!a || !b) return;
-    cudaEventRecord(b, h->stream);
+    cudaEventRecord(b, s);
     h->intervals.push_back({stage, a, b});
     a = b = nullptr;
   }
@@ -760,8 +765,12 @@ aiwc_status aiwc_create(const aiwc_config* cfg, aiwc_handle** out) {
   cudaError_t e;
   if ((e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, cfg->device)) != cudaSuccess)
     return bail(cuda_fail(nullptr, "cudaDeviceGetAttribute", e));
-  if ((e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking)) != cudaSuccess)
+  if ((e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking)) != cudaSuccess)
     return bail(cuda_fail(nullptr, "cudaStreamCreate", e));
+  if ((e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming)) != cudaSuccess)
+    return bail(cuda_fail(nullptr, "cudaEventCreate", e));
   for (int i = 0; i < 2; ++i) {
     if ((e = cudaEventCreateWithFlags(&h->ev_copied[i], cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&h->ev_free[i], cudaEventDisableTiming)) != cudaSuccess)
@@ -1233,17 +1242,17 @@ void enqueue_part1(aiwc_handle* h, cudaStream_t st, const Plan& p) {
   if (p.site_sort) {
     // the site list, n_sites and the longest site; the sorted output follows
     // once the branch path is chosen
-    StageScope sc(h, kStBrSort);
+    StageScope sc(h, kStBrSort, st);
     launch_site_sort_count(site_sort_args(h), st);
     return;
   }
   SortDesc bsort = branch_sort_desc(h);
   {
-    StageScope sc(h, kStBrSort);
+    StageScope sc(h, kStBrSort, st);
     launch_branch_mask(h->arena, st);
     sort_keys(bsort, st, p.br_passes);
   }
-  StageScope sc(h, kStWindows);
+  StageScope sc(h, kStWindows, st);
   launch_site_heads(site_args(h, bsort), st);
   if (p.gated) launch_persite_decide(h->arena, h->cfg.history_len, h->c_sites_cap, h->cfg.plan != 1, st);
 }
@@ -1251,8 +1260,10 @@ void enqueue_part1(aiwc_handle* h, cudaStream_t st, const Plan& p) {
 aiwc_status enqueue_finalize(aiwc_handle* h, cudaStream_t st);
 
 // Everything after the branch-path choice, the result copies and the reset.
-aiwc_status enqueue_part2(aiwc_handle* h, cudaStream_t st, const Plan& p) {
-  const u64 n_mem = h->n_mem, n_br = h->n_br, n_runs = h->n_runs;
+// The memory reduction after the ingest: segment scatter and walks (hash
+// plan) or the sort and run lengths (sort plan).
+void enqueue_mem_path(aiwc_handle* h, cudaStream_t st, const Plan& p) {
+  const u64 n_mem = h->n_mem;
   DevState* dst = &h->arena->st;
   u64* over = (u64*)h->over_a.p;
   const u64 over_cap = h->c_over_cap;
@@ -1281,18 +1292,18 @@ aiwc_status enqueue_part2(aiwc_handle* h, cudaStream_t st, const Plan& p) {
     ha.big_hist = (u32*)h->mem_a.p;
     ha.big_cap = mem_hash_big_segments(n_mem, h->mem_a.cap, p.seg_shift);
     {
-      StageScope sc(h, kStMemScatter);
+      StageScope sc(h, kStMemScatter, st);
       launch_mem_hash_scatter(ha, st);
     }
-    StageScope sc(h, kStMemLevels);
+    StageScope sc(h, kStMemLevels, st);
     launch_mem_hash_segments(ha, st);
   } else if (n_mem) {
     SortDesc d = sort_desc(h, h->mem_a, h->mem_b, kSortMem, &dst->n_words, &dst->mem_or, &dst->mem_and, ~0ull, n_mem);
     {
-      StageScope sc(h, kStMemSort);
+      StageScope sc(h, kStMemSort, st);
       sort_keys(d, st, active_passes(h->h_state->mem_or, h->h_state->mem_and, ~0ull));
     }
-    StageScope sc(h, kStMemLevels);
+    StageScope sc(h, kStMemLevels, st);
     LevelArgs la;
     la.a = d.a;
     la.b = d.b;
@@ -1307,6 +1318,16 @@ aiwc_status enqueue_part2(aiwc_handle* h, cudaStream_t st, const Plan& p) {
     launch_mem_levels(la, st);
     launch_runs_fixup(0, la.tiles, la.ntiles, &dst->n_words, 0, kLevels, over, over_cap, h->arena, st);
   }
+}
+
+// The branch reduction after the branch sort: per-site patterns or the global
+// path (windows, pattern sort, pattern runs).
+void enqueue_branch_path(aiwc_handle* h, cudaStream_t st, const Plan& p) {
+  const u64 n_br = h->n_br;
+  DevState* dst = &h->arena->st;
+  u64* over = (u64*)h->over_a.p;
+  const u64 over_cap = h->c_over_cap;
+  const int grid = h->sm_count * 3;
   if (n_br) {
     // per-site patterns in shared memory, or the global path (windows,
     // pattern sort, pattern runs); with `gated` both are launched and a
@@ -1315,13 +1336,13 @@ aiwc_status enqueue_part2(aiwc_handle* h, cudaStream_t st, const Plan& p) {
     SortDesc bsort = branch_sort_desc(h);
     if (p.site_sort) {
       // the per-site path needs only the outcome bits: one byte per event
-      StageScope sc(h, kStBrSort);
+      StageScope sc(h, kStBrSort, st);
       SiteSortArgs ss = site_sort_args(h);
       if (p.per_site && !h->cfg.history_scope) ss.dst8 = (uint8_t*)h->br_b.p;
       launch_site_sort_scatter(ss, st);
     }
     if (p.gated || p.per_site) {
-      StageScope sc(h, kStPatRuns);
+      StageScope sc(h, kStPatRuns, st);
       SiteArgs sa = site_args(h, bsort);
       sa.gate = gate;
       sa.gate_want = 1;
@@ -1348,7 +1369,7 @@ aiwc_status enqueue_part2(aiwc_handle* h, cudaStream_t st, const Plan& p) {
       wa.arena = h->arena;
       wa.grid = grid;
       {
-        StageScope sc(h, kStWindows);
+        StageScope sc(h, kStWindows, st);
         launch_branch_windows(wa, st);
         launch_runs_fixup(1, wa.tiles, wa.ntiles, nullptr, n_br, 1, over, over_cap, h->arena, st, gate, 0,
                           h->cfg.history_scope ? 0u : h->cfg.history_len);
@@ -1358,10 +1379,10 @@ aiwc_status enqueue_part2(aiwc_handle* h, cudaStream_t st, const Plan& p) {
       ps.gate = gate;
       ps.gate_want = 0;
       {
-        StageScope sc(h, kStPatSort);
+        StageScope sc(h, kStPatSort, st);
         sort_keys(ps, st);
       }
-      StageScope sc(h, kStPatRuns);
+      StageScope sc(h, kStPatRuns, st);
       PatternArgs pa;
       pa.gate = gate;
       pa.gate_want = 0;
@@ -1381,14 +1402,21 @@ aiwc_status enqueue_part2(aiwc_handle* h, cudaStream_t st, const Plan& p) {
                         st, gate, 0);
     }
   }
-  // instructions: chain each work-item's runs
+}
+
+// Instruction runs chained per work-item, then (unless deferred) the finalisation.
+aiwc_status enqueue_tail(aiwc_handle* h, cudaStream_t st, const Plan& p) {
+  const u64 n_runs = h->n_runs;
+  DevState* dst = &h->arena->st;
+  u64* over = (u64*)h->over_a.p;
+  const u64 over_cap = h->c_over_cap;
   if (n_runs) {
     SortDesc d = sort_desc(h, h->rk_a, h->rk_b, kSortRuns, &dst->n_runs, &dst->run_or, &dst->run_and, ~0ull, n_runs);
     {
-      StageScope sc(h, kStRunSort);
+      StageScope sc(h, kStRunSort, st);
       sort_keys(d, st, p.run_passes);
     }
-    StageScope sc(h, kStCombine);
+    StageScope sc(h, kStCombine, st);
     CombineArgs ca;
     ca.a = d.a;
     ca.b = d.b;
@@ -1404,6 +1432,13 @@ aiwc_status enqueue_part2(aiwc_handle* h, cudaStream_t st, const Plan& p) {
   return enqueue_finalize(h, st);
 }
 
+// Every stage after the branch-path choice, in one stream.
+aiwc_status enqueue_part2(aiwc_handle* h, cudaStream_t st, const Plan& p) {
+  enqueue_mem_path(h, st, p);
+  enqueue_branch_path(h, st, p);
+  return enqueue_tail(h, st, p);
+}
+
 // The end of an invocation: opcode distribution, work-item count, overflow
 // sort, the finalize kernel, the result copies and the reset.
 aiwc_status enqueue_finalize(aiwc_handle* h, cudaStream_t st) {
@@ -1411,7 +1446,7 @@ aiwc_status enqueue_finalize(aiwc_handle* h, cudaStream_t st) {
   u64* over = (u64*)h->over_a.p;
   const u64 over_cap = h->c_over_cap;
   {
-    StageScope fin_scope(h, kStFinalize);
+    StageScope fin_scope(h, kStFinalize, st);
     launch_opcode_dist((const u64*)h->d_hist, h->cfg.n_opcodes, over, over_cap, h->arena, st);
     launch_wi_count(h->wi_bitmap, h->arena, st);
     SortDesc d = sort_desc(h, h->over_a, h->over_b, kSortOver, &dst->n_over, &dst->over_or, &dst->over_and, ~0ull,
@@ -1503,16 +1538,33 @@ aiwc_status reduce_current(aiwc_handle* h, bool defer_finalize) {
   Plan p;
   plan_from_ingest(h, &p);
   p.defer_finalize = defer_finalize;
-  enqueue_part1(h, st, p);
+  // In the hash plan the memory and branch reductions share no scratch
+  // buffer (both only add to their own distributions and append to the
+  // overflow list atomically): the branch reduction runs on the side stream,
+  // forked after the ingest and joined before the tail.
+  const bool split = p.hash_ok && h->n_br != 0;
+  cudaStream_t sb = split ? h->side_stream : st;
+  if (split) {
+    CK(cudaEventRecord(h->ev_fork, st));
+    CK(cudaStreamWaitEvent(sb, h->ev_fork, 0));
+    enqueue_mem_path(h, st, p);
+  }
+  enqueue_part1(h, sb, p);
   if (h->n_br) {
-    // the branch path depends on the longest site
-    CK(cudaMemcpyAsync(h->h_state, &h->arena->st, sizeof(DevState), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    // the branch path depends on the longest site (only the branch fields of
+    // the copy are read: the memory reduction may be running meanwhile)
+    CK(cudaMemcpyAsync(h->h_state, &h->arena->st, sizeof(DevState), cudaMemcpyDeviceToHost, sb));
+    CK(cudaStreamSynchronize(sb));
     const DevState& hs = *h->h_state;
     p.per_site = h->cfg.history_len <= kSiteMaxHist && hs.br_site_max <= kSiteMaxLen &&
                  hs.n_sites <= h->c_sites_cap && h->cfg.plan != 1;
   }
-  return enqueue_part2(h, st, p);
+  if (!split) return enqueue_part2(h, st, p);
+  enqueue_branch_path(h, sb, p);
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(h->ev_join, sb));
+  CK(cudaStreamWaitEvent(st, h->ev_join, 0));
+  return enqueue_tail(h, st, p);
 }
 
 // Partitioned invocation: each partition is pushed to the device and reduced
@@ -1769,6 +1821,12 @@ aiwc_status aiwc_destroy(aiwc_handle* h) {
     cudaEventDestroy(iv.b);
   }
   for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->side_stream) {
+    cudaStreamSynchronize(h->side_stream);
+    cudaStreamDestroy(h->side_stream);
+  }
   if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
   delete h;
   return AIWC_OK;
@@ -1786,7 +1844,8 @@ bool aiwc::handle_config_matches(const aiwc_handle* h, const aiwc_config* c) {
   const aiwc_config& a = h->cfg;
   return a.history_len == c->history_len && a.cover_num == c->cover_num && a.cover_den == c->cover_den &&
          a.n_opcodes == c->n_opcodes && a.space_mask == (c->space_mask & 0xFu) && a.precision == c->precision &&
-         a.plan == c->plan && a.max_work_items == c->max_work_items && a.table_slots == c->table_slots;
+         a.plan == c->plan && a.max_work_items == c->max_work_items && a.table_slots == c->table_slots &&
+         a.byte_addresses == c->byte_addresses && a.history_scope == c->history_scope;
 }
 
 void aiwc::handle_set_budget(aiwc_handle* h, uint64_t bytes) { h->cfg.hbm_budget = bytes; }

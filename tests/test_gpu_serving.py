@@ -99,3 +99,22 @@ def test_serving_admission_limits(P):
         c = srv.open(700 << 20, max_work_items=1 << 20, table_slots=1 << 12)
         assert c is not None
         c.wait()
+
+
+def test_serving_job_options_are_honoured(P):
+    """A slot's handle is reused only by a job with the same metric options:
+    jobs that switch byte-granular addresses and history scope on and off in
+    one slot each get their own options' results."""
+    from paper_1805_04207_gb300.serving import Server
+    from tests.helpers import random_trace
+    tr = random_trace(5, n_mem=3000, n_br=3000, n_wi=8, n_sites=5, addr_pool=300, addr_span_bits=14,
+                      size_choices=[1, 2, 4, 8])
+    with Server(max_jobs=1, workers=1, hbm_budget=2 << 30) as srv:
+        for opts in (dict(), dict(byte_addresses=1), dict(history_scope=1), dict(byte_addresses=1, history_scope=1),
+                     dict()):
+            job = srv.open(256 << 20, n_opcodes=tr.n_opcodes, history_len=3, max_work_items=1 << 20,
+                           table_slots=1 << 12, **opts)
+            assert job is not None
+            _push_chunks(job, tr)
+            r = job.wait(want_hist=True)
+            assert_parity(r, oracle.compute(tr, history_len=3, **opts))

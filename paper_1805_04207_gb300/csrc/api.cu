@@ -1503,6 +1503,7 @@ aiwc_status recover(aiwc_handle* h) {
   h->replaying = false;
   h->part_err = 0;
   for (auto& pb : h->parts) pb.clear();
+  cudaStreamSynchronize(h->side_stream);
   cudaGetLastError();
   if (reset_device_state(h, h->stream) == AIWC_OK && cudaStreamSynchronize(h->stream) == cudaSuccess) h->broken = false;
   return AIWC_ESTATE;
@@ -1798,6 +1799,7 @@ aiwc_status aiwc_destroy(aiwc_handle* h) {
   if (!h) return AIWC_OK;
   DeviceGuard g(h->cfg.device);
   if (h->stream || h->copy_stream) cudaStreamSynchronize(h->stream);
+  if (h->side_stream) cudaStreamSynchronize(h->side_stream);
   DevBuf* bufs[] = {&h->mem_a, &h->mem_b, &h->br_a, &h->br_b, &h->pat_a, &h->pat_b, &h->rk_a, &h->rk_b,
                     &h->run_sum, &h->over_a, &h->over_b, &h->counts, &h->bsums, &h->tiles, &h->stage[0],
                     &h->stage[1], &h->desc, &h->sbt, &h->sbt_scan, &h->sites, &h->over_total,
@@ -1823,10 +1825,7 @@ aiwc_status aiwc_destroy(aiwc_handle* h) {
   for (cudaEvent_t e : h->event_pool) cudaEventDestroy(e);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
-  if (h->side_stream) {
-    cudaStreamSynchronize(h->side_stream);
-    cudaStreamDestroy(h->side_stream);
-  }
+  if (h->side_stream) cudaStreamDestroy(h->side_stream);
   if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
   delete h;
   return AIWC_OK;

@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(kRbThreads) k_rebuild_words(const u64* slotw, 
   }
 }
 
-constexpr int kCocSmem = 256;  // group sizes below this are counted in shared memory
+constexpr int kCocSmem = 128;  // group sizes below this are counted in shared memory (more resident blocks than 256)
 
 // Adds `times` groups of size c at skip levels lo..lev (lo < lev only when the
 // low address bits are all zero, so that those levels group identically):

@@ -606,3 +606,26 @@ def test_history_scope_batched_and_partitioned(P):
             c.close()
     for t, o in zip(traces, expect):
         assert_parity(_run_partitioned(P, t, 8, history_len=3, history_scope=1), o)
+
+
+def test_options_in_a_batch(P):
+    """Handles with byte-granular addresses and per-(site, work-item)
+    histories reduced together in one batched graph, twice."""
+    from paper_1805_04207_gb300.api import compute_batch, push_trace
+    traces = [random_trace(61, n_mem=4000, n_br=3000, n_wi=12, n_sites=9, addr_pool=500, addr_span_bits=20,
+                           size_choices=[1, 2, 4, 8, 16]),
+              synth.large(seed=13, n_mem=200_001, n_br=100_000, n_wi=40, per_wi=300, zipf_distinct=1 << 14),
+              synth.tiny()]
+    cfgs = [dict(byte_addresses=1, history_len=2, history_scope=1), dict(byte_addresses=1),
+            dict(history_scope=1, history_len=3)]
+    expect = [oracle.compute(t, **c) for t, c in zip(traces, cfgs)]
+    chars = [P.Characterizer(n_opcodes=t.n_opcodes, max_work_items=1 << 24, **c) for t, c in zip(traces, cfgs)]
+    try:
+        for _ in range(2):
+            for c, t in zip(chars, traces):
+                push_trace(c, t.to("cuda"))
+            for g, o in zip(compute_batch(chars), expect):
+                assert_parity(g, o)
+    finally:
+        for c in chars:
+            c.close()

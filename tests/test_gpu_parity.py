@@ -629,3 +629,29 @@ def test_options_in_a_batch(P):
     finally:
         for c in chars:
             c.close()
+
+
+def test_repeated_invocations_identical(P):
+    """One handle reduces the same invocation twenty times (memory and branch
+    reductions on two streams at once): every result equals the oracle's and
+    the first result to the bit, so no ordering between the streams leaks in."""
+    tr = synth.large(seed=21, n_mem=1_000_003, n_br=400_001, n_wi=200, per_wi=500, zipf_distinct=1 << 16)
+    o = oracle.compute(tr)
+    from paper_1805_04207_gb300.api import push_trace
+    trd = tr.to("cuda")
+    with P.Characterizer(n_opcodes=tr.n_opcodes) as c:
+        first = None
+        for _ in range(20):
+            push_trace(c, trd)
+            g = c.compute()
+            if first is None:
+                first = g
+                assert_parity(g, o)
+            else:
+                for k, v in first.items():
+                    if k == "opcode_hist":
+                        assert np.array_equal(np.asarray(g[k]), np.asarray(v))
+                    elif isinstance(v, float) and math.isnan(v):
+                        assert math.isnan(g[k]), k
+                    else:
+                        assert g[k] == v, k

@@ -134,6 +134,9 @@ struct aiwc_handle {
   u64 c_over_cap = 0, c_sites_cap = 0;
   size_t c_low_off = 0;
   u64 value_bound = 0;  // bound on ITB / IPT values >= kValDense (each uses kValDense instructions)
+  // run tables of host run pushes, one per staging buffer (pinned, so that
+  // their copies are asynchronous)
+  pinned_vector<unsigned char> tab_pin[2];
   // pending single-run pushes (host data, or device pointers)
   std::vector<uint16_t> pend_ops;
   std::vector<uint32_t> pend_wi;
@@ -389,13 +392,17 @@ aiwc_status runs_device(aiwc_handle* h, const u32* run_wi, const u64* run_off, c
 }
 
 // Host run tables: copied in batches whose opcode span fits a stage buffer.
+// Each batch's run table is built in the pinned table of its staging buffer
+// while the previous batch is still being copied; the host waits only before
+// it rewrites a table and, at the end, for the last copy (the caller may
+// reuse its opcodes when the call returns).
 aiwc_status runs_host(aiwc_handle* h, const uint32_t* run_wi, const uint64_t* run_off, const uint64_t* run_len,
                       size_t n_runs, const uint16_t* ops, size_t n_ops) {
   for (size_t r = 0; r < n_runs; ++r)
     if (run_off[r] > n_ops || run_len[r] > n_ops - run_off[r])
       return fail(h, AIWC_EINVAL, "instruction run reaches past its opcode array", false);
   size_t r0 = 0;
-  std::vector<unsigned char> tab;
+  int last = -1;
   while (r0 < n_runs) {
     u64 lo = run_off[r0], hi = run_off[r0] + run_len[r0];
     size_t r1 = r0 + 1;
@@ -413,7 +420,9 @@ aiwc_status runs_host(aiwc_handle* h, const uint32_t* run_wi, const uint64_t* ru
     const int k = h->stage_next;
     h->stage_next ^= 1;
     ENSURE(h->stage[k], std::max(need, kStageBytes), false);
-    tab.resize(nb * 24);
+    CK(cudaEventSynchronize(h->ev_copied[k]));  // this table's previous copy is done
+    auto& tab = h->tab_pin[k];
+    if (tab.size() < nb * 24) tab.resize(nb * 24);
     u64* offs = (u64*)tab.data();
     u64* lens = offs + nb;
     u32* wis = (u32*)(lens + nb);
@@ -432,9 +441,10 @@ aiwc_status runs_host(aiwc_handle* h, const uint32_t* run_wi, const uint64_t* ru
                                 (const u64*)(base + ops_bytes + nb * 8), nb, (const uint16_t*)base, hi - lo, hi - lo);
     if (s != AIWC_OK) return s;
     CK(cudaEventRecord(h->ev_free[k], h->stream));
-    CK(cudaEventSynchronize(h->ev_copied[k]));  // tab is reused; the caller may reuse ops
+    last = k;
     r0 = r1;
   }
+  if (last >= 0) CK(cudaEventSynchronize(h->ev_copied[last]));  // the caller may reuse ops
   return AIWC_OK;
 }
 

@@ -16,7 +16,10 @@
  *     unmodified until the next aiwc_compute on that handle returns, because
  *     work is queued on the handle's CUDA stream.
  *   - All GPU work of a handle is ordered on the stream given in
- *     aiwc_config.cuda_stream. The library owns all of its device scratch.
+ *     aiwc_config.cuda_stream: the handle's own streams (copies of host data;
+ *     the branch reduction, which runs beside the memory reduction) fork from
+ *     it and join it again with events before a call's work there ends. The
+ *     library owns all of its device scratch.
  *   - After an error other than AIWC_EINVAL the handle answers AIWC_ESTATE
  *     until aiwc_compute (which then resets it) or aiwc_destroy.
  *     AIWC_EINVAL found inside event data is reported by aiwc_compute, which
@@ -263,12 +266,15 @@ uint64_t aiwc_device_bytes(const aiwc_handle* h);
 uint64_t aiwc_kernel_launches(void);
 
 /* Stage timing: when on, every push and aiwc_compute brackets its stages with
- * CUDA events on the handle's stream (no extra synchronisation); after
- * aiwc_compute returns, aiwc_stage_times reports the elapsed milliseconds of
- * each stage of that invocation, summed over pushes. Stages, in order:
- *   0 mem_ingest   1 branch_ingest  2 instr_runs    3 mem_sort
- *   4 mem_levels   5 branch_sort    6 windows       7 pattern_sort
- *   8 pattern_runs 9 run_sort      10 run_combine  11 finalize
+ * CUDA events on the stream each stage runs on (no extra synchronisation);
+ * after aiwc_compute returns, aiwc_stage_times reports the elapsed
+ * milliseconds of each stage of that invocation, summed over pushes. Stages
+ * that run at the same time on two streams each include the other's share of
+ * the GPU. Stages, in order:
+ *   0 mem_ingest    1 branch_ingest  2 instr_runs    3 mem_sort
+ *   4 mem_scatter   5 mem_levels     6 branch_sort   7 windows
+ *   8 pattern_sort  9 pattern_runs  10 run_sort     11 run_combine
+ *  12 finalize     13 mem_expand
  * Returns the number of stages written (at most n); names may be NULL. */
 aiwc_status aiwc_set_stage_timing(aiwc_handle* h, int on);
 int aiwc_stage_times(const aiwc_handle* h, double* ms, const char** names, int n);

@@ -82,8 +82,10 @@ __device__ __forceinline__ void place_words(const MemIngestArgs& a, DevState* st
 // its full word goes to the spill list. FILTER: the space mask drops events,
 // so outputs are compacted behind one atomicAdd per block-tile. FULL: a.n is
 // a multiple of the block tile, so every event slot is valid (no tests).
+// Hash plan: six blocks per SM (40 registers, a few spilled) hide more of the
+// table-probe and atomic latency than four blocks of 64 registers.
 template <bool FILTER, bool HASH, bool FULL>
-__global__ void __launch_bounds__(kIngestThreads, HASH ? 4 : 3) k_mem_ingest(MemIngestArgs a) {
+__global__ void __launch_bounds__(kIngestThreads, HASH ? 6 : 3) k_mem_ingest(MemIngestArgs a) {
   constexpr int ITEMS = HASH ? kHashItems : 8;
   __shared__ u64 red64[32];
   __shared__ u32 red32[32];
@@ -287,7 +289,7 @@ __global__ void __launch_bounds__(1024) k_expand_scan(ExpandArgs a) {
 // ingest's and land at the tile's offset. Work-items and start addresses were
 // handled by k_expand_count.
 template <bool HASH>
-__global__ void __launch_bounds__(kIngestThreads, HASH ? 4 : 3) k_mem_ingest_bytes(MemIngestArgs a, const u64* tile_off) {
+__global__ void __launch_bounds__(kIngestThreads, HASH ? 6 : 3) k_mem_ingest_bytes(MemIngestArgs a, const u64* tile_off) {
   constexpr int ITEMS = HASH ? kHashItems : 8;
   constexpr int EV = (int)kExpandTile / kIngestThreads;  // events each thread stages
   __shared__ u64 s_word[kExpandTile];

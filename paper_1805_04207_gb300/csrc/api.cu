@@ -2,10 +2,13 @@
 // staging of host pushes, and the end-of-invocation pipeline.
 //
 // Pushes run their ingest kernels immediately on the handle's stream (the
-// memory and branch ingests turn events into sort words; the instruction
-// kernel reduces each run at once), so host-to-device copies of one chunk
-// overlap the ingest of the previous one. aiwc_compute then sorts, measures
-// runs, finalises and copies one fixed-size result back.
+// memory ingest counts each event's superblock and writes slot words, or sort
+// words in the sort plan; the branch ingest writes branch words; the
+// instruction kernel reduces each run at once), so host-to-device copies of
+// one chunk overlap the ingest of the previous one. aiwc_compute then reads
+// the ingest-time counters once to plan, reduces the memory events on the
+// handle's stream and (hash plan) the branch events on a side stream at the
+// same time, finalises and copies one fixed-size result back.
 #include <algorithm>
 #include <atomic>
 #include <cstddef>

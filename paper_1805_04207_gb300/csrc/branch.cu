@@ -2,13 +2,16 @@
 // outcomes appended per branch location while work-items run one after
 // another) and the average linear branch entropy of De Pestel et al.
 //
-// Branch word: (site << 32) | (work_item << 1) | taken. A stable sort on bits
-// 1..63 orders events by (site, work-item) and keeps push (program) order
-// inside each work-item, which is the per-site history order. A pattern word
-// (site << 32) | (history << 1) | outcome is emitted for every outcome that
-// has `h` predecessors at its site; sorting pattern words puts each
-// (site, history) pattern in one run whose length is n and whose sum of low
-// bits is the number taken, t. M = sum min(t, n - t), N' = sum n.
+// Branch word: (site << 32) | (work_item << 1) | taken. A stable sort by site
+// (a counting sort when work-items arrive in order and site ids are small,
+// else a radix sort on the varying bits 1..63) orders events by (site,
+// work-item) and keeps push (program) order inside each work-item, which is
+// the per-site history order. Per-site path: one block per site counts each
+// h-outcome window's (taken, total) in shared-memory bins. Global path: a
+// pattern word (site << 32) | (history << 1) | outcome is emitted for every
+// outcome that has `h` predecessors in its history; sorting pattern words puts
+// each (site, history) pattern in one run whose length is n and whose sum of
+// low bits is the number taken, t. Either way M = sum min(t, n - t), N' = sum n.
 #include <algorithm>
 
 #include "aiwc_internal.cuh"

@@ -190,16 +190,18 @@ def run_reference(args, rank, world):
     import oracle  # noqa: F401
     oracle.build()
     shift = args.scale
-    vals = []
+    vals, dts = [], []
     for _ in range(min(args.warmup, 1)):
         cpu_baseline(shift + 3, options(args))
     for _ in range(min(args.steps, 3)):
         b, dt = cpu_baseline(shift + 3, options(args))
         vals.append(b["value"])
+        dts.append(dt)
     v = statistics.median(vals)
     b["value"] = v
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * statistics.median(dts), 3),
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64+f64", "data": "synthetic",
             "config": {"workload": workload_name(args), "reference_sample": b["sample"]},
             "cpu_baseline": b, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

@@ -99,3 +99,18 @@ def test_product_package_does_not_reach_the_oracle():
             text = open(path).read()
             assert "import oracle" not in text and "from oracle" not in text, path
             assert "aiwc_oracle" not in text and "liboracle" not in text, path
+
+
+def test_import_fails_loudly_without_the_library(tmp_path):
+    """A copy of the package whose library was never built refuses to import:
+    there is no CPU fallback to land on."""
+    import shutil
+    import subprocess
+    import sys
+    dst = tmp_path / "paper_1805_04207_gb300"
+    shutil.copytree(os.path.join(ROOT, "paper_1805_04207_gb300"), dst,
+                    ignore=shutil.ignore_patterns("_build", "__pycache__"))
+    r = subprocess.run([sys.executable, "-c", "import paper_1805_04207_gb300"], cwd=tmp_path,
+                       capture_output=True, text=True, env={**os.environ, "PYTHONPATH": str(tmp_path)})
+    assert r.returncode != 0
+    assert "libaiwc.so is not built" in r.stderr

@@ -29,6 +29,10 @@ MUTATIONS = {
                         "const uint64_t touched = cfg->byte_addresses ? (size ? size - 1 : 0) : 1;"),
     "bytes_all_at_start": ("uint64_t key = ((uint64_t)space << 61) | (addr + b);",
                            "uint64_t key = ((uint64_t)space << 61) | addr;"),
+    "bytes_size0_counts_one": ("const uint64_t touched = cfg->byte_addresses ? size : 1;",
+                               "const uint64_t touched = cfg->byte_addresses ? (size ? size : 1) : 1;"),
+    "bytes_domain_unchecked": ("if (cfg->byte_addresses && size > 0 && addr + size - 1 >= kAddrLimit) return 1;",
+                               "if (0) return 1;"),
     "per_wi_history_not_split": ("for (auto& e : seq) per_wi[e.first].push_back(e.second);",
                                  "for (auto& e : seq) per_wi[0].push_back(e.second);"),
     "per_wi_patterns_keyed_by_wi": ("for (auto& w : per_wi) predict(kv.first, w.second);",
@@ -122,6 +126,12 @@ def _pins_pass(lib):
         o = comp(mem_only([0, 2], sizes=[4, 4]), byte_addresses=1)
         if (o["footprint"], o["total_reads"]) != (6, 8) or abs(o["entropy"][0] - 2.5) > 1e-15:
             return False
+        # a last byte outside the 61-bit domain is invalid data
+        try:
+            comp(mem_only([(1 << 61) - 2], sizes=[4]), byte_addresses=1)
+            return False
+        except oracle.OracleInvalidInput:
+            pass
         # per-(site, work-item) histories: brute force and the interleaved-loop closed form
         for seed in range(12):
             tr = random_trace(seed, n_mem=0, n_br=60, n_wi=3, n_runs=1, n_ops=8, n_sites=2)

@@ -50,6 +50,8 @@ MUTATIONS = {
     "barrier_counted_as_instruction": ("        itb.push_back(st.first);\n        st.first = 0;\n        ++barriers;",
                                        "        itb.push_back(st.first);\n        st.first = 0;\n        ++barriers;\n        ++hist[0];"),
     "work_items_memory_ignored": ("    work_items.insert(wi);\n    if (addr", "    if (addr"),
+    "yokota_site_term_dropped": ("site_sum.add(n * std::log2(n));", "site_sum.add(0.0 * n);"),
+    "yokota_not_per_bit": ("((double)npat * (double)h)", "((double)npat)"),
     "simd_square_dropped": ("q += w * w;", "q += w;"),
     "simd_max_first_only": ("if (w > m) m = w;", "if (i == 0) m = w;"),
 }
@@ -76,6 +78,8 @@ def _pins_pass(lib):
             if list(o["opcode_hist"]) != list(b["opcode_hist"]):
                 return False
             if max(abs(x - y) for x, y in zip(o["entropy"], b["entropy"])) > 1e-12:
+                return False
+            if abs(o["yokota"] - b["yokota"]) > 1e-12:
                 return False
         for ex in json.load(open(GOLDEN))["examples"]:
             if "mem" in ex:

@@ -9,6 +9,7 @@
 // a worker thread that runs the end-of-kernel reduction; aiwc_job_poll /
 // aiwc_job_wait return the metrics and release the slot. Results are those
 // of aiwc_compute on the same events: jobs share no device state.
+#include <atomic>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -43,7 +44,10 @@ struct aiwc_job {
   aiwc_server* srv = nullptr;
   size_t slot = 0;
   aiwc_handle* h = nullptr;
-  enum State { kOpen, kQueued, kDone } state = kOpen;
+  // the caller's thread reads the state without the server lock (push guards,
+  // aiwc_job_wait) while a worker sets kDone under it
+  enum State { kOpen, kQueued, kDone };
+  std::atomic<State> state{kOpen};
   aiwc_status status = AIWC_OK;
   aiwc_metrics result;
   std::vector<uint64_t> hist;

@@ -1,0 +1,44 @@
+"""bench.py's reference arm (the oracle timed on the host cores) keeps the
+one-JSON-line contract, on CPU: a small sample of the large workload, rank 0
+prints, any other rank exits 0 without work."""
+from __future__ import annotations
+
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _run(extra_env=None, *args):
+    env = {**os.environ, **(extra_env or {})}
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--scale", "8", "--steps", "2",
+                        "--warmup", "3", *args], cwd=ROOT, capture_output=True, text=True, env=env, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return [ln for ln in r.stdout.splitlines() if ln.strip()]
+
+
+def test_reference_arm_prints_one_contract_line():
+    lines = _run()
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference"
+    assert d["metric"].startswith("memory events/s characterized")
+    assert d["unit"] == "events/s" and d["higher_is_better"] is True
+    assert d["value"] > 0 and d["ms_per_step"] > 0
+    assert (d["n_gpus"], d["steps"], d["warmup"]) == (1, 2, 3)
+    assert d["scaling"] == "weak" and d["vs_baseline"] is None and d["data"] == "synthetic"
+    assert "large invocation" in d["config"]["workload"]
+    b = d["cpu_baseline"]
+    assert b["kind"] == "oracle" and b["cores"] >= 1 and b["sample"] and b["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_names_the_workload_options():
+    d = json.loads(_run(None, "--byte-addresses", "--history-scope", "1")[0])
+    assert "byte-granular" in d["config"]["workload"] and "(site, work-item)" in d["config"]["workload"]
+
+
+def test_reference_arm_other_ranks_exit_quietly():
+    assert _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}) == []

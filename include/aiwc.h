@@ -40,9 +40,11 @@ extern "C" {
 
 /* One memory access (Sec. V: memoryLoad / memoryStore / memoryAtomicLoad /
  * memoryAtomicStore notifications). 16 bytes, little-endian.
- *   addr       start address; must be < 2^61 (the 61-bit address domain).
+ *   addr       start address; must be < 2^61 (the 61-bit address domain);
+ *              with byte_addresses = 1 the last byte, addr + size - 1, must be.
  *   work_item  id of the issuing work-item.
- *   size       access size in bytes (carried, not used by any metric).
+ *   size       access size in bytes: used only with byte_addresses = 1, where
+ *              every byte it covers counts; otherwise carried and unused.
  *   flags      bit 0: 1 = store (write), 0 = load (read);
  *              bits 1-2: OpenCL address space (0 global, 1 local,
  *              2 constant, 3 private); other bits ignored.

@@ -191,23 +191,38 @@ typedef struct aiwc_handle aiwc_handle;
 aiwc_status aiwc_create(const aiwc_config* cfg, aiwc_handle** out);
 
 /* Memory notifications (Sec. V) in bulk: n events, in any order (the memory
- * metrics do not depend on event order). Invalid addresses are reported by
- * aiwc_compute as AIWC_EINVAL. */
+ * metrics do not depend on event order). Device events must be 16-byte
+ * aligned. Invalid addresses are reported by aiwc_compute as AIWC_EINVAL.
+ * Errors: AIWC_EINVAL (ev NULL with n > 0, misaligned device events),
+ * AIWC_ENOMEM, AIWC_ECUDA, AIWC_ESTATE. */
 aiwc_status aiwc_push_mem(aiwc_handle* h, const aiwc_mem_event* ev, size_t n, int on_device);
 
 /* Branch outcomes (Sec. III, Sec. V) in bulk. Each site's history is ordered
  * by (work-item id, push order): events of one work-item must be pushed in
- * program order; different work-items may interleave freely. */
+ * program order; different work-items may interleave freely. Device events
+ * must be 8-byte aligned.
+ * Errors: AIWC_EINVAL (ev NULL with n > 0, misaligned device events),
+ * AIWC_ENOMEM, AIWC_ECUDA, AIWC_ESTATE. */
 aiwc_status aiwc_push_branch(aiwc_handle* h, const aiwc_branch_event* ev, size_t n, int on_device);
 
 /* Instruction stream of one work-item (Sec. V: instructionExecuted), n
  * opcodes in program order with AIWC_BARRIER markers. Successive pushes for
- * the same work-item continue its stream. */
+ * the same work-item continue its stream; n = 0 still makes the work-item one
+ * of the instruction stream's (its final tally, 0, counts). Device opcodes
+ * must be 2-byte aligned. Invalid opcodes are reported by aiwc_compute.
+ * Errors: AIWC_EINVAL (ops NULL with n > 0, misaligned device opcodes),
+ * AIWC_ENOMEM, AIWC_ECUDA, AIWC_ESTATE. */
 aiwc_status aiwc_push_instr(aiwc_handle* h, uint32_t work_item, const uint16_t* ops, size_t n, int on_device);
 
 /* Bulk form of aiwc_push_instr: n_runs runs, run r covering
  * ops[run_off[r] .. run_off[r] + run_len[r]) for work-item run_wi[r], in
- * push order. All five arrays are on the same side (on_device). */
+ * push order. All five arrays are on the same side (on_device), device
+ * arrays aligned to their element size. A run reaching past n_ops is
+ * invalid: this call refuses it in a host table, aiwc_compute reports it
+ * from a device table.
+ * Errors: AIWC_EINVAL (a NULL table with n_runs > 0, ops NULL with n_ops > 0,
+ * misaligned device arrays, a host run past n_ops, more than 2^32 - 1 runs in
+ * one invocation), AIWC_ENOMEM, AIWC_ECUDA, AIWC_ESTATE. */
 aiwc_status aiwc_push_instr_runs(aiwc_handle* h, const uint32_t* run_wi, const uint64_t* run_off,
                                  const uint64_t* run_len, size_t n_runs, const uint16_t* ops,
                                  size_t n_ops, int on_device);

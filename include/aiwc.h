@@ -352,7 +352,8 @@ aiwc_status aiwc_job_wait(aiwc_job* j, aiwc_metrics* out);
 aiwc_status aiwc_server_stats(const aiwc_server* s, uint64_t* admitted, uint64_t* rejected, uint64_t* completed,
                               uint64_t* device_bytes);
 
-/* Waits for queued reductions, then frees everything (open jobs are dropped). */
+/* Waits for queued reductions, then frees everything, jobs not yet collected
+ * included (their pointers become invalid). */
 aiwc_status aiwc_server_destroy(aiwc_server* s);
 
 /* ------------------------------------------------- without any allocation */

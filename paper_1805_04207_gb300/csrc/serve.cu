@@ -16,6 +16,7 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <unordered_set>
 #include <vector>
 
 #include "aiwc_internal.cuh"
@@ -35,6 +36,7 @@ struct aiwc_server {
   std::vector<Slot> slots;
   uint64_t reserved_total = 0;
   std::deque<aiwc_job*> queue;
+  std::unordered_set<aiwc_job*> jobs;  // opened and not yet collected
   std::vector<std::thread> workers;
   bool stopping = false;
   uint64_t admitted = 0, rejected = 0, completed = 0;
@@ -205,6 +207,7 @@ aiwc_status aiwc_job_open(aiwc_server* s, const aiwc_config* job_cfg, uint64_t r
   j->slot = k;
   j->h = sl.h;
   j->hist.assign(c.n_opcodes, 0);
+  s->jobs.insert(j);
   *out = j;
   return AIWC_OK;
 }
@@ -256,6 +259,7 @@ static aiwc_status collect(aiwc_job* j, aiwc_metrics* out) {
   sl.busy = false;
   s->reserved_total -= sl.reserved;
   sl.reserved = 0;
+  s->jobs.erase(j);
   delete j;
   return st;
 }
@@ -299,6 +303,7 @@ aiwc_status aiwc_server_destroy(aiwc_server* s) {
   }
   s->cv_work.notify_all();
   for (auto& t : s->workers) t.join();
+  for (aiwc_job* j : s->jobs) delete j;
   for (auto& sl : s->slots) {
     if (sl.h) aiwc_destroy(sl.h);
     if (sl.stream) cudaStreamDestroy(sl.stream);

@@ -192,11 +192,21 @@ def _to_dict(m: aiwc_metrics) -> dict:
     return out
 
 
+def _hist_ptr(a):
+    """The library writes n_opcodes u64 counts through this pointer: only a
+    writable, C-contiguous uint64 numpy array (the caller's own) will do."""
+    import numpy as np
+    if not isinstance(a, np.ndarray) or a.dtype != np.uint64 or not a.flags.c_contiguous or \
+            not a.flags.writeable:
+        raise ValueError("opcode_hist must be a writable, contiguous uint64 numpy array of n_opcodes")
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+
+
 def aiwc_compute(h, opcode_hist=None) -> dict:
     """opcode_hist: optional writable uint64 numpy array of n_opcodes."""
     m = aiwc_metrics()
     if opcode_hist is not None:
-        m.opcode_hist = opcode_hist.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+        m.opcode_hist = _hist_ptr(opcode_hist)
     _check(lib.aiwc_compute(h, ctypes.byref(m)), h)
     return _to_dict(m)
 
@@ -208,7 +218,7 @@ def aiwc_compute_batch(hs, hists=None) -> list[dict]:
     if hists is not None:
         for i, hh in enumerate(hists):
             if hh is not None:
-                outs[i].opcode_hist = hh.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+                outs[i].opcode_hist = _hist_ptr(hh)
     _check(lib.aiwc_compute_batch(arr, n, outs))
     return [_to_dict(outs[i]) for i in range(n)]
 
@@ -297,7 +307,7 @@ def aiwc_job_poll(j, opcode_hist=None):
     """The metrics dict once the job is done (the job is then released), else None."""
     m = aiwc_metrics()
     if opcode_hist is not None:
-        m.opcode_hist = opcode_hist.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+        m.opcode_hist = _hist_ptr(opcode_hist)
     st = lib.aiwc_job_poll(j, ctypes.byref(m))
     if st == AIWC_EAGAIN:
         return None
@@ -308,7 +318,7 @@ def aiwc_job_poll(j, opcode_hist=None):
 def aiwc_job_wait(j, opcode_hist=None) -> dict:
     m = aiwc_metrics()
     if opcode_hist is not None:
-        m.opcode_hist = opcode_hist.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+        m.opcode_hist = _hist_ptr(opcode_hist)
     _check(lib.aiwc_job_wait(j, ctypes.byref(m)))
     return _to_dict(m)
 

@@ -11,13 +11,18 @@ from . import (aiwc_compute, aiwc_compute_batch, aiwc_config_default, aiwc_creat
 
 
 def _ptr(t):
-    """(address, on_device) of a contiguous torch tensor or numpy array."""
+    """(address, on_device) of a contiguous torch tensor or numpy array.
+
+    The address is the caller's own buffer: anything that would need a
+    temporary copy (a list, a strided view) is refused, since the copy would
+    be freed before the library reads it."""
     if hasattr(t, "data_ptr"):
         if not t.is_contiguous():
             raise ValueError("tensor must be contiguous")
         return t.data_ptr(), bool(t.is_cuda)
-    a = np.ascontiguousarray(t)
-    return a.ctypes.data, False
+    if not isinstance(t, np.ndarray) or not t.flags.c_contiguous:
+        raise ValueError("host input must be a contiguous torch tensor or numpy array")
+    return t.ctypes.data, False
 
 
 class Characterizer:

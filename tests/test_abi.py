@@ -114,3 +114,33 @@ def test_import_fails_loudly_without_the_library(tmp_path):
                        capture_output=True, text=True, env={**os.environ, "PYTHONPATH": str(tmp_path)})
     assert r.returncode != 0
     assert "libaiwc.so is not built" in r.stderr
+
+
+def test_binding_passes_only_the_callers_own_buffers():
+    """The binding hands the library the caller's buffer itself, never a
+    temporary copy that would be freed before the library reads it."""
+    import numpy as np
+    import torch
+
+    from paper_1805_04207_gb300.api import _ptr
+    a = np.arange(8, dtype=np.int64)
+    assert _ptr(a) == (a.ctypes.data, False)
+    t = torch.arange(8, dtype=torch.int64)
+    assert _ptr(t) == (t.data_ptr(), False)
+    for bad in ([1, 2, 3], a[::2], t[::2]):
+        with pytest.raises(ValueError):
+            _ptr(bad)
+
+
+def test_histogram_buffer_is_checked_before_the_library_writes_it():
+    import numpy as np
+
+    import paper_1805_04207_gb300 as P
+    assert P._hist_ptr(np.zeros(4, dtype=np.uint64))
+    for bad in (np.zeros(4, dtype=np.int32), np.zeros(8, dtype=np.uint64)[::2], [0, 0, 0]):
+        with pytest.raises(ValueError):
+            P._hist_ptr(bad)
+    ro = np.zeros(4, dtype=np.uint64)
+    ro.flags.writeable = False
+    with pytest.raises(ValueError):
+        P._hist_ptr(ro)

@@ -25,6 +25,26 @@ def _ptr(t):
     return t.ctypes.data, False
 
 
+def _nbytes(t) -> int:
+    return t.numel() * t.element_size() if hasattr(t, "element_size") else t.nbytes
+
+
+def _records(t, size: int, what: str) -> int:
+    """Number of `size`-byte records in a buffer; its bytes must be whole records."""
+    nb = _nbytes(t)
+    if nb % size:
+        raise ValueError(f"{what}: {nb} bytes is not a whole number of {size}-byte records")
+    return nb // size
+
+
+def _elements(t, size: int, what: str) -> int:
+    """Number of elements of a table whose elements must be `size` bytes wide."""
+    es = t.element_size() if hasattr(t, "element_size") else t.itemsize
+    if es != size:
+        raise ValueError(f"{what} must have {size}-byte elements, not {es}")
+    return t.numel() if hasattr(t, "numel") else t.size
+
+
 class Characterizer:
     """One AIWC invocation at a time on one device (a handle of the C ABI)."""
 
@@ -53,32 +73,28 @@ class Characterizer:
     def push_mem(self, events) -> None:
         """events: (n, 2) int64 tensor / array holding 16-byte aiwc_mem_event records."""
         p, dev = _ptr(events)
-        n = events.numel() // 2 if hasattr(events, "numel") else np.asarray(events).size // 2
-        aiwc_push_mem(self.h, p, n, dev)
+        aiwc_push_mem(self.h, p, _records(events, 16, "memory events"), dev)
         if dev:
             self._keep.append(events)
 
     def push_branch(self, events) -> None:
         """events: (n,) int64 tensor / array holding 8-byte aiwc_branch_event records."""
         p, dev = _ptr(events)
-        n = events.numel() if hasattr(events, "numel") else np.asarray(events).size
-        aiwc_push_branch(self.h, p, n, dev)
+        aiwc_push_branch(self.h, p, _records(events, 8, "branch events"), dev)
         if dev:
             self._keep.append(events)
 
     def push_instr(self, work_item: int, ops) -> None:
         """ops: (n,) int16 / uint16 opcodes of one work-item, 0xFFFF = barrier."""
         p, dev = _ptr(ops)
-        n = ops.numel() if hasattr(ops, "numel") else np.asarray(ops).size
-        aiwc_push_instr(self.h, work_item, p, n, dev)
+        aiwc_push_instr(self.h, work_item, p, _elements(ops, 2, "opcodes"), dev)
         if dev:
             self._keep.append(ops)
 
     def push_widths(self, widths) -> None:
         """widths: (n,) int16 / uint16 result widths of executed instructions."""
         p, dev = _ptr(widths)
-        n = widths.numel() if hasattr(widths, "numel") else np.asarray(widths).size
-        aiwc_push_widths(self.h, p, n, dev)
+        aiwc_push_widths(self.h, p, _elements(widths, 2, "widths"), dev)
         if dev:
             self._keep.append(widths)
 
@@ -90,8 +106,10 @@ class Characterizer:
         pp, d4 = _ptr(ops)
         if len({d1, d2, d3, d4}) != 1:
             raise ValueError("run table and opcodes must all be on the device or all on the host")
-        n_runs = run_wi.numel() if hasattr(run_wi, "numel") else np.asarray(run_wi).size
-        n_ops = ops.numel() if hasattr(ops, "numel") else np.asarray(ops).size
+        n_runs = _elements(run_wi, 4, "run_wi")
+        if _elements(run_off, 8, "run_off") != n_runs or _elements(run_len, 8, "run_len") != n_runs:
+            raise ValueError("run_wi, run_off and run_len must have one entry per run")
+        n_ops = _elements(ops, 2, "opcodes")
         aiwc_push_instr_runs(self.h, pw, po, pl, n_runs, pp, n_ops, d1)
         if d1:
             self._keep.extend([run_wi, run_off, run_len, ops])

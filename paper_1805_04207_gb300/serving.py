@@ -7,7 +7,7 @@ from . import (aiwc_config_default, aiwc_job_finish, aiwc_job_open, aiwc_job_pol
                aiwc_job_push_instr_runs, aiwc_job_push_mem, aiwc_job_push_widths, aiwc_job_wait,
                aiwc_server_config_default,
                aiwc_server_create, aiwc_server_destroy, aiwc_server_stats)
-from .api import _ptr
+from .api import _elements, _ptr, _records
 
 
 class Job:
@@ -21,27 +21,32 @@ class Job:
 
     def push_mem(self, events) -> None:
         p, dev = _ptr(events)
-        aiwc_job_push_mem(self.j, p, events.shape[0], dev)
+        aiwc_job_push_mem(self.j, p, _records(events, 16, "memory events"), dev)
         if dev:
             self._keep.append(events)
 
     def push_branch(self, events) -> None:
         p, dev = _ptr(events)
-        aiwc_job_push_branch(self.j, p, events.shape[0], dev)
+        aiwc_job_push_branch(self.j, p, _records(events, 8, "branch events"), dev)
         if dev:
             self._keep.append(events)
 
     def push_widths(self, widths) -> None:
         p, dev = _ptr(widths)
-        aiwc_job_push_widths(self.j, p, widths.shape[0], dev)
+        aiwc_job_push_widths(self.j, p, _elements(widths, 2, "widths"), dev)
         if dev:
             self._keep.append(widths)
 
     def push_instr_runs(self, run_wi, run_off, run_len, ops) -> None:
         ptrs = [_ptr(t) for t in (run_wi, run_off, run_len, ops)]
         dev = ptrs[0][1]
-        aiwc_job_push_instr_runs(self.j, ptrs[0][0], ptrs[1][0], ptrs[2][0], run_wi.shape[0], ptrs[3][0],
-                                 ops.shape[0], dev)
+        if any(d != dev for _, d in ptrs):
+            raise ValueError("run table and opcodes must all be on the device or all on the host")
+        n_runs = _elements(run_wi, 4, "run_wi")
+        if _elements(run_off, 8, "run_off") != n_runs or _elements(run_len, 8, "run_len") != n_runs:
+            raise ValueError("run_wi, run_off and run_len must have one entry per run")
+        aiwc_job_push_instr_runs(self.j, ptrs[0][0], ptrs[1][0], ptrs[2][0], n_runs, ptrs[3][0],
+                                 _elements(ops, 2, "opcodes"), dev)
         if dev:
             self._keep.extend([run_wi, run_off, run_len, ops])
 

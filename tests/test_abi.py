@@ -144,3 +144,50 @@ def test_histogram_buffer_is_checked_before_the_library_writes_it():
     ro.flags.writeable = False
     with pytest.raises(ValueError):
         P._hist_ptr(ro)
+
+
+def test_binding_counts_records_by_bytes_and_checks_table_widths():
+    import numpy as np
+    import torch
+
+    from paper_1805_04207_gb300.api import _elements, _records
+    assert _records(torch.zeros((5, 2), dtype=torch.int64), 16, "m") == 5
+    assert _records(torch.zeros(80, dtype=torch.uint8), 16, "m") == 5
+    assert _records(np.zeros(3, dtype=np.int64), 8, "b") == 3
+    with pytest.raises(ValueError):
+        _records(torch.zeros(3, dtype=torch.int64), 16, "m")  # 24 bytes: not whole 16-byte events
+    assert _elements(torch.zeros(7, dtype=torch.int32), 4, "run_wi") == 7
+    with pytest.raises(ValueError):
+        _elements(torch.zeros(7, dtype=torch.int64), 4, "run_wi")  # a 64-bit run table would be misread
+    with pytest.raises(ValueError):
+        _elements(np.zeros(7, dtype=np.int32), 2, "opcodes")
+
+
+def test_push_wrappers_pass_record_counts(monkeypatch):
+    """With the C calls replaced by recorders (no device needed), pushing a
+    synthetic invocation hands the library each stream's record count and
+    the tensors' own addresses."""
+    import torch
+
+    import synth
+    from paper_1805_04207_gb300 import api
+    calls = []
+    for name in ("aiwc_push_mem", "aiwc_push_branch", "aiwc_push_widths"):
+        monkeypatch.setattr(api, name, lambda h, p, n, dev, _n=name: calls.append((_n, p, n, dev)))
+    monkeypatch.setattr(api, "aiwc_push_instr_runs",
+                        lambda h, pw, po, pl, nr, pp, no, dev: calls.append(("runs", pw, po, pl, nr, pp, no, dev)))
+    c = object.__new__(api.Characterizer)
+    c.h, c._keep = None, []
+    tr = synth.tiny()
+    api.push_trace(c, tr)
+    got = {k[0]: k for k in calls}
+    assert got["aiwc_push_mem"][1:] == (tr.mem.data_ptr(), tr.mem.shape[0], False)
+    assert got["aiwc_push_branch"][1:] == (tr.br.data_ptr(), tr.br.shape[0], False)
+    assert got["aiwc_push_widths"][1:] == (tr.widths.data_ptr(), tr.widths.shape[0], False)
+    r = got["runs"]
+    assert r[2:5] == (tr.run_off.data_ptr(), tr.run_len.data_ptr(), tr.run_wi.shape[0])
+    assert r[5:] == (tr.ops.data_ptr(), tr.ops.shape[0], False)
+    with pytest.raises(ValueError):
+        c.push_instr_runs(tr.run_wi, tr.run_off, tr.run_len, tr.ops)  # 64-bit work-item table
+    with pytest.raises(ValueError):
+        c.push_instr_runs(tr.run_wi.to(torch.int32), tr.run_off[:-1], tr.run_len, tr.ops)

@@ -218,6 +218,16 @@ def max_over_ranks(x: float, dist, device) -> float:
     return float(t.item())
 
 
+L2_BYTES = 129 << 20
+
+
+def inputs_note(n_bytes: int) -> str:
+    """How the timed inputs relate to L2: above it no flush is needed between
+    steps; at or below it (small test scales only) the note says so."""
+    rel = "> L2 (no flush)" if n_bytes > L2_BYTES else "<= L2 (test scale: L2-resident between steps)"
+    return f"device-resident, {n_bytes / 1e9:.2f} GB {rel}"
+
+
 def replica_throughput(units_per_rank: int, world: int, seconds: float) -> float:
     """Whole-job throughput of `world` replicas each processing units_per_rank."""
     return world * units_per_rank / seconds
@@ -457,6 +467,7 @@ def main():
                      zipf_distinct=1 << (26 - s))
     run_wi32 = tr.run_wi.to(torch.int32)
     n_ops = tr.n_ops
+    in_bytes = 16 * n_mem + 8 * n_br + 2 * n_ops + (4 + 8 + 8) * tr.run_wi.numel()
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     opts = options(args)
@@ -555,7 +566,7 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64+f64",
                 "data": "synthetic", "impl": "ours",
                 "config": {"workload": workload_name(args), "seed": "rank",
-                           "inputs": "device-resident, 6.98 GB > L2 (no flush)",
+                           "inputs": inputs_note(in_bytes),
                            "parallelism": f"replicas x{world}", "scale_shift": s, **opts},
                 "roofline": roof,
                 "roofline_step": {"bound": "hbm", "achieved": round(step_ach, 1), "peak": hbm, "unit": "GB/s",

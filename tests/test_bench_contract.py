@@ -42,3 +42,11 @@ def test_reference_arm_names_the_workload_options():
 
 def test_reference_arm_other_ranks_exit_quietly():
     assert _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}) == []
+
+
+def test_inputs_note_against_l2():
+    sys.path.insert(0, ROOT)
+    import bench
+    full = 16 * (1 << 28) + 8 * (1 << 26) + 2 * (1 << 30) + 20 * (1 << 20)
+    assert bench.inputs_note(full) == "device-resident, 7.00 GB > L2 (no flush)"
+    assert "<= L2" in bench.inputs_note(64 << 20)

@@ -54,6 +54,19 @@ MUTATIONS = {
     "yokota_not_per_bit": ("((double)npat * (double)h)", "((double)npat)"),
     "simd_square_dropped": ("q += w * w;", "q += w;"),
     "simd_max_first_only": ("if (w > m) m = w;", "if (i == 0) m = w;"),
+    "space_mask_ignored": ("if (!((cfg->space_mask >> space) & 1u)) continue;", "if (0) continue;"),
+    "unique_writes_are_unique_reads": (
+        "out->unique_writes = std::unique(write_keys.begin(), write_keys.end()) - write_keys.begin();",
+        "out->unique_writes = out->unique_reads;"),
+    "branch_cover_over_predicted": ("site_counts.push_back(seq.size());",
+                                    "site_counts.push_back(seq.size() > h ? seq.size() - h : 0);"),
+    "ipt_counts_barriers": ("        itb.push_back(st.first);\n        st.first = 0;\n        ++barriers;",
+                            "        itb.push_back(st.first);\n        st.first = 0;\n        ++barriers;\n        ++st.second;"),
+    "reread_ratio_inverted": ("out->reread_ratio = (double)out->unique_reads / (double)out->total_reads;",
+                              "out->reread_ratio = (double)out->total_reads / (double)out->unique_reads;"),
+    "cover_fraction_swapped": (
+        "if ((unsigned __int128)den * cum >= (unsigned __int128)num * total) return k + 1;",
+        "if ((unsigned __int128)num * cum >= (unsigned __int128)den * total) return k + 1;"),
 }
 
 
@@ -69,7 +82,8 @@ def _pins_pass(lib):
                               n_ops=int(rng.integers(8, 64)), addr_pool=int(rng.integers(1, 20)),
                               n_sites=int(rng.integers(1, 4)), addr_span_bits=int(rng.integers(1, 16)))
             h = int(rng.choice([1, 2, 3]))
-            o, b = comp(tr, history_len=h), brute.metrics(tr, history_len=h)
+            mask = 0xF if seed % 2 else int(rng.choice([0x1, 0x3, 0xA]))
+            o, b = comp(tr, history_len=h, space_mask=mask), brute.metrics(tr, history_len=h, space_mask=mask)
             for f in INT_FIELDS:
                 if o[f] != b[f]:
                     return False
@@ -79,7 +93,7 @@ def _pins_pass(lib):
                 return False
             if max(abs(x - y) for x, y in zip(o["entropy"], b["entropy"])) > 1e-12:
                 return False
-            if abs(o["yokota"] - b["yokota"]) > 1e-12:
+            if abs(o["yokota"] - b["yokota"]) > 1e-12 or abs(o["albe"] - b["albe"]) > 1e-15:
                 return False
         for ex in json.load(open(GOLDEN))["examples"]:
             if "mem" in ex:

@@ -94,7 +94,8 @@ typedef struct aiwc_config {
   uint32_t cover_den;     /* coverage fraction denominator (10) */
   uint32_t n_opcodes;     /* valid opcodes are 0..n_opcodes-1, n_opcodes <= 65535 */
   uint32_t space_mask;    /* bit s set: address space s takes part in the memory metrics (0xF) */
-  uint32_t precision;     /* entropy finalisation: 0 = FP64, 1 = FP32 compensated sums */
+  uint32_t precision;     /* entropy finalisation: 0 = FP64, 1 = FP32 compensated sums (each entropy
+                             within 2^-22 bits of FP64; every count identical) */
   uint32_t plan;          /* distinct-address counting: 0 = auto (hash, sort on overflow), 1 = sort, 2 = hash */
   uint64_t max_work_items;/* work-item ids must be < this (sizes the work-item bitmap); 0 = 2^32 */
   uint64_t hbm_budget;    /* bytes of device scratch the handle may hold; 0 = unlimited */

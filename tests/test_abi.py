@@ -191,3 +191,17 @@ def test_push_wrappers_pass_record_counts(monkeypatch):
         c.push_instr_runs(tr.run_wi, tr.run_off, tr.run_len, tr.ops)  # 64-bit work-item table
     with pytest.raises(ValueError):
         c.push_instr_runs(tr.run_wi.to(torch.int32), tr.run_off[:-1], tr.run_len, tr.ops)
+
+
+def test_plain_c_client_links_and_runs(tmp_path):
+    """The boundary is a C ABI: a C program built against include/aiwc.h and
+    linked to libaiwc.so runs the calls that need no device."""
+    import paper_1805_04207_gb300 as P
+    libdir = os.path.dirname(P.LIB_PATH)
+    exe = tmp_path / "c_client"
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "c_client.c"), "-L", libdir, "-laiwc", f"-Wl,-rpath,{libdir}",
+                    "-o", str(exe)], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == "c client ok"

@@ -165,23 +165,62 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def cpu_baseline(scale_shift: int, opts=None):
-    """The oracle, as it stands, on a bounded sample of the same workload."""
-    import oracle
+def _oracle_sample(scale_shift: int, opts: dict, seed: int):
+    """A bounded, large-shaped sample for the oracle: (trace, n_mem, n_br, n_wi)."""
     import synth
-    opts = opts or {}
     if opts.get("byte_addresses"):
         scale_shift += 3  # about five one-byte accesses per event
     n_mem = 1 << (26 - scale_shift)
     n_br = 1 << (24 - scale_shift)
     n_wi = max(1, 1 << (18 - scale_shift))
-    tr = synth.large(seed=0, n_mem=n_mem, n_br=n_br, n_wi=n_wi, per_wi=1024, zipf_distinct=1 << (24 - scale_shift))
+    tr = synth.large(seed=seed, n_mem=n_mem, n_br=n_br, n_wi=n_wi, per_wi=1024,
+                     zipf_distinct=1 << (24 - scale_shift))
+    return tr, n_mem, n_br, n_wi, scale_shift
+
+
+def cpu_baseline(scale_shift: int, opts=None):
+    """The oracle, as it stands, on a bounded sample of the same workload."""
+    import oracle
+    opts = opts or {}
+    tr, n_mem, n_br, n_wi, sh = _oracle_sample(scale_shift, opts, 0)
     t0 = time.perf_counter()
     oracle.compute(tr, **opts)
     dt = time.perf_counter() - t0
     return {"value": n_mem / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"large-shaped sample: {n_mem} memory, {n_br} branch, {n_wi * 1024} opcodes "
-                      f"(Zipf over 2^{24 - scale_shift}), single-threaded C++ oracle, {dt:.1f} s"}, dt
+                      f"(Zipf over 2^{24 - sh}), single-threaded C++ oracle, {dt:.1f} s"}, dt
+
+
+def _oracle_replica(job):
+    """One process of the all-cores baseline: build its own sample, wait for
+    every replica, then time the oracle on it (wall clock of this host)."""
+    scale_shift, opts, seed, barrier = job
+    import oracle
+    tr, n_mem, _, _, _ = _oracle_sample(scale_shift, opts, seed)
+    barrier.wait(timeout=600)
+    t0 = time.time()
+    oracle.compute(tr, **opts)
+    return n_mem, t0, time.time()
+
+
+def cpu_baseline_all_cores(scale_shift: int, opts=None, procs: int = 0):
+    """The oracle, as it stands, as independent replicas on every host core:
+    one process per core, each reducing its own sample (seed = its index),
+    all started together. Throughput = all samples' events / the span from
+    the first start to the last finish."""
+    import multiprocessing as mp
+    opts = opts or {}
+    procs = procs or os.cpu_count() or 1
+    ctx = mp.get_context("spawn")  # the parent may hold a CUDA context: never fork
+    with ctx.Manager() as man:
+        barrier = man.Barrier(procs)
+        with ctx.Pool(procs) as pool:
+            res = pool.map(_oracle_replica, [(scale_shift, opts, seed, barrier) for seed in range(procs)])
+    n = sum(r[0] for r in res)
+    span = max(r[2] for r in res) - min(r[1] for r in res)
+    return {"value": n / span, "unit": UNIT, "cores": procs, "kind": "oracle replicas",
+            "sample": f"{procs} processes, each the single-threaded C++ oracle on its own large-shaped sample "
+                      f"of {res[0][0]} memory events; {span:.2f} s from the first start to the last finish"}
 
 
 def run_reference(args, rank, world):
@@ -556,9 +595,13 @@ def main():
                "ms_per_step": round(e_s * 1e3, 3), "steps": ek}
         del hmem, hbr, hops
 
-    base = None
+    base = base_all = None
     if rank == 0 and not args.no_cpu_baseline:
         base, _ = cpu_baseline(s, opts)
+        try:
+            base_all = cpu_baseline_all_cores(s + 3, opts)
+        except Exception as e:  # a reported baseline only: never lose the bench line to it
+            base_all = {"unavailable": f"{type(e).__name__}: {e}"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -572,7 +615,8 @@ def main():
                 "roofline_step": {"bound": "hbm", "achieved": round(step_ach, 1), "peak": hbm, "unit": "GB/s",
                                   "frac": round(step_ach / hbm, 4), "alg_bytes_per_step": step_alg},
                 "stage_ms_per_step": {k: round(v, 4) for k, v in per_step.items()},
-                "e2e": e2e, "cpu_baseline": base, "clocks": clocks, "gpu_launches": launches,
+                "e2e": e2e, "cpu_baseline": base, "cpu_baseline_all_cores": base_all,
+                "clocks": clocks, "gpu_launches": launches,
                 "gpu_launches_per_step": launches / args.steps,
                 "result_check": {"footprint": D, "entropy0": out["entropy"][0], "albe": out["albe"],
                                  "itb_median": out["itb_median"], "work_items": out["work_items"]}}

@@ -50,3 +50,13 @@ def test_inputs_note_against_l2():
     full = 16 * (1 << 28) + 8 * (1 << 26) + 2 * (1 << 30) + 20 * (1 << 20)
     assert bench.inputs_note(full) == "device-resident, 7.00 GB > L2 (no flush)"
     assert "<= L2" in bench.inputs_note(64 << 20)
+
+
+def test_all_cores_baseline_runs_oracle_replicas():
+    """The all-cores CPU baseline: the oracle as it stands, one spawned process
+    per core on its own sample, timed from the first start to the last finish."""
+    sys.path.insert(0, ROOT)
+    import bench
+    b = bench.cpu_baseline_all_cores(10, {}, procs=2)
+    assert b["kind"] == "oracle replicas" and b["cores"] == 2 and b["unit"] == "events/s"
+    assert b["value"] > 0 and "2 processes" in b["sample"] and "65536 memory events" in b["sample"]

@@ -210,12 +210,15 @@ def cpu_baseline_all_cores(scale_shift: int, opts=None, procs: int = 0):
     the first start to the last finish."""
     import multiprocessing as mp
     opts = opts or {}
-    procs = procs or os.cpu_count() or 1
+    if not procs:
+        procs = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
     ctx = mp.get_context("spawn")  # the parent may hold a CUDA context: never fork
     with ctx.Manager() as man:
         barrier = man.Barrier(procs)
         with ctx.Pool(procs) as pool:
-            res = pool.map(_oracle_replica, [(scale_shift, opts, seed, barrier) for seed in range(procs)])
+            # a bounded wait: a replica that dies must not hang the benchmark
+            res = pool.map_async(_oracle_replica,
+                                 [(scale_shift, opts, seed, barrier) for seed in range(procs)]).get(timeout=900)
     n = sum(r[0] for r in res)
     span = max(r[2] for r in res) - min(r[1] for r in res)
     return {"value": n / span, "unit": UNIT, "cores": procs, "kind": "oracle replicas",

@@ -53,3 +53,36 @@ def test_two_replicas_slowest_rank_sets_the_time():
     (fp0, h0, v0), (fp1, h1, v1) = got
     assert v0 == v1 == pytest.approx(2 * 20_000 / 1.5)  # 2 replicas x 20,000 events / slowest 1.5 s
     assert (fp0, h0) != (fp1, h1)  # replicas reduce different invocations (seed = rank)
+
+
+def _leaving_rank(rank, world, port, out):
+    """Rank 1 fails between steps (it exits before the timing reduction); rank
+    0 must get an error from that reduction, not wait for ever."""
+    from datetime import timedelta
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=timedelta(seconds=10))
+    import bench
+    if rank == 1:
+        os._exit(3)  # a replica that dies with no collective in flight
+    try:
+        bench.max_over_ranks(1.0, dist, "cpu")
+        out.put("no error")
+    except Exception as e:  # gloo: connection closed by the peer, or the timeout
+        out.put(type(e).__name__)
+    out.close()
+    out.join_thread()
+    os._exit(0)  # skip process-group teardown with a dead peer
+
+
+def test_a_rank_that_leaves_fails_the_others_collective():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_leaving_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+    assert got in ("RuntimeError", "DistBackendError", "DistError", "DistNetworkError"), got
+    assert procs[1].exitcode == 3 and procs[0].exitcode == 0

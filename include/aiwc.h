@@ -293,7 +293,9 @@ uint64_t aiwc_kernel_launches(void);
  *   4 mem_scatter   5 mem_levels     6 branch_sort   7 windows
  *   8 pattern_sort  9 pattern_runs  10 run_sort     11 run_combine
  *  12 finalize     13 mem_expand
- * Returns the number of stages written (at most n); names may be NULL. */
+ * Returns the number of stages written (at most n); names may be NULL.
+ * Whether timing is on or off, each stage is also an NVTX range with the
+ * stage's name, for profilers that record NVTX (nsys; ncu --nvtx). */
 aiwc_status aiwc_set_stage_timing(aiwc_handle* h, int on);
 int aiwc_stage_times(const aiwc_handle* h, double* ms, const char** names, int n);
 

@@ -21,6 +21,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "aiwc_internal.cuh"
 
 using namespace aiwc;
@@ -206,6 +208,7 @@ struct StageScope {
   int stage;
   cudaStream_t s;
   cudaEvent_t a = nullptr, b = nullptr;
+  bool range = false;  // an NVTX range named after the stage (seen by nsys / ncu --nvtx)
   cudaEvent_t take() {
     cudaEvent_t e = nullptr;
     if (!h->event_pool.empty()) {
@@ -219,18 +222,26 @@ struct StageScope {
   }
   // s: the stream the stage's kernels go to (the handle's stream by default)
   StageScope(aiwc_handle* hh, int st, cudaStream_t ss = nullptr) : h(hh), stage(st), s(ss ? ss : hh->stream) {
+    nvtxRangePushA(kStageNames[st]);
+    range = true;
     if (!h->timing) return;
     a = take();
     b = take();
     if (a) cudaEventRecord(a, s);
   }
   void end() {
+    if (range) {
+      nvtxRangePop();
+      range = false;
+    }
     if (!a || !b) return;
     cudaEventRecord(b, s);
     h->intervals.push_back({stage, a, b});
     a = b = nullptr;
   }
   ~StageScope() { end(); }
+  StageScope(const StageScope&) = delete;  // one push and one pop per range
+  StageScope& operator=(const StageScope&) = delete;
 };
 
 // After the stream is synchronised: fold the recorded intervals into stage times.

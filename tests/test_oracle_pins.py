@@ -463,3 +463,73 @@ def test_per_work_item_interleaved_loops_closed_form(h):
     o = oracle.compute(branch_only(st, wi, tk), history_len=h, history_scope=1)
     assert (o["branch_patterns"], o["branch_minsum"]) == (2 * (L - h), 0)
     assert o["albe"] == 0.0
+
+
+# ---- partitions into whole units (reading of the trace-size limit, Sec. VI) ----
+
+def _mem_parts(mem, unit_shift: int, P: int):
+    """Memory events split into P parts by a function of (space, address >> unit_shift)."""
+    raw = mem.numpy().view(np.uint64).reshape(-1, 2)
+    unit = (raw[:, 0] >> np.uint64(unit_shift)) * np.uint64(0x9E3779B1) + ((raw[:, 1] >> np.uint64(41)) & np.uint64(3))
+    part = (unit >> np.uint64(7)) % np.uint64(P)
+    return [mem[torch.from_numpy(part == p)] for p in range(P)]
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_partitions_into_whole_units_add_up_exactly(seed):
+    """A partitioned invocation is exact because every distribution the
+    metrics are taken from adds over parts made of whole units. Memory: all
+    groups of skip levels 0..10 lie inside one superblock of 2^11 addresses.
+    Branches: histories lie inside one site. Instructions: ITB chains lie
+    inside one work-item. Checked with the oracle's exact distributions; a
+    split at 2^9 addresses, which cuts skip-level-10 groups, must fail."""
+    from collections import Counter
+    tr = random_trace(seed, n_mem=600, n_br=400, n_wi=6, n_runs=16, n_ops=300, addr_pool=200, n_sites=6,
+                      addr_span_bits=16)
+    P = 4
+    whole = oracle.compute(tr, history_len=2)
+    parts = _mem_parts(tr.mem, 11, P)
+    for n in range(11):
+        summed = Counter()
+        for m in parts:
+            summed.update(oracle.count_of_counts(m, n))
+        assert dict(summed) == oracle.count_of_counts(tr.mem, n), n
+    pm = [oracle.compute(synth.Trace("m", m), history_len=2) for m in parts]
+    for f in ("total_reads", "total_writes", "footprint", "unique_reads", "unique_writes"):
+        assert sum(o[f] for o in pm) == whole[f], f
+    # branches by site
+    raw = tr.br.numpy().view(np.uint64)
+    site = raw & np.uint64(0xFFFFFFFF)
+    pb = [oracle.compute(synth.Trace("b", br=tr.br[torch.from_numpy(site % np.uint64(P) == p)]), history_len=2)
+          for p in range(P)]
+    for f in ("branch_events", "branch_sites", "branch_patterns", "branch_minsum"):
+        assert sum(o[f] for o in pb) == whole[f], f
+    # the Yokota numerator, N' h H(history | site), adds over sites
+    num = sum(o["yokota"] * o["branch_patterns"] for o in pb)
+    assert abs(num - whole["yokota"] * whole["branch_patterns"]) <= 1e-9 * max(1.0, num)
+    # instructions by work-item
+    wi = tr.run_wi.numpy()
+    pi = []
+    for p in range(P):
+        sel = np.nonzero(wi % P == p)[0]
+        runs = [(int(wi[r]), tr.ops[int(tr.run_off[r]):int(tr.run_off[r] + tr.run_len[r])].tolist()) for r in sel]
+        pi.append(oracle.compute(instr_only(runs, n_opcodes=tr.n_opcodes)) if runs else None)
+    pi = [o for o in pi if o is not None]
+    for f in ("total_instructions", "barriers", "itb_count", "ipt_count"):
+        assert sum(o[f] for o in pi) == whole[f], f
+    assert min(o["itb_min"] for o in pi) == whole["itb_min"] and max(o["itb_max"] for o in pi) == whole["itb_max"]
+    assert (np.sum([o["opcode_hist"] for o in pi], axis=0) == whole["opcode_hist"]).all()
+
+
+def test_partitions_that_cut_groups_do_not_add_up():
+    """The control: parts of 2^9 addresses cut skip-level-10 groups, and the
+    summed distribution differs from the whole's for some trace."""
+    from collections import Counter
+    differs = False
+    for seed in range(6):
+        tr = random_trace(seed, n_mem=600, n_br=0, n_runs=1, n_ops=8, addr_pool=200, addr_span_bits=16)
+        summed = Counter()
+        for m in _mem_parts(tr.mem, 9, 4):
+            summed.update(oracle.count_of_counts(m, 10))
+        differs |= dict(summed) != oracle.count_of_counts(tr.mem, 10)
+    assert differs

@@ -533,3 +533,35 @@ def test_partitions_that_cut_groups_do_not_add_up():
             summed.update(oracle.count_of_counts(m, 10))
         differs |= dict(summed) != oracle.count_of_counts(tr.mem, 10)
     assert differs
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_byte_accesses_split_at_a_superblock_edge_are_unchanged(seed):
+    """With byte-granular addresses an access is the set of bytes it touches,
+    so cutting one that crosses a 2^11-address boundary into two accesses
+    (how a partitioned invocation routes it) changes no metric."""
+    rng = np.random.default_rng(seed)
+    n = 300
+    edge = (rng.integers(1, 6, n) << 11).astype(np.int64)
+    addr = edge - rng.integers(0, 12, n)           # start up to 12 bytes before an edge
+    size = rng.integers(0, 17, n)
+    st, sp, wi = rng.integers(0, 2, n), rng.integers(0, 4, n), rng.integers(0, 5, n)
+    tr = mem_only(addr.tolist(), st.tolist(), sp.tolist(), wi.tolist(), size.tolist())
+    a2, s2, st2, sp2, wi2 = [], [], [], [], []
+    for i in range(n):
+        cut = max(0, min(int(size[i]), int(edge[i] - addr[i])))
+        pieces = [(int(addr[i]), cut), (int(edge[i]), int(size[i]) - cut)] if 0 < cut < size[i] else \
+            [(int(addr[i]), int(size[i]))]
+        for a, s in pieces:
+            a2.append(a)
+            s2.append(s)
+            st2.append(int(st[i]))
+            sp2.append(int(sp[i]))
+            wi2.append(int(wi[i]))
+    split = mem_only(a2, st2, sp2, wi2, s2)
+    assert len(a2) > n  # some accesses did cross
+    o, b = oracle.compute(tr, byte_addresses=1), oracle.compute(split, byte_addresses=1)
+    for f in ("total_reads", "total_writes", "footprint", "footprint_cover", "unique_reads", "unique_writes",
+              "work_items"):
+        assert o[f] == b[f], f
+    assert o["entropy"] == b["entropy"]

@@ -229,6 +229,10 @@ def cpu_baseline_all_cores(scale_shift: int, opts=None, procs: int = 0):
 def run_reference(args, rank, world):
     if rank != 0:
         return
+    if args.workload != "large":
+        print(json.dumps({"impl": "reference", "unavailable": f"the reference arm (the oracle on the host cores) "
+                          f"times the large invocation only, not the {args.workload} workload"}), flush=True)
+        return
     import oracle  # noqa: F401
     oracle.build()
     shift = args.scale

@@ -60,3 +60,8 @@ def test_all_cores_baseline_runs_oracle_replicas():
     b = bench.cpu_baseline_all_cores(10, {}, procs=2)
     assert b["kind"] == "oracle replicas" and b["cores"] == 2 and b["unit"] == "events/s"
     assert b["value"] > 0 and "2 processes" in b["sample"] and "65536 memory events" in b["sample"]
+
+
+def test_reference_arm_refuses_other_workloads():
+    d = json.loads(_run(None, "--workload", "serving")[0])
+    assert d["impl"] == "reference" and "large invocation only" in d["unavailable"]

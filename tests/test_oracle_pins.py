@@ -497,16 +497,18 @@ def test_partitions_into_whole_units_add_up_exactly(seed):
     pm = [oracle.compute(synth.Trace("m", m), history_len=2) for m in parts]
     for f in ("total_reads", "total_writes", "footprint", "unique_reads", "unique_writes"):
         assert sum(o[f] for o in pm) == whole[f], f
-    # branches by site
+    # branches by site, in both history scopes
     raw = tr.br.numpy().view(np.uint64)
     site = raw & np.uint64(0xFFFFFFFF)
-    pb = [oracle.compute(synth.Trace("b", br=tr.br[torch.from_numpy(site % np.uint64(P) == p)]), history_len=2)
-          for p in range(P)]
-    for f in ("branch_events", "branch_sites", "branch_patterns", "branch_minsum"):
-        assert sum(o[f] for o in pb) == whole[f], f
-    # the Yokota numerator, N' h H(history | site), adds over sites
-    num = sum(o["yokota"] * o["branch_patterns"] for o in pb)
-    assert abs(num - whole["yokota"] * whole["branch_patterns"]) <= 1e-9 * max(1.0, num)
+    for scope in (0, 1):
+        ws = oracle.compute(tr, history_len=2, history_scope=scope)
+        pb = [oracle.compute(synth.Trace("b", br=tr.br[torch.from_numpy(site % np.uint64(P) == p)]), history_len=2,
+                             history_scope=scope) for p in range(P)]
+        for f in ("branch_events", "branch_sites", "branch_patterns", "branch_minsum"):
+            assert sum(o[f] for o in pb) == ws[f], (scope, f)
+        # the Yokota numerator, N' h H(history | site), adds over sites
+        num = sum(o["yokota"] * o["branch_patterns"] for o in pb)
+        assert abs(num - ws["yokota"] * ws["branch_patterns"]) <= 1e-9 * max(1.0, num), scope
     # instructions by work-item
     wi = tr.run_wi.numpy()
     pi = []

@@ -227,30 +227,43 @@ def cpu_baseline_all_cores(scale_shift: int, opts=None, procs: int = 0):
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the oracle, as it stands, on the host cores. Every
+    one of the --warmup + --steps steps reduces the same bounded sample of the
+    large workload (2^23 memory events of the same shapes, sized so that the
+    whole run takes a minute or so); the line reports the steps it ran and the
+    time per sample step."""
     if rank != 0:
         return
     if args.workload != "large":
         print(json.dumps({"impl": "reference", "unavailable": f"the reference arm (the oracle on the host cores) "
                           f"times the large invocation only, not the {args.workload} workload"}), flush=True)
         return
-    import oracle  # noqa: F401
+    import oracle
     oracle.build()
-    shift = args.scale
-    vals, dts = [], []
-    for _ in range(min(args.warmup, 1)):
-        cpu_baseline(shift + 3, options(args))
-    for _ in range(min(args.steps, 3)):
-        b, dt = cpu_baseline(shift + 3, options(args))
-        vals.append(b["value"])
-        dts.append(dt)
-    v = statistics.median(vals)
-    b["value"] = v
+    opts = options(args)
+    tr, n_mem, n_br, n_wi, sh = _oracle_sample(args.scale + 3, opts, 0)
+    for _ in range(args.warmup):
+        oracle.compute(tr, **opts)
+    dts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.compute(tr, **opts)
+        dts.append(time.perf_counter() - t0)
+    step_s = sum(dts) / len(dts)
+    v = n_mem / step_s
+    sample = (f"{n_mem} memory, {n_br} branch, {n_wi * 1024} opcode events of the large invocation's shapes "
+              f"(Zipf over 2^{24 - sh}) per step")
+    workload = f"{workload_name(args)}; reference sample per step: {sample}"
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * statistics.median(dts), 3),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * step_s, 3),
             "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64+f64", "data": "synthetic",
-            "config": {"workload": workload_name(args), "reference_sample": b["sample"]},
-            "cpu_baseline": b, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "config": {"workload": workload, "seed": 0, "inputs": "host memory (the oracle runs on the CPU)",
+                       "parallelism": "one host core", "scale_shift": args.scale, **opts},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{sample}; single-threaded C++ oracle, {args.steps} timed steps of "
+                                       f"{step_s:.2f} s"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 

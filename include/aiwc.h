@@ -95,7 +95,8 @@ typedef struct aiwc_config {
   uint32_t n_opcodes;     /* valid opcodes are 0..n_opcodes-1, n_opcodes <= 65535 */
   uint32_t space_mask;    /* bit s set: address space s takes part in the memory metrics (0xF) */
   uint32_t precision;     /* entropy finalisation: 0 = FP64, 1 = FP32 compensated sums (each entropy
-                             within 2^-22 bits of FP64; every count identical) */
+                             within 2^-22 bits of FP64; every count identical; the linear branch
+                             entropy, one division of exact integers, is FP64 in both modes) */
   uint32_t plan;          /* distinct-address counting: 0 = auto (hash, sort on overflow), 1 = sort, 2 = hash */
   uint64_t max_work_items;/* work-item ids must be < this (sizes the work-item bitmap); 0 = 2^32 */
   uint64_t hbm_budget;    /* bytes of device scratch the handle may hold; 0 = unlimited */
@@ -373,11 +374,13 @@ aiwc_status aiwc_server_destroy(aiwc_server* s);
  *   device       CUDA device ordinal; events must live on it.
  *   cuda_stream  cudaStream_t the work is ordered on (NULL = default stream).
  *   events       DEVICE pointer to n aiwc_mem_event records, 16-byte aligned,
- *                owned by the caller and only read.
+ *                owned by the caller and only read; device memory of another
+ *                device or pageable host memory -> AIWC_EINVAL.
  *   n            at most 262144 (2^18) events; larger n -> AIWC_EINVAL.
  *   space_mask   as aiwc_config.space_mask.
  *   out          HOST pointer; the memory fields and work_items are written,
- *                every other field is zero (out->opcode_hist is left as is).
+ *                every other field is zero (out->opcode_hist is left as is);
+ *                on any status but AIWC_OK every field is zero.
  * Work-item ids must be below 2^20. Blocks until the result is on the host.
  *
  * Scratch: one file-scope device array of about 24 MiB inside the library

@@ -220,9 +220,9 @@ def _agg_real(vals, mode):
     return 0.5 * (v[(len(v) - 1) // 2] + v[len(v) // 2])
 
 
-def count_of_counts(mem, n: int, space_mask: int = 0xF) -> dict:
+def count_of_counts(mem, n: int, space_mask: int = 0xF, lib_path: str | None = None) -> dict:
     """{c: m_c} of the memory accesses grouped by key >> n."""
-    lib = _load()
+    lib = _load() if lib_path is None else _bind(ctypes.CDLL(lib_path))
     b, n_mem = _mem_bytes(mem)
     cap = 1 << 16
     while True:

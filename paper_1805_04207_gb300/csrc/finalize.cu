@@ -419,10 +419,9 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(FinalizeArgs a) {
     m->branch_sites = st.branch_sites;
     m->branch_patterns = st.npat;
     m->branch_minsum = st.minsum;
-    if (a.precision)
-      m->albe = st.npat ? (double)((2.0f * (float)st.minsum) / (float)st.npat) : 0.0;
-    else
-      m->albe = st.npat ? 2.0 * (double)st.minsum / (double)st.npat : 0.0;
+    // one FP64 division of two exact integers in both precision modes: there is
+    // no sum to compensate, so FP32 would only lose accuracy
+    m->albe = st.npat ? 2.0 * (double)st.minsum / (double)st.npat : 0.0;
     m->unique_rw_ratio = (double)st.unique_reads / (double)st.unique_writes;
     m->reread_ratio = (double)st.unique_reads / (double)st.total_reads;
     m->rewrite_ratio = (double)st.unique_writes / (double)st.total_writes;

@@ -47,16 +47,25 @@ static_assert(kNoAllocBytes <= (32ull << 20), "the no-allocation scratch must st
 // The scratch every call of aiwc_mem_metrics_noalloc shares (one per device).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-// Device addresses of g_noalloc_scratch, looked up once per device.
+// Device addresses of g_noalloc_scratch and SM counts, looked up once per device.
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_addr[kMaxDevices] = {};
+int g_sms[kMaxDevices] = {};
 
+// Makes device d current for the call and restores the caller's device.
 struct Guard {
   int prev = -1;
+  bool ok = true;
   explicit Guard(int d) {
-    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-    if (prev != d) cudaSetDevice(d);
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      cudaGetLastError();
+      prev = -1;
+    }
+    if (prev != d && cudaSetDevice(d) != cudaSuccess) {
+      cudaGetLastError();
+      ok = false;
+    }
   }
   ~Guard() {
     if (prev >= 0) cudaSetDevice(prev);
@@ -75,26 +84,64 @@ using namespace aiwc;
 
 extern "C" aiwc_status aiwc_mem_metrics_noalloc(int device, void* cuda_stream, const aiwc_mem_event* events,
                                                 size_t n, uint32_t space_mask, aiwc_metrics* out) {
-  if (!out || (n && !events)) return fail(AIWC_EINVAL, "null events or output");
+  if (!out) return fail(AIWC_EINVAL, "null output");
+  uint64_t* user_hist = out->opcode_hist;
+  // on any error every field reads zero (the caller's histogram pointer kept)
+  *out = aiwc_metrics{};
+  out->opcode_hist = user_hist;
+  if (n && !events) return fail(AIWC_EINVAL, "null events");
   if (n > kNoAllocMaxEvents)
     return fail(AIWC_EINVAL, "aiwc_mem_metrics_noalloc takes at most 262144 (2^18) memory events per call");
   if ((uintptr_t)events & 15u) return fail(AIWC_EINVAL, "device memory events must be 16-byte aligned");
-  if (device < 0 || device >= kMaxDevices) return fail(AIWC_EINVAL, "no such CUDA device");
+  int n_dev = 0;
+  cudaError_t e = cudaGetDeviceCount(&n_dev);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(AIWC_ECUDA, std::string("cudaGetDeviceCount: ") + cudaGetErrorString(e));
+  }
+  if (device < 0 || device >= n_dev || device >= kMaxDevices)
+    return fail(AIWC_EINVAL, "aiwc_mem_metrics_noalloc: no CUDA device " + std::to_string(device));
   Guard g(device);
-  uint64_t* user_hist = out->opcode_hist;
+  if (!g.ok) return fail(AIWC_EINVAL, "aiwc_mem_metrics_noalloc: cannot make device " + std::to_string(device) +
+                                          " current");
+  if (n) {
+    // the events must be memory this device can read: device memory of another
+    // device, or plain pageable host memory, would be a fault, not an error
+    cudaPointerAttributes pa{};
+    e = cudaPointerGetAttributes(&pa, events);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(AIWC_EINVAL, std::string("aiwc_mem_metrics_noalloc: events pointer: ") + cudaGetErrorString(e));
+    }
+    if (pa.type == cudaMemoryTypeUnregistered)
+      return fail(AIWC_EINVAL, "aiwc_mem_metrics_noalloc: events must be device memory");
+    if (pa.type == cudaMemoryTypeDevice && pa.device != device)
+      return fail(AIWC_EINVAL, "aiwc_mem_metrics_noalloc: events live on device " + std::to_string(pa.device) +
+                                   ", not on device " + std::to_string(device));
+  }
   void* base = nullptr;
+  int sms = 0;
   {
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_addr[device]) {
       // set-up on the first call on this device, with the device current
-      cudaError_t e = cudaGetSymbolAddress(&g_addr[device], g_noalloc_scratch);
+      void* addr = nullptr;
+      e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
       if (e != cudaSuccess) {
-        g_addr[device] = nullptr;
         cudaGetLastError();
         return fail(AIWC_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
       }
+      int count = 0;
+      e = cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, device);
+      if (e != cudaSuccess || count < 1) {
+        cudaGetLastError();
+        return fail(AIWC_ECUDA, std::string("cudaDeviceGetAttribute: ") + cudaGetErrorString(e));
+      }
+      g_sms[device] = count;
+      g_addr[device] = addr;
     }
     base = g_addr[device];
+    sms = g_sms[device];
   }
   cudaStream_t s = (cudaStream_t)cuda_stream;
   char* p = (char*)base;
@@ -108,7 +155,6 @@ extern "C" aiwc_status aiwc_mem_metrics_noalloc(int device, void* cuda_stream, c
   u32* used_list = (u32*)(p + kOffTable + (kSbtClearBytes + 4) * kNoAllocSlots);
   u32* bitmap = (u32*)(p + kOffBitmap);
   // the previous call's contents remain: clear what has to start at zero
-  cudaError_t e;
   if ((e = cudaMemsetAsync(arena, 0, sizeof(Arena), s)) != cudaSuccess ||
       (e = cudaMemsetAsync(tab.keys, 0, kSbtClearBytes * kNoAllocSlots, s)) != cudaSuccess ||
       (e = cudaMemsetAsync(bitmap, 0, kNoAllocMaxWi / 8, s)) != cudaSuccess)
@@ -141,8 +187,8 @@ extern "C" aiwc_status aiwc_mem_metrics_noalloc(int device, void* cuda_stream, c
   ha.over = over_a;
   ha.over_cap = kNoAllocOverCap;
   ha.arena = arena;
-  ha.grid_scatter = 152 * 2;
-  ha.sm_count = 152;
+  ha.grid_scatter = sms * 8;  // the launch shapes of the handle path
+  ha.sm_count = sms;
   ha.seg_shift = 0;  // the event alignment is not read back: the general layout
   ha.big_hist = (u32*)(p + kOffBig);
   ha.big_cap = mem_hash_big_segments(n, kNoAllocBigBytes, 0);
@@ -183,11 +229,11 @@ extern "C" aiwc_status aiwc_mem_metrics_noalloc(int device, void* cuda_stream, c
           cudaSuccess ||
       (e = cudaStreamSynchronize(s)) != cudaSuccess)
     return fail(AIWC_ECUDA, std::string("aiwc_mem_metrics_noalloc: ") + cudaGetErrorString(e));
-  *out = r.m;
-  out->opcode_hist = user_hist;
   if (table_overflow) return fail(AIWC_ENOMEM, "superblock table of the no-allocation scratch overflowed");
   if (r.err & kErrOverflow) return fail(AIWC_ENOMEM, "overflow list of the no-allocation scratch overflowed");
   if (r.err & kErrAddr) return fail(AIWC_EINVAL, "memory address outside the 61-bit domain");
   if (r.err & kErrWorkItem) return fail(AIWC_EINVAL, "work-item id >= 2^20 in aiwc_mem_metrics_noalloc");
+  *out = r.m;
+  out->opcode_hist = user_hist;
   return AIWC_OK;
 }

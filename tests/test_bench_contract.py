@@ -7,20 +7,25 @@ import json
 import os
 import subprocess
 import sys
+import time
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _run(extra_env=None, *args):
+def _run(extra_env=None, *args, wall=None):
     env = {**os.environ, **(extra_env or {})}
+    t0 = time.perf_counter()
     r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--scale", "8", "--steps", "2",
                         "--warmup", "3", *args], cwd=ROOT, capture_output=True, text=True, env=env, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
+    if wall is not None:
+        wall.append(time.perf_counter() - t0)
     return [ln for ln in r.stdout.splitlines() if ln.strip()]
 
 
 def test_reference_arm_prints_one_contract_line():
-    lines = _run()
+    wall = []
+    lines = _run(None, wall=wall)
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference"
@@ -30,6 +35,9 @@ def test_reference_arm_prints_one_contract_line():
     assert (d["n_gpus"], d["steps"], d["warmup"]) == (1, 2, 3)
     assert d["scaling"] == "weak" and d["vs_baseline"] is None and d["data"] == "synthetic"
     assert "large invocation" in d["config"]["workload"]
+    # every claimed step ran, on the sample the workload names
+    assert "reference sample per step" in d["config"]["workload"]
+    assert d["steps"] * d["ms_per_step"] / 1e3 < wall[0]
     b = d["cpu_baseline"]
     assert b["kind"] == "oracle" and b["cores"] >= 1 and b["sample"] and b["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}

@@ -19,7 +19,7 @@ import oracle
 import synth
 from tests import brute
 from tests.helpers import branch_only, instr_only, mem_only, random_trace
-from tests.test_oracle_pins import GOLDEN, INT_FIELDS
+from tests.test_oracle_pins import GOLDEN, INT_FIELDS, colliding_spaces_trace, entropy_from_coc
 
 MUTATIONS = {
     "history_skips_one_more": ("for (size_t j = h; j < seq.size(); ++j)", "for (size_t j = h + 1; j < seq.size(); ++j)"),
@@ -64,6 +64,11 @@ MUTATIONS = {
                             "        itb.push_back(st.first);\n        st.first = 0;\n        ++barriers;\n        ++st.second;"),
     "reread_ratio_inverted": ("out->reread_ratio = (double)out->unique_reads / (double)out->total_reads;",
                               "out->reread_ratio = (double)out->total_reads / (double)out->unique_reads;"),
+    "coc_no_space_tag": ("keys.push_back((((uint64_t)space << 61) | addr) >> n);", "keys.push_back(addr >> n);"),
+    "coc_skip_ignored": ("keys.push_back((((uint64_t)space << 61) | addr) >> n);",
+                         "keys.push_back(((uint64_t)space << 61) | addr);"),
+    "coc_space_mask_ignored": ("if (!((space_mask >> space) & 1u)) continue;", "if (0) continue;"),
+    "coc_group_counted_twice": ("coc[j - i] += 1;", "coc[j - i] += 1 + (j - i > 1);"),
     "cover_fraction_swapped": (
         "if ((unsigned __int128)den * cum >= (unsigned __int128)num * total) return k + 1;",
         "if ((unsigned __int128)num * cum >= (unsigned __int128)den * total) return k + 1;"),
@@ -116,6 +121,15 @@ def _pins_pass(lib):
                         return False
                 elif abs(o[k] - v) > 1e-12:
                     return False
+        # the count-of-counts helper reproduces every entropy level on every space mask
+        for seed in range(2):
+            tr = colliding_spaces_trace(seed)
+            for mask in (0xF, 0x5):
+                o = comp(tr, space_mask=mask)
+                for n in range(11):
+                    coc = oracle.count_of_counts(tr.mem, n, space_mask=mask, lib_path=lib)
+                    if abs(entropy_from_coc(coc) - o["entropy"][n]) > 1e-12:
+                        return False
         o = comp(synth.tiny())
         if (o["itb_median"], o["branch_minsum"], o["branch_patterns"]) != (391.0, 240, 7936):
             return False

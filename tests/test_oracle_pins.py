@@ -567,3 +567,39 @@ def test_byte_accesses_split_at_a_superblock_edge_are_unchanged(seed):
               "work_items"):
         assert o[f] == b[f], f
     assert o["entropy"] == b["entropy"]
+
+
+def entropy_from_coc(coc: dict) -> float:
+    """H = log2 N - (1/N) sum_c m_c c log2 c (Table I memory entropy under reading R1)."""
+    N = sum(c * m for c, m in coc.items())
+    if N == 0:
+        return 0.0
+    return math.log2(N) - math.fsum(m * c * math.log2(c) for c, m in coc.items()) / N
+
+
+def colliding_spaces_trace(seed: int) -> "synth.Trace":
+    """Accesses in all four address spaces whose numeric addresses repeat
+    across spaces, at several alignments, so that dropping the space tag or
+    the skip shift changes the grouping."""
+    rng = np.random.default_rng(seed)
+    pool = np.concatenate([rng.integers(0, 1 << 13, 24), (rng.integers(0, 64, 8) << 6)]).astype(np.int64)
+    n = 3000
+    addr = pool[rng.integers(0, pool.size, n)]
+    space = rng.integers(0, 4, n)
+    store = rng.integers(0, 2, n)
+    return mem_only(addr.tolist(), store.tolist(), space.tolist())
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_count_of_counts_gives_every_entropy(seed):
+    """The helper's m_c at skip level n must reproduce the oracle's entropy[n]
+    for every n = 0..10, on every space mask: the helper forms its groups
+    (space tag, address >> n) on its own, so a slip in it shows here."""
+    tr = colliding_spaces_trace(seed)
+    for mask in (0xF, 0x5, 0x2):
+        o = oracle.compute(tr, space_mask=mask)
+        for n in range(11):
+            coc = oracle.count_of_counts(tr.mem, n, space_mask=mask)
+            assert sum(c * m for c, m in coc.items()) == o["total_reads"] + o["total_writes"]
+            assert abs(entropy_from_coc(coc) - o["entropy"][n]) <= 1e-12, (mask, n)
+        assert sum(oracle.count_of_counts(tr.mem, 0, space_mask=mask).values()) == o["footprint"]

@@ -13,6 +13,7 @@ import ctypes
 import pytest
 import torch
 
+import oracle
 import synth
 from tests.helpers import mem_only
 
@@ -41,6 +42,13 @@ def _assert_same(a, b):
         assert abs(a["entropy"][n] - b["entropy"][n]) <= 1e-9, n
 
 
+def _in_range(ev):
+    """The large workload's work-item ids exceed 2^20; fold them into range."""
+    ev = ev.clone()
+    ev[:, 1] = (ev[:, 1] & ~0xFFFFFFFF) | ((ev[:, 1] & 0xFFFFFFFF) % (1 << 20))
+    return ev
+
+
 def test_noalloc_matches_regular_entry_point_on_consecutive_calls():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -48,9 +56,7 @@ def test_noalloc_matches_regular_entry_point_on_consecutive_calls():
     traces = [synth.large(seed=21, n_mem=200_003, n_br=0, n_wi=0, per_wi=1, zipf_distinct=1 << 14),
               synth.large(seed=22, n_mem=(1 << 18), n_br=0, n_wi=0, per_wi=1, zipf_distinct=1 << 16)]
     for k, tr in enumerate(traces):
-        ev = tr.mem.cuda()
-        # work-item ids of the large workload exceed 2^20; keep them in range
-        ev[:, 1] = (ev[:, 1] & ~0xFFFFFFFF) | ((ev[:, 1] & 0xFFFFFFFF) % (1 << 20))
+        ev = _in_range(tr.mem.cuda())
         ref = _regular(P, ev)
         torch.cuda.synchronize()
         free0 = torch.cuda.mem_get_info()[0]
@@ -59,10 +65,29 @@ def test_noalloc_matches_regular_entry_point_on_consecutive_calls():
         if k > 0:  # the first call may load the library's device image; later calls allocate nothing
             assert torch.cuda.mem_get_info()[0] >= free0
         _assert_same(got, ref)
+        # and directly against the oracle on the same events
+        _assert_same(got, oracle.compute(synth.Trace("m", mem=ev.cpu())))
         assert got["branch_events"] == 0 and got["total_instructions"] == 0
     # and once more on the first trace, after the scratch held the second one
-    ev = traces[0].mem.cuda()
-    ev[:, 1] = (ev[:, 1] & ~0xFFFFFFFF) | ((ev[:, 1] & 0xFFFFFFFF) % (1 << 20))
+    ev = _in_range(traces[0].mem.cuda())
+    _assert_same(_noalloc(P, ev), _regular(P, ev))
+
+
+def test_noalloc_recovers_after_a_failed_call_and_takes_empty_input():
+    """A call that fails on its data leaves the shared scratch dirty; the next
+    call must still clear everything it needs. An empty call gives zeros."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1805_04207_gb300 as P
+    bad = mem_only([64, 128], wis=[5, 1 << 20]).mem.cuda()
+    with pytest.raises(P.AiwcError) as e:
+        _noalloc(P, bad)
+    assert e.value.status == P.AIWC_EINVAL and "2^20" in str(e.value)
+    ev = _in_range(synth.large(seed=21, n_mem=200_003, n_br=0, n_wi=0, per_wi=1, zipf_distinct=1 << 14).mem.cuda())
+    _assert_same(_noalloc(P, ev), _regular(P, ev))
+    empty = torch.zeros((0, 2), dtype=torch.int64, device="cuda")
+    z = _noalloc(P, empty)
+    assert all(z[f] == 0 for f in MEM_FIELDS) and all(x == 0.0 for x in z["entropy"])
     _assert_same(_noalloc(P, ev), _regular(P, ev))
 
 

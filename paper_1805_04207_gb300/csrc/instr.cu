@@ -50,18 +50,23 @@ __device__ __forceinline__ u32 warp_seg_scan32(u32 x, u32* agg) {
   return lane == 0 ? 0u : ex;
 }
 
-// hist_mode: 0 = per-warp shared histograms, 1 = one shared histogram per
+// HMODE: 0 = per-warp shared histograms, 1 = one shared histogram per
 // block, 2 = global atomics. Every opcode slot adds to bin min(opcode,
 // n_opcodes): the spare bin n_opcodes takes barriers, padding (written as
 // barrier markers) and invalid opcodes, so invalid opcodes are found at the
-// end as spare - barriers - padding.
-__global__ void __launch_bounds__(kInThreads) k_instr_runs(RunBatchArgs a, int hist_mode) {
+// end as spare - barriers - padding. Opcodes are handled two per 32-bit word
+// (a halfword compare finds the barrier markers, a halfword minimum clamps
+// the bins).
+template <int HMODE>
+__global__ void __launch_bounds__(kInThreads) k_instr_runs(RunBatchArgs a) {
+  constexpr int hist_mode = HMODE;
   extern __shared__ u32 dyn[];
   __shared__ u32 itb_small[kValSmem];
   __shared__ u64 red64[32];
   __shared__ u32 red32[32];
   DevState* st = &a.arena->st;
   const u32 nop = a.n_opcodes;
+  const u32 clampv = nop | (nop << 16);
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const u32 hstride = nop + 1;
   const u32 hwords = hist_mode == 0 ? hstride * kInWarps : (hist_mode == 1 ? hstride : 0u);
@@ -122,15 +127,19 @@ __global__ void __launch_bounds__(kInThreads) k_instr_runs(RunBatchArgs a, int h
       // bit k of bm: opcode k is a barrier marker
       u32 bm = 0;
 #pragma unroll
-      for (int k = 0; k < kOpsPerLane; ++k) {
-        const u32 o = (pk[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu;
-        bm |= (o == AIWC_BARRIER ? 1u : 0u) << k;
-        const u32 bin = min(o, nop);
+      for (int k = 0; k < kOpsPerLane / 2; ++k) {
+        const u32 eq = __vcmpeq2(pk[k], 0xFFFFFFFFu);  // 0xFFFF in each half holding a marker
+        bm |= ((eq & 1u) | ((eq >> 15) & 2u)) << (2 * k);
         if (hist_mode == 2) {
-          if (bin < nop) atomicAdd(&a.opc_hist[bin], 1ull);
+          const u32 lo = pk[k] & 0xFFFFu, hi = pk[k] >> 16;
+          if (lo < nop) atomicAdd(&a.opc_hist[lo], 1ull);
+          else ++nspare_g;
+          if (hi < nop) atomicAdd(&a.opc_hist[hi], 1ull);
           else ++nspare_g;
         } else {
-          atomicAdd(&my_hist[bin], 1u);
+          const u32 c = __vminu2(pk[k], clampv);  // both bins: min(opcode, n_opcodes)
+          atomicAdd(&my_hist[c & 0xFFFFu], 1u);
+          atomicAdd(&my_hist[c >> 16], 1u);
         }
       }
       const u32 vm = nv >= 32 ? 0xFFFFFFFFu : ((1u << nv) - 1u);
@@ -336,12 +345,15 @@ void launch_instr_runs(const RunBatchArgs& a, cudaStream_t s) {
   else { mode = 2; smem = 0; }
   u64 blocks = (a.n_runs + kInWarps - 1) / kInWarps;
   if (blocks > 152ull * 4) blocks = 152ull * 4;
-  k_instr_runs<<<(unsigned)blocks, kInThreads, smem, s>>>(a, mode);
+  if (mode == 0) k_instr_runs<0><<<(unsigned)blocks, kInThreads, smem, s>>>(a);
+  else if (mode == 1) k_instr_runs<1><<<(unsigned)blocks, kInThreads, smem, s>>>(a);
+  else k_instr_runs<2><<<(unsigned)blocks, kInThreads, smem, s>>>(a);
   count_launches(1);
 }
 
 void init_instr_attributes() {
-  cudaFuncSetAttribute(k_instr_runs, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+  cudaFuncSetAttribute(k_instr_runs<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+  cudaFuncSetAttribute(k_instr_runs<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
 }
 
 void launch_instr_combine(const CombineArgs& a, cudaStream_t s) {

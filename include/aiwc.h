@@ -271,6 +271,76 @@ aiwc_status aiwc_destroy(aiwc_handle* h);
 #define AIWC_AGG_MEDIAN 1
 aiwc_status aiwc_aggregate(const aiwc_metrics* runs, size_t n, int mode, aiwc_metrics* out);
 
+/* ------------------------------------------------------- sharded invocations
+ *
+ * One invocation reduced by several ranks (one process per GPU). Sec. V adds
+ * each work-group's results into the kernel's global state; every metric is a
+ * function of distributions that add exactly over any split of the events
+ * into whole units -- memory superblocks of 2^11 addresses (with their space),
+ * branch sites, work-items' instruction runs -- so ranks that each reduce
+ * whole units and add their exact distributions reproduce the single-device
+ * result bit for bit. The protocol, for N ranks that each hold any slice of
+ * the invocation's streams (in push order, rank r's slice before rank r+1's):
+ *   1. route: each rank splits its slice into N shards with the calls below;
+ *   2. exchange (all-to-all): rank s receives shard s of every rank;
+ *   3. push the received slices in source-rank order, then aiwc_shard_export;
+ *   4. gather the N blobs (in rank order) on one or every rank and call
+ *      aiwc_shard_merge, which finalises once.
+ * Routing is host code (no device, no handle); the collective is the
+ * caller's (NCCL on device buffers, gloo on host buffers). */
+
+/* Stable split of host memory events into n_shards (1..256) shards by
+ * superblock. With byte_addresses, an access whose bytes cross a superblock
+ * boundary becomes two accesses, one on each side (as aiwc_config.
+ * byte_addresses reads the stream), so *n_out may exceed n. out == NULL:
+ * size query (*n_out and counts only). Else out (host, out_cap events)
+ * receives shard 0's events, then shard 1's, ..., counts[s] of them each.
+ * Errors: AIWC_EINVAL (bad n_shards, null pointers, out_cap < *n_out). */
+aiwc_status aiwc_shard_route_mem(uint32_t n_shards, int byte_addresses, const aiwc_mem_event* ev, size_t n,
+                                 aiwc_mem_event* out, size_t out_cap, uint64_t* counts, size_t* n_out);
+
+/* Stable split of host branch events by site into out (n events, shard 0's
+ * first) with counts[s] per shard. Errors: AIWC_EINVAL. */
+aiwc_status aiwc_shard_route_branch(uint32_t n_shards, const aiwc_branch_event* ev, size_t n, aiwc_branch_event* out,
+                                    uint64_t* counts);
+
+/* Stable split of host instruction runs (as aiwc_push_instr_runs) by
+ * work-item: out_wi / out_off / out_len receive shard 0's runs, then shard
+ * 1's, ... (run_counts[s] each); out_ops receives each shard's opcodes as one
+ * segment (op_counts[s] opcodes; the segments follow each other) and out_off
+ * is relative to the start of the run's own shard segment, so that a shard's
+ * run table and segment can be sent and pushed as they are. out_ops holds
+ * the sum of run_len. Errors: AIWC_EINVAL (null pointers, a run past n_ops). */
+aiwc_status aiwc_shard_route_runs(uint32_t n_shards, const uint32_t* run_wi, const uint64_t* run_off,
+                                  const uint64_t* run_len, size_t n_runs, const uint16_t* ops, size_t n_ops,
+                                  uint32_t* out_wi, uint64_t* out_off, uint64_t* out_len, uint16_t* out_ops,
+                                  uint64_t* run_counts, uint64_t* op_counts);
+
+/* Ends this rank's part of a sharded invocation: reduces what was pushed with
+ * the finalisation deferred and writes the exact distributions (dense
+ * count-of-counts and value bins, counters, overflow entries, opcode
+ * histogram, the rank's work-item bitmap words) as a host blob. The first call
+ * after the pushes reduces, keeps the blob on the host and resets the handle
+ * for its next invocation; *size is then the blob's size. blob == NULL: only
+ * *size (the blob stays held). blob with cap >= *size: the blob is copied
+ * there and released. The blob is valid for aiwc_shard_merge of the same
+ * library build and metric configuration. Invalid event data is carried in
+ * the blob and reported by the merge. Errors: AIWC_EINVAL (null pointers, cap
+ * too small, a partitioned handle), AIWC_ENOMEM, AIWC_ECUDA, AIWC_ESTATE. */
+aiwc_status aiwc_shard_export(aiwc_handle* h, void* blob, size_t cap, size_t* size);
+
+/* Adds n ranks' blobs (host pointers, sizes from aiwc_shard_export) into the
+ * handle's device state and finalises the invocation once: *out is the
+ * metric set of the whole sharded invocation (out->opcode_hist as for
+ * aiwc_compute). h must hold no pushed events and share the blobs' metric
+ * configuration (history length, opcodes, space mask, byte addresses,
+ * history scope, max_work_items); precision and coverage fraction are h's.
+ * Errors: AIWC_EINVAL (a blob of another build or configuration, inconsistent
+ * sizes, invalid event data), AIWC_ESTATE (pushed events pending),
+ * AIWC_ENOMEM, AIWC_ECUDA. */
+aiwc_status aiwc_shard_merge(aiwc_handle* h, const void* const* blobs, const size_t* sizes, size_t n,
+                             aiwc_metrics* out);
+
 /* Text of the last error on h (or of the last global error when h is NULL). */
 const char* aiwc_last_error(const aiwc_handle* h);
 

@@ -87,6 +87,11 @@ SIGNATURES = {
     "aiwc_set_stage_timing": (_ST, [_VP, ctypes.c_int]),
     "aiwc_stage_times": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_char_p),
                                         ctypes.c_int]),
+    "aiwc_shard_route_mem": (_ST, [ctypes.c_uint32, ctypes.c_int, _VP, _SZ, _VP, _SZ, _VP, ctypes.POINTER(_SZ)]),
+    "aiwc_shard_route_branch": (_ST, [ctypes.c_uint32, _VP, _SZ, _VP, _VP]),
+    "aiwc_shard_route_runs": (_ST, [ctypes.c_uint32, _VP, _VP, _VP, _SZ, _VP, _SZ, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "aiwc_shard_export": (_ST, [_VP, _VP, _SZ, ctypes.POINTER(_SZ)]),
+    "aiwc_shard_merge": (_ST, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(_SZ), _SZ, ctypes.POINTER(aiwc_metrics)]),
     "aiwc_mem_metrics_noalloc": (_ST, [ctypes.c_int, _VP, _VP, _SZ, ctypes.c_uint32, ctypes.POINTER(aiwc_metrics)]),
     "aiwc_server_config_default": (None, [ctypes.POINTER(aiwc_server_config)]),
     "aiwc_server_create": (_ST, [ctypes.POINTER(aiwc_server_config), ctypes.POINTER(_VP)]),
@@ -254,6 +259,74 @@ def aiwc_mem_metrics_noalloc(device: int, stream, events_ptr: int, n: int, space
     """Memory metrics of n device-resident events without any device allocation."""
     m = aiwc_metrics()
     _check(lib.aiwc_mem_metrics_noalloc(device, stream, events_ptr, n, space_mask, ctypes.byref(m)))
+    return _to_dict(m)
+
+
+# ------------------------------------------------------- sharded invocations
+
+def aiwc_shard_route_mem(n_shards: int, events, byte_addresses: int = 0):
+    """(routed events, counts per shard) of a host uint8/int64 buffer of 16-byte events (numpy)."""
+    import numpy as np
+    ev = np.ascontiguousarray(events).view(np.uint8).reshape(-1)
+    n = ev.size // 16
+    counts = np.zeros(n_shards, dtype=np.uint64)
+    n_out = ctypes.c_size_t()
+    _check(lib.aiwc_shard_route_mem(n_shards, byte_addresses, ev.ctypes.data, n, None, 0, counts.ctypes.data,
+                                    ctypes.byref(n_out)))
+    out = np.empty(16 * n_out.value, dtype=np.uint8)
+    _check(lib.aiwc_shard_route_mem(n_shards, byte_addresses, ev.ctypes.data, n, out.ctypes.data, n_out.value,
+                                    counts.ctypes.data, ctypes.byref(n_out)))
+    return out, counts
+
+
+def aiwc_shard_route_branch(n_shards: int, events):
+    """(routed events, counts per shard) of a host buffer of 8-byte branch events (numpy)."""
+    import numpy as np
+    ev = np.ascontiguousarray(events).view(np.uint8).reshape(-1)
+    n = ev.size // 8
+    out = np.empty(8 * n, dtype=np.uint8)
+    counts = np.zeros(n_shards, dtype=np.uint64)
+    _check(lib.aiwc_shard_route_branch(n_shards, ev.ctypes.data, n, out.ctypes.data, counts.ctypes.data))
+    return out, counts
+
+
+def aiwc_shard_route_runs(n_shards: int, run_wi, run_off, run_len, ops):
+    """Routed (run_wi u32, run_off u64, run_len u64, ops u16, run_counts, op_counts) of host run tables."""
+    import numpy as np
+    wi = np.ascontiguousarray(run_wi, dtype=np.uint32)
+    off = np.ascontiguousarray(run_off, dtype=np.uint64)
+    ln = np.ascontiguousarray(run_len, dtype=np.uint64)
+    op = np.ascontiguousarray(ops).view(np.uint16)
+    n = wi.size
+    o_wi, o_off, o_len = np.empty(n, np.uint32), np.empty(n, np.uint64), np.empty(n, np.uint64)
+    total = int(ln.sum()) if n else 0
+    o_ops = np.empty(max(total, 1), np.uint16)
+    rc, oc = np.zeros(n_shards, np.uint64), np.zeros(n_shards, np.uint64)
+    _check(lib.aiwc_shard_route_runs(n_shards, wi.ctypes.data, off.ctypes.data, ln.ctypes.data, n, op.ctypes.data,
+                                     op.size, o_wi.ctypes.data, o_off.ctypes.data, o_len.ctypes.data,
+                                     o_ops.ctypes.data, rc.ctypes.data, oc.ctypes.data))
+    return o_wi, o_off, o_len, o_ops[:total], rc, oc
+
+
+def aiwc_shard_export(h) -> bytes:
+    """This rank's exact distributions as a host blob; the handle is reset."""
+    size = ctypes.c_size_t()
+    _check(lib.aiwc_shard_export(h, None, 0, ctypes.byref(size)), h)
+    buf = ctypes.create_string_buffer(size.value)
+    _check(lib.aiwc_shard_export(h, buf, size.value, ctypes.byref(size)), h)
+    return buf.raw
+
+
+def aiwc_shard_merge(h, blobs, opcode_hist=None) -> dict:
+    """Metrics of the invocation whose ranks exported `blobs` (bytes each, in rank order)."""
+    n = len(blobs)
+    keep = [ctypes.create_string_buffer(b, len(b)) for b in blobs]
+    ptrs = (_VP * max(n, 1))(*[ctypes.cast(k, _VP) for k in keep])
+    sizes = (ctypes.c_size_t * max(n, 1))(*[len(b) for b in blobs])
+    m = aiwc_metrics()
+    if opcode_hist is not None:
+        m.opcode_hist = _hist_ptr(opcode_hist)
+    _check(lib.aiwc_shard_merge(h, ptrs, sizes, n, ctypes.byref(m)), h)
     return _to_dict(m)
 
 

@@ -441,5 +441,8 @@ void launch_finalize(const FinalizeArgs& a, cudaStream_t s);
 // Partitioned invocations: adds one partition's arena (and overflow entries) to the total's.
 void launch_merge_partition(const Arena* part, const u64* part_over, u64 part_cap, Arena* total, u64* total_over,
                             u64 total_cap, cudaStream_t s);
+// Sharded invocations: dst[i] += src[i] (opcode histograms), dst[i] |= src[i] (work-item bitmap words).
+void launch_add_u64(u64* dst, const u64* src, u64 n, int sm_count, cudaStream_t s);
+void launch_or_u32(u32* dst, const u32* src, u64 n, int sm_count, cudaStream_t s);
 
 }  // namespace aiwc

@@ -24,6 +24,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "aiwc_internal.cuh"
+#include "route.h"
 
 using namespace aiwc;
 
@@ -177,6 +178,10 @@ struct aiwc_handle {
   u32 part_err = 0;                // routing found an invalid run (reported by compute)
   Arena* total = nullptr;          // the partitions' merged distributions
   DevBuf over_total;
+  // sharded invocations: this rank's exported distributions, held until the
+  // caller takes them; staging for the blobs being merged
+  std::vector<uint8_t> shard_blob;
+  DevBuf shard_tmp;
 };
 
 namespace {
@@ -518,15 +523,6 @@ aiwc_status reset_device_state(aiwc_handle* h, cudaStream_t st) {
 
 // ---------------------------------------------------------------- partitioned invocations
 
-// Partition of a routing key (SplitMix64's output function, Steele, Lea &
-// Flood 2014, as a hash).
-inline u32 part_of(uint64_t key, u32 n_parts) {
-  uint64_t z = key + 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return (u32)((z ^ (z >> 31)) & (uint64_t)(n_parts - 1));
-}
-
 bool routing(const aiwc_handle* h) { return !h->parts.empty() && !h->replaying; }
 
 // Host copy of caller data (device pointers are read back first).
@@ -542,51 +538,6 @@ aiwc_status host_view(aiwc_handle* h, const T* p, size_t n, int on_device, std::
   return AIWC_OK;
 }
 
-// A stable partition of n items over the host's cores: the partition of
-// each item, per-thread counts, offsets by (partition, thread), then each
-// thread copies its items in order. `key(i)` names item i's partition;
-// `size(i)` its length in units; `copy(i, p, at)` writes item i to
-// partition p at unit offset `at`; `grow(p, units)` resizes partition p.
-template <typename Key, typename Size, typename Grow, typename Copy>
-void stable_partition(size_t n, u32 P, Key key, Size size, Grow grow, Copy copy) {
-  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-  const size_t T = n < (1u << 16) ? 1 : std::min<size_t>(hw, 32);
-  std::vector<uint8_t> pid(n);
-  std::vector<std::vector<uint64_t>> cnt(T, std::vector<uint64_t>(P, 0));
-  auto range = [&](size_t t) { return std::make_pair(n * t / T, n * (t + 1) / T); };
-  auto par = [&](auto fn) {
-    std::vector<std::thread> ts;
-    for (size_t t = 1; t < T; ++t) ts.emplace_back(fn, t);
-    fn(0);
-    for (auto& th : ts) th.join();
-  };
-  par([&](size_t t) {
-    auto r = range(t);
-    for (size_t i = r.first; i < r.second; ++i) {
-      const u32 p = key(i);
-      pid[i] = (uint8_t)p;
-      cnt[t][p] += size(i);
-    }
-  });
-  std::vector<std::vector<uint64_t>> at(T, std::vector<uint64_t>(P, 0));
-  for (u32 p = 0; p < P; ++p) {
-    uint64_t base = grow(p, 0);  // current length
-    for (size_t t = 0; t < T; ++t) {
-      at[t][p] = base;
-      base += cnt[t][p];
-    }
-    grow(p, base);
-  }
-  par([&](size_t t) {
-    auto r = range(t);
-    for (size_t i = r.first; i < r.second; ++i) {
-      const u32 p = pid[i];
-      copy(i, p, at[t][p]);
-      at[t][p] += size(i);
-    }
-  });
-}
-
 // Memory events go with their superblock (space, address >> 11): every
 // skip-level group lies inside one superblock, so a partition's groups are
 // whole.
@@ -596,39 +547,13 @@ aiwc_status route_mem(aiwc_handle* h, const aiwc_mem_event* ev, size_t n, int on
   aiwc_status s = host_view(h, ev, n, on_device, &tmp, &e);
   if (s != AIWC_OK) return s;
   std::vector<aiwc_mem_event> split;
-  if (h->cfg.byte_addresses) {
-    // a partition holds whole superblocks: an access whose bytes cross a
-    // superblock boundary travels as two accesses, one on each side
-    auto crosses = [](const aiwc_mem_event& x) {
-      return x.addr < AIWC_ADDR_LIMIT && x.size > 1 && (x.addr >> 11) != ((x.addr + x.size - 1) >> 11);
-    };
-    size_t cross = 0;
-    for (size_t i = 0; i < n; ++i) cross += crosses(e[i]) ? 1 : 0;
-    if (cross) {
-      split.reserve(n + cross);
-      for (size_t i = 0; i < n; ++i) {
-        if (!crosses(e[i])) {
-          split.push_back(e[i]);
-          continue;
-        }
-        const uint64_t b = ((e[i].addr >> 11) + 1) << 11;
-        aiwc_mem_event lo = e[i], hi = e[i];
-        lo.size = (uint8_t)(b - e[i].addr);
-        hi.addr = b;
-        hi.size = (uint8_t)(e[i].size - lo.size);
-        split.push_back(lo);
-        split.push_back(hi);
-      }
-      e = split.data();
-      n = split.size();
-    }
+  if (h->cfg.byte_addresses && split_at_superblocks(e, n, &split)) {
+    e = split.data();
+    n = split.size();
   }
   const u32 P = (u32)h->parts.size();
   stable_partition(
-      n, P,
-      [&](size_t i) {
-        return part_of(((uint64_t)((e[i].flags >> 1) & 3u) << 56) | ((e[i].addr & (AIWC_ADDR_LIMIT - 1)) >> 11), P);
-      },
+      n, P, [&](size_t i) { return part_of(mem_route_key(e[i]), P); },
       [](size_t) { return (uint64_t)1; },
       [&](u32 p, uint64_t len) {
         auto& m = h->parts[p].mem;
@@ -721,6 +646,7 @@ aiwc_status route_widths(aiwc_handle* h, const uint16_t* w, size_t n, int on_dev
 }
 
 aiwc_status compute_partitioned(aiwc_handle* h, aiwc_metrics* out);
+aiwc_status finalize_merged(aiwc_handle* h, u64 total_cap, aiwc_metrics* out, uint64_t* user_hist);
 
 // Runs a routing step; page-locked host memory running out is AIWC_ENOMEM.
 template <typename F>
@@ -1644,7 +1570,16 @@ aiwc_status compute_partitioned(aiwc_handle* h, aiwc_metrics* out) {
     reset_host(h);
   }
   h->replaying = false;
-  // finalise the merged distributions in the handle's own arena and overflow list
+  return finalize_merged(h, total_cap, out, user_hist);
+}
+
+// The end of a partitioned or sharded invocation: the merged distributions
+// (h->total and total_cap entries of h->over_total; the opcode histogram and
+// the work-item bitmap already merged in place) are finalised in the handle's
+// own arena and overflow list.
+aiwc_status finalize_merged(aiwc_handle* h, u64 total_cap, aiwc_metrics* out, uint64_t* user_hist) {
+  cudaStream_t st = h->stream;
+  aiwc_status s;
   const u64 cap = std::max<u64>(total_cap, 1);
   ENSURE(h->over_a, cap * 8, false);
   ENSURE(h->over_b, cap * 8, false);
@@ -1827,7 +1762,7 @@ aiwc_status aiwc_destroy(aiwc_handle* h) {
   DevBuf* bufs[] = {&h->mem_a, &h->mem_b, &h->br_a, &h->br_b, &h->pat_a, &h->pat_b, &h->rk_a, &h->rk_b,
                     &h->run_sum, &h->over_a, &h->over_b, &h->counts, &h->bsums, &h->tiles, &h->stage[0],
                     &h->stage[1], &h->desc, &h->sbt, &h->sbt_scan, &h->sites, &h->over_total,
-                    &h->exp_meta};
+                    &h->exp_meta, &h->shard_tmp};
   for (DevBuf* b : bufs) release(h, *b);
   if (h->total) cudaFree(h->total);
   if (h->wi_bitmap) cudaFree(h->wi_bitmap);
@@ -1853,6 +1788,163 @@ aiwc_status aiwc_destroy(aiwc_handle* h) {
   if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
   delete h;
   return AIWC_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Host blob of one rank's exact distributions (aiwc_shard_export): this
+// header, the arena (every dense distribution and counter), the overflow
+// entries, the opcode histogram and the words of the work-item bitmap that
+// hold the rank's work-items. Valid between builds of the same library only:
+// the arena's layout is internal, its size is checked.
+struct ShardHeader {
+  uint64_t magic;
+  uint32_t version, arena_bytes;
+  uint32_t n_opcodes, history_len, space_mask, byte_addresses, history_scope, pad;
+  uint64_t max_wi;
+  uint64_t n_over;
+  uint64_t wi_word0, wi_words;
+};
+constexpr uint64_t kShardMagic = 0x3144524853435741ull;  // "AWCSHRD1" in little-endian bytes
+constexpr uint32_t kShardVersion = 1;
+
+size_t shard_blob_bytes(const ShardHeader& hd) {
+  return sizeof(ShardHeader) + hd.arena_bytes + 8 * hd.n_over + 8ull * hd.n_opcodes + 4 * hd.wi_words;
+}
+
+// Reduces what the handle holds with the finalisation deferred, copies the
+// distributions into h->shard_blob and resets the handle.
+aiwc_status shard_capture(aiwc_handle* h) {
+  cudaStream_t st = h->stream;
+  aiwc_status s = reduce_current(h, true);
+  if (s != AIWC_OK) return s;
+  CK(cudaStreamSynchronize(st));
+  CK(cudaMemcpy(h->h_state, &h->arena->st, sizeof(DevState), cudaMemcpyDeviceToHost));
+  const DevState& ds = *h->h_state;
+  ShardHeader hd{};
+  hd.magic = kShardMagic;
+  hd.version = kShardVersion;
+  hd.arena_bytes = (uint32_t)sizeof(Arena);
+  hd.n_opcodes = h->cfg.n_opcodes;
+  hd.history_len = h->cfg.history_len;
+  hd.space_mask = h->cfg.space_mask;
+  hd.byte_addresses = h->cfg.byte_addresses;
+  hd.history_scope = h->cfg.history_scope;
+  hd.max_wi = h->max_wi;
+  hd.n_over = std::min<u64>(ds.n_over, h->c_over_cap);  // an overflow is flagged in the arena's error bits
+  if (ds.wi_min <= ds.wi_max && h->wi_bitmap) {
+    hd.wi_word0 = ds.wi_min >> 5;
+    hd.wi_words = (ds.wi_max >> 5) - hd.wi_word0 + 1;
+  }
+  h->shard_blob.resize(shard_blob_bytes(hd));
+  uint8_t* b = h->shard_blob.data();
+  memcpy(b, &hd, sizeof(hd));
+  b += sizeof(hd);
+  CK(cudaMemcpy(b, h->arena, sizeof(Arena), cudaMemcpyDeviceToHost));
+  b += sizeof(Arena);
+  if (hd.n_over) CK(cudaMemcpy(b, h->over_a.p, 8 * hd.n_over, cudaMemcpyDeviceToHost));
+  b += 8 * hd.n_over;
+  CK(cudaMemcpy(b, h->d_hist, 8ull * hd.n_opcodes, cudaMemcpyDeviceToHost));
+  b += 8ull * hd.n_opcodes;
+  if (hd.wi_words) CK(cudaMemcpy(b, h->wi_bitmap + hd.wi_word0, 4 * hd.wi_words, cudaMemcpyDeviceToHost));
+  if ((s = reset_device_state(h, st)) != AIWC_OK) return s;
+  CK(cudaStreamSynchronize(st));
+  collect_stage_times(h);
+  reset_host(h);
+  return AIWC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+aiwc_status aiwc_shard_export(aiwc_handle* h, void* blob, size_t cap, size_t* size) {
+  if (!h || !size) return fail(h, AIWC_EINVAL, "null handle or size pointer", false);
+  DeviceGuard g(h->cfg.device);
+  if (h->broken) return recover(h);
+  if (!h->parts.empty())
+    return fail(h, AIWC_EINVAL, "aiwc_shard_export: a partitioned handle cannot export a shard", false);
+  if (h->shard_blob.empty()) {
+    aiwc_status s = shard_capture(h);
+    if (s != AIWC_OK) {
+      h->shard_blob.clear();
+      return s;
+    }
+  }
+  *size = h->shard_blob.size();
+  if (!blob) return AIWC_OK;
+  if (cap < h->shard_blob.size())
+    return fail(h, AIWC_EINVAL, "aiwc_shard_export: the blob buffer is smaller than *size", false);
+  memcpy(blob, h->shard_blob.data(), h->shard_blob.size());
+  h->shard_blob.clear();
+  return AIWC_OK;
+}
+
+aiwc_status aiwc_shard_merge(aiwc_handle* h, const void* const* blobs, const size_t* sizes, size_t n,
+                             aiwc_metrics* out) {
+  if (!h || !out || (n && (!blobs || !sizes))) return fail(h, AIWC_EINVAL, "null argument", false);
+  DeviceGuard g(h->cfg.device);
+  uint64_t* user_hist = out->opcode_hist;
+  if (h->broken) return recover(h);
+  if (!h->parts.empty())
+    return fail(h, AIWC_EINVAL, "aiwc_shard_merge: a partitioned handle cannot merge shards", false);
+  if (h->n_mem || h->n_br || h->n_runs || !h->pend_wi.empty())
+    return fail(h, AIWC_ESTATE, "aiwc_shard_merge: the handle holds pushed events of another invocation", false);
+  // check every blob before anything is merged
+  std::vector<ShardHeader> hds(n);
+  u64 total_cap = 0, max_over = 0, max_words = 0;
+  const u64 bitmap_words = (h->max_wi + 31) / 32;
+  for (size_t i = 0; i < n; ++i) {
+    if (!blobs[i] || sizes[i] < sizeof(ShardHeader)) return fail(h, AIWC_EINVAL, "shard blob too short", false);
+    ShardHeader& hd = hds[i];
+    memcpy(&hd, blobs[i], sizeof(hd));
+    if (hd.magic != kShardMagic || hd.version != kShardVersion || hd.arena_bytes != sizeof(Arena))
+      return fail(h, AIWC_EINVAL, "not a shard blob of this library build", false);
+    if (hd.n_opcodes != h->cfg.n_opcodes || hd.history_len != h->cfg.history_len ||
+        hd.space_mask != h->cfg.space_mask || hd.byte_addresses != h->cfg.byte_addresses ||
+        hd.history_scope != h->cfg.history_scope || hd.max_wi != h->max_wi)
+      return fail(h, AIWC_EINVAL, "shard blob reduced under another metric configuration", false);
+    if (hd.wi_words > bitmap_words || hd.wi_word0 > bitmap_words - hd.wi_words || hd.n_over > (1ull << 40) ||
+        sizes[i] != shard_blob_bytes(hd))
+      return fail(h, AIWC_EINVAL, "shard blob size or work-item range is inconsistent", false);
+    total_cap += hd.n_over;
+    max_over = std::max<u64>(max_over, hd.n_over);
+    max_words = std::max<u64>(max_words, hd.wi_words);
+  }
+  cudaStream_t st = h->stream;
+  aiwc_status s;
+  if (!h->total) {
+    CK(cudaMalloc(&h->total, sizeof(Arena)));
+    h->bytes += sizeof(Arena);
+  }
+  ENSURE(h->over_total, std::max<u64>(total_cap, 1) * 8, false);
+  ENSURE(h->over_a, std::max<u64>(max_over, 1) * 8, false);
+  ENSURE(h->shard_tmp, std::max<u64>(8ull * h->cfg.n_opcodes, 4 * max_words), false);
+  if ((s = ensure_bitmap(h)) != AIWC_OK) return s;
+  CK(cudaMemsetAsync(h->total, 0, sizeof(Arena), st));
+  launch_reset_identities(h->total, st);
+  for (size_t i = 0; i < n; ++i) {
+    const ShardHeader& hd = hds[i];
+    const uint8_t* b = static_cast<const uint8_t*>(blobs[i]) + sizeof(ShardHeader);
+    // the handle's own arena and overflow list stage this rank's distributions
+    CK(cudaMemcpyAsync(h->arena, b, sizeof(Arena), cudaMemcpyHostToDevice, st));
+    b += sizeof(Arena);
+    if (hd.n_over) CK(cudaMemcpyAsync(h->over_a.p, b, 8 * hd.n_over, cudaMemcpyHostToDevice, st));
+    b += 8 * hd.n_over;
+    launch_merge_partition(h->arena, (const u64*)h->over_a.p, hd.n_over, h->total, (u64*)h->over_total.p,
+                           total_cap, st);
+    CK(cudaMemcpyAsync(h->shard_tmp.p, b, 8ull * hd.n_opcodes, cudaMemcpyHostToDevice, st));
+    launch_add_u64((u64*)h->d_hist, (const u64*)h->shard_tmp.p, hd.n_opcodes, h->sm_count, st);
+    b += 8ull * hd.n_opcodes;
+    if (hd.wi_words) {
+      CK(cudaMemcpyAsync(h->shard_tmp.p, b, 4 * hd.wi_words, cudaMemcpyHostToDevice, st));
+      launch_or_u32(h->wi_bitmap + hd.wi_word0, (const u32*)h->shard_tmp.p, hd.wi_words, h->sm_count, st);
+    }
+  }
+  CK(cudaGetLastError());
+  return finalize_merged(h, total_cap, out, user_hist);
 }
 
 const char* aiwc_last_error(const aiwc_handle* h) { return h ? h->err.c_str() : g_last_error.c_str(); }

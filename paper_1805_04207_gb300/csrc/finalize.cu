@@ -6,6 +6,8 @@
 // every sum below runs in a fixed order (results do not depend on scheduling).
 #include <math.h>
 
+#include <algorithm>
+
 #include "aiwc_internal.cuh"
 #include "common.cuh"
 
@@ -505,6 +507,30 @@ __global__ void k_merge_arena(const Arena* part, Arena* total, u64 part_cap, u64
 }
 
 }  // namespace
+
+// Sharded invocations: a rank's opcode histogram is added to the merged one,
+// and its work-item bitmap words are ORed into the merged bitmap.
+__global__ void k_add_u64(u64* dst, const u64* src, u64 n) {
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x)
+    if (src[i]) dst[i] += src[i];
+}
+__global__ void k_or_u32(u32* dst, const u32* src, u64 n) {
+  for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (u64)gridDim.x * blockDim.x)
+    if (src[i]) dst[i] |= src[i];
+}
+
+void launch_add_u64(u64* dst, const u64* src, u64 n, int sm_count, cudaStream_t s) {
+  if (!n) return;
+  const u64 g = std::min<u64>((n + 255) / 256, (u64)sm_count * 4);
+  k_add_u64<<<(unsigned)g, 256, 0, s>>>(dst, src, n);
+  count_launches(1);
+}
+void launch_or_u32(u32* dst, const u32* src, u64 n, int sm_count, cudaStream_t s) {
+  if (!n) return;
+  const u64 g = std::min<u64>((n + 255) / 256, (u64)sm_count * 4);
+  k_or_u32<<<(unsigned)g, 256, 0, s>>>(dst, src, n);
+  count_launches(1);
+}
 
 void launch_merge_partition(const Arena* part, const u64* part_over, u64 part_cap, Arena* total, u64* total_over,
                             u64 total_cap, cudaStream_t s) {

@@ -292,15 +292,6 @@ def replica_throughput(units_per_rank: int, world: int, seconds: float) -> float
     return world * units_per_rank / seconds
 
 
-def plan_for(n_mem: int) -> dict:
-    """Per-trace plan: the sort plan for small invocations (its fixed cost is
-    lower), the hash plan with a table of about n_mem / 2 slots otherwise."""
-    if n_mem <= (1 << 15):
-        return {"plan": 1}
-    slots = 1 << max(12, min(20, (max(1, n_mem // 2) - 1).bit_length()))
-    return {"plan": 0, "table_slots": slots}
-
-
 def base_line(args, world, value, ms, extra):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": round(ms, 4), "higher_is_better": True,
@@ -314,7 +305,7 @@ def run_batched(args, P, torch, local, world, rank):
     from paper_1805_04207_gb300.api import compute_batch, push_trace
     traces = synth.batched(512, device="cuda", seed=rank)
     n_mem = sum(t.n_mem for t in traces)
-    chars = [P.Characterizer(device=local, n_opcodes=t.n_opcodes, max_work_items=1 << 20, **plan_for(t.n_mem))
+    chars = [P.Characterizer(device=local, n_opcodes=t.n_opcodes, max_work_items=1 << 20)
              for t in traces]
     for t in traces:
         t.run_wi = t.run_wi.to(torch.int32)
@@ -342,7 +333,8 @@ def run_batched(args, P, torch, local, world, rank):
                                "log-uniform 2^8..2^22, patterns stream/stencil/gemm/zipf/uniform; one "
                                "aiwc_compute_batch (one CUDA graph) per step",
                    "memory_events_per_step": n_mem, "timing": "wall clock per step incl. pushes, synchronised",
-                   "plans": "sort for <= 2^15 events, else hash with ~n/2 table slots"},
+                   "plans": "the library's automatic plan per invocation (sort plan up to 2^15 memory events, "
+                            "else hash plan with a table of at least n slots)"},
         "clocks": clocks, "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
         "result_check": {"footprint_sum": sum(o["footprint"] for o in outs)}})
 
@@ -379,7 +371,10 @@ def run_serving(args, P, torch, local, world, rank):
             # device bytes a handle holds: about 19 B per memory event, 33 B per branch event, plus
             # fixed scratch (64 MB staging pair, table, work-item bitmap, arena)
             reserve = 24 * jb["n_mem"] + 40 * n_br + (256 << 20)
-            h = srv.open(reserve, n_opcodes=64, max_work_items=1 << 26, **plan_for(jb["n_mem"]))
+            # a streamed job's first chunk does not show its size; the caller
+            # knows it and sizes the superblock table (a larger one needs no regrowth)
+            slots = 1 << max(12, min(20, (jb["n_mem"] - 1).bit_length()))
+            h = srv.open(reserve, n_opcodes=64, max_work_items=1 << 26, table_slots=slots)
             if h is None:
                 break
             for ch in chunks_of(jb):
@@ -462,7 +457,7 @@ def run_partitioned(args, P, torch, local, world, rank):
         setattr(tr, t, getattr(tr, t).contiguous().pin_memory())
     out, times, held = {}, {}, {}
     for parts in (1, args.partitions):
-        c = P.Characterizer(device=local, n_opcodes=tr.n_opcodes, partitions=parts, **plan_for(tr.n_mem))
+        c = P.Characterizer(device=local, n_opcodes=tr.n_opcodes, partitions=parts)
         for _ in range(max(3, args.warmup)):
             push_trace(c, tr)
             out[parts] = c.compute(want_hist=False)

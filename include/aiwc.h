@@ -97,12 +97,16 @@ typedef struct aiwc_config {
   uint32_t precision;     /* entropy finalisation: 0 = FP64, 1 = FP32 compensated sums (each entropy
                              within 2^-22 bits of FP64; every count identical; the linear branch
                              entropy, one division of exact integers, is FP64 in both modes) */
-  uint32_t plan;          /* distinct-address counting: 0 = auto (hash, sort on overflow), 1 = sort, 2 = hash */
+  uint32_t plan;          /* distinct-address counting: 0 = automatic, per invocation, from its first
+                             memory push of n events: n <= 2^15 takes the sort plan, larger ones the
+                             hash plan (the sort plan finishes one whose table overflowed);
+                             1 = sort (and the radix-sort branch path); 2 = hash */
   uint64_t max_work_items;/* work-item ids must be < this (sizes the work-item bitmap); 0 = 2^32 */
   uint64_t hbm_budget;    /* bytes of device scratch the handle may hold; 0 = unlimited */
-  uint64_t table_slots;   /* hash plan: initial superblock-table slots (power of two, 0 = 2^20); an
-                             invocation that overflows the table is finished by the sort plan and
-                             the next one gets a 4x larger table */
+  uint64_t table_slots;   /* hash plan: initial superblock-table slots (power of two); 0 = automatic:
+                             at least n slots for a first memory push of n events, 2^12 .. 2^20,
+                             never shrinking. An invocation that overflows the table is finished by
+                             the sort plan and the next one gets a 4x larger table */
   uint32_t partitions;    /* invocations larger than device memory (Sec. VI names the trace size as the
                              tool's limit): 0 or 1 = off; P > 1 (a power of two <= 256) routes pushes on
                              the host into P partitions that keep every unit of the method whole --

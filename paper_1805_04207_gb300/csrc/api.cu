@@ -130,6 +130,8 @@ struct aiwc_handle {
   DevBuf sbt, sbt_scan;
   u64 sbt_cap = 0;       // slots currently allocated
   u64 sbt_want = 1ull << 20;
+  u64 sbt_floor = 0;     // slots an overflowing invocation asked for (the automatic size never goes below)
+  int inv_plan = 0;      // plan 0: this invocation's memory plan, chosen by its first memory push (1 sort, 2 hash)
   DevState* h_state = nullptr;  // pinned copy of the device counters
   DevBuf sites;                 // per-site segment list
   bool last_plan_hash = false;
@@ -332,7 +334,25 @@ aiwc_status staged_copy(aiwc_handle* h, const void* src, size_t bytes, size_t un
   return AIWC_OK;
 }
 
-bool use_hash(const aiwc_handle* h) { return h->cfg.plan != 1; }
+bool use_hash(const aiwc_handle* h) { return h->cfg.plan == 2 || (h->cfg.plan == 0 && h->inv_plan != 1); }
+
+// Automatic planning (plan 0), per invocation, from its first memory push of
+// n events: up to kAutoSortMax events take the sort plan (its fixed cost, a
+// few radix passes over a small array, is below the hash plan's table clear
+// and scan); larger ones the hash plan with a table of at least n slots
+// (table_slots 0: a single push cannot overflow it), between 2^12 and 2^20
+// and never below what an earlier overflow asked for. The table only grows
+// between invocations.
+constexpr u64 kAutoSortMax = 1ull << 15;
+void auto_plan(aiwc_handle* h, u64 n) {
+  if (h->cfg.plan != 0) return;
+  h->inv_plan = n <= kAutoSortMax ? 1 : 2;
+  if (h->inv_plan == 2 && !h->cfg.table_slots) {
+    u64 want = 1ull << 12;
+    while (want < n && want < kMaxHashSlots) want <<= 1;
+    h->sbt_want = std::max<u64>(want, h->sbt_floor);
+  }
+}
 
 SbTable table_view(aiwc_handle* h) {
   SbTable t;
@@ -750,6 +770,7 @@ namespace {
 // current invocation.
 aiwc_status ingest_args(aiwc_handle* h, size_t n, MemIngestArgs* a) {
   aiwc_status s;
+  if (h->n_mem == 0) auto_plan(h, n);
   ENSURE(h->mem_a, (h->n_mem + n) * 8, true);
   if ((s = ensure_bitmap(h)) != AIWC_OK) return s;
   if (use_hash(h) && (s = ensure_table(h)) != AIWC_OK) return s;
@@ -1423,6 +1444,7 @@ aiwc_status enqueue_finalize(aiwc_handle* h, cudaStream_t st) {
 
 void reset_host(aiwc_handle* h) {
   h->n_mem = h->n_br = h->n_runs = 0;
+  h->inv_plan = 0;
   h->br_pushes = 0;
   h->value_bound = 0;
   h->pend_ops.clear();
@@ -1465,7 +1487,7 @@ void plan_from_ingest(aiwc_handle* h, Plan* p) {
   const bool hashed = h->n_mem && use_hash(h) && h->sbt_cap;
   // segment offsets are 32-bit: 2^32 kept events or more go to the sort plan
   p->hash_ok = hashed && hs.sbt_overflow == 0 && hs.n_words < (1ull << 32);
-  if (hashed && hs.sbt_overflow) h->sbt_want = std::min<u64>(h->sbt_cap * 4, kMaxHashSlots);
+  if (hashed && hs.sbt_overflow) h->sbt_want = h->sbt_floor = std::min<u64>(h->sbt_cap * 4, kMaxHashSlots);
   p->br_passes = active_passes(hs.br_or, hs.br_and, hs.br_unsorted ? ~1ull : 0xFFFFFFFF00000000ull);
   p->run_passes = hs.run_unsorted ? active_passes(hs.run_or, hs.run_and, ~0ull) : 0u;
   // address bits sit above the store bit of the word

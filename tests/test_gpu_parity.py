@@ -370,6 +370,31 @@ def test_batch_matches_oracle_and_replays(P):
             c.close()
 
 
+def test_batch_of_64_with_automatic_plans(P):
+    """The batched workload's shapes at oracle-sized counts: 64 invocations,
+    memory events log-uniform over 2^10..2^18 and footprints over 2^6..2^16,
+    patterns drawn from the five of the batched workload, every handle on the
+    library's own plan choice (sort or hash plan, table size), reduced in one
+    graph, twice, element by element against the oracle."""
+    from paper_1805_04207_gb300.api import compute_batch, push_trace
+    traces = synth.batched(64, seed=3, lo_log2=10, hi_log2=18, f_lo_log2=6, f_hi_log2=16)
+    kinds = {t.meta["kind"] for t in traces}
+    assert kinds == set(synth.PATTERNS)
+    assert min(t.n_mem for t in traces) <= (1 << 15) < max(t.n_mem for t in traces)  # both plans occur
+    expect = [oracle.compute(t) for t in traces]
+    chars = [P.Characterizer(n_opcodes=t.n_opcodes, max_work_items=1 << 20) for t in traces]
+    dev = [t.to("cuda") for t in traces]
+    try:
+        for _ in range(2):
+            for c, t in zip(chars, dev):
+                push_trace(c, t)
+            for g, o in zip(compute_batch(chars), expect):
+                assert_parity(g, o)
+    finally:
+        for c in chars:
+            c.close()
+
+
 @pytest.mark.parametrize("n_mem", [1 << 20, (1 << 21) + 4321])
 def test_precision_fp32_compensated_within_bound(P, n_mem):
     """The FP32-compensated finalisation (c log2 c = c e + c log2 f; the first

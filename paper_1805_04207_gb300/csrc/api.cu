@@ -1676,7 +1676,15 @@ aiwc_status aiwc_compute_batch(aiwc_handle* const* hs, size_t n, aiwc_metrics* o
     plans[i].gated = true;
     plan_from_ingest(hs[i], &plans[i]);
     const aiwc_handle* h = hs[i];
+    // the branch-path choice needs the longest site, known only on the device;
+    // up to kSiteMaxLen events no site can be longer, so the per-site path is
+    // certain and the graph holds it alone
+    if (h->n_br <= kSiteMaxLen && h->cfg.history_len <= kSiteMaxHist && h->cfg.plan != 1) {
+      plans[i].gated = false;
+      plans[i].per_site = true;
+    }
     sig.insert(sig.end(), {(u64)(uintptr_t)h, h->n_mem, h->n_br, h->n_runs, h->epoch, (u64)plans[i].hash_ok,
+                           (u64)plans[i].gated,
                            plans[i].br_passes, plans[i].run_passes, h->sbt_cap, (u64)plans[i].seg_shift,
                            active_passes(h->h_state->mem_or, h->h_state->mem_and, ~0ull)});
   }

@@ -243,6 +243,76 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(SortDesc d, int pass) 
   }
 }
 
+// A sort that fits one tile (at most kSortTile keys): every pass in one block,
+// ranking as k_scatter does (stable), the keys held in shared memory between
+// passes and written back to the live buffer at the end (so `cur` does not
+// change). One launch instead of six per pass.
+__global__ void __launch_bounds__(kSortThreads) k_sort_tile(SortDesc d, u32 host_passes) {
+  int shift0;
+  if (!gate_open(d.gate, d.gate_want)) return;
+  (void)shift0;
+  __shared__ u32 wcnt[kWarps][256];
+  __shared__ u32 dofs[256];
+  __shared__ u32 wt[33];
+  __shared__ u64 buf[2][kSortTile];
+  const u64 n = umin64(umin64(*d.n, d.n_cap), (u64)kSortTile);
+  u64* live = *d.cur ? d.b : d.a;
+  for (u32 j = threadIdx.x; j < n; j += kSortThreads) buf[0][j] = live[j];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const u32 lt_mask = (1u << lane) - 1u;
+  const u64 m = eff_mask(d);
+  const u64 varying = ((*d.key_or) ^ (*d.key_and)) & m;
+  int src = 0;
+  const int passes = (64 - d.lo_bit + 7) / 8;
+  for (int p = 0; p < passes; ++p) {
+    const int shift = d.lo_bit + 8 * p;
+    if (!((host_passes >> p) & 1u) || ((varying >> shift) & 0xFFull) == 0) continue;
+    for (int i = threadIdx.x; i < kWarps * 256; i += kSortThreads) (&wcnt[0][0])[i] = 0;
+    __syncthreads();
+    u64 key[kSortItems];
+    u32 rank[kSortItems];
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+      const u32 i = (u32)w * (32 * kSortItems) + (u32)k * 32 + lane;
+      const bool valid = i < n;
+      key[k] = valid ? buf[src][i] : 0ull;
+      const u32 dig = valid ? (u32)(((key[k] & m) >> shift) & 0xFF) : 256u + lane;
+      const u32 peers = __match_any_sync(0xffffffffu, dig);
+      const u32 before = valid ? wcnt[w][dig] : 0u;
+      rank[k] = before + __popc(peers & lt_mask);
+      __syncwarp();
+      if (valid && lane == 31 - __clz(peers)) wcnt[w][dig] = before + __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    {
+      const int dg = threadIdx.x;  // one thread per digit
+      u32 tot = 0;
+#pragma unroll
+      for (int q = 0; q < kWarps; ++q) {
+        const u32 c = wcnt[q][dg];
+        wcnt[q][dg] = tot;
+        tot += c;
+      }
+      u32 all;
+      dofs[dg] = block_excl_scan<u32>(tot, &all, wt);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+      const u32 i = (u32)w * (32 * kSortItems) + (u32)k * 32 + lane;
+      if (i < n) {
+        const u32 dig = (u32)(((key[k] & m) >> shift) & 0xFF);
+        buf[src ^ 1][dofs[dig] + wcnt[w][dig] + rank[k]] = key[k];
+      }
+    }
+    __syncthreads();
+    src ^= 1;
+  }
+  if (src)
+    for (u32 j = threadIdx.x; j < n; j += kSortThreads) live[j] = buf[1][j];
+}
+
 __global__ void k_flip(SortDesc d, int pass) {
   int shift;
   if (pass_shift(d, pass, &shift)) *d.cur ^= 1u;
@@ -264,6 +334,13 @@ u32 sort_tiles(u64 n) { return (u32)((n + kSortTile - 1) / kSortTile); }
 
 void sort_keys(const SortDesc& d, cudaStream_t s, u32 host_passes) {
   if (d.ntiles == 0) return;
+  if (d.ntiles == 1) {  // one tile: every pass in one launch
+    if (host_passes & ((1u << ((64 - d.lo_bit + 7) / 8)) - 1u)) {
+      k_sort_tile<<<1, kSortThreads, 0, s>>>(d, host_passes);
+      count_launches(1);
+    }
+    return;
+  }
   const u64 len = 256ull * d.ntiles;
   const u32 nb = (u32)((len + kScanBlock - 1) / kScanBlock);
   const int passes = (64 - d.lo_bit + 7) / 8;

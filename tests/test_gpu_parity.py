@@ -379,7 +379,7 @@ def test_batch_of_64_with_automatic_plans(P):
     from paper_1805_04207_gb300.api import compute_batch, push_trace
     traces = synth.batched(64, seed=3, lo_log2=10, hi_log2=18, f_lo_log2=6, f_hi_log2=16)
     kinds = {t.meta["kind"] for t in traces}
-    assert kinds == set(synth.PATTERNS)
+    assert kinds == set(synth.traces.PATTERNS)
     assert min(t.n_mem for t in traces) <= (1 << 15) < max(t.n_mem for t in traces)  # both plans occur
     expect = [oracle.compute(t) for t in traces]
     chars = [P.Characterizer(n_opcodes=t.n_opcodes, max_work_items=1 << 20) for t in traces]

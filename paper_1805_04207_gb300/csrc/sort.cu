@@ -248,9 +248,7 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(SortDesc d, int pass) 
 // passes and written back to the live buffer at the end (so `cur` does not
 // change). One launch instead of six per pass.
 __global__ void __launch_bounds__(kSortThreads) k_sort_tile(SortDesc d, u32 host_passes) {
-  int shift0;
   if (!gate_open(d.gate, d.gate_want)) return;
-  (void)shift0;
   __shared__ u32 wcnt[kWarps][256];
   __shared__ u32 dofs[256];
   __shared__ u32 wt[33];
@@ -263,6 +261,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_tile(SortDesc d, u32 host
   const u64 m = eff_mask(d);
   const u64 varying = ((*d.key_or) ^ (*d.key_and)) & m;
   int src = 0;
+  bool ran = false;
   const int passes = (64 - d.lo_bit + 7) / 8;
   for (int p = 0; p < passes; ++p) {
     const int shift = d.lo_bit + 8 * p;
@@ -308,9 +307,10 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_tile(SortDesc d, u32 host
     }
     __syncthreads();
     src ^= 1;
+    ran = true;
   }
-  if (src)
-    for (u32 j = threadIdx.x; j < n; j += kSortThreads) live[j] = buf[1][j];
+  if (ran)
+    for (u32 j = threadIdx.x; j < n; j += kSortThreads) live[j] = buf[src][j];
 }
 
 __global__ void k_flip(SortDesc d, int pass) {

@@ -27,10 +27,11 @@ __device__ __forceinline__ void place_words(const MemIngestArgs& a, DevState* st
                                             const bool (&keep)[ITEMS], u64 (&sw)[ITEMS], u32* sbt_fail) {
   const int lane = threadIdx.x & 31;
   // batch the home-slot loads, then resolve
-  u64 pos[ITEMS], first[ITEMS];
+  u32 pos[ITEMS];
+  u64 first[ITEMS];
 #pragma unroll
   for (int k = 0; k < ITEMS; ++k) {
-    pos[k] = sbt_hash((word[k] >> 12) + 1ull) & a.tab.mask;
+    pos[k] = (u32)(sbt_hash((word[k] >> 12) + 1ull) & a.tab.mask);
     // an L1-cached copy may still read 0 for a slot another SM just
     // claimed; sbt_place then loses the CAS and reads the real key
     first[k] = keep[k] ? a.tab.keys[pos[k]] : 0ull;
@@ -108,7 +109,10 @@ __global__ void __launch_bounds__(kIngestThreads, HASH ? 6 : 3) k_mem_ingest(Mem
   DevState* st = &a.arena->st;
   const uint4* ev = reinterpret_cast<const uint4*>(a.ev);
   const int lane = threadIdx.x & 31;
-  u64 writes = 0, wor = 0, wand = ~0ull, kept = 0;
+  // per thread: counts fit 32 bits; the hash plan keeps no AND over the words
+  // (the sort fallback then treats every set bit as varying, a superset)
+  u32 writes = 0, kept = 0;
+  u64 wor = 0, wand = HASH ? 0ull : ~0ull;
   u32 wmin = 0xFFFFFFFFu, wmax = 0u, err = 0u, sbt_fail = 0u;
   const u64 per_block = (u64)kIngestThreads * ITEMS;
   for (u64 t0 = (u64)blockIdx.x * per_block; t0 < a.n; t0 += (u64)gridDim.x * per_block) {
@@ -144,7 +148,7 @@ __global__ void __launch_bounds__(kIngestThreads, HASH ? 6 : 3) k_mem_ingest(Mem
         ++nkeep;
         writes += store;  // reads follow from the kept count
         wor |= word[k];
-        wand &= word[k];
+        if (!HASH) wand &= word[k];
       }
     }
     kept += nkeep;
@@ -187,11 +191,11 @@ __global__ void __launch_bounds__(kIngestThreads, HASH ? 6 : 3) k_mem_ingest(Mem
       }
     }
   }
-  writes = block_reduce(writes, OpAdd(), 0ull, red64);
+  const u64 b_writes = block_reduce((u64)writes, OpAdd(), 0ull, red64);
   wor = block_reduce(wor, OpOr(), 0ull, red64);
-  wand = block_reduce(wand, OpAnd(), ~0ull, red64);
-  kept = block_reduce(kept, OpAdd(), 0ull, red64);
-  const u64 reads = kept - writes;
+  if (!HASH) wand = block_reduce(wand, OpAnd(), ~0ull, red64);
+  const u64 b_kept = block_reduce((u64)kept, OpAdd(), 0ull, red64);
+  const u64 reads = b_kept - b_writes;
   wmin = block_reduce(wmin, OpMin(), 0xFFFFFFFFu, red32);
   wmax = block_reduce(wmax, OpMax(), 0u, red32);
   err = block_reduce(err, OpOr(), 0u, red32);
@@ -199,11 +203,11 @@ __global__ void __launch_bounds__(kIngestThreads, HASH ? 6 : 3) k_mem_ingest(Mem
   if (threadIdx.x == 0) {
     if (sbt_fail) atomicOr(&st->sbt_overflow, 1u);
     if (reads) atomicAdd(&st->total_reads, reads);
-    if (writes) atomicAdd(&st->total_writes, writes);
-    if (kept) {
+    if (b_writes) atomicAdd(&st->total_writes, b_writes);
+    if (b_kept) {
       atomicOr(&st->mem_or, wor);
       atomicAnd(&st->mem_and, wand);
-      if (!FILTER) atomicAdd(&st->n_words, kept);
+      if (!FILTER) atomicAdd(&st->n_words, b_kept);
     }
     if (wmin <= wmax) {
       atomicMin(&st->wi_min, wmin);

@@ -310,10 +310,27 @@ def run_batched(args, P, torch, local, world, rank):
     for t in traces:
         t.run_wi = t.run_wi.to(torch.int32)
 
-    def step():
+    stream = torch.cuda.current_stream()
+    split = {"push_s": 0.0, "compute_s": 0.0, "push_gpu_ms": 0.0, "compute_gpu_ms": 0.0}
+
+    def step(measure=False):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        t0 = time.perf_counter()
+        e0.record(stream)
         for c, t in zip(chars, traces):
             push_trace(c, t)
-        return compute_batch(chars, want_hist=False)
+        e1.record(stream)
+        t1 = time.perf_counter()
+        out = compute_batch(chars, want_hist=False)
+        e2.record(stream)
+        t2 = time.perf_counter()
+        if measure:
+            e2.synchronize()
+            split["push_s"] += t1 - t0
+            split["compute_s"] += t2 - t1
+            split["push_gpu_ms"] += e0.elapsed_time(e1)
+            split["compute_gpu_ms"] += e1.elapsed_time(e2)
+        return out
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
@@ -326,6 +343,12 @@ def run_batched(args, P, torch, local, world, rank):
     dt = (time.perf_counter() - t0) / args.steps
     clocks = sampler.stop()
     launches = P.aiwc_kernel_launches() - l0
+    # the same steps again, each split into its pushes and its batched compute
+    # (wall clock and CUDA events on the stream), outside the timed region
+    for _ in range(args.steps):
+        step(measure=True)
+    breakdown = {k: round((v * 1e3 if k.endswith("_s") else v) / args.steps, 3) for k, v in split.items()}
+    breakdown = {k.replace("_s", "_ms"): v for k, v in breakdown.items()}
     for c in chars:
         c.close()
     return base_line(args, world, world * n_mem / dt, dt * 1e3, {
@@ -336,6 +359,7 @@ def run_batched(args, P, torch, local, world, rank):
                    "plans": "the library's automatic plan per invocation (sort plan up to 2^15 memory events, "
                             "else hash plan with a table of at least n slots)"},
         "clocks": clocks, "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
+        "step_breakdown_ms": breakdown,
         "result_check": {"footprint_sum": sum(o["footprint"] for o in outs)}})
 
 

@@ -104,29 +104,9 @@ struct SbTable {
 };
 // Slot word of the hash plan: rank << kRankShift | stripe << 32 | slot << 12
 // | the word's low 12 bits; a rank >= kRankLimit sends the invocation to the
-// sort plan (as a full table does). Bit 63 is clear.
+// sort plan (as a full table does).
 constexpr int kRankShift = 32 + kStripeBits;
-constexpr u32 kRankLimit = 1u << (31 - kStripeBits);
-// Hot superblocks. A superblock that a sample of the invocation's first
-// memory push finds among its most frequent is placed in the table before the
-// ingest, its key tagged with kHotFlag and its hot index (< kMaxHot) at bit
-// kHotIdxShift. Its events are counted over kHotStripes counters (one per
-// warp-index residue, at unrelated addresses) instead of kSbtStripes, which
-// takes the same-address atomics of the hottest superblocks off the L2's
-// critical path. Their slot words: kHotFlag | rank << kHotRankShift |
-// hot stripe << 32 | hot index << 12 | low 12 bits.
-constexpr u64 kHotFlag = 1ull << 63;
-constexpr int kHotIdxShift = 53;
-constexpr u64 kKeyMask = (1ull << kHotIdxShift) - 1;  // superblock keys are below 2^53
-constexpr int kMaxHot = 64;
-constexpr int kHotStripes = 32;
-constexpr int kHotRankShift = 37;
-constexpr u32 kHotRankLimit = 1u << (63 - kHotRankShift);
-constexpr int kHotCntStride = 8;                      // u32 words between counters (one 32-byte sector each)
-constexpr u32 kHotSampleSlots = 1u << 16;             // sample table of the hot-superblock search
-constexpr u32 kHotSamples = 1u << 16;                 // events sampled from the first push
-constexpr u32 kHotMinSamples = 16;                    // samples a superblock needs to be hot
-constexpr u64 kHotMinEvents = 1ull << 20;             // smaller first pushes take no sample
+constexpr u32 kRankLimit = 1u << (32 - kStripeBits);
 
 // Sort slots (index into DevState::sort_cur).
 enum SortSlot { kSortMem = 0, kSortBranch = 1, kSortPattern = 2, kSortRuns = 3, kSortOver = 4 };
@@ -152,13 +132,6 @@ struct Arena {
   u32 yok_done;
   u64 site_pat_coc[kValDense];       // m_c of the predicted-outcome counts of sites
   u64 tag_begin[kNumTags + 1];       // segment of each tag in the sorted overflow list
-  // hot superblocks (hash plan): per (hot stripe, hot index) event counts,
-  // replaced by the stripes' segment offsets after the table scan
-  u32 hot_cnt[kHotStripes * kMaxHot * kHotCntStride];
-  u64 hot_key[kMaxHot];              // superblock key + 1 of each hot index
-  u32 hot_slot[kMaxHot];             // its table slot
-  u32 n_hot;
-  u32 hot_pad;
 };
 // the order statistics read the value bins 16 bytes at a time
 static_assert(offsetof(Arena, itb_dense) % 16 == 0 && offsetof(Arena, ipt_dense) % 16 == 0,
@@ -228,12 +201,6 @@ struct MemIngestArgs {
   Arena* arena{};
 };
 void launch_mem_ingest(const MemIngestArgs& a, cudaStream_t s);
-// Hot superblocks: samples kHotSamples of the push's n events (space mask
-// applied) into the sample table, picks up to kMaxHot superblocks with at
-// least kHotMinSamples samples, places them in the (empty) table tagged hot
-// and clears the sample table. samp: kHotSampleSlots keys then counts.
-void launch_hot_detect(const void* ev, u64 n, u32 space_mask, SbTable tab, u64* samp, Arena* arena, cudaStream_t s);
-size_t hot_sample_bytes();
 
 // Byte-granular addresses: the one-byte accesses of a chunk of memory events
 // (addr + b for b < size, with the event's kind and space), for the events

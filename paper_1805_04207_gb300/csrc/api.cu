@@ -184,7 +184,6 @@ struct aiwc_handle {
   // caller takes them; staging for the blobs being merged
   std::vector<uint8_t> shard_blob;
   DevBuf shard_tmp;
-  DevBuf hot_samp;  // sample table of the hot-superblock search (kept cleared between uses)
 };
 
 namespace {
@@ -797,17 +796,10 @@ aiwc_status push_mem_events(aiwc_handle* h, const aiwc_mem_event* ev, size_t n, 
   aiwc_status s = ingest_args(h, n, &a);
   if (s != AIWC_OK) return s;
   const u64 base = h->n_mem;
-  // the first push of a hash-plan invocation looks for its hot superblocks
-  const bool detect = a.use_tab && base == 0 && n >= kHotMinEvents;
-  if (detect && !h->hot_samp.p) {
-    ENSURE(h->hot_samp, hot_sample_bytes(), false);
-    CK(cudaMemsetAsync(h->hot_samp.p, 0, hot_sample_bytes(), h->stream));
-  }
   StageScope scope(h, kStMemIngest);
   if (on_device) {
     a.ev = ev;
     a.n = n;
-    if (detect) launch_hot_detect(ev, n, a.space_mask, a.tab, (u64*)h->hot_samp.p, h->arena, h->stream);
     launch_mem_ingest(a, h->stream);
     CK(cudaGetLastError());
   } else {
@@ -816,8 +808,6 @@ aiwc_status push_mem_events(aiwc_handle* h, const aiwc_mem_event* ev, size_t n, 
       b.ev = p;
       b.n = cnt;
       b.word_base = base + first;
-      if (detect && first == 0)  // the first staged piece stands for the push
-        launch_hot_detect(p, cnt, a.space_mask, a.tab, (u64*)h->hot_samp.p, h->arena, h->stream);
       launch_mem_ingest(b, h->stream);
     });
     if (s != AIWC_OK) return s;
@@ -1802,7 +1792,7 @@ aiwc_status aiwc_destroy(aiwc_handle* h) {
   DevBuf* bufs[] = {&h->mem_a, &h->mem_b, &h->br_a, &h->br_b, &h->pat_a, &h->pat_b, &h->rk_a, &h->rk_b,
                     &h->run_sum, &h->over_a, &h->over_b, &h->counts, &h->bsums, &h->tiles, &h->stage[0],
                     &h->stage[1], &h->desc, &h->sbt, &h->sbt_scan, &h->sites, &h->over_total,
-                    &h->exp_meta, &h->shard_tmp, &h->hot_samp};
+                    &h->exp_meta, &h->shard_tmp};
   for (DevBuf* b : bufs) release(h, *b);
   if (h->total) cudaFree(h->total);
   if (h->wi_bitmap) cudaFree(h->wi_bitmap);

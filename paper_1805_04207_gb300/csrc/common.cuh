@@ -89,27 +89,15 @@ __device__ __forceinline__ u64 sbt_hash(u64 k) {
   return (u64)(y ^ (y >> 15));
 }
 
-// Slot of key k (> 0, below 2^53), inserting it if absent; kNoSlot when the
-// probe limit is reached. `first` is keys[pos] already loaded for the home
-// position pos. Stored keys may carry the hot tag above kKeyMask; *stored
-// receives the stored word of the slot (tag included).
-__device__ __forceinline__ u32 sbt_place(const SbTable& t, u64 k, u64 pos, u64 first, u64* stored) {
+// Slot of key k (> 0), inserting it if absent; kNoSlot when the probe limit is
+// reached. `first` is keys[pos] already loaded for the home position pos.
+__device__ __forceinline__ u32 sbt_place(const SbTable& t, u64 k, u64 pos, u64 first) {
   u64 cur = first;
   for (int p = 0; p < kMaxProbe; ++p) {
-    if ((cur & kKeyMask) == k) {
-      *stored = cur;
-      return (u32)pos;
-    }
+    if (cur == k) return (u32)pos;
     if (cur == 0ull) {
       const u64 old = atomicCAS(&t.keys[pos], 0ull, k);
-      if (old == 0ull) {
-        *stored = k;
-        return (u32)pos;
-      }
-      if ((old & kKeyMask) == k) {
-        *stored = old;
-        return (u32)pos;
-      }
+      if (old == 0ull || old == k) return (u32)pos;
     }
     pos = (pos + 1) & t.mask;
     cur = __ldcg(&t.keys[pos]);
@@ -122,7 +110,7 @@ __device__ __forceinline__ u32 sbt_find(const SbTable& t, u64 k) {
   u64 pos = sbt_hash(k) & t.mask;
   for (int p = 0; p < kMaxProbe; ++p) {
     const u64 cur = t.keys[pos];
-    if ((cur & kKeyMask) == k) return (u32)pos;
+    if (cur == k) return (u32)pos;
     if (cur == 0ull) return kNoSlot;
     pos = (pos + 1) & t.mask;
   }

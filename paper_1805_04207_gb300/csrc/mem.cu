@@ -36,29 +36,22 @@ __device__ __forceinline__ void place_words(const MemIngestArgs& a, DevState* st
     // claimed; sbt_place then loses the CAS and reads the real key
     first[k] = keep[k] ? a.tab.keys[pos[k]] : 0ull;
   }
-  u32 slot[ITEMS], hot[ITEMS];  // hot: hot index + 1, 0 for an ordinary superblock
+  u32 slot[ITEMS];
 #pragma unroll
   for (int k = 0; k < ITEMS; ++k) {
     slot[k] = kNoSlot;
-    hot[k] = 0u;
     if (keep[k]) {
-      u64 stored = 0;
-      slot[k] = sbt_place(a.tab, (word[k] >> 12) + 1ull, pos[k], first[k], &stored);
+      slot[k] = sbt_place(a.tab, (word[k] >> 12) + 1ull, pos[k], first[k]);
       if (slot[k] == kNoSlot) {
         *sbt_fail = 1u;
         a.spill[atomicAdd(&st->n_spill, 1ull)] = word[k];
-      } else if (stored & kHotFlag) {
-        hot[k] = (u32)((stored >> kHotIdxShift) & (u64)(kMaxHot - 1)) + 1u;
       }
     }
   }
   // all counting atomics in flight before any result is needed; this warp's
-  // counter stripe (and hot stripe)
-  const u32 gw = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-  const u32 stripe = gw & (u32)(kSbtStripes - 1);
-  const u32 hstripe = gw & (u32)(kHotStripes - 1);
+  // counter stripe
+  const u32 stripe = (blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5)) & (u32)(kSbtStripes - 1);
   u32* cnt_s = a.tab.cnt + (u64)stripe * (a.tab.mask + 1);
-  u32* hot_s = a.arena->hot_cnt + hstripe * (kMaxHot * kHotCntStride);
   u32 peers[ITEMS], rb[ITEMS];
 #pragma unroll
   for (int k = 0; k < ITEMS; ++k)
@@ -66,22 +59,15 @@ __device__ __forceinline__ void place_words(const MemIngestArgs& a, DevState* st
 #pragma unroll
   for (int k = 0; k < ITEMS; ++k) {
     rb[k] = 0u;
-    if (slot[k] != kNoSlot && lane == __ffs(peers[k]) - 1)
-      rb[k] = atomicAdd(hot[k] ? hot_s + (hot[k] - 1u) * kHotCntStride : cnt_s + slot[k], (u32)__popc(peers[k]));
+    if (slot[k] != kNoSlot && lane == __ffs(peers[k]) - 1) rb[k] = atomicAdd(&cnt_s[slot[k]], (u32)__popc(peers[k]));
   }
 #pragma unroll
   for (int k = 0; k < ITEMS; ++k) {
     const u32 r = __shfl_sync(0xffffffffu, rb[k], __ffs(peers[k]) - 1) + (u32)__popc(peers[k] & ((1u << lane) - 1u));
-    const u32 low = (u32)(word[k] & 0xFFFull);
-    if (slot[k] == kNoSlot) {
-      sw[k] = (u64)kSlotWordNone;
-    } else if (hot[k]) {
-      if (r >= kHotRankLimit) *sbt_fail = 1u;
-      sw[k] = kHotFlag | ((u64)r << kHotRankShift) | ((u64)hstripe << 32) | ((hot[k] - 1u) << 12) | low;
-    } else {
-      if (r >= kRankLimit) *sbt_fail = 1u;
-      sw[k] = ((u64)r << kRankShift) | ((u64)stripe << 32) | (slot[k] << 12) | low;
-    }
+    if (slot[k] != kNoSlot && r >= kRankLimit) *sbt_fail = 1u;
+    sw[k] = slot[k] != kNoSlot ? (((u64)r << kRankShift) | ((u64)stripe << 32) | (slot[k] << 12) |
+                                  (u32)(word[k] & 0xFFFull))
+                               : (u64)kSlotWordNone;
   }
 }
 

@@ -150,124 +150,6 @@ __global__ void __launch_bounds__(kScanT) k_sbt_down(u32* cnt, u64 len, const u3
   }
 }
 
-// Hot superblocks, before the scan: each hot superblock's count is the sum
-// of its hot stripes (its ordinary stripes count nothing).
-__global__ void k_hot_fold(HashArgs a) {
-  if (!gate_open(a.gate, a.gate_want)) return;
-  Arena* ar = a.arena;
-  const u32 h = threadIdx.x;
-  if (h >= ar->n_hot || h >= (u32)kMaxHot) return;
-  if (ar->hot_slot[h] == kNoSlot) return;
-  u32 t = 0;
-  for (int s = 0; s < kHotStripes; ++s) t += ar->hot_cnt[(s * kMaxHot + h) * kHotCntStride];
-  a.tab.cnt[ar->hot_slot[h]] += t;
-}
-
-// ... after the scan: each hot stripe's count becomes the offset where its
-// events start in the superblock's segment.
-__global__ void k_hot_offsets(HashArgs a) {
-  if (!gate_open(a.gate, a.gate_want)) return;
-  Arena* ar = a.arena;
-  const u32 h = threadIdx.x;
-  if (h >= ar->n_hot || h >= (u32)kMaxHot || ar->hot_slot[h] == kNoSlot) return;
-  u32 at = a.tab.off[ar->hot_slot[h]];
-  for (int s = 0; s < kHotStripes; ++s) {
-    u32* c = &ar->hot_cnt[(s * kMaxHot + h) * kHotCntStride];
-    const u32 v = *c;
-    *c = at;
-    at += v;
-  }
-}
-
-// Hot-superblock search, one sample of the first memory push: kHotSamples
-// events spread evenly over it, their superblocks counted in an
-// open-addressing sample table (keys, then u32 counts).
-__global__ void __launch_bounds__(256) k_hot_sample(const uint4* ev, u64 n, u32 space_mask, u64* samp) {
-  const u32 j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= kHotSamples) return;
-  const uint4 e = ev[(u64)j * n / kHotSamples];
-  const u32 space = (e.w >> 9) & 3u;
-  if (!((space_mask >> space) & 1u) || (e.y >> 29)) return;
-  const u64 addr = (u64)e.x | ((u64)e.y << 32);
-  const u64 key = (((u64)space << 50) | (addr >> 11)) + 1ull;
-  u64* keys = samp;
-  u32* cnt = reinterpret_cast<u32*>(samp + kHotSampleSlots);
-  u32 h = (u32)sbt_hash(key) & (kHotSampleSlots - 1);
-  for (int p = 0; p < 64; ++p) {
-    const u64 cur = keys[h];
-    if (cur == key) {
-      atomicAdd(&cnt[h], 1u);
-      return;
-    }
-    if (cur == 0ull) {
-      const u64 old = atomicCAS(&keys[h], 0ull, key);
-      if (old == 0ull || old == key) {
-        atomicAdd(&cnt[h], 1u);
-        return;
-      }
-    }
-    h = (h + 1) & (kHotSampleSlots - 1);
-  }
-  // a full neighbourhood drops the sample: the search is a heuristic
-}
-
-// One block: the superblocks with at least kHotMinSamples samples, the most
-// frequent kMaxHot of them when there are more (the threshold doubles until
-// they fit), are placed in the empty superblock table with the hot tag; the
-// sample table is cleared for the next invocation.
-constexpr int kSelThreads = 1024;
-constexpr u32 kMaxCand = kHotSamples / kHotMinSamples;
-__global__ void __launch_bounds__(kSelThreads) k_hot_select(SbTable tab, u64* samp, Arena* ar) {
-  __shared__ u32 cand[kMaxCand];
-  __shared__ u32 ncand, nsel, nabove;
-  u64* keys = samp;
-  u32* cnt = reinterpret_cast<u32*>(samp + kHotSampleSlots);
-  if (threadIdx.x == 0) ncand = nsel = 0u;
-  __syncthreads();
-  for (u32 i = threadIdx.x; i < kHotSampleSlots; i += kSelThreads)
-    if (cnt[i] >= kHotMinSamples) {
-      const u32 q = atomicAdd(&ncand, 1u);
-      if (q < kMaxCand) cand[q] = i;
-    }
-  __syncthreads();
-  const u32 nc = min(ncand, kMaxCand);
-  u32 thr = kHotMinSamples;
-  for (;;) {  // at most log2(kHotSamples) rounds
-    if (threadIdx.x == 0) nabove = 0u;
-    __syncthreads();
-    for (u32 q = threadIdx.x; q < nc; q += kSelThreads)
-      if (cnt[cand[q]] >= thr) atomicAdd(&nabove, 1u);
-    __syncthreads();
-    const u32 na = nabove;
-    __syncthreads();
-    if (na <= (u32)kMaxHot || thr > kHotSamples) break;
-    thr *= 2u;
-  }
-  for (u32 q = threadIdx.x; q < nc; q += kSelThreads) {
-    const u32 i = cand[q];
-    if (cnt[i] < thr) continue;
-    const u32 hidx = atomicAdd(&nsel, 1u);
-    if (hidx >= (u32)kMaxHot) continue;
-    const u64 key = keys[i];
-    u64 pos = sbt_hash(key) & tab.mask;
-    bool placed = false;
-    for (int p = 0; p < kMaxProbe && !placed; ++p) {
-      placed = atomicCAS(&tab.keys[pos], 0ull, key | kHotFlag | ((u64)hidx << kHotIdxShift)) == 0ull;
-      if (!placed) pos = (pos + 1) & tab.mask;
-    }
-    // a table too full to place it leaves the hot index unused: no event can
-    // reach it, and the scan skips it
-    ar->hot_key[hidx] = placed ? key : 0ull;
-    ar->hot_slot[hidx] = placed ? (u32)pos : kNoSlot;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) ar->n_hot = min(nsel, (u32)kMaxHot);
-  for (u32 i = threadIdx.x; i < kHotSampleSlots; i += kSelThreads) {
-    keys[i] = 0ull;
-    cnt[i] = 0u;
-  }
-}
-
 constexpr int kScThreads = 256;
 constexpr int kScItems = 8;
 
@@ -290,21 +172,15 @@ __global__ void __launch_bounds__(kScThreads, 4) k_mem_scatter(HashArgs a) {
 #pragma unroll
     for (int k = 0; k < kScItems; ++k) {
       const u32 w = (u32)sw[k];
-      if (sw[k] & kHotFlag) {  // hot stripe start + rank
-        const u32 hs = (u32)(sw[k] >> 32) & (u32)(kHotStripes - 1);
-        off[k] = __ldg(a.arena->hot_cnt + (hs * kMaxHot + ((w >> 12) & (kMaxHot - 1))) * kHotCntStride) +
-                 (u32)((sw[k] >> kHotRankShift) & (kHotRankLimit - 1));
-      } else {
-        const u32 stripe = (u32)(sw[k] >> 32) & (u32)(kSbtStripes - 1);
-        off[k] = w == kSlotWordNone ? 0u
-                 : (stripe ? __ldg(a.tab.cnt + (u64)stripe * C + (w >> 12)) : __ldg(a.tab.off + (w >> 12))) +
-                       (u32)(sw[k] >> kRankShift);
-      }
+      const u32 stripe = (u32)(sw[k] >> 32) & (u32)(kSbtStripes - 1);
+      off[k] = w == kSlotWordNone ? 0u
+               : stripe ? __ldg(a.tab.cnt + (u64)stripe * C + (w >> 12))
+                        : __ldg(a.tab.off + (w >> 12));
     }
 #pragma unroll
     for (int k = 0; k < kScItems; ++k) {
       const u32 w = (u32)sw[k];
-      if (w != kSlotWordNone) a.low[off[k]] = (uint16_t)(w & 0xFFFu);
+      if (w != kSlotWordNone) a.low[off[k] + (u32)(sw[k] >> kRankShift)] = (uint16_t)(w & 0xFFFu);
     }
   }
 }
@@ -324,13 +200,13 @@ __global__ void __launch_bounds__(kRbThreads) k_rebuild_words(const u64* slotw, 
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const u64 per_block = (u64)kRbThreads * kRbItems;
   for (u64 t0 = (u64)blockIdx.x * per_block; t0 < n; t0 += (u64)gridDim.x * per_block) {
-    u64 sw[kRbItems];
+    u32 sw[kRbItems];
     u32 cnt = 0;
 #pragma unroll
     for (int k = 0; k < kRbItems; ++k) {
       const u64 i = t0 + (u64)k * kRbThreads + threadIdx.x;
-      sw[k] = i < n ? slotw[i] : (u64)kSlotWordNone;
-      cnt += (u32)sw[k] != kSlotWordNone;
+      sw[k] = i < n ? (u32)slotw[i] : kSlotWordNone;
+      cnt += sw[k] != kSlotWordNone;
     }
     u32 inc = cnt;
 #pragma unroll
@@ -349,11 +225,7 @@ __global__ void __launch_bounds__(kRbThreads) k_rebuild_words(const u64* slotw, 
     u64 pos = s_base + scan_tot[w] + inc - cnt;
 #pragma unroll
     for (int k = 0; k < kRbItems; ++k)
-      if ((u32)sw[k] != kSlotWordNone) {
-        const u32 w = (u32)sw[k];
-        const u64 key = (sw[k] & kHotFlag) ? arena->hot_key[(w >> 12) & (kMaxHot - 1)] : (tab.keys[w >> 12] & kKeyMask);
-        words[pos++] = ((key - 1ull) << 12) | (w & 0xFFFu);
-      }
+      if (sw[k] != kSlotWordNone) words[pos++] = ((tab.keys[sw[k] >> 12] - 1ull) << 12) | (sw[k] & 0xFFFu);
     __syncthreads();
   }
 }
@@ -667,23 +539,12 @@ size_t sbt_scan_words(u64 cap) { return (size_t)((cap + kScanB - 1) / kScanB + 1
 void launch_mem_hash_scatter(const HashArgs& a, cudaStream_t s) {
   const u64 C = a.tab.mask + 1;
   const u32 nb = (u32)((C + kScanB - 1) / kScanB);
-  k_hot_fold<<<1, kMaxHot, 0, s>>>(a);
   k_sbt_reduce<<<nb, kScanT, 0, s>>>(a.tab.cnt, C, a.scan_tmp, a.gate, a.gate_want);
   k_sbt_top<<<1, kScanT, 0, s>>>(a.scan_tmp, nb, a.gate, a.gate_want);
   k_sbt_down<<<nb, kScanT, 0, s>>>(a.tab.cnt, C, a.scan_tmp, a.tab.off, a.n_used, a.used_list, a.gate,
                                    a.gate_want);
-  k_hot_offsets<<<1, kMaxHot, 0, s>>>(a);
   k_mem_scatter<<<a.grid_scatter, kScThreads, 0, s>>>(a);
-  count_launches(6);
-}
-
-size_t hot_sample_bytes() { return (size_t)kHotSampleSlots * 12; }
-
-void launch_hot_detect(const void* ev, u64 n, u32 space_mask, SbTable tab, u64* samp, Arena* arena, cudaStream_t s) {
-  if (n < kHotMinEvents) return;
-  k_hot_sample<<<kHotSamples / 256, 256, 0, s>>>(static_cast<const uint4*>(ev), n, space_mask, samp);
-  k_hot_select<<<1, kSelThreads, 0, s>>>(tab, samp, arena);
-  count_launches(2);
+  count_launches(4);
 }
 
 u64 mem_hash_big_segments(u64 n_words, size_t bytes, int seg_shift) {

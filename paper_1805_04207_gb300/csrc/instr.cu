@@ -344,7 +344,7 @@ void launch_instr_runs(const RunBatchArgs& a, cudaStream_t s) {
   else if (bins * 4 <= 96 * 1024) { mode = 1; smem = bins * 4; }
   else { mode = 2; smem = 0; }
   u64 blocks = (a.n_runs + kInWarps - 1) / kInWarps;
-  if (blocks > 152ull * 4) blocks = 152ull * 4;
+  if (blocks > 152ull * 16) blocks = 152ull * 16;
   if (mode == 0) k_instr_runs<0><<<(unsigned)blocks, kInThreads, smem, s>>>(a);
   else if (mode == 1) k_instr_runs<1><<<(unsigned)blocks, kInThreads, smem, s>>>(a);
   else k_instr_runs<2><<<(unsigned)blocks, kInThreads, smem, s>>>(a);

@@ -305,7 +305,9 @@ def run_batched(args, P, torch, local, world, rank):
     from paper_1805_04207_gb300.api import compute_batch, push_trace
     traces = synth.batched(512, device="cuda", seed=rank)
     n_mem = sum(t.n_mem for t in traces)
-    chars = [P.Characterizer(device=local, n_opcodes=t.n_opcodes, max_work_items=1 << 20)
+    # device pushes are deferred to the batched compute, which ingests the
+    # invocations side by side
+    chars = [P.Characterizer(device=local, n_opcodes=t.n_opcodes, max_work_items=1 << 20, defer_pushes=1)
              for t in traces]
     for t in traces:
         t.run_wi = t.run_wi.to(torch.int32)

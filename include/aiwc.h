@@ -128,6 +128,14 @@ typedef struct aiwc_config {
                              inside each); 1 = one history per (site, work-item), that work-item's
                              outcomes in program order. Patterns stay keyed by (site, history); the
                              first history_len outcomes of every history predict nothing. */
+  uint32_t defer_pushes;  /* 1: pushes of DEVICE data (memory events without byte_addresses, branch
+                             events, instruction run tables, widths) are recorded and ingested when
+                             the invocation is computed -- aiwc_compute_batch then ingests every
+                             handle's pushes on parallel streams, so that many small invocations
+                             share the GPU. The data must stay unmodified until the compute (the
+                             ownership rule of device pointers already asks this). A host push first
+                             ingests the recorded ones, so order is kept. Results are identical;
+                             push-time data errors surface at the compute. Not with partitions. */
 } aiwc_config;
 
 /* Fills the paper's defaults: history 16, 90% coverage, all address spaces,

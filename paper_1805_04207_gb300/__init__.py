@@ -28,7 +28,8 @@ class aiwc_config(ctypes.Structure):
                 ("space_mask", ctypes.c_uint32), ("precision", ctypes.c_uint32), ("plan", ctypes.c_uint32),
                 ("max_work_items", ctypes.c_uint64), ("hbm_budget", ctypes.c_uint64),
                 ("table_slots", ctypes.c_uint64), ("partitions", ctypes.c_uint32),
-                ("byte_addresses", ctypes.c_uint32), ("history_scope", ctypes.c_uint32)]
+                ("byte_addresses", ctypes.c_uint32), ("history_scope", ctypes.c_uint32),
+                ("defer_pushes", ctypes.c_uint32)]
 
 
 class aiwc_server_config(ctypes.Structure):

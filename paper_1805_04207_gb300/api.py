@@ -51,7 +51,7 @@ class Characterizer:
     def __init__(self, device: int = 0, stream=None, history_len: int = 16, cover=(9, 10), n_opcodes: int = 65535,
                  space_mask: int = 0xF, precision: int = 0, plan: int = 0, max_work_items: int = 0,
                  hbm_budget: int = 0, table_slots: int = 0, partitions: int = 0, byte_addresses: int = 0,
-                 history_scope: int = 0):
+                 history_scope: int = 0, defer_pushes: int = 0):
         if stream is None:
             try:
                 import torch
@@ -66,7 +66,8 @@ class Characterizer:
                                        space_mask=space_mask, precision=precision, plan=plan,
                                        max_work_items=max_work_items, hbm_budget=hbm_budget,
                                        table_slots=table_slots, partitions=partitions,
-                                       byte_addresses=byte_addresses, history_scope=history_scope)
+                                       byte_addresses=byte_addresses, history_scope=history_scope,
+                                       defer_pushes=defer_pushes)
         self.h = aiwc_create(self.cfg)
         self._keep = []  # device inputs must outlive the next compute
 

@@ -184,6 +184,14 @@ struct aiwc_handle {
   // caller takes them; staging for the blobs being merged
   std::vector<uint8_t> shard_blob;
   DevBuf shard_tmp;
+  // defer_pushes: device pushes recorded in order, ingested at compute time
+  struct Deferred {
+    int kind;  // 0 memory events, 1 branch events, 2 instruction runs, 3 widths
+    const void* p[4];
+    size_t n, n_ops;
+  };
+  std::vector<Deferred> deferred;
+  bool flushing = false;  // the recorded pushes are being ingested
 };
 
 namespace {
@@ -680,6 +688,53 @@ aiwc_status routed(aiwc_handle* h, F&& f) {
 
 }  // namespace
 
+namespace {
+
+// defer_pushes: does this device push wait for the compute?
+bool defers(const aiwc_handle* h, int on_device) {
+  return h->cfg.defer_pushes && on_device && !h->flushing && h->parts.empty();
+}
+
+aiwc_status record(aiwc_handle* h, int kind, const void* p0, const void* p1, const void* p2, const void* p3,
+                   size_t n, size_t n_ops) {
+  aiwc_handle::Deferred d;
+  d.kind = kind;
+  d.p[0] = p0;
+  d.p[1] = p1;
+  d.p[2] = p2;
+  d.p[3] = p3;
+  d.n = n;
+  d.n_ops = n_ops;
+  h->deferred.push_back(d);
+  return AIWC_OK;
+}
+
+}  // namespace
+
+// Ingests the recorded device pushes in their order on h->stream.
+aiwc_status flush_deferred(aiwc_handle* h) {
+  if (h->deferred.empty() || h->flushing) return AIWC_OK;
+  h->flushing = true;
+  std::vector<aiwc_handle::Deferred> list;
+  list.swap(h->deferred);
+  aiwc_status s = AIWC_OK;
+  for (const auto& d : list) {
+    switch (d.kind) {
+      case 0: s = aiwc_push_mem(h, static_cast<const aiwc_mem_event*>(d.p[0]), d.n, 1); break;
+      case 1: s = aiwc_push_branch(h, static_cast<const aiwc_branch_event*>(d.p[0]), d.n, 1); break;
+      case 2:
+        s = aiwc_push_instr_runs(h, static_cast<const uint32_t*>(d.p[0]), static_cast<const uint64_t*>(d.p[1]),
+                                 static_cast<const uint64_t*>(d.p[2]), d.n, static_cast<const uint16_t*>(d.p[3]),
+                                 d.n_ops, 1);
+        break;
+      default: s = aiwc_push_widths(h, static_cast<const uint16_t*>(d.p[0]), d.n, 1); break;
+    }
+    if (s != AIWC_OK) break;
+  }
+  h->flushing = false;
+  return s;
+}
+
 extern "C" {
 
 void aiwc_config_default(aiwc_config* c) {
@@ -715,6 +770,8 @@ aiwc_status aiwc_create(const aiwc_config* cfg, aiwc_handle** out) {
     return fail(nullptr, AIWC_EINVAL, "partitions must be 0 or a power of two <= 256");
   if (cfg->byte_addresses > 1 || cfg->history_scope > 1)
     return fail(nullptr, AIWC_EINVAL, "byte_addresses and history_scope must be 0 or 1");
+  if (cfg->defer_pushes > 1 || (cfg->defer_pushes && cfg->partitions > 1))
+    return fail(nullptr, AIWC_EINVAL, "defer_pushes must be 0 or 1, and 0 with partitions");
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
     cudaGetLastError();
@@ -888,6 +945,8 @@ aiwc_status aiwc_push_mem(aiwc_handle* h, const aiwc_mem_event* ev, size_t n, in
   DeviceGuard g(h->cfg.device);
   if (on_device && ((uintptr_t)ev & 15u))
     return fail(h, AIWC_EINVAL, "device memory events must be 16-byte aligned", false);
+  if (defers(h, on_device) && !h->cfg.byte_addresses) return record(h, 0, ev, nullptr, nullptr, nullptr, n, 0);
+  if ((s = flush_deferred(h)) != AIWC_OK) return s;
   if (routing(h)) return routed(h, [&] { return route_mem(h, ev, n, on_device); });
   if (!h->cfg.byte_addresses) return push_mem_events(h, ev, n, on_device);
   if (on_device) return expand_events(h, ev, n);
@@ -906,6 +965,8 @@ aiwc_status aiwc_push_branch(aiwc_handle* h, const aiwc_branch_event* ev, size_t
   DeviceGuard g(h->cfg.device);
   if (on_device && ((uintptr_t)ev & 7u))
     return fail(h, AIWC_EINVAL, "device branch events must be 8-byte aligned", false);
+  if (defers(h, on_device)) return record(h, 1, ev, nullptr, nullptr, nullptr, n, 0);
+  if ((s = flush_deferred(h)) != AIWC_OK) return s;
   if (routing(h)) return routed(h, [&] { return route_branch(h, ev, n, on_device); });
   ENSURE(h->br_a, (h->n_br + n) * 8, true);
   if ((s = ensure_bitmap(h)) != AIWC_OK) return s;
@@ -923,6 +984,9 @@ aiwc_status aiwc_push_branch(aiwc_handle* h, const aiwc_branch_event* ev, size_t
     a.word_base = base;
     launch_branch_ingest(a, h->stream);
     CK(cudaGetLastError());
+    h->br_pushes++;
+    h->n_br += n;
+    return AIWC_OK;
   } else {
     s = staged_copy(h, ev, n * 8, 8, [&](void* p, size_t first, size_t cnt) {
       BranchIngestArgs b = a;
@@ -934,7 +998,6 @@ aiwc_status aiwc_push_branch(aiwc_handle* h, const aiwc_branch_event* ev, size_t
     });
     if (s != AIWC_OK) return s;
   }
-  if (on_device) h->br_pushes++;
   h->n_br += n;
   return AIWC_OK;
 }
@@ -945,6 +1008,8 @@ aiwc_status aiwc_push_widths(aiwc_handle* h, const uint16_t* widths, size_t n, i
   if (n == 0) return AIWC_OK;
   if (!widths) return fail(h, AIWC_EINVAL, "null width pointer", false);
   DeviceGuard g(h->cfg.device);
+  if (defers(h, on_device)) return record(h, 3, widths, nullptr, nullptr, nullptr, n, 0);
+  if ((s = flush_deferred(h)) != AIWC_OK) return s;
   if (routing(h)) return routed(h, [&] { return route_widths(h, widths, n, on_device); });
   StageScope scope(h, kStInstrRuns);
   if (on_device) {
@@ -964,6 +1029,7 @@ aiwc_status aiwc_push_instr(aiwc_handle* h, uint32_t work_item, const uint16_t* 
   DeviceGuard g(h->cfg.device);
   const bool dev = on_device != 0;
   if (dev && ((uintptr_t)ops & 1u)) return fail(h, AIWC_EINVAL, "device opcodes must be 2-byte aligned", false);
+  if ((s = flush_deferred(h)) != AIWC_OK) return s;
   if (routing(h)) {
     const uint64_t off = 0, len = n;
     std::vector<uint16_t> one;
@@ -995,10 +1061,12 @@ aiwc_status aiwc_push_instr_runs(aiwc_handle* h, const uint32_t* run_wi, const u
   if (n_runs == 0) return AIWC_OK;
   if (!run_wi || !run_off || !run_len || (n_ops && !ops)) return fail(h, AIWC_EINVAL, "null run table", false);
   DeviceGuard g(h->cfg.device);
-  if ((s = flush_pending(h)) != AIWC_OK) return s;
   if (on_device && (((uintptr_t)ops & 1u) || ((uintptr_t)run_wi & 3u) || ((uintptr_t)run_off & 7u) ||
                     ((uintptr_t)run_len & 7u)))
     return fail(h, AIWC_EINVAL, "device run tables / opcodes are misaligned", false);
+  if (defers(h, on_device) && h->pend_wi.empty()) return record(h, 2, run_wi, run_off, run_len, ops, n_runs, n_ops);
+  if ((s = flush_deferred(h)) != AIWC_OK) return s;
+  if ((s = flush_pending(h)) != AIWC_OK) return s;
   if (routing(h)) return routed(h, [&] { return route_runs(h, run_wi, run_off, run_len, n_runs, ops, n_ops, on_device); });
   if (on_device)
     return runs_device(h, run_wi, (const u64*)run_off, (const u64*)run_len, n_runs, ops, n_ops, n_ops);
@@ -1094,6 +1162,36 @@ BatchGraph& batch_graph(int device) {
   return graphs[device & 63];
 }
 
+// Streams on which aiwc_compute_batch ingests the handles' deferred pushes in
+// parallel (one set per device, created on first use).
+struct PushForks {
+  std::mutex mu;
+  std::vector<cudaStream_t> s;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
+  aiwc_status init() {
+    if (fork) return AIWC_OK;
+    constexpr int kStreams = 16;
+    cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    for (int i = 0; i < kStreams && e == cudaSuccess; ++i) {
+      cudaStream_t st;
+      cudaEvent_t j;
+      e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j, cudaEventDisableTiming);
+      if (e == cudaSuccess) {
+        s.push_back(st);
+        join.push_back(j);
+      }
+    }
+    if (e != cudaSuccess) return cuda_fail(nullptr, "push streams", e);
+    return AIWC_OK;
+  }
+};
+PushForks& push_forks(int device) {
+  static PushForks forks[64];
+  return forks[device & 63];
+}
+
 }  // namespace
 
 namespace {
@@ -1121,8 +1219,9 @@ u32 active_passes(u64 kor, u64 kand, u64 mask) {
 
 // Host part of a compute: pending runs, and every buffer the stages need.
 aiwc_status prepare(aiwc_handle* h) {
-  aiwc_status s = flush_pending(h);
+  aiwc_status s = flush_deferred(h);
   if (s != AIWC_OK) return s;
+  if ((s = flush_pending(h)) != AIWC_OK) return s;
   const u64 n_mem = h->n_mem, n_br = h->n_br, n_runs = h->n_runs;
   ENSURE(h->over_a, over_bound(h, n_mem, n_br, n_runs) * 8, true);
   h->c_over_cap = h->over_a.cap / 8;
@@ -1472,6 +1571,8 @@ aiwc_status finish(aiwc_handle* h, aiwc_metrics* out, uint64_t* user_hist) {
 // Recovers a broken handle: drops the invocation.
 aiwc_status recover(aiwc_handle* h) {
   reset_host(h);
+  h->deferred.clear();
+  h->flushing = false;
   h->replaying = false;
   h->part_err = 0;
   for (auto& pb : h->parts) pb.clear();
@@ -1650,10 +1751,43 @@ aiwc_status aiwc_compute_batch(aiwc_handle* const* hs, size_t n, aiwc_metrics* o
   std::vector<uint64_t*> hists(n);
   aiwc_status worst = AIWC_OK;
   std::vector<char> live(n, 1);
+  // deferred device pushes: every handle's on one of the push streams, so
+  // that small invocations ingest side by side; the user stream waits for all
+  std::vector<aiwc_status> pushed(n, AIWC_OK);
+  bool any_deferred = false;
+  for (size_t i = 0; i < n; ++i) any_deferred |= !hs[i]->broken && !hs[i]->deferred.empty();
+  if (any_deferred) {
+    PushForks& pf = push_forks(hs[0]->cfg.device);
+    std::lock_guard<std::mutex> lk(pf.mu);
+    aiwc_status e = pf.init();
+    if (e != AIWC_OK) return e;
+    if (cudaEventRecord(pf.fork, user) != cudaSuccess) return cuda_fail(nullptr, "push fork", cudaGetLastError());
+    const size_t S = pf.s.size();
+    std::vector<char> used(S, 0);
+    size_t k = 0;
+    for (size_t i = 0; i < n; ++i) {
+      aiwc_handle* h = hs[i];
+      if (h->broken || h->deferred.empty()) continue;
+      const size_t j = k++ % S;
+      if (!used[j]) {
+        if (cudaStreamWaitEvent(pf.s[j], pf.fork, 0) != cudaSuccess)
+          return cuda_fail(nullptr, "push fork", cudaGetLastError());
+        used[j] = 1;
+      }
+      cudaStream_t own = h->stream;
+      h->stream = pf.s[j];
+      pushed[i] = flush_deferred(h);
+      h->stream = own;
+    }
+    for (size_t j = 0; j < S; ++j)
+      if (used[j] && (cudaEventRecord(pf.join[j], pf.s[j]) != cudaSuccess ||
+                      cudaStreamWaitEvent(user, pf.join[j], 0) != cudaSuccess))
+        return cuda_fail(nullptr, "push join", cudaGetLastError());
+  }
   for (size_t i = 0; i < n; ++i) {
     hists[i] = outs[i].opcode_hist;
     aiwc_handle* h = hs[i];
-    aiwc_status s = h->broken ? recover(h) : prepare(h);
+    aiwc_status s = pushed[i] != AIWC_OK ? pushed[i] : (h->broken ? recover(h) : prepare(h));
     if (s != AIWC_OK) {
       live[i] = 0;
       memset(&outs[i], 0, sizeof(aiwc_metrics));
@@ -1920,7 +2054,7 @@ aiwc_status aiwc_shard_merge(aiwc_handle* h, const void* const* blobs, const siz
   if (h->broken) return recover(h);
   if (!h->parts.empty())
     return fail(h, AIWC_EINVAL, "aiwc_shard_merge: a partitioned handle cannot merge shards", false);
-  if (h->n_mem || h->n_br || h->n_runs || !h->pend_wi.empty())
+  if (h->n_mem || h->n_br || h->n_runs || !h->pend_wi.empty() || !h->deferred.empty())
     return fail(h, AIWC_ESTATE, "aiwc_shard_merge: the handle holds pushed events of another invocation", false);
   // check every blob before anything is merged
   std::vector<ShardHeader> hds(n);
@@ -1990,7 +2124,8 @@ bool aiwc::handle_config_matches(const aiwc_handle* h, const aiwc_config* c) {
   return a.history_len == c->history_len && a.cover_num == c->cover_num && a.cover_den == c->cover_den &&
          a.n_opcodes == c->n_opcodes && a.space_mask == (c->space_mask & 0xFu) && a.precision == c->precision &&
          a.plan == c->plan && a.max_work_items == c->max_work_items && a.table_slots == c->table_slots &&
-         a.byte_addresses == c->byte_addresses && a.history_scope == c->history_scope;
+         a.byte_addresses == c->byte_addresses && a.history_scope == c->history_scope &&
+         a.defer_pushes == c->defer_pushes;
 }
 
 void aiwc::handle_set_budget(aiwc_handle* h, uint64_t bytes) { h->cfg.hbm_budget = bytes; }

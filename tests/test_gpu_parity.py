@@ -395,6 +395,44 @@ def test_batch_of_64_with_automatic_plans(P):
             c.close()
 
 
+def test_deferred_pushes_give_the_same_results(P):
+    """defer_pushes: device pushes recorded and ingested at compute time (in a
+    batch: on parallel streams) give exactly the immediate results, also when
+    host pushes of the same streams come between them (order is kept)."""
+    from paper_1805_04207_gb300.api import compute_batch, push_trace
+    traces = synth.batched(12, seed=5, lo_log2=10, hi_log2=17, f_lo_log2=6, f_hi_log2=14)
+    expect = [oracle.compute(t) for t in traces]
+    dev = [t.to("cuda") for t in traces]
+    for defer in (1, 0, 1):
+        chars = [P.Characterizer(n_opcodes=t.n_opcodes, max_work_items=1 << 20, defer_pushes=defer) for t in traces]
+        try:
+            for c, t in zip(chars, dev):
+                push_trace(c, t)
+            for g, o in zip(compute_batch(chars), expect):
+                assert_parity(g, o)
+        finally:
+            for c in chars:
+                c.close()
+    # one handle, device and host pushes of each stream interleaved
+    tr = synth.large(seed=12, n_mem=50_001, n_br=40_003, n_wi=40, per_wi=333, zipf_distinct=1 << 12)
+    o = oracle.compute(tr)
+    d = tr.to("cuda")
+    with P.Characterizer(n_opcodes=tr.n_opcodes, defer_pushes=1) as c:
+        for k, (lo, hi) in enumerate([(0, 1000), (1000, 20000), (20000, tr.n_br)]):
+            c.push_branch(d.br[lo:hi].contiguous() if k != 1 else tr.br[lo:hi].contiguous())
+        c.push_mem(d.mem[:30000].contiguous())
+        c.push_mem(tr.mem[30000:].contiguous())
+        R = tr.run_wi.shape[0]
+        c.push_instr_runs(d.run_wi[:R // 2].to(torch.int32).contiguous(), d.run_off[:R // 2].contiguous(),
+                          d.run_len[:R // 2].contiguous(), d.ops)
+        c.push_instr_runs(tr.run_wi[R // 2:].to(torch.int32).contiguous(), tr.run_off[R // 2:].contiguous(),
+                          tr.run_len[R // 2:].contiguous(), tr.ops)
+        assert_parity(c.compute(), o)
+        # and all device pushes, deferred to the compute
+        push_trace(c, d)
+        assert_parity(c.compute(), o)
+
+
 @pytest.mark.parametrize("n_mem", [1 << 20, (1 << 21) + 4321])
 def test_precision_fp32_compensated_within_bound(P, n_mem):
     """The FP32-compensated finalisation (c log2 c = c e + c log2 f; the first

@@ -38,7 +38,7 @@ WORKLOAD = ("large invocation: 2^28 memory events (stencil 256^3 + tiled SGEMM 2
 # credited with one read and one write of each 8-byte key it orders.
 ALG_BYTES = {"mem_event": 16, "branch_event": 8, "opcode": 2, "distinct_key": 16, "pattern": 8}
 KERNEL_FILES = {"mem_ingest": "mem.cu", "branch_ingest": "branch.cu", "instr_runs": "instr.cu", "mem_sort": "sort.cu",
-                "mem_scatter": "mem_hash.cu", "mem_levels": "mem_hash.cu", "branch_sort": "sort.cu", "windows": "branch.cu", "pattern_sort": "sort.cu",
+                "mem_scatter": "mem_hash.cu", "mem_levels": "mem_hash.cu", "branch_sort": "branch.cu", "windows": "branch.cu", "pattern_sort": "sort.cu",
                 "pattern_runs": "branch.cu", "run_sort": "sort.cu", "run_combine": "instr.cu",
                 "finalize": "finalize.cu", "mem_expand": "mem.cu"}
 

@@ -606,7 +606,9 @@ def main():
                 ALG_BYTES["distinct_key"] * D + ALG_BYTES["pattern"] * Bp)
     step_ach = step_alg / (ms_max / args.steps / 1e3) / 1e9
     roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-            "frac": round(achieved / hbm, 4), "traffic": traffic_for(dom), "peak_kind": peak_kind,
+            "frac": round(achieved / hbm, 4),
+            # the committed counters describe the event ingest, not the byte ingest
+            "traffic": None if byte_mode else traffic_for(dom), "peak_kind": peak_kind,
             "alg_bytes_per_launch": alg.get(dom, 0), "ms_per_launch": round(dom_ms, 4)}
 
     # end to end through the public API from pinned host buffers

@@ -243,6 +243,141 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(SortDesc d, int pass) 
   }
 }
 
+// A sort of a few tiles (at most kFewTiles): two launches per pass instead of
+// six. The pass reads the buffer its parity gives -- the live buffer when the
+// sort starts, flipped by every pass that runs (launched and with a varying
+// window) -- so no pass writes `cur`; one launch at the end flips it by the
+// parity of the passes that ran. The scatter computes each digit's global
+// offset for its tile from all tiles' counts itself (256 x ntiles reads).
+constexpr u32 kFewTiles = 64;
+
+__device__ __forceinline__ bool few_pass(const SortDesc& d, int pass, u32 host_passes, int* shift, int* parity) {
+  if (!gate_open(d.gate, d.gate_want)) return false;
+  const u64 varying = ((*d.key_or) ^ (*d.key_and)) & eff_mask(d);
+  int before = 0;
+  for (int q = 0; q < pass; ++q) {
+    const int sq = d.lo_bit + 8 * q;
+    if (sq < 64 && ((host_passes >> q) & 1u) && ((varying >> sq) & 0xFFull)) ++before;
+  }
+  *shift = d.lo_bit + 8 * pass;
+  *parity = before & 1;
+  return *shift < 64 && ((varying >> *shift) & 0xFFull) != 0;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_hist_few(SortDesc d, int pass, u32 host_passes) {
+  int shift, parity;
+  if (!few_pass(d, pass, host_passes, &shift, &parity)) return;
+  const u32 nt = live_tiles(d);
+  if (blockIdx.x >= nt) return;
+  __shared__ u32 h[kWarps][256];
+  for (int i = threadIdx.x; i < kWarps * 256; i += kSortThreads) (&h[0][0])[i] = 0;
+  __syncthreads();
+  const u64 n = umin64(*d.n, d.n_cap);
+  const u64* src = (*d.cur ^ (u32)parity) ? d.b : d.a;
+  const u64 base = (u64)blockIdx.x * kSortTile;
+  const int w = threadIdx.x >> 5;
+  const u64 m = eff_mask(d);
+#pragma unroll 4
+  for (int k = 0; k < kSortItems; ++k) {
+    const u64 i = base + (u64)k * kSortThreads + threadIdx.x;
+    if (i < n) atomicAdd(&h[w][((src[i] & m) >> shift) & 0xFF], 1u);
+  }
+  __syncthreads();
+  u32 s = 0;
+#pragma unroll
+  for (int q = 0; q < kWarps; ++q) s += h[q][threadIdx.x];
+  d.counts[(u64)threadIdx.x * nt + blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_scatter_few(SortDesc d, int pass, u32 host_passes) {
+  int shift, parity;
+  if (!few_pass(d, pass, host_passes, &shift, &parity)) return;
+  const u32 nt = live_tiles(d);
+  if (blockIdx.x >= nt) return;
+  __shared__ u32 wcnt[kWarps][256];
+  __shared__ u32 dofs[256];
+  __shared__ u32 gofs[256];
+  __shared__ u32 wt[33];
+  __shared__ u64 stage[kSortTile];
+  for (int i = threadIdx.x; i < kWarps * 256; i += kSortThreads) (&wcnt[0][0])[i] = 0;
+  {
+    // this tile's global offset for digit dg: the keys of smaller digits, then
+    // those of digit dg in earlier tiles
+    const int dg = threadIdx.x;
+    u32 before = 0, total = 0;
+    for (u32 t = 0; t < nt; ++t) {
+      const u32 c = d.counts[(u64)dg * nt + t];
+      if (t < blockIdx.x) before += c;
+      total += c;
+    }
+    u32 all;
+    gofs[dg] = block_excl_scan<u32>(total, &all, wt) + before;
+  }
+  __syncthreads();
+  const u64 n = umin64(*d.n, d.n_cap);
+  const u32 cur = *d.cur ^ (u32)parity;
+  const u64* src = cur ? d.b : d.a;
+  u64* dst = cur ? d.a : d.b;
+  const u64 base = (u64)blockIdx.x * kSortTile;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const u32 lt_mask = (1u << lane) - 1u;
+  const u64 m = eff_mask(d);
+  u64 key[kSortItems];
+  u32 rank[kSortItems];
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
+    const u64 i = base + (u64)w * (32 * kSortItems) + (u64)k * 32 + lane;
+    const bool valid = i < n;
+    key[k] = valid ? src[i] : 0ull;
+    const u32 dig = valid ? (u32)(((key[k] & m) >> shift) & 0xFF) : 256u + lane;
+    const u32 peers = __match_any_sync(0xffffffffu, dig);
+    const u32 before = valid ? wcnt[w][dig] : 0u;
+    rank[k] = before + __popc(peers & lt_mask);
+    __syncwarp();
+    if (valid && lane == 31 - __clz(peers)) wcnt[w][dig] = before + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  {
+    const int dg = threadIdx.x;
+    u32 tot = 0;
+#pragma unroll
+    for (int q = 0; q < kWarps; ++q) {
+      const u32 c = wcnt[q][dg];
+      wcnt[q][dg] = tot;
+      tot += c;
+    }
+    u32 all;
+    dofs[dg] = block_excl_scan<u32>(tot, &all, wt);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {
+    const u64 i = base + (u64)w * (32 * kSortItems) + (u64)k * 32 + lane;
+    if (i < n) {
+      const u32 dig = (u32)(((key[k] & m) >> shift) & 0xFF);
+      stage[dofs[dig] + wcnt[w][dig] + rank[k]] = key[k];
+    }
+  }
+  __syncthreads();
+  const u64 tile_n = n > base ? (n - base < (u64)kSortTile ? n - base : (u64)kSortTile) : 0ull;
+  for (u32 j = threadIdx.x; j < tile_n; j += kSortThreads) {
+    const u64 kv = stage[j];
+    const u32 dig = (u32)(((kv & m) >> shift) & 0xFF);
+    dst[(u64)gofs[dig] + (j - dofs[dig])] = kv;
+  }
+}
+
+// After the passes: the live buffer is the other one when an odd number ran.
+__global__ void k_flip_few(SortDesc d, u32 host_passes) {
+  if (!gate_open(d.gate, d.gate_want)) return;
+  const u64 varying = ((*d.key_or) ^ (*d.key_and)) & eff_mask(d);
+  int ran = 0;
+  for (int q = 0; 8 * q + d.lo_bit < 64; ++q)
+    if (((host_passes >> q) & 1u) && ((varying >> (d.lo_bit + 8 * q)) & 0xFFull)) ++ran;
+  if (ran & 1) *d.cur ^= 1u;
+}
+
 // A sort that fits one tile (at most kSortTile keys): every pass in one block,
 // ranking as k_scatter does (stable), the keys held in shared memory between
 // passes and written back to the live buffer at the end (so `cur` does not
@@ -334,10 +469,25 @@ u32 sort_tiles(u64 n) { return (u32)((n + kSortTile - 1) / kSortTile); }
 
 void sort_keys(const SortDesc& d, cudaStream_t s, u32 host_passes) {
   if (d.ntiles == 0) return;
+  const int npass = (64 - d.lo_bit + 7) / 8;
   if (d.ntiles == 1) {  // one tile: every pass in one launch
-    if (host_passes & ((1u << ((64 - d.lo_bit + 7) / 8)) - 1u)) {
+    if (host_passes & ((1u << npass) - 1u)) {
       k_sort_tile<<<1, kSortThreads, 0, s>>>(d, host_passes);
       count_launches(1);
+    }
+    return;
+  }
+  if (d.ntiles <= kFewTiles) {  // a few tiles: two launches per pass, one flip
+    int launched = 0;
+    for (int p = 0; p < npass; ++p) {
+      if (!((host_passes >> p) & 1u)) continue;
+      ++launched;
+      k_hist_few<<<d.ntiles, kSortThreads, 0, s>>>(d, p, host_passes);
+      k_scatter_few<<<d.ntiles, kSortThreads, 0, s>>>(d, p, host_passes);
+    }
+    if (launched) {
+      k_flip_few<<<1, 1, 0, s>>>(d, host_passes);
+      count_launches(2ull * launched + 1);
     }
     return;
   }

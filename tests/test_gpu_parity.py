@@ -395,6 +395,22 @@ def test_batch_of_64_with_automatic_plans(P):
             c.close()
 
 
+@pytest.mark.parametrize("n", [1, 2047, 2048, 2049, 64 * 2048, 64 * 2048 + 1, 65 * 2048 + 7])
+def test_sort_sizes_at_tile_boundaries(P, n):
+    """The radix sort's three forms -- one tile in one launch, up to 64 tiles
+    with two launches per pass, more tiles with six -- at and around their
+    limits: the sort plan orders the memory words, the radix path the branch
+    words (events arrive out of work-item order) and the run table (runs out of
+    work-item order), all compared with the oracle."""
+    rng = np.random.default_rng(n)
+    tr = random_trace(n, n_mem=n, n_br=n, n_wi=int(rng.integers(2, 200)), n_runs=max(1, min(n, 3000)),
+                      n_ops=max(12, min(4 * n, 20000)), addr_pool=int(rng.integers(1, 5000)), n_sites=7,
+                      addr_span_bits=30)
+    o = oracle.compute(tr, history_len=5)
+    assert_parity(run_gpu(P, tr, plan=1, history_len=5), o)
+    assert_parity(run_gpu(P, tr, plan=0, history_len=5), o)
+
+
 def test_deferred_pushes_give_the_same_results(P):
     """defer_pushes: device pushes recorded and ingested at compute time (in a
     batch: on parallel streams) give exactly the immediate results, also when

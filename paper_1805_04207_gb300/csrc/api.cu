@@ -1519,9 +1519,23 @@ aiwc_status enqueue_finalize(aiwc_handle* h, cudaStream_t st) {
     StageScope fin_scope(h, kStFinalize, st);
     launch_opcode_dist((const u64*)h->d_hist, h->cfg.n_opcodes, over, over_cap, h->arena, st);
     launch_wi_count(h->wi_bitmap, h->arena, st);
+    // Outside a graph capture the overflow list is complete here: one
+    // synchronisation sizes its sort by the entries it holds (a few thousand
+    // where the bound is millions) and runs only the passes whose digits vary.
+    u64 n_sort = over_cap;
+    u32 passes = 0xFFu;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone) {
+      CK(cudaMemcpyAsync(h->h_state, dst, sizeof(DevState), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      n_sort = std::min<u64>(h->h_state->n_over, over_cap);
+      passes = active_passes(h->h_state->over_or, h->h_state->over_and, ~0ull);
+    } else {
+      cudaGetLastError();
+    }
     SortDesc d = sort_desc(h, h->over_a, h->over_b, kSortOver, &dst->n_over, &dst->over_or, &dst->over_and, ~0ull,
-                           over_cap);
-    sort_keys(d, st);
+                           n_sort);
+    sort_keys(d, st, passes);
     FinalizeArgs fa;
     fa.over_a = d.a;
     fa.over_b = d.b;

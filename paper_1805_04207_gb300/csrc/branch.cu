@@ -41,7 +41,7 @@ __device__ __forceinline__ void emit_site_predicted(u64 m, u32 h, u64* over, u64
   if (m > h) emit_site_pred_count(m - h, over, cap, ar);
 }
 
-__global__ void __launch_bounds__(kBrThreads) k_branch_ingest(BranchIngestArgs a) {
+__global__ void __launch_bounds__(kBrThreads, 4) k_branch_ingest(BranchIngestArgs a) {
   __shared__ u64 red64[32];
   __shared__ u32 red32[32];
   DevState* st = &a.arena->st;

@@ -21,7 +21,7 @@ namespace {
 
 constexpr int kInThreads = 256;
 constexpr int kInWarps = kInThreads / 32;
-constexpr int kOpsPerLane = 16;  // opcodes each lane takes per step (two 16-byte loads)
+constexpr int kOpsPerLane = 32;  // opcodes each lane takes per step (16-byte loads of 8; at most 32)
 
 // Value histograms (ITB / IPT): privatised in shared memory below kValSmem,
 // global dense below kValDense, overflow list above.
@@ -112,9 +112,14 @@ __global__ void __launch_bounds__(kInThreads) k_instr_runs(RunBatchArgs a) {
       u32 pk[kOpsPerLane / 2];  // two opcodes per word, low half first; padding = barrier marker
       if (nv == kOpsPerLane && aligned) {
         const uint4* q = reinterpret_cast<const uint4*>(p + my0);
-        const uint4 v0 = __ldcs(q), v1 = __ldcs(q + 1);
-        pk[0] = v0.x; pk[1] = v0.y; pk[2] = v0.z; pk[3] = v0.w;
-        pk[4] = v1.x; pk[5] = v1.y; pk[6] = v1.z; pk[7] = v1.w;
+#pragma unroll
+        for (int v = 0; v < kOpsPerLane / 8; ++v) {
+          const uint4 x = __ldcs(q + v);
+          pk[4 * v] = x.x;
+          pk[4 * v + 1] = x.y;
+          pk[4 * v + 2] = x.z;
+          pk[4 * v + 3] = x.w;
+        }
       } else {
 #pragma unroll
         for (int k = 0; k < kOpsPerLane / 2; ++k) {

@@ -1768,7 +1768,6 @@ aiwc_status aiwc_compute_batch(aiwc_handle* const* hs, size_t n, aiwc_metrics* o
   // deferred device pushes: every handle's on one of the push streams, so
   // that small invocations ingest side by side; the user stream waits for all
   std::vector<aiwc_status> pushed(n, AIWC_OK);
-  std::vector<char> prepared(n, 0);
   bool any_deferred = false;
   for (size_t i = 0; i < n; ++i) any_deferred |= !hs[i]->broken && !hs[i]->deferred.empty();
   if (any_deferred) {
@@ -1779,7 +1778,6 @@ aiwc_status aiwc_compute_batch(aiwc_handle* const* hs, size_t n, aiwc_metrics* o
     if (cudaEventRecord(pf.fork, user) != cudaSuccess) return cuda_fail(nullptr, "push fork", cudaGetLastError());
     const size_t S = pf.s.size();
     std::vector<char> used(S, 0);
-    std::vector<std::vector<size_t>> on_stream(S);
     size_t k = 0;
     for (size_t i = 0; i < n; ++i) {
       aiwc_handle* h = hs[i];
@@ -1790,29 +1788,11 @@ aiwc_status aiwc_compute_batch(aiwc_handle* const* hs, size_t n, aiwc_metrics* o
           return cuda_fail(nullptr, "push fork", cudaGetLastError());
         used[j] = 1;
       }
-      on_stream[j].push_back(i);
+      cudaStream_t own = h->stream;
+      h->stream = pf.s[j];
+      pushed[i] = flush_deferred(h);
+      h->stream = own;
     }
-    // the launches are host-bound (a few per handle): host threads issue the
-    // streams' handles side by side, each handle's ingest then its preparation
-    const int device = hs[0]->cfg.device;
-    auto work = [&](size_t t, size_t T) {
-      DeviceGuard tg(device);
-      for (size_t j = t; j < S; j += T)
-        for (size_t i : on_stream[j]) {
-          aiwc_handle* h = hs[i];
-          cudaStream_t own = h->stream;
-          h->stream = pf.s[j];
-          pushed[i] = flush_deferred(h);
-          if (pushed[i] == AIWC_OK) pushed[i] = prepare(h);
-          prepared[i] = 1;
-          h->stream = own;
-        }
-    };
-    const size_t T = std::min<size_t>(S, std::max(1u, std::min(8u, std::thread::hardware_concurrency())));
-    std::vector<std::thread> pool;
-    for (size_t t = 1; t < T; ++t) pool.emplace_back(work, t, T);
-    work(0, T);
-    for (auto& th : pool) th.join();
     for (size_t j = 0; j < S; ++j)
       if (used[j] && (cudaEventRecord(pf.join[j], pf.s[j]) != cudaSuccess ||
                       cudaStreamWaitEvent(user, pf.join[j], 0) != cudaSuccess))
@@ -1821,7 +1801,7 @@ aiwc_status aiwc_compute_batch(aiwc_handle* const* hs, size_t n, aiwc_metrics* o
   for (size_t i = 0; i < n; ++i) {
     hists[i] = outs[i].opcode_hist;
     aiwc_handle* h = hs[i];
-    aiwc_status s = prepared[i] || pushed[i] != AIWC_OK ? pushed[i] : (h->broken ? recover(h) : prepare(h));
+    aiwc_status s = pushed[i] != AIWC_OK ? pushed[i] : (h->broken ? recover(h) : prepare(h));
     if (s != AIWC_OK) {
       live[i] = 0;
       memset(&outs[i], 0, sizeof(aiwc_metrics));

@@ -71,6 +71,8 @@ struct DevState {
   u64 br_sort_mask;      // bits the branch sort must order (site only when work-items arrive sorted)
   u64 br_site_max;       // longest per-site outcome sequence
   u64 n_sites;           // entries of the site list
+  u64 n_long;            // sites longer than kSiteMaxLen (counted in chunks by the per-site path)
+  u64 long_next;         // entries of the long-site list
   u32 br_unsorted;       // some work-item id arrived below its predecessor
   u32 br_persite;        // the per-site branch path applies (set on the device)
   u32 br_last_wi[2];     // last work-item id of the previous / current push (by push parity)
@@ -343,6 +345,11 @@ struct SiteArgs {
   int grid{};
   const uint8_t* outcomes{};  // per-site path: outcome bytes sorted by site instead of the words
   bool per_wi{};       // one history per (site, work-item): needs the words (outcomes == nullptr)
+  // sites longer than kSiteMaxLen: a dense table of 2^h (taken << 32 | total)
+  // pattern counters per site, and per site (start, length, predicted outcomes)
+  u64* long_tab{};
+  u64* long_list{};
+  u64 long_cap{};      // long sites the table and the list hold
 };
 // Stable counting sort of the branch words by site, for site ids below
 // kCsSites when work-item ids arrived in non-decreasing order (the site alone
@@ -370,10 +377,18 @@ void launch_site_sort_scatter(const SiteSortArgs& a, cudaStream_t s);  // the so
 constexpr u32 kSiteMaxHist = 17;       // dense pattern bins: 2^15 per pass, at most 4 passes
 constexpr u64 kSiteMaxLen = 65535;     // packed 16-bit taken / total counters
 constexpr u64 kSiteListCap = 1ull << 20;  // sites listed for the per-site path
+// Long sites: at most n / (kSiteMaxLen + 1) of n branch events; their tables
+// take 8 << h bytes and their list entries 24 bytes each.
+inline u64 long_sites_cap(size_t tab_bytes, size_t list_bytes, u32 h) {
+  const u64 a = (u64)tab_bytes / (8ull << h), b = (u64)list_bytes / 24;
+  return a < b ? a : b;
+}
 void launch_site_heads(const SiteArgs& a, cudaStream_t s);
 // Device-side choice of the branch path: br_persite = the per-site path applies.
-void launch_persite_decide(Arena* arena, u32 h, u64 sites_cap, int allow, cudaStream_t s);
+void launch_persite_decide(Arena* arena, u32 h, u64 sites_cap, u64 long_cap, int allow, cudaStream_t s);
 void launch_site_patterns(const SiteArgs& a, cudaStream_t s);
+// The long sites of the per-site path: list and clear, count chunks, walk the tables.
+void launch_site_long(const SiteArgs& a, cudaStream_t s);
 void launch_branch_mask(Arena* arena, cudaStream_t s);
 
 // Cross-tile fix-up of run lengths. kind: 0 = memory levels, 1 = sites, 2 = patterns.

@@ -1206,6 +1206,7 @@ struct Plan {
   u32 br_passes = 0xFFu, run_passes = 0xFFu;
   int seg_shift = 0;      // memory, hash plan: low address bits that are zero in every kept event (0..3)
   bool site_sort = false; // branch: stable counting sort by site (in order work-item ids, site ids < kCsSites)
+  bool long_sites = false;  // branch, per-site path: sites longer than kSiteMaxLen may exist
   bool defer_finalize = false;  // partitioned invocation: reduce only, the partitions are merged first
 };
 
@@ -1275,6 +1276,11 @@ SortDesc branch_sort_desc(aiwc_handle* h) {
   return d;
 }
 
+// Long sites the per-site path can take: their tables live in the first
+// pattern buffer, their list in the second (both free on that path once the
+// site sort has run).
+u64 long_cap_of(const aiwc_handle* h) { return long_sites_cap(h->pat_a.cap, h->pat_b.cap, h->cfg.history_len); }
+
 SiteArgs site_args(aiwc_handle* h, const SortDesc& bsort) {
   SiteArgs sa;
   sa.a = bsort.a;
@@ -1288,6 +1294,9 @@ SiteArgs site_args(aiwc_handle* h, const SortDesc& bsort) {
   sa.over_cap = h->c_over_cap;
   sa.arena = h->arena;
   sa.grid = h->sm_count;
+  sa.long_tab = (u64*)h->pat_a.p;
+  sa.long_list = (u64*)h->pat_b.p;
+  sa.long_cap = long_cap_of(h);
   return sa;
 }
 
@@ -1324,7 +1333,8 @@ void enqueue_part1(aiwc_handle* h, cudaStream_t st, const Plan& p) {
   }
   StageScope sc(h, kStWindows, st);
   launch_site_heads(site_args(h, bsort), st);
-  if (p.gated) launch_persite_decide(h->arena, h->cfg.history_len, h->c_sites_cap, h->cfg.plan != 1, st);
+  if (p.gated)
+    launch_persite_decide(h->arena, h->cfg.history_len, h->c_sites_cap, long_cap_of(h), h->cfg.plan != 1, st);
 }
 
 aiwc_status enqueue_finalize(aiwc_handle* h, cudaStream_t st);
@@ -1419,6 +1429,7 @@ void enqueue_branch_path(aiwc_handle* h, cudaStream_t st, const Plan& p) {
       if (p.site_sort && !h->cfg.history_scope) sa.outcomes = (const uint8_t*)h->br_b.p;
       sa.per_wi = h->cfg.history_scope != 0;
       launch_site_patterns(sa, st);
+      if (p.long_sites) launch_site_long(sa, st);
     }
     if (p.gated || !p.per_site) {
       WindowArgs wa;
@@ -1596,6 +1607,25 @@ aiwc_status recover(aiwc_handle* h) {
   return AIWC_ESTATE;
 }
 
+// The stable counting sort by site applies: work-item ids arrived in order
+// and site ids are below kCsSites (h->h_state must be current).
+bool site_sort_ok(const aiwc_handle* h) {
+  const DevState& hs = *h->h_state;
+  return h->n_br >= (1ull << 16) && h->n_br < (1ull << 32) && !hs.br_unsorted && (hs.br_or >> 32) < kCsSites &&
+         h->cfg.plan != 1;
+}
+
+// The per-site branch path applies whatever the sites turn out to be: no
+// more sites than the list holds (n_br of them at most, or kCsSites with the
+// counting sort), and a table for every long site (each has more than
+// kSiteMaxLen of the n_br events).
+bool per_site_certain(const aiwc_handle* h, bool site_sort) {
+  if (h->cfg.history_len > kSiteMaxHist || h->cfg.plan == 1) return false;
+  if (h->n_br <= kSiteMaxLen) return true;
+  const bool sites_fit = site_sort || h->n_br <= h->c_sites_cap;
+  return sites_fit && h->n_br < (1ull << 32) && long_cap_of(h) >= h->n_br / (kSiteMaxLen + 1);
+}
+
 // Host decisions from the ingest-time counters (h->h_state must be current).
 void plan_from_ingest(aiwc_handle* h, Plan* p) {
   const DevState& hs = *h->h_state;
@@ -1610,8 +1640,7 @@ void plan_from_ingest(aiwc_handle* h, Plan* p) {
   p->seg_shift = addr_or ? std::min(__builtin_ctzll(addr_or), 3) : 3;
   // the counting sort's per-tile counts (n_br / 4 words or less) live in the
   // pattern buffers, which hold 2 n_br words each
-  p->site_sort = !p->gated && h->n_br >= (1ull << 16) && h->n_br < (1ull << 32) && !hs.br_unsorted &&
-                 (hs.br_or >> 32) < kCsSites && h->cfg.plan != 1;
+  p->site_sort = !p->gated && site_sort_ok(h);
 }
 
 // Everything a compute enqueues for what is pushed now: the plan from the
@@ -1644,8 +1673,11 @@ aiwc_status reduce_current(aiwc_handle* h, bool defer_finalize) {
     CK(cudaMemcpyAsync(h->h_state, &h->arena->st, sizeof(DevState), cudaMemcpyDeviceToHost, sb));
     CK(cudaStreamSynchronize(sb));
     const DevState& hs = *h->h_state;
-    p.per_site = h->cfg.history_len <= kSiteMaxHist && hs.br_site_max <= kSiteMaxLen &&
-                 hs.n_sites <= h->c_sites_cap && h->cfg.plan != 1;
+    const bool longs_fit = hs.br_site_max <= kSiteMaxLen ||
+                           (hs.n_long <= long_cap_of(h) && hs.br_site_max < (1ull << 32));
+    p.per_site = h->cfg.history_len <= kSiteMaxHist && longs_fit && hs.n_sites <= h->c_sites_cap &&
+                 h->cfg.plan != 1;
+    p.long_sites = hs.n_long != 0;
   }
   if (!split) return enqueue_part2(h, st, p);
   enqueue_branch_path(h, sb, p);
@@ -1824,15 +1856,19 @@ aiwc_status aiwc_compute_batch(aiwc_handle* const* hs, size_t n, aiwc_metrics* o
     plans[i].gated = true;
     plan_from_ingest(hs[i], &plans[i]);
     const aiwc_handle* h = hs[i];
-    // the branch-path choice needs the longest site, known only on the device;
-    // up to kSiteMaxLen events no site can be longer, so the per-site path is
-    // certain and the graph holds it alone
-    if (h->n_br <= kSiteMaxLen && h->cfg.history_len <= kSiteMaxHist && h->cfg.plan != 1) {
+    // the branch-path choice needs the number of sites and of long sites,
+    // known only on the device; where the per-site path is certain anyway the
+    // graph holds it alone (gated, both paths are launched and a device flag
+    // picks one)
+    const bool cs = site_sort_ok(h);
+    plans[i].long_sites = h->n_br > kSiteMaxLen;
+    if (per_site_certain(h, cs)) {
       plans[i].gated = false;
       plans[i].per_site = true;
+      plans[i].site_sort = cs;
     }
     sig.insert(sig.end(), {(u64)(uintptr_t)h, h->n_mem, h->n_br, h->n_runs, h->epoch, (u64)plans[i].hash_ok,
-                           (u64)plans[i].gated,
+                           (u64)plans[i].gated | ((u64)plans[i].site_sort << 1) | ((u64)plans[i].long_sites << 2),
                            plans[i].br_passes, plans[i].run_passes, h->sbt_cap, (u64)plans[i].seg_shift,
                            active_passes(h->h_state->mem_or, h->h_state->mem_and, ~0ull)});
   }

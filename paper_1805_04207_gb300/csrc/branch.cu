@@ -117,9 +117,12 @@ __global__ void k_branch_mask(Arena* arena) {
   st->br_sort_mask = st->br_unsorted ? ~1ull : 0xFFFFFFFF00000000ull;
 }
 
-__global__ void k_persite_decide(Arena* arena, u32 h, u64 sites_cap, int allow) {
+// Sites longer than kSiteMaxLen are counted in chunks when the long-site
+// tables hold them all (and their 32-bit counters cannot overflow).
+__global__ void k_persite_decide(Arena* arena, u32 h, u64 sites_cap, u64 long_cap, int allow) {
   DevState* st = &arena->st;
-  st->br_persite = (allow && h <= kSiteMaxHist && st->br_site_max <= kSiteMaxLen && st->n_sites <= sites_cap) ? 1u : 0u;
+  const bool longs_fit = st->br_site_max <= kSiteMaxLen || (st->n_long <= long_cap && st->br_site_max < (1ull << 32));
+  st->br_persite = (allow && h <= kSiteMaxHist && longs_fit && st->n_sites <= sites_cap) ? 1u : 0u;
 }
 
 // Lists each site's segment of the sorted branch words: (start, length).
@@ -138,6 +141,7 @@ __global__ void __launch_bounds__(256) k_site_heads(SiteArgs a) {
     }
     const u64 len = lo - i;
     mx = len > mx ? len : mx;
+    if (len > kSiteMaxLen) atomicAdd(&st->n_long, 1ull);
     const u64 k = atomicAdd(&st->n_sites, 1ull);
     if (k < a.sites_cap) {
       a.sites[2 * k] = i;
@@ -270,11 +274,12 @@ __global__ void __launch_bounds__(kCsScanThreads) k_cs_scan_sites(SiteSortArgs a
   __syncthreads();
   u64 start = wt64[w] + inc - mine;
   u64 k = wt32[w] + inz - nz;
-  u64 mx = 0;
+  u64 mx = 0, nl = 0;
   u32 sv[kCsPer];
 #pragma unroll
   for (int q = 0; q < kCsPer; ++q) {
     sv[q] = (u32)start;
+    nl += tot[q] > kSiteMaxLen;
     if (tot[q]) {
       if (k < a.sites_cap) {
         a.sites[2 * k] = start;
@@ -287,9 +292,11 @@ __global__ void __launch_bounds__(kCsScanThreads) k_cs_scan_sites(SiteSortArgs a
   }
   reinterpret_cast<uint4*>(starts)[threadIdx.x] = make_uint4(sv[0], sv[1], sv[2], sv[3]);
   mx = block_reduce(mx, OpMax(), 0ull, red64);
+  nl = block_reduce(nl, OpAdd(), 0ull, red64);
   if (threadIdx.x == kCsScanThreads - 1) st->n_sites = k;  // the last thread's count is the total
   if (threadIdx.x == 0) {
     st->br_site_max = mx;
+    st->n_long = nl;
     *a.sort_cur = 1u;
   }
 }
@@ -379,111 +386,149 @@ constexpr int kSpThreads = 1024;
 constexpr int kPatSmem = 1024;  // pattern counts below this are counted in shared memory first
 constexpr int kSpBinsLog = 15;
 constexpr int kSpBitWords = (int)((kSiteMaxLen + 32) / 32) + 2;
+constexpr u32 kLongChunk = 16384;  // predicted outcomes of a long site per block work item
 
-// One block per site: its outcomes become a bit string in shared memory; for
-// every outcome with h predecessors in its history, the packed counter of its
-// history gets
-// +1 total (low 16 bits) and +outcome taken (high 16 bits). Histories are
-// binned 2^15 at a time (more passes for h > 15). The first increment of a
-// bin lists it, so a pass visits and clears only the bins it used. M and N'
-// follow from the bins. Any fixed bijection of the h-bit window names the
-// pattern equally well; here bit k of the pattern is the outcome k+1 places
-// after the oldest. With one history per (site, work-item) a second bit string
-// marks where the work-item changes inside the site (the words are sorted by
-// work-item within a site); a window counts only when no change falls inside
-// it, and the site's predicted outcomes are the windows counted.
-__global__ void __launch_bounds__(kSpThreads) k_site_patterns(SiteArgs a) {
-  if (!gate_open(a.gate, a.gate_want)) return;
-  extern __shared__ u32 spm[];
-  u32* bits = spm;
-  u32* brk = spm + kSpBitWords;
-  u32* cnt = spm + 2 * kSpBitWords;
-  uint16_t* used = reinterpret_cast<uint16_t*>(cnt + (1 << kSpBinsLog));
-  __shared__ u32 n_used;
-  __shared__ u64 red64[32];
-  __shared__ u32 pcoc[kPatSmem];  // pattern count-of-counts for small counts
-  DevState* st = &a.arena->st;
-  const u64* w = *a.cur ? a.b : a.a;
-  for (int i = threadIdx.x; i < kPatSmem; i += kSpThreads) pcoc[i] = 0u;
+// Shared memory of the window-counting kernels: the outcome bit string, the
+// work-item change bit string, 2^kSpBinsLog packed counters (total in the low
+// 16 bits, taken in the high 16) and the list of the bins a pass used.
+struct WinSmem {
+  u32* bits;
+  u32* brk;
+  u32* cnt;
+  uint16_t* used;
+  u32* n_used;
+};
+
+__device__ __forceinline__ WinSmem win_smem(u32* spm, u32* n_used) {
+  WinSmem s;
+  s.bits = spm;
+  s.brk = spm + kSpBitWords;
+  s.cnt = spm + 2 * kSpBitWords;
+  s.used = reinterpret_cast<uint16_t*>(s.cnt + (1 << kSpBinsLog));
+  s.n_used = n_used;
+  return s;
+}
+
+// Counts the windows of the outcome positions [b0, e) of one site (positions
+// relative to the site, whose words or outcome bytes start at `start`): each
+// position j in [j0, e), j0 >= b0 + h, is counted under its history, the h
+// outcomes before it. The positions become a bit string in shared memory;
+// the packed counter of j's history gets +1 total and +outcome taken.
+// Histories are binned 2^15 at a time (more passes for h > 15); the first
+// increment of a bin lists it, and after each pass flush(pattern, counter)
+// is called once for every bin the pass used, which is then cleared. Any
+// fixed bijection of the h-bit window names the pattern equally well; here
+// bit k of the pattern is the outcome k+1 places after the oldest. With one
+// history per (site, work-item) a second bit string marks where the
+// work-item changes (the words are sorted by work-item within a site); a
+// window counts only when no change falls inside it, and the return value
+// is this thread's number of such windows. Called by the whole block, which
+// it leaves synchronised.
+template <typename Flush>
+__device__ __forceinline__ u64 count_windows(const SiteArgs& a, const u64* w, u64 start, u64 b0, u64 j0, u64 e,
+                                             const WinSmem& sm, Flush&& flush) {
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = kSpThreads / 32;
   const u32 h = a.h;
   const int pbits = h > (u32)kSpBinsLog ? kSpBinsLog : (int)h;
   const u32 nbins = 1u << pbits;
   const u32 passes = h > (u32)kSpBinsLog ? (1u << (h - kSpBinsLog)) : 1u;
   const u64 hmask = (1ull << h) - 1ull;
-  const u64 n_sites = umin64(st->n_sites, a.sites_cap);
-  for (u32 i = threadIdx.x; i < nbins; i += kSpThreads) cnt[i] = 0u;
+  const u64 len = e - b0;
+  const u32 nwords = (u32)((len + 31) / 32);
+  // eight 32-position groups per warp in flight at a time
+  for (u32 c0 = wp; c0 < nwords + 2; c0 += 8 * nw) {
+    bool t[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const u64 l = (u64)(c0 + q * nw) * 32 + lane;
+      t[q] = l < len && (a.outcomes ? (a.outcomes[start + b0 + l] & 1u) : (w[start + b0 + l] & 1ull));
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const u32 b = __ballot_sync(0xffffffffu, t[q]);
+      if (lane == 0 && c0 + q * nw < nwords + 2) sm.bits[c0 + q * nw] = b;
+    }
+    if (a.per_wi) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const u64 l = (u64)(c0 + q * nw) * 32 + lane;
+        const u64 p = b0 + l;
+        const bool change = l < len && p > 0 && (w[start + p] >> 1) != (w[start + p - 1] >> 1);
+        const u32 b = __ballot_sync(0xffffffffu, change);
+        if (lane == 0 && c0 + q * nw < nwords + 2) sm.brk[c0 + q * nw] = b;
+      }
+    }
+  }
+  __syncthreads();
+  u64 spred = 0;
+  for (u32 q = 0; q < passes; ++q) {
+    for (u64 j = j0 + threadIdx.x; j < e; j += kSpThreads) {
+      const u64 jl = j - b0, pos = jl - h;
+      const u64 two = (u64)sm.bits[pos >> 5] | ((u64)sm.bits[(pos >> 5) + 1] << 32);
+      const u32 win = (u32)((two >> (pos & 31)) & hmask);
+      const u32 outcome = (sm.bits[jl >> 5] >> (jl & 31)) & 1u;
+      if (a.per_wi) {
+        // work-item changes at positions pos + 1 .. jl end the window's history
+        const u64 p1 = pos + 1;
+        const u64 tb = (u64)sm.brk[p1 >> 5] | ((u64)sm.brk[(p1 >> 5) + 1] << 32);
+        if ((tb >> (p1 & 31)) & hmask) continue;
+        if (q == 0) ++spred;
+      }
+      if ((win >> pbits) == q) {
+        const u32 b = win & (nbins - 1);
+        if (atomicAdd(&sm.cnt[b], 1u + (outcome << 16)) == 0u) sm.used[atomicAdd(sm.n_used, 1u)] = (uint16_t)b;
+      }
+    }
+    __syncthreads();
+    const u32 nu = *sm.n_used;
+    for (u32 i = threadIdx.x; i < nu; i += kSpThreads) {
+      const u32 b = sm.used[i];
+      const u32 v = sm.cnt[b];
+      sm.cnt[b] = 0u;
+      flush((q << pbits) | b, v);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *sm.n_used = 0;
+    __syncthreads();
+  }
+  return spred;
+}
+
+// One block per site of at most kSiteMaxLen outcomes (longer ones are
+// counted in chunks, below): every window of the site is counted in shared
+// memory, and M and N' follow from the bins.
+__global__ void __launch_bounds__(kSpThreads) k_site_patterns(SiteArgs a) {
+  if (!gate_open(a.gate, a.gate_want)) return;
+  extern __shared__ u32 spm[];
+  __shared__ u32 n_used;
+  __shared__ u64 red64[32];
+  __shared__ u32 pcoc[kPatSmem];  // pattern count-of-counts for small counts
+  const WinSmem sm = win_smem(spm, &n_used);
+  DevState* st = &a.arena->st;
+  const u64* w = *a.cur ? a.b : a.a;
+  for (int i = threadIdx.x; i < kPatSmem; i += kSpThreads) pcoc[i] = 0u;
+  for (int i = threadIdx.x; i < (1 << kSpBinsLog); i += kSpThreads) sm.cnt[i] = 0u;
   if (threadIdx.x == 0) n_used = 0;
   __syncthreads();
+  const u32 h = a.h;
+  const u64 n_sites = umin64(st->n_sites, a.sites_cap);
   u64 msum = 0, nsum = 0, nsite = 0;
   for (u64 si = blockIdx.x; si < n_sites; si += gridDim.x) {
     const u64 start = a.sites[2 * si], m = a.sites[2 * si + 1];
+    if (m > kSiteMaxLen) continue;
     if (threadIdx.x == 0) {
       ++nsite;
       if (m < (u64)kCocDense) atomicAdd(&a.arena->site_coc[m], 1ull);
       else overflow_append(a.over, a.over_cap, st, kTagSites, m);
       if (!a.per_wi) emit_site_predicted(m, h, a.over, a.over_cap, a.arena);
     }
-    const u32 nwords = (u32)((m + 31) / 32);
-    // eight 32-event groups per warp in flight at a time
-    for (u32 c0 = wp; c0 < nwords + 2; c0 += 8 * nw) {
-      bool t[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const u64 j = (u64)(c0 + q * nw) * 32 + lane;
-        t[q] = j < m && (a.outcomes ? (a.outcomes[start + j] & 1u) : (w[start + j] & 1ull));
-      }
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const u32 b = __ballot_sync(0xffffffffu, t[q]);
-        if (lane == 0 && c0 + q * nw < nwords + 2) bits[c0 + q * nw] = b;
-      }
-      if (a.per_wi) {
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const u64 j = (u64)(c0 + q * nw) * 32 + lane;
-          const bool change = j > 0 && j < m && (w[start + j] >> 1) != (w[start + j - 1] >> 1);
-          const u32 b = __ballot_sync(0xffffffffu, change);
-          if (lane == 0 && c0 + q * nw < nwords + 2) brk[c0 + q * nw] = b;
-        }
-      }
-    }
-    __syncthreads();
-    u64 spred = 0;  // this site's predicted outcomes (one history per (site, work-item))
-    for (u32 q = 0; q < passes; ++q) {
-      for (u64 j = h + threadIdx.x; j < m; j += kSpThreads) {
-        const u64 pos = j - h;
-        const u64 two = (u64)bits[pos >> 5] | ((u64)bits[(pos >> 5) + 1] << 32);
-        const u32 win = (u32)((two >> (pos & 31)) & hmask);
-        const u32 outcome = (bits[j >> 5] >> (j & 31)) & 1u;
-        if (a.per_wi) {
-          // work-item changes at positions pos + 1 .. j end the window's history
-          const u64 p1 = pos + 1;
-          const u64 tb = (u64)brk[p1 >> 5] | ((u64)brk[(p1 >> 5) + 1] << 32);
-          if ((tb >> (p1 & 31)) & hmask) continue;
-          if (q == 0) ++spred;
-        }
-        if ((win >> pbits) == q) {
-          const u32 b = win & (nbins - 1);
-          if (atomicAdd(&cnt[b], 1u + (outcome << 16)) == 0u) used[atomicAdd(&n_used, 1u)] = (uint16_t)b;
-        }
-      }
-      __syncthreads();
-      const u32 nu = n_used;
-      for (u32 i = threadIdx.x; i < nu; i += kSpThreads) {
-        const u32 b = used[i];
-        const u32 v = cnt[b];
-        cnt[b] = 0u;
-        const u32 nn = v & 0xFFFFu, t = v >> 16;
-        msum += t < nn - t ? t : nn - t;
-        nsum += nn;
-        if (nn < (u32)kPatSmem) atomicAdd(&pcoc[nn], 1u);
-        else atomicAdd(&a.arena->pat_coc[nn], 1ull);  // nn <= kSiteMaxLen < kValDense
-      }
-      __syncthreads();
-      if (threadIdx.x == 0) n_used = 0;
-      __syncthreads();
-    }
+    u64 spred = count_windows(a, w, start, 0, h, m, sm, [&](u32, u32 v) {
+      const u32 nn = v & 0xFFFFu, t = v >> 16;
+      msum += t < nn - t ? t : nn - t;
+      nsum += nn;
+      if (nn < (u32)kPatSmem) atomicAdd(&pcoc[nn], 1u);
+      else atomicAdd(&a.arena->pat_coc[nn], 1ull);  // nn <= kSiteMaxLen < kValDense
+    });
     if (a.per_wi) {
       spred = block_reduce(spred, OpAdd(), 0ull, red64);
       if (threadIdx.x == 0) emit_site_pred_count(spred, a.over, a.over_cap, a.arena);
@@ -491,6 +536,121 @@ __global__ void __launch_bounds__(kSpThreads) k_site_patterns(SiteArgs a) {
   }
   __syncthreads();
   for (int i = threadIdx.x; i < kPatSmem; i += kSpThreads)
+    if (pcoc[i]) atomicAdd(&a.arena->pat_coc[i], (u64)pcoc[i]);
+  msum = block_reduce(msum, OpAdd(), 0ull, red64);
+  nsum = block_reduce(nsum, OpAdd(), 0ull, red64);
+  nsite = block_reduce(nsite, OpAdd(), 0ull, red64);
+  if (threadIdx.x == 0) {
+    if (msum) atomicAdd(&st->minsum, msum);
+    if (nsum) atomicAdd(&st->npat, nsum);
+    if (nsite) atomicAdd(&st->branch_sites, nsite);
+  }
+}
+
+// Sites longer than kSiteMaxLen (a chunk's counters still fit 16 bits, a
+// site's may not): k_long_prep lists them and clears their tables,
+// k_site_chunks counts each chunk of kLongChunk predicted outcomes as above
+// and adds its bins to the site's dense table of 2^h (taken << 32 | total)
+// counters, and k_long_walk takes M, N' and the pattern counts from the
+// tables, one block per site. The chunks partition the site's predicted
+// outcomes, so every (site, history) count is the same sum as in one pass.
+__global__ void __launch_bounds__(256) k_long_prep(SiteArgs a) {
+  if (!gate_open(a.gate, a.gate_want)) return;
+  DevState* st = &a.arena->st;
+  const u64 n_sites = umin64(st->n_sites, a.sites_cap);
+  const u64 n_long = umin64(st->n_long, a.long_cap);
+  const u64 tid = (u64)blockIdx.x * blockDim.x + threadIdx.x, nt = (u64)gridDim.x * blockDim.x;
+  for (u64 i = tid; i < n_sites; i += nt) {
+    const u64 m = a.sites[2 * i + 1];
+    if (m > kSiteMaxLen) {
+      const u64 k = atomicAdd(&st->long_next, 1ull);
+      if (k < a.long_cap) {
+        a.long_list[3 * k] = a.sites[2 * i];
+        a.long_list[3 * k + 1] = m;
+        a.long_list[3 * k + 2] = 0ull;
+      }
+    }
+  }
+  ulonglong2* t2 = reinterpret_cast<ulonglong2*>(a.long_tab);
+  const u64 pairs = (n_long << a.h) / 2;  // h >= 1
+  for (u64 i = tid; i < pairs; i += nt) t2[i] = make_ulonglong2(0ull, 0ull);
+}
+
+// Chunk q of long site i goes to block (chunks of the sites before i + q)
+// mod gridDim.x.
+__global__ void __launch_bounds__(kSpThreads) k_site_chunks(SiteArgs a) {
+  if (!gate_open(a.gate, a.gate_want)) return;
+  extern __shared__ u32 spm[];
+  __shared__ u32 n_used;
+  __shared__ u64 red64[32];
+  const WinSmem sm = win_smem(spm, &n_used);
+  DevState* st = &a.arena->st;
+  const u64* w = *a.cur ? a.b : a.a;
+  for (int i = threadIdx.x; i < (1 << kSpBinsLog); i += kSpThreads) sm.cnt[i] = 0u;
+  if (threadIdx.x == 0) n_used = 0;
+  __syncthreads();
+  const u32 h = a.h;
+  const u64 n_long = umin64(umin64(st->n_long, st->long_next), a.long_cap);  // the listed ones
+  const u64 G = gridDim.x;
+  u64 qbase = 0;
+  for (u64 i = 0; i < n_long; ++i) {
+    const u64 start = a.long_list[3 * i], m = a.long_list[3 * i + 1];
+    const u64 nch = (m + kLongChunk - 1) / kLongChunk;
+    u64* tab = a.long_tab + (i << h);
+    u64 spred = 0;
+    for (u64 q = (blockIdx.x + G - qbase % G) % G; q < nch; q += G) {
+      const u64 c0 = q * kLongChunk, e = umin64(m, c0 + kLongChunk);
+      const u64 j0 = c0 > (u64)h ? c0 : (u64)h;
+      spred += count_windows(a, w, start, j0 - h, j0, e, sm, [&](u32 pat, u32 v) {
+        atomicAdd(&tab[pat], ((u64)(v >> 16) << 32) | (u64)(v & 0xFFFFu));
+      });
+    }
+    if (a.per_wi) {
+      spred = block_reduce(spred, OpAdd(), 0ull, red64);
+      if (threadIdx.x == 0 && spred) atomicAdd(&a.long_list[3 * i + 2], spred);
+    }
+    qbase += nch;
+  }
+}
+
+constexpr int kLwThreads = 1024;
+
+__global__ void __launch_bounds__(kLwThreads) k_long_walk(SiteArgs a) {
+  if (!gate_open(a.gate, a.gate_want)) return;
+  __shared__ u64 red64[32];
+  __shared__ u32 pcoc[kPatSmem];
+  for (int i = threadIdx.x; i < kPatSmem; i += kLwThreads) pcoc[i] = 0u;
+  __syncthreads();
+  DevState* st = &a.arena->st;
+  const u32 h = a.h;
+  const u64 n_long = umin64(umin64(st->n_long, st->long_next), a.long_cap);
+  u64 msum = 0, nsum = 0, nsite = 0;
+  for (u64 i = blockIdx.x; i < n_long; i += gridDim.x) {
+    const u64 m = a.long_list[3 * i + 1];
+    if (threadIdx.x == 0) {
+      ++nsite;
+      if (m < (u64)kCocDense) atomicAdd(&a.arena->site_coc[m], 1ull);
+      else overflow_append(a.over, a.over_cap, st, kTagSites, m);
+      if (a.per_wi) emit_site_pred_count(a.long_list[3 * i + 2], a.over, a.over_cap, a.arena);
+      else emit_site_predicted(m, h, a.over, a.over_cap, a.arena);
+    }
+    const ulonglong2* tab = reinterpret_cast<const ulonglong2*>(a.long_tab + (i << h));
+    for (u32 b = threadIdx.x; b < (1u << h) / 2; b += kLwThreads) {
+      const ulonglong2 v2 = tab[b];
+      const u64 v[2] = {v2.x, v2.y};
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        if (!v[k]) continue;
+        const u64 nn = v[k] & 0xFFFFFFFFull, t = v[k] >> 32;
+        msum += umin64(t, nn - t);
+        nsum += nn;
+        if (nn < (u64)kPatSmem) atomicAdd(&pcoc[nn], 1u);
+        else emit_pattern_count(nn, a.over, a.over_cap, a.arena);
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kPatSmem; i += kLwThreads)
     if (pcoc[i]) atomicAdd(&a.arena->pat_coc[i], (u64)pcoc[i]);
   msum = block_reduce(msum, OpAdd(), 0ull, red64);
   nsum = block_reduce(nsum, OpAdd(), 0ull, red64);
@@ -778,8 +938,8 @@ void launch_site_heads(const SiteArgs& a, cudaStream_t s) {
   count_launches(1);
 }
 
-void launch_persite_decide(Arena* arena, u32 h, u64 sites_cap, int allow, cudaStream_t s) {
-  k_persite_decide<<<1, 1, 0, s>>>(arena, h, sites_cap, allow);
+void launch_persite_decide(Arena* arena, u32 h, u64 sites_cap, u64 long_cap, int allow, cudaStream_t s) {
+  k_persite_decide<<<1, 1, 0, s>>>(arena, h, sites_cap, long_cap, allow);
   count_launches(1);
 }
 
@@ -789,6 +949,7 @@ static size_t site_patterns_smem() {
 
 void init_branch_attributes() {
   cudaFuncSetAttribute(k_site_patterns, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)site_patterns_smem());
+  cudaFuncSetAttribute(k_site_chunks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)site_patterns_smem());
   cudaFuncSetAttribute(k_cs_scatter<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCsScatterSmem);
   cudaFuncSetAttribute(k_cs_scatter<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCsScatterSmem);
 }
@@ -796,6 +957,13 @@ void init_branch_attributes() {
 void launch_site_patterns(const SiteArgs& a, cudaStream_t s) {
   k_site_patterns<<<a.grid, kSpThreads, site_patterns_smem(), s>>>(a);
   count_launches(1);
+}
+
+void launch_site_long(const SiteArgs& a, cudaStream_t s) {
+  k_long_prep<<<a.grid, 256, 0, s>>>(a);
+  k_site_chunks<<<a.grid, kSpThreads, site_patterns_smem(), s>>>(a);
+  k_long_walk<<<a.grid, kLwThreads, 0, s>>>(a);
+  count_launches(3);
 }
 
 void launch_branch_windows(const WindowArgs& a, cudaStream_t s) {

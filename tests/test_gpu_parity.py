@@ -208,6 +208,73 @@ def test_site_counting_sort(P, n, n_sites, wi_sorted, split, h):
     assert_parity(run_gpu(P, tr, split=split, history_len=h), oracle.compute(tr, history_len=h))
 
 
+def _long_site_trace(seed, n, weights, wi_sorted=True):
+    """Branch events over len(weights) sites drawn with those weights: site 0
+    is always taken (one history pattern predicts nearly all its outcomes),
+    the others are taken with a probability of their own."""
+    rng = np.random.default_rng(seed)
+    w = np.asarray(weights, dtype=float)
+    sites = rng.choice(len(w), n, p=w / w.sum())
+    wis = np.arange(n) // 64 if wi_sorted else rng.integers(0, 1 << 16, n)
+    p_site = rng.random(len(w))
+    p_site[0] = 1.0
+    taken = (rng.random(n) < p_site[sites]).astype(np.int64)
+    return branch_only(sites.tolist(), wis.tolist(), taken.tolist())
+
+
+@pytest.mark.parametrize("n,weights,wi_sorted,h,scope", [
+    (400_003, [1, 1, 1], True, 16, 0),                # counting sort; about 133K outcomes per site
+    (400_003, [1, 1, 1], False, 16, 0),               # work-items out of order: radix sort
+    (300_001, [6, 1] + [0.01] * 300, True, 17, 0),    # long sites among short ones, two passes of bins
+    (250_007, [3, 1], False, 5, 1),                   # one history per (site, work-item)
+    (200_003, [5, 1, 1], True, 1, 1),
+])
+def test_long_sites(P, n, weights, wi_sorted, h, scope):
+    """Sites longer than 65,535 outcomes are counted in chunks on the per-site
+    path; the branch metrics equal the oracle's and the global path's."""
+    tr = _long_site_trace(900 + n % 97, n, weights, wi_sorted)
+    o = oracle.compute(tr, history_len=h, history_scope=scope)
+    for split, plan in ((1, 0), (3, 0), (1, 1)):
+        assert_parity(run_gpu(P, tr, split=split, history_len=h, history_scope=scope, plan=plan), o)
+
+
+@pytest.mark.parametrize("h,scope", [(1, 0), (16, 0), (3, 1)])
+def test_site_lengths_at_the_chunk_limits(P, h, scope):
+    """Sites of 65,536 and 65,535 outcomes (one above and at the per-block
+    limit), one of exactly two chunks plus h + 1, interleaved in push order."""
+    rng = np.random.default_rng(h + 10 * scope)
+    sites = np.concatenate([np.zeros(65_536, np.int64), np.ones(65_535, np.int64),
+                            np.full(2 * 16_384 + h + 1, 2, np.int64), np.full(5, 3, np.int64)])
+    sites = sites[rng.permutation(sites.size)]
+    n = sites.size
+    wis = np.arange(n) // 100
+    taken = (rng.random(n) < np.array([0.9, 0.5, 0.2, 0.5])[sites]).astype(np.int64)
+    tr = branch_only(sites.tolist(), wis.tolist(), taken.tolist())
+    o = oracle.compute(tr, history_len=h, history_scope=scope)
+    for split, plan in ((1, 0), (2, 0), (1, 1)):
+        assert_parity(run_gpu(P, tr, split=split, history_len=h, history_scope=scope, plan=plan), o)
+
+
+def test_long_sites_in_a_batch(P):
+    """Long sites in one batched graph, twice: with the counting sort (the
+    per-site path certain on the host), and with more than 2^20 events
+    arriving out of work-item order (the path chosen on the device)."""
+    from paper_1805_04207_gb300.api import compute_batch, push_trace
+    traces = [_long_site_trace(41, 400_003, [1, 1, 1], True), _long_site_trace(42, 1_200_001, [4, 2, 1, 1, 1], False),
+              _site_trace(43, 70_000, 300, True), synth.tiny()]
+    expect = [oracle.compute(t) for t in traces]
+    chars = [P.Characterizer(n_opcodes=t.n_opcodes) for t in traces]
+    try:
+        for _ in range(2):
+            for c, t in zip(chars, traces):
+                push_trace(c, t.to("cuda"))
+            for g, o in zip(compute_batch(chars), expect):
+                assert_parity(g, o)
+    finally:
+        for c in chars:
+            c.close()
+
+
 @pytest.mark.parametrize("n,offset,on_device", [(0, 0, True), (1, 0, True), (4099, 1, True), (300_001, 0, False),
                                                   (1_000_003, 3, True)])
 def test_simd_widths(P, n, offset, on_device):

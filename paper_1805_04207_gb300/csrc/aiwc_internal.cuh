@@ -337,7 +337,7 @@ struct SiteArgs {
   const u32* cur{};
   u64 n{};               // branch events
   u32 h{};             // history length (<= kSiteMaxHist)
-  u64* sites{};        // site list: (start, length) pairs, 2 words per site
+  u64* sites{};        // site list: one word per site, start << 32 | length
   u64 sites_cap{};
   u64* over{};
   u64 over_cap{};
@@ -364,7 +364,7 @@ struct SiteSortArgs {
   u64 n{};
   u32* counts{};         // scratch: site_sort_count_words(n) words
   u32* chunks{};         // scratch: site_sort_chunk_words(n) words
-  u64* sites{};          // out: (start, length) per site with events
+  u64* sites{};          // out: start << 32 | length per site with events
   u64 sites_cap{};
   Arena* arena{};
   int sm_count{};
@@ -376,7 +376,6 @@ void launch_site_sort_scatter(const SiteSortArgs& a, cudaStream_t s);  // the so
 
 constexpr u32 kSiteMaxHist = 17;       // dense pattern bins: 2^15 per pass, at most 4 passes
 constexpr u64 kSiteMaxLen = 65535;     // packed 16-bit taken / total counters
-constexpr u64 kSiteListCap = 1ull << 20;  // sites listed for the per-site path
 // Long sites: at most n / (kSiteMaxLen + 1) of n branch events; their tables
 // take 8 << h bytes and their list entries 24 bytes each.
 inline u64 long_sites_cap(size_t tab_bytes, size_t list_bytes, u32 h) {

@@ -133,13 +133,14 @@ struct aiwc_handle {
   u64 sbt_floor = 0;     // slots an overflowing invocation asked for (the automatic size never goes below)
   int inv_plan = 0;      // plan 0: this invocation's memory plan, chosen by its first memory push (1 sort, 2 hash)
   DevState* h_state = nullptr;  // pinned copy of the device counters
-  DevBuf sites;                 // per-site segment list
+  DevBuf sites;                 // the per-site path's list of long sites (the site list lives in pat_b)
   bool last_plan_hash = false;
   u64 n_mem = 0, n_br = 0, n_runs = 0;
   u32 br_pushes = 0;    // branch ingest launches in this invocation (orders the sortedness check)
   u64 epoch = 0;        // changes whenever a device buffer of the handle moves (keys cached graphs)
   // sizes fixed by prepare() for the current compute
   u64 c_over_cap = 0, c_sites_cap = 0;
+  size_t c_site_off = 0;        // the site list's byte offset in pat_b (after the counting sort's chunk sums)
   size_t c_low_off = 0;
   u64 value_bound = 0;  // bound on ITB / IPT values >= kValDense (each uses kValDense instructions)
   // run tables of host run pushes, one per staging buffer (pinned, so that
@@ -1234,7 +1235,10 @@ aiwc_status prepare(aiwc_handle* h) {
   ENSURE(h->br_a, std::max<u64>(n_br, 1) * 8, true);
   ENSURE(h->br_b, std::max<u64>(n_br, 1) * 8, false);
   ENSURE(h->pat_a, std::max<u64>(n_br, 1) * 8, false);
-  ENSURE(h->pat_b, std::max<u64>(n_br, 1) * 8, false);
+  // the site list (one word per site, n_br at most) follows the counting
+  // sort's chunk sums in the second pattern buffer
+  h->c_site_off = (site_sort_chunk_words(n_br) * 4 + 255) & ~size_t(255);
+  ENSURE(h->pat_b, std::max<size_t>(h->c_site_off + n_br * 8, std::max<u64>(n_br, 1) * 8), false);
   ENSURE(h->rk_a, std::max<u64>(n_runs, 1) * 8, true);
   ENSURE(h->rk_b, std::max<u64>(n_runs, 1) * 8, false);
   ENSURE(h->run_sum, std::max<u64>(n_runs, 1) * 32, true);
@@ -1243,8 +1247,10 @@ aiwc_status prepare(aiwc_handle* h) {
   ENSURE(h->bsums, sort_block_sums_words(nmax) * 4, false);
   // memory levels, or the branch site runs, or two levels of pattern runs
   ENSURE(h->tiles, std::max<u64>((u64)kLevels * ntiles_of(n_mem), 2 * ntiles_of(n_br) + 1) * sizeof(TileSum), false);
-  h->c_sites_cap = std::min<u64>(std::max<u64>(n_br, 1), kSiteListCap);
-  ENSURE(h->sites, h->c_sites_cap * 16, false);
+  // site starts and lengths are 32-bit fields: no list (the global path) from 2^32 events
+  h->c_sites_cap = n_br < (1ull << 32) ? n_br : 0;
+  // the long-site list: every long site has more than kSiteMaxLen events
+  ENSURE(h->sites, (n_br / (kSiteMaxLen + 1) + 1) * 24, false);
   // runs pushed in (work-item, push) order need no sort: checked before the
   // counters are read back
   launch_keys_sorted((const u64*)h->rk_a.p, n_runs, &h->arena->st.run_unsorted, h->stream);
@@ -1277,9 +1283,9 @@ SortDesc branch_sort_desc(aiwc_handle* h) {
 }
 
 // Long sites the per-site path can take: their tables live in the first
-// pattern buffer, their list in the second (both free on that path once the
-// site sort has run).
-u64 long_cap_of(const aiwc_handle* h) { return long_sites_cap(h->pat_a.cap, h->pat_b.cap, h->cfg.history_len); }
+// pattern buffer (free on that path once the site sort has run), their list
+// in `sites`.
+u64 long_cap_of(const aiwc_handle* h) { return long_sites_cap(h->pat_a.cap, h->sites.cap, h->cfg.history_len); }
 
 SiteArgs site_args(aiwc_handle* h, const SortDesc& bsort) {
   SiteArgs sa;
@@ -1288,14 +1294,14 @@ SiteArgs site_args(aiwc_handle* h, const SortDesc& bsort) {
   sa.cur = bsort.cur;
   sa.n = h->n_br;
   sa.h = h->cfg.history_len;
-  sa.sites = (u64*)h->sites.p;
+  sa.sites = (u64*)((char*)h->pat_b.p + h->c_site_off);
   sa.sites_cap = h->c_sites_cap;
   sa.over = (u64*)h->over_a.p;
   sa.over_cap = h->c_over_cap;
   sa.arena = h->arena;
   sa.grid = h->sm_count;
   sa.long_tab = (u64*)h->pat_a.p;
-  sa.long_list = (u64*)h->pat_b.p;
+  sa.long_list = (u64*)h->sites.p;
   sa.long_cap = long_cap_of(h);
   return sa;
 }
@@ -1308,7 +1314,7 @@ SiteSortArgs site_sort_args(aiwc_handle* h) {
   ss.n = h->n_br;
   ss.counts = (u32*)h->pat_a.p;
   ss.chunks = (u32*)h->pat_b.p;
-  ss.sites = (u64*)h->sites.p;
+  ss.sites = (u64*)((char*)h->pat_b.p + h->c_site_off);
   ss.sites_cap = h->c_sites_cap;
   ss.arena = h->arena;
   ss.sm_count = h->sm_count;

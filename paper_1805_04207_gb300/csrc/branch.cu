@@ -143,10 +143,7 @@ __global__ void __launch_bounds__(256) k_site_heads(SiteArgs a) {
     mx = len > mx ? len : mx;
     if (len > kSiteMaxLen) atomicAdd(&st->n_long, 1ull);
     const u64 k = atomicAdd(&st->n_sites, 1ull);
-    if (k < a.sites_cap) {
-      a.sites[2 * k] = i;
-      a.sites[2 * k + 1] = len;
-    }
+    if (k < a.sites_cap) a.sites[k] = (i << 32) | len;  // a list exists only below 2^32 events
   }
   if (mx) atomicMax(&st->br_site_max, mx);
 }
@@ -281,10 +278,7 @@ __global__ void __launch_bounds__(kCsScanThreads) k_cs_scan_sites(SiteSortArgs a
     sv[q] = (u32)start;
     nl += tot[q] > kSiteMaxLen;
     if (tot[q]) {
-      if (k < a.sites_cap) {
-        a.sites[2 * k] = start;
-        a.sites[2 * k + 1] = tot[q];
-      }
+      if (k < a.sites_cap) a.sites[k] = (start << 32) | tot[q];
       ++k;
       mx = tot[q] > mx ? tot[q] : mx;
     }
@@ -514,7 +508,7 @@ __global__ void __launch_bounds__(kSpThreads) k_site_patterns(SiteArgs a) {
   const u64 n_sites = umin64(st->n_sites, a.sites_cap);
   u64 msum = 0, nsum = 0, nsite = 0;
   for (u64 si = blockIdx.x; si < n_sites; si += gridDim.x) {
-    const u64 start = a.sites[2 * si], m = a.sites[2 * si + 1];
+    const u64 start = a.sites[si] >> 32, m = a.sites[si] & 0xFFFFFFFFull;
     if (m > kSiteMaxLen) continue;
     if (threadIdx.x == 0) {
       ++nsite;
@@ -561,11 +555,11 @@ __global__ void __launch_bounds__(256) k_long_prep(SiteArgs a) {
   const u64 n_long = umin64(st->n_long, a.long_cap);
   const u64 tid = (u64)blockIdx.x * blockDim.x + threadIdx.x, nt = (u64)gridDim.x * blockDim.x;
   for (u64 i = tid; i < n_sites; i += nt) {
-    const u64 m = a.sites[2 * i + 1];
+    const u64 m = a.sites[i] & 0xFFFFFFFFull;
     if (m > kSiteMaxLen) {
       const u64 k = atomicAdd(&st->long_next, 1ull);
       if (k < a.long_cap) {
-        a.long_list[3 * k] = a.sites[2 * i];
+        a.long_list[3 * k] = a.sites[i] >> 32;
         a.long_list[3 * k + 1] = m;
         a.long_list[3 * k + 2] = 0ull;
       }

@@ -41,6 +41,7 @@ constexpr u32 kErrOpcode = 2u;      // opcode >= n_opcodes and not a barrier
 constexpr u32 kErrWorkItem = 4u;    // work-item id >= max_work_items
 constexpr u32 kErrOverflow = 8u;    // an internal list exceeded its capacity
 constexpr u32 kErrRun = 16u;        // a run reaches past its opcode array
+constexpr u32 kErrSort = 32u;       // a sort's bounded wait for an earlier tile gave up
 
 // Device-resident counters of one invocation. Zeroed by a memset, then the
 // AND accumulators and minima are set to their identities.
@@ -161,9 +162,10 @@ struct SortDesc {
   u64 mask{};
   const u64* dmask{}; // optional device mask, ANDed with mask (NULL = none)
   int lo_bit{};
-  u32* counts{};      // 256 * ntiles digit counts (scanned in place)
-  u32* block_sums{};
+  u32* counts{};      // sort_counts_words(n_cap) words: digit counts, or the one-sweep look-back words
+  u32* block_sums{};  // sort_block_sums_words(n_cap) words: scan sums, or digit totals and tile tickets
   u32 ntiles{};
+  u32* err{};         // DevState::err: kErrSort when a bounded wait gave up (NULL: not reported)
 };
 
 // Text returned by aiwc_last_error(NULL) on this thread.

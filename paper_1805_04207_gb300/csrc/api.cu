@@ -1272,6 +1272,7 @@ SortDesc sort_desc(aiwc_handle* h, DevBuf& a, DevBuf& b, int slot, const u64* n_
   d.counts = (u32*)h->counts.p;
   d.block_sums = (u32*)h->bsums.p;
   d.ntiles = sort_tiles(n_host);
+  d.err = &h->arena->st.err;
   return d;
 }
 
@@ -1371,7 +1372,8 @@ void enqueue_mem_path(aiwc_handle* h, cudaStream_t st, const Plan& p) {
     ha.over = over;
     ha.over_cap = over_cap;
     ha.arena = h->arena;
-    ha.grid_scatter = h->sm_count * 8;
+    // up to eight blocks per SM, none without events (2048 events per block and step)
+    ha.grid_scatter = (int)std::min<u64>((u64)h->sm_count * 8, std::max<u64>((n_mem + 2047) / 2048, 1));
     ha.sm_count = h->sm_count;
     ha.seg_shift = p.seg_shift;
     // the 64-bit word buffer is free in the hash plan: wide-segment histograms
@@ -1596,6 +1598,7 @@ aiwc_status finish(aiwc_handle* h, aiwc_metrics* out, uint64_t* user_hist) {
   if (err & kErrOpcode) return fail(h, AIWC_EINVAL, "opcode >= n_opcodes that is not a barrier", false);
   if (err & kErrWorkItem) return fail(h, AIWC_EINVAL, "work-item id >= max_work_items", false);
   if (err & kErrRun) return fail(h, AIWC_EINVAL, "instruction run reaches past its opcode array", false);
+  if (err & kErrSort) return fail(h, AIWC_ETIMEOUT, "a radix sort pass waited too long for an earlier tile", false);
   return AIWC_OK;
 }
 

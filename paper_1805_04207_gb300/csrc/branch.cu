@@ -499,6 +499,7 @@ __global__ void __launch_bounds__(kSpThreads) k_site_patterns(SiteArgs a) {
   __shared__ u32 pcoc[kPatSmem];  // pattern count-of-counts for small counts
   const WinSmem sm = win_smem(spm, &n_used);
   DevState* st = &a.arena->st;
+  if (blockIdx.x >= umin64(st->n_sites, a.sites_cap)) return;  // no site for this block
   const u64* w = *a.cur ? a.b : a.a;
   for (int i = threadIdx.x; i < kPatSmem; i += kSpThreads) pcoc[i] = 0u;
   for (int i = threadIdx.x; i < (1 << kSpBinsLog); i += kSpThreads) sm.cnt[i] = 0u;
@@ -580,12 +581,17 @@ __global__ void __launch_bounds__(kSpThreads) k_site_chunks(SiteArgs a) {
   const WinSmem sm = win_smem(spm, &n_used);
   DevState* st = &a.arena->st;
   const u64* w = *a.cur ? a.b : a.a;
-  for (int i = threadIdx.x; i < (1 << kSpBinsLog); i += kSpThreads) sm.cnt[i] = 0u;
-  if (threadIdx.x == 0) n_used = 0;
-  __syncthreads();
   const u32 h = a.h;
   const u64 n_long = umin64(umin64(st->n_long, st->long_next), a.long_cap);  // the listed ones
   const u64 G = gridDim.x;
+  {
+    u64 chunks = 0;
+    for (u64 i = 0; i < n_long; ++i) chunks += (a.long_list[3 * i + 1] + kLongChunk - 1) / kLongChunk;
+    if (blockIdx.x >= chunks) return;  // no chunk for this block
+  }
+  for (int i = threadIdx.x; i < (1 << kSpBinsLog); i += kSpThreads) sm.cnt[i] = 0u;
+  if (threadIdx.x == 0) n_used = 0;
+  __syncthreads();
   u64 qbase = 0;
   for (u64 i = 0; i < n_long; ++i) {
     const u64 start = a.long_list[3 * i], m = a.long_list[3 * i + 1];
@@ -613,11 +619,12 @@ __global__ void __launch_bounds__(kLwThreads) k_long_walk(SiteArgs a) {
   if (!gate_open(a.gate, a.gate_want)) return;
   __shared__ u64 red64[32];
   __shared__ u32 pcoc[kPatSmem];
-  for (int i = threadIdx.x; i < kPatSmem; i += kLwThreads) pcoc[i] = 0u;
-  __syncthreads();
   DevState* st = &a.arena->st;
   const u32 h = a.h;
   const u64 n_long = umin64(umin64(st->n_long, st->long_next), a.long_cap);
+  if (blockIdx.x >= n_long) return;
+  for (int i = threadIdx.x; i < kPatSmem; i += kLwThreads) pcoc[i] = 0u;
+  __syncthreads();
   u64 msum = 0, nsum = 0, nsite = 0;
   for (u64 i = blockIdx.x; i < n_long; i += gridDim.x) {
     const u64 m = a.long_list[3 * i + 1];

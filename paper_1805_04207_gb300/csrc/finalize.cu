@@ -182,19 +182,21 @@ __device__ u64 cover_walk(const u64* dense, int dense_n, const u64* over, u64 ob
 
 // Order statistics of a value distribution: dense[v] values v for v <
 // kValDense, then the ascending overflow segment [ob, oe). Each thread owns
-// kPer consecutive bins; one pass sums them (independent loads), one block
-// scan places every thread's slice, and the threads whose slices hold the
-// wanted ranks find the values.
+// kPer consecutive bins; one pass sums them (independent loads; bins from
+// dense_n on are known to be empty and are not read), one block scan places
+// every thread's slice, and the threads whose slices hold the wanted ranks
+// find the values.
 constexpr int kPer = kValDense / kFinThreads;
 static_assert(kValDense % kFinThreads == 0, "bins must split evenly over the block");
 
-__device__ void order_stats(const u64* dense, const u64* over, u64 ob, u64 oe, u64* cnt, u64* mn, u64* mx, u64* lo,
-                            u64* hi, double* med, Shared& s) {
+__device__ void order_stats(const u64* dense, int dense_n, const u64* over, u64 ob, u64 oe, u64* cnt, u64* mn,
+                            u64* mx, u64* lo, u64* hi, double* med, Shared& s) {
   const int b0 = threadIdx.x * kPer;
   const ulonglong2* d2 = reinterpret_cast<const ulonglong2*>(dense + b0);
   u64 mine = 0;
 #pragma unroll 8
   for (int q = 0; q < kPer / 2; ++q) {
+    if (b0 + 2 * q >= dense_n) break;
     const ulonglong2 v = d2[q];
     mine += v.x + v.y;
   }
@@ -332,6 +334,10 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(FinalizeArgs a) {
   aiwc_metrics* m = &a.result->m;
   const int task = blockIdx.x;
   const u64 N = st.total_reads + st.total_writes;
+  // bins past these are empty: an ITB or IPT value counts at most every
+  // instruction slot, a pattern or site at most every branch outcome
+  const int val_n = (int)umin64(st.total_instructions + st.barriers + 1, (u64)kValDense);
+  const int pat_n = (int)umin64(st.n_branch + 1, (u64)kValDense);
   if (task < kLevels) {
     const int l = task;
     const double S = clog_sum(ar->mem_coc[l], kCocDense, over, s.tag_begin[l], s.tag_begin[l + 1], a.precision, s);
@@ -367,8 +373,8 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(FinalizeArgs a) {
     const int tag = itb ? kTagItb : kTagIpt;
     u64 c, mn, mx, lo, hi;
     double med;
-    order_stats(itb ? ar->itb_dense : ar->ipt_dense, over, s.tag_begin[tag], s.tag_begin[tag + 1], &c, &mn, &mx, &lo,
-                &hi, &med, s);
+    order_stats(itb ? ar->itb_dense : ar->ipt_dense, val_n, over, s.tag_begin[tag], s.tag_begin[tag + 1], &c, &mn,
+                &mx, &lo, &hi, &med, s);
     if (threadIdx.x == 0) {
       if (itb) {
         m->itb_count = c; m->itb_min = mn; m->itb_max = mx; m->itb_median_lo = lo; m->itb_median_hi = hi;
@@ -388,9 +394,9 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(FinalizeArgs a) {
     if (part < kYokParts) {
       constexpr int kSlice = kValDense / kYokParts;
       const u64 ob = part == 0 ? s.tag_begin[kTagPat] : 0, oe = part == 0 ? s.tag_begin[kTagPat + 1] : 0;
-      v = clog_sum(ar->pat_coc, (part + 1) * kSlice, over, ob, oe, 0, s, part * kSlice);
+      v = clog_sum(ar->pat_coc, min((part + 1) * kSlice, pat_n), over, ob, oe, 0, s, part * kSlice);
     } else {
-      v = clog_sum(ar->site_pat_coc, kValDense, over, s.tag_begin[kTagSitePat], s.tag_begin[kTagSitePat + 1], 0, s);
+      v = clog_sum(ar->site_pat_coc, pat_n, over, s.tag_begin[kTagSitePat], s.tag_begin[kTagSitePat + 1], 0, s);
     }
     __shared__ bool last;
     if (threadIdx.x == 0) {

@@ -410,11 +410,12 @@ __global__ void __launch_bounds__(SegShape<S>::T) k_mem_segments(HashArgs a) {
   __shared__ u32 coc[kLevels][kCocSmem];
   __shared__ u32 wsum[8];
   __shared__ u64 red64[32];
+  const u64 n_list = umin64(a.n_used[0], a.tab.mask + 1);
+  if (blockIdx.x >= n_list) return;  // no segment for this block
   for (int i = threadIdx.x; i < kLevels * kCocSmem; i += T) (&coc[0][0])[i] = 0u;
   for (int i = threadIdx.x; i < 2 * NA; i += T) hist[i] = 0u;
   __syncthreads();
   u64 fp = 0, ur = 0, uw = 0;
-  const u64 n_list = umin64(a.n_used[0], a.tab.mask + 1);
   for (u64 u = blockIdx.x; u < n_list; u += gridDim.x) {
     const u32 s = a.used_list[u];
     const u32 cnt = a.tab.cnt[s];
@@ -447,9 +448,10 @@ __global__ void __launch_bounds__(kBfThreads) k_mem_big_fill(HashArgs a) {
   __shared__ __align__(16) u32 hist[2 * NA];
   __shared__ u32 m_off[kBfThreads], m_cnt[kBfThreads], m_pre[kBfThreads];
   __shared__ u32 wt[33];
-  for (int i = threadIdx.x; i < 2 * NA; i += kBfThreads) hist[i] = 0u;
   const u64 C = a.tab.mask + 1;
   const u64 n_big = umin64(umin64(a.n_used[1], C), a.big_cap);
+  if (n_big == 0) return;
+  for (int i = threadIdx.x; i < 2 * NA; i += kBfThreads) hist[i] = 0u;
   const u64 G = gridDim.x;
   u64 qbase = 0;  // chunks in earlier batches
   for (u64 i0 = 0; i0 < n_big; i0 += kBfThreads) {
@@ -500,11 +502,12 @@ __global__ void __launch_bounds__(SegShape<S>::T) k_mem_big_walk(HashArgs a) {
   __shared__ u32 coc[kLevels][kCocSmem];
   __shared__ u32 wsum[8];
   __shared__ u64 red64[32];
+  const u64 n_big = umin64(umin64(a.n_used[1], a.tab.mask + 1), a.big_cap);
+  if (blockIdx.x == 0 && threadIdx.x == 0 && a.n_used[1] > a.big_cap) atomicOr(&a.arena->st.err, kErrOverflow);
+  if (blockIdx.x >= n_big) return;  // no wide segment for this block
   for (int i = threadIdx.x; i < kLevels * kCocSmem; i += T) (&coc[0][0])[i] = 0u;
   __syncthreads();
   u64 fp = 0, ur = 0, uw = 0;
-  const u64 n_big = umin64(umin64(a.n_used[1], a.tab.mask + 1), a.big_cap);
-  if (blockIdx.x == 0 && threadIdx.x == 0 && a.n_used[1] > a.big_cap) atomicOr(&a.arena->st.err, kErrOverflow);
   for (u64 i = blockIdx.x; i < n_big; i += gridDim.x) {
     walk_superblock<S, T>(a.big_hist + i * (u64)(2 * NA), coc, wsum, a, fp, ur, uw);
     __syncthreads();

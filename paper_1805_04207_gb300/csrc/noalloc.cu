@@ -34,10 +34,12 @@ constexpr size_t kOffTable = kOffLow + a256(2 * kNoAllocMaxEvents);
 constexpr size_t kOffScan = kOffTable + a256(kSbtBytes * kNoAllocSlots);
 constexpr size_t kOffOverA = kOffScan + a256(4 * (kNoAllocSlots / 4096 + 1));
 constexpr size_t kOffOverB = kOffOverA + a256(8 * kNoAllocOverCap);
-constexpr size_t kCountsWords = 256 * ((kNoAllocOverCap + 2047) / 2048);  // sort tiles of 2048 keys
+// the radix sort's scratch for this capacity (tiles of 2048 keys): look-back
+// words or digit counts, then digit totals and tile tickets
+constexpr size_t kCountsWords = 512 * ((kNoAllocOverCap + 2047) / 2048);
 constexpr size_t kOffCounts = kOffOverB + a256(8 * kNoAllocOverCap);
 constexpr size_t kOffBsums = kOffCounts + a256(4 * kCountsWords);
-constexpr size_t kOffBitmap = kOffBsums + a256(4 * (kCountsWords / 4096 + 2));
+constexpr size_t kOffBitmap = kOffBsums + a256(4 * (8 * 256 + 16));
 constexpr size_t kOffBig = kOffBitmap + a256(kNoAllocMaxWi / 8);
 constexpr size_t kNoAllocBigBytes = (kNoAllocMaxEvents / 16384) * 2 * 2048 * 4;  // wide-segment histograms
 constexpr size_t kNoAllocBytes = kOffBig + a256(kNoAllocBigBytes);

@@ -3,11 +3,14 @@
 // Each pass handles one 8-bit window of the key. A pass whose window holds no
 // bit that varies between keys (known from the OR and AND over all keys,
 // accumulated by the kernel that produced them) is skipped on the device, so
-// the host launches a fixed sequence and never waits for a count. Each pass is
-// reduce-then-scan: per-tile digit counts, an exclusive scan over
-// (digit, tile), then a stable scatter staged through shared memory so that
-// each digit's keys leave the tile as one contiguous run. No block ever waits
-// for another block.
+// the host launches a fixed sequence and never waits for a count. Three forms:
+// one tile (every pass in one block, in shared memory); fewer than 2^30 keys
+// (one-sweep passes: one launch each, the tiles' digit offsets found by a
+// bounded look-back over earlier tiles); more (reduce-then-scan passes:
+// per-tile digit counts, an exclusive scan over (digit, tile), a stable
+// scatter staged through shared memory). In every form each digit's keys
+// leave a tile as one contiguous run.
+#include <algorithm>
 #include <atomic>
 
 #include "aiwc_internal.cuh"
@@ -243,13 +246,35 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(SortDesc d, int pass) 
   }
 }
 
-// A sort of a few tiles (at most kFewTiles): two launches per pass instead of
-// six. The pass reads the buffer its parity gives -- the live buffer when the
-// sort starts, flipped by every pass that runs (launched and with a varying
-// window) -- so no pass writes `cur`; one launch at the end flips it by the
-// parity of the passes that ran. The scatter computes each digit's global
-// offset for its tile from all tiles' counts itself (256 x ntiles reads).
-constexpr u32 kFewTiles = 64;
+// One-sweep form (sorts of more than one tile and fewer than 2^30 keys): one
+// launch counts the digits of every pass at once (k_hist_all), then one
+// launch per pass ranks each tile, publishes the tile's digit counts and finds
+// the counts of the tiles before it by decoupled look-back (each tile waits
+// only for tiles that took their tickets earlier, so every wait ends), and
+// scatters. A pass reads the buffer its parity gives -- the live buffer when
+// the sort starts, flipped by every pass that runs (launched and with a
+// varying window) -- so no pass writes `cur`; one launch at the end flips it
+// by the parity of the passes that ran.
+//
+// Scratch: block_sums holds the digit totals of the eight windows (8 x 256)
+// and eight tile tickets, zeroed before the sort; counts holds two regions of
+// look-back words (ntiles x 256 each), the pass of parity q using region q & 1
+// and clearing its tile's words of the other region for the next pass. A
+// look-back word is state << 30 | count: 0 not yet published, kLbAgg the
+// tile's own count, kLbInc the count of this and every earlier tile.
+constexpr u32 kLbAgg = 1u << 30, kLbInc = 2u << 30, kLbCount = (1u << 30) - 1u;
+constexpr u32 kSpinLimit = 1u << 20;  // polls of one word (with a short sleep each) before giving up
+constexpr u32 kTotWords = 8 * 256;    // digit totals; the eight tickets follow
+
+// Look-back words are read and written at GPU scope (not from a stale L1 line).
+__device__ __forceinline__ u32 ld_gpu(const u32* p) {
+  u32 v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_gpu(u32* p, u32 v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
 
 __device__ __forceinline__ bool few_pass(const SortDesc& d, int pass, u32 host_passes, int* shift, int* parity) {
   if (!gate_open(d.gate, d.gate_want)) return false;
@@ -261,69 +286,65 @@ __device__ __forceinline__ bool few_pass(const SortDesc& d, int pass, u32 host_p
   }
   *shift = d.lo_bit + 8 * pass;
   *parity = before & 1;
-  return *shift < 64 && ((varying >> *shift) & 0xFFull) != 0;
+  return *shift < 64 && ((host_passes >> pass) & 1u) && ((varying >> *shift) & 0xFFull) != 0;
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_hist_few(SortDesc d, int pass, u32 host_passes) {
-  int shift, parity;
-  if (!few_pass(d, pass, host_passes, &shift, &parity)) return;
-  const u32 nt = live_tiles(d);
-  if (blockIdx.x >= nt) return;
-  __shared__ u32 h[kWarps][256];
-  for (int i = threadIdx.x; i < kWarps * 256; i += kSortThreads) (&h[0][0])[i] = 0;
+// Digit totals of every pass that will run, and the first pass's look-back region cleared.
+__global__ void __launch_bounds__(kSortThreads) k_hist_all(SortDesc d, u32 host_passes) {
+  if (!gate_open(d.gate, d.gate_want)) return;
+  __shared__ u32 h[4][8][256];  // one copy per pair of warps
+  for (int i = threadIdx.x; i < 4 * 8 * 256; i += kSortThreads) (&h[0][0][0])[i] = 0u;
   __syncthreads();
   const u64 n = umin64(*d.n, d.n_cap);
-  const u64* src = (*d.cur ^ (u32)parity) ? d.b : d.a;
-  const u64 base = (u64)blockIdx.x * kSortTile;
-  const int w = threadIdx.x >> 5;
+  const u64* src = *d.cur ? d.b : d.a;
   const u64 m = eff_mask(d);
-#pragma unroll 4
-  for (int k = 0; k < kSortItems; ++k) {
-    const u64 i = base + (u64)k * kSortThreads + threadIdx.x;
-    if (i < n) atomicAdd(&h[w][((src[i] & m) >> shift) & 0xFF], 1u);
+  const u64 varying = ((*d.key_or) ^ (*d.key_and)) & m;
+  u32 act = 0;  // passes that run
+  for (int p = 0; p < 8 && d.lo_bit + 8 * p < 64; ++p)
+    if (((host_passes >> p) & 1u) && ((varying >> (d.lo_bit + 8 * p)) & 0xFFull)) act |= 1u << p;
+  u32 (*hh)[256] = h[(threadIdx.x >> 6) & 3];
+  const u64 stride = (u64)gridDim.x * kSortThreads;
+  for (u64 i = (u64)blockIdx.x * kSortThreads + threadIdx.x; i < n; i += stride) {
+    const u64 k = src[i] & m;
+#pragma unroll
+    for (int p = 0; p < 8; ++p)
+      if ((act >> p) & 1u) atomicAdd(&hh[p][(u32)(k >> (d.lo_bit + 8 * p)) & 0xFFu], 1u);
   }
   __syncthreads();
-  u32 s = 0;
-#pragma unroll
-  for (int q = 0; q < kWarps; ++q) s += h[q][threadIdx.x];
-  d.counts[(u64)threadIdx.x * nt + blockIdx.x] = s;
+  for (int i = threadIdx.x; i < 8 * 256; i += kSortThreads) {
+    const u32 c = (&h[0][0][0])[i] + (&h[1][0][0])[i] + (&h[2][0][0])[i] + (&h[3][0][0])[i];
+    if (c) atomicAdd(&d.block_sums[i], c);
+  }
+  const u64 words = 256ull * live_tiles(d);
+  for (u64 i = (u64)blockIdx.x * kSortThreads + threadIdx.x; i < words; i += stride) d.counts[i] = 0u;
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_scatter_few(SortDesc d, int pass, u32 host_passes) {
+__global__ void __launch_bounds__(kSortThreads) k_onesweep(SortDesc d, int pass, u32 host_passes) {
   int shift, parity;
   if (!few_pass(d, pass, host_passes, &shift, &parity)) return;
-  const u32 nt = live_tiles(d);
-  if (blockIdx.x >= nt) return;
   __shared__ u32 wcnt[kWarps][256];
   __shared__ u32 dofs[256];
   __shared__ u32 gofs[256];
   __shared__ u32 wt[33];
+  __shared__ u32 s_tile;
   __shared__ u64 stage[kSortTile];
+  const u32 nt = live_tiles(d);
+  if (threadIdx.x == 0) s_tile = atomicAdd(&d.block_sums[kTotWords + pass], 1u);
   for (int i = threadIdx.x; i < kWarps * 256; i += kSortThreads) (&wcnt[0][0])[i] = 0;
-  {
-    // this tile's global offset for digit dg: the keys of smaller digits, then
-    // those of digit dg in earlier tiles
-    const int dg = threadIdx.x;
-    u32 before = 0, total = 0;
-    for (u32 t = 0; t < nt; ++t) {
-      const u32 c = d.counts[(u64)dg * nt + t];
-      if (t < blockIdx.x) before += c;
-      total += c;
-    }
-    u32 all;
-    gofs[dg] = block_excl_scan<u32>(total, &all, wt) + before;
-  }
   __syncthreads();
+  const u32 t = s_tile;
+  if (t >= nt) return;
   const u64 n = umin64(*d.n, d.n_cap);
   const u32 cur = *d.cur ^ (u32)parity;
   const u64* src = cur ? d.b : d.a;
   u64* dst = cur ? d.a : d.b;
-  const u64 base = (u64)blockIdx.x * kSortTile;
+  const u64 base = (u64)t * kSortTile;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const u32 lt_mask = (1u << lane) - 1u;
   const u64 m = eff_mask(d);
   u64 key[kSortItems];
   u32 rank[kSortItems];
+  // warp w ranks positions base + w*256 + k*32 + lane in that order (stable)
 #pragma unroll
   for (int k = 0; k < kSortItems; ++k) {
     const u64 i = base + (u64)w * (32 * kSortItems) + (u64)k * 32 + lane;
@@ -338,18 +359,46 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter_few(SortDesc d, int pa
     __syncwarp();
   }
   __syncthreads();
-  {
-    const int dg = threadIdx.x;
-    u32 tot = 0;
+  const int dg = threadIdx.x;  // one thread per digit
+  u32 tot = 0;
 #pragma unroll
-    for (int q = 0; q < kWarps; ++q) {
-      const u32 c = wcnt[q][dg];
-      wcnt[q][dg] = tot;
-      tot += c;
-    }
-    u32 all;
-    dofs[dg] = block_excl_scan<u32>(tot, &all, wt);
+  for (int q = 0; q < kWarps; ++q) {
+    const u32 c = wcnt[q][dg];
+    wcnt[q][dg] = tot;
+    tot += c;
   }
+  u32 all;
+  dofs[dg] = block_excl_scan<u32>(tot, &all, wt);
+  const u32 dstart = block_excl_scan<u32>(d.block_sums[pass * 256 + dg], &all, wt);
+  u32* look = d.counts + (size_t)(parity & 1) * 256u * d.ntiles;
+  u32* mine = look + (size_t)t * 256 + dg;
+  u32 excl = 0;
+  if (t == 0) {
+    st_gpu(mine, kLbInc | tot);
+  } else {
+    st_gpu(mine, kLbAgg | tot);
+    for (u32 j = t - 1;; --j) {
+      const u32* pw = look + (size_t)j * 256 + dg;
+      u32 v = ld_gpu(pw);
+      for (u32 spin = 0; !(v >> 30); ++spin) {
+        if (spin == kSpinLimit) {
+          // every earlier tile has its ticket and runs, so this does not
+          // happen; should it, the counts so far keep every position in range
+          if (d.err) atomicOr(d.err, kErrSort);
+          v = kLbInc;
+          break;
+        }
+        __nanosleep(64);
+        v = ld_gpu(pw);
+      }
+      excl += v & kLbCount;
+      if ((v & kLbInc) || j == 0) break;
+    }
+    st_gpu(mine, kLbInc | (excl + tot));
+  }
+  gofs[dg] = dstart + excl;
+  // the next pass's region: this tile's words start unpublished
+  d.counts[(size_t)((parity + 1) & 1) * 256u * d.ntiles + (size_t)t * 256 + dg] = 0u;
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < kSortItems; ++k) {
@@ -360,7 +409,7 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter_few(SortDesc d, int pa
     }
   }
   __syncthreads();
-  const u64 tile_n = n > base ? (n - base < (u64)kSortTile ? n - base : (u64)kSortTile) : 0ull;
+  const u64 tile_n = n > base ? umin64(n - base, (u64)kSortTile) : 0ull;
   for (u32 j = threadIdx.x; j < tile_n; j += kSortThreads) {
     const u64 kv = stage[j];
     const u32 dig = (u32)(((kv & m) >> shift) & 0xFF);
@@ -457,12 +506,12 @@ __global__ void k_flip(SortDesc d, int pass) {
 
 size_t sort_counts_words(u64 n_max) {
   u64 nt = (n_max + kSortTile - 1) / kSortTile;
-  return (size_t)(256 * (nt ? nt : 1));
+  return (size_t)(512 * (nt ? nt : 1));  // two look-back regions of the one-sweep form
 }
 
 size_t sort_block_sums_words(u64 n_max) {
-  u64 len = sort_counts_words(n_max);
-  return (size_t)((len + kScanBlock - 1) / kScanBlock + 1);
+  u64 len = 256 * ((n_max + kSortTile - 1) / kSortTile + 1);
+  return std::max<size_t>((size_t)((len + kScanBlock - 1) / kScanBlock + 1), kTotWords + 8);
 }
 
 u32 sort_tiles(u64 n) { return (u32)((n + kSortTile - 1) / kSortTile); }
@@ -477,18 +526,18 @@ void sort_keys(const SortDesc& d, cudaStream_t s, u32 host_passes) {
     }
     return;
   }
-  if (d.ntiles <= kFewTiles) {  // a few tiles: two launches per pass, one flip
+  if (d.n_cap < (1ull << 30)) {  // one sweep per pass, one histogram launch, one flip
+    if (!(host_passes & ((1u << npass) - 1u))) return;
+    cudaMemsetAsync(d.block_sums, 0, (kTotWords + 8) * sizeof(u32), s);
+    k_hist_all<<<std::min<u32>(d.ntiles, 152u * 4), kSortThreads, 0, s>>>(d, host_passes);
     int launched = 0;
     for (int p = 0; p < npass; ++p) {
       if (!((host_passes >> p) & 1u)) continue;
       ++launched;
-      k_hist_few<<<d.ntiles, kSortThreads, 0, s>>>(d, p, host_passes);
-      k_scatter_few<<<d.ntiles, kSortThreads, 0, s>>>(d, p, host_passes);
+      k_onesweep<<<d.ntiles, kSortThreads, 0, s>>>(d, p, host_passes);
     }
-    if (launched) {
-      k_flip_few<<<1, 1, 0, s>>>(d, host_passes);
-      count_launches(2ull * launched + 1);
-    }
+    k_flip_few<<<1, 1, 0, s>>>(d, host_passes);
+    count_launches(launched + 2ull);
     return;
   }
   const u64 len = 256ull * d.ntiles;

@@ -58,7 +58,7 @@ __device__ __forceinline__ u32 warp_seg_scan32(u32 x, u32* agg) {
 // (a halfword compare finds the barrier markers, a halfword minimum clamps
 // the bins).
 template <int HMODE>
-__global__ void __launch_bounds__(kInThreads) k_instr_runs(RunBatchArgs a) {
+__global__ void __launch_bounds__(kInThreads, 4) k_instr_runs(RunBatchArgs a) {
   constexpr int hist_mode = HMODE;
   extern __shared__ u32 dyn[];
   __shared__ u32 itb_small[kValSmem];
@@ -129,12 +129,17 @@ __global__ void __launch_bounds__(kInThreads) k_instr_runs(RunBatchArgs a) {
         }
         npad += (u64)(kOpsPerLane - nv);
       }
-      // bit k of bm: opcode k is a barrier marker
+      // bit k of bm: opcode k is a barrier marker. Per four opcodes: the
+      // halfword compares give 0xFFFF per marker, one byte permute keeps a
+      // byte of each, and a multiply gathers the four top bits into a nibble
       u32 bm = 0;
 #pragma unroll
+      for (int k = 0; k < kOpsPerLane / 2; k += 2) {
+        const u32 bytes = __byte_perm(__vcmpeq2(pk[k], 0xFFFFFFFFu), __vcmpeq2(pk[k + 1], 0xFFFFFFFFu), 0x7531);
+        bm |= (((bytes & 0x80808080u) * 0x00204081u) >> 28) << (2 * k);
+      }
+#pragma unroll
       for (int k = 0; k < kOpsPerLane / 2; ++k) {
-        const u32 eq = __vcmpeq2(pk[k], 0xFFFFFFFFu);  // 0xFFFF in each half holding a marker
-        bm |= ((eq & 1u) | ((eq >> 15) & 2u)) << (2 * k);
         if (hist_mode == 2) {
           const u32 lo = pk[k] & 0xFFFFu, hi = pk[k] >> 16;
           if (lo < nop) atomicAdd(&a.opc_hist[lo], 1ull);

@@ -304,11 +304,18 @@ __global__ void __launch_bounds__(kSortThreads) k_hist_all(SortDesc d, u32 host_
     if (((host_passes >> p) & 1u) && ((varying >> (d.lo_bit + 8 * p)) & 0xFFull)) act |= 1u << p;
   u32 (*hh)[256] = h[(threadIdx.x >> 6) & 3];
   const u64 stride = (u64)gridDim.x * kSortThreads;
-  for (u64 i = (u64)blockIdx.x * kSortThreads + threadIdx.x; i < n; i += stride) {
-    const u64 k = src[i] & m;
+  // eight keys per thread in flight
+  for (u64 i0 = (u64)blockIdx.x * kSortThreads + threadIdx.x; i0 < n; i0 += 8 * stride) {
+    u64 k[8];
 #pragma unroll
-    for (int p = 0; p < 8; ++p)
-      if ((act >> p) & 1u) atomicAdd(&hh[p][(u32)(k >> (d.lo_bit + 8 * p)) & 0xFFu], 1u);
+    for (int q = 0; q < 8; ++q) k[q] = i0 + q * stride < n ? src[i0 + q * stride] & m : 0ull;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (i0 + q * stride >= n) break;
+#pragma unroll
+      for (int p = 0; p < 8; ++p)
+        if ((act >> p) & 1u) atomicAdd(&hh[p][(u32)(k[q] >> (d.lo_bit + 8 * p)) & 0xFFu], 1u);
+    }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < 8 * 256; i += kSortThreads) {
@@ -344,12 +351,16 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(SortDesc d, int pass,
   const u64 m = eff_mask(d);
   u64 key[kSortItems];
   u32 rank[kSortItems];
+#pragma unroll
+  for (int k = 0; k < kSortItems; ++k) {  // every load in flight before the ranking
+    const u64 i = base + (u64)w * (32 * kSortItems) + (u64)k * 32 + lane;
+    key[k] = i < n ? src[i] : 0ull;
+  }
   // warp w ranks positions base + w*256 + k*32 + lane in that order (stable)
 #pragma unroll
   for (int k = 0; k < kSortItems; ++k) {
     const u64 i = base + (u64)w * (32 * kSortItems) + (u64)k * 32 + lane;
     const bool valid = i < n;
-    key[k] = valid ? src[i] : 0ull;
     const u32 dig = valid ? (u32)(((key[k] & m) >> shift) & 0xFF) : 256u + lane;
     const u32 peers = __match_any_sync(0xffffffffu, dig);
     const u32 before = valid ? wcnt[w][dig] : 0u;

@@ -1,15 +1,17 @@
 // Stable LSD radix sort of 64-bit keys with device-resident key counts.
 //
-// Each pass handles one 8-bit window of the key. A pass whose window holds no
-// bit that varies between keys (known from the OR and AND over all keys,
-// accumulated by the kernel that produced them) is skipped on the device, so
+// Each pass handles one 8-bit window of the key. Only bits that vary between
+// keys need ordering (known from the OR and AND over all keys, accumulated by
+// the kernel that produced them), and the device decides which passes run, so
 // the host launches a fixed sequence and never waits for a count. Three forms:
 // one tile (every pass in one block, in shared memory); fewer than 2^30 keys
 // (one-sweep passes: one launch each, the tiles' digit offsets found by a
 // bounded look-back over earlier tiles); more (reduce-then-scan passes:
 // per-tile digit counts, an exclusive scan over (digit, tile), a stable
-// scatter staged through shared memory). In every form each digit's keys
-// leave a tile as one contiguous run.
+// scatter staged through shared memory). The first two place each window at
+// the lowest bit still to be ordered; the last uses the key's bytes and skips
+// bytes without a varying bit. In every form each digit's keys leave a tile
+// as one contiguous run.
 #include <algorithm>
 #include <atomic>
 
@@ -247,14 +249,13 @@ __global__ void __launch_bounds__(kSortThreads) k_scatter(SortDesc d, int pass) 
 }
 
 // One-sweep form (sorts of more than one tile and fewer than 2^30 keys): one
-// launch counts the digits of every pass at once (k_hist_all), then one
-// launch per pass ranks each tile, publishes the tile's digit counts and finds
-// the counts of the tiles before it by decoupled look-back (each tile waits
-// only for tiles that took their tickets earlier, so every wait ends), and
-// scatters. A pass reads the buffer its parity gives -- the live buffer when
-// the sort starts, flipped by every pass that runs (launched and with a
-// varying window) -- so no pass writes `cur`; one launch at the end flips it
-// by the parity of the passes that ran.
+// launch counts the digits of every window at once (k_hist_all), then one
+// launch per window ranks each tile, publishes the tile's digit counts and
+// finds the counts of the tiles before it by decoupled look-back (each tile
+// waits only for tiles that took their tickets earlier, so every wait ends),
+// and scatters. Window p reads the buffer its parity gives (the live buffer
+// for p = 0), so no pass writes `cur`; one launch at the end flips it when
+// the number of windows is odd.
 //
 // Scratch: block_sums holds the digit totals of the eight windows (8 x 256)
 // and eight tile tickets, zeroed before the sort; counts holds two regions of
@@ -276,17 +277,26 @@ __device__ __forceinline__ void st_gpu(u32* p, u32 v) {
   asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ bool few_pass(const SortDesc& d, int pass, u32 host_passes, int* shift, int* parity) {
-  if (!gate_open(d.gate, d.gate_want)) return false;
-  const u64 varying = ((*d.key_or) ^ (*d.key_and)) & eff_mask(d);
-  int before = 0;
-  for (int q = 0; q < pass; ++q) {
-    const int sq = d.lo_bit + 8 * q;
-    if (sq < 64 && ((host_passes >> q) & 1u) && ((varying >> sq) & 0xFFull)) ++before;
+// Bits a sort must order: those that vary between keys, inside the mask and
+// inside the byte windows the host left on.
+__device__ __forceinline__ u64 sort_bits(const SortDesc& d, u32 host_passes) {
+  u64 allowed = 0;
+  for (int q = 0; q < 8 && d.lo_bit + 8 * q < 64; ++q)
+    if ((host_passes >> q) & 1u) allowed |= 0xFFull << (d.lo_bit + 8 * q);
+  return ((*d.key_or) ^ (*d.key_and)) & eff_mask(d) & allowed;
+}
+
+// Start bit of the p-th 8-bit window, or -1 past the last. Each window starts
+// at the lowest bit still to be ordered, so the windows are the fewest that
+// cover every such bit (never more than the bytes holding one), and ordering
+// them from low to high is a stable LSD sort on the bits that matter.
+__device__ __forceinline__ int window_shift(u64 bits, int p) {
+  for (int k = 0;; ++k) {
+    if (!bits) return -1;
+    const int b = __ffsll((long long)bits) - 1;
+    if (k == p) return b;
+    bits = b >= 56 ? 0ull : bits & (~0ull << (b + 8));
   }
-  *shift = d.lo_bit + 8 * pass;
-  *parity = before & 1;
-  return *shift < 64 && ((host_passes >> pass) & 1u) && ((varying >> *shift) & 0xFFull) != 0;
 }
 
 // Digit totals of every pass that will run, and the first pass's look-back region cleared.
@@ -298,10 +308,14 @@ __global__ void __launch_bounds__(kSortThreads) k_hist_all(SortDesc d, u32 host_
   const u64 n = umin64(*d.n, d.n_cap);
   const u64* src = *d.cur ? d.b : d.a;
   const u64 m = eff_mask(d);
-  const u64 varying = ((*d.key_or) ^ (*d.key_and)) & m;
-  u32 act = 0;  // passes that run
-  for (int p = 0; p < 8 && d.lo_bit + 8 * p < 64; ++p)
-    if (((host_passes >> p) & 1u) && ((varying >> (d.lo_bit + 8 * p)) & 0xFFull)) act |= 1u << p;
+  const u64 bits = sort_bits(d, host_passes);
+  int sh[8];
+  u32 act = 0;  // windows that exist
+#pragma unroll
+  for (int p = 0; p < 8; ++p) {
+    sh[p] = window_shift(bits, p);
+    if (sh[p] >= 0) act |= 1u << p;
+  }
   u32 (*hh)[256] = h[(threadIdx.x >> 6) & 3];
   const u64 stride = (u64)gridDim.x * kSortThreads;
   // eight keys per thread in flight
@@ -314,7 +328,7 @@ __global__ void __launch_bounds__(kSortThreads) k_hist_all(SortDesc d, u32 host_
       if (i0 + q * stride >= n) break;
 #pragma unroll
       for (int p = 0; p < 8; ++p)
-        if ((act >> p) & 1u) atomicAdd(&hh[p][(u32)(k[q] >> (d.lo_bit + 8 * p)) & 0xFFu], 1u);
+        if ((act >> p) & 1u) atomicAdd(&hh[p][(u32)(k[q] >> sh[p]) & 0xFFu], 1u);
     }
   }
   __syncthreads();
@@ -327,8 +341,10 @@ __global__ void __launch_bounds__(kSortThreads) k_hist_all(SortDesc d, u32 host_
 }
 
 __global__ void __launch_bounds__(kSortThreads) k_onesweep(SortDesc d, int pass, u32 host_passes) {
-  int shift, parity;
-  if (!few_pass(d, pass, host_passes, &shift, &parity)) return;
+  if (!gate_open(d.gate, d.gate_want)) return;
+  const int shift = window_shift(sort_bits(d, host_passes), pass);
+  if (shift < 0) return;
+  const int parity = pass & 1;  // windows 0 .. pass-1 ran before this one
   __shared__ u32 wcnt[kWarps][256];
   __shared__ u32 dofs[256];
   __shared__ u32 gofs[256];
@@ -429,12 +445,11 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(SortDesc d, int pass,
 }
 
 // After the passes: the live buffer is the other one when an odd number ran.
-__global__ void k_flip_few(SortDesc d, u32 host_passes) {
+__global__ void k_flip_windows(SortDesc d, u32 host_passes) {
   if (!gate_open(d.gate, d.gate_want)) return;
-  const u64 varying = ((*d.key_or) ^ (*d.key_and)) & eff_mask(d);
+  const u64 bits = sort_bits(d, host_passes);
   int ran = 0;
-  for (int q = 0; 8 * q + d.lo_bit < 64; ++q)
-    if (((host_passes >> q) & 1u) && ((varying >> (d.lo_bit + 8 * q)) & 0xFFull)) ++ran;
+  while (window_shift(bits, ran) >= 0) ++ran;
   if (ran & 1) *d.cur ^= 1u;
 }
 
@@ -454,13 +469,12 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_tile(SortDesc d, u32 host
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const u32 lt_mask = (1u << lane) - 1u;
   const u64 m = eff_mask(d);
-  const u64 varying = ((*d.key_or) ^ (*d.key_and)) & m;
+  const u64 bits = sort_bits(d, host_passes);
   int src = 0;
   bool ran = false;
-  const int passes = (64 - d.lo_bit + 7) / 8;
-  for (int p = 0; p < passes; ++p) {
-    const int shift = d.lo_bit + 8 * p;
-    if (!((host_passes >> p) & 1u) || ((varying >> shift) & 0xFFull) == 0) continue;
+  for (int p = 0; p < 8; ++p) {
+    const int shift = window_shift(bits, p);
+    if (shift < 0) break;
     for (int i = threadIdx.x; i < kWarps * 256; i += kSortThreads) (&wcnt[0][0])[i] = 0;
     __syncthreads();
     u64 key[kSortItems];
@@ -537,18 +551,15 @@ void sort_keys(const SortDesc& d, cudaStream_t s, u32 host_passes) {
     }
     return;
   }
-  if (d.n_cap < (1ull << 30)) {  // one sweep per pass, one histogram launch, one flip
-    if (!(host_passes & ((1u << npass) - 1u))) return;
+  if (d.n_cap < (1ull << 30)) {  // one sweep per window, one histogram launch, one flip
+    // at most one window per byte the host left on; the device finds how many there are
+    const int windows = __builtin_popcount(host_passes & ((1u << npass) - 1u));
+    if (!windows) return;
     cudaMemsetAsync(d.block_sums, 0, (kTotWords + 8) * sizeof(u32), s);
     k_hist_all<<<std::min<u32>(d.ntiles, 152u * 4), kSortThreads, 0, s>>>(d, host_passes);
-    int launched = 0;
-    for (int p = 0; p < npass; ++p) {
-      if (!((host_passes >> p) & 1u)) continue;
-      ++launched;
-      k_onesweep<<<d.ntiles, kSortThreads, 0, s>>>(d, p, host_passes);
-    }
-    k_flip_few<<<1, 1, 0, s>>>(d, host_passes);
-    count_launches(launched + 2ull);
+    for (int p = 0; p < windows; ++p) k_onesweep<<<d.ntiles, kSortThreads, 0, s>>>(d, p, host_passes);
+    k_flip_windows<<<1, 1, 0, s>>>(d, host_passes);
+    count_launches(windows + 2ull);
     return;
   }
   const u64 len = 256ull * d.ntiles;

@@ -69,7 +69,6 @@ struct DevState {
   u32 pad2;
   u64 sb_used[2];        // occupied superblock slots: below / at or above the wide-block threshold
   u64 n_spill;           // hash plan: events whose superblock the table could not place
-  u64 br_sort_mask;      // bits the branch sort must order (site only when work-items arrive sorted)
   u64 br_site_max;       // longest per-site outcome sequence
   u64 n_sites;           // entries of the site list
   u64 n_long;            // sites longer than kSiteMaxLen (counted in chunks by the per-site path)
@@ -145,6 +144,10 @@ struct Result {
   u32 err;         // DevState::err at finalisation
   u32 pad;
 };
+// A handle keeps its opcode histogram right after its result (device and
+// host alike), so that one copy brings both back.
+constexpr size_t kHistOffset = (sizeof(Result) + 255) & ~size_t(255);
+inline size_t result_bytes(u32 n_opcodes) { return kHistOffset + (size_t)n_opcodes * 8; }
 
 // A radix sort over 64-bit keys held in a ping-pong pair (a, b); the live
 // buffer is b when *cur is 1. Only bits in `mask` that vary between keys are
@@ -161,6 +164,7 @@ struct SortDesc {
   const u64* key_and{}; // device AND over keys
   u64 mask{};
   const u64* dmask{}; // optional device mask, ANDed with mask (NULL = none)
+  const u32* unsorted{};  // branch words: the site bits alone when *unsorted == 0, else every bit but the outcome
   int lo_bit{};
   u32* counts{};      // sort_counts_words(n_cap) words: digit counts, or the one-sweep look-back words
   u32* block_sums{};  // sort_block_sums_words(n_cap) words: scan sums, or digit totals and tile tickets
@@ -390,7 +394,6 @@ void launch_persite_decide(Arena* arena, u32 h, u64 sites_cap, u64 long_cap, int
 void launch_site_patterns(const SiteArgs& a, cudaStream_t s);
 // The long sites of the per-site path: list and clear, count chunks, walk the tables.
 void launch_site_long(const SiteArgs& a, cudaStream_t s);
-void launch_branch_mask(Arena* arena, cudaStream_t s);
 
 // Cross-tile fix-up of run lengths. kind: 0 = memory levels, 1 = sites, 2 = patterns.
 // h: history length (kind 1, the site runs: each site predicts len - h outcomes).
@@ -441,6 +444,11 @@ void launch_opcode_dist(const u64* hist, u32 n_opcodes, u64* over, u64 over_cap,
 void launch_wi_count(const u32* bitmap, Arena* arena, cudaStream_t s);
 void launch_wi_clear(u32* bitmap, Arena* arena, cudaStream_t s);
 void launch_reset_identities(Arena* arena, cudaStream_t s);
+// Opcode distribution and work-item count in one launch; the counted bitmap words are cleared.
+void launch_tail_counts(const u64* hist, u32 n_opcodes, u32* bitmap, u64* over, u64 over_cap, Arena* arena,
+                        cudaStream_t s);
+// Arena (with the identities), opcode histogram and sbt_words words of the superblock table to their start.
+void launch_reset(Arena* arena, u64* hist, u32 n_opcodes, u64* sbt, u64 sbt_words, cudaStream_t s);
 
 struct FinalizeArgs {
   const u64* over_a{};

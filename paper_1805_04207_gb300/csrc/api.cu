@@ -540,12 +540,12 @@ void release(aiwc_handle* h, DevBuf& b) {
   b.cap = 0;
 }
 
-aiwc_status reset_device_state(aiwc_handle* h, cudaStream_t st) {
-  if (h->wi_bitmap) launch_wi_clear(h->wi_bitmap, h->arena, st);
-  CK(cudaMemsetAsync(h->d_hist, 0, (size_t)h->cfg.n_opcodes * 8, st));
-  CK(cudaMemsetAsync(h->arena, 0, sizeof(Arena), st));
-  if (h->sbt.p) CK(cudaMemsetAsync(h->sbt.p, 0, kSbtClearBytes * h->sbt_cap, st));
-  launch_reset_identities(h->arena, st);
+// The device state back to the start of an invocation. clear_bitmap: the
+// work-item bitmap may hold marks (a finalisation counts and clears it).
+aiwc_status reset_device_state(aiwc_handle* h, cudaStream_t st, bool clear_bitmap) {
+  if (clear_bitmap && h->wi_bitmap) launch_wi_clear(h->wi_bitmap, h->arena, st);
+  launch_reset(h->arena, (u64*)h->d_hist, h->cfg.n_opcodes, h->sbt.p ? (u64*)h->sbt.p : nullptr,
+               h->sbt.p ? kSbtClearBytes * h->sbt_cap / 8 : 0, st);
   CK(cudaGetLastError());
   return AIWC_OK;
 }
@@ -804,17 +804,18 @@ aiwc_status aiwc_create(const aiwc_config* cfg, aiwc_handle** out) {
         (e = cudaEventCreateWithFlags(&h->ev_free[i], cudaEventDisableTiming)) != cudaSuccess)
       return bail(cuda_fail(nullptr, "cudaEventCreate", e));
   }
+  // the opcode histogram follows the result, on the device and on the host
   if ((e = cudaMalloc(&h->arena, sizeof(Arena))) != cudaSuccess ||
-      (e = cudaMalloc(&h->d_result, sizeof(Result))) != cudaSuccess ||
-      (e = cudaMalloc(&h->d_hist, (size_t)cfg->n_opcodes * 8)) != cudaSuccess ||
-      (e = cudaMallocHost(&h->h_result, sizeof(Result))) != cudaSuccess ||
-      (e = cudaMallocHost(&h->h_hist, (size_t)cfg->n_opcodes * 8)) != cudaSuccess ||
+      (e = cudaMalloc(&h->d_result, result_bytes(cfg->n_opcodes))) != cudaSuccess ||
+      (e = cudaMallocHost(&h->h_result, result_bytes(cfg->n_opcodes))) != cudaSuccess ||
       (e = cudaMallocHost(&h->h_state, sizeof(DevState))) != cudaSuccess)
     return bail(cuda_fail(nullptr, "allocation", e));
-  h->bytes = sizeof(Arena) + sizeof(Result) + (size_t)cfg->n_opcodes * 8;
+  h->d_hist = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(h->d_result) + kHistOffset);
+  h->h_hist = reinterpret_cast<uint64_t*>(reinterpret_cast<char*>(h->h_result) + kHistOffset);
+  h->bytes = sizeof(Arena) + result_bytes(cfg->n_opcodes);
   init_branch_attributes();
   init_instr_attributes();
-  if (reset_device_state(h, h->stream) != AIWC_OK) return bail(fail(nullptr, AIWC_ECUDA, h->err));
+  if (reset_device_state(h, h->stream, true) != AIWC_OK) return bail(fail(nullptr, AIWC_ECUDA, h->err));
   if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return bail(cuda_fail(nullptr, "initial reset", e));
   *out = h;
   return AIWC_OK;
@@ -1279,7 +1280,7 @@ SortDesc sort_desc(aiwc_handle* h, DevBuf& a, DevBuf& b, int slot, const u64* n_
 SortDesc branch_sort_desc(aiwc_handle* h) {
   DevState* dst = &h->arena->st;
   SortDesc d = sort_desc(h, h->br_a, h->br_b, kSortBranch, &dst->n_branch, &dst->br_or, &dst->br_and, ~1ull, h->n_br);
-  d.dmask = &dst->br_sort_mask;
+  d.unsorted = &dst->br_unsorted;
   return d;
 }
 
@@ -1335,7 +1336,6 @@ void enqueue_part1(aiwc_handle* h, cudaStream_t st, const Plan& p) {
   SortDesc bsort = branch_sort_desc(h);
   {
     StageScope sc(h, kStBrSort, st);
-    launch_branch_mask(h->arena, st);
     sort_keys(bsort, st, p.br_passes);
   }
   StageScope sc(h, kStWindows, st);
@@ -1536,8 +1536,7 @@ aiwc_status enqueue_finalize(aiwc_handle* h, cudaStream_t st) {
   const u64 over_cap = h->c_over_cap;
   {
     StageScope fin_scope(h, kStFinalize, st);
-    launch_opcode_dist((const u64*)h->d_hist, h->cfg.n_opcodes, over, over_cap, h->arena, st);
-    launch_wi_count(h->wi_bitmap, h->arena, st);
+    launch_tail_counts((const u64*)h->d_hist, h->cfg.n_opcodes, h->wi_bitmap, over, over_cap, h->arena, st);
     // Outside a graph capture the overflow list is complete here: one
     // synchronisation sizes its sort by the entries it holds (a few thousand
     // where the bound is millions) and runs only the passes whose digits vary.
@@ -1569,9 +1568,9 @@ aiwc_status enqueue_finalize(aiwc_handle* h, cudaStream_t st) {
     launch_finalize(fa, st);
   }
   CK(cudaGetLastError());
-  CK(cudaMemcpyAsync(h->h_result, h->d_result, sizeof(Result), cudaMemcpyDeviceToHost, st));
-  CK(cudaMemcpyAsync(h->h_hist, h->d_hist, (size_t)h->cfg.n_opcodes * 8, cudaMemcpyDeviceToHost, st));
-  return reset_device_state(h, st);
+  // the result and the opcode histogram after it: one copy
+  CK(cudaMemcpyAsync(h->h_result, h->d_result, result_bytes(h->cfg.n_opcodes), cudaMemcpyDeviceToHost, st));
+  return reset_device_state(h, st, false);
 }
 
 void reset_host(aiwc_handle* h) {
@@ -1612,7 +1611,8 @@ aiwc_status recover(aiwc_handle* h) {
   for (auto& pb : h->parts) pb.clear();
   cudaStreamSynchronize(h->side_stream);
   cudaGetLastError();
-  if (reset_device_state(h, h->stream) == AIWC_OK && cudaStreamSynchronize(h->stream) == cudaSuccess) h->broken = false;
+  if (reset_device_state(h, h->stream, true) == AIWC_OK && cudaStreamSynchronize(h->stream) == cudaSuccess)
+    h->broken = false;
   return AIWC_ESTATE;
 }
 
@@ -1990,10 +1990,8 @@ aiwc_status aiwc_destroy(aiwc_handle* h) {
   if (h->total) cudaFree(h->total);
   if (h->wi_bitmap) cudaFree(h->wi_bitmap);
   if (h->arena) cudaFree(h->arena);
-  if (h->d_result) cudaFree(h->d_result);
-  if (h->d_hist) cudaFree(h->d_hist);
+  if (h->d_result) cudaFree(h->d_result);  // the histograms live in the same allocations
   if (h->h_result) cudaFreeHost(h->h_result);
-  if (h->h_hist) cudaFreeHost(h->h_hist);
   if (h->h_state) cudaFreeHost(h->h_state);
   if (h->h_exp) cudaFreeHost(h->h_exp);
   for (int i = 0; i < 2; ++i) {
@@ -2072,7 +2070,7 @@ aiwc_status shard_capture(aiwc_handle* h) {
   CK(cudaMemcpy(b, h->d_hist, 8ull * hd.n_opcodes, cudaMemcpyDeviceToHost));
   b += 8ull * hd.n_opcodes;
   if (hd.wi_words) CK(cudaMemcpy(b, h->wi_bitmap + hd.wi_word0, 4 * hd.wi_words, cudaMemcpyDeviceToHost));
-  if ((s = reset_device_state(h, st)) != AIWC_OK) return s;
+  if ((s = reset_device_state(h, st, true)) != AIWC_OK) return s;
   CK(cudaStreamSynchronize(st));
   collect_stage_times(h);
   reset_host(h);

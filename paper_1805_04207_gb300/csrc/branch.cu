@@ -109,14 +109,6 @@ __global__ void __launch_bounds__(kBrThreads, 4) k_branch_ingest(BranchIngestArg
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&st->n_branch, a.n);
 }
 
-// Bits the branch sort orders: the site alone when work-item ids arrived in
-// non-decreasing order (a stable sort then keeps (work-item, program order)
-// inside each site); otherwise site and work-item (bit 0, the outcome, never).
-__global__ void k_branch_mask(Arena* arena) {
-  DevState* st = &arena->st;
-  st->br_sort_mask = st->br_unsorted ? ~1ull : 0xFFFFFFFF00000000ull;
-}
-
 // Sites longer than kSiteMaxLen are counted in chunks when the long-site
 // tables hold them all (and their 32-bit counters cannot overflow).
 __global__ void k_persite_decide(Arena* arena, u32 h, u64 sites_cap, u64 long_cap, int allow) {
@@ -940,11 +932,6 @@ void launch_site_sort_scatter(const SiteSortArgs& a, cudaStream_t s) {
   const unsigned g = (unsigned)std::min<u64>(cs_tiles(a.n), (u64)a.sm_count * 2);
   if (a.dst8) k_cs_scatter<true><<<g, kCsThreads, kCsScatterSmem, s>>>(a);
   else k_cs_scatter<false><<<g, kCsThreads, kCsScatterSmem, s>>>(a);
-  count_launches(1);
-}
-
-void launch_branch_mask(Arena* arena, cudaStream_t s) {
-  k_branch_mask<<<1, 1, 0, s>>>(arena);
   count_launches(1);
 }
 

@@ -60,6 +60,76 @@ __global__ void k_wi_clear(u32* bitmap, Arena* arena) {
     bitmap[w] = 0u;
 }
 
+static_assert(sizeof(DevState) % 8 == 0 && sizeof(Arena) % 8 == 0, "the reset clears whole words");
+
+// The end of an invocation's reductions in one launch: the first blocks take
+// the opcode distribution (as k_opcode_dist), every block counts the
+// work-item bitmap words in [wi_min, wi_max] and clears them behind it (the
+// bitmap is read by nothing after the count).
+__global__ void __launch_bounds__(256) k_tail_counts(const u64* hist, u32 n_opcodes, u32 op_blocks, u32* bitmap,
+                                                     u64* over, u64 cap, Arena* arena) {
+  __shared__ u64 red64[32];
+  DevState* st = &arena->st;
+  if (blockIdx.x < op_blocks) {
+    u64 uniq = 0, tot = 0;
+    for (u32 o = blockIdx.x * blockDim.x + threadIdx.x; o < n_opcodes; o += op_blocks * blockDim.x) {
+      const u64 c = hist[o];
+      if (c) {
+        ++uniq;
+        tot += c;
+        if (c < (u64)kCocDense) atomicAdd(&arena->opc_coc[c], 1ull);
+        else overflow_append(over, cap, st, kTagOpcodes, c);
+      }
+    }
+    uniq = block_reduce(uniq, OpAdd(), 0ull, red64);
+    tot = block_reduce(tot, OpAdd(), 0ull, red64);
+    if (threadIdx.x == 0) {
+      if (uniq) atomicAdd(&st->unique_opcodes, uniq);
+      if (tot) atomicAdd(&st->total_instructions, tot);
+    }
+  }
+  const u32 lo = st->wi_min, hi = st->wi_max;
+  u64 c = 0;
+  if (bitmap && lo <= hi) {
+    const u64 w0 = lo >> 5, w1 = hi >> 5;
+    for (u64 w = w0 + (u64)blockIdx.x * blockDim.x + threadIdx.x; w <= w1; w += (u64)gridDim.x * blockDim.x) {
+      c += __popc(bitmap[w]);
+      bitmap[w] = 0u;
+    }
+  }
+  c = block_reduce(c, OpAdd(), 0ull, red64);
+  if (threadIdx.x == 0 && c) atomicAdd(&st->work_items, c);
+}
+
+// A handle's device state back to the start of an invocation in one launch:
+// the arena zeroed (block 0 takes the counters and then sets the AND
+// accumulators and minima to their identities), the opcode histogram and the
+// superblock table's keys and counters zeroed.
+__global__ void __launch_bounds__(256) k_reset(Arena* arena, u64* hist, u32 n_opcodes, u64* sbt, u64 sbt_words) {
+  if (blockIdx.x == 0) {
+    u64* sw = reinterpret_cast<u64*>(&arena->st);
+    for (u32 i = threadIdx.x; i < sizeof(DevState) / 8; i += blockDim.x) sw[i] = 0ull;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      DevState* st = &arena->st;
+      st->mem_and = ~0ull;
+      st->br_and = ~0ull;
+      st->pat_and = ~0ull;
+      st->run_and = ~0ull;
+      st->over_and = ~0ull;
+      st->wi_min = 0xFFFFFFFFu;
+      st->wi_max = 0u;
+    }
+    return;
+  }
+  const u64 tid = (u64)(blockIdx.x - 1) * blockDim.x + threadIdx.x, nt = (u64)(gridDim.x - 1) * blockDim.x;
+  u64* rest = reinterpret_cast<u64*>(arena) + sizeof(DevState) / 8;
+  const u64 rest_words = (sizeof(Arena) - sizeof(DevState)) / 8;
+  for (u64 i = tid; i < rest_words; i += nt) rest[i] = 0ull;
+  for (u64 i = tid; i < n_opcodes; i += nt) hist[i] = 0ull;
+  for (u64 i = tid; i < sbt_words; i += nt) sbt[i] = 0ull;
+}
+
 __global__ void k_identities(Arena* arena) {
   DevState* st = &arena->st;
   st->mem_and = ~0ull;
@@ -550,6 +620,18 @@ void launch_opcode_dist(const u64* hist, u32 n_opcodes, u64* over, u64 over_cap,
   unsigned blocks = (n_opcodes + 255) / 256;
   if (blocks > 64) blocks = 64;
   k_opcode_dist<<<blocks, 256, 0, s>>>(hist, n_opcodes, over, over_cap, arena);
+  count_launches(1);
+}
+
+void launch_tail_counts(const u64* hist, u32 n_opcodes, u32* bitmap, u64* over, u64 over_cap, Arena* arena,
+                        cudaStream_t s) {
+  const u32 op_blocks = std::max<u32>(1u, std::min<u32>((n_opcodes + 255) / 256, 64u));
+  k_tail_counts<<<152 * 2, 256, 0, s>>>(hist, n_opcodes, op_blocks, bitmap, over, over_cap, arena);
+  count_launches(1);
+}
+
+void launch_reset(Arena* arena, u64* hist, u32 n_opcodes, u64* sbt, u64 sbt_words, cudaStream_t s) {
+  k_reset<<<1 + 152 * 2, 256, 0, s>>>(arena, hist, n_opcodes, sbt, sbt_words);
   count_launches(1);
 }
 

@@ -36,7 +36,12 @@ constexpr int kScanThreads = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanBlock = kScanThreads * kScanItems;
 
-__device__ __forceinline__ u64 eff_mask(const SortDesc& d) { return d.dmask ? (d.mask & *d.dmask) : d.mask; }
+__device__ __forceinline__ u64 eff_mask(const SortDesc& d) {
+  u64 m = d.dmask ? (d.mask & *d.dmask) : d.mask;
+  // work-item ids in push order: a stable sort by site keeps (work-item, program order)
+  if (d.unsorted) m &= *d.unsorted ? ~1ull : 0xFFFFFFFF00000000ull;
+  return m;
+}
 
 // Tiles holding keys: the device count decides, so that a sort sized for a
 // capacity (the overflow list, the pattern words) works on what is there. The

@@ -254,7 +254,9 @@ aiwc_status aiwc_push_widths(aiwc_handle* h, const uint16_t* widths, size_t n, i
  * then resets the handle for the next invocation. Blocks until done.
  * Errors: AIWC_EINVAL (invalid event data: an address >= 2^61 or an opcode
  * >= n_opcodes that is not AIWC_BARRIER, a run past its opcode array, a
- * work-item >= max_work_items), AIWC_ECUDA, AIWC_ESTATE. */
+ * work-item >= max_work_items), AIWC_ECUDA, AIWC_ESTATE, AIWC_ETIMEOUT (a radix
+ * sort pass gave up its bounded wait for an earlier tile's digit counts; valid
+ * launches always finish those waits). */
 aiwc_status aiwc_compute(aiwc_handle* h, aiwc_metrics* out);
 
 /* Several invocations at once: outs[i] receives the metrics of hs[i], exactly

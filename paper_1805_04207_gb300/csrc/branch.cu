@@ -163,22 +163,7 @@ __global__ void __launch_bounds__(kCsThreads) k_cs_count(SiteSortArgs a) {
     __syncthreads();
     const u64 base = t * kCsTile;
     const u64 end = umin64(a.n, base + kCsTile);
-    // warps take 32 consecutive events at a time, four groups in flight; the
-    // lanes of one site add their count with one atomic
-    const int lane = threadIdx.x & 31;
-    for (u64 i0 = base + (threadIdx.x & ~31u); i0 < end; i0 += 4 * kCsThreads) {
-      u32 site[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const u64 i = i0 + (u64)q * kCsThreads + lane;
-        site[q] = i < end ? (u32)(a.src[i] >> 32) : (0xFFFFF000u | (u32)lane);
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const u32 peers = __match_any_sync(0xffffffffu, site[q]);
-        if (site[q] < kCsSites && lane == __ffs(peers) - 1) atomicAdd(&hist[site[q]], (u32)__popc(peers));
-      }
-    }
+    for (u64 i = base + threadIdx.x; i < end; i += kCsThreads) atomicAdd(&hist[(u32)(a.src[i] >> 32)], 1u);
     __syncthreads();
     uint4* out = reinterpret_cast<uint4*>(a.counts + t * kCsSites);
     for (int i = threadIdx.x; i < (int)kCsSites / 4; i += kCsThreads)
@@ -325,20 +310,18 @@ __global__ void __launch_bounds__(kCsThreads) k_cs_scatter(SiteSortArgs a) {
     __syncthreads();
     const u64 w0 = t * kCsTile + (u64)wp * kCsWarpEvents;
     const u64 w1 = umin64(a.n, w0 + kCsWarpEvents);
-    // this warp's count per site: the lanes of one site add theirs with one
-    // atomic, four groups of 32 events in flight
-    for (u64 i0 = w0; i0 < w1; i0 += 128) {
-      u32 st4[4];
+    {
+      u64 i = w0 + lane;
+      for (; i + 96 < w1; i += 128) {  // four loads in flight
+        u32 st4[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const u64 i = i0 + 32 * q + lane;
-        st4[q] = i < w1 ? (u32)(a.src[i] >> 32) : (0xFFFFF000u | (u32)lane);
+        for (int q = 0; q < 4; ++q) st4[q] = (u32)(a.src[i + 32 * q] >> 32);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) atomicAdd(&wc[wp][st4[q] >> 1], 1u << ((st4[q] & 1u) * 16));
       }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const u32 peers = __match_any_sync(0xffffffffu, st4[q]);
-        if (st4[q] < kCsSites && lane == __ffs(peers) - 1)
-          atomicAdd(&wc[wp][st4[q] >> 1], (u32)__popc(peers) << ((st4[q] & 1u) * 16));
+      for (; i < w1; i += 32) {
+        const u32 site = (u32)(a.src[i] >> 32);
+        atomicAdd(&wc[wp][site >> 1], 1u << ((site & 1u) * 16));
       }
     }
     __syncthreads();

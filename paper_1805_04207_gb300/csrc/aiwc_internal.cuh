@@ -288,6 +288,7 @@ struct BranchIngestArgs {
   const void* ev{};
   u64 n{};
   u64* words{};
+  uint16_t* compact{};   // out: site << 1 | taken per event (sites below kCsSites; 0xFFFF otherwise)
   u64 word_base{};
   u32* wi_bitmap{};
   u64 max_wi{};
@@ -364,6 +365,7 @@ struct SiteArgs {
 constexpr u32 kCsSites = 4096;
 struct SiteSortArgs {
   const u64* src{};      // branch words in push order
+  const uint16_t* src16{};  // the same events as site << 1 | taken (read when only sites and outcomes are needed)
   u64* dst{};            // out: words sorted by site (stable), or
   uint8_t* dst8{};       // out: just their outcome bits, one byte each (the per-site path reads no more)
   u32* sort_cur{};       // set to 1: dst is the live buffer

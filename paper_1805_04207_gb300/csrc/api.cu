@@ -121,6 +121,7 @@ struct aiwc_handle {
   u64 max_wi = 0;
   size_t bytes = 0;
   DevBuf mem_a, mem_b, br_a, br_b, pat_a, pat_b, rk_a, rk_b, run_sum, over_a, over_b, counts, bsums, tiles;
+  DevBuf br_c;                  // branch events as site << 1 | taken, two bytes each (the site counting sort reads these)
   DevBuf stage[2];
   DevBuf desc;
   // byte-granular addresses: the tile offsets and byte counts of a batch of chunks
@@ -971,10 +972,12 @@ aiwc_status aiwc_push_branch(aiwc_handle* h, const aiwc_branch_event* ev, size_t
   if ((s = flush_deferred(h)) != AIWC_OK) return s;
   if (routing(h)) return routed(h, [&] { return route_branch(h, ev, n, on_device); });
   ENSURE(h->br_a, (h->n_br + n) * 8, true);
+  ENSURE(h->br_c, (h->n_br + n) * 2, true);
   if ((s = ensure_bitmap(h)) != AIWC_OK) return s;
   BranchIngestArgs a;
   a.push_index = h->br_pushes;
   a.words = (u64*)h->br_a.p;
+  a.compact = (uint16_t*)h->br_c.p;
   a.wi_bitmap = h->wi_bitmap;
   a.max_wi = h->max_wi;
   a.arena = h->arena;
@@ -1311,6 +1314,7 @@ SiteArgs site_args(aiwc_handle* h, const SortDesc& bsort) {
 SiteSortArgs site_sort_args(aiwc_handle* h) {
   SiteSortArgs ss;
   ss.src = (const u64*)h->br_a.p;
+  ss.src16 = (const uint16_t*)h->br_c.p;
   ss.dst = (u64*)h->br_b.p;
   ss.sort_cur = &h->arena->st.sort_cur[kSortBranch];
   ss.n = h->n_br;
@@ -1982,7 +1986,7 @@ aiwc_status aiwc_destroy(aiwc_handle* h) {
   DeviceGuard g(h->cfg.device);
   if (h->stream || h->copy_stream) cudaStreamSynchronize(h->stream);
   if (h->side_stream) cudaStreamSynchronize(h->side_stream);
-  DevBuf* bufs[] = {&h->mem_a, &h->mem_b, &h->br_a, &h->br_b, &h->pat_a, &h->pat_b, &h->rk_a, &h->rk_b,
+  DevBuf* bufs[] = {&h->mem_a, &h->mem_b, &h->br_a, &h->br_b, &h->br_c, &h->pat_a, &h->pat_b, &h->rk_a, &h->rk_b,
                     &h->run_sum, &h->over_a, &h->over_b, &h->counts, &h->bsums, &h->tiles, &h->stage[0],
                     &h->stage[1], &h->desc, &h->sbt, &h->sbt_scan, &h->sites, &h->over_total,
                     &h->exp_meta, &h->shard_tmp};

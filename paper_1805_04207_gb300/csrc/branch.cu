@@ -81,6 +81,9 @@ __global__ void __launch_bounds__(kBrThreads, 4) k_branch_ingest(BranchIngestArg
         if (i == a.n - 1) st->br_last_wi[a.push_index & 1] = wi;
         const u64 w = ((u64)e[k].x << 32) | ((u64)wi << 1) | (u64)(e[k].y >> 31);
         a.words[a.word_base + i] = w;
+        // the counting sort by site reads two bytes per event instead of eight
+        if (a.compact)
+          a.compact[a.word_base + i] = e[k].x < kCsSites ? (uint16_t)((e[k].x << 1) | (e[k].y >> 31)) : (uint16_t)0xFFFFu;
         wor |= w;
         wand &= w;
         if ((u64)wi < a.max_wi) {
@@ -163,7 +166,8 @@ __global__ void __launch_bounds__(kCsThreads) k_cs_count(SiteSortArgs a) {
     __syncthreads();
     const u64 base = t * kCsTile;
     const u64 end = umin64(a.n, base + kCsTile);
-    for (u64 i = base + threadIdx.x; i < end; i += kCsThreads) atomicAdd(&hist[(u32)(a.src[i] >> 32)], 1u);
+    for (u64 i = base + threadIdx.x; i < end; i += kCsThreads)
+      atomicAdd(&hist[a.src16 ? (u32)(a.src16[i] >> 1) : (u32)(a.src[i] >> 32)], 1u);
     __syncthreads();
     uint4* out = reinterpret_cast<uint4*>(a.counts + t * kCsSites);
     for (int i = threadIdx.x; i < (int)kCsSites / 4; i += kCsThreads)
@@ -315,12 +319,12 @@ __global__ void __launch_bounds__(kCsThreads) k_cs_scatter(SiteSortArgs a) {
       for (; i + 96 < w1; i += 128) {  // four loads in flight
         u32 st4[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) st4[q] = (u32)(a.src[i + 32 * q] >> 32);
+        for (int q = 0; q < 4; ++q) st4[q] = OUT8 ? (u32)(a.src16[i + 32 * q] >> 1) : (u32)(a.src[i + 32 * q] >> 32);
 #pragma unroll
         for (int q = 0; q < 4; ++q) atomicAdd(&wc[wp][st4[q] >> 1], 1u << ((st4[q] & 1u) * 16));
       }
       for (; i < w1; i += 32) {
-        const u32 site = (u32)(a.src[i] >> 32);
+        const u32 site = OUT8 ? (u32)(a.src16[i] >> 1) : (u32)(a.src[i] >> 32);
         atomicAdd(&wc[wp][site >> 1], 1u << ((site & 1u) * 16));
       }
     }
@@ -343,7 +347,8 @@ __global__ void __launch_bounds__(kCsThreads) k_cs_scatter(SiteSortArgs a) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const u64 i = i0 + 32 * q + lane;
-        word[q] = i < w1 ? a.src[i] : 0ull;
+        // OUT8: the compact record in the word's place, site above bit 32 and the outcome in bit 0
+        word[q] = i < w1 ? (OUT8 ? (((u64)(a.src16[i] >> 1) << 32) | (a.src16[i] & 1u)) : a.src[i]) : 0ull;
       }
 #pragma unroll
       for (int q = 0; q < 4; ++q) {

@@ -1651,7 +1651,7 @@ void plan_from_ingest(aiwc_handle* h, Plan* p) {
   // address bits sit above the store bit of the word
   const u64 addr_or = (hs.mem_or >> 1) & ((1ull << 61) - 1);
   p->seg_shift = addr_or ? std::min(__builtin_ctzll(addr_or), 3) : 3;
-  // the counting sort's per-tile counts (n_br / 4 words or less) live in the
+  // the counting sort's per-tile counts (n_br / 8 words or less) live in the
   // pattern buffers, which hold 2 n_br words each
   p->site_sort = !p->gated && site_sort_ok(h);
 }

@@ -147,8 +147,10 @@ __global__ void __launch_bounds__(256) k_site_heads(SiteArgs a) {
 
 constexpr int kCsThreads = 256;
 constexpr int kCsWarps = kCsThreads / 32;
-constexpr int kCsWarpEvents = 2048;                     // each warp ranks a contiguous run of events
-constexpr int kCsTile = kCsWarps * kCsWarpEvents;       // 16384 events per tile
+constexpr int kCsWarpEvents = 4096;                     // each warp ranks a contiguous run of events
+constexpr int kCsTile = kCsWarps * kCsWarpEvents;       // 32768 events per tile: the per-site offsets and
+                                                        // counts a tile reads and writes cover more events
+static_assert(kCsTile < 65536, "the per-warp site counters are 16-bit halves");
 constexpr int kCsChunk = 64;                            // tiles per scan chunk
 constexpr int kCsScanThreads = 1024;
 constexpr int kCsPer = kCsSites / kCsScanThreads;       // sites per scan thread (4)
@@ -336,7 +338,7 @@ __global__ void __launch_bounds__(kCsThreads) k_cs_scatter(SiteSortArgs a) {
       for (int q = 0; q < kCsWarps; ++q) {
         const u32 c = wc[q][pr];
         wc[q][pr] = run;
-        run += c;  // both halves stay below 2^16: a tile has 16384 events
+        run += c;  // both halves stay below 2^16: a tile has 32768 events
       }
     }
     __syncthreads();

@@ -196,7 +196,8 @@ def _site_trace(seed, n, n_sites, wi_sorted=True):
 
 @pytest.mark.parametrize("n,n_sites,wi_sorted,split,h", [
     ((1 << 16) + 3, 4096, True, 1, 16),       # one ragged tile past four
-    (1_100_000 + 77, 4000, True, 3, 16),      # several scan chunks, three pushes
+    (1_100_000 + 77, 4000, True, 3, 16),      # three pushes
+    (2_200_003, 3000, True, 2, 16),           # more than one scan chunk of 64 tiles
     (300_001, 50, True, 2, 3),                # few, long sites
     (200_000, 5000, True, 1, 16),             # site ids >= 4096: radix sort
     (200_000, 1000, False, 1, 16),            # work-items out of order: radix sort

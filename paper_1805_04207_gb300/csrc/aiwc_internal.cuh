@@ -376,9 +376,11 @@ struct SiteSortArgs {
   u64 sites_cap{};
   Arena* arena{};
   int sm_count{};
+  u32 tile_shift{14};    // tiles of 2^tile_shift events (14 or 15): site_sort_tile_shift
 };
 size_t site_sort_count_words(u64 n);
 size_t site_sort_chunk_words(u64 n);
+u32 site_sort_tile_shift(u64 n, int sm_count);
 void launch_site_sort_count(const SiteSortArgs& a, cudaStream_t s);    // counts, scan, site list
 void launch_site_sort_scatter(const SiteSortArgs& a, cudaStream_t s);  // the sorted output
 

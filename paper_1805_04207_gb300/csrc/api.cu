@@ -1324,6 +1324,7 @@ SiteSortArgs site_sort_args(aiwc_handle* h) {
   ss.sites_cap = h->c_sites_cap;
   ss.arena = h->arena;
   ss.sm_count = h->sm_count;
+  ss.tile_shift = site_sort_tile_shift(h->n_br, h->sm_count);
   return ss;
 }
 

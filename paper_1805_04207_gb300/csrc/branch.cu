@@ -147,27 +147,29 @@ __global__ void __launch_bounds__(256) k_site_heads(SiteArgs a) {
 
 constexpr int kCsThreads = 256;
 constexpr int kCsWarps = kCsThreads / 32;
-constexpr int kCsWarpEvents = 4096;                     // each warp ranks a contiguous run of events
-constexpr int kCsTile = kCsWarps * kCsWarpEvents;       // 32768 events per tile: the per-site offsets and
-                                                        // counts a tile reads and writes cover more events
-static_assert(kCsTile < 65536, "the per-warp site counters are 16-bit halves");
+// Tiles of 2^tile_shift events (14 or 15; each warp ranks an eighth, a
+// contiguous run): the larger tile halves the per-site offsets and counts read
+// and written per event, the smaller keeps two tiles per SM on mid-size
+// sorts. Either stays below 2^16, the range of the per-warp site counters.
+constexpr u32 kCsMaxShift = 15;
+static_assert((1u << kCsMaxShift) < 65536, "the per-warp site counters are 16-bit halves");
 constexpr int kCsChunk = 64;                            // tiles per scan chunk
 constexpr int kCsScanThreads = 1024;
 constexpr int kCsPer = kCsSites / kCsScanThreads;       // sites per scan thread (4)
 static_assert(kCsPer == 4, "the scan reads four sites as one 16-byte vector");
 
-__host__ __device__ inline u64 cs_tiles(u64 n) { return (n + kCsTile - 1) / kCsTile; }
-__host__ __device__ inline u64 cs_chunks(u64 n) { return (cs_tiles(n) + kCsChunk - 1) / kCsChunk; }
+__host__ __device__ inline u64 cs_tiles(u64 n, u32 shift) { return (n + (1ull << shift) - 1) >> shift; }
+__host__ __device__ inline u64 cs_chunks(u64 n, u32 shift) { return (cs_tiles(n, shift) + kCsChunk - 1) / kCsChunk; }
 
 // Phase 1: per-tile site counts, counts[tile][site].
 __global__ void __launch_bounds__(kCsThreads) k_cs_count(SiteSortArgs a) {
   __shared__ u32 hist[kCsSites];
-  const u64 ntiles = cs_tiles(a.n);
+  const u64 ntiles = cs_tiles(a.n, a.tile_shift);
   for (u64 t = blockIdx.x; t < ntiles; t += gridDim.x) {
     for (int i = threadIdx.x; i < (int)kCsSites; i += kCsThreads) hist[i] = 0u;
     __syncthreads();
-    const u64 base = t * kCsTile;
-    const u64 end = umin64(a.n, base + kCsTile);
+    const u64 base = t << a.tile_shift;
+    const u64 end = umin64(a.n, base + (1ull << a.tile_shift));
     for (u64 i = base + threadIdx.x; i < end; i += kCsThreads)
       atomicAdd(&hist[a.src16 ? (u32)(a.src16[i] >> 1) : (u32)(a.src[i] >> 32)], 1u);
     __syncthreads();
@@ -185,7 +187,7 @@ constexpr int kCs2Sites = kCs2Threads * 4;                 // sites per phase-2a
 // prefixes over the chunk's tiles; chunks[chunk][site] gets the chunk total.
 // Blocks: (chunk, quarter of the sites).
 __global__ void __launch_bounds__(kCs2Threads) k_cs_scan_chunks(SiteSortArgs a) {
-  const u64 ntiles = cs_tiles(a.n), nchunks = cs_chunks(a.n);
+  const u64 ntiles = cs_tiles(a.n, a.tile_shift), nchunks = cs_chunks(a.n, a.tile_shift);
   const u32 col = blockIdx.y * (kCs2Sites / 4) + threadIdx.x;  // uint4 column
   for (u64 c = blockIdx.x; c < nchunks; c += gridDim.x) {
     uint4 run = make_uint4(0u, 0u, 0u, 0u);
@@ -210,7 +212,7 @@ __global__ void __launch_bounds__(kCs2Threads) k_cs_scan_chunks(SiteSortArgs a) 
 // Phase 2b: per site (one per thread), exclusive prefix over the chunks and
 // the site's total (in the words after the chunk rows).
 __global__ void __launch_bounds__(kCs2Threads) k_cs_scan_site_chunks(SiteSortArgs a) {
-  const u64 nchunks = cs_chunks(a.n);
+  const u64 nchunks = cs_chunks(a.n, a.tile_shift);
   const u32 site = blockIdx.x * kCs2Threads + threadIdx.x;
   u32 run = 0;
   for (u64 c0 = 0; c0 < nchunks; c0 += 8) {
@@ -233,7 +235,7 @@ __global__ void __launch_bounds__(kCsScanThreads) k_cs_scan_sites(SiteSortArgs a
   __shared__ u32 wt32[33];
   __shared__ u64 red64[32];
   DevState* st = &a.arena->st;
-  const u64 nchunks = cs_chunks(a.n);
+  const u64 nchunks = cs_chunks(a.n, a.tile_shift);
   const u32* totals = a.chunks + nchunks * kCsSites;
   u32* starts = a.chunks + (nchunks + 1) * kCsSites;
   const uint4 tv = reinterpret_cast<const uint4*>(totals)[threadIdx.x];
@@ -306,16 +308,17 @@ __global__ void __launch_bounds__(kCsThreads) k_cs_scatter(SiteSortArgs a) {
   u32* toff = csm + kCsWarps * kCsSites / 2;
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const u32 lt = (1u << lane) - 1u;
-  const u64 ntiles = cs_tiles(a.n);
+  const u64 ntiles = cs_tiles(a.n, a.tile_shift);
   for (u64 t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const u32* cc = a.chunks + (t / kCsChunk) * kCsSites;
     const u32* ct = a.counts + t * kCsSites;
-    const u32* cs = a.chunks + (cs_chunks(a.n) + 1) * kCsSites;  // site starts
+    const u32* cs = a.chunks + (cs_chunks(a.n, a.tile_shift) + 1) * kCsSites;  // site starts
     for (int i = threadIdx.x; i < (int)kCsSites; i += kCsThreads) toff[i] = cs[i] + cc[i] + ct[i];
     for (int i = threadIdx.x; i < kCsWarps * (int)kCsSites / 2; i += kCsThreads) (&wc[0][0])[i] = 0u;
     __syncthreads();
-    const u64 w0 = t * kCsTile + (u64)wp * kCsWarpEvents;
-    const u64 w1 = umin64(a.n, w0 + kCsWarpEvents);
+    const u64 warp_events = 1ull << (a.tile_shift - 3);  // kCsWarps = 8 runs per tile
+    const u64 w0 = (t << a.tile_shift) + (u64)wp * warp_events;
+    const u64 w1 = umin64(a.n, w0 + warp_events);
     {
       u64 i = w0 + lane;
       for (; i + 96 < w1; i += 128) {  // four loads in flight
@@ -338,7 +341,7 @@ __global__ void __launch_bounds__(kCsThreads) k_cs_scatter(SiteSortArgs a) {
       for (int q = 0; q < kCsWarps; ++q) {
         const u32 c = wc[q][pr];
         wc[q][pr] = run;
-        run += c;  // both halves stay below 2^16: a tile has 32768 events
+        run += c;  // both halves stay below 2^16: a tile has at most 32768 events
       }
     }
     __syncthreads();
@@ -904,12 +907,14 @@ void launch_branch_ingest(const BranchIngestArgs& a, cudaStream_t s) {
   count_launches(1);
 }
 
-size_t site_sort_count_words(u64 n) { return (size_t)(cs_tiles(n) ? cs_tiles(n) : 1) * kCsSites; }
-size_t site_sort_chunk_words(u64 n) { return (size_t)(cs_chunks(n) + 2) * kCsSites; }  // + totals, starts
+// Sized for the smaller tile, which has more of them.
+size_t site_sort_count_words(u64 n) { return (size_t)(cs_tiles(n, 14) ? cs_tiles(n, 14) : 1) * kCsSites; }
+size_t site_sort_chunk_words(u64 n) { return (size_t)(cs_chunks(n, 14) + 2) * kCsSites; }  // + totals, starts
+u32 site_sort_tile_shift(u64 n, int sm_count) { return cs_tiles(n, kCsMaxShift) >= 2ull * (u64)sm_count ? 15u : 14u; }
 
 void launch_site_sort_count(const SiteSortArgs& a, cudaStream_t s) {
   if (a.n == 0) return;
-  const u64 ntiles = cs_tiles(a.n), nchunks = cs_chunks(a.n);
+  const u64 ntiles = cs_tiles(a.n, a.tile_shift), nchunks = cs_chunks(a.n, a.tile_shift);
   k_cs_count<<<(unsigned)std::min<u64>(ntiles, (u64)a.sm_count * 8), kCsThreads, 0, s>>>(a);
   k_cs_scan_chunks<<<dim3((unsigned)nchunks, kCsSites / kCs2Sites), kCs2Threads, 0, s>>>(a);
   k_cs_scan_site_chunks<<<kCsSites / kCs2Threads, kCs2Threads, 0, s>>>(a);
@@ -919,7 +924,7 @@ void launch_site_sort_count(const SiteSortArgs& a, cudaStream_t s) {
 
 void launch_site_sort_scatter(const SiteSortArgs& a, cudaStream_t s) {
   if (a.n == 0) return;
-  const unsigned g = (unsigned)std::min<u64>(cs_tiles(a.n), (u64)a.sm_count * 2);
+  const unsigned g = (unsigned)std::min<u64>(cs_tiles(a.n, a.tile_shift), (u64)a.sm_count * 2);
   if (a.dst8) k_cs_scatter<true><<<g, kCsThreads, kCsScatterSmem, s>>>(a);
   else k_cs_scatter<false><<<g, kCsThreads, kCsScatterSmem, s>>>(a);
   count_launches(1);

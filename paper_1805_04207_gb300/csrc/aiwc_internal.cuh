@@ -444,7 +444,6 @@ struct CombineArgs {
 };
 void launch_instr_combine(const CombineArgs& a, cudaStream_t s);
 
-void launch_opcode_dist(const u64* hist, u32 n_opcodes, u64* over, u64 over_cap, Arena* arena, cudaStream_t s);
 void launch_wi_count(const u32* bitmap, Arena* arena, cudaStream_t s);
 void launch_wi_clear(u32* bitmap, Arena* arena, cudaStream_t s);
 void launch_reset_identities(Arena* arena, cudaStream_t s);

@@ -16,27 +16,6 @@ namespace {
 
 constexpr int kFinThreads = 1024;
 
-__global__ void k_opcode_dist(const u64* hist, u32 n_opcodes, u64* over, u64 cap, Arena* arena) {
-  __shared__ u64 red64[32];
-  DevState* st = &arena->st;
-  u64 uniq = 0, tot = 0;
-  for (u32 o = blockIdx.x * blockDim.x + threadIdx.x; o < n_opcodes; o += gridDim.x * blockDim.x) {
-    const u64 c = hist[o];
-    if (c) {
-      ++uniq;
-      tot += c;
-      if (c < (u64)kCocDense) atomicAdd(&arena->opc_coc[c], 1ull);
-      else overflow_append(over, cap, st, kTagOpcodes, c);
-    }
-  }
-  uniq = block_reduce(uniq, OpAdd(), 0ull, red64);
-  tot = block_reduce(tot, OpAdd(), 0ull, red64);
-  if (threadIdx.x == 0) {
-    if (uniq) atomicAdd(&st->unique_opcodes, uniq);
-    if (tot) atomicAdd(&st->total_instructions, tot);
-  }
-}
-
 __global__ void k_wi_count(const u32* bitmap, Arena* arena) {
   __shared__ u64 red64[32];
   DevState* st = &arena->st;
@@ -63,7 +42,7 @@ __global__ void k_wi_clear(u32* bitmap, Arena* arena) {
 static_assert(sizeof(DevState) % 8 == 0 && sizeof(Arena) % 8 == 0, "the reset clears whole words");
 
 // The end of an invocation's reductions in one launch: the first blocks take
-// the opcode distribution (as k_opcode_dist), every block counts the
+// the opcode distribution (unique opcodes, their total and its count-of-counts), every block counts the
 // work-item bitmap words in [wi_min, wi_max] and clears them behind it (the
 // bitmap is read by nothing after the count).
 __global__ void __launch_bounds__(256) k_tail_counts(const u64* hist, u32 n_opcodes, u32 op_blocks, u32* bitmap,
@@ -613,14 +592,6 @@ void launch_merge_partition(const Arena* part, const u64* part_over, u64 part_ca
   k_merge_over<<<152 * 2, 256, 0, s>>>(part, part_over, part_cap, total, total_over, total_cap);
   k_merge_arena<<<152 * 2, 256, 0, s>>>(part, total, part_cap, total_cap);
   count_launches(2);
-}
-
-void launch_opcode_dist(const u64* hist, u32 n_opcodes, u64* over, u64 over_cap, Arena* arena, cudaStream_t s) {
-  if (n_opcodes == 0) return;
-  unsigned blocks = (n_opcodes + 255) / 256;
-  if (blocks > 64) blocks = 64;
-  k_opcode_dist<<<blocks, 256, 0, s>>>(hist, n_opcodes, over, over_cap, arena);
-  count_launches(1);
 }
 
 void launch_tail_counts(const u64* hist, u32 n_opcodes, u32* bitmap, u64* over, u64 over_cap, Arena* arena,

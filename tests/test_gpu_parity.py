@@ -276,6 +276,27 @@ def test_long_sites_in_a_batch(P):
             c.close()
 
 
+def test_gated_branch_path_in_a_batch(P):
+    """History length 17 with more than 65,535 branch events: the per-site
+    path is not certain on the host, so the batched graph holds both branch
+    paths (and the one-sweep pattern sort) behind the device's choice; twice,
+    against the oracle."""
+    from paper_1805_04207_gb300.api import compute_batch, push_trace
+    traces = [_long_site_trace(51, 300_001, [6, 1] + [0.01] * 300, True), _site_trace(52, 90_000, 5000, False),
+              synth.tiny()]
+    expect = [oracle.compute(t, history_len=17) for t in traces]
+    chars = [P.Characterizer(n_opcodes=t.n_opcodes, history_len=17) for t in traces]
+    try:
+        for _ in range(2):
+            for c, t in zip(chars, traces):
+                push_trace(c, t.to("cuda"))
+            for g, o in zip(compute_batch(chars), expect):
+                assert_parity(g, o)
+    finally:
+        for c in chars:
+            c.close()
+
+
 @pytest.mark.parametrize("n,offset,on_device", [(0, 0, True), (1, 0, True), (4099, 1, True), (300_001, 0, False),
                                                   (1_000_003, 3, True)])
 def test_simd_widths(P, n, offset, on_device):
